@@ -1,0 +1,406 @@
+"""Plain FP64 CPU oracle of the decoupled Fourier pose search (Fast-MbyM, Sec. III-C, Alg. 1).
+
+TEST INFRASTRUCTURE ONLY. Nothing on the product path imports this module: only the
+tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference`` legs
+of ``bench.py`` may call it.  It shares no code with the CUDA library.
+
+Every function follows one step of Alg. 1 in the paper's order, in float64, with the
+numpy FFT as the only library primitive (Alg. 1 itself computes its correlations with
+FFT2d / iFFT2d).  Readings of the places where the paper is silent or ambiguous:
+
+* A1  correlations conjugate the first operand: c = iFFT(conj(FFT a) * FFT b)  (Eq. 3, 7, 8
+      define correlation; Alg. 1 prints the product without the conjugate).
+* A2  the rotation score is Eq. 7 at radial lag 0: c_theta[k] = sum_r sum_a a_f[a,r] a_g[a+k,r].
+* A3  a periodic Hann window w[n] = 0.5 - 0.5 cos(2 pi n / N), applied in stage 1 only.
+* A4  band-pass = hard radial annulus band_lo <= rho <= band_hi on the DFT grid (rho in bins).
+* A5  soft-argmax scores are z-scored (population std) before softmax(z / T); score_norm=1
+      gives the literal softmax(c / T).
+* A6  candidates are integer lags times the bin size: k in [-(n//2), n - n//2).
+* A7  zero padding to P = 2N (linear correlation), lags s in [-N/2, N/2) per axis;
+      pad_mode=1 is the N-periodic (circular) correlation.
+* A8  the source f is rotated by +theta about c = (N/2, N/2) (bilinear, zero outside); the
+      translation is then the stage-2 soft-argmax directly, so BuildSO2 / MatMul of Alg. 1
+      reduce to the identity.  theta > 0 turns +x (column) toward +y (row).
+* A9  polar angles span [0, pi) (|F| of a real image is centrosymmetric).
+* A14 |z| has derivative z/|z| (0 at z = 0); bilinear weights use the floor cell.
+
+Layouts: images are [N, N] row-major, y = row, x = column.  Score surfaces are stored in lag
+order (index 0 is the most negative lag).  The pose is (theta [rad], t_x, t_y [delta_xy units]).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+# ----------------------------------------------------------------------------------------------
+# configuration (Alg. 1 signature; defaults are the readings listed above)
+# ----------------------------------------------------------------------------------------------
+
+def make_cfg(n, n_theta, n_r, temp_theta=1.0, temp_xy=1.0, delta_xy=1.0, window=1, pad_mode=0,
+             score_norm=0, band_lo=2.0, band_hi=None):
+    """Alg. 1 parameters (n_theta, T_theta, n_xy = n, delta_xy, T_xy) plus the A3-A7 switches."""
+    return dict(n=int(n), n_theta=int(n_theta), n_r=int(n_r), temp_theta=float(temp_theta),
+                temp_xy=float(temp_xy), delta_xy=float(delta_xy), window=int(window),
+                pad_mode=int(pad_mode), score_norm=int(score_norm), band_lo=float(band_lo),
+                band_hi=float(n / 2 if band_hi is None else band_hi))
+
+
+def lags(n):
+    """Candidate integer lags of a length-n circular score vector (A6): -(n//2) ... n-1-n//2."""
+    return np.arange(n) - n // 2
+
+
+# ----------------------------------------------------------------------------------------------
+# stage 1: rotation (Alg. 1 stage 1, Eq. 4-7)
+# ----------------------------------------------------------------------------------------------
+
+def hann(n):
+    """Periodic Hann window (Alg. 1 HanningFilter; reading A3)."""
+    i = np.arange(n, dtype=np.float64)
+    return 0.5 - 0.5 * np.cos(2.0 * np.pi * i / n)
+
+
+def band_mask(n, band_lo, band_hi):
+    """Radial band-pass on the half spectrum [N, N/2+1] (Alg. 1 BandPassFilter; reading A4)."""
+    v = np.arange(n)
+    vs = np.where(v <= n // 2, v, v - n).astype(np.float64)
+    u = np.arange(n // 2 + 1, dtype=np.float64)
+    rho = np.sqrt(vs[:, None] ** 2 + u[None, :] ** 2)
+    return ((rho >= band_lo) & (rho <= band_hi)).astype(np.float64)
+
+
+def spectrum(x, cfg):
+    """Windowed 2D DFT of a real scan, half plane u in [0, N/2] (Alg. 1 FFT2d; Eq. 4).
+
+    F[v, u] = sum_y sum_x w[y] w[x] x[y, x] exp(-2 pi i (v y + u x) / N)."""
+    n = cfg["n"]
+    x = np.asarray(x, dtype=np.float64)
+    if cfg["window"]:
+        w = hann(n)
+        x = x * w[:, None] * w[None, :]
+    return np.fft.rfft2(x)
+
+
+def magnitude(F, cfg):
+    """Band-passed magnitude spectrum a = |h_band o F| on the half plane (Alg. 1 Abs; Eq. 6)."""
+    return np.abs(F) * band_mask(cfg["n"], cfg["band_lo"], cfg["band_hi"])
+
+
+def polar_points(n, n_theta, n_r):
+    """Sample points of Cart2Pol: alpha_a = a pi / n_theta, rho_r = r (N/2) / n_r (A9, A4).
+
+    Returns (u, v) arrays [n_theta, n_r]: u = rho cos(alpha) along x, v = rho sin(alpha) along y."""
+    alpha = np.arange(n_theta, dtype=np.float64) * np.pi / n_theta
+    rho = np.arange(n_r, dtype=np.float64) * (n / 2.0) / n_r
+    return rho[None, :] * np.cos(alpha)[:, None], rho[None, :] * np.sin(alpha)[:, None]
+
+
+def half_index(n, vi, ui):
+    """Map integer frequencies (vi, ui) of the N-periodic full spectrum onto the half plane.
+
+    |F| of a real image satisfies |F(-v,-u)| = |F(v,u)| (Hermitian), so a column ui > N/2 is
+    read at (-vi, -ui).  Returns index arrays into the [N, N/2+1] half spectrum."""
+    vi = np.mod(vi, n)
+    ui = np.mod(ui, n)
+    mirror = ui > n // 2
+    vv = np.where(mirror, np.mod(-vi, n), vi)
+    uu = np.where(mirror, n - ui, ui)
+    return vv, uu
+
+
+def cart2pol(a, cfg):
+    """Bilinear resampling of the magnitude spectrum onto the (angle x radius) grid (Alg. 1
+    Cart2Pol; bilinear as in the spatial transformer, Sec. III-C).  Returns [n_theta, n_r]."""
+    n = cfg["n"]
+    u, v = polar_points(n, cfg["n_theta"], cfg["n_r"])
+    x0 = np.floor(u)
+    y0 = np.floor(v)
+    fx = u - x0
+    fy = v - y0
+    x0 = x0.astype(np.int64)
+    y0 = y0.astype(np.int64)
+    out = np.zeros_like(u)
+    for dy, wy in ((0, 1.0 - fy), (1, fy)):
+        for dx, wx in ((0, 1.0 - fx), (1, fx)):
+            vv, uu = half_index(n, y0 + dy, x0 + dx)
+            out += wy * wx * a[vv, uu]
+    return out
+
+
+def angle_scores(af, ag):
+    """Circular cross-correlation along angle summed over radius (Eq. 7 with reading A2):
+    c[k] = sum_a sum_r af[a, r] ag[(a + k) mod n_theta, r] for k in lags(n_theta)."""
+    n = af.shape[0]
+    c = np.empty(n, dtype=np.float64)
+    for i, k in enumerate(lags(n)):
+        c[i] = np.sum(af * np.roll(ag, -k, axis=0))
+    return c
+
+
+def normalise_scores(c, score_norm):
+    """A5: z = (c - mean) / std (population) for score_norm=0, the raw scores for 1."""
+    c = np.asarray(c, dtype=np.float64)
+    if score_norm == 1:
+        return c.copy()
+    mu = c.mean()
+    sd = np.sqrt(np.mean((c - mu) ** 2))
+    if sd == 0.0:
+        return np.zeros_like(c)
+    return (c - mu) / sd
+
+
+def soft_argmax(c, temp, score_norm):
+    """Temperature softmax over the scores (Alg. 1 SoftArgMax; Sec. III-C).
+
+    Returns the probabilities p (same shape as c); the expectation is taken by the caller
+    over the candidate coordinates."""
+    z = normalise_scores(c, score_norm).ravel() / temp
+    z = z - z.max()
+    e = np.exp(z)
+    return (e / e.sum()).reshape(np.shape(c))
+
+
+# ----------------------------------------------------------------------------------------------
+# stage 2: translation (Alg. 1 stage 2, Eq. 8)
+# ----------------------------------------------------------------------------------------------
+
+def rotate(x, theta):
+    """Rotate a scan by +theta about c = (N/2, N/2) with bilinear sampling and zero fill
+    (Alg. 1 Rotate; reading A8).  out[Y, X] = bilinear(x, c + R(-theta) ([X, Y] - c))."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    c = n / 2.0
+    Y, X = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
+    ct, st = np.cos(theta), np.sin(theta)
+    dx, dy = X - c, Y - c
+    px = c + ct * dx + st * dy
+    py = c - st * dx + ct * dy
+    x0 = np.floor(px)
+    y0 = np.floor(py)
+    fx = px - x0
+    fy = py - y0
+    x0 = x0.astype(np.int64)
+    y0 = y0.astype(np.int64)
+    out = np.zeros_like(px)
+    for oy, wy in ((0, 1.0 - fy), (1, fy)):
+        for ox, wx in ((0, 1.0 - fx), (1, fx)):
+            yy, xx = y0 + oy, x0 + ox
+            inside = (yy >= 0) & (yy < n) & (xx >= 0) & (xx < n)
+            out += np.where(inside, wy * wx * x[np.clip(yy, 0, n - 1), np.clip(xx, 0, n - 1)], 0.0)
+    return out
+
+
+def xcorr2d(fr, g, pad_mode):
+    """Translation scores c[s] = sum_x fr(x) g(x + s), s in [-N/2, N/2)^2 (Eq. 3 and 8),
+    through the correlation theorem as in Alg. 1: ZeroPad to P = 2N, then
+    iFFT2d(conj(FFT2d(fr)) o FFT2d(g)) (A1, A7).  pad_mode=1: N-periodic correlation."""
+    n = fr.shape[0]
+    p = n if pad_mode == 1 else 2 * n
+    Fp = np.fft.fft2(np.asarray(fr, np.float64), s=(p, p))
+    Gp = np.fft.fft2(np.asarray(g, np.float64), s=(p, p))
+    full = np.real(np.fft.ifft2(np.conj(Fp) * Gp))
+    s = np.mod(lags(n), p)
+    return full[np.ix_(s, s)]
+
+
+def xcorr2d_direct(fr, g, sy, sx, pad_mode):
+    """One translation score by its definition, sum_x fr(x) g(x + s) (Eq. 3), no FFT.
+    Zero outside the scan for pad_mode=0, N-periodic for pad_mode=1."""
+    n = fr.shape[0]
+    fr = np.asarray(fr, np.float64)
+    g = np.asarray(g, np.float64)
+    if pad_mode == 1:
+        return float(np.sum(fr * np.roll(g, (-sy, -sx), axis=(0, 1))))
+    y0, y1 = max(0, -sy), min(n, n - sy)
+    x0, x1 = max(0, -sx), min(n, n - sx)
+    if y0 >= y1 or x0 >= x1:
+        return 0.0
+    return float(np.sum(fr[y0:y1, x0:x1] * g[y0 + sy:y1 + sy, x0 + sx:x1 + sx]))
+
+
+# ----------------------------------------------------------------------------------------------
+# the whole search (Alg. 1)
+# ----------------------------------------------------------------------------------------------
+
+def pose(f, g, cfg, keep=False):
+    """ScanMatch(f, g) of Alg. 1 under the readings above.
+
+    Returns dict(theta, tx, ty, c_theta [n_theta], c_xy [N, N]) and, with keep=True, every
+    intermediate the backward pass needs."""
+    n, nt = cfg["n"], cfg["n_theta"]
+    f = np.asarray(f, np.float64)
+    g = np.asarray(g, np.float64)
+    # stage 1 (Alg. 1 stage 1)
+    Ff, Fg = spectrum(f, cfg), spectrum(g, cfg)
+    af, ag = magnitude(Ff, cfg), magnitude(Fg, cfg)
+    pf, pg = cart2pol(af, cfg), cart2pol(ag, cfg)
+    c_theta = angle_scores(pf, pg)
+    p_theta = soft_argmax(c_theta, cfg["temp_theta"], cfg["score_norm"])
+    d_theta = np.pi / nt
+    theta = float(np.sum(p_theta * lags(nt) * d_theta))
+    # stage 2 (Alg. 1 stage 2)
+    fr = rotate(f, theta)
+    c_xy = xcorr2d(fr, g, cfg["pad_mode"])
+    p_xy = soft_argmax(c_xy, cfg["temp_xy"], cfg["score_norm"])
+    s = lags(n) * cfg["delta_xy"]
+    tx = float(np.sum(p_xy * s[None, :]))
+    ty = float(np.sum(p_xy * s[:, None]))
+    out = dict(theta=theta, tx=tx, ty=ty, c_theta=c_theta, c_xy=c_xy)
+    if keep:
+        out.update(Ff=Ff, Fg=Fg, af=af, ag=ag, pf=pf, pg=pg, p_theta=p_theta, fr=fr, p_xy=p_xy)
+    return out
+
+
+def pose_batch(fs, gs, cfg):
+    """Alg. 1 applied to each pair of a batch; returns (pose [B,3], c_theta [B,n_theta], c_xy [B,N,N])."""
+    res = [pose(f, g, cfg) for f, g in zip(fs, gs)]
+    P = np.array([[r["theta"], r["tx"], r["ty"]] for r in res])
+    return P, np.stack([r["c_theta"] for r in res]), np.stack([r["c_xy"] for r in res])
+
+
+# ----------------------------------------------------------------------------------------------
+# adjoint of the whole search (differentiability, Sec. III-C and III-D): hand-derived, FP64
+# ----------------------------------------------------------------------------------------------
+
+def soft_argmax_backward(c, p, q, temp, score_norm):
+    """Adjoint of E_p[coord] with p = softmax(normalise(c) / T), given q = dL/dp.
+
+    softmax: dy = p (q - <p, q>); temperature: dz = dy / T; z-score (population std):
+    dc = (dz - mean(dz) - z mean(dz z)) / std."""
+    shape = np.shape(c)
+    p = np.asarray(p, np.float64).ravel()
+    q = np.asarray(q, np.float64).ravel()
+    dz = p * (q - np.dot(p, q)) / temp
+    if score_norm == 1:
+        return dz.reshape(shape)
+    c = np.asarray(c, np.float64).ravel()
+    mu = c.mean()
+    sd = np.sqrt(np.mean((c - mu) ** 2))
+    if sd == 0.0:
+        return np.zeros(shape)
+    z = (c - mu) / sd
+    return ((dz - dz.mean() - z * np.mean(dz * z)) / sd).reshape(shape)
+
+
+def xcorr2d_backward(fr, g, dc, pad_mode):
+    """Adjoint of c[s] = sum_x fr(x) g(x + s) (Eq. 3, lags s in [-N/2, N/2)^2).
+
+    d fr(x) = sum_s dc[s] g(x + s)  (correlation of dc with g)
+    d g(y)  = sum_s dc[s] fr(y - s) (convolution of dc with fr)
+    both evaluated through the same padded transforms as the forward pass."""
+    n = fr.shape[0]
+    p = n if pad_mode == 1 else 2 * n
+    D = np.zeros((p, p))
+    s = np.mod(lags(n), p)
+    D[np.ix_(s, s)] = dc
+    Dh = np.fft.fft2(D)
+    Gh = np.fft.fft2(np.asarray(g, np.float64), s=(p, p))
+    Fh = np.fft.fft2(np.asarray(fr, np.float64), s=(p, p))
+    dfr = np.real(np.fft.ifft2(np.conj(Dh) * Gh))[:n, :n]
+    dg = np.real(np.fft.ifft2(Dh * Fh))[:n, :n]
+    return dfr, dg
+
+
+def rotate_backward(x, theta, dout):
+    """Adjoint of rotate(): d x (transpose of the bilinear gather) and d theta.
+
+    With p(X) = c + R(-theta)(X - c):  d px / d theta = py - c,  d py / d theta = -(px - c)."""
+    x = np.asarray(x, np.float64)
+    n = x.shape[0]
+    c = n / 2.0
+    Y, X = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
+    ct, st = np.cos(theta), np.sin(theta)
+    dx, dy = X - c, Y - c
+    px = c + ct * dx + st * dy
+    py = c - st * dx + ct * dy
+    x0 = np.floor(px)
+    y0 = np.floor(py)
+    fx = px - x0
+    fy = py - y0
+    x0 = x0.astype(np.int64)
+    y0 = y0.astype(np.int64)
+
+    def tap(oy, ox):
+        yy, xx = y0 + oy, x0 + ox
+        inside = (yy >= 0) & (yy < n) & (xx >= 0) & (xx < n)
+        return yy, xx, inside, np.where(inside, x[np.clip(yy, 0, n - 1), np.clip(xx, 0, n - 1)], 0.0)
+
+    t00, t01, t10, t11 = tap(0, 0), tap(0, 1), tap(1, 0), tap(1, 1)
+    dxin = np.zeros_like(x)
+    for (yy, xx, inside, _), w in ((t00, (1 - fy) * (1 - fx)), (t01, (1 - fy) * fx),
+                                   (t10, fy * (1 - fx)), (t11, fy * fx)):
+        np.add.at(dxin, (yy[inside], xx[inside]), (w * dout)[inside])
+    v00, v01, v10, v11 = t00[3], t01[3], t10[3], t11[3]
+    dv_dpx = (1 - fy) * (v01 - v00) + fy * (v11 - v10)
+    dv_dpy = (1 - fx) * (v10 - v00) + fx * (v11 - v01)
+    dtheta = float(np.sum(dout * (dv_dpx * (py - c) - dv_dpy * (px - c))))
+    return dxin, dtheta
+
+
+def angle_scores_backward(af, ag, dc):
+    """Adjoint of angle_scores(): d af[a] = sum_k dc[k] ag[a + k], d ag[b] = sum_k dc[k] af[b - k]."""
+    daf = np.zeros_like(af)
+    dag = np.zeros_like(ag)
+    for i, k in enumerate(lags(af.shape[0])):
+        daf += dc[i] * np.roll(ag, -k, axis=0)
+        dag += dc[i] * np.roll(af, k, axis=0)
+    return daf, dag
+
+
+def cart2pol_backward(dp, cfg):
+    """Transpose of the bilinear polar gather onto the [N, N/2+1] half spectrum."""
+    n = cfg["n"]
+    u, v = polar_points(n, cfg["n_theta"], cfg["n_r"])
+    x0 = np.floor(u)
+    y0 = np.floor(v)
+    fx = u - x0
+    fy = v - y0
+    x0 = x0.astype(np.int64)
+    y0 = y0.astype(np.int64)
+    da = np.zeros((n, n // 2 + 1))
+    for dy, wy in ((0, 1.0 - fy), (1, fy)):
+        for dx, wx in ((0, 1.0 - fx), (1, fx)):
+            vv, uu = half_index(n, y0 + dy, x0 + dx)
+            np.add.at(da, (vv, uu), wy * wx * dp)
+    return da
+
+
+def magnitude_backward(F, da, cfg):
+    """Adjoint of a = band |F| w.r.t. (Re F, Im F), returned as dRe + i dIm; z/|z| is 0 at z = 0."""
+    m = np.abs(F)
+    unit = np.where(m > 0, F / np.where(m > 0, m, 1.0), 0.0)
+    return da * band_mask(cfg["n"], cfg["band_lo"], cfg["band_hi"]) * unit
+
+
+def spectrum_backward(dF, cfg):
+    """Adjoint of the windowed half-plane DFT: d x[y,x] = w[y] w[x] Re sum_{v, u<=N/2} dF[v,u]
+    exp(+2 pi i (v y + u x) / N)."""
+    n = cfg["n"]
+    D = np.zeros((n, n), dtype=np.complex128)
+    D[:, : n // 2 + 1] = dF
+    dx = np.real(np.fft.ifft2(D)) * (n * n)
+    if cfg["window"]:
+        w = hann(n)
+        dx = dx * w[:, None] * w[None, :]
+    return dx
+
+
+def pose_backward(f, g, cfg, dpose):
+    """Gradient of L with respect to f and g given dL/d(theta, tx, ty) (Eq. 13 drives this in
+    training).  Recomputes the forward intermediates; the stage-2 translation depends on theta
+    through Rotate, so d theta collects the direct term and the term through the rotated source."""
+    n, nt = cfg["n"], cfg["n_theta"]
+    r = pose(f, g, cfg, keep=True)
+    dth_out, dtx, dty = (float(v) for v in dpose)
+    s = lags(n) * cfg["delta_xy"]
+    q_xy = dtx * s[None, :] + dty * s[:, None]
+    dc_xy = soft_argmax_backward(r["c_xy"], r["p_xy"], q_xy, cfg["temp_xy"], cfg["score_norm"])
+    dfr, dg = xcorr2d_backward(r["fr"], g, dc_xy, cfg["pad_mode"])
+    df, dth_rot = rotate_backward(f, r["theta"], dfr)
+    dth = dth_out + dth_rot
+    q_t = dth * lags(nt) * (np.pi / nt)
+    dc_t = soft_argmax_backward(r["c_theta"], r["p_theta"], q_t, cfg["temp_theta"], cfg["score_norm"])
+    dpf, dpg = angle_scores_backward(r["pf"], r["pg"], dc_t)
+    df = df + spectrum_backward(magnitude_backward(r["Ff"], cart2pol_backward(dpf, cfg), cfg), cfg)
+    dg = dg + spectrum_backward(magnitude_backward(r["Fg"], cart2pol_backward(dpg, cfg), cfg), cfg)
+    return df, dg, dict(dtheta_total=dth, dtheta_rot=dth_rot, dc_xy=dc_xy, dc_theta=dc_t)

@@ -1,0 +1,146 @@
+"""Seeded synthetic radar-like scan pairs (stand-in for the Oxford Radar RobotCar scans, Sec. IV-A).
+
+This module only makes inputs.  It holds none of the search's arithmetic: a scene of point
+scatterers and line "walls" is rendered analytically, once in the source frame and once in the
+target frame (Eq. 1: x' = R x + t about the image centre), so the ground-truth pose is exact to
+sub-pixel precision and neither the oracle nor the CUDA library is needed to make a target.
+
+Scene recipe (per scan pair):
+* K point scatterers at uniform continuous positions, amplitude U(5, 20);
+* W walls: centre uniform, length U(0.1 N, 0.5 N), orientation U[0, pi), sampled every 0.5 px,
+  amplitude U(2, 8);
+* every scatterer and wall sample carries an Exp(1) speckle factor (shared by both frames);
+* each element is drawn as a normalised Gaussian footprint of sigma = 0.8 px on the N-periodic
+  grid (the 3x3 blur of the recipe, evaluated analytically at the element's exact position);
+* each scan then gets its own additive |N(0, 0.3)| noise.
+
+The target carries the source scene moved by the pose (theta, t_x, t_y): an element at p in the
+source is at c + R(theta) (p - c) + t in the target, wrapped onto the N-periodic grid, with
+c = (N/2, N/2) and theta > 0 turning +x toward +y.  Random numbers come from numpy's Philox
+counter-based generator keyed by (seed, pair index); all distributions are built from uniform
+doubles so that the stream does not depend on numpy's sampling routines.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SIGMA_PX = 0.8
+FOOT = 3  # footprint half-width in pixels
+
+
+def _rng(seed, index):
+    return np.random.Generator(np.random.Philox(key=(int(seed) << 32) + int(index)))
+
+
+def _exp1(rng, size):
+    return -np.log1p(-rng.random(size))
+
+
+def _abs_normal(rng, size, sd):
+    u1 = rng.random(size)
+    u2 = rng.random(size)
+    return np.abs(sd * np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2))
+
+
+def scene(rng, n, n_points, n_walls):
+    """Element positions (x, y) and amplitudes of one random scene in the source frame."""
+    px = rng.random(n_points) * n
+    py = rng.random(n_points) * n
+    amp = 5.0 + 15.0 * rng.random(n_points)
+    xs, ys, amps = [px], [py], [amp]
+    for _ in range(n_walls):
+        cx, cy = rng.random() * n, rng.random() * n
+        length = (0.1 + 0.4 * rng.random()) * n
+        ang = rng.random() * np.pi
+        a = 2.0 + 6.0 * rng.random()
+        m = max(2, int(length / 0.5) + 1)
+        s = np.linspace(-0.5 * length, 0.5 * length, m)
+        xs.append(cx + s * math.cos(ang))
+        ys.append(cy + s * math.sin(ang))
+        amps.append(np.full(m, a))
+    x = np.concatenate(xs)
+    y = np.concatenate(ys)
+    a = np.concatenate(amps) * _exp1(rng, x.size)
+    return x, y, a
+
+
+def render(n, x, y, a):
+    """Sum of normalised Gaussian footprints on the N-periodic grid (float64 [N, N])."""
+    ix = np.floor(x).astype(np.int64)
+    iy = np.floor(y).astype(np.int64)
+    acc = np.zeros(n * n, dtype=np.float64)
+    offs = np.arange(-FOOT, FOOT + 2)
+    norm = 1.0 / (2.0 * np.pi * SIGMA_PX * SIGMA_PX)
+    for oy in offs:
+        gy = iy + oy
+        wy = np.exp(-((gy - y) ** 2) / (2 * SIGMA_PX ** 2))
+        for ox in offs:
+            gx = ix + ox
+            w = wy * np.exp(-((gx - x) ** 2) / (2 * SIGMA_PX ** 2)) * norm * a
+            idx = np.mod(gy, n) * n + np.mod(gx, n)
+            acc += np.bincount(idx, weights=w, minlength=n * n)
+    return acc.reshape(n, n)
+
+
+def move(n, x, y, theta, tx, ty):
+    """Element positions in the target frame: c + R(theta)(p - c) + t (Eq. 1 about the centre)."""
+    c = n / 2.0
+    ct, st = math.cos(theta), math.sin(theta)
+    dx, dy = x - c, y - c
+    return c + ct * dx - st * dy + tx, c + st * dx + ct * dy + ty
+
+
+def make_pair(n, n_points, n_walls, theta, tx, ty, seed, index, noise_sd=0.3):
+    """One (source, target) pair with pose (theta [rad], tx, ty [px]); float32 [N, N] each."""
+    rng = _rng(seed, index)
+    x, y, a = scene(rng, n, n_points, n_walls)
+    f = render(n, x, y, a) + _abs_normal(rng, (n, n), noise_sd)
+    x2, y2 = move(n, x, y, theta, tx, ty)
+    g = render(n, x2, y2, a) + _abs_normal(rng, (n, n), noise_sd)
+    return f.astype(np.float32), g.astype(np.float32)
+
+
+# Workloads: the scene sizes and pose ranges of the benchmark configurations.
+WORKLOADS = {
+    # 128^2, integer circular shifts, rotations on the 128-bin angle grid spacing 2 x 180/128 deg
+    "single128": dict(n=128, n_points=40, n_walls=6, n_theta=128, n_r=64, pairs=1, seed_id=1),
+    # 256^2, continuous theta ~ U(-5, 5) deg, t ~ U(-8, 8) px
+    "batch256": dict(n=256, n_points=150, n_walls=20, n_theta=400, n_r=128, pairs=256, seed_id=2,
+                     theta_deg=5.0, t_px=8.0),
+    # 512^2, theta ~ U(-8, 8) deg, t ~ U(-16, 16) px
+    "batch512": dict(n=512, n_points=400, n_walls=40, n_theta=400, n_r=256, pairs=32, seed_id=3,
+                     theta_deg=8.0, t_px=16.0),
+}
+
+SEED_BASE = 20220301
+
+
+def draw_pose(rng, spec):
+    """Ground-truth pose for one pair of a workload (see WORKLOADS)."""
+    if spec["n"] == 128 and "theta_deg" not in spec:
+        k = int(np.floor(rng.random() * 5)) - 2
+        t = np.floor(rng.random(2) * 9).astype(int) - 4
+        return k * (2.0 * np.pi / 128.0), float(t[0]), float(t[1])
+    th = math.radians(spec["theta_deg"]) * (2.0 * rng.random() - 1.0)
+    t = spec["t_px"] * (2.0 * rng.random(2) - 1.0)
+    return th, float(t[0]), float(t[1])
+
+
+def make_batch(name, pairs=None, start=0, spec=None):
+    """Pairs [start, start+pairs) of a named workload: (f [B,N,N], g [B,N,N], pose [B,3]) float32."""
+    spec = dict(WORKLOADS[name] if spec is None else spec)
+    b = spec["pairs"] if pairs is None else pairs
+    n = spec["n"]
+    seed = SEED_BASE + spec["seed_id"]
+    f = np.empty((b, n, n), np.float32)
+    g = np.empty((b, n, n), np.float32)
+    pose = np.empty((b, 3), np.float64)
+    for i in range(b):
+        idx = start + i
+        prng = _rng(seed + 1000, idx)
+        th, tx, ty = draw_pose(prng, spec)
+        f[i], g[i] = make_pair(n, spec["n_points"], spec["n_walls"], th, tx, ty, seed, idx)
+        pose[i] = (th, tx, ty)
+    return f, g, pose
