@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the decoupled Fourier pose search (Fast-MbyM Alg. 1) on one GB300 per rank.
+
+Workload (default): 32 scan pairs at 512 x 512 (polar grid 400 x 256), synthetic radar-like scans
+from paper_2203_00459_gb300.synth.  One step = one pass of the search over the batch: forward, and
+with --mode fwdbwd (default) the adjoint of the L2 pose loss as well.  Inputs stay resident in HBM;
+L2 is flushed (a 256 MB write) between timed steps, outside the timed events.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "scan-pairs/s (fwd, fwd+bwd) at 512^2 vs plain per-pair path, pose err <=1e-3px vs FP64"
+WORKLOAD = "batch512"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="fwdbwd", choices=["fwd", "fwdbwd"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic bytes and FLOPs per pair of each kernel (what the kernel must read and write)
+# ---------------------------------------------------------------------------------------------
+
+def kernel_model(n, p, nt, nr, chunks):
+    w, wp = n // 2, p // 2
+    c = 8  # bytes of a complex float
+    fft = lambda L: 5.0 * L * math.log2(L)  # nominal FLOPs of one complex length-L FFT
+    m = {
+        "s1_rows": (2 * n * n * 4 + 2 * n * w * c, 2 * (n // 2) * fft(n)),
+        "s1_cols": (2 * n * w * c + 2 * (w + 1) * n * 4, 2 * w * fft(n)),
+        "angle": (2 * (w + 1) * n * 4 + chunks * nt * c, nr * fft(nt)),
+        "theta": (chunks * nt * c + nt * 4, fft(nt)),
+        "s2_rows": (2 * n * n * 4 + 2 * n * wp * c, 2 * (n // 2) * fft(p)),
+        "s2_cols": (2 * n * wp * c + n * wp * c, 3 * wp * fft(p)),
+        "s2_c2r": (n * wp * c + n * n * 4, (n // 2) * fft(p)),
+        "sxy": (n * n * 4, 0.0),
+    }
+    return m
+
+
+# ncu dram traffic per launch (bytes) of the dominant kernel, with the hash of the sources it was
+# taken on; a traffic figure is reported only while the sources are unchanged.
+TRAFFIC = {}
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2203_00459_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle arm
+# ---------------------------------------------------------------------------------------------
+
+def _oracle_pair(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    import oracle as O
+    f, g, cfg, dpose = args
+    r = O.pose(f, g, cfg)
+    if dpose is not None:
+        O.pose_backward(f, g, cfg, np.asarray(dpose, np.float64))
+    return r["theta"]
+
+
+def oracle_rate(f, g, gt, spec, mode, pairs, pool):
+    """Pairs per second of the FP64 oracle over the first `pairs` pairs, spread over the pool."""
+    import numpy as np
+    import oracle as O
+    cfg = O.make_cfg(spec["n"], spec["n_theta"], spec["n_r"])
+    jobs = []
+    for i in range(pairs):
+        dpose = None
+        if mode == "fwdbwd":
+            dpose = [1.0, 0.5, -0.5]
+        jobs.append((f[i].astype(np.float64), g[i].astype(np.float64), cfg, dpose))
+    t0 = time.perf_counter()
+    list(pool.map(_oracle_pair, jobs))
+    return pairs / (time.perf_counter() - t0)
+
+
+def make_pool():
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def run_reference(args, spec, rank):
+    from paper_2203_00459_gb300 import synth
+    if rank != 0:
+        return
+    pool, cores = make_pool()
+    pairs = min(spec["pairs"], cores)
+    f, g, gt = synth.make_batch(args.workload, pairs=pairs)
+    for _ in range(max(0, args.warmup)):
+        oracle_rate(f, g, gt, spec, args.mode, min(pairs, cores), pool)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(f, g, gt, spec, args.mode, pairs, pool)
+    dt = time.perf_counter() - t0
+    pool.close()
+    v = pairs * args.steps / dt
+    unit = "scan-pairs/s"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "mode": args.mode,
+            "config": {"workload": args.workload, "n": spec["n"], "n_theta": spec["n_theta"], "n_r": spec["n_r"],
+                       "pairs_per_step": pairs},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": f"{pairs} pairs of {args.workload} per step ({args.mode}), one per core"},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    from paper_2203_00459_gb300 import synth
+    spec = dict(synth.WORKLOADS[args.workload])
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, spec, rank)
+        return
+
+    # the CPU pool for the oracle baseline is spawned before the first CUDA call
+    pool = cores = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool, cores = make_pool()
+
+    import numpy as np
+    import torch
+    from paper_2203_00459_gb300 import build
+    build.build()
+    from paper_2203_00459_gb300 import _lib
+    from paper_2203_00459_gb300.search import PoseSearch, size_cfg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    B = spec["pairs"]
+    n, nt, nr = spec["n"], spec["n_theta"], spec["n_r"]
+    f, g, gt = synth.make_batch(args.workload, pairs=B, start=rank * B)
+    cfg = size_cfg(n, nt, nr)
+    search = PoseSearch([cfg], max_pairs=B)
+    L = _lib.lib()
+    fd = torch.from_numpy(f).cuda()
+    gd = torch.from_numpy(g).cuda()
+    gtd = torch.from_numpy(gt.astype(np.float32)).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    pose = torch.empty((B, 3), device="cuda")
+    dpose = torch.empty((B, 3), device="cuda")
+    df = torch.empty_like(fd)
+    dg = torch.empty_like(gd)
+
+    def step():
+        search.pose(fd, gd, out=pose)
+        if args.mode == "fwdbwd":
+            torch.sub(pose, gtd, out=dpose)
+            dpose.mul_(2.0)
+            _lib.check(L.fmbym_pose_backward(search.handle, torch.cuda.current_stream().cuda_stream, B, None, None,
+                                             fd.data_ptr(), gd.data_ptr(), dpose.data_ptr(), df.data_ptr(),
+                                             dg.data_ptr()), search.handle)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-step CUDA events, L2 flushed between steps ----
+    _lib.check(L.fmbym_set_tracing(search.handle, 1), search.handle)
+    launches0 = L.fmbym_launch_count(search.handle)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record()
+        step()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = L.fmbym_launch_count(search.handle) - launches0
+    ms = [a.elapsed_time(b) for a, b in evs]
+    ms_step = sum(ms) / len(ms)
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    import ctypes
+    K = 32
+    tot = (ctypes.c_double * K)()
+    cnt = (ctypes.c_longlong * K)()
+    nk = ctypes.c_int()
+    _lib.check(L.fmbym_trace_summary(search.handle, K, tot, cnt, ctypes.byref(nk)), search.handle)
+    _lib.check(L.fmbym_set_tracing(search.handle, 0), search.handle)
+    kernels = {}
+    for k in range(nk.value):
+        if cnt[k]:
+            kernels[L.fmbym_trace_kind_name(k).decode()] = (tot[k], cnt[k])
+
+    value = world * B / (ms_step * 1e-3)
+
+    # ---- dominant kernel roofline ----
+    chunks = (nr + 15) // 16
+    model = kernel_model(n, 2 * n, nt, nr, chunks)
+    total_ms = sum(v[0] for v in kernels.values())
+    dom = max(kernels, key=lambda k: kernels[k][0]) if kernels else None
+    peaks, peak_src = measured_peaks()
+    roof = None
+    shares = {k: round(v[0] / total_ms, 4) for k, v in kernels.items()} if total_ms else {}
+    if dom and dom in model:
+        avg_ms = kernels[dom][0] / kernels[dom][1]
+        byts = model[dom][0] * B
+        flops = model[dom][1] * B
+        achieved = byts / (avg_ms * 1e-3) / 1e9
+        tr = TRAFFIC.get(dom)
+        traffic = tr[0] * B / tr[2] if (tr and tr[1] == src_hash()) else None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "peak_source": peak_src, "alg_bytes_per_launch": byts, "avg_launch_ms": round(avg_ms, 5),
+                "fp32_tflops": round(flops / (avg_ms * 1e-3) / 1e12, 2)}
+
+    # ---- end to end through the C ABI with host buffers (forward) ----
+    e2e = None
+    if rank == 0:
+        fh = torch.from_numpy(f).pin_memory()
+        gh = torch.from_numpy(g).pin_memory()
+        for _ in range(2):
+            search.pose_host(fh, gh)
+        t0 = time.perf_counter()
+        reps = max(3, args.steps)
+        for _ in range(reps):
+            search.pose_host(fh, gh)
+        dt = (time.perf_counter() - t0) / reps
+        e2e = {"value": B / dt, "unit": "scan-pairs/s", "h2d_bytes_per_step": 2 * f.nbytes,
+               "d2h_bytes_per_step": B * 12, "mode": "fwd", "api": "fmbym_pose_host"}
+
+    # ---- forward-only rate and the plain one-pair-per-call path ----
+    extra = {}
+    if rank == 0:
+        fwd_ms = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            search.pose(fd, gd, out=pose)
+            b.record()
+            torch.cuda.synchronize()
+            fwd_ms.append(a.elapsed_time(b))
+        extra["fwd_pairs_per_s"] = B / (statistics.mean(fwd_ms) * 1e-3)
+        if not args.no_plain:
+            one = PoseSearch([cfg], max_pairs=1)
+            plain = []
+            for _ in range(3):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for i in range(B):
+                    one.pose(fd[i:i + 1], gd[i:i + 1], out=pose[i:i + 1])
+                b.record()
+                torch.cuda.synchronize()
+                plain.append(a.elapsed_time(b))
+            extra["plain_fwd_pairs_per_s"] = B / (statistics.mean(plain[1:]) * 1e-3)
+            extra["batched_vs_plain_fwd"] = extra["fwd_pairs_per_s"] / extra["plain_fwd_pairs_per_s"]
+            one.close()
+
+    cpu = None
+    if pool is not None:
+        rate = oracle_rate(f, g, gt, spec, args.mode, B, pool)
+        pool.close()
+        cpu = {"value": rate, "unit": "scan-pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"all {B} pairs of {args.workload} ({args.mode}), one pair per process, spawn pool"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "scan-pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "mode": args.mode,
+                "config": {"workload": args.workload, "n": n, "n_theta": nt, "n_r": nr, "pairs_per_gpu": B,
+                           "pad": "zero to 2N", "l2": "flushed (256 MB write) between timed steps"},
+                "roofline": roof, "kernel_shares": shares, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk, **extra}
+        print(json.dumps(line), flush=True)
+    search.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

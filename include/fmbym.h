@@ -1,0 +1,152 @@
+/*
+ * fmbym.h -- C ABI of the GB300 decoupled Fourier pose search (Fast-MbyM, arXiv 2203.00459).
+ *
+ * The library implements ScanMatch of Alg. 1 for batches of scan pairs on one GPU:
+ *   stage 1 (rotation, Eq. 4-7): Hann window -> 2D FFT -> band-pass -> |.| -> Cart2Pol ->
+ *            circular correlation along angle -> soft-argmax over the angle candidates;
+ *   stage 2 (translation, Eq. 8): Rotate(source, theta) -> ZeroPad -> 2D FFT correlation ->
+ *            soft-argmax over the translation candidates;
+ * and the adjoint of the whole search (the differentiability of Sec. III-C that the masking
+ * network of Sec. III-D trains through, Eq. 13).
+ *
+ * Conventions shared by every call
+ *   - Scans are float32, row-major [N][N], y = row, x = column.  Scores are stored in lag order:
+ *     index 0 is the most negative lag (-N/2 for translations, -n_theta/2 for angles).
+ *   - The pose of a pair is float32 [3] = (theta [rad], t_x, t_y [units of delta_xy]).  The
+ *     source f is rotated by +theta about (N/2, N/2) (theta > 0 turns +x toward +y), after which
+ *     g(x) ~ f'(x - t); Alg. 1's BuildSO2/MatMul step is the identity in this convention.
+ *   - Device pointers are CUDA global memory on the handle's device; "host" pointers are CPU
+ *     memory (pinned memory makes the copies asynchronous).  The caller owns every buffer it
+ *     passes; the library owns only its workspace, which it allocates in fmbym_create.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream) unless stated otherwise.  A handle must be used from one host
+ *     thread and one stream at a time.
+ *   - Every call returns a status code; fmbym_last_error() describes the last failure.
+ *     FMBYM_ERR_CUDA is sticky: a CUDA error in the context is reported, not cleared.
+ */
+#ifndef FMBYM_H
+#define FMBYM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum fmbym_status {
+    FMBYM_OK = 0,
+    FMBYM_ERR_INVALID_ARG = 1,      /* NULL or out-of-range argument                         */
+    FMBYM_ERR_UNSUPPORTED_SIZE = 2, /* N not in {128,256,512} or n_theta not in {128,256,400} */
+    FMBYM_ERR_WORKSPACE = 3,        /* more pairs than the handle was created for            */
+    FMBYM_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed                  */
+    FMBYM_ERR_TIMEOUT = 5           /* a bounded device-side wait ran out                    */
+};
+
+/* Parameters of one scan size: the arguments of ScanMatch in Alg. 1 plus the readings of
+ * the places the paper leaves open.
+ *   n           scan side N (n_xy of Alg. 1); supported: 128, 256, 512
+ *   n_theta     number of angle candidates over a half turn (delta_theta = pi / n_theta,
+ *               Alg. 1 first Linspace); supported: 128, 256, 400
+ *   n_r         radii of the polar grid, rho_j = j * (N/2) / n_r, 1 <= n_r <= N/2 (Cart2Pol)
+ *   temp_theta  T_theta > 0, temp_xy  T_xy > 0 (SoftArgMax temperatures of Alg. 1)
+ *   delta_xy    translation bin size > 0 (the pose's t is lag * delta_xy)
+ *   window      1: periodic Hann window before the stage-1 FFT (Alg. 1 HanningFilter); 0: none
+ *   pad_mode    0: ZeroPad to 2N, linear correlation (Alg. 1 ZeroPad); 1: N-periodic
+ *   score_norm  0: softmax(zscore(c) / T); 1: softmax(c / T) (the literal form)
+ *   band_lo, band_hi  radial band-pass on the DFT grid, keep band_lo <= rho <= band_hi bins
+ *               (Alg. 1 BandPassFilter) */
+typedef struct fmbym_size_cfg {
+    int n;
+    int n_theta;
+    int n_r;
+    float temp_theta;
+    float temp_xy;
+    float delta_xy;
+    int window;
+    int pad_mode;
+    int score_norm;
+    float band_lo;
+    float band_hi;
+} fmbym_size_cfg;
+
+/* Handle configuration: n_sizes size configurations (host array, copied by fmbym_create),
+ * the largest number of pairs one call may carry, and flags (0; reserved). */
+typedef struct fmbym_config {
+    int n_sizes;
+    const fmbym_size_cfg* sizes;
+    int max_pairs;
+    int flags;
+} fmbym_config;
+
+typedef struct fmbym_handle fmbym_handle;
+
+/* Creates a handle on the current CUDA device: validates the sizes, builds the per-size plans
+ * (twiddle, window and polar-sample tables) and allocates the whole workspace for max_pairs
+ * pairs.  Synchronous.  On failure *out is NULL and the status says why. */
+int fmbym_create(fmbym_handle** out, const fmbym_config* cfg);
+
+/* Releases the handle and its device memory.  Synchronises the device.  NULL is a no-op. */
+void fmbym_destroy(fmbym_handle* h);
+
+/* Text of the last failure on this handle ("" if none); valid until the next call.  With a
+ * NULL handle, the last failure of fmbym_create on this thread. */
+const char* fmbym_last_error(const fmbym_handle* h);
+
+/* Bytes of device workspace the handle holds. */
+unsigned long long fmbym_workspace_bytes(const fmbym_handle* h);
+
+/* Forward search (Alg. 1) for n_pairs scan pairs in one call.
+ *   size_idx  host int[n_pairs]: index into cfg->sizes of each pair, or NULL for all 0
+ *   offsets   host long long[n_pairs]: element offset of pair p's scan in f and g (and in
+ *             c_xy), or NULL for packed order (offset of p = sum of N^2 over pairs < p)
+ *   f, g      device float32: source and target scans
+ *   pose      device float32 [n_pairs][3] out: (theta, t_x, t_y)
+ *   c_theta   device float32 out or NULL: the n_theta angle scores of each pair, packed in pair
+ *             order (pair p starts at sum of n_theta over pairs < p), lag order
+ *   c_xy      device float32 out or NULL: the N x N translation scores of each pair at the pair's
+ *             offset, rows = t_y lags, columns = t_x lags, lag order
+ * Pairs of different sizes may be mixed in any order.  Returns FMBYM_ERR_WORKSPACE if n_pairs
+ * exceeds max_pairs. */
+int fmbym_pose(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx,
+               const long long* offsets, const float* f, const float* g, float* pose,
+               float* c_theta, float* c_xy);
+
+/* Adjoint of fmbym_pose: given dL/dpose (device float32 [n_pairs][3]) writes dL/df and dL/dg
+ * (device float32, laid out like f and g, overwritten).  Recomputes every forward intermediate
+ * from f and g; keeps nothing between calls.  Differentiation follows Sec. III-C: soft-argmax,
+ * FFTs, bilinear Rotate and Cart2Pol, |z| (derivative z/|z|, 0 at z = 0), Hann window. */
+int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx,
+                        const long long* offsets, const float* f, const float* g,
+                        const float* dpose, float* df, float* dg);
+
+/* fmbym_pose with HOST buffers: copies f and g (host float32, total elements as laid out by
+ * offsets) into the handle's device staging area, runs the search on the stream, copies the
+ * pose (host float32 [n_pairs][3]) back and synchronises the stream.  total_elems is the
+ * length of f and of g in floats; it must not exceed what max_pairs scans of the largest
+ * configured size hold. */
+int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx,
+                    const long long* offsets, long long total_elems, const float* f_host,
+                    const float* g_host, float* pose_host);
+
+/* Launch tracing (the CUDA-event timing of Sec. IV-C, per kernel).  With on = 1 the handle records a
+ * CUDA event on the launching stream before each kernel launch and after the last launch of each
+ * call, so that every kernel's device time is the interval to the next event; on = 0 stops
+ * recording.  Either way the recorded intervals are cleared.  Synchronises the device. */
+int fmbym_set_tracing(fmbym_handle* h, int on);
+
+/* Sums the recorded intervals per kernel kind: total_ms[k] and count[k] for k < cap (host
+ * arrays); *n_kinds (optional) receives the number of kinds.  Waits for the last recorded event. */
+int fmbym_trace_summary(fmbym_handle* h, int cap, double* total_ms, long long* count, int* n_kinds);
+
+/* Name of kernel kind k ("" if out of range); static storage. */
+const char* fmbym_trace_kind_name(int kind);
+
+/* Number of kernels the handle has launched since it was created. */
+long long fmbym_launch_count(const fmbym_handle* h);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fmbym_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMBYM_H */

@@ -1,0 +1,76 @@
+"""ctypes binding of libfmbym.so (include/fmbym.h): argument marshalling only.
+
+The library is built in-tree by ``paper_2203_00459_gb300.build``; loading fails loudly when it is
+missing, so nothing above this module can fall back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfmbym.so")
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT = range(6)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE", 4: "CUDA", 5: "TIMEOUT"}
+
+
+class SizeCfg(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_r", ctypes.c_int),
+                ("temp_theta", ctypes.c_float), ("temp_xy", ctypes.c_float), ("delta_xy", ctypes.c_float),
+                ("window", ctypes.c_int), ("pad_mode", ctypes.c_int), ("score_norm", ctypes.c_int),
+                ("band_lo", ctypes.c_float), ("band_hi", ctypes.c_float)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n_sizes", ctypes.c_int), ("sizes", ctypes.POINTER(SizeCfg)), ("max_pairs", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+# exported symbol -> (restype, argtypes)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+SIGNATURES = {
+    "fmbym_version": (_I, []),
+    "fmbym_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Config)]),
+    "fmbym_destroy": (None, [_P]),
+    "fmbym_last_error": (ctypes.c_char_p, [_P]),
+    "fmbym_workspace_bytes": (ctypes.c_ulonglong, [_P]),
+    "fmbym_pose": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
+    "fmbym_pose_backward": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
+    "fmbym_pose_host": (_I, [_P, _P, _I, _P, _P, _LL, _P, _P, _P]),
+    "fmbym_set_tracing": (_I, [_P, _I]),
+    "fmbym_trace_summary": (_I, [_P, _I, _P, _P, _P]),
+    "fmbym_trace_kind_name": (ctypes.c_char_p, [_I]),
+    "fmbym_launch_count": (_LL, [_P]),
+}
+
+_lib = None
+
+
+class FmbymError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib(path: str = LIB_PATH):
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2203_00459_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status, handle=None):
+    if status != OK:
+        msg = lib().fmbym_last_error(handle)
+        raise FmbymError(status, msg.decode() if msg else "")

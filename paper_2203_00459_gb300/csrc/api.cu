@@ -1,0 +1,481 @@
+// Host side of the C ABI (include/fmbym.h): handle, per-size plans, workspace, argument checks,
+// grouping of mixed-size batches, and the host-buffer entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fmbym.h"
+#include "common.cuh"
+
+using namespace fmbym;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct HostPlan {
+    fmbym_size_cfg cfg;
+    DevPlan dev;
+    void* tables = nullptr;  // one allocation holding every table of the plan
+};
+
+thread_local std::string g_create_error;
+
+bool supported_n(int n) { return n == 128 || n == 256 || n == 512; }
+bool supported_nt(int nt) { return nt == 128 || nt == 256 || nt == 400; }
+
+}  // namespace
+
+struct fmbym_handle {
+    int device = 0;
+    int max_pairs = 0;
+    std::vector<HostPlan> plans;
+    void* ws = nullptr;
+    size_t ws_size = 0;
+    long long* d_tab = nullptr;   // [max_pairs][3]
+    long long* h_tab = nullptr;   // pinned staging of the pair table
+    cudaEvent_t tab_free = nullptr;
+    float* d_stage_f = nullptr;   // host-buffer entry point staging
+    float* d_stage_g = nullptr;
+    float* d_stage_pose = nullptr;
+    unsigned* d_cnt = nullptr;    // [max_pairs] completion counters, zero between launches
+    long long stage_elems = 0;
+    Tracer tracer;
+    std::string err;
+};
+
+namespace fmbym {
+
+// Workspace of one size group of B pairs; every region starts on a 256-byte boundary.
+static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* r = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return r;
+    };
+    const size_t n = p.n, P = p.p, Wn = n / 2, Wp = P / 2, b = (size_t)B;
+    Ws t{};
+    t.s1 = (float2*)take(2 * b * n * Wn * sizeof(float2));
+    t.mt = (float*)take(2 * b * (Wn + 1) * n * sizeof(float));
+    t.sp = (float2*)take(b * angle_chunks(p) * p.nt * sizeof(float2));
+    t.th = (float*)take(b * 8 * sizeof(float));
+    t.s2 = (float2*)take(2 * b * n * Wp * sizeof(float2));
+    t.s3 = (float2*)take(b * n * Wp * sizeof(float2));
+    t.cxy = (float*)take(b * n * n * sizeof(float));
+    t.st = (float*)take(b * c2r_blocks(p) * 4 * sizeof(float));
+    t.sx = (float*)take(b * kSplitXY * 4 * sizeof(float));
+    if (backward) {
+        t.b1 = (float2*)take(b * n * Wp * sizeof(float2));
+        t.b2 = (float2*)take(2 * b * n * Wp * sizeof(float2));
+        t.gfr = (float*)take(b * n * n * sizeof(float));
+        t.gth = (float*)take(b * 4 * sizeof(float));
+        t.gpol = (float*)take(2 * b * p.nt * p.nr * sizeof(float));
+        t.gmt = (float*)take(2 * b * (Wn + 1) * n * sizeof(float));
+        t.gs1 = (float2*)take(2 * b * n * Wn * sizeof(float2));
+        t.gxx = (float*)take(b * kSplitXY * 4 * sizeof(float));
+    }
+    if (w) *w = t;
+    return off;
+}
+
+size_t ws_bytes(const DevPlan& p, int B, bool backward) { return carve(p, B, nullptr, nullptr, backward); }
+Ws ws_carve(const DevPlan& p, int B, void* base, bool backward) {
+    Ws w;
+    carve(p, B, (char*)base, &w, backward);
+    return w;
+}
+
+cudaError_t prepare_forward_kernels();
+cudaError_t prepare_backward_kernels();
+cudaError_t prepare_kernels() {
+    cudaError_t e = prepare_forward_kernels();
+    if (e != cudaSuccess) return e;
+    return prepare_backward_kernels();
+}
+
+}  // namespace fmbym
+
+namespace {
+
+int fail(fmbym_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(fmbym_handle* h, cudaError_t e, const char* what) {
+    return fail(h, FMBYM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+std::string validate(const fmbym_size_cfg& c) {
+    char buf[256];
+    if (!supported_n(c.n)) {
+        snprintf(buf, sizeof buf, "n=%d not supported (128, 256, 512)", c.n);
+        return buf;
+    }
+    if (!supported_nt(c.n_theta)) {
+        snprintf(buf, sizeof buf, "n_theta=%d not supported (128, 256, 400)", c.n_theta);
+        return buf;
+    }
+    if (c.n_r < 1 || c.n_r > c.n / 2) return "n_r must be in [1, n/2]";
+    if (!(c.temp_theta > 0.f) || !(c.temp_xy > 0.f) || !(c.delta_xy > 0.f))
+        return "temperatures and delta_xy must be positive";
+    if (c.window != 0 && c.window != 1) return "window must be 0 or 1";
+    if (c.pad_mode != 0 && c.pad_mode != 1) return "pad_mode must be 0 or 1";
+    if (c.score_norm != 0 && c.score_norm != 1) return "score_norm must be 0 or 1";
+    if (!(c.band_lo >= 0.f) || !(c.band_hi >= c.band_lo)) return "need 0 <= band_lo <= band_hi";
+    return "";
+}
+
+// Builds the device tables of one size in double precision.
+cudaError_t build_plan(HostPlan& hp) {
+    const fmbym_size_cfg& c = hp.cfg;
+    DevPlan& d = hp.dev;
+    d.n = c.n;
+    d.p = c.pad_mode == 1 ? c.n : 2 * c.n;
+    d.nt = c.n_theta;
+    d.nr = c.n_r;
+    d.window = c.window;
+    d.score_norm = c.score_norm;
+    d.temp_theta = c.temp_theta;
+    d.temp_xy = c.temp_xy;
+    d.delta_xy = c.delta_xy;
+    // band-pass on integer rho^2 = v^2 + u^2: keep band_lo <= sqrt(m) <= band_hi
+    const int mmax = (c.n / 2) * (c.n / 2) * 2;
+    d.m_lo = mmax + 1;
+    d.m_hi = -1;
+    for (int m = 0; m <= mmax; ++m) {
+        const double r = std::sqrt((double)m);
+        if (r >= c.band_lo && d.m_lo > mmax) d.m_lo = m;
+        if (r <= c.band_hi) d.m_hi = m;
+    }
+    std::vector<float> win(c.n);
+    for (int i = 0; i < c.n; ++i) win[i] = (float)(0.5 - 0.5 * std::cos(2.0 * kPi * i / c.n));
+    auto twiddles = [](int L) {
+        std::vector<float2> t(L);
+        for (int k = 0; k < L; ++k) {
+            const double a = -2.0 * kPi * (double)k / (double)L;
+            t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        return t;
+    };
+    std::vector<float2> twn = twiddles(d.n), twp = twiddles(d.p), twt = twiddles(d.nt);
+    std::vector<PolarSample> pol((size_t)d.nt * d.nr);
+    for (int a = 0; a < d.nt; ++a) {
+        const double alpha = (double)a * kPi / d.nt;
+        for (int r = 0; r < d.nr; ++r) {
+            const double rho = (double)r * (d.n / 2.0) / d.nr;
+            const double u = rho * std::cos(alpha), v = rho * std::sin(alpha);
+            const double x0 = std::floor(u), y0 = std::floor(v);
+            pol[(size_t)a * d.nr + r] = PolarSample{(int)x0, (int)y0, (float)(u - x0), (float)(v - y0)};
+        }
+    }
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_win = al(win.size() * 4), b_twn = al(twn.size() * 8), b_twp = al(twp.size() * 8),
+                 b_twt = al(twt.size() * 8), b_pol = al(pol.size() * sizeof(PolarSample));
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, b_win + b_twn + b_twp + b_twt + b_pol);
+    if (e != cudaSuccess) return e;
+    hp.tables = base;
+    char* cur = base;
+    auto put = [&](const void* src, size_t bytes, size_t padded) {
+        char* dst = cur;
+        cudaError_t err = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+        cur += padded;
+        return std::make_pair(dst, err);
+    };
+    auto r1 = put(win.data(), win.size() * 4, b_win);
+    auto r2 = put(twn.data(), twn.size() * 8, b_twn);
+    auto r3 = put(twp.data(), twp.size() * 8, b_twp);
+    auto r4 = put(twt.data(), twt.size() * 8, b_twt);
+    auto r5 = put(pol.data(), pol.size() * sizeof(PolarSample), b_pol);
+    for (auto& r : {r1, r2, r3, r4, r5})
+        if (r.second != cudaSuccess) return r.second;
+    d.win = (const float*)r1.first;
+    d.tw_n = (const float2*)r2.first;
+    d.tw_p = (const float2*)r3.first;
+    d.tw_t = (const float2*)r4.first;
+    d.polar = (const PolarSample*)r5.first;
+    return cudaSuccess;
+}
+
+struct Group {
+    int size_idx;
+    int count;
+    int first;  // first row of the group in the pair table
+};
+
+// Validates the per-call arguments and fills the pinned pair table grouped by size.
+int make_table(fmbym_handle* h, int n_pairs, const int* size_idx, const long long* offsets,
+               std::vector<Group>& groups, long long* total_elems) {
+    if (n_pairs < 0) return fail(h, FMBYM_ERR_INVALID_ARG, "n_pairs < 0");
+    if (n_pairs > h->max_pairs) return fail(h, FMBYM_ERR_WORKSPACE, "n_pairs exceeds max_pairs of the handle");
+    const int ns = (int)h->plans.size();
+    std::vector<long long> off(n_pairs), ct(n_pairs);
+    long long acc = 0, acc_t = 0, end = 0;
+    for (int i = 0; i < n_pairs; ++i) {
+        const int s = size_idx ? size_idx[i] : 0;
+        if (s < 0 || s >= ns) return fail(h, FMBYM_ERR_INVALID_ARG, "size_idx out of range");
+        const long long nn = (long long)h->plans[s].cfg.n * h->plans[s].cfg.n;
+        off[i] = offsets ? offsets[i] : acc;
+        if (off[i] < 0 || (off[i] & 3)) return fail(h, FMBYM_ERR_INVALID_ARG, "offsets must be >= 0 and multiples of 4");
+        acc += nn;
+        ct[i] = acc_t;
+        acc_t += h->plans[s].cfg.n_theta;
+        end = std::max(end, off[i] + nn);
+    }
+    if (total_elems) *total_elems = end;
+    // wait until the previous call's copy of the table has been consumed
+    cudaError_t e = cudaEventSynchronize(h->tab_free);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    groups.clear();
+    int row = 0;
+    for (int s = 0; s < ns; ++s) {
+        Group g{s, 0, row};
+        for (int i = 0; i < n_pairs; ++i) {
+            if ((size_idx ? size_idx[i] : 0) != s) continue;
+            h->h_tab[3 * row] = off[i];
+            h->h_tab[3 * row + 1] = ct[i];
+            h->h_tab[3 * row + 2] = i;
+            ++row;
+            ++g.count;
+        }
+        if (g.count) groups.push_back(g);
+    }
+    return FMBYM_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int fmbym_version(void) { return 10000; }
+
+const char* fmbym_last_error(const fmbym_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+unsigned long long fmbym_workspace_bytes(const fmbym_handle* h) { return h ? h->ws_size : 0ull; }
+
+void fmbym_destroy(fmbym_handle* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    for (auto& p : h->plans) cudaFree(p.tables);
+    cudaFree(h->ws);
+    cudaFree(h->d_tab);
+    cudaFree(h->d_stage_f);
+    cudaFree(h->d_stage_g);
+    cudaFree(h->d_stage_pose);
+    cudaFree(h->d_cnt);
+    if (h->h_tab) cudaFreeHost(h->h_tab);
+    for (cudaEvent_t e : h->tracer.ev) cudaEventDestroy(e);
+    if (h->tab_free) cudaEventDestroy(h->tab_free);
+    delete h;
+}
+
+int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg || cfg->n_sizes < 1 || !cfg->sizes) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "need at least one size");
+    if (cfg->max_pairs < 1) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "max_pairs must be >= 1");
+    for (int i = 0; i < cfg->n_sizes; ++i) {
+        const std::string v = validate(cfg->sizes[i]);
+        if (!v.empty()) {
+            const bool size = !supported_n(cfg->sizes[i].n) || !supported_nt(cfg->sizes[i].n_theta);
+            return fail(nullptr, size ? FMBYM_ERR_UNSUPPORTED_SIZE : FMBYM_ERR_INVALID_ARG,
+                        "size " + std::to_string(i) + ": " + v);
+        }
+    }
+    fmbym_handle* h = new fmbym_handle();
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+    h->max_pairs = cfg->max_pairs;
+    static bool prepared = false;
+    if (!prepared) {
+        e = prepare_kernels();
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(nullptr, e, "kernel attributes");
+        }
+        prepared = true;
+    }
+    size_t ws = 0;
+    int nmax = 0;
+    for (int i = 0; i < cfg->n_sizes; ++i) {
+        HostPlan hp;
+        hp.cfg = cfg->sizes[i];
+        e = build_plan(hp);
+        h->plans.push_back(hp);
+        if (e != cudaSuccess) {
+            fmbym_destroy(h);
+            return cuda_fail(nullptr, e, "plan tables");
+        }
+        ws = std::max(ws, ws_bytes(hp.dev, cfg->max_pairs, true));
+        nmax = std::max(nmax, hp.cfg.n);
+    }
+    h->ws_size = ws;
+    if ((e = cudaMalloc(&h->ws, ws)) != cudaSuccess || (e = cudaMemset(h->ws, 0, ws)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_tab, sizeof(long long) * 3 * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMallocHost(&h->h_tab, sizeof(long long) * 3 * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->tab_free, cudaEventDisableTiming)) != cudaSuccess) {
+        fmbym_destroy(h);
+        return cuda_fail(nullptr, e, "workspace allocation");
+    }
+    h->stage_elems = (long long)cfg->max_pairs * nmax * nmax;
+    if ((e = cudaMalloc(&h->d_stage_f, sizeof(float) * h->stage_elems)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_stage_g, sizeof(float) * h->stage_elems)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_stage_pose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs)) != cudaSuccess) {
+        fmbym_destroy(h);
+        return cuda_fail(nullptr, e, "staging allocation");
+    }
+    *out = h;
+    return FMBYM_OK;
+}
+
+int fmbym_pose(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
+               const float* f, const float* g, float* pose, float* c_theta, float* c_xy) {
+    if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    h->err.clear();
+    if (n_pairs == 0) return FMBYM_OK;
+    if (!f || !g || !pose) return fail(h, FMBYM_ERR_INVALID_ARG, "f, g and pose must not be NULL");
+    if (!aligned16(f) || !aligned16(g) || (c_xy && !aligned16(c_xy)))
+        return fail(h, FMBYM_ERR_INVALID_ARG, "f, g and c_xy must be 16-byte aligned");
+    std::vector<Group> groups;
+    int rc = make_table(h, n_pairs, size_idx, offsets, groups, nullptr);
+    if (rc != FMBYM_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pair table copy");
+    if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    for (const Group& gr : groups) {
+        const DevPlan& p = h->plans[gr.size_idx].dev;
+        Ws w = ws_carve(p, gr.count, h->ws, true);
+        w.tr = &h->tracer;
+        w.cnt = h->d_cnt;
+        e = launch_forward(p, w, gr.count, h->d_tab + 3 * gr.first, f, g, pose, c_theta, c_xy, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
+    }
+    return FMBYM_OK;
+}
+
+int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
+                        const float* f, const float* g, const float* dpose, float* df, float* dg) {
+    if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    h->err.clear();
+    if (n_pairs == 0) return FMBYM_OK;
+    if (!f || !g || !dpose || !df || !dg) return fail(h, FMBYM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(f) || !aligned16(g) || !aligned16(df) || !aligned16(dg))
+        return fail(h, FMBYM_ERR_INVALID_ARG, "f, g, df and dg must be 16-byte aligned");
+    std::vector<Group> groups;
+    int rc = make_table(h, n_pairs, size_idx, offsets, groups, nullptr);
+    if (rc != FMBYM_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pair table copy");
+    if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    for (const Group& gr : groups) {
+        const DevPlan& p = h->plans[gr.size_idx].dev;
+        Ws w = ws_carve(p, gr.count, h->ws, true);
+        w.tr = &h->tracer;
+        w.cnt = h->d_cnt;
+        e = launch_backward(p, w, gr.count, h->d_tab + 3 * gr.first, f, g, dpose, df, dg, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
+    }
+    return FMBYM_OK;
+}
+
+int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
+                    long long total_elems, const float* f_host, const float* g_host, float* pose_host) {
+    if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    h->err.clear();
+    if (n_pairs == 0) return FMBYM_OK;
+    if (!f_host || !g_host || !pose_host) return fail(h, FMBYM_ERR_INVALID_ARG, "NULL buffer");
+    if (total_elems < 0 || total_elems > h->stage_elems)
+        return fail(h, FMBYM_ERR_WORKSPACE, "total_elems exceeds the staging area");
+    std::vector<Group> groups;
+    long long need = 0;
+    int rc = make_table(h, n_pairs, size_idx, offsets, groups, &need);
+    if (rc != FMBYM_OK) return rc;
+    if (need > total_elems) return fail(h, FMBYM_ERR_INVALID_ARG, "offsets reach beyond total_elems");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->d_stage_f, f_host, sizeof(float) * total_elems, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(h->d_stage_g, g_host, sizeof(float) * total_elems, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+        return cuda_fail(h, e, "host-to-device copy");
+    if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    for (const Group& gr : groups) {
+        const DevPlan& p = h->plans[gr.size_idx].dev;
+        Ws w = ws_carve(p, gr.count, h->ws, true);
+        w.tr = &h->tracer;
+        w.cnt = h->d_cnt;
+        e = launch_forward(p, w, gr.count, h->d_tab + 3 * gr.first, h->d_stage_f, h->d_stage_g, h->d_stage_pose,
+                           nullptr, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
+    }
+    if ((e = cudaMemcpyAsync(pose_host, h->d_stage_pose, sizeof(float) * 3 * n_pairs, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+        return cuda_fail(h, e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return FMBYM_OK;
+}
+
+int fmbym_set_tracing(fmbym_handle* h, int on) {
+    if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+    if (on && h->tracer.ev.empty()) {
+        const size_t n = 1 << 14;
+        h->tracer.ev.resize(n);
+        h->tracer.kind.resize(n);
+        for (size_t i = 0; i < n; ++i)
+            if ((e = cudaEventCreate(&h->tracer.ev[i])) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+    }
+    h->tracer.on = on != 0;
+    h->tracer.used = 0;
+    return FMBYM_OK;
+}
+
+int fmbym_trace_summary(fmbym_handle* h, int cap, double* total_ms, long long* count, int* n_kinds) {
+    if (!h || !total_ms || !count || cap < 1) return fail(h, FMBYM_ERR_INVALID_ARG, "bad arguments");
+    const int nk = std::min(cap, (int)K_COUNT);
+    for (int k = 0; k < nk; ++k) {
+        total_ms[k] = 0.0;
+        count[k] = 0;
+    }
+    if (n_kinds) *n_kinds = (int)K_COUNT;
+    Tracer& t = h->tracer;
+    if (t.used == 0) return FMBYM_OK;
+    cudaError_t e = cudaEventSynchronize(t.ev[t.used - 1]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    for (size_t i = 0; i + 1 < t.used; ++i) {
+        const int k = t.kind[i];
+        if (k < 0 || k >= nk) continue;
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, t.ev[i], t.ev[i + 1])) != cudaSuccess)
+            return cuda_fail(h, e, "cudaEventElapsedTime");
+        total_ms[k] += ms;
+        count[k] += 1;
+    }
+    return FMBYM_OK;
+}
+
+const char* fmbym_trace_kind_name(int kind) { return (kind >= 0 && kind < K_COUNT) ? kKindNames[kind] : ""; }
+
+long long fmbym_launch_count(const fmbym_handle* h) { return h ? h->tracer.launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Shared declarations of the CUDA library: per-size device plans, the workspace layout of one
+// size group, and the launchers of the forward and backward kernel sequences.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "fft.cuh"
+
+namespace fmbym {
+
+constexpr int kThreads = 256;   // threads of the FFT kernels
+constexpr int kAngleRadii = 16; // radii per CTA of the angle-correlation kernel
+constexpr int kSplitXY = 8;     // CTAs per pair of the translation soft-argmax
+
+// One bilinear Cart2Pol sample: floor of the (u, v) frequency and the fractions.
+struct PolarSample {
+    int x0, y0;
+    float fx, fy;
+};
+
+// Device-side plan of one scan size (tables built on the host in double precision).
+struct DevPlan {
+    int n, p, nt, nr;      // scan side, padded side (2N or N), angle bins, radii
+    int m_lo, m_hi;        // band-pass: keep integer rho^2 in [m_lo, m_hi]
+    int window, score_norm;
+    float temp_theta, temp_xy, delta_xy;
+    const float* win;      // [N] periodic Hann
+    const float2* tw_n;    // [N]  exp(-2 pi i k / N)
+    const float2* tw_p;    // [P]  exp(-2 pi i k / P)
+    const float2* tw_t;    // [n_theta] exp(-2 pi i k / n_theta)
+    const PolarSample* polar;  // [n_theta][n_r]
+};
+
+inline int angle_chunks(const DevPlan& p) { return (p.nr + kAngleRadii - 1) / kAngleRadii; }
+inline int fft_threads(int L) { return L / 16 == 25 ? 25 : L / 16; }
+inline int c2r_blocks(const DevPlan& p) { return (p.n / 2) / (kThreads / fft_threads(p.p)); }
+
+// Kernel kinds, for the launch tracer.
+enum Kind {
+    K_S1_ROWS, K_S1_COLS, K_ANGLE, K_THETA, K_S2_ROWS, K_S2_COLS, K_S2_C2R, K_SXY,
+    K_B_SXY, K_B_COLS, K_B_ROWS, K_B_ROT, K_B_THETA, K_B_ANGLE, K_B_S1COLS, K_B_S1ROWS, K_B_MISC,
+    K_COUNT
+};
+extern const char* const kKindNames[K_COUNT];
+
+// Launch tracer: counts launches and, when on, records one CUDA event before every launch and one
+// after the last launch of a call on the launching stream, so kernel i lasts from its event to the
+// next one.  Events come from a fixed pool; recording stops when the pool is used up.
+struct Tracer {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    size_t used = 0;
+    long long launches = 0;
+    void before(int k, cudaStream_t st) {
+        ++launches;
+        if (!on || used >= ev.size()) return;
+        cudaEventRecord(ev[used], st);
+        kind[used++] = k;
+    }
+    void close(cudaStream_t st) {
+        if (!on || used >= ev.size()) return;
+        cudaEventRecord(ev[used], st);
+        kind[used++] = -1;
+    }
+};
+
+// Workspace of one size group of B pairs (pointers into the handle's workspace).
+struct Ws {
+    float2* s1;   // [2][B][N][N/2]   stage-1 row spectra (packed real FFT rows)
+    float* mt;    // [2][B][N/2+1][N] stage-1 band-passed magnitudes, u-major
+    float2* sp;   // [B][chunks][n_theta] per-chunk sums of conj(A_f) A_g along angle
+    float* th;    // [B][8] theta, cos hi/lo, sin hi/lo
+    float2* s2;   // [2][B][N][P/2]   stage-2 row spectra of the rotated source and the target
+    float2* s3;   // [B][N][P/2]      product after the inverse column pass, lag rows
+    float* cxy;   // [B][N][N]        translation scores when the caller does not keep them
+    float* st;    // [B][c2r blocks][4] per-block mean, M2, max of the translation scores
+    float* sx;    // [B][kSplitXY][4] soft-argmax partial sums
+    unsigned* cnt;  // [B] completion counters of the last-block reductions: a handle-wide array that
+                    // is zero between launches (the last block of a pair resets its counter)
+    // backward extras
+    float2* b1;   // [B][N][P/2]     adjoint spectra
+    float2* b2;   // [2][B][N][P/2]
+    float* gfr;   // [B][N][N]       d rotated source
+    float* gth;   // [B][4]          d theta partial sums / total
+    float* gpol;  // [2][B][n_theta][n_r] d polar arrays
+    float* gmt;   // [2][B][N/2+1][N] d magnitudes
+    float2* gs1;  // [2][B][N][N/2]
+    float* gxx;   // [B][kSplitXY][4] soft-argmax adjoint partial sums
+    Tracer* tr;   // launch tracer of the handle
+};
+
+size_t ws_bytes(const DevPlan& p, int B, bool backward);
+Ws ws_carve(const DevPlan& p, int B, void* base, bool backward);
+
+// tab: device long long [B][3] = (scan offset, c_theta offset, pair index)
+cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                           const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st);
+cudaError_t launch_backward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st);
+cudaError_t prepare_kernels();
+
+}  // namespace fmbym

@@ -1,0 +1,213 @@
+// Shared-memory FFT engine for sm_103a.
+//
+// A group of T threads transforms one complex sequence of length L that lives in shared
+// memory.  The transform is a Stockham autosort FFT (natural order in, natural order out): each
+// pass p of radix R reads the butterfly inputs x[b + t L/R] (t < R) of butterfly b into
+// registers, multiplies them by the twiddles W_{Ns R}^{(b mod Ns) t} (Ns = product of the
+// radices of the earlier passes), does the radix-R DFT in registers and writes the outputs to
+// x[(b / Ns) Ns R + (b mod Ns) + t Ns].  All reads of a pass finish before its writes start
+// (one __syncthreads between them), so a single buffer suffices.
+//
+// Element i of a sequence sits at base + spad(i) * es, with spad(i) = i + i/16: the padding
+// word every 16 elements makes the radix-16 scatter of the first pass bank-conflict free, and
+// an element stride es > 1 interleaves several sequences (column tiles).
+//
+// Twiddles come from a table tw[k] = exp(-2 pi i k / L), k < L, computed in double precision on
+// the host and rounded to float; the inverse transform uses their conjugates.  Forward is the
+// unnormalised DFT X[k] = sum_n x[n] exp(-2 pi i n k / L); inverse has the + sign and no 1/L.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fmbym {
+
+__host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 c_cjmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+// a * (S i): S = -1 (forward) gives a * (-i), S = +1 gives a * i
+template <int S> __device__ __forceinline__ float2 c_rot(float2 a) {
+    return S < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// ---------------------------------------------------------------------------------------------
+// small DFTs in registers, y[k] = sum_n x[n] exp(S 2 pi i n k / R), in place, natural order
+// ---------------------------------------------------------------------------------------------
+
+template <int S> __device__ __forceinline__ void dft2(float2* v) {
+    float2 a = v[0];
+    v[0] = c_add(a, v[1]);
+    v[1] = c_sub(a, v[1]);
+}
+
+template <int S> __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+    float2 a = c_add(x0, x2), b = c_sub(x0, x2), c = c_add(x1, x3), d = c_rot<S>(c_sub(x1, x3));
+    x0 = c_add(a, c);
+    x2 = c_sub(a, c);
+    x1 = c_add(b, d);
+    x3 = c_sub(b, d);
+}
+
+template <int S> __device__ __forceinline__ void dft4(float2* v) { dft4<S>(v[0], v[1], v[2], v[3]); }
+
+constexpr float kSqrtHalf = 0.70710678118654752440f;
+constexpr float kCos8 = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kSin8 = 0.38268343236508977173f;  // sin(pi/8)
+
+template <int S> __device__ __forceinline__ void dft8(float2* v) {
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<S>(e0, e1, e2, e3);
+    dft4<S>(o0, o1, o2, o3);
+    // W8^1 = (1 + S i)/sqrt2, W8^2 = S i, W8^3 = (-1 + S i)/sqrt2
+    o1 = make_float2((o1.x - S * o1.y) * kSqrtHalf, (o1.y + S * o1.x) * kSqrtHalf);
+    o2 = c_rot<S>(o2);
+    o3 = make_float2((-o3.x - S * o3.y) * kSqrtHalf, (-o3.y + S * o3.x) * kSqrtHalf);
+    v[0] = c_add(e0, o0); v[4] = c_sub(e0, o0);
+    v[1] = c_add(e1, o1); v[5] = c_sub(e1, o1);
+    v[2] = c_add(e2, o2); v[6] = c_sub(e2, o2);
+    v[3] = c_add(e3, o3); v[7] = c_sub(e3, o3);
+}
+
+// W16^m = exp(S 2 pi i m / 16) for the products m = n2 k1 that the 4 x 4 split needs
+template <int S, int M> __device__ __forceinline__ float2 tw16(float2 a) {
+    constexpr int m = M & 15;
+    if constexpr (m == 0) return a;
+    else if constexpr (m == 4) return c_rot<S>(a);
+    else if constexpr (m == 8) return make_float2(-a.x, -a.y);
+    else {
+        constexpr float cs[16] = {1.f, kCos8, kSqrtHalf, kSin8, 0.f, -kSin8, -kSqrtHalf, -kCos8,
+                                  -1.f, -kCos8, -kSqrtHalf, -kSin8, 0.f, kSin8, kSqrtHalf, kCos8};
+        constexpr float sn[16] = {0.f, kSin8, kSqrtHalf, kCos8, 1.f, kCos8, kSqrtHalf, kSin8,
+                                  0.f, -kSin8, -kSqrtHalf, -kCos8, -1.f, -kCos8, -kSqrtHalf, -kSin8};
+        return c_mul(a, make_float2(cs[m], S * sn[m]));
+    }
+}
+
+// 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.
+template <int S> __device__ __forceinline__ void dft16(float2* v) {
+    // step 1: length-4 DFTs over n1 for each n2 (results A[n2][k1] stored at v[4 k1 + n2])
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<S>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    // step 2: twiddles W16^{n2 k1}
+    v[5] = tw16<S, 1>(v[5]);   v[6] = tw16<S, 2>(v[6]);   v[7] = tw16<S, 3>(v[7]);
+    v[9] = tw16<S, 2>(v[9]);   v[10] = tw16<S, 4>(v[10]); v[11] = tw16<S, 6>(v[11]);
+    v[13] = tw16<S, 3>(v[13]); v[14] = tw16<S, 6>(v[14]); v[15] = tw16<S, 9>(v[15]);
+    // step 3: length-4 DFTs over n2 for each k1; output k1 + 4 k2
+    float2 y[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 a0 = v[4 * k1], a1 = v[4 * k1 + 1], a2 = v[4 * k1 + 2], a3 = v[4 * k1 + 3];
+        dft4<S>(a0, a1, a2, a3);
+        y[k1] = a0; y[k1 + 4] = a1; y[k1 + 8] = a2; y[k1 + 12] = a3;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = y[i];
+}
+
+// 5-point DFT from cos/sin of 2 pi/5 and 4 pi/5
+template <int S> __device__ __forceinline__ void dft5(float2* v) {
+    constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+    constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+    constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+    constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+    float2 x0 = v[0];
+    float2 t1 = c_add(v[1], v[4]), t2 = c_add(v[2], v[3]);
+    float2 t3 = c_sub(v[1], v[4]), t4 = c_sub(v[2], v[3]);
+    float2 a1 = make_float2(x0.x + c1 * t1.x + c2 * t2.x, x0.y + c1 * t1.y + c2 * t2.y);
+    float2 a2 = make_float2(x0.x + c2 * t1.x + c1 * t2.x, x0.y + c2 * t1.y + c1 * t2.y);
+    float2 b1 = make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+    float2 b2 = make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+    v[0] = make_float2(x0.x + t1.x + t2.x, x0.y + t1.y + t2.y);
+    // y1 = a1 + S i b1, y4 = a1 - S i b1, y2 = a2 + S i b2, y3 = a2 - S i b2
+    float2 ib1 = c_rot<S>(b1), ib2 = c_rot<S>(b2);
+    v[1] = c_add(a1, ib1);
+    v[4] = c_sub(a1, ib1);
+    v[2] = c_add(a2, ib2);
+    v[3] = c_sub(a2, ib2);
+}
+
+template <int R, int S> __device__ __forceinline__ void dft(float2* v) {
+    if constexpr (R == 2) dft2<S>(v);
+    else if constexpr (R == 4) dft4<S>(v);
+    else if constexpr (R == 5) dft5<S>(v);
+    else if constexpr (R == 8) dft8<S>(v);
+    else if constexpr (R == 16) dft16<S>(v);
+    else static_assert(R == 2, "unsupported radix");
+}
+
+// ---------------------------------------------------------------------------------------------
+// one Stockham pass; every thread of the CTA must call it (it contains __syncthreads)
+// ---------------------------------------------------------------------------------------------
+template <int L, int T, int R, int NS, int S>
+__device__ __forceinline__ void fft_pass(float2* buf, int es, int j, bool active, const float2* __restrict__ tw) {
+    constexpr int NB = L / R;                // butterflies in the pass
+    constexpr int BPT = (NB + T - 1) / T;    // butterflies per thread
+    static_assert(L % R == 0, "radix must divide the length");
+    float2 v[BPT][R];
+#pragma unroll
+    for (int m = 0; m < BPT; ++m) {
+        const int b = j + m * T;
+        if (active && (NB % T == 0 || b < NB)) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[m][t] = buf[spad(b + t * NB) * es];
+            if constexpr (NS > 1) {
+                const int bm = b % NS;
+#pragma unroll
+                for (int t = 1; t < R; ++t) {
+                    float2 w = __ldg(&tw[bm * t * (L / (NS * R))]);
+                    if constexpr (S > 0) w.y = -w.y;
+                    v[m][t] = c_mul(v[m][t], w);
+                }
+            }
+            dft<R, S>(v[m]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < BPT; ++m) {
+        const int b = j + m * T;
+        if (active && (NB % T == 0 || b < NB)) {
+            const int base = (b / NS) * NS * R + (b % NS);
+#pragma unroll
+            for (int t = 0; t < R; ++t) buf[spad(base + t * NS) * es] = v[m][t];
+        }
+    }
+    __syncthreads();
+}
+
+template <int L, int T, int S, int NS, int R, int... Rest>
+__device__ __forceinline__ void fft_passes(float2* buf, int es, int j, bool active, const float2* __restrict__ tw) {
+    fft_pass<L, T, R, NS, S>(buf, es, j, active, tw);
+    if constexpr (sizeof...(Rest) > 0) fft_passes<L, T, S, NS * R, Rest...>(buf, es, j, active, tw);
+}
+
+// Radix plans: every length uses radix 16 first; T = threads per sequence.
+template <int L> struct FftPlan;
+template <> struct FftPlan<128> { static constexpr int T = 8; };
+template <> struct FftPlan<256> { static constexpr int T = 16; };
+template <> struct FftPlan<400> { static constexpr int T = 25; };
+template <> struct FftPlan<512> { static constexpr int T = 32; };
+template <> struct FftPlan<1024> { static constexpr int T = 64; };
+
+// In-place FFT of one sequence (element i at buf[spad(i) * es]) by thread j < T of its group.
+// S = -1 forward, +1 inverse.  Threads with active = false only take part in the barriers.
+template <int L, int S>
+__device__ __forceinline__ void fft(float2* buf, int es, int j, bool active, const float2* __restrict__ tw) {
+    constexpr int T = FftPlan<L>::T;
+    if constexpr (L == 128) fft_passes<L, T, S, 1, 16, 8>(buf, es, j, active, tw);
+    else if constexpr (L == 256) fft_passes<L, T, S, 1, 16, 16>(buf, es, j, active, tw);
+    else if constexpr (L == 400) fft_passes<L, T, S, 1, 16, 5, 5>(buf, es, j, active, tw);
+    else if constexpr (L == 512) fft_passes<L, T, S, 1, 16, 16, 2>(buf, es, j, active, tw);
+    else if constexpr (L == 1024) fft_passes<L, T, S, 1, 16, 16, 4>(buf, es, j, active, tw);
+}
+
+}  // namespace fmbym

@@ -1,0 +1,655 @@
+// Forward kernels of the decoupled Fourier pose search (Alg. 1) for sm_103a.
+//
+// Per size group of B pairs the search is eight launches on one stream:
+//   k_s1_rows   Hann window + real row FFTs of f and g (two real rows per complex FFT)
+//   k_s1_cols   column FFTs, band-pass and |.|                       -> magnitudes [u][v]
+//   k_angle     bilinear Cart2Pol of both magnitudes + FFT along angle, summed over radii
+//   k_theta     inverse FFT along angle -> c_theta, z-score, softmax, expectation -> theta
+//   k_s2_rows   bilinear Rotate of f by theta (on load) + ZeroPad + real row FFTs of f' and g
+//   k_s2_cols   column FFTs of f' and g, conj(F') G, inverse column FFT, keep the N lag rows
+//   k_s2_c2r    inverse real row FFTs, keep the N lag columns -> c_xy + block statistics
+//   k_sxy       z-score, softmax and expectation over c_xy -> (t_x, t_y)
+// Every FFT runs in shared memory (fft.cuh); HBM sees each spectrum once per pass.
+#include <cfloat>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace fmbym {
+
+// ---------------------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum (or max) over a block whose size is a multiple of 32; every thread gets the result.
+template <bool MAX>
+__device__ __forceinline__ float block_reduce(float v, float* red) {
+    v = MAX ? warp_max(v) : warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        float r = lane < nw ? red[lane] : (MAX ? -FLT_MAX : 0.f);
+        r = MAX ? warp_max(r) : warp_sum(r);
+        if (lane == 0) red[0] = r;
+    }
+    __syncthreads();
+    return red[0];
+}
+
+// |F| at integer frequency (vi, ui) of the N-periodic spectrum, read from the u-major half plane
+// m[u][v] (u <= N/2) through |F(-v,-u)| = |F(v,u)|.
+__device__ __forceinline__ float mag_at(const float* __restrict__ m, int n, int vi, int ui) {
+    vi &= n - 1;
+    ui &= n - 1;
+    if (ui > (n >> 1)) {
+        vi = (n - vi) & (n - 1);
+        ui = n - ui;
+    }
+    return __ldg(&m[ui * n + vi]);
+}
+
+// p = c + a d1 + b d2 with a = ah + al and b = bh + bl (float splits of double values) and small
+// integer d1, d2.  Error-free products and sums keep p to ~1e-7 px so that the rotation does not
+// add error beyond the rounding of theta itself.  Returns floor(p) and p - floor(p).
+__device__ __forceinline__ void rot_coord(float ah, float al, float d1, float bh, float bl, float d2, float c,
+                                          int& i0, float& fr) {
+    const float p1 = __fmul_rn(ah, d1), e1 = fmaf(ah, d1, -p1);
+    const float p2 = __fmul_rn(bh, d2), e2 = fmaf(bh, d2, -p2);
+    const float s = __fadd_rn(p1, p2), t = __fsub_rn(s, p1);
+    const float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, t)), __fsub_rn(p2, t));
+    const float h = __fadd_rn(c, s), t2 = __fsub_rn(h, c);
+    const float eh = __fadd_rn(__fsub_rn(c, __fsub_rn(h, t2)), __fsub_rn(s, t2));
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(es, eh)), fmaf(al, d1, __fmul_rn(bl, d2)));
+    float fl = floorf(h);
+    float f = __fadd_rn(__fsub_rn(h, fl), lo);
+    if (f < 0.f) {
+        f += 1.f;
+        fl -= 1.f;
+    } else if (f >= 1.f) {
+        f -= 1.f;
+        fl += 1.f;
+    }
+    i0 = (int)fl;
+    fr = f;
+}
+
+// f'(X, Y) = bilinear(f, c + R(-theta)([X, Y] - c)), zero outside the scan (Alg. 1 Rotate).
+__device__ __forceinline__ float rotated_sample(const float* __restrict__ src, int n, int X, int Y, float ch,
+                                                float cl, float sh, float sl) {
+    const float c = 0.5f * n, dx = (float)X - c, dy = (float)Y - c;
+    int x0, y0;
+    float fx, fy;
+    rot_coord(ch, cl, dx, sh, sl, dy, c, x0, fx);    // px = c + cos dx + sin dy
+    rot_coord(ch, cl, dy, -sh, -sl, dx, c, y0, fy);  // py = c - sin dx + cos dy
+    float v = 0.f;
+    const bool xin0 = (unsigned)x0 < (unsigned)n, xin1 = (unsigned)(x0 + 1) < (unsigned)n;
+    if ((unsigned)y0 < (unsigned)n) {
+        const float* r = src + (size_t)y0 * n;
+        if (xin0) v += (1.f - fy) * (1.f - fx) * __ldg(r + x0);
+        if (xin1) v += (1.f - fy) * fx * __ldg(r + x0 + 1);
+    }
+    if ((unsigned)(y0 + 1) < (unsigned)n) {
+        const float* r = src + (size_t)(y0 + 1) * n;
+        if (xin0) v += fy * (1.f - fx) * __ldg(r + x0);
+        if (xin1) v += fy * fx * __ldg(r + x0 + 1);
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// stage 1
+// ---------------------------------------------------------------------------------------------
+
+// Hann-windowed real row FFTs of f (z = 0) and g (z = 1).  Rows 2k and 2k+1 share one complex
+// FFT; the output row keeps u in [0, N/2) with the real DC and Nyquist values packed in u = 0.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_s1_rows(DevPlan p, const long long* __restrict__ tab,
+                                                      const float* __restrict__ f, const float* __restrict__ g,
+                                                      float2* __restrict__ s1, int B) {
+    constexpr int T = FftPlan<N>::T, FPC = kThreads / T, SL = spad(N), W = N / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z;
+    const float* __restrict__ src = (s ? g : f) + tab[3 * q];
+    const int r0 = blockIdx.x * FPC * 2;
+    for (int idx = threadIdx.x; idx < FPC * 2 * (N / 4); idx += kThreads) {
+        const int rr = idx / (N / 4), x4 = (idx % (N / 4)) * 4, row = r0 + rr;
+        float4 v = __ldg(reinterpret_cast<const float4*>(src + (size_t)row * N + x4));
+        if (p.window) {
+            const float wr = __ldg(&p.win[row]);
+            v.x *= wr * __ldg(&p.win[x4]);
+            v.y *= wr * __ldg(&p.win[x4 + 1]);
+            v.z *= wr * __ldg(&p.win[x4 + 2]);
+            v.w *= wr * __ldg(&p.win[x4 + 3]);
+        }
+        float* base = reinterpret_cast<float*>(sm + (rr >> 1) * SL) + (rr & 1);
+        base[2 * spad(x4)] = v.x;
+        base[2 * spad(x4 + 1)] = v.y;
+        base[2 * spad(x4 + 2)] = v.z;
+        base[2 * spad(x4 + 3)] = v.w;
+    }
+    __syncthreads();
+    fft<N, -1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_n);
+    float2* out = s1 + (size_t)(s * B + q) * N * W;
+    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+        const int k = idx / W, u = idx % W, row = r0 + 2 * k;
+        const float2* Z = sm + k * SL;
+        float2 xa, xb;
+        if (u == 0) {
+            const float2 z0 = Z[0], zn = Z[spad(W)];
+            xa = make_float2(z0.x, zn.x);
+            xb = make_float2(z0.y, zn.y);
+        } else {
+            const float2 zu = Z[spad(u)], zm = Z[spad(N - u)];
+            xa = make_float2(0.5f * (zu.x + zm.x), 0.5f * (zu.y - zm.y));
+            xb = make_float2(0.5f * (zu.y + zm.y), -0.5f * (zu.x - zm.x));
+        }
+        out[(size_t)row * W + u] = xa;
+        out[(size_t)(row + 1) * W + u] = xb;
+    }
+}
+
+// Column FFTs of the packed row spectra, band-pass and magnitude.  Column 0 holds the DC and
+// Nyquist columns as one complex sequence; they are separated after the transform.  Output is
+// the u-major half plane m[u][v], u in [0, N/2], v in [0, N).
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* __restrict__ s1,
+                                                      float* __restrict__ mt, int B) {
+    constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C + 1, W = N / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
+    const float2* in = s1 + (size_t)(s * B + q) * N * W;
+    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
+        const int v = idx / C, c = idx % C;
+        sm[spad(v) * ES + c] = in[(size_t)v * W + u0 + c];
+    }
+    __syncthreads();
+    fft<N, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
+    float* out = mt + (size_t)(s * B + q) * (W + 1) * N;
+    for (int idx = threadIdx.x; idx < C * N; idx += kThreads) {
+        const int cc = idx / N, v = idx % N;
+        const int vs = v <= W ? v : v - N;
+        const float2 z = sm[spad(v) * ES + cc];
+        if (u0 + cc == 0) {
+            const float2 zm = sm[spad((N - v) & (N - 1)) * ES + cc];
+            const float ax = 0.5f * (z.x + zm.x), ay = 0.5f * (z.y - zm.y);
+            const float bx = 0.5f * (z.y + zm.y), by = -0.5f * (z.x - zm.x);
+            const int m0 = vs * vs, mn = vs * vs + W * W;
+            out[v] = (m0 >= p.m_lo && m0 <= p.m_hi) ? sqrtf(fmaf(ax, ax, ay * ay)) : 0.f;
+            out[(size_t)W * N + v] = (mn >= p.m_lo && mn <= p.m_hi) ? sqrtf(fmaf(bx, bx, by * by)) : 0.f;
+        } else {
+            const int u = u0 + cc, m = vs * vs + u * u;
+            out[(size_t)u * N + v] = (m >= p.m_lo && m <= p.m_hi) ? sqrtf(fmaf(z.x, z.x, z.y * z.y)) : 0.f;
+        }
+    }
+}
+
+// Cart2Pol of both magnitudes for kAngleRadii radii, packed as z[a] = A_f[a] + i A_g[a], FFT along
+// angle, then S[k] = sum_r conj(A^_f[k, r]) A^_g[k, r] for this chunk of radii.  The inverse FFT of
+// S summed over chunks is the circular correlation along angle summed over radius (Eq. 7).
+template <int NT>
+__global__ void k_angle(DevPlan p, const float* __restrict__ mt, float2* __restrict__ sp, int B) {
+    constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC + 1;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, ch = blockIdx.x, r0 = ch * RC, n = p.n, W = n / 2;
+    const float* mf = mt + (size_t)q * (W + 1) * n;
+    const float* mg = mt + (size_t)(B + q) * (W + 1) * n;
+    for (int idx = threadIdx.x; idx < NT * RC; idx += blockDim.x) {
+        const int a = idx / RC, rr = idx % RC, r = r0 + rr;
+        float2 z = make_float2(0.f, 0.f);
+        if (r < p.nr) {
+            const PolarSample ps = p.polar[a * p.nr + r];
+            const float w00 = (1.f - ps.fy) * (1.f - ps.fx), w01 = (1.f - ps.fy) * ps.fx;
+            const float w10 = ps.fy * (1.f - ps.fx), w11 = ps.fy * ps.fx;
+            z.x = w00 * mag_at(mf, n, ps.y0, ps.x0) + w01 * mag_at(mf, n, ps.y0, ps.x0 + 1) +
+                  w10 * mag_at(mf, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mf, n, ps.y0 + 1, ps.x0 + 1);
+            z.y = w00 * mag_at(mg, n, ps.y0, ps.x0) + w01 * mag_at(mg, n, ps.y0, ps.x0 + 1) +
+                  w10 * mag_at(mg, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mg, n, ps.y0 + 1, ps.x0 + 1);
+        }
+        sm[spad(a) * ES + rr] = z;
+    }
+    __syncthreads();
+    fft<NT, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, threadIdx.x < T * RC, p.tw_t);
+    float2* out = sp + ((size_t)q * gridDim.x + ch) * NT;
+    for (int k = threadIdx.x; k < NT; k += blockDim.x) {
+        const int km = k == 0 ? 0 : NT - k;
+        float sx = 0.f, sy = 0.f;
+#pragma unroll 4
+        for (int rr = 0; rr < RC; ++rr) {
+            const float2 z = sm[spad(k) * ES + rr], zm = sm[spad(km) * ES + rr];
+            const float ax = 0.5f * (z.x + zm.x), ay = 0.5f * (z.y - zm.y);
+            const float bx = 0.5f * (z.y + zm.y), by = -0.5f * (z.x - zm.x);
+            sx += ax * bx + ay * by;
+            sy += ax * by - ay * bx;
+        }
+        out[k] = make_float2(sx, sy);
+    }
+}
+
+// Sum the chunk spectra, inverse FFT along angle -> c_theta (lag order), then the soft-argmax of
+// Alg. 1 over the angle candidates k delta_theta, delta_theta = pi / n_theta.
+template <int NT>
+__global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restrict__ sp, int nch,
+                                               const long long* __restrict__ tab, float* __restrict__ th,
+                                               float* __restrict__ pose, float* __restrict__ c_theta) {
+    constexpr int T = FftPlan<NT>::T;
+    __shared__ float2 z[spad(NT)];
+    __shared__ float c[NT];
+    __shared__ float red[32];
+    const int q = blockIdx.x;
+    for (int k = threadIdx.x; k < NT; k += blockDim.x) {
+        float sx = 0.f, sy = 0.f;
+        for (int h = 0; h < nch; ++h) {
+            const float2 v = sp[((size_t)q * nch + h) * NT + k];
+            sx += v.x;
+            sy += v.y;
+        }
+        z[spad(k)] = make_float2(sx, sy);
+    }
+    __syncthreads();
+    fft<NT, +1>(z, 1, threadIdx.x, threadIdx.x < T, p.tw_t);
+    float lsum = 0.f, lmax = -FLT_MAX;
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) {
+        const float v = z[spad((i - NT / 2 + NT) % NT)].x * (1.f / NT);
+        c[i] = v;
+        lsum += v;
+        lmax = fmaxf(lmax, v);
+    }
+    const float mean = block_reduce<false>(lsum, red) * (1.f / NT);
+    const float cmax = block_reduce<true>(lmax, red);
+    float lvar = 0.f;
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) lvar += (c[i] - mean) * (c[i] - mean);
+    const float sd = sqrtf(block_reduce<false>(lvar, red) * (1.f / NT));
+    const float inv = p.score_norm == 1 ? 1.f / p.temp_theta : (sd > 0.f ? 1.f / (sd * p.temp_theta) : 0.f);
+    float le = 0.f, lek = 0.f;
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) {
+        const float e = expf((c[i] - cmax) * inv);
+        le += e;
+        lek += e * (float)(i - NT / 2);
+    }
+    const float se = block_reduce<false>(le, red);
+    const float sek = block_reduce<false>(lek, red);
+    if (c_theta) {
+        float* out = c_theta + tab[3 * q + 1];
+        for (int i = threadIdx.x; i < NT; i += blockDim.x) out[i] = c[i];
+    }
+    if (threadIdx.x == 0) {
+        const float theta = (float)((double)sek / (double)se * (3.14159265358979323846 / NT));
+        pose[3 * tab[3 * q + 2]] = theta;
+        double sd_, cd_;
+        sincos((double)theta, &sd_, &cd_);
+        const float ch = (float)cd_, sh = (float)sd_;
+        float* t = th + 8 * q;
+        t[0] = theta;
+        t[1] = ch;
+        t[2] = (float)(cd_ - (double)ch);
+        t[3] = sh;
+        t[4] = (float)(sd_ - (double)sh);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// stage 2
+// ---------------------------------------------------------------------------------------------
+
+// Rows of the rotated source f' (z = 0, rotation on load) and of g (z = 1), zero-padded to P,
+// real row FFTs packed two rows per complex FFT, output u in [0, P/2) (DC/Nyquist packed in 0).
+template <int N, int P>
+__global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
+                                                      const float* __restrict__ f, const float* __restrict__ g,
+                                                      const float* __restrict__ th, float2* __restrict__ s2, int B) {
+    constexpr int T = FftPlan<P>::T, FPC = kThreads / T, SL = spad(P), W = P / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
+    const float* __restrict__ src = (s ? g : f) + tab[3 * q];
+    if (s == 0) {
+        const float* t = th + 8 * q;
+        const float ch = t[1], cl = t[2], sh = t[3], sl = t[4];
+        for (int idx = threadIdx.x; idx < FPC * 2 * N; idx += kThreads) {
+            const int rr = idx / N, x = idx % N;
+            const float v = rotated_sample(src, N, x, r0 + rr, ch, cl, sh, sl);
+            reinterpret_cast<float*>(sm + (rr >> 1) * SL + spad(x))[rr & 1] = v;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < FPC * 2 * (N / 4); idx += kThreads) {
+            const int rr = idx / (N / 4), x4 = (idx % (N / 4)) * 4;
+            const float4 v = __ldg(reinterpret_cast<const float4*>(src + (size_t)(r0 + rr) * N + x4));
+            float* base = reinterpret_cast<float*>(sm + (rr >> 1) * SL) + (rr & 1);
+            base[2 * spad(x4)] = v.x;
+            base[2 * spad(x4 + 1)] = v.y;
+            base[2 * spad(x4 + 2)] = v.z;
+            base[2 * spad(x4 + 3)] = v.w;
+        }
+    }
+    if constexpr (P > N) {
+        for (int idx = threadIdx.x; idx < FPC * (P - N); idx += kThreads) {
+            const int k = idx / (P - N), x = N + idx % (P - N);
+            sm[k * SL + spad(x)] = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    fft<P, -1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
+    float2* out = s2 + (size_t)(s * B + q) * N * W;
+    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+        const int k = idx / W, u = idx % W, row = r0 + 2 * k;
+        const float2* Z = sm + k * SL;
+        float2 xa, xb;
+        if (u == 0) {
+            const float2 z0 = Z[0], zn = Z[spad(W)];
+            xa = make_float2(z0.x, zn.x);
+            xb = make_float2(z0.y, zn.y);
+        } else {
+            const float2 zu = Z[spad(u)], zm = Z[spad(P - u)];
+            xa = make_float2(0.5f * (zu.x + zm.x), 0.5f * (zu.y - zm.y));
+            xb = make_float2(0.5f * (zu.y + zm.y), -0.5f * (zu.x - zm.x));
+        }
+        out[(size_t)row * W + u] = xa;
+        out[(size_t)(row + 1) * W + u] = xb;
+    }
+}
+
+// Column pass of the correlation: FFT the columns of F' and G (rows >= N are the zero pad),
+// multiply conj(F') G (A1), inverse FFT, keep the N lag rows s_y in [-N/2, N/2).  Column 0 holds
+// the DC and Nyquist columns packed; their products are formed after separating them.
+template <int N, int P>
+__global__ void __launch_bounds__(kThreads) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
+                                                      float2* __restrict__ s3, int B) {
+    constexpr int T = FftPlan<P>::T, C = kThreads / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
+    constexpr int PER = P * C / kThreads;
+    extern __shared__ float2 sm[];
+    float2* tf = sm;
+    float2* tg = sm + TILE;
+    const int q = blockIdx.y, u0 = blockIdx.x * C;
+    const float2* inf = s2 + (size_t)q * N * W;
+    const float2* ing = s2 + (size_t)(B + q) * N * W;
+    for (int idx = threadIdx.x; idx < P * C; idx += kThreads) {
+        const int v = idx / C, c = idx % C;
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (v < N) {
+            a = inf[(size_t)v * W + u0 + c];
+            b = ing[(size_t)v * W + u0 + c];
+        }
+        tf[spad(v) * ES + c] = a;
+        tg[spad(v) * ES + c] = b;
+    }
+    __syncthreads();
+    const int c = threadIdx.x / T, j = threadIdx.x % T;
+    fft<P, -1>(tf + c, ES, j, true, p.tw_p);
+    fft<P, -1>(tg + c, ES, j, true, p.tw_p);
+    float2 qv[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * kThreads, v = idx / C, cc = idx % C;
+        const float2 F = tf[spad(v) * ES + cc], G = tg[spad(v) * ES + cc];
+        if (u0 + cc == 0) {
+            const int vm = (P - v) & (P - 1);
+            const float2 Fm = tf[spad(vm) * ES + cc], Gm = tg[spad(vm) * ES + cc];
+            const float2 af = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
+            const float2 bf = make_float2(0.5f * (F.y + Fm.y), -0.5f * (F.x - Fm.x));
+            const float2 ag = make_float2(0.5f * (G.x + Gm.x), 0.5f * (G.y - Gm.y));
+            const float2 bg = make_float2(0.5f * (G.y + Gm.y), -0.5f * (G.x - Gm.x));
+            const float2 p0 = c_cjmul(af, ag), pn = c_cjmul(bf, bg);
+            qv[m] = make_float2(p0.x - pn.y, p0.y + pn.x);
+        } else {
+            qv[m] = c_cjmul(F, G);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * kThreads, v = idx / C, cc = idx % C;
+        tg[spad(v) * ES + cc] = qv[m];
+    }
+    __syncthreads();
+    fft<P, +1>(tg + c, ES, j, true, p.tw_p);
+    float2* out = s3 + (size_t)q * N * W;
+    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
+        const int i = idx / C, cc = idx % C, v = (i - N / 2 + P) & (P - 1);
+        out[(size_t)i * W + u0 + cc] = tg[spad(v) * ES + cc];
+    }
+}
+
+// Inverse real row FFTs (two lag rows per complex FFT, Hermitian extension of the packed half
+// rows), keep the N lag columns s_x in [-N/2, N/2), scale by 1/P^2 -> c_xy.  Each block also
+// writes the mean, sum of squared deviations and maximum of its scores for the z-score.
+template <int N, int P>
+__global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long* __restrict__ tab,
+                                                     const float2* __restrict__ s3, float* __restrict__ cxy_ws,
+                                                     float* __restrict__ cxy_out, float* __restrict__ st, int B) {
+    constexpr int T = FftPlan<P>::T, FPC = kThreads / T, SL = spad(P), W = P / 2;
+    extern __shared__ float2 sm[];
+    __shared__ float red[32];
+    const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
+    const float2* in = s3 + (size_t)q * N * W;
+    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+        const int k = idx / W, u = idx % W;
+        const float2 a = in[(size_t)(i0 + 2 * k) * W + u], b = in[(size_t)(i0 + 2 * k + 1) * W + u];
+        float2* Z = sm + k * SL;
+        if (u == 0) {
+            Z[0] = make_float2(a.x, b.x);
+            Z[spad(W)] = make_float2(a.y, b.y);
+        } else {
+            Z[spad(u)] = make_float2(a.x - b.y, a.y + b.x);
+            Z[spad(P - u)] = make_float2(a.x + b.y, b.x - a.y);
+        }
+    }
+    __syncthreads();
+    fft<P, +1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
+    const float scale = 1.f / ((float)P * (float)P);
+    float* out = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N;
+    float lsum = 0.f, lmax = -FLT_MAX;
+    for (int idx = threadIdx.x; idx < FPC * N; idx += kThreads) {
+        const int k = idx / N, jj = idx % N, nn = (jj - N / 2 + P) & (P - 1);
+        const float2 z = sm[k * SL + spad(nn)];
+        const float va = z.x * scale, vb = z.y * scale;
+        out[(size_t)(i0 + 2 * k) * N + jj] = va;
+        out[(size_t)(i0 + 2 * k + 1) * N + jj] = vb;
+        lsum += va + vb;
+        lmax = fmaxf(lmax, fmaxf(va, vb));
+    }
+    constexpr float cnt = (float)(FPC * 2 * N);
+    const float mean = block_reduce<false>(lsum, red) * (1.f / cnt);
+    const float bmax = block_reduce<true>(lmax, red);
+    float lm2 = 0.f;
+    for (int idx = threadIdx.x; idx < FPC * N; idx += kThreads) {
+        const int k = idx / N, jj = idx % N, nn = (jj - N / 2 + P) & (P - 1);
+        const float2 z = sm[k * SL + spad(nn)];
+        const float da = z.x * scale - mean, db = z.y * scale - mean;
+        lm2 += da * da + db * db;
+    }
+    const float m2 = block_reduce<false>(lm2, red);
+    if (threadIdx.x == 0) {
+        float* o = st + ((size_t)q * gridDim.x + blockIdx.x) * 4;
+        o[0] = mean;
+        o[1] = m2;
+        o[2] = bmax;
+        o[3] = cnt;
+    }
+}
+
+// Soft-argmax over the translation candidates (Alg. 1 stage 2): the blocks of a pair first
+// combine the per-block statistics of k_s2_c2r into the mean, population std and maximum, then
+// each sums exp((c - max) / (std T)) and its first moments over a slab of rows; the last block
+// of the pair adds the slabs in order and writes (t_x, t_y) = delta_xy E[s].
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __restrict__ tab,
+                                                  const float* __restrict__ cxy_ws, const float* __restrict__ cxy_out,
+                                                  const float* __restrict__ st, int nblk, float* __restrict__ sx,
+                                                  unsigned* __restrict__ cnt, float* __restrict__ pose) {
+    __shared__ float red[32];
+    __shared__ float stat[2];
+    __shared__ bool last;
+    const int q = blockIdx.y;
+    if (threadIdx.x < 32) {
+        const float* s = st + (size_t)q * nblk * 4;
+        float lsum = 0.f, lmax = -FLT_MAX;
+        for (int i = threadIdx.x; i < nblk; i += 32) {
+            lsum += s[4 * i];
+            lmax = fmaxf(lmax, s[4 * i + 2]);
+        }
+        const float mu = warp_sum(lsum) / nblk;
+        const float cmax = warp_max(lmax);
+        float lm2 = 0.f;
+        for (int i = threadIdx.x; i < nblk; i += 32) {
+            const float d = s[4 * i] - mu;
+            lm2 += s[4 * i + 1] + s[4 * i + 3] * d * d;
+        }
+        const float m2 = warp_sum(lm2);
+        if (threadIdx.x == 0) {
+            const float sd = sqrtf(m2 / ((float)N * (float)N));
+            stat[0] = cmax;
+            stat[1] = p.score_norm == 1 ? 1.f / p.temp_xy : (sd > 0.f ? 1.f / (sd * p.temp_xy) : 0.f);
+        }
+    }
+    __syncthreads();
+    const float cmax = stat[0], inv = stat[1];
+    const float* c = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N;
+    constexpr int ROWS = N / kSplitXY;
+    const int y0 = blockIdx.x * ROWS;
+    float le = 0.f, lx = 0.f, ly = 0.f;
+    for (int idx = threadIdx.x; idx < ROWS * (N / 4); idx += kThreads) {
+        const int yy = y0 + idx / (N / 4), x4 = (idx % (N / 4)) * 4;
+        const float4 v = *reinterpret_cast<const float4*>(c + (size_t)yy * N + x4);
+        const float e0 = expf((v.x - cmax) * inv), e1 = expf((v.y - cmax) * inv);
+        const float e2 = expf((v.z - cmax) * inv), e3 = expf((v.w - cmax) * inv);
+        const float es = (e0 + e1) + (e2 + e3);
+        const float sx0 = (float)(x4 - N / 2);
+        le += es;
+        lx += es * sx0 + (e1 + 2.f * e2 + 3.f * e3);
+        ly += es * (float)(yy - N / 2);
+    }
+    const float se = block_reduce<false>(le, red);
+    const float sxx = block_reduce<false>(lx, red);
+    const float syy = block_reduce<false>(ly, red);
+    if (threadIdx.x == 0) {
+        float* o = sx + ((size_t)q * kSplitXY + blockIdx.x) * 4;
+        o[0] = se;
+        o[1] = sxx;
+        o[2] = syy;
+        __threadfence();
+        last = atomicAdd(&cnt[q], 1u) == kSplitXY - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile float* o = sx + (size_t)q * kSplitXY * 4;
+        float a = 0.f, bx = 0.f, by = 0.f;
+        for (int i = 0; i < kSplitXY; ++i) {
+            a += o[4 * i];
+            bx += o[4 * i + 1];
+            by += o[4 * i + 2];
+        }
+        const long long pr = tab[3 * q + 2];
+        pose[3 * pr + 1] = p.delta_xy * (bx / a);
+        pose[3 * pr + 2] = p.delta_xy * (by / a);
+        cnt[q] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+
+template <int N> constexpr size_t smem_rows() { return (size_t)(kThreads / FftPlan<N>::T) * spad(N) * sizeof(float2); }
+template <int N> constexpr size_t smem_cols1() {
+    return (size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) * sizeof(float2);
+}
+template <int P> constexpr size_t smem_cols2() {
+    return 2 * (size_t)spad(P) * (kThreads / FftPlan<P>::T + 1) * sizeof(float2);
+}
+template <int NT> constexpr size_t smem_angle() { return (size_t)spad(NT) * (kAngleRadii + 1) * sizeof(float2); }
+
+template <int NT>
+static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, const long long* tab, float* pose,
+                                       float* c_theta, cudaStream_t st) {
+    const int nch = angle_chunks(p);
+    w.tr->before(K_ANGLE, st);
+    k_angle<NT><<<dim3(nch, B), FftPlan<NT>::T * kAngleRadii, smem_angle<NT>(), st>>>(p, w.mt, w.sp, B);
+    w.tr->before(K_THETA, st);
+    k_theta<NT><<<B, 256, 0, st>>>(p, w.sp, nch, tab, w.th, pose, c_theta);
+    return cudaGetLastError();
+}
+
+template <int N, int P>
+static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                             const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
+    constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T;
+    w.tr->before(K_S1_ROWS, st);
+    k_s1_rows<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st>>>(p, tab, f, g, w.s1, B);
+    w.tr->before(K_S1_COLS, st);
+    k_s1_cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_cols1<N>(), st>>>(p, w.s1, w.mt, B);
+    cudaError_t e;
+    if (p.nt == 128) e = launch_stage1_angle<128>(p, w, B, tab, pose, c_theta, st);
+    else if (p.nt == 256) e = launch_stage1_angle<256>(p, w, B, tab, pose, c_theta, st);
+    else e = launch_stage1_angle<400>(p, w, B, tab, pose, c_theta, st);
+    if (e != cudaSuccess) return e;
+    w.tr->before(K_S2_ROWS, st);
+    k_s2_rows<N, P><<<dim3((N / 2) / (kThreads / T2), B, 2), kThreads, smem_rows<P>(), st>>>(p, tab, f, g, w.th,
+                                                                                                w.s2, B);
+    w.tr->before(K_S2_COLS, st);
+    k_s2_cols<N, P><<<dim3((P / 2) / (kThreads / T2), B), kThreads, smem_cols2<P>(), st>>>(p, w.s2, w.s3, B);
+    const int nblk = (N / 2) / (kThreads / T2);
+    w.tr->before(K_S2_C2R, st);
+    k_s2_c2r<N, P><<<dim3(nblk, B), kThreads, smem_rows<P>(), st>>>(p, tab, w.s3, w.cxy, c_xy, w.st, B);
+    w.tr->before(K_SXY, st);
+    k_sxy<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose);
+    w.tr->close(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                           const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    if (p.n == 128) return p.p == 256 ? launch_np<128, 256>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+                                      : launch_np<128, 128>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+    if (p.n == 256) return p.p == 512 ? launch_np<256, 512>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+                                      : launch_np<256, 256>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+    return p.p == 1024 ? launch_np<512, 1024>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+                       : launch_np<512, 512>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int N, int P>
+static cudaError_t prepare_np() {
+    cudaError_t e;
+    if ((e = allow_smem(k_s1_rows<N>, smem_rows<N>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_s1_cols<N>, smem_cols1<N>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_s2_rows<N, P>, smem_rows<P>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_s2_cols<N, P>, smem_cols2<P>())) != cudaSuccess) return e;
+    return allow_smem(k_s2_c2r<N, P>, smem_rows<P>());
+}
+
+const char* const kKindNames[K_COUNT] = {
+    "s1_rows", "s1_cols", "angle", "theta", "s2_rows", "s2_cols", "s2_c2r", "sxy",
+    "b_sxy", "b_cols", "b_rows", "b_rot", "b_theta", "b_angle", "b_s1cols", "b_s1rows", "b_misc"};
+
+cudaError_t prepare_forward_kernels() {
+    cudaError_t e;
+    if ((e = prepare_np<128, 256>()) != cudaSuccess) return e;
+    if ((e = prepare_np<128, 128>()) != cudaSuccess) return e;
+    if ((e = prepare_np<256, 512>()) != cudaSuccess) return e;
+    if ((e = prepare_np<256, 256>()) != cudaSuccess) return e;
+    if ((e = prepare_np<512, 1024>()) != cudaSuccess) return e;
+    if ((e = prepare_np<512, 512>()) != cudaSuccess) return e;
+    if ((e = allow_smem(k_angle<128>, smem_angle<128>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_angle<256>, smem_angle<256>())) != cudaSuccess) return e;
+    return allow_smem(k_angle<400>, smem_angle<400>());
+}
+
+}  // namespace fmbym

@@ -1,0 +1,150 @@
+"""Python face of the C ABI: a handle object over torch CUDA tensors and an autograd Function.
+
+Only marshalling happens here: every step of the search runs in the CUDA library.  torch supplies
+device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def size_cfg(n, n_theta, n_r, temp_theta=1.0, temp_xy=1.0, delta_xy=1.0, window=1, pad_mode=0,
+             score_norm=0, band_lo=2.0, band_hi=None):
+    """Parameters of one scan size (fmbym_size_cfg); band_hi defaults to N/2."""
+    return dict(n=int(n), n_theta=int(n_theta), n_r=int(n_r), temp_theta=float(temp_theta),
+                temp_xy=float(temp_xy), delta_xy=float(delta_xy), window=int(window), pad_mode=int(pad_mode),
+                score_norm=int(score_norm), band_lo=float(band_lo),
+                band_hi=float(n / 2 if band_hi is None else band_hi))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class PoseSearch:
+    """A library handle: plans and workspace for the given sizes and up to max_pairs pairs per call."""
+
+    def __init__(self, sizes, max_pairs, device=None):
+        self.sizes = [dict(s) for s in sizes]
+        self.max_pairs = int(max_pairs)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        L = _lib.lib()
+        arr = (_lib.SizeCfg * len(self.sizes))(*[_lib.SizeCfg(**s) for s in self.sizes])
+        self._arr = arr
+        cfg = _lib.Config(len(self.sizes), arr, self.max_pairs, 0)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(L.fmbym_create(ctypes.byref(h), ctypes.byref(cfg)), None)
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("handle is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().fmbym_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self):
+        return int(_lib.lib().fmbym_workspace_bytes(self.handle))
+
+    # -- layout helpers ------------------------------------------------------------------------
+    def _layout(self, f, size_idx, offsets):
+        """Returns (n_pairs, size_idx array or None, offsets array or None, n_theta list)."""
+        if size_idx is None:
+            if f.dim() != 3:
+                raise ValueError("f must be [B, N, N] when size_idx is not given")
+            n_pairs = f.shape[0]
+            if f.shape[1] != self.sizes[0]["n"] or f.shape[2] != self.sizes[0]["n"]:
+                raise ValueError("scan size does not match size 0 of the handle")
+            return n_pairs, None, None, [self.sizes[0]["n_theta"]] * n_pairs, [self.sizes[0]["n"]] * n_pairs
+        si = np.ascontiguousarray(np.asarray(size_idx, dtype=np.int32))
+        n_pairs = si.size
+        off = None if offsets is None else np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        return n_pairs, si, off, [self.sizes[i]["n_theta"] for i in si], [self.sizes[i]["n"] for i in si]
+
+    # -- calls ---------------------------------------------------------------------------------
+    def pose(self, f, g, size_idx=None, offsets=None, want_c_theta=False, want_c_xy=False, stream=None,
+             out=None):
+        """Forward search; returns dict(pose [B,3], c_theta (flat) or None, c_xy (like f) or None)."""
+        n_pairs, si, off, nts, _ = self._layout(f, size_idx, offsets)
+        pose = out if out is not None else torch.empty((n_pairs, 3), device=f.device, dtype=torch.float32)
+        ct = torch.empty(sum(nts), device=f.device, dtype=torch.float32) if want_c_theta else None
+        cxy = torch.empty_like(f) if want_c_xy else None
+        st = _lib.lib().fmbym_pose(self.handle, _stream(stream), n_pairs,
+                                   None if si is None else si.ctypes.data_as(ctypes.c_void_p),
+                                   None if off is None else off.ctypes.data_as(ctypes.c_void_p),
+                                   _ptr(f), _ptr(g), _ptr(pose), _ptr(ct), _ptr(cxy))
+        _lib.check(st, self.handle)
+        return dict(pose=pose, c_theta=ct, c_xy=cxy)
+
+    def pose_backward(self, f, g, dpose, size_idx=None, offsets=None, stream=None):
+        """Adjoint: (df, dg) given dL/dpose [B, 3]."""
+        n_pairs, si, off, _, _ = self._layout(f, size_idx, offsets)
+        df = torch.empty_like(f)
+        dg = torch.empty_like(g)
+        dpose = dpose.contiguous().to(torch.float32)
+        st = _lib.lib().fmbym_pose_backward(self.handle, _stream(stream), n_pairs,
+                                            None if si is None else si.ctypes.data_as(ctypes.c_void_p),
+                                            None if off is None else off.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(f), _ptr(g), _ptr(dpose), _ptr(df), _ptr(dg))
+        _lib.check(st, self.handle)
+        return df, dg
+
+    def pose_host(self, f_host, g_host, size_idx=None, offsets=None, stream=None):
+        """Forward search from host (CPU, ideally pinned) tensors; returns the pose as a CPU tensor.
+        Copies in, computes and copies out inside the call, which synchronises the stream."""
+        if size_idx is None:
+            n_pairs = f_host.shape[0]
+            si = off = None
+        else:
+            si = np.ascontiguousarray(np.asarray(size_idx, dtype=np.int32))
+            n_pairs = si.size
+            off = None if offsets is None else np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        pose = torch.empty((n_pairs, 3), dtype=torch.float32, pin_memory=f_host.is_pinned())
+        st = _lib.lib().fmbym_pose_host(self.handle, _stream(stream), n_pairs,
+                                        None if si is None else si.ctypes.data_as(ctypes.c_void_p),
+                                        None if off is None else off.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.c_longlong(f_host.numel()), _ptr(f_host), _ptr(g_host), _ptr(pose))
+        _lib.check(st, self.handle)
+        return pose
+
+
+class PoseFunction(torch.autograd.Function):
+    """pose = ScanMatch(f, g) with the library's hand-written adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, f, g, search, size_idx=None, offsets=None):
+        ctx.search, ctx.size_idx, ctx.offsets = search, size_idx, offsets
+        ctx.save_for_backward(f, g)
+        return search.pose(f.contiguous(), g.contiguous(), size_idx, offsets)["pose"]
+
+    @staticmethod
+    def backward(ctx, dpose):
+        f, g = ctx.saved_tensors
+        df, dg = ctx.search.pose_backward(f.contiguous(), g.contiguous(), dpose, ctx.size_idx, ctx.offsets)
+        return df, dg, None, None, None
+
+
+def scan_match(f, g, search, size_idx=None, offsets=None):
+    """Differentiable batched ScanMatch (Alg. 1): pose [B, 3] = (theta, t_x, t_y)."""
+    return PoseFunction.apply(f, g, search, size_idx, offsets)

@@ -1,0 +1,67 @@
+"""CPU-side checks of the CUDA library: it builds for sm_103a, loads, exports every entry point
+that include/fmbym.h declares, and rejects bad configurations before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2203_00459_gb300 import build, _lib
+    build.build()
+    return _lib.lib()
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(fmbym_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert "fmbym_pose" in names and "fmbym_create" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version(L):
+    assert L.fmbym_version() >= 10000
+
+
+def _create(L, **over):
+    from paper_2203_00459_gb300 import _lib
+    from paper_2203_00459_gb300.search import size_cfg
+    c = size_cfg(128, 128, 64)
+    c.update(over)
+    arr = (_lib.SizeCfg * 1)(_lib.SizeCfg(**c))
+    cfg = _lib.Config(1, arr, 4, 0)
+    h = ctypes.c_void_p()
+    st = L.fmbym_create(ctypes.byref(h), ctypes.byref(cfg))
+    return st, h, L.fmbym_last_error(None).decode()
+
+
+@pytest.mark.parametrize("over,status", [
+    (dict(n=100), 2), (dict(n=1024), 2), (dict(n_theta=733), 2), (dict(n_r=0), 1), (dict(n_r=65), 1),
+    (dict(temp_theta=0.0), 1), (dict(delta_xy=-1.0), 1), (dict(pad_mode=2), 1), (dict(score_norm=3), 1),
+    (dict(window=7), 1), (dict(band_lo=5.0, band_hi=4.0), 1)])
+def test_create_rejects_bad_sizes_before_any_cuda_call(L, over, status):
+    st, h, msg = _create(L, **over)
+    assert st == status and not h.value and msg
+
+
+def test_null_arguments(L):
+    assert L.fmbym_create(None, None) == 1
+    h = ctypes.c_void_p()
+    assert L.fmbym_create(ctypes.byref(h), None) == 1
+    assert L.fmbym_pose(None, None, 1, None, None, None, None, None, None, None) == 1
+    assert L.fmbym_pose_backward(None, None, 1, None, None, None, None, None, None, None) == 1
+    L.fmbym_destroy(None)
