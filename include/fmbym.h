@@ -142,6 +142,33 @@ const char* fmbym_trace_kind_name(int kind);
 /* Number of kernels the handle has launched since it was created. */
 long long fmbym_launch_count(const fmbym_handle* h);
 
+/* fmbym_pose without a handle and without any device allocation.  (The paper has no counterpart:
+ * this is a deployment convenience.)  Some callers cannot call cudaMalloc: a plug-in inside a host
+ * framework that owns every device allocation, or a real-time process whose device memory is
+ * fixed at start-up.  This call uses the same kernels as fmbym_pose, but all of its scratch (the
+ * size tables, the pair table, counters and every intermediate) lives in one static device array
+ * of fmbym_noalloc_capacity() bytes (16 MiB) inside the library, which every device that loads the
+ * library reserves until the process exits.
+ *   cfg       host pointer to one size configuration (validated as in fmbym_create)
+ *   n_pairs   pairs packed back to back: pair p at element offset p * N * N of f, g and c_xy
+ *   f, g, pose, c_theta, c_xy  as in fmbym_pose (device, caller-owned; c_theta and c_xy may be NULL)
+ * Limit: the whole footprint must fit the array (with the benchmark grids: one 512x512 pair, five
+ * 256x256 pairs or 24 128x128 pairs); larger requests return FMBYM_ERR_WORKSPACE and the message
+ * gives the bytes needed.  The first call on a device does a one-time set-up (it looks up the array's
+ * device address and sets kernel attributes), so make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents: the call clears what must
+ * start at zero itself, and re-uploads the size tables (a small synchronous host-to-device copy)
+ * when cfg differs from the previous call's.  Calls that overlap on the GPU (other streams, other
+ * host threads) race on the array.  Errors are reported by fmbym_noalloc_last_error(). */
+int fmbym_pose_noalloc(void* stream, const fmbym_size_cfg* cfg, int n_pairs, const float* f,
+                       const float* g, float* pose, float* c_theta, float* c_xy);
+
+/* Bytes of the static scratch array used by fmbym_pose_noalloc. */
+unsigned long long fmbym_noalloc_capacity(void);
+
+/* Text of the last failure of fmbym_pose_noalloc on this host thread ("" if none). */
+const char* fmbym_noalloc_last_error(void);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int fmbym_version(void);
 
