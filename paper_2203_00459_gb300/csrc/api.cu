@@ -43,6 +43,7 @@ struct fmbym_handle {
     float* d_stage_g = nullptr;
     float* d_stage_pose = nullptr;
     unsigned* d_cnt = nullptr;    // [max_pairs] completion counters, zero between launches
+    float* d_bpose = nullptr;     // [max_pairs][3] pose recomputed by the adjoint
     long long stage_elems = 0;
     Tracer tracer;
     std::string err;
@@ -69,15 +70,18 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
     t.cxy = (float*)take(b * n * n * sizeof(float));
     t.st = (float*)take(b * c2r_blocks(p) * 4 * sizeof(float));
     t.sx = (float*)take(b * kSplitXY * 4 * sizeof(float));
+    t.ct = (float*)take(b * p.nt * sizeof(float));
     if (backward) {
+        t.bsc = (float*)take(b * 16 * sizeof(float));
+        t.gpart = (float*)take(b * (n * n / 256) * sizeof(float));
+        t.gxx = (float*)take(b * kSplitXY * 4 * sizeof(float));
         t.b1 = (float2*)take(b * n * Wp * sizeof(float2));
         t.b2 = (float2*)take(2 * b * n * Wp * sizeof(float2));
         t.gfr = (float*)take(b * n * n * sizeof(float));
-        t.gth = (float*)take(b * 4 * sizeof(float));
+        t.bdc = (float2*)take(b * p.nt * sizeof(float2));
         t.gpol = (float*)take(2 * b * p.nt * p.nr * sizeof(float));
         t.gmt = (float*)take(2 * b * (Wn + 1) * n * sizeof(float));
         t.gs1 = (float2*)take(2 * b * n * Wn * sizeof(float2));
-        t.gxx = (float*)take(b * kSplitXY * 4 * sizeof(float));
     }
     if (w) *w = t;
     return off;
@@ -175,11 +179,44 @@ cudaError_t build_plan(HostPlan& hp) {
             pol[(size_t)a * d.nr + r] = PolarSample{(int)x0, (int)y0, (float)(u - x0), (float)(v - y0)};
         }
     }
+    // transpose of the gather: for each half-plane element, the samples (a n_r + r) that read it
+    // and their bilinear weights, computed in float exactly as the gather kernel forms them
+    const int ne = (d.n / 2 + 1) * d.n;
+    std::vector<int> cnt(ne + 1, 0), col;
+    std::vector<float> wt;
+    {
+        struct Tap { int e, s; float w; };
+        std::vector<Tap> taps;
+        taps.reserve((size_t)4 * pol.size());
+        for (size_t sidx = 0; sidx < pol.size(); ++sidx) {
+            const PolarSample& ps = pol[sidx];
+            const float wy[2] = {1.f - ps.fy, ps.fy}, wx[2] = {1.f - ps.fx, ps.fx};
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    int vi = (ps.y0 + dy) & (d.n - 1), ui = (ps.x0 + dx) & (d.n - 1);
+                    if (ui > d.n / 2) {
+                        vi = (d.n - vi) & (d.n - 1);
+                        ui = d.n - ui;
+                    }
+                    taps.push_back(Tap{ui * d.n + vi, (int)sidx, wy[dy] * wx[dx]});
+                }
+        }
+        for (const Tap& t : taps) cnt[t.e + 1]++;
+        for (int i = 0; i < ne; ++i) cnt[i + 1] += cnt[i];
+        col.resize(taps.size());
+        wt.resize(taps.size());
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (const Tap& t : taps) {
+            col[fill[t.e]] = t.s;
+            wt[fill[t.e]++] = t.w;
+        }
+    }
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b_win = al(win.size() * 4), b_twn = al(twn.size() * 8), b_twp = al(twp.size() * 8),
-                 b_twt = al(twt.size() * 8), b_pol = al(pol.size() * sizeof(PolarSample));
+                 b_twt = al(twt.size() * 8), b_pol = al(pol.size() * sizeof(PolarSample)),
+                 b_ptr = al(cnt.size() * 4), b_col = al(col.size() * 4), b_wt = al(wt.size() * 4);
     char* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, b_win + b_twn + b_twp + b_twt + b_pol);
+    cudaError_t e = cudaMalloc(&base, b_win + b_twn + b_twp + b_twt + b_pol + b_ptr + b_col + b_wt);
     if (e != cudaSuccess) return e;
     hp.tables = base;
     char* cur = base;
@@ -194,8 +231,14 @@ cudaError_t build_plan(HostPlan& hp) {
     auto r3 = put(twp.data(), twp.size() * 8, b_twp);
     auto r4 = put(twt.data(), twt.size() * 8, b_twt);
     auto r5 = put(pol.data(), pol.size() * sizeof(PolarSample), b_pol);
-    for (auto& r : {r1, r2, r3, r4, r5})
+    auto r6 = put(cnt.data(), cnt.size() * 4, b_ptr);
+    auto r7 = put(col.data(), col.size() * 4, b_col);
+    auto r8 = put(wt.data(), wt.size() * 4, b_wt);
+    for (auto& r : {r1, r2, r3, r4, r5, r6, r7, r8})
         if (r.second != cudaSuccess) return r.second;
+    d.csr_ptr = (const int*)r6.first;
+    d.csr_col = (const int*)r7.first;
+    d.csr_w = (const float*)r8.first;
     d.win = (const float*)r1.first;
     d.tw_n = (const float2*)r2.first;
     d.tw_p = (const float2*)r3.first;
@@ -272,6 +315,7 @@ void fmbym_destroy(fmbym_handle* h) {
     cudaFree(h->d_stage_g);
     cudaFree(h->d_stage_pose);
     cudaFree(h->d_cnt);
+    cudaFree(h->d_bpose);
     if (h->h_tab) cudaFreeHost(h->h_tab);
     for (cudaEvent_t e : h->tracer.ev) cudaEventDestroy(e);
     if (h->tab_free) cudaEventDestroy(h->tab_free);
@@ -335,7 +379,8 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
         (e = cudaMalloc(&h->d_stage_g, sizeof(float) * h->stage_elems)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_pose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs)) != cudaSuccess ||
-        (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs)) != cudaSuccess) {
+        (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_bpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess) {
         fmbym_destroy(h);
         return cuda_fail(nullptr, e, "staging allocation");
     }
@@ -389,6 +434,7 @@ int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* s
         Ws w = ws_carve(p, gr.count, h->ws, true);
         w.tr = &h->tracer;
         w.cnt = h->d_cnt;
+        w.bpose = h->d_bpose;
         e = launch_backward(p, w, gr.count, h->d_tab + 3 * gr.first, f, g, dpose, df, dg, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
     }

@@ -1,13 +1,739 @@
-// Adjoint kernels of the decoupled Fourier pose search.
+// Adjoint of the decoupled Fourier pose search (the end-to-end differentiability of Sec. III-C,
+// through which the masking network of Sec. III-D is trained by Eq. 13).
+//
+// Given dL/d(theta, t_x, t_y) per pair, the kernels below produce dL/df and dL/dg.  The forward
+// intermediates are recomputed first (launch_forward into the workspace); nothing is kept between
+// calls.  Order of the adjoint, last forward step first:
+//   k_b_stats    translation soft-argmax adjoint: the two z-score reductions of dz
+//   k_b_rows     d c_xy formed on load, embedded in the P x P lag grid, real row FFTs
+//   k_b_cols     column FFTs of D, F' and G; conj(D) G (-> d f') and D F' (-> d g); inverse
+//   k_b_c2r      inverse row FFTs, keep x in [0, N): d f' and the stage-2 part of d g
+//   k_b_rot      Rotate adjoint: d f (transpose of the bilinear gather, in gather form) and
+//                d theta through the rotated source, reduced per pair
+//   k_b_theta    angle soft-argmax adjoint -> d c_theta, then its FFT along angle
+//   k_b_angle    angle-correlation adjoint in frequency: d A_f, d A_g
+//   k_b_polT     transpose of the bilinear Cart2Pol gather (precomputed CSR, no atomics)
+//   k_b_s1cols   |z| adjoint z/|z| with the band-pass, inverse column FFTs of the half plane
+//   k_b_s1rows   inverse row FFTs of the half plane, window -> stage-1 parts of d f and d g
+// Every reduction has a fixed order, so repeated calls give identical bits.
+#include <cfloat>
+
 #include "common.cuh"
+#include "dev_util.cuh"
 
 namespace fmbym {
 
-cudaError_t launch_backward(const DevPlan&, const Ws&, int, const long long*, const float*, const float*,
-                            const float*, float*, float*, cudaStream_t) {
-    return cudaErrorNotSupported;
+// ---------------------------------------------------------------------------------------------
+// translation soft-argmax adjoint
+// ---------------------------------------------------------------------------------------------
+
+// With p = softmax(y), y = (c - mean)/(std T), t = delta E_p[s]: dL/dy = p (q - <p, q>) with
+// q_s = delta (dtx s_x + dty s_y) and <p, q> = dtx t_x + dty t_y; dz = dL/dy / T.  The z-score
+// adjoint needs mean(dz) and mean(dz z) over all lags: each block sums a slab of rows and the last
+// block of a pair adds the slabs in order.  bsc[q] receives (mean dz, mean dz z, mean, std, max,
+// 1/(std T), sum of exp, <p, q>).
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_b_stats(DevPlan p, const long long* __restrict__ tab,
+                                                      const float* __restrict__ cxy, const float* __restrict__ st,
+                                                      int nblk, const float* __restrict__ sx,
+                                                      const float* __restrict__ bpose,
+                                                      const float* __restrict__ dpose, float* __restrict__ gxx,
+                                                      unsigned* __restrict__ cnt, float* __restrict__ bsc) {
+    __shared__ float red[32];
+    __shared__ float sh[8];
+    __shared__ bool last;
+    const int q = blockIdx.y;
+    const long long pr = tab[3 * q + 2];
+    if (threadIdx.x < 32) {
+        float mu, sd, cmax;
+        xy_stats_warp(st + (size_t)q * nblk * 4, nblk, (float)N * (float)N, mu, sd, cmax);
+        if (threadIdx.x == 0) {
+            const float* o = sx + (size_t)q * kSplitXY * 4;
+            float se = 0.f;
+            for (int i = 0; i < kSplitXY; ++i) se += o[4 * i];
+            sh[0] = mu;
+            sh[1] = sd;
+            sh[2] = cmax;
+            sh[3] = p.score_norm == 1 ? 1.f / p.temp_xy : (sd > 0.f ? 1.f / (sd * p.temp_xy) : 0.f);
+            sh[4] = se;
+        }
+    }
+    __syncthreads();
+    const float mu = sh[0], sd = sh[1], cmax = sh[2], inv = sh[3], se = sh[4];
+    const float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
+    const float pq = dtx * bpose[3 * pr + 1] + dty * bpose[3 * pr + 2];
+    const float dl = p.delta_xy, invT = 1.f / p.temp_xy, isd = sd > 0.f ? 1.f / sd : 0.f;
+    const float* c = cxy + (size_t)q * N * N;
+    constexpr int ROWS = N / kSplitXY;
+    const int y0 = blockIdx.x * ROWS;
+    float l1 = 0.f, l2 = 0.f;
+    for (int idx = threadIdx.x; idx < ROWS * N; idx += kThreads) {
+        const int yy = y0 + idx / N, xx = idx % N;
+        const float cv = c[(size_t)yy * N + xx];
+        const float pp = expf((cv - cmax) * inv) / se;
+        const float qq = dl * (dtx * (float)(xx - N / 2) + dty * (float)(yy - N / 2));
+        const float dz = pp * (qq - pq) * invT;
+        l1 += dz;
+        l2 += dz * (cv - mu) * isd;
+    }
+    const float s1 = block_reduce<false>(l1, red);
+    const float s2 = block_reduce<false>(l2, red);
+    if (threadIdx.x == 0) {
+        float* o = gxx + ((size_t)q * kSplitXY + blockIdx.x) * 4;
+        o[0] = s1;
+        o[1] = s2;
+        __threadfence();
+        last = atomicAdd(&cnt[q], 1u) == kSplitXY - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile float* o = gxx + (size_t)q * kSplitXY * 4;
+        float a = 0.f, b = 0.f;
+        for (int i = 0; i < kSplitXY; ++i) {
+            a += o[4 * i];
+            b += o[4 * i + 1];
+        }
+        float* r = bsc + (size_t)q * 16;
+        const float inn = 1.f / ((float)N * (float)N);
+        r[0] = a * inn;
+        r[1] = b * inn;
+        r[2] = mu;
+        r[3] = sd;
+        r[4] = cmax;
+        r[5] = inv;
+        r[6] = se;
+        r[7] = pq;
+        cnt[q] = 0u;
+    }
 }
 
-cudaError_t prepare_backward_kernels() { return cudaSuccess; }
+// d c_xy at lag (i, j) from the scores and the per-pair scalars of k_b_stats.
+__device__ __forceinline__ float dcxy(const DevPlan& p, const float* r, float cv, int i, int j, int n, float dtx,
+                                      float dty) {
+    const float pp = expf((cv - r[4]) * r[5]) / r[6];
+    const float qq = p.delta_xy * (dtx * (float)(j - n / 2) + dty * (float)(i - n / 2));
+    const float dz = pp * (qq - r[7]) / p.temp_xy;
+    if (p.score_norm == 1) return dz;
+    if (!(r[3] > 0.f)) return 0.f;
+    const float z = (cv - r[2]) / r[3];
+    return (dz - r[0] - z * r[1]) / r[3];
+}
+
+// ---------------------------------------------------------------------------------------------
+// padded correlation adjoint: d f'(x) = sum_s D(s) g(x + s), d g(y) = sum_s D(s) f'(y - s)
+// ---------------------------------------------------------------------------------------------
+
+// Lag rows of D (row i holds s_y = i - N/2; column j sits at P-position (j - N/2) mod P), two
+// rows per complex FFT of length P, packed real-FFT output rows [N][P/2].
+template <int N, int P>
+__global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long* __restrict__ tab,
+                                                     const float* __restrict__ cxy, const float* __restrict__ bsc,
+                                                     const float* __restrict__ dpose, float2* __restrict__ b1, int B) {
+    constexpr int T = FftPlan<P>::T, FPC = kThreads / T, SL = spad(P), W = P / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
+    const long long pr = tab[3 * q + 2];
+    const float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
+    const float* r = bsc + (size_t)q * 16;
+    const float* c = cxy + (size_t)q * N * N;
+    for (int idx = threadIdx.x; idx < FPC * P; idx += kThreads) {
+        const int k = idx / P, x = idx % P, j = (x + N / 2) & (P - 1), i = i0 + 2 * k;
+        float2 v = make_float2(0.f, 0.f);
+        if (j < N) {
+            v.x = dcxy(p, r, c[(size_t)i * N + j], i, j, N, dtx, dty);
+            v.y = dcxy(p, r, c[(size_t)(i + 1) * N + j], i + 1, j, N, dtx, dty);
+        }
+        sm[k * SL + spad(x)] = v;
+    }
+    __syncthreads();
+    fft<P, -1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
+    float2* out = b1 + (size_t)q * N * W;
+    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+        const int k = idx / W, u = idx % W, row = i0 + 2 * k;
+        const float2* Z = sm + k * SL;
+        float2 xa, xb;
+        if (u == 0) {
+            const float2 z0 = Z[0], zn = Z[spad(W)];
+            xa = make_float2(z0.x, zn.x);
+            xb = make_float2(z0.y, zn.y);
+        } else {
+            const float2 zu = Z[spad(u)], zm = Z[spad(P - u)];
+            xa = make_float2(0.5f * (zu.x + zm.x), 0.5f * (zu.y - zm.y));
+            xb = make_float2(0.5f * (zu.y + zm.y), -0.5f * (zu.x - zm.x));
+        }
+        out[(size_t)row * W + u] = xa;
+        out[(size_t)(row + 1) * W + u] = xb;
+    }
+}
+
+// Separates the packed column 0 of an FFT'd tile into the DC column (A) and Nyquist column (B).
+__device__ __forceinline__ void split0(float2 z, float2 zm, float2& a, float2& b) {
+    a = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+    b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+}
+
+// Column pass of the correlation adjoint: FFT columns of D (lag rows placed at their P-rows), F'
+// and G (rows < N); Q1 = conj(D) G and Q2 = D F' (the packed column 0 per DC/Nyquist part); inverse
+// column FFTs; keep the spatial rows y < N.
+template <int N, int P>
+__global__ void __launch_bounds__(kThreads) k_b_cols(DevPlan p, const float2* __restrict__ b1,
+                                                     const float2* __restrict__ s2, float2* __restrict__ b2, int B) {
+    constexpr int T = FftPlan<P>::T, C = kThreads / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
+    constexpr int PER = P * C / kThreads;
+    extern __shared__ float2 sm[];
+    float2* tD = sm;
+    float2* tF = sm + TILE;
+    float2* tG = sm + 2 * TILE;
+    const int q = blockIdx.y, u0 = blockIdx.x * C;
+    const float2* inD = b1 + (size_t)q * N * W;
+    const float2* inF = s2 + (size_t)q * N * W;
+    const float2* inG = s2 + (size_t)(B + q) * N * W;
+    for (int idx = threadIdx.x; idx < P * C; idx += kThreads) {
+        const int v = idx / C, c = idx % C, i = (v + N / 2) & (P - 1);
+        const float2 zero = make_float2(0.f, 0.f);
+        tD[spad(v) * ES + c] = i < N ? inD[(size_t)i * W + u0 + c] : zero;
+        tF[spad(v) * ES + c] = v < N ? inF[(size_t)v * W + u0 + c] : zero;
+        tG[spad(v) * ES + c] = v < N ? inG[(size_t)v * W + u0 + c] : zero;
+    }
+    __syncthreads();
+    const int c = threadIdx.x / T, j = threadIdx.x % T;
+    fft<P, -1>(tD + c, ES, j, true, p.tw_p);
+    fft<P, -1>(tF + c, ES, j, true, p.tw_p);
+    fft<P, -1>(tG + c, ES, j, true, p.tw_p);
+    float2 q1[PER], q2[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * kThreads, v = idx / C, cc = idx % C;
+        const float2 D = tD[spad(v) * ES + cc], F = tF[spad(v) * ES + cc], G = tG[spad(v) * ES + cc];
+        if (u0 + cc == 0) {
+            const int vm = (P - v) & (P - 1);
+            float2 ad, bd, af, bf, ag, bg;
+            split0(D, tD[spad(vm) * ES + cc], ad, bd);
+            split0(F, tF[spad(vm) * ES + cc], af, bf);
+            split0(G, tG[spad(vm) * ES + cc], ag, bg);
+            const float2 g0 = c_cjmul(ad, ag), gn = c_cjmul(bd, bg);
+            const float2 f0 = c_mul(ad, af), fn = c_mul(bd, bf);
+            q1[m] = make_float2(g0.x - gn.y, g0.y + gn.x);
+            q2[m] = make_float2(f0.x - fn.y, f0.y + fn.x);
+        } else {
+            q1[m] = c_cjmul(D, G);
+            q2[m] = c_mul(D, F);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * kThreads, v = idx / C, cc = idx % C;
+        tG[spad(v) * ES + cc] = q1[m];
+        tF[spad(v) * ES + cc] = q2[m];
+    }
+    __syncthreads();
+    fft<P, +1>(tG + c, ES, j, true, p.tw_p);
+    fft<P, +1>(tF + c, ES, j, true, p.tw_p);
+    float2* o1 = b2 + (size_t)q * N * W;
+    float2* o2 = b2 + (size_t)(B + q) * N * W;
+    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
+        const int y = idx / C, cc = idx % C;
+        o1[(size_t)y * W + u0 + cc] = tG[spad(y) * ES + cc];
+        o2[(size_t)y * W + u0 + cc] = tF[spad(y) * ES + cc];
+    }
+}
+
+// Inverse row FFTs of the two adjoint spectra, keep x in [0, N), scale 1/P^2:
+// z = 0 -> d f' (workspace), z = 1 -> d g (stage-2 part, written to the caller's buffer).
+template <int N, int P>
+__global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* __restrict__ tab,
+                                                    const float2* __restrict__ b2, float* __restrict__ gfr,
+                                                    float* __restrict__ dg, int B) {
+    constexpr int T = FftPlan<P>::T, FPC = kThreads / T, SL = spad(P), W = P / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z, i0 = blockIdx.x * FPC * 2;
+    const float2* in = b2 + (size_t)(s * B + q) * N * W;
+    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+        const int k = idx / W, u = idx % W;
+        const float2 a = in[(size_t)(i0 + 2 * k) * W + u], b = in[(size_t)(i0 + 2 * k + 1) * W + u];
+        float2* Z = sm + k * SL;
+        if (u == 0) {
+            Z[0] = make_float2(a.x, b.x);
+            Z[spad(W)] = make_float2(a.y, b.y);
+        } else {
+            Z[spad(u)] = make_float2(a.x - b.y, a.y + b.x);
+            Z[spad(P - u)] = make_float2(a.x + b.y, b.x - a.y);
+        }
+    }
+    __syncthreads();
+    fft<P, +1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
+    const float scale = 1.f / ((float)P * (float)P);
+    float* out = s == 0 ? gfr + (size_t)q * N * N : dg + tab[3 * q];
+    for (int idx = threadIdx.x; idx < FPC * N; idx += kThreads) {
+        const int k = idx / N, x = idx % N;
+        const float2 z = sm[k * SL + spad(x)];
+        out[(size_t)(i0 + 2 * k) * N + x] = z.x * scale;
+        out[(size_t)(i0 + 2 * k + 1) * N + x] = z.y * scale;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Rotate adjoint
+// ---------------------------------------------------------------------------------------------
+
+// One thread per pixel, which plays two roles:
+//  (a) output pixel X of f': its d theta term d f'(X) (dv/dpx (py - c) - dv/dpy (px - c)), since
+//      d px / d theta = py - c and d py / d theta = -(px - c);
+//  (b) source pixel y of f: d f(y) = sum over the output pixels X whose bilinear sample reads y of
+//      weight * d f'(X).  Such X lie within sqrt 2 of c + R(theta)(y - c), i.e. in the 3 x 3 box
+//      around its rounded position; each candidate's sample point is recomputed exactly as the
+//      forward computes it, so the weights are the forward's weights.
+// d theta is reduced per pair (last block adds the block sums in order) into bsc[q][8] together
+// with the direct term dL/dtheta.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* __restrict__ tab,
+                                                    const float* __restrict__ f, const float* __restrict__ th,
+                                                    const float* __restrict__ gfr, const float* __restrict__ dpose,
+                                                    float* __restrict__ df, float* __restrict__ gpart,
+                                                    unsigned* __restrict__ cnt, float* __restrict__ bsc) {
+    __shared__ float red[32];
+    __shared__ bool last;
+    constexpr int NB = N * N / kThreads;
+    const int q = blockIdx.y;
+    const float* t = th + 8 * q;
+    const float ch = t[1], cl = t[2], sh = t[3], sl = t[4];
+    const float c = 0.5f * N;
+    const float* src = f + tab[3 * q];
+    const float* d = gfr + (size_t)q * N * N;
+    const int idx = blockIdx.x * kThreads + threadIdx.x;
+    const int Y = idx / N, X = idx % N;
+    // (a) d theta at output pixel X
+    float contrib;
+    {
+        int x0, y0;
+        float fx, fy;
+        rot_coord(ch, cl, (float)X - c, sh, sl, (float)Y - c, c, x0, fx);
+        rot_coord(ch, cl, (float)Y - c, -sh, -sl, (float)X - c, c, y0, fy);
+        auto at = [&](int yy, int xx) {
+            return ((unsigned)yy < (unsigned)N && (unsigned)xx < (unsigned)N) ? __ldg(src + (size_t)yy * N + xx) : 0.f;
+        };
+        const float v00 = at(y0, x0), v01 = at(y0, x0 + 1), v10 = at(y0 + 1, x0), v11 = at(y0 + 1, x0 + 1);
+        const float dvx = (1.f - fy) * (v01 - v00) + fy * (v11 - v10);
+        const float dvy = (1.f - fx) * (v10 - v00) + fx * (v11 - v01);
+        const float pxc = ((float)x0 - c) + fx, pyc = ((float)y0 - c) + fy;
+        contrib = d[idx] * (dvx * pyc - dvy * pxc);
+    }
+    // (b) d f at source pixel (X, Y)
+    {
+        const float dx = (float)X - c, dy = (float)Y - c;
+        const float ex = c + ch * dx - sh * dy, ey = c + sh * dx + ch * dy;
+        const int mx0 = (int)rintf(ex) - 1, my0 = (int)rintf(ey) - 1;
+        float acc = 0.f;
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+            const int my = my0 + oy;
+            if ((unsigned)my >= (unsigned)N) continue;
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+                const int mx = mx0 + ox;
+                if ((unsigned)mx >= (unsigned)N) continue;
+                int x0, y0;
+                float fx, fy;
+                rot_coord(ch, cl, (float)mx - c, sh, sl, (float)my - c, c, x0, fx);
+                float wx;
+                if (x0 == X) wx = 1.f - fx;
+                else if (x0 + 1 == X) wx = fx;
+                else continue;
+                rot_coord(ch, cl, (float)my - c, -sh, -sl, (float)mx - c, c, y0, fy);
+                float wy;
+                if (y0 == Y) wy = 1.f - fy;
+                else if (y0 + 1 == Y) wy = fy;
+                else continue;
+                acc += wy * wx * d[(size_t)my * N + mx];
+            }
+        }
+        df[tab[3 * q] + idx] = acc;
+    }
+    const float bs = block_reduce<false>(contrib, red);
+    if (threadIdx.x == 0) {
+        gpart[(size_t)q * NB + blockIdx.x] = bs;
+        __threadfence();
+        last = atomicAdd(&cnt[q], 1u) == NB - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        const volatile float* g = gpart + (size_t)q * NB;
+        float s = 0.f;
+        for (int i = threadIdx.x; i < NB; i += kThreads) s += g[i];
+        s = block_reduce<false>(s, red);
+        if (threadIdx.x == 0) {
+            bsc[(size_t)q * 16 + 8] = dpose[3 * tab[3 * q + 2]] + s;
+            cnt[q] = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// stage-1 adjoint
+// ---------------------------------------------------------------------------------------------
+
+// Angle soft-argmax adjoint (as for the translation, with q_k = dtheta k delta_theta), z-score
+// adjoint, then the FFT along angle of d c_theta laid out circularly (lag k at index k mod n).
+template <int NT>
+__global__ void __launch_bounds__(256) k_b_theta(DevPlan p, const float* __restrict__ ct,
+                                                 const float* __restrict__ bsc, float2* __restrict__ bdc) {
+    constexpr int T = FftPlan<NT>::T;
+    __shared__ float2 z[spad(NT)];
+    __shared__ float c[NT];
+    __shared__ float red[32];
+    const int q = blockIdx.x;
+    float lsum = 0.f, lmax = -FLT_MAX;
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) {
+        const float v = ct[(size_t)q * NT + i];
+        c[i] = v;
+        lsum += v;
+        lmax = fmaxf(lmax, v);
+    }
+    const float mean = block_reduce<false>(lsum, red) * (1.f / NT);
+    const float cmax = block_reduce<true>(lmax, red);
+    float lvar = 0.f;
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) lvar += (c[i] - mean) * (c[i] - mean);
+    const float sd = sqrtf(block_reduce<false>(lvar, red) * (1.f / NT));
+    const float inv = p.score_norm == 1 ? 1.f / p.temp_theta : (sd > 0.f ? 1.f / (sd * p.temp_theta) : 0.f);
+    float le = 0.f;
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) le += expf((c[i] - cmax) * inv);
+    const float se = block_reduce<false>(le, red);
+    const float dth = bsc[(size_t)q * 16 + 8];
+    const float dl = 3.14159265358979323846f / NT;
+    float lpq = 0.f;
+    for (int i = threadIdx.x; i < NT; i += blockDim.x)
+        lpq += expf((c[i] - cmax) * inv) / se * (dth * (float)(i - NT / 2) * dl);
+    const float pq = block_reduce<false>(lpq, red);
+    float l1 = 0.f, l2 = 0.f;
+    float dz[(NT + 255) / 256];
+#pragma unroll
+    for (int m = 0; m < (NT + 255) / 256; ++m) {
+        const int i = threadIdx.x + 256 * m;
+        dz[m] = 0.f;
+        if (i < NT) {
+            const float pp = expf((c[i] - cmax) * inv) / se;
+            dz[m] = pp * (dth * (float)(i - NT / 2) * dl - pq) / p.temp_theta;
+            l1 += dz[m];
+            l2 += dz[m] * (sd > 0.f ? (c[i] - mean) / sd : 0.f);
+        }
+    }
+    const float m1 = block_reduce<false>(l1, red) * (1.f / NT);
+    const float m2 = block_reduce<false>(l2, red) * (1.f / NT);
+#pragma unroll
+    for (int m = 0; m < (NT + 255) / 256; ++m) {
+        const int i = threadIdx.x + 256 * m;
+        if (i < NT) {
+            float dc = dz[m];
+            if (p.score_norm != 1) dc = sd > 0.f ? (dz[m] - m1 - (c[i] - mean) / sd * m2) / sd : 0.f;
+            z[spad((i - NT / 2 + NT) % NT)] = make_float2(dc, 0.f);
+        }
+    }
+    __syncthreads();
+    fft<NT, -1>(z, 1, threadIdx.x, threadIdx.x < T, p.tw_t);
+    for (int k = threadIdx.x; k < NT; k += blockDim.x) bdc[(size_t)q * NT + k] = z[spad(k)];
+}
+
+// Angle-correlation adjoint for a chunk of radii: recompute A^_f, A^_g (gather + FFT along angle as
+// in the forward), then d A_f = iFFT(conj(DC) A^_g) / n and d A_g = iFFT(DC A^_f) / n, both real,
+// packed as one inverse FFT of U_f + i U_g.
+template <int NT>
+__global__ void k_b_angle(DevPlan p, const float* __restrict__ mt, const float2* __restrict__ bdc,
+                          float* __restrict__ gpol, int B) {
+    constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC + 1;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, ch = blockIdx.x, r0 = ch * RC, n = p.n, W = n / 2;
+    const float* mf = mt + (size_t)q * (W + 1) * n;
+    const float* mg = mt + (size_t)(B + q) * (W + 1) * n;
+    for (int idx = threadIdx.x; idx < NT * RC; idx += blockDim.x) {
+        const int a = idx / RC, rr = idx % RC, r = r0 + rr;
+        float2 z = make_float2(0.f, 0.f);
+        if (r < p.nr) {
+            const PolarSample ps = p.polar[a * p.nr + r];
+            const float w00 = (1.f - ps.fy) * (1.f - ps.fx), w01 = (1.f - ps.fy) * ps.fx;
+            const float w10 = ps.fy * (1.f - ps.fx), w11 = ps.fy * ps.fx;
+            z.x = w00 * mag_at(mf, n, ps.y0, ps.x0) + w01 * mag_at(mf, n, ps.y0, ps.x0 + 1) +
+                  w10 * mag_at(mf, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mf, n, ps.y0 + 1, ps.x0 + 1);
+            z.y = w00 * mag_at(mg, n, ps.y0, ps.x0) + w01 * mag_at(mg, n, ps.y0, ps.x0 + 1) +
+                  w10 * mag_at(mg, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mg, n, ps.y0 + 1, ps.x0 + 1);
+        }
+        sm[spad(a) * ES + rr] = z;
+    }
+    __syncthreads();
+    const int rr0 = threadIdx.x / T, j = threadIdx.x % T;
+    const bool active = threadIdx.x < T * RC;
+    fft<NT, -1>(sm + rr0, ES, j, active, p.tw_t);
+    constexpr int PER = (NT * RC + T * RC - 1) / (T * RC);
+    float2 wv[PER];
+    const float2* DC = bdc + (size_t)q * NT;
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * blockDim.x;
+        if (idx < NT * RC) {
+            const int k = idx / RC, rr = idx % RC, km = k == 0 ? 0 : NT - k;
+            float2 af, ag;
+            split0(sm[spad(k) * ES + rr], sm[spad(km) * ES + rr], af, ag);
+            const float2 dc = __ldg(&DC[k]);
+            const float2 uf = c_cjmul(dc, ag), ug = c_mul(dc, af);
+            wv[m] = make_float2(uf.x - ug.y, uf.y + ug.x);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * blockDim.x;
+        if (idx < NT * RC) sm[spad(idx / RC) * ES + idx % RC] = wv[m];
+    }
+    __syncthreads();
+    fft<NT, +1>(sm + rr0, ES, j, active, p.tw_t);
+    const float sc = 1.f / NT;
+    float* of = gpol + (size_t)q * NT * p.nr;
+    float* og = gpol + (size_t)(B + q) * NT * p.nr;
+    for (int idx = threadIdx.x; idx < NT * RC; idx += blockDim.x) {
+        const int a = idx / RC, rr = idx % RC, r = r0 + rr;
+        if (r < p.nr) {
+            const float2 v = sm[spad(a) * ES + rr];
+            of[a * p.nr + r] = v.x * sc;
+            og[a * p.nr + r] = v.y * sc;
+        }
+    }
+}
+
+// Transpose of the Cart2Pol gather: d a[e] = sum over the samples that read element e of the
+// half plane, with the forward's bilinear weights (precomputed CSR on the host).
+__global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float* __restrict__ gpol,
+                                                     float* __restrict__ gmt, int B) {
+    const int n = p.n, E = (n / 2 + 1) * n;
+    const int e = blockIdx.x * kThreads + threadIdx.x;
+    if (e >= E) return;
+    const int q = blockIdx.y, s = blockIdx.z;
+    const float* da = gpol + (size_t)(s * B + q) * p.nt * p.nr;
+    float acc = 0.f;
+    for (int k = __ldg(&p.csr_ptr[e]); k < __ldg(&p.csr_ptr[e + 1]); ++k)
+        acc += __ldg(&p.csr_w[k]) * __ldg(&da[__ldg(&p.csr_col[k])]);
+    gmt[(size_t)(s * B + q) * E + e] = acc;
+}
+
+// |z| adjoint with the band-pass, then the column part of the half-plane DFT adjoint.  The
+// column FFT of the stage-1 row spectra is recomputed to get F; dF = d a band F/|F|.  The DFT
+// adjoint is d x[y,x] = Re sum_{v, u <= N/2} dF[v,u] exp(+2 pi i (v y + u x)/N): here the inverse
+// column transform, with interior columns halved (a real row transform counts them twice) and the
+// DC/Nyquist columns made Hermitian (only the real part of their row sums counts) so that they
+// can share the packed column 0.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_b_s1cols(DevPlan p, const float2* __restrict__ s1,
+                                                       const float* __restrict__ gmt, float2* __restrict__ gs1,
+                                                       int B) {
+    constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C + 1, W = N / 2, PER = C * N / kThreads;
+    extern __shared__ float2 sm[];
+    float2* nyq = sm + spad(N) * ES;  // Nyquist column of the packed column 0
+    const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
+    const float2* in = s1 + (size_t)(s * B + q) * N * W;
+    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
+        const int v = idx / C, c = idx % C;
+        sm[spad(v) * ES + c] = in[(size_t)v * W + u0 + c];
+    }
+    __syncthreads();
+    fft<N, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
+    const float* dm = gmt + (size_t)(s * B + q) * (W + 1) * N;
+    auto unit = [](float2 z) {
+        const float a = sqrtf(fmaf(z.x, z.x, z.y * z.y));
+        return a > 0.f ? make_float2(z.x / a, z.y / a) : make_float2(0.f, 0.f);
+    };
+    float2 r0[PER], r1[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * kThreads, cc = idx / N, v = idx % N;
+        const int vs = v <= W ? v : v - N;
+        const float2 z = sm[spad(v) * ES + cc];
+        if (u0 + cc == 0) {
+            float2 a, b;
+            split0(z, sm[spad((N - v) & (N - 1)) * ES + cc], a, b);
+            const int m0 = vs * vs, mn = vs * vs + W * W;
+            const float g0 = (m0 >= p.m_lo && m0 <= p.m_hi) ? dm[v] : 0.f;
+            const float gn = (mn >= p.m_lo && mn <= p.m_hi) ? dm[(size_t)W * N + v] : 0.f;
+            r0[m] = c_scale(unit(a), g0);
+            r1[m] = c_scale(unit(b), gn);
+        } else {
+            const int u = u0 + cc, mm = vs * vs + u * u;
+            const float gv = (mm >= p.m_lo && mm <= p.m_hi) ? dm[(size_t)u * N + v] : 0.f;
+            r0[m] = c_scale(unit(z), 0.5f * gv);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * kThreads, cc = idx / N, v = idx % N;
+        sm[spad(v) * ES + cc] = r0[m];
+        if (u0 + cc == 0) nyq[spad(v)] = r1[m];
+    }
+    __syncthreads();
+    if (u0 == 0) {  // uniform per block
+        float2 pk[(N + kThreads - 1) / kThreads];
+#pragma unroll
+        for (int m = 0; m < (N + kThreads - 1) / kThreads; ++m) {
+            const int v = threadIdx.x + m * kThreads;
+            if (v < N) {
+                const int vm = (N - v) & (N - 1);
+                const float2 a = sm[spad(v) * ES], am = sm[spad(vm) * ES], b = nyq[spad(v)], bm = nyq[spad(vm)];
+                const float2 sa = make_float2(0.5f * (a.x + am.x), 0.5f * (a.y - am.y));
+                const float2 sb = make_float2(0.5f * (b.x + bm.x), 0.5f * (b.y - bm.y));
+                pk[m] = make_float2(sa.x - sb.y, sa.y + sb.x);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < (N + kThreads - 1) / kThreads; ++m) {
+            const int v = threadIdx.x + m * kThreads;
+            if (v < N) sm[spad(v) * ES] = pk[m];
+        }
+        __syncthreads();
+    }
+    fft<N, +1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
+    float2* out = gs1 + (size_t)(s * B + q) * N * W;
+    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
+        const int y = idx / C, cc = idx % C;
+        out[(size_t)y * W + u0 + cc] = sm[spad(y) * ES + cc];
+    }
+}
+
+// Row part of the half-plane DFT adjoint (a real inverse FFT of each row, two rows per complex
+// FFT), times the window; added to d f (z = 0) or d g (z = 1).
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_b_s1rows(DevPlan p, const long long* __restrict__ tab,
+                                                       const float2* __restrict__ gs1, float* __restrict__ df,
+                                                       float* __restrict__ dg, int B) {
+    constexpr int T = FftPlan<N>::T, FPC = kThreads / T, SL = spad(N), W = N / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
+    const float2* in = gs1 + (size_t)(s * B + q) * N * W;
+    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+        const int k = idx / W, u = idx % W;
+        const float2 a = in[(size_t)(r0 + 2 * k) * W + u], b = in[(size_t)(r0 + 2 * k + 1) * W + u];
+        float2* Z = sm + k * SL;
+        if (u == 0) {
+            Z[0] = make_float2(a.x, b.x);
+            Z[spad(W)] = make_float2(a.y, b.y);
+        } else {
+            Z[spad(u)] = make_float2(a.x - b.y, a.y + b.x);
+            Z[spad(N - u)] = make_float2(a.x + b.y, b.x - a.y);
+        }
+    }
+    __syncthreads();
+    fft<N, +1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_n);
+    float* out = (s ? dg : df) + tab[3 * q];
+    for (int idx = threadIdx.x; idx < FPC * N; idx += kThreads) {
+        const int k = idx / N, x = idx % N, y = r0 + 2 * k;
+        const float2 z = sm[k * SL + spad(x)];
+        float va = z.x, vb = z.y;
+        if (p.window) {
+            const float wx = __ldg(&p.win[x]);
+            va *= __ldg(&p.win[y]) * wx;
+            vb *= __ldg(&p.win[y + 1]) * wx;
+        }
+        out[(size_t)y * N + x] += va;
+        out[(size_t)(y + 1) * N + x] += vb;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+
+template <int N> constexpr size_t b_smem_rows() { return (size_t)(kThreads / FftPlan<N>::T) * spad(N) * sizeof(float2); }
+template <int P> constexpr size_t b_smem_cols() {
+    return 3 * (size_t)spad(P) * (kThreads / FftPlan<P>::T + 1) * sizeof(float2);
+}
+template <int N> constexpr size_t b_smem_s1cols() {
+    return ((size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) + spad(N)) * sizeof(float2);
+}
+template <int NT> constexpr size_t b_smem_angle() { return (size_t)spad(NT) * (kAngleRadii + 1) * sizeof(float2); }
+
+template <int NT>
+static void launch_stage1_adjoint(const DevPlan& p, const Ws& w, int B, cudaStream_t st) {
+    w.tr->before(K_B_THETA, st);
+    k_b_theta<NT><<<B, 256, 0, st>>>(p, w.ct, w.bsc, w.bdc);
+    w.tr->before(K_B_ANGLE, st);
+    k_b_angle<NT><<<dim3(angle_chunks(p), B), FftPlan<NT>::T * kAngleRadii, b_smem_angle<NT>(), st>>>(p, w.mt, w.bdc,
+                                                                                                    w.gpol, B);
+}
+
+template <int N, int P>
+static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st) {
+    cudaError_t e = launch_forward(p, w, B, tab, f, g, w.bpose, nullptr, nullptr, st);
+    if (e != cudaSuccess) return e;
+    constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T;
+    const int nblk = (N / 2) / (kThreads / T2);
+    w.tr->before(K_B_SXY, st);
+    k_b_stats<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, w.st, nblk, w.sx, w.bpose, dpose, w.gxx,
+                                                          w.cnt, w.bsc);
+    w.tr->before(K_B_ROWS, st);
+    k_b_rows<N, P><<<dim3((N / 2) / (kThreads / T2), B), kThreads, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.bsc,
+                                                                                             dpose, w.b1, B);
+    w.tr->before(K_B_COLS, st);
+    k_b_cols<N, P><<<dim3((P / 2) / (kThreads / T2), B), kThreads, b_smem_cols<P>(), st>>>(p, w.b1, w.s2, w.b2, B);
+    w.tr->before(K_B_MISC, st);
+    k_b_c2r<N, P><<<dim3((N / 2) / (kThreads / T2), B, 2), kThreads, b_smem_rows<P>(), st>>>(p, tab, w.b2, w.gfr,
+                                                                                               dg, B);
+    w.tr->before(K_B_ROT, st);
+    k_b_rot<N><<<dim3(N * N / kThreads, B), kThreads, 0, st>>>(p, tab, f, w.th, w.gfr, dpose, df, w.gpart, w.cnt,
+                                                              w.bsc);
+    if (p.nt == 128) launch_stage1_adjoint<128>(p, w, B, st);
+    else if (p.nt == 256) launch_stage1_adjoint<256>(p, w, B, st);
+    else launch_stage1_adjoint<400>(p, w, B, st);
+    w.tr->before(K_B_MISC, st);
+    const int E = (N / 2 + 1) * N;
+    k_b_polT<<<dim3((E + kThreads - 1) / kThreads, B, 2), kThreads, 0, st>>>(p, w.gpol, w.gmt, B);
+    w.tr->before(K_B_S1COLS, st);
+    k_b_s1cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st>>>(p, w.s1, w.gmt,
+                                                                                                 w.gs1, B);
+    w.tr->before(K_B_S1ROWS, st);
+    k_b_s1rows<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_rows<N>(), st>>>(p, tab, w.gs1, df, dg,
+                                                                                               B);
+    w.tr->close(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    if (p.n == 128) return p.p == 256 ? launch_b<128, 256>(p, w, B, tab, f, g, dpose, df, dg, st)
+                                      : launch_b<128, 128>(p, w, B, tab, f, g, dpose, df, dg, st);
+    if (p.n == 256) return p.p == 512 ? launch_b<256, 512>(p, w, B, tab, f, g, dpose, df, dg, st)
+                                      : launch_b<256, 256>(p, w, B, tab, f, g, dpose, df, dg, st);
+    return p.p == 1024 ? launch_b<512, 1024>(p, w, B, tab, f, g, dpose, df, dg, st)
+                       : launch_b<512, 512>(p, w, B, tab, f, g, dpose, df, dg, st);
+}
+
+template <typename K>
+static cudaError_t allow(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int N, int P>
+static cudaError_t prepare_b() {
+    cudaError_t e;
+    if ((e = allow(k_b_rows<N, P>, b_smem_rows<P>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_cols<N, P>, b_smem_cols<P>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_c2r<N, P>, b_smem_rows<P>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_s1cols<N>, b_smem_s1cols<N>())) != cudaSuccess) return e;
+    return allow(k_b_s1rows<N>, b_smem_rows<N>());
+}
+
+cudaError_t prepare_backward_kernels() {
+    cudaError_t e;
+    if ((e = prepare_b<128, 256>()) != cudaSuccess) return e;
+    if ((e = prepare_b<128, 128>()) != cudaSuccess) return e;
+    if ((e = prepare_b<256, 512>()) != cudaSuccess) return e;
+    if ((e = prepare_b<256, 256>()) != cudaSuccess) return e;
+    if ((e = prepare_b<512, 1024>()) != cudaSuccess) return e;
+    if ((e = prepare_b<512, 512>()) != cudaSuccess) return e;
+    if ((e = allow(k_b_angle<128>, b_smem_angle<128>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_angle<256>, b_smem_angle<256>())) != cudaSuccess) return e;
+    return allow(k_b_angle<400>, b_smem_angle<400>());
+}
 
 }  // namespace fmbym

@@ -30,6 +30,11 @@ struct DevPlan {
     const float2* tw_p;    // [P]  exp(-2 pi i k / P)
     const float2* tw_t;    // [n_theta] exp(-2 pi i k / n_theta)
     const PolarSample* polar;  // [n_theta][n_r]
+    // transpose of the bilinear polar gather onto the u-major half plane [N/2+1][N]: the
+    // samples that read element e are csr_col[csr_ptr[e] .. csr_ptr[e+1]) with weights csr_w
+    const int* csr_ptr;
+    const int* csr_col;
+    const float* csr_w;
 };
 
 inline int angle_chunks(const DevPlan& p) { return (p.nr + kAngleRadii - 1) / kAngleRadii; }
@@ -79,15 +84,19 @@ struct Ws {
     float* sx;    // [B][kSplitXY][4] soft-argmax partial sums
     unsigned* cnt;  // [B] completion counters of the last-block reductions: a handle-wide array that
                     // is zero between launches (the last block of a pair resets its counter)
-    // backward extras
-    float2* b1;   // [B][N][P/2]     adjoint spectra
-    float2* b2;   // [2][B][N][P/2]
-    float* gfr;   // [B][N][N]       d rotated source
-    float* gth;   // [B][4]          d theta partial sums / total
+    float* ct;    // [B][n_theta]     angle scores in lag order (kept for the adjoint)
+    // adjoint
+    float* bpose; // [pairs][3]       recomputed pose, indexed by pair (handle-wide)
+    float* bsc;   // [B][16]          per-pair scalars of the soft-argmax adjoints
+    float* gpart; // [B][N*N/256]     per-block partial sums of d theta through Rotate
+    float* gxx;   // [B][kSplitXY][4] partial sums of the translation soft-argmax adjoint
+    float2* b1;   // [B][N][P/2]      row spectra of the embedded d c_xy (lag rows)
+    float2* b2;   // [2][B][N][P/2]   inverse column pass of conj(D) G and D F'
+    float* gfr;   // [B][N][N]        d rotated source
+    float2* bdc;  // [B][n_theta]     FFT of d c_theta along angle
     float* gpol;  // [2][B][n_theta][n_r] d polar arrays
     float* gmt;   // [2][B][N/2+1][N] d magnitudes
-    float2* gs1;  // [2][B][N][N/2]
-    float* gxx;   // [B][kSplitXY][4] soft-argmax adjoint partial sums
+    float2* gs1;  // [2][B][N][N/2]   inverse column pass of the stage-1 adjoint
     Tracer* tr;   // launch tracer of the handle
 };
 

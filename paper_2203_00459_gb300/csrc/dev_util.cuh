@@ -1,0 +1,123 @@
+// Device helpers shared by the forward and adjoint kernels: warp/block reductions, the
+// Hermitian half-plane magnitude lookup, and the error-free rotation coordinates of Rotate.
+#pragma once
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace fmbym {
+
+// ---------------------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum (or max) over a block whose size is a multiple of 32; every thread gets the result.
+template <bool MAX>
+__device__ __forceinline__ float block_reduce(float v, float* red) {
+    v = MAX ? warp_max(v) : warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        float r = lane < nw ? red[lane] : (MAX ? -FLT_MAX : 0.f);
+        r = MAX ? warp_max(r) : warp_sum(r);
+        if (lane == 0) red[0] = r;
+    }
+    __syncthreads();
+    return red[0];
+}
+
+// |F| at integer frequency (vi, ui) of the N-periodic spectrum, read from the u-major half plane
+// m[u][v] (u <= N/2) through |F(-v,-u)| = |F(v,u)|.
+__device__ __forceinline__ float mag_at(const float* __restrict__ m, int n, int vi, int ui) {
+    vi &= n - 1;
+    ui &= n - 1;
+    if (ui > (n >> 1)) {
+        vi = (n - vi) & (n - 1);
+        ui = n - ui;
+    }
+    return __ldg(&m[ui * n + vi]);
+}
+
+// p = c + a d1 + b d2 with a = ah + al and b = bh + bl (float splits of double values) and small
+// integer d1, d2.  Error-free products and sums keep p to ~1e-7 px so that the rotation does not
+// add error beyond the rounding of theta itself.  Returns floor(p) and p - floor(p).
+__device__ __forceinline__ void rot_coord(float ah, float al, float d1, float bh, float bl, float d2, float c,
+                                          int& i0, float& fr) {
+    const float p1 = __fmul_rn(ah, d1), e1 = fmaf(ah, d1, -p1);
+    const float p2 = __fmul_rn(bh, d2), e2 = fmaf(bh, d2, -p2);
+    const float s = __fadd_rn(p1, p2), t = __fsub_rn(s, p1);
+    const float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, t)), __fsub_rn(p2, t));
+    const float h = __fadd_rn(c, s), t2 = __fsub_rn(h, c);
+    const float eh = __fadd_rn(__fsub_rn(c, __fsub_rn(h, t2)), __fsub_rn(s, t2));
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(es, eh)), fmaf(al, d1, __fmul_rn(bl, d2)));
+    float fl = floorf(h);
+    float f = __fadd_rn(__fsub_rn(h, fl), lo);
+    if (f < 0.f) {
+        f += 1.f;
+        fl -= 1.f;
+    } else if (f >= 1.f) {
+        f -= 1.f;
+        fl += 1.f;
+    }
+    i0 = (int)fl;
+    fr = f;
+}
+
+// f'(X, Y) = bilinear(f, c + R(-theta)([X, Y] - c)), zero outside the scan (Alg. 1 Rotate).
+__device__ __forceinline__ float rotated_sample(const float* __restrict__ src, int n, int X, int Y, float ch,
+                                                float cl, float sh, float sl) {
+    const float c = 0.5f * n, dx = (float)X - c, dy = (float)Y - c;
+    int x0, y0;
+    float fx, fy;
+    rot_coord(ch, cl, dx, sh, sl, dy, c, x0, fx);    // px = c + cos dx + sin dy
+    rot_coord(ch, cl, dy, -sh, -sl, dx, c, y0, fy);  // py = c - sin dx + cos dy
+    float v = 0.f;
+    const bool xin0 = (unsigned)x0 < (unsigned)n, xin1 = (unsigned)(x0 + 1) < (unsigned)n;
+    if ((unsigned)y0 < (unsigned)n) {
+        const float* r = src + (size_t)y0 * n;
+        if (xin0) v += (1.f - fy) * (1.f - fx) * __ldg(r + x0);
+        if (xin1) v += (1.f - fy) * fx * __ldg(r + x0 + 1);
+    }
+    if ((unsigned)(y0 + 1) < (unsigned)n) {
+        const float* r = src + (size_t)(y0 + 1) * n;
+        if (xin0) v += fy * (1.f - fx) * __ldg(r + x0);
+        if (xin1) v += fy * fx * __ldg(r + x0 + 1);
+    }
+    return v;
+}
+
+// Combines per-block (mean, M2, max, count) statistics of the translation scores into the mean,
+// population std and maximum over all `total` scores (equal block counts; Chan's update).  Run by
+// one full warp; every lane returns the results.
+__device__ __forceinline__ void xy_stats_warp(const float* __restrict__ s, int nblk, float total, float& mu,
+                                              float& sd, float& cmax) {
+    const int lane = threadIdx.x & 31;
+    float lsum = 0.f, lmax = -FLT_MAX;
+    for (int i = lane; i < nblk; i += 32) {
+        lsum += s[4 * i];
+        lmax = fmaxf(lmax, s[4 * i + 2]);
+    }
+    mu = warp_sum(lsum) / nblk;
+    cmax = warp_max(lmax);
+    float lm2 = 0.f;
+    for (int i = lane; i < nblk; i += 32) {
+        const float d = s[4 * i] - mu;
+        lm2 += s[4 * i + 1] + s[4 * i + 3] * d * d;
+    }
+    sd = sqrtf(warp_sum(lm2) / total);
+}
+
+}  // namespace fmbym

@@ -14,100 +14,9 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "dev_util.cuh"
 
 namespace fmbym {
-
-// ---------------------------------------------------------------------------------------------
-// small helpers
-// ---------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Sum (or max) over a block whose size is a multiple of 32; every thread gets the result.
-template <bool MAX>
-__device__ __forceinline__ float block_reduce(float v, float* red) {
-    v = MAX ? warp_max(v) : warp_sum(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        float r = lane < nw ? red[lane] : (MAX ? -FLT_MAX : 0.f);
-        r = MAX ? warp_max(r) : warp_sum(r);
-        if (lane == 0) red[0] = r;
-    }
-    __syncthreads();
-    return red[0];
-}
-
-// |F| at integer frequency (vi, ui) of the N-periodic spectrum, read from the u-major half plane
-// m[u][v] (u <= N/2) through |F(-v,-u)| = |F(v,u)|.
-__device__ __forceinline__ float mag_at(const float* __restrict__ m, int n, int vi, int ui) {
-    vi &= n - 1;
-    ui &= n - 1;
-    if (ui > (n >> 1)) {
-        vi = (n - vi) & (n - 1);
-        ui = n - ui;
-    }
-    return __ldg(&m[ui * n + vi]);
-}
-
-// p = c + a d1 + b d2 with a = ah + al and b = bh + bl (float splits of double values) and small
-// integer d1, d2.  Error-free products and sums keep p to ~1e-7 px so that the rotation does not
-// add error beyond the rounding of theta itself.  Returns floor(p) and p - floor(p).
-__device__ __forceinline__ void rot_coord(float ah, float al, float d1, float bh, float bl, float d2, float c,
-                                          int& i0, float& fr) {
-    const float p1 = __fmul_rn(ah, d1), e1 = fmaf(ah, d1, -p1);
-    const float p2 = __fmul_rn(bh, d2), e2 = fmaf(bh, d2, -p2);
-    const float s = __fadd_rn(p1, p2), t = __fsub_rn(s, p1);
-    const float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, t)), __fsub_rn(p2, t));
-    const float h = __fadd_rn(c, s), t2 = __fsub_rn(h, c);
-    const float eh = __fadd_rn(__fsub_rn(c, __fsub_rn(h, t2)), __fsub_rn(s, t2));
-    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(es, eh)), fmaf(al, d1, __fmul_rn(bl, d2)));
-    float fl = floorf(h);
-    float f = __fadd_rn(__fsub_rn(h, fl), lo);
-    if (f < 0.f) {
-        f += 1.f;
-        fl -= 1.f;
-    } else if (f >= 1.f) {
-        f -= 1.f;
-        fl += 1.f;
-    }
-    i0 = (int)fl;
-    fr = f;
-}
-
-// f'(X, Y) = bilinear(f, c + R(-theta)([X, Y] - c)), zero outside the scan (Alg. 1 Rotate).
-__device__ __forceinline__ float rotated_sample(const float* __restrict__ src, int n, int X, int Y, float ch,
-                                                float cl, float sh, float sl) {
-    const float c = 0.5f * n, dx = (float)X - c, dy = (float)Y - c;
-    int x0, y0;
-    float fx, fy;
-    rot_coord(ch, cl, dx, sh, sl, dy, c, x0, fx);    // px = c + cos dx + sin dy
-    rot_coord(ch, cl, dy, -sh, -sl, dx, c, y0, fy);  // py = c - sin dx + cos dy
-    float v = 0.f;
-    const bool xin0 = (unsigned)x0 < (unsigned)n, xin1 = (unsigned)(x0 + 1) < (unsigned)n;
-    if ((unsigned)y0 < (unsigned)n) {
-        const float* r = src + (size_t)y0 * n;
-        if (xin0) v += (1.f - fy) * (1.f - fx) * __ldg(r + x0);
-        if (xin1) v += (1.f - fy) * fx * __ldg(r + x0 + 1);
-    }
-    if ((unsigned)(y0 + 1) < (unsigned)n) {
-        const float* r = src + (size_t)(y0 + 1) * n;
-        if (xin0) v += fy * (1.f - fx) * __ldg(r + x0);
-        if (xin1) v += fy * fx * __ldg(r + x0 + 1);
-    }
-    return v;
-}
 
 // ---------------------------------------------------------------------------------------------
 // stage 1
@@ -243,7 +152,8 @@ __global__ void k_angle(DevPlan p, const float* __restrict__ mt, float2* __restr
 template <int NT>
 __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restrict__ sp, int nch,
                                                const long long* __restrict__ tab, float* __restrict__ th,
-                                               float* __restrict__ pose, float* __restrict__ c_theta) {
+                                               float* __restrict__ pose, float* __restrict__ c_theta,
+                                               float* __restrict__ ct) {
     constexpr int T = FftPlan<NT>::T;
     __shared__ float2 z[spad(NT)];
     __shared__ float c[NT];
@@ -281,6 +191,7 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
     }
     const float se = block_reduce<false>(le, red);
     const float sek = block_reduce<false>(lek, red);
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) ct[(size_t)q * NT + i] = c[i];
     if (c_theta) {
         float* out = c_theta + tab[3 * q + 1];
         for (int i = threadIdx.x; i < NT; i += blockDim.x) out[i] = c[i];
@@ -493,22 +404,9 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
     __shared__ bool last;
     const int q = blockIdx.y;
     if (threadIdx.x < 32) {
-        const float* s = st + (size_t)q * nblk * 4;
-        float lsum = 0.f, lmax = -FLT_MAX;
-        for (int i = threadIdx.x; i < nblk; i += 32) {
-            lsum += s[4 * i];
-            lmax = fmaxf(lmax, s[4 * i + 2]);
-        }
-        const float mu = warp_sum(lsum) / nblk;
-        const float cmax = warp_max(lmax);
-        float lm2 = 0.f;
-        for (int i = threadIdx.x; i < nblk; i += 32) {
-            const float d = s[4 * i] - mu;
-            lm2 += s[4 * i + 1] + s[4 * i + 3] * d * d;
-        }
-        const float m2 = warp_sum(lm2);
+        float mu, sd, cmax;
+        xy_stats_warp(st + (size_t)q * nblk * 4, nblk, (float)N * (float)N, mu, sd, cmax);
         if (threadIdx.x == 0) {
-            const float sd = sqrtf(m2 / ((float)N * (float)N));
             stat[0] = cmax;
             stat[1] = p.score_norm == 1 ? 1.f / p.temp_xy : (sd > 0.f ? 1.f / (sd * p.temp_xy) : 0.f);
         }
@@ -578,7 +476,7 @@ static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, con
     w.tr->before(K_ANGLE, st);
     k_angle<NT><<<dim3(nch, B), FftPlan<NT>::T * kAngleRadii, smem_angle<NT>(), st>>>(p, w.mt, w.sp, B);
     w.tr->before(K_THETA, st);
-    k_theta<NT><<<B, 256, 0, st>>>(p, w.sp, nch, tab, w.th, pose, c_theta);
+    k_theta<NT><<<B, 256, 0, st>>>(p, w.sp, nch, tab, w.th, pose, c_theta, w.ct);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,153 @@
+"""Parity of the CUDA adjoint (fmbym_pose_backward) with the FP64 oracle's hand-derived adjoint and
+with FP64 central finite differences of the oracle's forward search, through the C ABI."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2203_00459_gb300 import synth  # noqa: E402
+from gpu_util import oracle_cfg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD = 1e-3   # max |gpu - reference| / max |reference| per gradient image
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_00459_gb300 import build
+    build.build()
+    from paper_2203_00459_gb300 import search
+    return search
+
+
+def grad_err(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(1e-300, np.max(np.abs(b))))
+
+
+def gpu_backward(search, cfg, f, g, dpose):
+    s = search.PoseSearch([cfg], max_pairs=f.shape[0])
+    ft, gt = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    dp = torch.from_numpy(dpose.astype(np.float32)).cuda()
+    df, dg = s.pose_backward(ft, gt, dp)
+    torch.cuda.synchronize()
+    out = df.cpu().numpy(), dg.cpu().numpy()
+    s.close()
+    return out
+
+
+def check_against_oracle(cfg, f, g, dpose, df, dg, tag):
+    oc = oracle_cfg(cfg)
+    for i in range(f.shape[0]):
+        odf, odg, _ = O.pose_backward(f[i], g[i], oc, dpose[i])
+        ef, eg = grad_err(df[i], odf), grad_err(dg[i], odg)
+        assert ef <= TOL_GRAD and eg <= TOL_GRAD, (tag, i, ef, eg)
+
+
+DP = np.array([[0.8, -0.35, 0.6], [-0.5, 1.0, 0.25], [0.3, 0.2, -0.9], [1.0, 0.0, 0.0], [0.0, 1.0, 1.0]])
+
+
+@pytest.mark.parametrize("name,pairs", [("single128", 5), ("batch256", 2), ("batch512", 1)])
+def test_adjoint_matches_oracle(lib, name, pairs):
+    spec = synth.WORKLOADS[name]
+    f, g, _ = synth.make_batch(name, pairs=pairs, start=3)
+    cfg = lib.size_cfg(spec["n"], spec["n_theta"], spec["n_r"])
+    dpose = DP[:pairs]
+    df, dg = gpu_backward(lib, cfg, f, g, dpose)
+    check_against_oracle(cfg, f, g, dpose, df, dg, name)
+
+
+def test_adjoint_raw_scores_no_window_ragged_radii(lib):
+    f, g, _ = synth.make_batch("batch256", pairs=2)
+    cfg = lib.size_cfg(256, 256, 100, temp_theta=2.0e8, temp_xy=1.0e4, window=0, score_norm=1, band_lo=3.5,
+                       band_hi=100.0)
+    df, dg = gpu_backward(lib, cfg, f, g, DP[:2])
+    check_against_oracle(cfg, f, g, DP[:2], df, dg, "raw")
+
+
+def test_adjoint_circular_padding(lib):
+    f, g, _ = synth.make_batch("single128", pairs=2, start=11)
+    cfg = lib.size_cfg(128, 128, 64, pad_mode=1, temp_xy=0.5)
+    df, dg = gpu_backward(lib, cfg, f, g, DP[:2])
+    check_against_oracle(cfg, f, g, DP[:2], df, dg, "circular")
+
+
+def test_adjoint_matches_central_differences_512(lib):
+    """The 512^2 configuration's check: the GPU gradient of an L2 pose loss against FP64 central
+    finite differences (h = 1e-4) of the oracle's forward search on 64 random pixels."""
+    spec = synth.WORKLOADS["batch512"]
+    f, g, gt = synth.make_batch("batch512", pairs=1, start=5)
+    cfg = lib.size_cfg(512, spec["n_theta"], spec["n_r"])
+    oc = oracle_cfg(cfg)
+    f64, g64 = f[0].astype(np.float64), g[0].astype(np.float64)
+    r = O.pose(f64, g64, oc)
+    pose = np.array([r["theta"], r["tx"], r["ty"]])
+
+    def loss(a, b):
+        rr = O.pose(a, b, oc)
+        return float(np.sum((np.array([rr["theta"], rr["tx"], rr["ty"]]) - gt[0]) ** 2))
+
+    dpose = 2.0 * (pose - gt[0])
+    df, dg = gpu_backward(lib, cfg, f, g, dpose[None, :])
+    rng = np.random.default_rng(64)
+    h = 1e-4
+    scale = max(np.max(np.abs(df[0])), np.max(np.abs(dg[0])))
+    for k in range(64):
+        which = k % 2
+        y, x = rng.integers(0, 512, 2)
+        a, b = f64.copy(), g64.copy()
+        (a if which == 0 else b)[y, x] += h
+        lp = loss(a, b)
+        (a if which == 0 else b)[y, x] -= 2 * h
+        lm = loss(a, b)
+        fd = (lp - lm) / (2 * h)
+        an = (df if which == 0 else dg)[0, y, x]
+        assert abs(fd - an) <= TOL_GRAD * scale, (k, which, y, x, fd, an, scale)
+
+
+def test_autograd_function_and_determinism(lib):
+    from paper_2203_00459_gb300.search import PoseSearch, scan_match
+    f, g, gt = synth.make_batch("batch256", pairs=3)
+    s = PoseSearch([lib.size_cfg(256, 400, 128)], max_pairs=3)
+    ft = torch.from_numpy(f).cuda().requires_grad_(True)
+    gtn = torch.from_numpy(g).cuda().requires_grad_(True)
+    target = torch.from_numpy(gt.astype(np.float32)).cuda()
+    pose = scan_match(ft, gtn, s)
+    loss = ((pose - target) ** 2).sum()
+    loss.backward()
+    dpose = 2.0 * (pose.detach() - target)
+    df, dg = s.pose_backward(ft.detach(), gtn.detach(), dpose)
+    torch.cuda.synchronize()
+    assert torch.equal(ft.grad, df) and torch.equal(gtn.grad, dg)
+    df2, dg2 = s.pose_backward(ft.detach(), gtn.detach(), dpose)
+    torch.cuda.synchronize()
+    assert torch.equal(df, df2) and torch.equal(dg, dg2)
+    s.close()
+
+
+def test_adjoint_mixed_sizes_in_one_call(lib):
+    from paper_2203_00459_gb300.search import PoseSearch
+    cfgs = [lib.size_cfg(128, 128, 64), lib.size_cfg(256, 400, 128)]
+    names = ["single128", "batch256"]
+    order = [1, 0, 0]
+    scans = [synth.make_batch(names[s], pairs=1, start=20 + k) for k, s in enumerate(order)]
+    offs, cur = [], 0
+    for f, _, _ in scans:
+        offs.append(cur)
+        cur += f.size
+    F = np.concatenate([f.ravel() for f, _, _ in scans])
+    G = np.concatenate([g.ravel() for _, g, _ in scans])
+    s = PoseSearch(cfgs, max_pairs=3)
+    dp = torch.from_numpy(DP[:3].astype(np.float32)).cuda()
+    df, dg = s.pose_backward(torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda(), dp, size_idx=order,
+                             offsets=offs)
+    torch.cuda.synchronize()
+    df, dg = df.cpu().numpy(), dg.cpu().numpy()
+    for k, si in enumerate(order):
+        n = cfgs[si]["n"]
+        f, g, _ = scans[k]
+        odf, odg, _ = O.pose_backward(f[0], g[0], oracle_cfg(cfgs[si]), DP[k])
+        assert grad_err(df[offs[k]:offs[k] + n * n].reshape(n, n), odf) <= TOL_GRAD
+        assert grad_err(dg[offs[k]:offs[k] + n * n].reshape(n, n), odg) <= TOL_GRAD
+    s.close()
