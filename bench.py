@@ -31,7 +31,7 @@ WORKLOAD = "batch512"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwd", "fwdbwd"])
@@ -58,6 +58,16 @@ def kernel_model(n, p, nt, nr, chunks):
         "s2_cols": (2 * n * wp * c + n * wp * c, 3 * wp * fft(p)),
         "s2_c2r": (n * wp * c + n * n * 4, (n // 2) * fft(p)),
         "sxy": (n * n * 4, 0.0),
+        "b_sxy": (n * n * 4, 0.0),
+        "b_rows": (n * n * 4 + n * wp * c, (n // 2) * fft(p)),
+        "b_cols": (3 * n * wp * c + 2 * n * wp * c, 5 * wp * fft(p)),
+        "b_c2r": (2 * n * wp * c + 2 * n * n * 4, n * fft(p)),
+        "b_rot": (3 * n * n * 4, 0.0),
+        "b_theta": (nt * 4 + nt * c, fft(nt)),
+        "b_angle": (2 * (w + 1) * n * 4 + 2 * nt * nr * 4, 2 * nr * fft(nt)),
+        "b_polT": (2 * nt * nr * 4 + 2 * (w + 1) * n * 4, 0.0),
+        "b_s1cols": (2 * n * w * c + 2 * (w + 1) * n * 4 + 2 * n * w * c, 4 * w * fft(n)),
+        "b_s1rows": (2 * n * w * c + 4 * n * n * 4, n * fft(n)),
     }
     return m
 
@@ -100,7 +110,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "25"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
 
@@ -170,29 +180,35 @@ def make_pool():
 
 
 def run_reference(args, spec, rank):
+    """The FP64 oracle on the host cores, on this arm's workload, metric and unit.  Each step is a
+    bounded sample of pairs (one per core at most), sized from a first timed pair so that the
+    K + W steps end within about two minutes."""
     from paper_2203_00459_gb300 import synth
     if rank != 0:
         return
     pool, cores = make_pool()
-    pairs = min(spec["pairs"], cores)
-    f, g, gt = synth.make_batch(args.workload, pairs=pairs)
+    f, g, gt = synth.make_batch(args.workload, pairs=min(spec["pairs"], cores))
+    t_pair = 1.0 / oracle_rate(f, g, gt, spec, args.mode, 1, pool)
+    steps = max(1, args.steps)
+    pairs = max(1, min(f.shape[0], int(120.0 * cores / ((steps + args.warmup) * t_pair))))
     for _ in range(max(0, args.warmup)):
-        oracle_rate(f, g, gt, spec, args.mode, min(pairs, cores), pool)
+        oracle_rate(f, g, gt, spec, args.mode, pairs, pool)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         oracle_rate(f, g, gt, spec, args.mode, pairs, pool)
     dt = time.perf_counter() - t0
     pool.close()
-    v = pairs * args.steps / dt
+    v = pairs * steps / dt
     unit = "scan-pairs/s"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "mode": args.mode,
             "config": {"workload": args.workload, "n": spec["n"], "n_theta": spec["n_theta"], "n_r": spec["n_r"],
                        "pairs_per_step": pairs},
             "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
-                             "sample": f"{pairs} pairs of {args.workload} per step ({args.mode}), one per core"},
+                             "sample": f"{pairs} pairs of {args.workload} per step ({args.mode}), "
+                                       f"one pair per spawned process"},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -242,17 +258,24 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     pose = torch.empty((B, 3), device="cuda")
     dpose = torch.empty((B, 3), device="cuda")
+    loss = torch.empty(1, device="cuda")
     df = torch.empty_like(fd)
     dg = torch.empty_like(gd)
 
-    def step():
-        search.pose(fd, gd, out=pose)
+    def run_step(srch, fx, gx, gtx, px, dpx, lx, dfx, dgx, nb):
+        """One step through the library only: search, L2 pose loss (the 512^2 configuration's loss)
+        and its adjoint."""
+        st = torch.cuda.current_stream().cuda_stream
+        _lib.check(L.fmbym_pose(srch.handle, st, nb, None, None, fx.data_ptr(), gx.data_ptr(), px.data_ptr(), None,
+                                None), srch.handle)
         if args.mode == "fwdbwd":
-            torch.sub(pose, gtd, out=dpose)
-            dpose.mul_(2.0)
-            _lib.check(L.fmbym_pose_backward(search.handle, torch.cuda.current_stream().cuda_stream, B, None, None,
-                                             fd.data_ptr(), gd.data_ptr(), dpose.data_ptr(), df.data_ptr(),
-                                             dg.data_ptr()), search.handle)
+            _lib.check(L.fmbym_pose_loss(srch.handle, st, nb, px.data_ptr(), gtx.data_ptr(), 2, lx.data_ptr(),
+                                         dpx.data_ptr()), srch.handle)
+            _lib.check(L.fmbym_pose_backward(srch.handle, st, nb, None, None, fx.data_ptr(), gx.data_ptr(),
+                                             dpx.data_ptr(), dfx.data_ptr(), dgx.data_ptr()), srch.handle)
+
+    def step():
+        run_step(search, fd, gd, gtd, pose, dpose, loss, df, dg, B)
 
     for _ in range(args.warmup):
         step()
@@ -318,20 +341,46 @@ def main():
                 "peak_source": peak_src, "alg_bytes_per_launch": byts, "avg_launch_ms": round(avg_ms, 5),
                 "fp32_tflops": round(flops / (avg_ms * 1e-3) / 1e12, 2)}
 
-    # ---- end to end through the C ABI with host buffers (forward) ----
+    # ---- end to end with host buffers ----
     e2e = None
     if rank == 0:
         fh = torch.from_numpy(f).pin_memory()
         gh = torch.from_numpy(g).pin_memory()
-        for _ in range(2):
-            search.pose_host(fh, gh)
-        t0 = time.perf_counter()
-        reps = max(3, args.steps)
-        for _ in range(reps):
-            search.pose_host(fh, gh)
-        dt = (time.perf_counter() - t0) / reps
-        e2e = {"value": B / dt, "unit": "scan-pairs/s", "h2d_bytes_per_step": 2 * f.nbytes,
-               "d2h_bytes_per_step": B * 12, "mode": "fwd", "api": "fmbym_pose_host"}
+        if args.mode == "fwd":
+            for _ in range(2):
+                search.pose_host(fh, gh)
+            t0 = time.perf_counter()
+            reps = max(3, args.steps)
+            for _ in range(reps):
+                search.pose_host(fh, gh)
+            dt = (time.perf_counter() - t0) / reps
+            e2e = {"value": B / dt, "unit": "scan-pairs/s", "h2d_bytes_per_step": 2 * f.nbytes,
+                   "d2h_bytes_per_step": B * 12, "mode": "fwd", "api": "fmbym_pose_host"}
+        else:
+            gth = torch.from_numpy(gt.astype(np.float32)).pin_memory()
+            pose_h = torch.empty((B, 3), pin_memory=True)
+            loss_h = torch.empty(1, pin_memory=True)
+            fe, ge, gte = torch.empty_like(fd), torch.empty_like(gd), torch.empty_like(gtd)
+
+            def e2e_step():
+                fe.copy_(fh, non_blocking=True)
+                ge.copy_(gh, non_blocking=True)
+                gte.copy_(gth, non_blocking=True)
+                run_step(search, fe, ge, gte, pose, dpose, loss, df, dg, B)
+                pose_h.copy_(pose, non_blocking=True)
+                loss_h.copy_(loss, non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+
+            for _ in range(2):
+                e2e_step()
+            reps = max(3, args.steps)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                e2e_step()
+            dt = (time.perf_counter() - t0) / reps
+            e2e = {"value": B / dt, "unit": "scan-pairs/s", "h2d_bytes_per_step": 2 * f.nbytes + B * 12,
+                   "d2h_bytes_per_step": B * 12 + 4, "mode": "fwdbwd",
+                   "api": "fmbym_pose + fmbym_pose_loss + fmbym_pose_backward from pinned host buffers"}
 
     # ---- forward-only rate and the plain one-pair-per-call path ----
     extra = {}
@@ -348,18 +397,24 @@ def main():
         extra["fwd_pairs_per_s"] = B / (statistics.mean(fwd_ms) * 1e-3)
         if not args.no_plain:
             one = PoseSearch([cfg], max_pairs=1)
-            plain = []
-            for _ in range(3):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                for i in range(B):
-                    one.pose(fd[i:i + 1], gd[i:i + 1], out=pose[i:i + 1])
-                b.record()
-                torch.cuda.synchronize()
-                plain.append(a.elapsed_time(b))
-            extra["plain_fwd_pairs_per_s"] = B / (statistics.mean(plain[1:]) * 1e-3)
+            for label, mode in (("fwd", "fwd"), ("step", args.mode)):
+                plain = []
+                for _ in range(3):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    for i in range(B):
+                        if mode == "fwd":
+                            one.pose(fd[i:i + 1], gd[i:i + 1], out=pose[i:i + 1])
+                        else:
+                            run_step(one, fd[i:i + 1], gd[i:i + 1], gtd[i:i + 1], pose[i:i + 1], dpose[i:i + 1],
+                                     loss, df[i:i + 1], dg[i:i + 1], 1)
+                    b.record()
+                    torch.cuda.synchronize()
+                    plain.append(a.elapsed_time(b))
+                extra[f"plain_{label}_pairs_per_s"] = B / (statistics.mean(plain[1:]) * 1e-3)
             extra["batched_vs_plain_fwd"] = extra["fwd_pairs_per_s"] / extra["plain_fwd_pairs_per_s"]
+            extra["batched_vs_plain_step"] = value / extra["plain_step_pairs_per_s"]
             one.close()
 
     cpu = None

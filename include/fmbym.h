@@ -117,6 +117,16 @@ int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* s
                         const long long* offsets, const float* f, const float* g,
                         const float* dpose, float* df, float* dg);
 
+/* Pose loss of Eq. 13 and its gradient, for training through the search (Sec. III-D).
+ *   pose, gt  device float32 [n_pairs][3]: estimated and ground-truth (theta, t_x, t_y)
+ *   kind      1: L1, |pose - gt| summed over the three components (Eq. 13);
+ *             2: L2, (pose - gt)^2 summed over the three components
+ *   loss      device float32 [1] out, or NULL: the mean over pairs (the expectation of Eq. 13)
+ *   dpose     device float32 [n_pairs][3] out, or NULL: dloss/dpose (the L1 derivative is 0 at 0)
+ * Deterministic.  Returns FMBYM_ERR_INVALID_ARG for another kind. */
+int fmbym_pose_loss(fmbym_handle* h, void* stream, int n_pairs, const float* pose, const float* gt,
+                    int kind, float* loss, float* dpose);
+
 /* fmbym_pose with HOST buffers: copies f and g (host float32, total elements as laid out by
  * offsets) into the handle's device staging area, runs the search on the stream, copies the
  * pose (host float32 [n_pairs][3]) back and synchronises the stream.  total_elems is the

@@ -211,12 +211,18 @@ cudaError_t build_plan(HostPlan& hp) {
             wt[fill[t.e]++] = t.w;
         }
     }
+    std::vector<int> heavy;
+    for (int i = 0; i < ne; ++i)
+        if (cnt[i + 1] - cnt[i] > kHeavyRow) heavy.push_back(i);
+    if (heavy.empty()) heavy.push_back(-1);  // keeps the allocation non-empty; n_heavy stays 0
+    d.n_heavy = heavy[0] < 0 ? 0 : (int)heavy.size();
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b_win = al(win.size() * 4), b_twn = al(twn.size() * 8), b_twp = al(twp.size() * 8),
                  b_twt = al(twt.size() * 8), b_pol = al(pol.size() * sizeof(PolarSample)),
-                 b_ptr = al(cnt.size() * 4), b_col = al(col.size() * 4), b_wt = al(wt.size() * 4);
+                 b_ptr = al(cnt.size() * 4), b_col = al(col.size() * 4), b_wt = al(wt.size() * 4),
+                 b_hv = al(heavy.size() * 4);
     char* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, b_win + b_twn + b_twp + b_twt + b_pol + b_ptr + b_col + b_wt);
+    cudaError_t e = cudaMalloc(&base, b_win + b_twn + b_twp + b_twt + b_pol + b_ptr + b_col + b_wt + b_hv);
     if (e != cudaSuccess) return e;
     hp.tables = base;
     char* cur = base;
@@ -234,8 +240,10 @@ cudaError_t build_plan(HostPlan& hp) {
     auto r6 = put(cnt.data(), cnt.size() * 4, b_ptr);
     auto r7 = put(col.data(), col.size() * 4, b_col);
     auto r8 = put(wt.data(), wt.size() * 4, b_wt);
-    for (auto& r : {r1, r2, r3, r4, r5, r6, r7, r8})
+    auto r9 = put(heavy.data(), heavy.size() * 4, b_hv);
+    for (auto& r : {r1, r2, r3, r4, r5, r6, r7, r8, r9})
         if (r.second != cudaSuccess) return r.second;
+    d.heavy = (const int*)r9.first;
     d.csr_ptr = (const int*)r6.first;
     d.csr_col = (const int*)r7.first;
     d.csr_w = (const float*)r8.first;
@@ -477,6 +485,18 @@ int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_
         cudaSuccess)
         return cuda_fail(h, e, "device-to-host copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return FMBYM_OK;
+}
+
+int fmbym_pose_loss(fmbym_handle* h, void* stream, int n_pairs, const float* pose, const float* gt, int kind,
+                    float* loss, float* dpose) {
+    if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    h->err.clear();
+    if (n_pairs < 0 || (kind != 1 && kind != 2)) return fail(h, FMBYM_ERR_INVALID_ARG, "n_pairs < 0 or kind not 1/2");
+    if (n_pairs == 0) return FMBYM_OK;
+    if (!pose || !gt) return fail(h, FMBYM_ERR_INVALID_ARG, "pose and gt must not be NULL");
+    cudaError_t e = launch_pose_loss(n_pairs, pose, gt, kind, loss, dpose, &h->tracer, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loss launch");
     return FMBYM_OK;
 }
 

@@ -502,18 +502,33 @@ __global__ void k_b_angle(DevPlan p, const float* __restrict__ mt, const float2*
 }
 
 // Transpose of the Cart2Pol gather: d a[e] = sum over the samples that read element e of the
-// half plane, with the forward's bilinear weights (precomputed CSR on the host).
+// half plane, with the forward's bilinear weights (precomputed CSR on the host).  Blocks below
+// `light_blocks` give each element a thread and skip the heavy rows; the blocks after them give
+// each heavy row a warp (lane-strided taps, fixed-order warp sum).
 __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float* __restrict__ gpol,
-                                                     float* __restrict__ gmt, int B) {
+                                                     float* __restrict__ gmt, int B, int light_blocks) {
     const int n = p.n, E = (n / 2 + 1) * n;
-    const int e = blockIdx.x * kThreads + threadIdx.x;
-    if (e >= E) return;
     const int q = blockIdx.y, s = blockIdx.z;
     const float* da = gpol + (size_t)(s * B + q) * p.nt * p.nr;
+    float* out = gmt + (size_t)(s * B + q) * E;
+    if ((int)blockIdx.x < light_blocks) {
+        const int e = blockIdx.x * kThreads + threadIdx.x;
+        if (e >= E) return;
+        const int k0 = __ldg(&p.csr_ptr[e]), k1 = __ldg(&p.csr_ptr[e + 1]);
+        if (k1 - k0 > kHeavyRow) return;
+        float acc = 0.f;
+        for (int k = k0; k < k1; ++k) acc += __ldg(&p.csr_w[k]) * __ldg(&da[__ldg(&p.csr_col[k])]);
+        out[e] = acc;
+        return;
+    }
+    const int hw = ((int)blockIdx.x - light_blocks) * (kThreads / 32) + (threadIdx.x >> 5);
+    if (hw >= p.n_heavy) return;
+    const int e = __ldg(&p.heavy[hw]), lane = threadIdx.x & 31;
+    const int k0 = __ldg(&p.csr_ptr[e]), k1 = __ldg(&p.csr_ptr[e + 1]);
     float acc = 0.f;
-    for (int k = __ldg(&p.csr_ptr[e]); k < __ldg(&p.csr_ptr[e + 1]); ++k)
-        acc += __ldg(&p.csr_w[k]) * __ldg(&da[__ldg(&p.csr_col[k])]);
-    gmt[(size_t)(s * B + q) * E + e] = acc;
+    for (int k = k0 + lane; k < k1; k += 32) acc += __ldg(&p.csr_w[k]) * __ldg(&da[__ldg(&p.csr_col[k])]);
+    acc = warp_sum(acc);
+    if (lane == 0) out[e] = acc;
 }
 
 // |z| adjoint with the band-pass, then the column part of the half-plane DFT adjoint.  The
@@ -639,6 +654,43 @@ __global__ void __launch_bounds__(kThreads) k_b_s1rows(DevPlan p, const long lon
 }
 
 // ---------------------------------------------------------------------------------------------
+// pose loss (Eq. 13) and its gradient
+// ---------------------------------------------------------------------------------------------
+
+// L = mean over pairs of sum over (theta, t_x, t_y) of |pose - gt| (kind 1, Eq. 13) or
+// (pose - gt)^2 (kind 2); dpose = dL/dpose.  One block; fixed-order reduction.
+__global__ void __launch_bounds__(256) k_pose_loss(int n_pairs, const float* __restrict__ pose,
+                                                   const float* __restrict__ gt, int kind, float* __restrict__ loss,
+                                                   float* __restrict__ dpose) {
+    __shared__ float red[32];
+    const float inv = 1.f / (float)n_pairs;
+    float acc = 0.f;
+    for (int i = threadIdx.x; i < 3 * n_pairs; i += blockDim.x) {
+        const float d = pose[i] - gt[i];
+        float l, gr;
+        if (kind == 1) {
+            l = fabsf(d);
+            gr = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+        } else {
+            l = d * d;
+            gr = 2.f * d * inv;
+        }
+        acc += l;
+        if (dpose) dpose[i] = gr;
+    }
+    acc = block_reduce<false>(acc, red);
+    if (threadIdx.x == 0 && loss) loss[0] = acc * inv;
+}
+
+cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, int kind, float* loss, float* dpose,
+                             Tracer* tr, cudaStream_t st) {
+    tr->before(K_LOSS, st);
+    k_pose_loss<<<1, 256, 0, st>>>(n_pairs, pose, gt, kind, loss, dpose);
+    tr->close(st);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
 
@@ -675,7 +727,7 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
                                                                                              dpose, w.b1, B);
     w.tr->before(K_B_COLS, st);
     k_b_cols<N, P><<<dim3((P / 2) / (kThreads / T2), B), kThreads, b_smem_cols<P>(), st>>>(p, w.b1, w.s2, w.b2, B);
-    w.tr->before(K_B_MISC, st);
+    w.tr->before(K_B_C2R, st);
     k_b_c2r<N, P><<<dim3((N / 2) / (kThreads / T2), B, 2), kThreads, b_smem_rows<P>(), st>>>(p, tab, w.b2, w.gfr,
                                                                                                dg, B);
     w.tr->before(K_B_ROT, st);
@@ -684,9 +736,10 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     if (p.nt == 128) launch_stage1_adjoint<128>(p, w, B, st);
     else if (p.nt == 256) launch_stage1_adjoint<256>(p, w, B, st);
     else launch_stage1_adjoint<400>(p, w, B, st);
-    w.tr->before(K_B_MISC, st);
-    const int E = (N / 2 + 1) * N;
-    k_b_polT<<<dim3((E + kThreads - 1) / kThreads, B, 2), kThreads, 0, st>>>(p, w.gpol, w.gmt, B);
+    w.tr->before(K_B_POLT, st);
+    const int E = (N / 2 + 1) * N, lb = (E + kThreads - 1) / kThreads;
+    const int hb = (p.n_heavy + kThreads / 32 - 1) / (kThreads / 32);
+    k_b_polT<<<dim3(lb + hb, B, 2), kThreads, 0, st>>>(p, w.gpol, w.gmt, B, lb);
     w.tr->before(K_B_S1COLS, st);
     k_b_s1cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st>>>(p, w.s1, w.gmt,
                                                                                                  w.gs1, B);

@@ -35,7 +35,13 @@ struct DevPlan {
     const int* csr_ptr;
     const int* csr_col;
     const float* csr_w;
+    // elements whose CSR row has more than kHeavyRow taps (near the DC bin every angle samples the
+    // same few elements); the adjoint gives each of them a warp instead of a thread
+    const int* heavy;
+    int n_heavy;
 };
+
+constexpr int kHeavyRow = 32;
 
 inline int angle_chunks(const DevPlan& p) { return (p.nr + kAngleRadii - 1) / kAngleRadii; }
 inline int fft_threads(int L) { return L / 16 == 25 ? 25 : L / 16; }
@@ -44,8 +50,8 @@ inline int c2r_blocks(const DevPlan& p) { return (p.n / 2) / (kThreads / fft_thr
 // Kernel kinds, for the launch tracer.
 enum Kind {
     K_S1_ROWS, K_S1_COLS, K_ANGLE, K_THETA, K_S2_ROWS, K_S2_COLS, K_S2_C2R, K_SXY,
-    K_B_SXY, K_B_COLS, K_B_ROWS, K_B_ROT, K_B_THETA, K_B_ANGLE, K_B_S1COLS, K_B_S1ROWS, K_B_MISC,
-    K_COUNT
+    K_B_SXY, K_B_COLS, K_B_ROWS, K_B_ROT, K_B_THETA, K_B_ANGLE, K_B_S1COLS, K_B_S1ROWS, K_B_C2R, K_B_POLT,
+    K_LOSS, K_COUNT
 };
 extern const char* const kKindNames[K_COUNT];
 
@@ -108,6 +114,8 @@ cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long
                            const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st);
 cudaError_t launch_backward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                             const float* g, const float* dpose, float* df, float* dg, cudaStream_t st);
+cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, int kind, float* loss, float* dpose,
+                             Tracer* tr, cudaStream_t st);
 cudaError_t prepare_kernels();
 
 }  // namespace fmbym

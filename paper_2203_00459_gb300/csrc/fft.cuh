@@ -13,7 +13,9 @@
 // an element stride es > 1 interleaves several sequences (column tiles).
 //
 // Twiddles come from a table tw[k] = exp(-2 pi i k / L), k < L, computed in double precision on
-// the host and rounded to float; the inverse transform uses their conjugates.  Forward is the
+// the host and rounded to float; the inverse transform uses their conjugates.  A butterfly loads
+// one base twiddle (two for radix 16) and forms the other powers by at most three complex
+// products, which keeps the table loads (divergent across a warp) off the L1 critical path.  Forward is the
 // unnormalised DFT X[k] = sum_n x[n] exp(-2 pi i n k / L); inverse has the + sign and no 1/L.
 #pragma once
 #include <cuda_runtime.h>
@@ -160,13 +162,29 @@ __device__ __forceinline__ void fft_pass(float2* buf, int es, int j, bool active
 #pragma unroll
             for (int t = 0; t < R; ++t) v[m][t] = buf[spad(b + t * NB) * es];
             if constexpr (NS > 1) {
+                // twiddles W^(bm t), W = W_{NS R}: one table load of W^bm (and of W^(4 bm) for
+                // radix 16); the other powers by complex products at most three deep
+                constexpr int STEP = L / (NS * R);
                 const int bm = b % NS;
+                float2 w[R];
+                w[1] = __ldg(&tw[bm * STEP]);
+                if constexpr (S > 0) w[1].y = -w[1].y;
+                if constexpr (R >= 16) {
+                    w[4] = __ldg(&tw[4 * bm * STEP]);
+                    if constexpr (S > 0) w[4].y = -w[4].y;
+                    w[2] = c_mul(w[1], w[1]);
+                    w[3] = c_mul(w[2], w[1]);
+                    w[8] = c_mul(w[4], w[4]);
+                    w[12] = c_mul(w[8], w[4]);
 #pragma unroll
-                for (int t = 1; t < R; ++t) {
-                    float2 w = __ldg(&tw[bm * t * (L / (NS * R))]);
-                    if constexpr (S > 0) w.y = -w.y;
-                    v[m][t] = c_mul(v[m][t], w);
+                    for (int t = 5; t < R; ++t)
+                        if ((t & 3) != 0) w[t] = c_mul(w[t & ~3], w[t & 3]);
+                } else {
+#pragma unroll
+                    for (int t = 2; t < R; ++t) w[t] = (t & 1) ? c_mul(w[t - 1], w[1]) : c_mul(w[t / 2], w[t / 2]);
                 }
+#pragma unroll
+                for (int t = 1; t < R; ++t) v[m][t] = c_mul(v[m][t], w[t]);
             }
             dft<R, S>(v[m]);
         }

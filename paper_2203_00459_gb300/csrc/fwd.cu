@@ -535,7 +535,8 @@ static cudaError_t prepare_np() {
 
 const char* const kKindNames[K_COUNT] = {
     "s1_rows", "s1_cols", "angle", "theta", "s2_rows", "s2_cols", "s2_c2r", "sxy",
-    "b_sxy", "b_cols", "b_rows", "b_rot", "b_theta", "b_angle", "b_s1cols", "b_s1rows", "b_misc"};
+    "b_sxy", "b_cols", "b_rows", "b_rot", "b_theta", "b_angle", "b_s1cols", "b_s1rows", "b_c2r", "b_polT",
+    "loss"};
 
 cudaError_t prepare_forward_kernels() {
     cudaError_t e;

@@ -110,6 +110,16 @@ class PoseSearch:
         _lib.check(st, self.handle)
         return df, dg
 
+    def pose_loss(self, pose, gt, kind=1, loss=None, dpose=None, stream=None):
+        """Eq. 13 loss (kind 1 = L1, 2 = L2; mean over pairs) and dloss/dpose, on the device."""
+        n_pairs = pose.shape[0]
+        loss = torch.empty(1, device=pose.device) if loss is None else loss
+        dpose = torch.empty_like(pose) if dpose is None else dpose
+        st = _lib.lib().fmbym_pose_loss(self.handle, _stream(stream), n_pairs, _ptr(pose.contiguous()),
+                                        _ptr(gt.contiguous()), int(kind), _ptr(loss), _ptr(dpose))
+        _lib.check(st, self.handle)
+        return loss, dpose
+
     def pose_host(self, f_host, g_host, size_idx=None, offsets=None, stream=None):
         """Forward search from host (CPU, ideally pinned) tensors; returns the pose as a CPU tensor.
         Copies in, computes and copies out inside the call, which synchronises the stream."""
