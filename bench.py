@@ -250,7 +250,8 @@ def main():
     n, nt, nr = spec["n"], spec["n_theta"], spec["n_r"]
     f, g, gt = synth.make_batch(args.workload, pairs=B, start=rank * B)
     cfg = size_cfg(n, nt, nr)
-    search = PoseSearch([cfg], max_pairs=B)
+    search = PoseSearch([cfg], max_pairs=B, flags=_lib.FLAG_GRAPH)   # production path: graph replays
+    traced = PoseSearch([cfg], max_pairs=B)                          # direct launches, per-kernel events
     L = _lib.lib()
     fd = torch.from_numpy(f).cuda()
     gd = torch.from_numpy(g).cuda()
@@ -277,12 +278,15 @@ def main():
     def step():
         run_step(search, fd, gd, gtd, pose, dpose, loss, df, dg, B)
 
+    def traced_step():
+        run_step(traced, fd, gd, gtd, pose, dpose, loss, df, dg, B)
+
     for _ in range(args.warmup):
         step()
+        traced_step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, per-step CUDA events, L2 flushed between steps ----
-    _lib.check(L.fmbym_set_tracing(search.handle, 1), search.handle)
+    # ---- timed region: K steps (CUDA-graph replays), per-step CUDA events, L2 flushed between ----
     launches0 = L.fmbym_launch_count(search.handle)
     clocks = ClockSampler(local)
     clocks.start()
@@ -307,13 +311,27 @@ def main():
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
+
+    # ---- second timed region, same K steps launched directly with the library's tracer on: the
+    # event before each launch gives every kernel's device time on the launching stream ----
     import ctypes
+    _lib.check(L.fmbym_set_tracing(traced.handle, 1), traced.handle)
+    tms = []
+    for k in range(args.steps):
+        flush.zero_()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record()
+        traced_step()
+        b_.record()
+        tms.append((a_, b_))
+    torch.cuda.synchronize()
+    ms_traced = sum(a_.elapsed_time(b_) for a_, b_ in tms) / len(tms)
     K = 32
     tot = (ctypes.c_double * K)()
     cnt = (ctypes.c_longlong * K)()
     nk = ctypes.c_int()
-    _lib.check(L.fmbym_trace_summary(search.handle, K, tot, cnt, ctypes.byref(nk)), search.handle)
-    _lib.check(L.fmbym_set_tracing(search.handle, 0), search.handle)
+    _lib.check(L.fmbym_trace_summary(traced.handle, K, tot, cnt, ctypes.byref(nk)), traced.handle)
+    _lib.check(L.fmbym_set_tracing(traced.handle, 0), traced.handle)
     kernels = {}
     for k in range(nk.value):
         if cnt[k]:
@@ -430,10 +448,12 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "mode": args.mode,
                 "config": {"workload": args.workload, "n": n, "n_theta": nt, "n_r": nr, "pairs_per_gpu": B,
                            "pad": "zero to 2N", "l2": "flushed (256 MB write) between timed steps"},
-                "roofline": roof, "kernel_shares": shares, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "kernel_shares": shares, "ms_per_step_direct_launch": ms_traced,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, **extra}
         print(json.dumps(line), flush=True)
     search.close()
+    traced.close()
     if dist:
         dist.destroy_process_group()
 

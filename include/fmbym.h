@@ -67,8 +67,18 @@ typedef struct fmbym_size_cfg {
     float band_hi;
 } fmbym_size_cfg;
 
+/* Handle flags.
+ *   FMBYM_FLAG_GRAPH  capture each distinct call layout (forward or backward; pair count, sizes
+ *                     and offsets; buffer pointers) into a CUDA graph on first use and replay it
+ *                     with one launch afterwards (up to 16 layouts are kept, least recently used
+ *                     released).  The first call of a layout must not happen while the caller's
+ *                     stream is being captured.  Ignored while tracing is on. */
+enum fmbym_flags { FMBYM_FLAG_GRAPH = 1 };
+
 /* Handle configuration: n_sizes size configurations (host array, copied by fmbym_create),
- * the largest number of pairs one call may carry, and flags (0; reserved). */
+ * the largest number of pairs one call may carry, and flags (fmbym_flags).  Pairs of different
+ * sizes in one call run as concurrent groups, one per size, on internal streams forked from and
+ * joined back to the caller's stream. */
 typedef struct fmbym_config {
     int n_sizes;
     const fmbym_size_cfg* sizes;

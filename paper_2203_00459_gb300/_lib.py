@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfmbym.so")
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT = range(6)
+FLAG_GRAPH = 1
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE", 4: "CUDA", 5: "TIMEOUT"}
 
 

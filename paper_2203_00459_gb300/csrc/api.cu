@@ -30,12 +30,28 @@ bool supported_nt(int nt) { return nt == 128 || nt == 256 || nt == 400; }
 
 }  // namespace
 
+// One captured call layout: its CUDA graph and the device copy of its pair table.
+struct GraphEntry {
+    std::vector<long long> key;  // kind, pair count, buffer pointers, pair table
+    cudaGraphExec_t exec = nullptr;
+    long long* d_tab = nullptr;
+    long long kernels = 0;
+    unsigned long long last_use = 0;
+};
+
 struct fmbym_handle {
     int device = 0;
     int max_pairs = 0;
+    int flags = 0;
     std::vector<HostPlan> plans;
-    void* ws = nullptr;
+    std::vector<void*> ws;        // one workspace region per size, for max_pairs pairs
     size_t ws_size = 0;
+    std::vector<cudaStream_t> side;   // streams of the size groups after the first
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    cudaStream_t cap = nullptr;       // capture stream of the graph cache
+    std::vector<GraphEntry> graphs;
+    unsigned long long use_clock = 0;
     long long* d_tab = nullptr;   // [max_pairs][3]
     long long* h_tab = nullptr;   // pinned staging of the pair table
     cudaEvent_t tab_free = nullptr;
@@ -301,6 +317,123 @@ int make_table(fmbym_handle* h, int n_pairs, const int* size_idx, const long lon
     return FMBYM_OK;
 }
 
+// Buffers of one forward (kind 0) or backward (kind 1) call.
+struct LaunchArgs {
+    int kind;
+    const float* f;
+    const float* g;
+    float* pose;
+    float* c_theta;
+    float* c_xy;
+    const float* dpose;
+    float* df;
+    float* dg;
+};
+
+cudaError_t launch_group(fmbym_handle* h, const Group& gr, const long long* dtab, const LaunchArgs& a,
+                         cudaStream_t s) {
+    const DevPlan& p = h->plans[gr.size_idx].dev;
+    Ws w = ws_carve(p, gr.count, h->ws[gr.size_idx], true);
+    w.tr = &h->tracer;
+    w.cnt = h->d_cnt + (size_t)gr.size_idx * h->max_pairs;
+    w.bpose = h->d_bpose;
+    if (a.kind == 0)
+        return launch_forward(p, w, gr.count, dtab + 3 * gr.first, a.f, a.g, a.pose, a.c_theta, a.c_xy, s);
+    return launch_backward(p, w, gr.count, dtab + 3 * gr.first, a.f, a.g, a.dpose, a.df, a.dg, s);
+}
+
+// Launches every size group: the first on the caller's stream, the others on the handle's side
+// streams forked from it and joined back, so that groups of different sizes run concurrently.
+// With more than one group the tracer only counts launches (its events assume one stream).
+cudaError_t enqueue(fmbym_handle* h, cudaStream_t st, const std::vector<Group>& groups, const long long* dtab,
+                    const LaunchArgs& a) {
+    if (groups.size() == 1) return launch_group(h, groups[0], dtab, a, st);
+    const bool tracing = h->tracer.on;
+    h->tracer.on = false;
+    cudaError_t e = cudaEventRecord(h->ev_fork, st);
+    for (size_t k = 1; k < groups.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(h->side[k - 1], h->ev_fork, 0);
+    for (size_t k = 0; k < groups.size() && e == cudaSuccess; ++k) {
+        cudaStream_t s = k == 0 ? st : h->side[k - 1];
+        e = launch_group(h, groups[k], dtab, a, s);
+        if (e == cudaSuccess && k > 0) e = cudaEventRecord(h->ev_join[k - 1], s);
+        if (e == cudaSuccess && k > 0) e = cudaStreamWaitEvent(st, h->ev_join[k - 1], 0);
+    }
+    h->tracer.on = tracing;
+    return e;
+}
+
+constexpr size_t kMaxGraphs = 16;
+
+// Runs one call.  With FMBYM_FLAG_GRAPH (and tracing off) each distinct layout (kind, pairs,
+// buffers, pair table) is captured once into a CUDA graph whose pair table lives in its own
+// device buffer, and replayed with a single cudaGraphLaunch; the least recently used of more than
+// kMaxGraphs graphs is released.  Otherwise the pair table is copied from pinned memory and the
+// groups are launched directly.
+int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Group>& groups, const LaunchArgs& a) {
+    cudaError_t e;
+    if ((h->flags & FMBYM_FLAG_GRAPH) && !h->tracer.on) {
+        std::vector<long long> key = {a.kind, n_pairs, (long long)(uintptr_t)a.f, (long long)(uintptr_t)a.g,
+                                      (long long)(uintptr_t)a.pose, (long long)(uintptr_t)a.c_theta,
+                                      (long long)(uintptr_t)a.c_xy, (long long)(uintptr_t)a.dpose,
+                                      (long long)(uintptr_t)a.df, (long long)(uintptr_t)a.dg};
+        key.insert(key.end(), h->h_tab, h->h_tab + 3 * (size_t)n_pairs);
+        GraphEntry* ge = nullptr;
+        for (auto& x : h->graphs)
+            if (x.key == key) ge = &x;
+        if (!ge) {
+            if (h->graphs.size() >= kMaxGraphs) {
+                auto lru = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                            [](const GraphEntry& x, const GraphEntry& y) { return x.last_use < y.last_use; });
+                if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+                cudaGraphExecDestroy(lru->exec);
+                cudaFree(lru->d_tab);
+                h->graphs.erase(lru);
+            }
+            GraphEntry n;
+            n.key = key;
+            if ((e = cudaMalloc(&n.d_tab, sizeof(long long) * 3 * n_pairs)) != cudaSuccess ||
+                (e = cudaMemcpy(n.d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice)) !=
+                    cudaSuccess) {
+                cudaFree(n.d_tab);
+                return cuda_fail(h, e, "graph table");
+            }
+            const long long before = h->tracer.launches;
+            cudaGraph_t graph = nullptr;
+            if ((e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+                cudaFree(n.d_tab);
+                return cuda_fail(h, e, "cudaStreamBeginCapture");
+            }
+            cudaError_t le = enqueue(h, h->cap, groups, n.d_tab, a);
+            e = cudaStreamEndCapture(h->cap, &graph);
+            n.kernels = h->tracer.launches - before;
+            h->tracer.launches = before;
+            if (le != cudaSuccess || e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaFree(n.d_tab);
+                return cuda_fail(h, le != cudaSuccess ? le : e, "graph capture");
+            }
+            e = cudaGraphInstantiate(&n.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaFree(n.d_tab);
+                return cuda_fail(h, e, "cudaGraphInstantiate");
+            }
+            h->graphs.push_back(std::move(n));
+            ge = &h->graphs.back();
+        }
+        ge->last_use = ++h->use_clock;
+        if ((e = cudaGraphLaunch(ge->exec, st)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+        h->tracer.launches += ge->kernels;
+        return FMBYM_OK;
+    }
+    if ((e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return cuda_fail(h, e, "pair table copy");
+    if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    if ((e = enqueue(h, st, groups, h->d_tab, a)) != cudaSuccess) return cuda_fail(h, e, a.kind ? "backward launch" : "forward launch");
+    return FMBYM_OK;
+}
+
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
@@ -317,7 +450,15 @@ void fmbym_destroy(fmbym_handle* h) {
     if (!h) return;
     cudaDeviceSynchronize();
     for (auto& p : h->plans) cudaFree(p.tables);
-    cudaFree(h->ws);
+    for (void* w : h->ws) cudaFree(w);
+    for (auto& ge : h->graphs) {
+        if (ge.exec) cudaGraphExecDestroy(ge.exec);
+        cudaFree(ge.d_tab);
+    }
+    for (cudaStream_t st : h->side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : h->ev_join) cudaEventDestroy(ev);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->cap) cudaStreamDestroy(h->cap);
     cudaFree(h->d_tab);
     cudaFree(h->d_stage_f);
     cudaFree(h->d_stage_g);
@@ -360,7 +501,7 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
         }
         prepared = true;
     }
-    size_t ws = 0;
+    h->flags = cfg->flags;
     int nmax = 0;
     for (int i = 0; i < cfg->n_sizes; ++i) {
         HostPlan hp;
@@ -371,23 +512,39 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
             fmbym_destroy(h);
             return cuda_fail(nullptr, e, "plan tables");
         }
-        ws = std::max(ws, ws_bytes(hp.dev, cfg->max_pairs, true));
+        const size_t b = ws_bytes(hp.dev, cfg->max_pairs, true);
+        void* w = nullptr;
+        if ((e = cudaMalloc(&w, b)) != cudaSuccess || (e = cudaMemset(w, 0, b)) != cudaSuccess) {
+            fmbym_destroy(h);
+            return cuda_fail(nullptr, e, "workspace allocation");
+        }
+        h->ws.push_back(w);
+        h->ws_size += b;
         nmax = std::max(nmax, hp.cfg.n);
     }
-    h->ws_size = ws;
-    if ((e = cudaMalloc(&h->ws, ws)) != cudaSuccess || (e = cudaMemset(h->ws, 0, ws)) != cudaSuccess ||
+    for (int i = 1; i < cfg->n_sizes; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) break;
+        h->side.push_back(st);
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) break;
+        h->ev_join.push_back(ev);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess ||
         (e = cudaMalloc(&h->d_tab, sizeof(long long) * 3 * cfg->max_pairs)) != cudaSuccess ||
         (e = cudaMallocHost(&h->h_tab, sizeof(long long) * 3 * cfg->max_pairs)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->tab_free, cudaEventDisableTiming)) != cudaSuccess) {
         fmbym_destroy(h);
-        return cuda_fail(nullptr, e, "workspace allocation");
+        return cuda_fail(nullptr, e, "stream, event or table allocation");
     }
     h->stage_elems = (long long)cfg->max_pairs * nmax * nmax;
     if ((e = cudaMalloc(&h->d_stage_f, sizeof(float) * h->stage_elems)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_g, sizeof(float) * h->stage_elems)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_pose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs)) != cudaSuccess ||
-        (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
+        (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_bpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess) {
         fmbym_destroy(h);
         return cuda_fail(nullptr, e, "staging allocation");
@@ -407,19 +564,14 @@ int fmbym_pose(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, 
     std::vector<Group> groups;
     int rc = make_table(h, n_pairs, size_idx, offsets, groups, nullptr);
     if (rc != FMBYM_OK) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "pair table copy");
-    if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
-    for (const Group& gr : groups) {
-        const DevPlan& p = h->plans[gr.size_idx].dev;
-        Ws w = ws_carve(p, gr.count, h->ws, true);
-        w.tr = &h->tracer;
-        w.cnt = h->d_cnt;
-        e = launch_forward(p, w, gr.count, h->d_tab + 3 * gr.first, f, g, pose, c_theta, c_xy, st);
-        if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
-    }
-    return FMBYM_OK;
+    LaunchArgs a{};
+    a.kind = 0;
+    a.f = f;
+    a.g = g;
+    a.pose = pose;
+    a.c_theta = c_theta;
+    a.c_xy = c_xy;
+    return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
 }
 
 int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
@@ -433,20 +585,14 @@ int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* s
     std::vector<Group> groups;
     int rc = make_table(h, n_pairs, size_idx, offsets, groups, nullptr);
     if (rc != FMBYM_OK) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "pair table copy");
-    if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
-    for (const Group& gr : groups) {
-        const DevPlan& p = h->plans[gr.size_idx].dev;
-        Ws w = ws_carve(p, gr.count, h->ws, true);
-        w.tr = &h->tracer;
-        w.cnt = h->d_cnt;
-        w.bpose = h->d_bpose;
-        e = launch_backward(p, w, gr.count, h->d_tab + 3 * gr.first, f, g, dpose, df, dg, st);
-        if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
-    }
-    return FMBYM_OK;
+    LaunchArgs a{};
+    a.kind = 1;
+    a.f = f;
+    a.g = g;
+    a.dpose = dpose;
+    a.df = df;
+    a.dg = dg;
+    return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
 }
 
 int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
@@ -467,20 +613,15 @@ int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_
     if ((e = cudaMemcpyAsync(h->d_stage_f, f_host, sizeof(float) * total_elems, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess ||
         (e = cudaMemcpyAsync(h->d_stage_g, g_host, sizeof(float) * total_elems, cudaMemcpyHostToDevice, st)) !=
-            cudaSuccess ||
-        (e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
         return cuda_fail(h, e, "host-to-device copy");
-    if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
-    for (const Group& gr : groups) {
-        const DevPlan& p = h->plans[gr.size_idx].dev;
-        Ws w = ws_carve(p, gr.count, h->ws, true);
-        w.tr = &h->tracer;
-        w.cnt = h->d_cnt;
-        e = launch_forward(p, w, gr.count, h->d_tab + 3 * gr.first, h->d_stage_f, h->d_stage_g, h->d_stage_pose,
-                           nullptr, nullptr, st);
-        if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
-    }
+    LaunchArgs a{};
+    a.kind = 0;
+    a.f = h->d_stage_f;
+    a.g = h->d_stage_g;
+    a.pose = h->d_stage_pose;
+    rc = run_call(h, st, n_pairs, groups, a);
+    if (rc != FMBYM_OK) return rc;
     if ((e = cudaMemcpyAsync(pose_host, h->d_stage_pose, sizeof(float) * 3 * n_pairs, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
         return cuda_fail(h, e, "device-to-host copy");

@@ -34,14 +34,15 @@ def _stream(stream):
 class PoseSearch:
     """A library handle: plans and workspace for the given sizes and up to max_pairs pairs per call."""
 
-    def __init__(self, sizes, max_pairs, device=None):
+    def __init__(self, sizes, max_pairs, device=None, flags=0):
         self.sizes = [dict(s) for s in sizes]
         self.max_pairs = int(max_pairs)
+        self.flags = int(flags)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         L = _lib.lib()
         arr = (_lib.SizeCfg * len(self.sizes))(*[_lib.SizeCfg(**s) for s in self.sizes])
         self._arr = arr
-        cfg = _lib.Config(len(self.sizes), arr, self.max_pairs, 0)
+        cfg = _lib.Config(len(self.sizes), arr, self.max_pairs, self.flags)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(L.fmbym_create(ctypes.byref(h), ctypes.byref(cfg)), None)
