@@ -189,6 +189,80 @@ unsigned long long fmbym_noalloc_capacity(void);
 /* Text of the last failure of fmbym_pose_noalloc on this host thread ("" if none). */
 const char* fmbym_noalloc_last_error(void);
 
+/* ---------------------------------------------------------------------------------------------
+ * Masking network h_alpha (Sec. III-D, Eq. 10-12; layout of Tab. II).  A U-Net over the two-channel
+ * image [f, g]: per level two 3x3 convolutions (no bias) each followed by BatchNorm and ReLU,
+ * 2x2 max-pool down, bilinear x2 up (align_corners = False) concatenated before the skip
+ * ([up, skip]), and a 1x1 convolution to 2 channels with bias and a sigmoid giving the masks
+ * m_f, m_g; the outputs are f o m_f and g o m_g (Eq. 11).  Convolutions run on bf16 tensor cores
+ * with float32 accumulation; activations after BN + ReLU, pooling and upsampling are bf16;
+ * parameters are float32 masters.  BatchNorm uses batch statistics in training (population
+ * variance; running mean/var updated with momentum 0.1 and the unbiased variance; eps 1e-5) and the
+ * running statistics in evaluation.
+ *
+ * Flat parameter layout (float32): for every convolution in the order enc0a, enc0b, enc1a, ...,
+ * enc{L-1}b, dec{L-2}a, dec{L-2}b, ..., dec0a, dec0b: weight [c_out][c_in][3][3], BN gamma [c_out],
+ * BN beta [c_out]; then the head weight [2][c_1] and bias [2].  Running statistics: per convolution
+ * in the same order, mean [c_out] then var [c_out].  Gradients use the parameter layout.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct fmbym_unet fmbym_unet;
+
+/* levels L in [2, 8]; channels c_1..c_L each 8, 16, 32 or 64, non-decreasing, with
+ * c_i + c_{i+1} <= 128; height a multiple of 8 * 2^(L-1) and width of 32 * 2^(L-1);
+ * max_batch = the largest number of scan pairs per call. */
+typedef struct fmbym_unet_config {
+    int levels;
+    int channels[8];
+    int height;
+    int width;
+    int max_batch;
+} fmbym_unet_config;
+
+/* Allocates parameters (zero), Adam moments (zero), running statistics (mean 0, var 1), and every
+ * activation and gradient buffer for max_batch pairs.  Synchronous. */
+int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg);
+void fmbym_unet_destroy(fmbym_unet* u);
+const char* fmbym_unet_last_error(const fmbym_unet* u);
+
+/* Element counts of the parameter and running-statistics arrays, and their device addresses
+ * (owned by the handle; the caller may read and write them between calls). */
+long long fmbym_unet_param_count(const fmbym_unet* u);
+long long fmbym_unet_running_count(const fmbym_unet* u);
+float* fmbym_unet_params(fmbym_unet* u);
+float* fmbym_unet_grads(fmbym_unet* u);
+float* fmbym_unet_running(fmbym_unet* u);
+
+/* Copies parameters and/or running statistics (device float32 in the flat layouts, or NULL to keep
+ * the current ones) into the handle; loading parameters also resets the Adam moments.  Store copies
+ * the handle's parameters, running statistics and gradients out (each device pointer or NULL). */
+int fmbym_unet_load(fmbym_unet* u, void* stream, const float* params, const float* running);
+int fmbym_unet_store(fmbym_unet* u, void* stream, float* params, float* running, float* grads);
+
+/* Inspection: copies one tensor of convolution layer `layer` (0-based, in the parameter order) for
+ * the first n pairs of the last call, widened to float32 NHWC, into dst (device): which = 0 the
+ * convolution output y (pre-BN), 1 the bf16 activation a (post-ReLU), 2 dL/da, 3 the bf16 dL/dy.
+ * Synchronous. */
+int fmbym_unet_layer_tensor(fmbym_unet* u, void* stream, int layer, int which, int n, float* dst);
+
+/* Forward (Eq. 10-11) for n pairs: f, g device float32 [n][height][width]; training = 1 uses and
+ * updates batch statistics (and keeps the activations for fmbym_unet_backward), 0 uses the running
+ * statistics.  f_out, g_out (device float32 like f, or NULL) receive f o m_f and g o m_g; masks
+ * (device float32 [n][2][height][width], or NULL) the masks. */
+int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const float* g, int training,
+                       float* f_out, float* g_out, float* masks);
+
+/* Backward of the last training forward (same n, f and g): given dL/d(f o m_f) and dL/d(g o m_g)
+ * (device float32 like f), overwrites the gradient array with dL/dparameters.  Deterministic. */
+int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, const float* g,
+                        const float* df_out, const float* dg_out);
+
+/* One Adam step (the optimiser of Sec. IV-B) on the parameters with the current gradients;
+ * step counts from 1 (bias correction). */
+int fmbym_unet_adam(fmbym_unet* u, void* stream, float lr, float beta1, float beta2, float eps, int step);
+
+/* Number of kernels the network handle has launched. */
+long long fmbym_unet_launch_count(const fmbym_unet* u);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int fmbym_version(void);
 

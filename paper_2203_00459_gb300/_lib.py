@@ -28,6 +28,11 @@ class Config(ctypes.Structure):
                 ("flags", ctypes.c_int)]
 
 
+class UnetConfig(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("channels", ctypes.c_int * 8), ("height", ctypes.c_int),
+                ("width", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
 # exported symbol -> (restype, argtypes)
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -46,6 +51,24 @@ SIGNATURES = {
     "fmbym_trace_summary": (_I, [_P, _I, _P, _P, _P]),
     "fmbym_trace_kind_name": (ctypes.c_char_p, [_I]),
     "fmbym_launch_count": (_LL, [_P]),
+    "fmbym_pose_noalloc": (_I, [_P, _P, _I, _P, _P, _P, _P, _P]),
+    "fmbym_noalloc_capacity": (ctypes.c_ulonglong, []),
+    "fmbym_noalloc_last_error": (ctypes.c_char_p, []),
+    "fmbym_unet_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(UnetConfig)]),
+    "fmbym_unet_destroy": (None, [_P]),
+    "fmbym_unet_last_error": (ctypes.c_char_p, [_P]),
+    "fmbym_unet_param_count": (_LL, [_P]),
+    "fmbym_unet_running_count": (_LL, [_P]),
+    "fmbym_unet_params": (_P, [_P]),
+    "fmbym_unet_grads": (_P, [_P]),
+    "fmbym_unet_running": (_P, [_P]),
+    "fmbym_unet_forward": (_I, [_P, _P, _I, _P, _P, _I, _P, _P, _P]),
+    "fmbym_unet_backward": (_I, [_P, _P, _I, _P, _P, _P, _P]),
+    "fmbym_unet_adam": (_I, [_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I]),
+    "fmbym_unet_launch_count": (_LL, [_P]),
+    "fmbym_unet_load": (_I, [_P, _P, _P, _P]),
+    "fmbym_unet_layer_tensor": (_I, [_P, _P, _I, _I, _I, _P]),
+    "fmbym_unet_store": (_I, [_P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -75,4 +98,10 @@ def lib(path: str = LIB_PATH):
 def check(status, handle=None):
     if status != OK:
         msg = lib().fmbym_last_error(handle)
+        raise FmbymError(status, msg.decode() if msg else "")
+
+
+def check_unet(status, handle=None):
+    if status != OK:
+        msg = lib().fmbym_unet_last_error(handle)
         raise FmbymError(status, msg.decode() if msg else "")

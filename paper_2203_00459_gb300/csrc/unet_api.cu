@@ -1,0 +1,547 @@
+// Host side of the masking network h_alpha (Sec. III-D): the layer graph of a U-Net with L levels
+// (two 3x3 conv + BN + ReLU per level, max-pool down, bilinear x2 up concatenated before the skip,
+// 1x1 sigmoid head), its buffers, and the forward, backward and Adam entry points of
+// include/fmbym.h.
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fmbym.h"
+#include "unet_kernels.cuh"
+
+using namespace fmbym::unet;
+
+namespace {
+
+int round16(int c) { return (c + 15) / 16 * 16; }
+
+// One 3x3 conv + BN + ReLU layer and its buffers.
+struct Layer {
+    std::string name;
+    int cin, cout, H, W;       // input channels, output channels, resolution
+    int cinp, coutp;           // channels rounded up to 16
+    long long w_off, g_off, b_off, rs_off;  // offsets in the parameter and running-stat arrays
+    bf16* wf = nullptr;        // forward weights [cout][9][cinp]
+    bf16* wd = nullptr;        // dgrad weights [cin][9][coutp]
+    float* y = nullptr;        // pre-BN output, float32 NHWC
+    bf16* a = nullptr;         // post-ReLU output, bf16 NHWC
+    float* da = nullptr;       // gradient of a
+    bf16* dy = nullptr;        // gradient of y (bf16, tensor-core operand)
+    float2* bn = nullptr;      // (mean, invstd) used by the last forward
+    float2* bsums = nullptr;   // adjoint means
+    // input: planes (first layer), or [in0 (c0), in1 (c1)]
+    bool planes = false;
+    const bf16* in0 = nullptr;
+    int c0 = 0;
+    const bf16* in1 = nullptr;
+    int c1 = 0;
+};
+
+}  // namespace
+
+struct fmbym_unet {
+    int levels = 0, ch[8] = {0}, H = 0, W = 0, max_batch = 0;
+    std::vector<Layer> layers;          // enc0a, enc0b, ..., enc{L-1}b, dec{L-2}a, ..., dec0b
+    std::vector<bf16*> pooled;          // pooled[i] = maxpool(a of enc{i-1}b), level i >= 1
+    std::vector<bf16*> upped;           // upped[i] = upsample(deeper) at level i < L-1
+    std::vector<float*> dpool, dup;     // gradients of pooled and upped
+    long long n_params = 0, n_running = 0, head_w = 0, head_b = 0;
+    float* params = nullptr;            // float32 master parameters
+    float* grads = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* running = nullptr;           // running mean / var of every BN channel
+    float2* stats = nullptr;            // per-CTA conv statistics
+    float2* bnpart = nullptr;           // BN adjoint partials
+    float* wpart = nullptr;             // wgrad partials
+    float* hpart = nullptr;             // head partials
+    size_t stats_cap = 0, bnpart_cap = 0, wpart_cap = 0, hpart_cap = 0;
+    std::vector<void*> allocs;
+    long long launches = 0;
+    int last_batch = -1;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_unet_create_error;
+
+int ufail(fmbym_unet* u, int code, const std::string& m) {
+    if (u) u->err = m;
+    else g_unet_create_error = m;
+    return code;
+}
+
+int ucuda(fmbym_unet* u, cudaError_t e, const char* what) {
+    return ufail(u, FMBYM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t ualloc(fmbym_unet* u, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e == cudaSuccess) {
+        u->allocs.push_back(q);
+        *p = (T*)q;
+    }
+    return e;
+}
+
+const int kBlock = 256;
+inline unsigned blocks(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <int COUT>
+cudaError_t conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
+                        float* out1, int split, int acc0, int acc1, float2* stats) {
+    const int cinp = dgrad ? L.coutp : L.cinp;
+    const bf16* w = dgrad ? L.wd : L.wf;
+    const size_t smem = conv_smem(COUT, cinp);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3x3<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid(L.W / kTW, L.H / kTH, B);
+    ++u->launches;
+    if (dgrad)
+        k_conv3x3<COUT><<<grid, 256, smem, st>>>(L.dy, L.cout, nullptr, 0, nullptr, nullptr, w, cinp, out0, out1,
+                                                 split, acc0, acc1, nullptr, L.H, L.W);
+    else
+        k_conv3x3<COUT><<<grid, 256, smem, st>>>(L.in0, L.c0, L.in1, L.c1, L.planes ? (const float*)L.in0 : nullptr,
+                                                 L.planes ? (const float*)L.in1 : nullptr, w, cinp, out0, out1,
+                                                 split, acc0, acc1, stats, L.H, L.W);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_dispatch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
+                          float* out1, int split, int acc0, int acc1, float2* stats) {
+    const int co = dgrad ? L.cin : L.cout;
+    switch (co) {
+        case 8: return conv_launch<8>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+        case 16: return conv_launch<16>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+        case 24: return conv_launch<24>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+        case 32: return conv_launch<32>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+        case 48: return conv_launch<48>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+        case 64: return conv_launch<64>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+        case 96: return conv_launch<96>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+        case 128: return conv_launch<128>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Inputs of layer k for a batch of B (planes for the first layer are set per call).
+void wire_inputs(fmbym_unet* u) {
+    const int L = u->levels;
+    for (int i = 0; i < L; ++i) {
+        Layer& a = u->layers[2 * i];
+        Layer& b = u->layers[2 * i + 1];
+        if (i > 0) {
+            a.in0 = u->pooled[i];
+            a.c0 = u->ch[i - 1];
+        }
+        b.in0 = a.a;
+        b.c0 = a.cout;
+    }
+    for (int j = 0; j < L - 1; ++j) {
+        const int i = L - 2 - j;  // level of this decoder pair
+        Layer& a = u->layers[2 * L + 2 * j];
+        Layer& b = u->layers[2 * L + 2 * j + 1];
+        a.in0 = u->upped[i];
+        a.c0 = u->ch[i + 1];
+        a.in1 = u->layers[2 * i + 1].a;  // skip: a of enc{i}b
+        a.c1 = u->ch[i];
+        b.in0 = a.a;
+        b.c0 = a.cout;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fmbym_unet_last_error(const fmbym_unet* u) { return u ? u->err.c_str() : g_unet_create_error.c_str(); }
+
+void fmbym_unet_destroy(fmbym_unet* u) {
+    if (!u) return;
+    cudaDeviceSynchronize();
+    for (void* p : u->allocs) cudaFree(p);
+    delete u;
+}
+
+int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
+    g_unet_create_error.clear();
+    if (!out || !cfg) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    const int L = cfg->levels;
+    if (L < 2 || L > 8) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "levels must be in [2, 8]");
+    for (int i = 0; i < L; ++i) {
+        const int c = cfg->channels[i];
+        if (c != 8 && c != 16 && c != 32 && c != 64)
+            return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "channels must be 8, 16, 32 or 64");
+        if (i > 0 && c < cfg->channels[i - 1]) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "channels must not decrease");
+    }
+    for (int i = 0; i + 1 < L; ++i)
+        if (cfg->channels[i] + cfg->channels[i + 1] > 128)
+            return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "decoder concatenation wider than 128 channels");
+    if (cfg->max_batch < 1) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "max_batch must be >= 1");
+    const int H = cfg->height, W = cfg->width;
+    if (H <= 0 || W <= 0 || H % (kTH << (L - 1)) || W % (kTW << (L - 1)))
+        return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE,
+                     "height must be a multiple of 8*2^(L-1) and width of 32*2^(L-1)");
+    fmbym_unet* u = new fmbym_unet();
+    u->levels = L;
+    for (int i = 0; i < L; ++i) u->ch[i] = cfg->channels[i];
+    u->H = H;
+    u->W = W;
+    u->max_batch = cfg->max_batch;
+    const int B = cfg->max_batch;
+    // layer list and parameter offsets (the order of the flat parameter array)
+    long long off = 0, roff = 0;
+    auto add = [&](const std::string& nm, int cin, int cout, int lvl) {
+        Layer l;
+        l.name = nm;
+        l.cin = cin;
+        l.cout = cout;
+        l.H = H >> lvl;
+        l.W = W >> lvl;
+        l.cinp = round16(cin);
+        l.coutp = round16(cout);
+        l.w_off = off;
+        off += (long long)cout * cin * 9;
+        l.g_off = off;
+        off += cout;
+        l.b_off = off;
+        off += cout;
+        l.rs_off = roff;
+        roff += 2 * cout;
+        u->layers.push_back(l);
+    };
+    int cprev = 2;
+    for (int i = 0; i < L; ++i) {
+        add("enc" + std::to_string(i) + "a", cprev, u->ch[i], i);
+        add("enc" + std::to_string(i) + "b", u->ch[i], u->ch[i], i);
+        cprev = u->ch[i];
+    }
+    int deeper = u->ch[L - 1];
+    for (int i = L - 2; i >= 0; --i) {
+        add("dec" + std::to_string(i) + "a", deeper + u->ch[i], u->ch[i], i);
+        add("dec" + std::to_string(i) + "b", u->ch[i], u->ch[i], i);
+        deeper = u->ch[i];
+    }
+    u->head_w = off;
+    off += 2 * u->ch[0];
+    u->head_b = off;
+    off += 2;
+    u->n_params = off;
+    u->n_running = roff;
+    u->layers[0].planes = true;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+    };
+    chk(ualloc(u, &u->params, off));
+    chk(ualloc(u, &u->grads, off));
+    chk(ualloc(u, &u->adam_m, off));
+    chk(ualloc(u, &u->adam_v, off));
+    chk(ualloc(u, &u->running, roff));
+    size_t stats_cap = 0, bn_cap = 0, w_cap = 0;
+    for (Layer& l : u->layers) {
+        const size_t px = (size_t)B * l.H * l.W;
+        chk(ualloc(u, &l.wf, (size_t)l.cout * 9 * l.cinp));
+        chk(ualloc(u, &l.wd, (size_t)l.cin * 9 * l.coutp));
+        chk(ualloc(u, &l.y, px * l.cout));
+        chk(ualloc(u, &l.a, px * l.cout));
+        chk(ualloc(u, &l.da, px * l.cout));
+        chk(ualloc(u, &l.dy, px * l.cout));
+        chk(ualloc(u, &l.bn, l.cout));
+        chk(ualloc(u, &l.bsums, l.cout));
+        stats_cap = std::max(stats_cap, px / (kTH * kTW) * l.cout);
+        bn_cap = std::max(bn_cap, (px / 1024 + 1) * l.cout);
+        w_cap = std::max(w_cap, (size_t)600 * l.cout * 9 * l.cin);
+    }
+    u->pooled.assign(L, nullptr);
+    u->upped.assign(L, nullptr);
+    u->dpool.assign(L, nullptr);
+    u->dup.assign(L, nullptr);
+    for (int i = 1; i < L; ++i) {
+        const size_t px = (size_t)B * (H >> i) * (W >> i);
+        chk(ualloc(u, &u->pooled[i], px * u->ch[i - 1]));
+        chk(ualloc(u, &u->dpool[i], px * u->ch[i - 1]));
+    }
+    for (int i = 0; i + 1 < L; ++i) {
+        const size_t px = (size_t)B * (H >> i) * (W >> i);
+        chk(ualloc(u, &u->upped[i], px * u->ch[i + 1]));
+        chk(ualloc(u, &u->dup[i], px * u->ch[i + 1]));
+    }
+    u->stats_cap = stats_cap;
+    u->bnpart_cap = bn_cap;
+    u->wpart_cap = w_cap;
+    u->hpart_cap = ((size_t)B * H * W / kBlock + 1) * (2 * u->ch[0] + 2);
+    chk(ualloc(u, &u->stats, stats_cap));
+    chk(ualloc(u, &u->bnpart, bn_cap));
+    chk(ualloc(u, &u->wpart, w_cap));
+    chk(ualloc(u, &u->hpart, u->hpart_cap));
+    if (e == cudaSuccess) {
+        // running statistics start at mean 0, variance 1
+        std::vector<float> rs(roff);
+        for (const Layer& l : u->layers)
+            for (int c = 0; c < l.cout; ++c) {
+                rs[l.rs_off + c] = 0.f;
+                rs[l.rs_off + l.cout + c] = 1.f;
+            }
+        chk(cudaMemcpy(u->running, rs.data(), rs.size() * 4, cudaMemcpyHostToDevice));
+        chk(cudaMemset(u->params, 0, off * 4));
+        chk(cudaMemset(u->grads, 0, off * 4));
+        chk(cudaMemset(u->adam_m, 0, off * 4));
+        chk(cudaMemset(u->adam_v, 0, off * 4));
+        chk(cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgradSmem));
+    }
+    if (e != cudaSuccess) {
+        fmbym_unet_destroy(u);
+        return ucuda(nullptr, e, "U-Net allocation");
+    }
+    wire_inputs(u);
+    *out = u;
+    return FMBYM_OK;
+}
+
+long long fmbym_unet_param_count(const fmbym_unet* u) { return u ? u->n_params : 0; }
+long long fmbym_unet_running_count(const fmbym_unet* u) { return u ? u->n_running : 0; }
+float* fmbym_unet_params(fmbym_unet* u) { return u ? u->params : nullptr; }
+float* fmbym_unet_grads(fmbym_unet* u) { return u ? u->grads : nullptr; }
+float* fmbym_unet_running(fmbym_unet* u) { return u ? u->running : nullptr; }
+long long fmbym_unet_launch_count(const fmbym_unet* u) { return u ? u->launches : 0; }
+
+int fmbym_unet_layer_tensor(fmbym_unet* u, void* stream, int layer, int which, int n, float* dst) {
+    if (!u || layer < 0 || layer >= (int)u->layers.size() || which < 0 || which > 3 || !dst || n < 1 ||
+        n > u->max_batch)
+        return ufail(u, FMBYM_ERR_INVALID_ARG, "bad layer tensor request");
+    const Layer& l = u->layers[layer];
+    const long long cnt = (long long)n * l.H * l.W * l.cout;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (which == 0) e = cudaMemcpyAsync(dst, l.y, cnt * 4, cudaMemcpyDeviceToDevice, st);
+    else if (which == 2) e = cudaMemcpyAsync(dst, l.da, cnt * 4, cudaMemcpyDeviceToDevice, st);
+    else {
+        // bf16 -> float32 widening through the upsample-free path: copy raw and widen on the host side
+        std::vector<uint16_t> tmp(cnt);
+        e = cudaMemcpyAsync(tmp.data(), which == 1 ? (const void*)l.a : (const void*)l.dy, cnt * 2,
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        std::vector<float> wide(cnt);
+        for (long long i = 0; i < cnt; ++i) {
+            const uint32_t bits = (uint32_t)tmp[i] << 16;
+            memcpy(&wide[i], &bits, 4);
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(dst, wide.data(), cnt * 4, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return ucuda(u, e, "layer tensor");
+    return FMBYM_OK;
+}
+
+int fmbym_unet_load(fmbym_unet* u, void* stream, const float* params, const float* running) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (params) e = cudaMemcpyAsync(u->params, params, u->n_params * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && running)
+        e = cudaMemcpyAsync(u->running, running, u->n_running * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && params) {
+        cudaMemsetAsync(u->adam_m, 0, u->n_params * 4, st);
+        e = cudaMemsetAsync(u->adam_v, 0, u->n_params * 4, st);
+    }
+    if (e != cudaSuccess) return ucuda(u, e, "load");
+    return FMBYM_OK;
+}
+
+int fmbym_unet_store(fmbym_unet* u, void* stream, float* params, float* running, float* grads) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (params) e = cudaMemcpyAsync(params, u->params, u->n_params * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && running)
+        e = cudaMemcpyAsync(running, u->running, u->n_running * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && grads) e = cudaMemcpyAsync(grads, u->grads, u->n_params * 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return ucuda(u, e, "store");
+    return FMBYM_OK;
+}
+
+int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const float* g, int training,
+                       float* f_out, float* g_out, float* masks) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    u->err.clear();
+    if (n < 0 || n > u->max_batch) return ufail(u, FMBYM_ERR_WORKSPACE, "batch exceeds max_batch");
+    if (n == 0) return FMBYM_OK;
+    if (!f || !g) return ufail(u, FMBYM_ERR_INVALID_ARG, "f and g must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    const int L = u->levels;
+    Layer& first = u->layers[0];
+    first.in0 = (const bf16*)f;  // planes: read as float inside the conv kernel
+    first.in1 = (const bf16*)g;
+    // weights for this step
+    for (Layer& l : u->layers) {
+        const int nf = l.cout * 9 * l.cinp, nd = l.cin * 9 * l.coutp;
+        ++u->launches;
+        k_prep_weights<<<blocks(std::max(nf, nd)), kBlock, 0, st>>>(u->params + l.w_off, l.cout, l.cin, l.cinp,
+                                                                  l.coutp, l.wf, l.wd);
+    }
+    auto conv_bn = [&](Layer& l) -> cudaError_t {
+        const long long px = (long long)n * l.H * l.W;
+        const int ncta = (int)(px / (kTH * kTW));
+        cudaError_t r = conv_dispatch(u, l, n, false, st, l.y, nullptr, l.cout, 0, 0, training ? u->stats : nullptr);
+        if (r != cudaSuccess) return r;
+        ++u->launches;
+        if (training)
+            k_bn_finalize<<<l.cout, 256, 0, st>>>(u->stats, ncta, l.cout, (float)(kTH * kTW), u->running + l.rs_off,
+                                                  u->running + l.rs_off + l.cout, l.bn);
+        else
+            k_bn_eval<<<1, 128, 0, st>>>(u->running + l.rs_off, u->running + l.rs_off + l.cout, l.cout, l.bn);
+        ++u->launches;
+        k_bn_relu<<<blocks(px * l.cout / 8), kBlock, 0, st>>>(l.y, l.bn, u->params + l.g_off, u->params + l.b_off,
+                                                              l.a, px * l.cout / 8, l.cout);
+        return cudaGetLastError();
+    };
+    for (int i = 0; i < L && e == cudaSuccess; ++i) {
+        if (i > 0) {
+            const Layer& prev = u->layers[2 * i - 1];
+            const long long np = (long long)n * (prev.H / 2) * (prev.W / 2) * prev.cout;
+            ++u->launches;
+            k_maxpool<<<blocks(np), kBlock, 0, st>>>(prev.a, u->pooled[i], n, prev.H, prev.W, prev.cout);
+        }
+        e = conv_bn(u->layers[2 * i]);
+        if (e == cudaSuccess) e = conv_bn(u->layers[2 * i + 1]);
+    }
+    for (int j = 0; j < L - 1 && e == cudaSuccess; ++j) {
+        const int i = L - 2 - j;
+        const Layer& deep = (j == 0) ? u->layers[2 * L - 1] : u->layers[2 * L + 2 * (j - 1) + 1];
+        const long long nu = (long long)n * (deep.H * 2) * (deep.W * 2) * deep.cout;
+        ++u->launches;
+        k_upsample<<<blocks(nu), kBlock, 0, st>>>(deep.a, u->upped[i], n, deep.H, deep.W, deep.cout);
+        e = conv_bn(u->layers[2 * L + 2 * j]);
+        if (e == cudaSuccess) e = conv_bn(u->layers[2 * L + 2 * j + 1]);
+    }
+    if (e == cudaSuccess) {
+        const Layer& last = u->layers.back();
+        const long long npix = (long long)n * u->H * u->W;
+        ++u->launches;
+        switch (u->ch[0]) {
+            case 8: k_head<8><<<blocks(npix), kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, f_out, g_out, masks, npix, u->H * u->W); break;
+            case 16: k_head<16><<<blocks(npix), kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, f_out, g_out, masks, npix, u->H * u->W); break;
+            case 32: k_head<32><<<blocks(npix), kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, f_out, g_out, masks, npix, u->H * u->W); break;
+            default: k_head<64><<<blocks(npix), kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, f_out, g_out, masks, npix, u->H * u->W); break;
+        }
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return ucuda(u, e, "U-Net forward");
+    u->last_batch = training ? n : -1;
+    return FMBYM_OK;
+}
+
+int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, const float* g, const float* df_out,
+                        const float* dg_out) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    u->err.clear();
+    if (n != u->last_batch) return ufail(u, FMBYM_ERR_INVALID_ARG, "backward needs a training forward of the same batch");
+    if (!f || !g || !df_out || !dg_out) return ufail(u, FMBYM_ERR_INVALID_ARG, "NULL buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    const int L = u->levels, C0 = u->ch[0];
+    const long long npix = (long long)n * u->H * u->W;
+    // head
+    {
+        const Layer& last = u->layers.back();
+        const int nb = blocks(npix), width = 2 * C0 + 2;
+        ++u->launches;
+        switch (C0) {
+            case 8: k_head_bwd<8><<<nb, kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, df_out, dg_out, last.da, u->hpart, npix); break;
+            case 16: k_head_bwd<16><<<nb, kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, df_out, dg_out, last.da, u->hpart, npix); break;
+            case 32: k_head_bwd<32><<<nb, kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, df_out, dg_out, last.da, u->hpart, npix); break;
+            default: k_head_bwd<64><<<nb, kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, df_out, dg_out, last.da, u->hpart, npix); break;
+        }
+        ++u->launches;
+        k_sum_parts<<<1, 256, 0, st>>>(u->hpart, nb, width, u->grads + u->head_w);
+    }
+    // one layer: BN/ReLU adjoint, weight gradient, and (unless first) dgrad into out0/out1
+    auto layer_bwd = [&](Layer& l, float* out0, float* out1, int split, int acc0, int acc1) -> cudaError_t {
+        const long long px = (long long)n * l.H * l.W;
+        const int C = l.cout, pix_per_cta = 1024;
+        const int nparts = (int)((px + pix_per_cta - 1) / pix_per_cta);
+        u->launches += 3;
+        k_bn_bwd_reduce<<<nparts, 256, 0, st>>>(l.y, l.da, l.bn, u->params + l.g_off, u->params + l.b_off, px, C,
+                                                pix_per_cta, u->bnpart);
+        k_bn_bwd_finalize<<<1, 64, 0, st>>>(u->bnpart, nparts, C, 1.f / (float)px, u->grads + l.g_off,
+                                            u->grads + l.b_off, l.bsums);
+        k_bn_bwd_dy<<<blocks(px * C), kBlock, 0, st>>>(l.y, l.da, l.bn, u->params + l.g_off, u->params + l.b_off,
+                                                       l.bsums, l.dy, px * C, C);
+        // weight gradient
+        const int ntiles = (int)(px / (kTH * kTW));
+        const int gy = (C + 15) / 16, gz = (l.cin + 63) / 64;
+        const int nchunks = std::max(1, std::min(ntiles, 600 / (gy * gz)));
+        const int tpc = (ntiles + nchunks - 1) / nchunks;
+        const int used = (ntiles + tpc - 1) / tpc;
+        u->launches += 2;
+        k_wgrad<<<dim3(used, gy, gz), 256, kWgradSmem, st>>>(
+            l.dy, C, l.planes ? nullptr : l.in0, l.planes ? 0 : l.c0, l.in1, l.c1, l.planes ? f : nullptr,
+            l.planes ? g : nullptr, n, l.H, l.W, tpc, u->wpart);
+        const int total = C * 9 * l.cin;
+        k_wgrad_reduce<<<blocks(total), kBlock, 0, st>>>(u->wpart, used, C, l.cin, u->grads + l.w_off);
+        cudaError_t r = cudaGetLastError();
+        if (r != cudaSuccess || !out0) return r;
+        return conv_dispatch(u, l, n, true, st, out0, out1, split, acc0, acc1, nullptr);
+    };
+    // decoder, last layer first
+    for (int j = L - 2; j >= 0 && e == cudaSuccess; --j) {
+        const int i = L - 2 - j;
+        Layer& la = u->layers[2 * L + 2 * j];
+        Layer& lb = u->layers[2 * L + 2 * j + 1];
+        e = layer_bwd(lb, la.da, nullptr, lb.cin, 0, 0);
+        if (e != cudaSuccess) break;
+        Layer& skip = u->layers[2 * i + 1];
+        e = layer_bwd(la, u->dup[i], skip.da, u->ch[i + 1], 0, 0);
+        if (e != cudaSuccess) break;
+        Layer& deep = (j == 0) ? u->layers[2 * L - 1] : u->layers[2 * L + 2 * (j - 1) + 1];
+        const long long nl = (long long)n * deep.H * deep.W * deep.cout;
+        ++u->launches;
+        k_upsample_bwd<<<blocks(nl), kBlock, 0, st>>>(u->dup[i], deep.da, n, deep.H, deep.W, deep.cout);
+        e = cudaGetLastError();
+    }
+    // encoder, deepest first
+    for (int i = L - 1; i >= 0 && e == cudaSuccess; --i) {
+        Layer& la = u->layers[2 * i];
+        Layer& lb = u->layers[2 * i + 1];
+        e = layer_bwd(lb, la.da, nullptr, lb.cin, 0, 0);
+        if (e != cudaSuccess) break;
+        if (i == 0) {
+            e = layer_bwd(la, nullptr, nullptr, 0, 0, 0);
+            break;
+        }
+        e = layer_bwd(la, u->dpool[i], nullptr, la.cin, 0, 0);
+        if (e != cudaSuccess) break;
+        Layer& prev = u->layers[2 * i - 1];
+        const long long np = (long long)n * (prev.H / 2) * (prev.W / 2) * prev.cout;
+        ++u->launches;
+        k_maxpool_bwd<<<blocks(np), kBlock, 0, st>>>(prev.a, u->dpool[i], prev.da, n, prev.H, prev.W, prev.cout);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return ucuda(u, e, "U-Net backward");
+    return FMBYM_OK;
+}
+
+int fmbym_unet_adam(fmbym_unet* u, void* stream, float lr, float beta1, float beta2, float eps, int step) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    if (step < 1) return ufail(u, FMBYM_ERR_INVALID_ARG, "step counts from 1");
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    ++u->launches;
+    k_adam<<<blocks(u->n_params), kBlock, 0, (cudaStream_t)stream>>>(u->params, u->grads, u->adam_m, u->adam_v,
+                                                                    u->n_params, lr, beta1, beta2, eps, c1, c2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ucuda(u, e, "Adam");
+    return FMBYM_OK;
+}
+
+}  // extern "C"
