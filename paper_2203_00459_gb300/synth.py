@@ -144,3 +144,77 @@ def make_batch(name, pairs=None, start=0, spec=None):
         f[i], g[i] = make_pair(n, spec["n_points"], spec["n_walls"], th, tx, ty, seed, idx)
         pose[i] = (th, tx, ty)
     return f, g, pose
+
+
+# ---------------------------------------------------------------------------------------------
+# trajectories with moving scatterers (the learned-mask workload, 256^2)
+# ---------------------------------------------------------------------------------------------
+
+def make_trajectory(n_frames, seed, index, n=256, n_static=150, n_walls=20, moving_frac=0.1,
+                    theta_deg=5.0, t_px=8.0, speed_px=6.0, moving_amp=(20.0, 60.0), noise_sd=0.3,
+                    pixel_speckle=False):
+    """Frames of one trajectory and the ego step between consecutive frames.
+
+    A static scene (scatterers and walls, as in make_pair) plus moving_frac * n_static moving
+    scatterers with amplitude U(moving_amp) and their own constant velocity (uniform in a disk of
+    radius speed_px per frame).  Frame k+1 sees every element of frame k moved by the ego step
+    (theta_k, t_k) ~ (U(+-theta_deg), U(+-t_px)^2) about the image centre (Eq. 1), and the moving
+    scatterers additionally displaced by their velocity.  Each frame gets fresh |N(0, noise_sd)|
+    noise and, with pixel_speckle, a fresh per-pixel Exp(1) multiplicative speckle (the image-level
+    speckle of the recipe, independent in every frame).  Returns (frames float32 [n_frames, N, N],
+    steps float64 [n_frames - 1, 3])."""
+    rng = _rng(seed, index)
+    xs, ys, amp = scene(rng, n, n_static, n_walls)
+    m = max(1, int(round(moving_frac * n_static)))
+    mx = rng.random(m) * n
+    my = rng.random(m) * n
+    ma = (moving_amp[0] + (moving_amp[1] - moving_amp[0]) * rng.random(m)) * _exp1(rng, m)
+    sp = speed_px * np.sqrt(rng.random(m))
+    ang = 2.0 * np.pi * rng.random(m)
+    vx, vy = sp * np.cos(ang), sp * np.sin(ang)
+    frames = np.empty((n_frames, n, n), np.float32)
+    steps = np.empty((n_frames - 1, 3), np.float64)
+    for k in range(n_frames):
+        img = render(n, np.concatenate([xs, mx]), np.concatenate([ys, my]), np.concatenate([amp, ma]))
+        if pixel_speckle:
+            img = img * _exp1(rng, (n, n))
+        frames[k] = (img + _abs_normal(rng, (n, n), noise_sd)).astype(np.float32)
+        if k == n_frames - 1:
+            break
+        th = math.radians(theta_deg) * (2.0 * rng.random() - 1.0)
+        t = t_px * (2.0 * rng.random(2) - 1.0)
+        steps[k] = (th, t[0], t[1])
+        xs, ys = move(n, xs, ys, th, t[0], t[1])
+        mx, my = move(n, mx + vx, my + vy, th, t[0], t[1])
+        # velocities turn with the sensor frame
+        c, s = math.cos(th), math.sin(th)
+        vx, vy = c * vx - s * vy, s * vx + c * vy
+    return frames, steps
+
+
+def trajectory_pairs(n_traj, n_frames, seed, **kw):
+    """Consecutive-frame pairs of n_traj trajectories: (f, g, pose) with pose the ego step."""
+    F, G, P = [], [], []
+    for j in range(n_traj):
+        fr, st = make_trajectory(n_frames, seed, j, **kw)
+        F.append(fr[:-1])
+        G.append(fr[1:])
+        P.append(st)
+    return np.concatenate(F), np.concatenate(G), np.concatenate(P)
+
+
+def _trajectory_job(args):
+    n_frames, seed, index, kw = args
+    fr, st = make_trajectory(n_frames, seed, index, **kw)
+    return fr[:-1], fr[1:], st
+
+
+def trajectory_pairs_parallel(n_traj, n_frames, seed, processes=None, **kw):
+    """trajectory_pairs over a spawn process pool (same pairs, same order)."""
+    import multiprocessing as mp
+    import os
+    procs = processes or min(n_traj, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        parts = pool.map(_trajectory_job, [(n_frames, seed, j, kw) for j in range(n_traj)])
+    return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+            np.concatenate([p[2] for p in parts]))

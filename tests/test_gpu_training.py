@@ -1,0 +1,56 @@
+"""What the learned mask gains (Sec. III-D, Tab. IIIb in spirit): the masking network trained end to end
+through the decoupled search on synthetic trajectories (moving scatterers, fresh per-frame speckle)
+lowers the translation error on held-out pairs, judged against ground truth and against the
+unmasked search -- both the GPU search and the FP64 oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_errors(args):
+    import oracle as O
+    f, g, gt = args
+    r = O.pose(f, g, O.make_cfg(256, 400, 128))
+    return abs(r["theta"] - gt[0]), abs(r["tx"] - gt[1]), abs(r["ty"] - gt[2]), r["theta"], r["tx"], r["ty"]
+
+
+def test_trained_mask_lowers_translation_error():
+    from paper_2203_00459_gb300 import build
+    build.build()
+    from paper_2203_00459_gb300 import train
+    F, G, P = train.trajectory_data(64, 33, 20220304, parallel=True)    # 2048 training pairs
+    Fe, Ge, Pe = train.trajectory_data(8, 17, 20229999, parallel=True)  # 128 held-out pairs
+    ms = train.MaskedSearch(batch=64, seed=1)
+    Ft, Gt = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
+    Pt = torch.from_numpy(P.astype(np.float32)).cuda()
+    Fe_t, Ge_t = torch.from_numpy(Fe).cuda(), torch.from_numpy(Ge).cuda()
+    plain = ms.poses(Fe_t, Ge_t, masked=False).cpu().numpy()
+    rng = np.random.default_rng(0)
+    nb = F.shape[0] // 64
+    for step in range(240):
+        if step % nb == 0:
+            perm = torch.from_numpy(rng.permutation(F.shape[0])).cuda()
+        idx = perm[(step % nb) * 64:(step % nb + 1) * 64]
+        ms.train_step(Ft[idx].contiguous(), Gt[idx].contiguous(), Pt[idx].contiguous(), lr=1e-3)
+    masked = ms.poses(Fe_t, Ge_t, masked=True).cpu().numpy()
+    torch.cuda.synchronize()
+    ms.close()
+    e_plain = train.pose_errors(plain, Pe)
+    e_mask = train.pose_errors(masked, Pe)
+    # the FP64 oracle's unmasked search on the same held-out pairs
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(16) as pool:
+        orc = np.array(pool.map(_oracle_errors, [(Fe[i].astype(np.float64), Ge[i].astype(np.float64), Pe[i])
+                                                 for i in range(len(Pe))]))
+    e_orc = orc[:, :3].mean(axis=0)
+    # parity of the unmasked GPU search with the oracle on this workload
+    assert np.max(np.abs(plain[:, 0] - orc[:, 3])) <= 1e-4
+    assert np.max(np.abs(plain[:, 1:] - orc[:, 4:])) <= 1e-3
+    t_plain, t_mask, t_orc = e_plain[1:].sum(), e_mask[1:].sum(), e_orc[1:].sum()
+    print("held-out mean |error| (theta rad, tx px, ty px): unmasked GPU", e_plain, "FP64 oracle", e_orc,
+          "trained mask", e_mask)
+    assert t_mask <= 0.9 * t_plain and t_mask <= 0.9 * t_orc, (e_mask, e_plain, e_orc)
+    assert e_mask[0] <= 1.1 * e_plain[0]
