@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwd", "fwdbwd"])
-    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "mixed", "masked256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     return ap.parse_args()
@@ -217,10 +217,127 @@ def run_reference(args, spec, rank):
 # GPU arm
 # ---------------------------------------------------------------------------------------------
 
+def run_mixed(args):
+    """The uneven batch: 512 pairs (256 at 128^2, 179 at 256^2, 77 at 512^2, shuffled) in one call;
+    a step is mask inference (one U-Net per resolution, evaluation statistics) then the search
+    forward, the L1 pose loss and the search adjoint over all pairs (graph replay, concurrent
+    size groups)."""
+    import numpy as np
+    import torch
+    from paper_2203_00459_gb300 import build, synth
+    build.build()
+    from paper_2203_00459_gb300 import _lib, masknet, train
+    from paper_2203_00459_gb300.search import PoseSearch, size_cfg
+    names = ["single128", "batch256", "batch512"]
+    counts = [256, 179, 77]
+    cfgs = [size_cfg(128, 128, 64), size_cfg(256, 400, 128), size_cfg(512, 400, 256)]
+    levels = [(8, 16, 32), (8, 16, 32, 64), (8, 16, 32, 64)]
+    order = np.concatenate([np.full(c, s) for s, c in enumerate(counts)])
+    np.random.default_rng(5).shuffle(order)
+    per = [np.flatnonzero(order == s) for s in range(3)]
+    sizes = [cfgs[s]["n"] ** 2 for s in range(3)]
+    offs = np.zeros(len(order), np.int64)
+    # pairs of one size are stored contiguously (the U-Net works per size); the search sees the
+    # shuffled order through offsets
+    base = 0
+    for s in range(3):
+        offs[per[s]] = base + np.arange(len(per[s])) * sizes[s]
+        base += len(per[s]) * sizes[s]
+    F = torch.empty(base, device="cuda")
+    G = torch.empty(base, device="cuda")
+    FM = torch.empty(base, device="cuda")
+    GM = torch.empty(base, device="cuda")
+    gt = torch.empty((len(order), 3), device="cuda")
+    nets = []
+    start = 0
+    for s in range(3):
+        n = cfgs[s]["n"]
+        f, g, pz = synth.make_batch(names[s], pairs=len(per[s]), spec=dict(synth.WORKLOADS[names[s]], pairs=len(per[s])))
+        F[start:start + f.size] = torch.from_numpy(f.ravel()).cuda()
+        G[start:start + g.size] = torch.from_numpy(g.ravel()).cuda()
+        gt[torch.from_numpy(per[s]).cuda()] = torch.from_numpy(pz.astype(np.float32)).cuda()
+        net = masknet.MaskNet(levels[s], n, n, max_batch=len(per[s]))
+        net.load(train.init_params(levels[s], seed=1 + s).cuda())
+        nets.append((net, start, len(per[s]), n))
+        start += f.size
+    search = PoseSearch(cfgs, max_pairs=len(order), flags=_lib.FLAG_GRAPH)
+    pose = torch.empty((len(order), 3), device="cuda")
+    dpose = torch.empty_like(pose)
+    loss = torch.empty(1, device="cuda")
+    dF, dG = torch.empty_like(F), torch.empty_like(G)
+    L = _lib.lib()
+    si = np.ascontiguousarray(order.astype(np.int32))
+
+    def step():
+        for net, st, cnt, n in nets:
+            view = lambda t: t[st:st + cnt * n * n].view(cnt, n, n)
+            net.forward(view(F), view(G), training=False, f_out=view(FM), g_out=view(GM))
+        search.pose(FM, GM, size_idx=si, offsets=offs, out=pose)
+        search.pose_loss(pose, gt, kind=1, loss=loss, dpose=dpose)
+        search.pose_backward(FM, GM, dpose, size_idx=si, offsets=offs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = L.fmbym_launch_count(search.handle) + sum(net.launch_count() for net, *_ in nets)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record()
+        step()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    launches = L.fmbym_launch_count(search.handle) + sum(net.launch_count() for net, *_ in nets) - l0
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    line = {"metric": "scan-pairs/s, uneven batch with mask inference, search fwd+bwd", "value": len(order) / (ms * 1e-3),
+            "unit": "scan-pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 search, bf16 mask",
+            "data": "synthetic", "gpu_launches": int(launches),
+            "config": {"workload": "mixed", "pairs": {"128": counts[0], "256": counts[1], "512": counts[2]},
+                       "mask_levels": {"128": 3, "256": 4, "512": 4}, "l2": "flushed between timed steps"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_masked256(args):
+    """The learned-mask training step at 256^2, batch 64: U-Net forward, masked search, L1 pose loss,
+    search adjoint, U-Net adjoint and Adam."""
+    import numpy as np
+    import torch
+    from paper_2203_00459_gb300 import build
+    build.build()
+    from paper_2203_00459_gb300 import train
+    F, G, P = train.trajectory_data(2, 33, 20220304)
+    ms = train.MaskedSearch(batch=64)
+    Ft, Gt = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
+    Pt = torch.from_numpy(P.astype(np.float32)).cuda()
+    for _ in range(args.warmup):
+        ms.train_step(Ft, Gt, Pt)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record()
+        ms.train_step(Ft, Gt, Pt)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    ms_step = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    line = {"metric": "scan-pairs/s, learned-mask training step (U-Net fwd+bwd, search fwd+bwd, Adam)",
+            "value": 64 / (ms_step * 1e-3), "unit": "scan-pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 mask, f32 search", "data": "synthetic",
+            "config": {"workload": "masked256", "n": 256, "batch": 64, "mask_channels": [8, 16, 32, 64]}}
+    ms.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     from paper_2203_00459_gb300 import synth
-    spec = dict(synth.WORKLOADS[args.workload])
+    if args.workload == "mixed" and args.impl == "ours":
+        return run_mixed(args)
+    if args.workload == "masked256" and args.impl == "ours":
+        return run_masked256(args)
+    spec = dict(synth.WORKLOADS[args.workload if args.workload in synth.WORKLOADS else "batch256"])
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -341,7 +458,7 @@ def main():
 
     # ---- dominant kernel roofline ----
     chunks = (nr + 15) // 16
-    model = kernel_model(n, 2 * n, nt, nr, chunks)
+    model = kernel_model(n, 3 * n // 2, nt, nr, chunks)   # zero padding to P = 1.5 N
     total_ms = sum(v[0] for v in kernels.values())
     dom = max(kernels, key=lambda k: kernels[k][0]) if kernels else None
     peaks, peak_src = measured_peaks()
@@ -447,7 +564,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "mode": args.mode,
                 "config": {"workload": args.workload, "n": n, "n_theta": nt, "n_r": nr, "pairs_per_gpu": B,
-                           "pad": "zero to 2N", "l2": "flushed (256 MB write) between timed steps"},
+                           "pad": "zero to 1.5N (same lags as 2N)", "l2": "flushed (256 MB write) between timed steps"},
                 "roofline": roof, "kernel_shares": shares, "ms_per_step_direct_launch": ms_traced,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, **extra}

@@ -157,7 +157,7 @@ cudaError_t build_plan(HostPlan& hp) {
     const fmbym_size_cfg& c = hp.cfg;
     DevPlan& d = hp.dev;
     d.n = c.n;
-    d.p = c.pad_mode == 1 ? c.n : 2 * c.n;
+    d.p = c.pad_mode == 1 ? c.n : 3 * c.n / 2;  // zero pad to 1.5 N: lags |s| <= N/2 never alias
     d.nt = c.n_theta;
     d.nr = c.n_r;
     d.window = c.window;

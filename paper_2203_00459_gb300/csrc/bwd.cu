@@ -130,15 +130,15 @@ template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long* __restrict__ tab,
                                                      const float* __restrict__ cxy, const float* __restrict__ bsc,
                                                      const float* __restrict__ dpose, float2* __restrict__ b1, int B) {
-    constexpr int T = FftPlan<P>::T, FPC = kThreads / T, SL = spad(P), W = P / 2;
+    constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
     const long long pr = tab[3 * q + 2];
     const float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
     const float* r = bsc + (size_t)q * 16;
     const float* c = cxy + (size_t)q * N * N;
-    for (int idx = threadIdx.x; idx < FPC * P; idx += kThreads) {
-        const int k = idx / P, x = idx % P, j = (x + N / 2) & (P - 1), i = i0 + 2 * k;
+    for (int idx = threadIdx.x; idx < FPC * P; idx += TPB) {
+        const int k = idx / P, x = idx % P, j = (x + N / 2) % P, i = i0 + 2 * k;
         float2 v = make_float2(0.f, 0.f);
         if (j < N) {
             v.x = dcxy(p, r, c[(size_t)i * N + j], i, j, N, dtx, dty);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long*
     __syncthreads();
     fft<P, -1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
     float2* out = b1 + (size_t)q * N * W;
-    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
         const int k = idx / W, u = idx % W, row = i0 + 2 * k;
         const float2* Z = sm + k * SL;
         float2 xa, xb;
@@ -179,8 +179,8 @@ __device__ __forceinline__ void split0(float2 z, float2 zm, float2& a, float2& b
 template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_b_cols(DevPlan p, const float2* __restrict__ b1,
                                                      const float2* __restrict__ s2, float2* __restrict__ b2, int B) {
-    constexpr int T = FftPlan<P>::T, C = kThreads / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
-    constexpr int PER = P * C / kThreads;
+    constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), C = TPB / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
+    constexpr int PER = P * C / TPB;
     extern __shared__ float2 sm[];
     float2* tD = sm;
     float2* tF = sm + TILE;
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(kThreads) k_b_cols(DevPlan p, const float2* __
     const float2* inD = b1 + (size_t)q * N * W;
     const float2* inF = s2 + (size_t)q * N * W;
     const float2* inG = s2 + (size_t)(B + q) * N * W;
-    for (int idx = threadIdx.x; idx < P * C; idx += kThreads) {
-        const int v = idx / C, c = idx % C, i = (v + N / 2) & (P - 1);
+    for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
+        const int v = idx / C, c = idx % C, i = (v + N / 2) % P;
         const float2 zero = make_float2(0.f, 0.f);
         tD[spad(v) * ES + c] = i < N ? inD[(size_t)i * W + u0 + c] : zero;
         tF[spad(v) * ES + c] = v < N ? inF[(size_t)v * W + u0 + c] : zero;
@@ -204,10 +204,10 @@ __global__ void __launch_bounds__(kThreads) k_b_cols(DevPlan p, const float2* __
     float2 q1[PER], q2[PER];
 #pragma unroll
     for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * kThreads, v = idx / C, cc = idx % C;
+        const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
         const float2 D = tD[spad(v) * ES + cc], F = tF[spad(v) * ES + cc], G = tG[spad(v) * ES + cc];
         if (u0 + cc == 0) {
-            const int vm = (P - v) & (P - 1);
+            const int vm = (v == 0 ? 0 : P - v);
             float2 ad, bd, af, bf, ag, bg;
             split0(D, tD[spad(vm) * ES + cc], ad, bd);
             split0(F, tF[spad(vm) * ES + cc], af, bf);
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_b_cols(DevPlan p, const float2* __
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * kThreads, v = idx / C, cc = idx % C;
+        const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
         tG[spad(v) * ES + cc] = q1[m];
         tF[spad(v) * ES + cc] = q2[m];
     }
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_b_cols(DevPlan p, const float2* __
     fft<P, +1>(tF + c, ES, j, true, p.tw_p);
     float2* o1 = b2 + (size_t)q * N * W;
     float2* o2 = b2 + (size_t)(B + q) * N * W;
-    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < N * C; idx += TPB) {
         const int y = idx / C, cc = idx % C;
         o1[(size_t)y * W + u0 + cc] = tG[spad(y) * ES + cc];
         o2[(size_t)y * W + u0 + cc] = tF[spad(y) * ES + cc];
@@ -246,11 +246,11 @@ template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* __restrict__ tab,
                                                     const float2* __restrict__ b2, float* __restrict__ gfr,
                                                     float* __restrict__ dg, int B) {
-    constexpr int T = FftPlan<P>::T, FPC = kThreads / T, SL = spad(P), W = P / 2;
+    constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, i0 = blockIdx.x * FPC * 2;
     const float2* in = b2 + (size_t)(s * B + q) * N * W;
-    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
         const int k = idx / W, u = idx % W;
         const float2 a = in[(size_t)(i0 + 2 * k) * W + u], b = in[(size_t)(i0 + 2 * k + 1) * W + u];
         float2* Z = sm + k * SL;
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
     fft<P, +1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
     const float scale = 1.f / ((float)P * (float)P);
     float* out = s == 0 ? gfr + (size_t)q * N * N : dg + tab[3 * q];
-    for (int idx = threadIdx.x; idx < FPC * N; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < FPC * N; idx += TPB) {
         const int k = idx / N, x = idx % N;
         const float2 z = sm[k * SL + spad(x)];
         out[(size_t)(i0 + 2 * k) * N + x] = z.x * scale;
@@ -694,9 +694,9 @@ cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, in
 // launchers
 // ---------------------------------------------------------------------------------------------
 
-template <int N> constexpr size_t b_smem_rows() { return (size_t)(kThreads / FftPlan<N>::T) * spad(N) * sizeof(float2); }
+template <int L> constexpr size_t b_smem_rows() { return (size_t)(tpb_for(L) / FftPlan<L>::T) * spad(L) * sizeof(float2); }
 template <int P> constexpr size_t b_smem_cols() {
-    return 3 * (size_t)spad(P) * (kThreads / FftPlan<P>::T + 1) * sizeof(float2);
+    return 3 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T + 1) * sizeof(float2);
 }
 template <int N> constexpr size_t b_smem_s1cols() {
     return ((size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) + spad(N)) * sizeof(float2);
@@ -717,19 +717,18 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
                             const float* g, const float* dpose, float* df, float* dg, cudaStream_t st) {
     cudaError_t e = launch_forward(p, w, B, tab, f, g, w.bpose, nullptr, nullptr, st);
     if (e != cudaSuccess) return e;
-    constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T;
-    const int nblk = (N / 2) / (kThreads / T2);
+    constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T, TB2 = tpb_for(P);
+    const int nblk = (N / 2) / (TB2 / T2);
     w.tr->before(K_B_SXY, st);
     k_b_stats<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, w.st, nblk, w.sx, w.bpose, dpose, w.gxx,
                                                           w.cnt, w.bsc);
     w.tr->before(K_B_ROWS, st);
-    k_b_rows<N, P><<<dim3((N / 2) / (kThreads / T2), B), kThreads, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.bsc,
-                                                                                             dpose, w.b1, B);
+    k_b_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.bsc, dpose, w.b1,
+                                                                                   B);
     w.tr->before(K_B_COLS, st);
-    k_b_cols<N, P><<<dim3((P / 2) / (kThreads / T2), B), kThreads, b_smem_cols<P>(), st>>>(p, w.b1, w.s2, w.b2, B);
+    k_b_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, b_smem_cols<P>(), st>>>(p, w.b1, w.s2, w.b2, B);
     w.tr->before(K_B_C2R, st);
-    k_b_c2r<N, P><<<dim3((N / 2) / (kThreads / T2), B, 2), kThreads, b_smem_rows<P>(), st>>>(p, tab, w.b2, w.gfr,
-                                                                                               dg, B);
+    k_b_c2r<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st>>>(p, tab, w.b2, w.gfr, dg, B);
     w.tr->before(K_B_ROT, st);
     k_b_rot<N><<<dim3(N * N / kThreads, B), kThreads, 0, st>>>(p, tab, f, w.th, w.gfr, dpose, df, w.gpart, w.cnt,
                                                               w.bsc);
@@ -753,12 +752,12 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
 cudaError_t launch_backward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                             const float* g, const float* dpose, float* df, float* dg, cudaStream_t st) {
     if (B <= 0) return cudaSuccess;
-    if (p.n == 128) return p.p == 256 ? launch_b<128, 256>(p, w, B, tab, f, g, dpose, df, dg, st)
+    if (p.n == 128) return p.p == 192 ? launch_b<128, 192>(p, w, B, tab, f, g, dpose, df, dg, st)
                                       : launch_b<128, 128>(p, w, B, tab, f, g, dpose, df, dg, st);
-    if (p.n == 256) return p.p == 512 ? launch_b<256, 512>(p, w, B, tab, f, g, dpose, df, dg, st)
+    if (p.n == 256) return p.p == 384 ? launch_b<256, 384>(p, w, B, tab, f, g, dpose, df, dg, st)
                                       : launch_b<256, 256>(p, w, B, tab, f, g, dpose, df, dg, st);
-    return p.p == 1024 ? launch_b<512, 1024>(p, w, B, tab, f, g, dpose, df, dg, st)
-                       : launch_b<512, 512>(p, w, B, tab, f, g, dpose, df, dg, st);
+    return p.p == 768 ? launch_b<512, 768>(p, w, B, tab, f, g, dpose, df, dg, st)
+                      : launch_b<512, 512>(p, w, B, tab, f, g, dpose, df, dg, st);
 }
 
 template <typename K>
@@ -778,11 +777,11 @@ static cudaError_t prepare_b() {
 
 cudaError_t prepare_backward_kernels() {
     cudaError_t e;
-    if ((e = prepare_b<128, 256>()) != cudaSuccess) return e;
+    if ((e = prepare_b<128, 192>()) != cudaSuccess) return e;
     if ((e = prepare_b<128, 128>()) != cudaSuccess) return e;
-    if ((e = prepare_b<256, 512>()) != cudaSuccess) return e;
+    if ((e = prepare_b<256, 384>()) != cudaSuccess) return e;
     if ((e = prepare_b<256, 256>()) != cudaSuccess) return e;
-    if ((e = prepare_b<512, 1024>()) != cudaSuccess) return e;
+    if ((e = prepare_b<512, 768>()) != cudaSuccess) return e;
     if ((e = prepare_b<512, 512>()) != cudaSuccess) return e;
     if ((e = allow(k_b_angle<128>, b_smem_angle<128>())) != cudaSuccess) return e;
     if ((e = allow(k_b_angle<256>, b_smem_angle<256>())) != cudaSuccess) return e;

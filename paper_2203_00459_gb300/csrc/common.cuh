@@ -45,7 +45,7 @@ constexpr int kHeavyRow = 32;
 
 inline int angle_chunks(const DevPlan& p) { return (p.nr + kAngleRadii - 1) / kAngleRadii; }
 inline int fft_threads(int L) { return L / 16 == 25 ? 25 : L / 16; }
-inline int c2r_blocks(const DevPlan& p) { return (p.n / 2) / (kThreads / fft_threads(p.p)); }
+inline int c2r_blocks(const DevPlan& p) { return (p.n / 2) / (tpb_for(p.p) / fft_threads(p.p)); }
 
 // Kernel kinds, for the launch tracer.
 enum Kind {

@@ -115,6 +115,17 @@ template <int S> __device__ __forceinline__ void dft16(float2* v) {
     for (int i = 0; i < 16; ++i) v[i] = y[i];
 }
 
+// 3-point DFT: y1 = x0 - (x1 + x2)/2 + S i (sqrt3/2)(x1 - x2), y2 the conjugate combination
+template <int S> __device__ __forceinline__ void dft3(float2* v) {
+    constexpr float h = 0.86602540378443864676f;  // sqrt(3)/2
+    const float2 t = c_add(v[1], v[2]);
+    const float2 d = c_rot<S>(c_sub(v[1], v[2]));
+    const float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    v[0] = c_add(v[0], t);
+    v[1] = make_float2(m.x + h * d.x, m.y + h * d.y);
+    v[2] = make_float2(m.x - h * d.x, m.y - h * d.y);
+}
+
 // 5-point DFT from cos/sin of 2 pi/5 and 4 pi/5
 template <int S> __device__ __forceinline__ void dft5(float2* v) {
     constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
@@ -139,6 +150,7 @@ template <int S> __device__ __forceinline__ void dft5(float2* v) {
 
 template <int R, int S> __device__ __forceinline__ void dft(float2* v) {
     if constexpr (R == 2) dft2<S>(v);
+    else if constexpr (R == 3) dft3<S>(v);
     else if constexpr (R == 4) dft4<S>(v);
     else if constexpr (R == 5) dft5<S>(v);
     else if constexpr (R == 8) dft8<S>(v);
@@ -211,6 +223,9 @@ __device__ __forceinline__ void fft_passes(float2* buf, int es, int j, bool acti
 // Radix plans: every length uses radix 16 first; T = threads per sequence.
 template <int L> struct FftPlan;
 template <> struct FftPlan<128> { static constexpr int T = 8; };
+template <> struct FftPlan<192> { static constexpr int T = 12; };
+template <> struct FftPlan<384> { static constexpr int T = 24; };
+template <> struct FftPlan<768> { static constexpr int T = 48; };
 template <> struct FftPlan<256> { static constexpr int T = 16; };
 template <> struct FftPlan<400> { static constexpr int T = 25; };
 template <> struct FftPlan<512> { static constexpr int T = 32; };
@@ -226,6 +241,13 @@ __device__ __forceinline__ void fft(float2* buf, int es, int j, bool active, con
     else if constexpr (L == 400) fft_passes<L, T, S, 1, 16, 5, 5>(buf, es, j, active, tw);
     else if constexpr (L == 512) fft_passes<L, T, S, 1, 16, 16, 2>(buf, es, j, active, tw);
     else if constexpr (L == 1024) fft_passes<L, T, S, 1, 16, 16, 4>(buf, es, j, active, tw);
+    else if constexpr (L == 192) fft_passes<L, T, S, 1, 16, 4, 3>(buf, es, j, active, tw);
+    else if constexpr (L == 384) fft_passes<L, T, S, 1, 16, 8, 3>(buf, es, j, active, tw);
+    else if constexpr (L == 768) fft_passes<L, T, S, 1, 16, 16, 3>(buf, es, j, active, tw);
 }
+
+// Threads of a CTA that runs several length-L sequences side by side: a multiple of both the
+// group size and 32 (192 for the 3 * 2^k lengths, 256 otherwise).
+__host__ __device__ constexpr int tpb_for(int L) { return (L % 3 == 0) ? 192 : 256; }
 
 }  // namespace fmbym

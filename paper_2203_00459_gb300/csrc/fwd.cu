@@ -221,20 +221,20 @@ template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
                                                       const float* __restrict__ f, const float* __restrict__ g,
                                                       const float* __restrict__ th, float2* __restrict__ s2, int B) {
-    constexpr int T = FftPlan<P>::T, FPC = kThreads / T, SL = spad(P), W = P / 2;
+    constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
     const float* __restrict__ src = (s ? g : f) + tab[3 * q];
     if (s == 0) {
         const float* t = th + 8 * q;
         const float ch = t[1], cl = t[2], sh = t[3], sl = t[4];
-        for (int idx = threadIdx.x; idx < FPC * 2 * N; idx += kThreads) {
+        for (int idx = threadIdx.x; idx < FPC * 2 * N; idx += TPB) {
             const int rr = idx / N, x = idx % N;
             const float v = rotated_sample(src, N, x, r0 + rr, ch, cl, sh, sl);
             reinterpret_cast<float*>(sm + (rr >> 1) * SL + spad(x))[rr & 1] = v;
         }
     } else {
-        for (int idx = threadIdx.x; idx < FPC * 2 * (N / 4); idx += kThreads) {
+        for (int idx = threadIdx.x; idx < FPC * 2 * (N / 4); idx += TPB) {
             const int rr = idx / (N / 4), x4 = (idx % (N / 4)) * 4;
             const float4 v = __ldg(reinterpret_cast<const float4*>(src + (size_t)(r0 + rr) * N + x4));
             float* base = reinterpret_cast<float*>(sm + (rr >> 1) * SL) + (rr & 1);
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long
         }
     }
     if constexpr (P > N) {
-        for (int idx = threadIdx.x; idx < FPC * (P - N); idx += kThreads) {
+        for (int idx = threadIdx.x; idx < FPC * (P - N); idx += TPB) {
             const int k = idx / (P - N), x = N + idx % (P - N);
             sm[k * SL + spad(x)] = make_float2(0.f, 0.f);
         }
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long
     __syncthreads();
     fft<P, -1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
     float2* out = s2 + (size_t)(s * B + q) * N * W;
-    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
         const int k = idx / W, u = idx % W, row = r0 + 2 * k;
         const float2* Z = sm + k * SL;
         float2 xa, xb;
@@ -277,15 +277,15 @@ __global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long
 template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
                                                       float2* __restrict__ s3, int B) {
-    constexpr int T = FftPlan<P>::T, C = kThreads / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
-    constexpr int PER = P * C / kThreads;
+    constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), C = TPB / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
+    constexpr int PER = P * C / TPB;
     extern __shared__ float2 sm[];
     float2* tf = sm;
     float2* tg = sm + TILE;
     const int q = blockIdx.y, u0 = blockIdx.x * C;
     const float2* inf = s2 + (size_t)q * N * W;
     const float2* ing = s2 + (size_t)(B + q) * N * W;
-    for (int idx = threadIdx.x; idx < P * C; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
         const int v = idx / C, c = idx % C;
         float2 a = make_float2(0.f, 0.f), b = a;
         if (v < N) {
@@ -302,10 +302,10 @@ __global__ void __launch_bounds__(kThreads) k_s2_cols(DevPlan p, const float2* _
     float2 qv[PER];
 #pragma unroll
     for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * kThreads, v = idx / C, cc = idx % C;
+        const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
         const float2 F = tf[spad(v) * ES + cc], G = tg[spad(v) * ES + cc];
         if (u0 + cc == 0) {
-            const int vm = (P - v) & (P - 1);
+            const int vm = (v == 0 ? 0 : P - v);
             const float2 Fm = tf[spad(vm) * ES + cc], Gm = tg[spad(vm) * ES + cc];
             const float2 af = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
             const float2 bf = make_float2(0.5f * (F.y + Fm.y), -0.5f * (F.x - Fm.x));
@@ -320,14 +320,14 @@ __global__ void __launch_bounds__(kThreads) k_s2_cols(DevPlan p, const float2* _
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * kThreads, v = idx / C, cc = idx % C;
+        const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
         tg[spad(v) * ES + cc] = qv[m];
     }
     __syncthreads();
     fft<P, +1>(tg + c, ES, j, true, p.tw_p);
     float2* out = s3 + (size_t)q * N * W;
-    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
-        const int i = idx / C, cc = idx % C, v = (i - N / 2 + P) & (P - 1);
+    for (int idx = threadIdx.x; idx < N * C; idx += TPB) {
+        const int i = idx / C, cc = idx % C, v = (i - N / 2 + P) % P;
         out[(size_t)i * W + u0 + cc] = tg[spad(v) * ES + cc];
     }
 }
@@ -339,12 +339,12 @@ template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long* __restrict__ tab,
                                                      const float2* __restrict__ s3, float* __restrict__ cxy_ws,
                                                      float* __restrict__ cxy_out, float* __restrict__ st, int B) {
-    constexpr int T = FftPlan<P>::T, FPC = kThreads / T, SL = spad(P), W = P / 2;
+    constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     __shared__ float red[32];
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
     const float2* in = s3 + (size_t)q * N * W;
-    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
         const int k = idx / W, u = idx % W;
         const float2 a = in[(size_t)(i0 + 2 * k) * W + u], b = in[(size_t)(i0 + 2 * k + 1) * W + u];
         float2* Z = sm + k * SL;
@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long*
     const float scale = 1.f / ((float)P * (float)P);
     float* out = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N;
     float lsum = 0.f, lmax = -FLT_MAX;
-    for (int idx = threadIdx.x; idx < FPC * N; idx += kThreads) {
-        const int k = idx / N, jj = idx % N, nn = (jj - N / 2 + P) & (P - 1);
+    for (int idx = threadIdx.x; idx < FPC * N; idx += TPB) {
+        const int k = idx / N, jj = idx % N, nn = (jj - N / 2 + P) % P;
         const float2 z = sm[k * SL + spad(nn)];
         const float va = z.x * scale, vb = z.y * scale;
         out[(size_t)(i0 + 2 * k) * N + jj] = va;
@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long*
     const float mean = block_reduce<false>(lsum, red) * (1.f / cnt);
     const float bmax = block_reduce<true>(lmax, red);
     float lm2 = 0.f;
-    for (int idx = threadIdx.x; idx < FPC * N; idx += kThreads) {
-        const int k = idx / N, jj = idx % N, nn = (jj - N / 2 + P) & (P - 1);
+    for (int idx = threadIdx.x; idx < FPC * N; idx += TPB) {
+        const int k = idx / N, jj = idx % N, nn = (jj - N / 2 + P) % P;
         const float2 z = sm[k * SL + spad(nn)];
         const float da = z.x * scale - mean, db = z.y * scale - mean;
         lm2 += da * da + db * db;
@@ -460,12 +460,12 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
 // launchers
 // ---------------------------------------------------------------------------------------------
 
-template <int N> constexpr size_t smem_rows() { return (size_t)(kThreads / FftPlan<N>::T) * spad(N) * sizeof(float2); }
+template <int L> constexpr size_t smem_rows() { return (size_t)(tpb_for(L) / FftPlan<L>::T) * spad(L) * sizeof(float2); }
 template <int N> constexpr size_t smem_cols1() {
     return (size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) * sizeof(float2);
 }
 template <int P> constexpr size_t smem_cols2() {
-    return 2 * (size_t)spad(P) * (kThreads / FftPlan<P>::T + 1) * sizeof(float2);
+    return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T + 1) * sizeof(float2);
 }
 template <int NT> constexpr size_t smem_angle() { return (size_t)spad(NT) * (kAngleRadii + 1) * sizeof(float2); }
 
@@ -483,7 +483,7 @@ static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, con
 template <int N, int P>
 static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                              const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
-    constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T;
+    constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T, TB2 = tpb_for(P);
     w.tr->before(K_S1_ROWS, st);
     k_s1_rows<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st>>>(p, tab, f, g, w.s1, B);
     w.tr->before(K_S1_COLS, st);
@@ -494,13 +494,12 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
     else e = launch_stage1_angle<400>(p, w, B, tab, pose, c_theta, st);
     if (e != cudaSuccess) return e;
     w.tr->before(K_S2_ROWS, st);
-    k_s2_rows<N, P><<<dim3((N / 2) / (kThreads / T2), B, 2), kThreads, smem_rows<P>(), st>>>(p, tab, f, g, w.th,
-                                                                                                w.s2, B);
+    k_s2_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st>>>(p, tab, f, g, w.th, w.s2, B);
     w.tr->before(K_S2_COLS, st);
-    k_s2_cols<N, P><<<dim3((P / 2) / (kThreads / T2), B), kThreads, smem_cols2<P>(), st>>>(p, w.s2, w.s3, B);
-    const int nblk = (N / 2) / (kThreads / T2);
+    k_s2_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, smem_cols2<P>(), st>>>(p, w.s2, w.s3, B);
+    const int nblk = (N / 2) / (TB2 / T2);
     w.tr->before(K_S2_C2R, st);
-    k_s2_c2r<N, P><<<dim3(nblk, B), kThreads, smem_rows<P>(), st>>>(p, tab, w.s3, w.cxy, c_xy, w.st, B);
+    k_s2_c2r<N, P><<<dim3(nblk, B), TB2, smem_rows<P>(), st>>>(p, tab, w.s3, w.cxy, c_xy, w.st, B);
     w.tr->before(K_SXY, st);
     k_sxy<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose);
     w.tr->close(st);
@@ -510,12 +509,12 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
 cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                            const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
     if (B <= 0) return cudaSuccess;
-    if (p.n == 128) return p.p == 256 ? launch_np<128, 256>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+    if (p.n == 128) return p.p == 192 ? launch_np<128, 192>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
                                       : launch_np<128, 128>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
-    if (p.n == 256) return p.p == 512 ? launch_np<256, 512>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+    if (p.n == 256) return p.p == 384 ? launch_np<256, 384>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
                                       : launch_np<256, 256>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
-    return p.p == 1024 ? launch_np<512, 1024>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
-                       : launch_np<512, 512>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+    return p.p == 768 ? launch_np<512, 768>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+                      : launch_np<512, 512>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
 }
 
 template <typename K>
@@ -540,11 +539,11 @@ const char* const kKindNames[K_COUNT] = {
 
 cudaError_t prepare_forward_kernels() {
     cudaError_t e;
-    if ((e = prepare_np<128, 256>()) != cudaSuccess) return e;
+    if ((e = prepare_np<128, 192>()) != cudaSuccess) return e;
     if ((e = prepare_np<128, 128>()) != cudaSuccess) return e;
-    if ((e = prepare_np<256, 512>()) != cudaSuccess) return e;
+    if ((e = prepare_np<256, 384>()) != cudaSuccess) return e;
     if ((e = prepare_np<256, 256>()) != cudaSuccess) return e;
-    if ((e = prepare_np<512, 1024>()) != cudaSuccess) return e;
+    if ((e = prepare_np<512, 768>()) != cudaSuccess) return e;
     if ((e = prepare_np<512, 512>()) != cudaSuccess) return e;
     if ((e = allow_smem(k_angle<128>, smem_angle<128>())) != cudaSuccess) return e;
     if ((e = allow_smem(k_angle<256>, smem_angle<256>())) != cudaSuccess) return e;

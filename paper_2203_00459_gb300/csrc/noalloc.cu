@@ -153,7 +153,7 @@ int fmbym_pose_noalloc(void* stream, const fmbym_size_cfg* cfg, int n_pairs, con
 
     DevPlan p{};
     p.n = cfg->n;
-    p.p = cfg->pad_mode == 1 ? cfg->n : 2 * cfg->n;
+    p.p = cfg->pad_mode == 1 ? cfg->n : 3 * cfg->n / 2;
     p.nt = cfg->n_theta;
     p.nr = cfg->n_r;
     p.window = cfg->window;

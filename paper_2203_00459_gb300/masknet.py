@@ -110,9 +110,10 @@ class MaskNet:
         _lib.check_unet(_lib.lib().fmbym_unet_store(self._h, _st(), _p(p), _p(r), _p(g)), self._h)
         return p, r, g
 
-    def forward(self, f, g, training=True, want_masks=False):
+    def forward(self, f, g, training=True, want_masks=False, f_out=None, g_out=None):
         n = f.shape[0]
-        fo, go = torch.empty_like(f), torch.empty_like(g)
+        fo = torch.empty_like(f) if f_out is None else f_out
+        go = torch.empty_like(g) if g_out is None else g_out
         m = torch.empty((n, 2) + tuple(f.shape[1:]), device=f.device) if want_masks else None
         st = _lib.lib().fmbym_unet_forward(self._h, _st(), n, _p(f), _p(g), int(bool(training)), _p(fo), _p(go), _p(m))
         _lib.check_unet(st, self._h)
