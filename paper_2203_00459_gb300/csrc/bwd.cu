@@ -282,9 +282,9 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
 //  (a) output pixel X of f': its d theta term d f'(X) (dv/dpx (py - c) - dv/dpy (px - c)), since
 //      d px / d theta = py - c and d py / d theta = -(px - c);
 //  (b) source pixel y of f: d f(y) = sum over the output pixels X whose bilinear sample reads y of
-//      weight * d f'(X).  Such X lie within sqrt 2 of c + R(theta)(y - c), i.e. in the 3 x 3 box
-//      around its rounded position; each candidate's sample point is recomputed exactly as the
-//      forward computes it, so the weights are the forward's weights.
+//      weight * d f'(X).  Such X lie within sqrt 2 of X0 = c + R(theta)(y - c), i.e. in the 3 x 3
+//      box around its rounded position, and the bilinear weight of y in X's sample is the tent
+//      (1 - |dx|)(1 - |dy|) of the offset R(-theta)(X - X0) of that sample from y.
 // d theta is reduced per pair (last block adds the block sums in order) into bsc[q][8] together
 // with the direct term dL/dtheta.
 template <int N>
@@ -320,33 +320,30 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
         const float pxc = ((float)x0 - c) + fx, pyc = ((float)y0 - c) + fy;
         contrib = d[idx] * (dvx * pyc - dvy * pxc);
     }
-    // (b) d f at source pixel (X, Y)
+    // (b) d f at source pixel (X, Y).  Its image X0 = c + R(theta)(y - c) (error-free coordinates);
+    // a candidate output pixel M samples at y + R(-theta)(M - X0), so its bilinear weight on y is the
+    // tent (1 - |dx|)(1 - |dy|) of (dx, dy) = R(-theta)(M - X0), small numbers exact to ~1e-7
     {
-        const float dx = (float)X - c, dy = (float)Y - c;
-        const float ex = c + ch * dx - sh * dy, ey = c + sh * dx + ch * dy;
-        const int mx0 = (int)rintf(ex) - 1, my0 = (int)rintf(ey) - 1;
+        int ix, iy;
+        float fx, fy;
+        rot_coord(ch, cl, (float)X - c, -sh, -sl, (float)Y - c, c, ix, fx);  // c + cos dx - sin dy
+        rot_coord(sh, sl, (float)X - c, ch, cl, (float)Y - c, c, iy, fy);    // c + sin dx + cos dy
+        const int mx0 = ix + (fx >= 0.5f ? 1 : 0) - 1, my0 = iy + (fy >= 0.5f ? 1 : 0) - 1;
+        const float ct = ch + cl, stn = sh + sl;
         float acc = 0.f;
 #pragma unroll
         for (int oy = 0; oy < 3; ++oy) {
             const int my = my0 + oy;
             if ((unsigned)my >= (unsigned)N) continue;
+            const float ey = (float)(my - iy) - fy;
 #pragma unroll
             for (int ox = 0; ox < 3; ++ox) {
                 const int mx = mx0 + ox;
                 if ((unsigned)mx >= (unsigned)N) continue;
-                int x0, y0;
-                float fx, fy;
-                rot_coord(ch, cl, (float)mx - c, sh, sl, (float)my - c, c, x0, fx);
-                float wx;
-                if (x0 == X) wx = 1.f - fx;
-                else if (x0 + 1 == X) wx = fx;
-                else continue;
-                rot_coord(ch, cl, (float)my - c, -sh, -sl, (float)mx - c, c, y0, fy);
-                float wy;
-                if (y0 == Y) wy = 1.f - fy;
-                else if (y0 + 1 == Y) wy = fy;
-                else continue;
-                acc += wy * wx * d[(size_t)my * N + mx];
+                const float ex = (float)(mx - ix) - fx;
+                const float dx = fmaf(ct, ex, stn * ey), dy = fmaf(ct, ey, -stn * ex);
+                const float wx = 1.f - fabsf(dx), wy = 1.f - fabsf(dy);
+                if (wx > 0.f && wy > 0.f) acc += wy * wx * d[(size_t)my * N + mx];
             }
         }
         df[tab[3 * q] + idx] = acc;

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long
 // multiply conj(F') G (A1), inverse FFT, keep the N lag rows s_y in [-N/2, N/2).  Column 0 holds
 // the DC and Nyquist columns packed; their products are formed after separating them.
 template <int N, int P>
-__global__ void __launch_bounds__(kThreads) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
+__global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
                                                       float2* __restrict__ s3, int B) {
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), C = TPB / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
     constexpr int PER = P * C / TPB;
