@@ -173,70 +173,73 @@ __device__ __forceinline__ void split0(float2 z, float2 zm, float2& a, float2& b
     b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
 }
 
-// Column pass of the correlation adjoint: FFT columns of D (lag rows placed at their P-rows), F'
-// and G (rows < N); Q1 = conj(D) G and Q2 = D F' (the packed column 0 per DC/Nyquist part); inverse
-// column FFTs; keep the spatial rows y < N.
+// Column pass of the correlation adjoint: FFT columns of D (lag rows placed at their P-rows) and
+// of G, Q1 = conj(D) G, inverse, keep the spatial rows y < N (-> d f'); then the same tile takes
+// F': FFT, Q2 = D F', inverse, keep y < N (-> d g).  The packed column 0 multiplies its DC and
+// Nyquist parts separately.  Two tiles are resident at a time.
 template <int N, int P>
-__global__ void __launch_bounds__(kThreads) k_b_cols(DevPlan p, const float2* __restrict__ b1,
-                                                     const float2* __restrict__ s2, float2* __restrict__ b2, int B) {
-    constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), C = TPB / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
+__global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_b_cols(DevPlan p, const float2* __restrict__ b1,
+                                                                       const float2* __restrict__ s2,
+                                                                       float2* __restrict__ b2, int B) {
+    constexpr int TPB = tpb_for(P), T = FftPlan<P>::T, C = TPB / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
     constexpr int PER = P * C / TPB;
     extern __shared__ float2 sm[];
     float2* tD = sm;
-    float2* tF = sm + TILE;
-    float2* tG = sm + 2 * TILE;
+    float2* tX = sm + TILE;
     const int q = blockIdx.y, u0 = blockIdx.x * C;
     const float2* inD = b1 + (size_t)q * N * W;
     const float2* inF = s2 + (size_t)q * N * W;
     const float2* inG = s2 + (size_t)(B + q) * N * W;
+    const float2 zero = make_float2(0.f, 0.f);
     for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
         const int v = idx / C, c = idx % C, i = (v + N / 2) % P;
-        const float2 zero = make_float2(0.f, 0.f);
         tD[spad(v) * ES + c] = i < N ? inD[(size_t)i * W + u0 + c] : zero;
-        tF[spad(v) * ES + c] = v < N ? inF[(size_t)v * W + u0 + c] : zero;
-        tG[spad(v) * ES + c] = v < N ? inG[(size_t)v * W + u0 + c] : zero;
+        tX[spad(v) * ES + c] = v < N ? inG[(size_t)v * W + u0 + c] : zero;
     }
     __syncthreads();
     const int c = threadIdx.x / T, j = threadIdx.x % T;
     fft<P, -1>(tD + c, ES, j, true, p.tw_p);
-    fft<P, -1>(tF + c, ES, j, true, p.tw_p);
-    fft<P, -1>(tG + c, ES, j, true, p.tw_p);
-    float2 q1[PER], q2[PER];
+#pragma unroll 1
+    for (int phase = 0; phase < 2; ++phase) {
+        fft<P, -1>(tX + c, ES, j, true, p.tw_p);
+        float2 qv[PER];
 #pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-        const float2 D = tD[spad(v) * ES + cc], F = tF[spad(v) * ES + cc], G = tG[spad(v) * ES + cc];
-        if (u0 + cc == 0) {
-            const int vm = (v == 0 ? 0 : P - v);
-            float2 ad, bd, af, bf, ag, bg;
-            split0(D, tD[spad(vm) * ES + cc], ad, bd);
-            split0(F, tF[spad(vm) * ES + cc], af, bf);
-            split0(G, tG[spad(vm) * ES + cc], ag, bg);
-            const float2 g0 = c_cjmul(ad, ag), gn = c_cjmul(bd, bg);
-            const float2 f0 = c_mul(ad, af), fn = c_mul(bd, bf);
-            q1[m] = make_float2(g0.x - gn.y, g0.y + gn.x);
-            q2[m] = make_float2(f0.x - fn.y, f0.y + fn.x);
-        } else {
-            q1[m] = c_cjmul(D, G);
-            q2[m] = c_mul(D, F);
+        for (int m = 0; m < PER; ++m) {
+            const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
+            const float2 D = tD[spad(v) * ES + cc], X = tX[spad(v) * ES + cc];
+            if (u0 + cc == 0) {
+                const int vm = v == 0 ? 0 : P - v;
+                float2 ad, bd, ax, bx;
+                split0(D, tD[spad(vm) * ES + cc], ad, bd);
+                split0(X, tX[spad(vm) * ES + cc], ax, bx);
+                const float2 q0 = phase == 0 ? c_cjmul(ad, ax) : c_mul(ad, ax);
+                const float2 qn = phase == 0 ? c_cjmul(bd, bx) : c_mul(bd, bx);
+                qv[m] = make_float2(q0.x - qn.y, q0.y + qn.x);
+            } else {
+                qv[m] = phase == 0 ? c_cjmul(D, X) : c_mul(D, X);
+            }
         }
-    }
-    __syncthreads();
+        __syncthreads();
 #pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-        tG[spad(v) * ES + cc] = q1[m];
-        tF[spad(v) * ES + cc] = q2[m];
-    }
-    __syncthreads();
-    fft<P, +1>(tG + c, ES, j, true, p.tw_p);
-    fft<P, +1>(tF + c, ES, j, true, p.tw_p);
-    float2* o1 = b2 + (size_t)q * N * W;
-    float2* o2 = b2 + (size_t)(B + q) * N * W;
-    for (int idx = threadIdx.x; idx < N * C; idx += TPB) {
-        const int y = idx / C, cc = idx % C;
-        o1[(size_t)y * W + u0 + cc] = tG[spad(y) * ES + cc];
-        o2[(size_t)y * W + u0 + cc] = tF[spad(y) * ES + cc];
+        for (int m = 0; m < PER; ++m) {
+            const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
+            tX[spad(v) * ES + cc] = qv[m];
+        }
+        __syncthreads();
+        fft<P, +1>(tX + c, ES, j, true, p.tw_p);
+        float2* o = b2 + (size_t)(phase * B + q) * N * W;
+        for (int idx = threadIdx.x; idx < N * C; idx += TPB) {
+            const int y = idx / C, cc = idx % C;
+            o[(size_t)y * W + u0 + cc] = tX[spad(y) * ES + cc];
+        }
+        if (phase == 0) {
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
+                const int v = idx / C, cc = idx % C;
+                tX[spad(v) * ES + cc] = v < N ? inF[(size_t)v * W + u0 + cc] : zero;
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -535,7 +538,7 @@ __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float* __r
 // DC/Nyquist columns made Hermitian (only the real part of their row sums counts) so that they
 // can share the packed column 0.
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_b_s1cols(DevPlan p, const float2* __restrict__ s1,
+__global__ void __launch_bounds__(kThreads, 3) k_b_s1cols(DevPlan p, const float2* __restrict__ s1,
                                                        const float* __restrict__ gmt, float2* __restrict__ gs1,
                                                        int B) {
     constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C + 1, W = N / 2, PER = C * N / kThreads;
@@ -693,7 +696,7 @@ cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, in
 
 template <int L> constexpr size_t b_smem_rows() { return (size_t)(tpb_for(L) / FftPlan<L>::T) * spad(L) * sizeof(float2); }
 template <int P> constexpr size_t b_smem_cols() {
-    return 3 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T + 1) * sizeof(float2);
+    return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T + 1) * sizeof(float2);
 }
 template <int N> constexpr size_t b_smem_s1cols() {
     return ((size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) + spad(N)) * sizeof(float2);
