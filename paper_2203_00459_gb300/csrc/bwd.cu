@@ -193,9 +193,12 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_b_cols(DevPl
     const float2 zero = make_float2(0.f, 0.f);
     for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
         const int v = idx / C, c = idx % C, i = (v + N / 2) % P;
-        tD[spad(v) * ES + c] = i < N ? inD[(size_t)i * W + u0 + c] : zero;
-        tX[spad(v) * ES + c] = v < N ? inG[(size_t)v * W + u0 + c] : zero;
+        if (i < N) cp_async8(&tD[spad(v) * ES + c], &inD[(size_t)i * W + u0 + c]);
+        else tD[spad(v) * ES + c] = zero;
+        if (v < N) cp_async8(&tX[spad(v) * ES + c], &inG[(size_t)v * W + u0 + c]);
+        else tX[spad(v) * ES + c] = zero;
     }
+    cp_async_wait_all();
     __syncthreads();
     const int c = threadIdx.x / T, j = threadIdx.x % T;
     fft<P, -1>(tD + c, ES, j, true, p.tw_p);
@@ -236,8 +239,10 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_b_cols(DevPl
             __syncthreads();
             for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
                 const int v = idx / C, cc = idx % C;
-                tX[spad(v) * ES + cc] = v < N ? inF[(size_t)v * W + u0 + cc] : zero;
+                if (v < N) cp_async8(&tX[spad(v) * ES + cc], &inF[(size_t)v * W + u0 + cc]);
+                else tX[spad(v) * ES + cc] = zero;
             }
+            cp_async_wait_all();
             __syncthreads();
         }
     }
@@ -548,8 +553,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_b_s1cols(DevPlan p, const float
     const float2* in = s1 + (size_t)(s * B + q) * N * W;
     for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
         const int v = idx / C, c = idx % C;
-        sm[spad(v) * ES + c] = in[(size_t)v * W + u0 + c];
+        cp_async8(&sm[spad(v) * ES + c], &in[(size_t)v * W + u0 + c]);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft<N, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
     const float* dm = gmt + (size_t)(s * B + q) * (W + 1) * N;

@@ -24,6 +24,14 @@ namespace fmbym {
 
 __host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >> 4); }
 
+// Asynchronous 8-byte global -> shared copy (cp.async); many can be in flight per thread.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// Waits for every cp.async this thread issued (a __syncthreads must follow before others read).
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {

@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* _
     const float2* in = s1 + (size_t)(s * B + q) * N * W;
     for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
         const int v = idx / C, c = idx % C;
-        sm[spad(v) * ES + c] = in[(size_t)v * W + u0 + c];
+        cp_async8(&sm[spad(v) * ES + c], &in[(size_t)v * W + u0 + c]);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft<N, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
     float* out = mt + (size_t)(s * B + q) * (W + 1) * N;
@@ -287,14 +288,15 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevP
     const float2* ing = s2 + (size_t)(B + q) * N * W;
     for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
         const int v = idx / C, c = idx % C;
-        float2 a = make_float2(0.f, 0.f), b = a;
         if (v < N) {
-            a = inf[(size_t)v * W + u0 + c];
-            b = ing[(size_t)v * W + u0 + c];
+            cp_async8(&tf[spad(v) * ES + c], &inf[(size_t)v * W + u0 + c]);
+            cp_async8(&tg[spad(v) * ES + c], &ing[(size_t)v * W + u0 + c]);
+        } else {
+            tf[spad(v) * ES + c] = make_float2(0.f, 0.f);
+            tg[spad(v) * ES + c] = make_float2(0.f, 0.f);
         }
-        tf[spad(v) * ES + c] = a;
-        tg[spad(v) * ES + c] = b;
     }
+    cp_async_wait_all();
     __syncthreads();
     const int c = threadIdx.x / T, j = threadIdx.x % T;
     fft<P, -1>(tf + c, ES, j, true, p.tw_p);
