@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long*
     const float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
     const float* r = bsc + (size_t)q * 16;
     const float* c = cxy + (size_t)q * N * N;
+    #pragma unroll 4
     for (int idx = threadIdx.x; idx < FPC * P; idx += TPB) {
         const int k = idx / P, x = idx % P, j = (x + N / 2) % P, i = i0 + 2 * k;
         float2 v = make_float2(0.f, 0.f);
@@ -258,6 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, i0 = blockIdx.x * FPC * 2;
     const float2* in = b2 + (size_t)(s * B + q) * N * W;
+    #pragma unroll 4
     for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
         const int k = idx / W, u = idx % W;
         const float2 a = in[(size_t)(i0 + 2 * k) * W + u], b = in[(size_t)(i0 + 2 * k + 1) * W + u];
@@ -630,6 +632,7 @@ __global__ void __launch_bounds__(kThreads) k_b_s1rows(DevPlan p, const long lon
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
     const float2* in = gs1 + (size_t)(s * B + q) * N * W;
+    #pragma unroll 4
     for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
         const int k = idx / W, u = idx % W;
         const float2 a = in[(size_t)(r0 + 2 * k) * W + u], b = in[(size_t)(r0 + 2 * k + 1) * W + u];

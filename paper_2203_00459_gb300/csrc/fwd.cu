@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kThreads) k_s1_rows(DevPlan p, const long long
     const int q = blockIdx.y, s = blockIdx.z;
     const float* __restrict__ src = (s ? g : f) + tab[3 * q];
     const int r0 = blockIdx.x * FPC * 2;
+    #pragma unroll 4
     for (int idx = threadIdx.x; idx < FPC * 2 * (N / 4); idx += kThreads) {
         const int rr = idx / (N / 4), x4 = (idx % (N / 4)) * 4, row = r0 + rr;
         float4 v = __ldg(reinterpret_cast<const float4*>(src + (size_t)row * N + x4));
@@ -229,12 +230,14 @@ __global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long
     if (s == 0) {
         const float* t = th + 8 * q;
         const float ch = t[1], cl = t[2], sh = t[3], sl = t[4];
+        #pragma unroll 4
         for (int idx = threadIdx.x; idx < FPC * 2 * N; idx += TPB) {
             const int rr = idx / N, x = idx % N;
             const float v = rotated_sample(src, N, x, r0 + rr, ch, cl, sh, sl);
             reinterpret_cast<float*>(sm + (rr >> 1) * SL + spad(x))[rr & 1] = v;
         }
     } else {
+        #pragma unroll 4
         for (int idx = threadIdx.x; idx < FPC * 2 * (N / 4); idx += TPB) {
             const int rr = idx / (N / 4), x4 = (idx % (N / 4)) * 4;
             const float4 v = __ldg(reinterpret_cast<const float4*>(src + (size_t)(r0 + rr) * N + x4));
@@ -346,6 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long*
     __shared__ float red[32];
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
     const float2* in = s3 + (size_t)q * N * W;
+    #pragma unroll 4
     for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
         const int k = idx / W, u = idx % W;
         const float2 a = in[(size_t)(i0 + 2 * k) * W + u], b = in[(size_t)(i0 + 2 * k + 1) * W + u];
