@@ -169,6 +169,42 @@ template <int R, int S> __device__ __forceinline__ void dft(float2* v) {
 // ---------------------------------------------------------------------------------------------
 // one Stockham pass; every thread of the CTA must call it (it contains __syncthreads)
 // ---------------------------------------------------------------------------------------------
+
+// Twiddles W_{NS R}^{(b mod NS) t} of butterfly b applied to its inputs v[1..R-1] (no-op for NS = 1):
+// one table load of W^bm (and of W^(4 bm) for radix 16); the other powers by complex products at
+// most three deep.
+template <int L, int R, int NS, int S>
+__device__ __forceinline__ void twiddle(float2* v, int b, const float2* __restrict__ tw) {
+    if constexpr (NS > 1) {
+        constexpr int STEP = L / (NS * R);
+        const int bm = b % NS;
+        float2 w[R];
+        w[1] = __ldg(&tw[bm * STEP]);
+        if constexpr (S > 0) w[1].y = -w[1].y;
+        if constexpr (R >= 16) {
+            w[4] = __ldg(&tw[4 * bm * STEP]);
+            if constexpr (S > 0) w[4].y = -w[4].y;
+            w[2] = c_mul(w[1], w[1]);
+            w[3] = c_mul(w[2], w[1]);
+            w[8] = c_mul(w[4], w[4]);
+            w[12] = c_mul(w[8], w[4]);
+#pragma unroll
+            for (int t = 5; t < R; ++t)
+                if ((t & 3) != 0) w[t] = c_mul(w[t & ~3], w[t & 3]);
+        } else {
+#pragma unroll
+            for (int t = 2; t < R; ++t) w[t] = (t & 1) ? c_mul(w[t - 1], w[1]) : c_mul(w[t / 2], w[t / 2]);
+        }
+#pragma unroll
+        for (int t = 1; t < R; ++t) v[t] = c_mul(v[t], w[t]);
+    }
+}
+
+// Position of output t of butterfly b in a pass of radix R after passes of product NS.
+template <int R, int NS> __device__ __forceinline__ int pass_out(int b, int t) {
+    return (b / NS) * NS * R + (b % NS) + t * NS;
+}
+
 template <int L, int T, int R, int NS, int S>
 __device__ __forceinline__ void fft_pass(float2* buf, int es, int j, bool active, const float2* __restrict__ tw) {
     constexpr int NB = L / R;                // butterflies in the pass
@@ -181,31 +217,7 @@ __device__ __forceinline__ void fft_pass(float2* buf, int es, int j, bool active
         if (active && (NB % T == 0 || b < NB)) {
 #pragma unroll
             for (int t = 0; t < R; ++t) v[m][t] = buf[spad(b + t * NB) * es];
-            if constexpr (NS > 1) {
-                // twiddles W^(bm t), W = W_{NS R}: one table load of W^bm (and of W^(4 bm) for
-                // radix 16); the other powers by complex products at most three deep
-                constexpr int STEP = L / (NS * R);
-                const int bm = b % NS;
-                float2 w[R];
-                w[1] = __ldg(&tw[bm * STEP]);
-                if constexpr (S > 0) w[1].y = -w[1].y;
-                if constexpr (R >= 16) {
-                    w[4] = __ldg(&tw[4 * bm * STEP]);
-                    if constexpr (S > 0) w[4].y = -w[4].y;
-                    w[2] = c_mul(w[1], w[1]);
-                    w[3] = c_mul(w[2], w[1]);
-                    w[8] = c_mul(w[4], w[4]);
-                    w[12] = c_mul(w[8], w[4]);
-#pragma unroll
-                    for (int t = 5; t < R; ++t)
-                        if ((t & 3) != 0) w[t] = c_mul(w[t & ~3], w[t & 3]);
-                } else {
-#pragma unroll
-                    for (int t = 2; t < R; ++t) w[t] = (t & 1) ? c_mul(w[t - 1], w[1]) : c_mul(w[t / 2], w[t / 2]);
-                }
-#pragma unroll
-                for (int t = 1; t < R; ++t) v[m][t] = c_mul(v[m][t], w[t]);
-            }
+            twiddle<L, R, NS, S>(v[m], b, tw);
             dft<R, S>(v[m]);
         }
     }
@@ -214,9 +226,44 @@ __device__ __forceinline__ void fft_pass(float2* buf, int es, int j, bool active
     for (int m = 0; m < BPT; ++m) {
         const int b = j + m * T;
         if (active && (NB % T == 0 || b < NB)) {
-            const int base = (b / NS) * NS * R + (b % NS);
 #pragma unroll
-            for (int t = 0; t < R; ++t) buf[spad(base + t * NS) * es] = v[m][t];
+            for (int t = 0; t < R; ++t) buf[spad(pass_out<R, NS>(b, t)) * es] = v[m][t];
+        }
+    }
+    __syncthreads();
+}
+
+// The same pass on two sequences at once (one pair of barriers for both).
+template <int L, int T, int R, int NS, int S>
+__device__ __forceinline__ void fft_pass2(float2* b0, float2* b1, int es, int j, const float2* __restrict__ tw) {
+    constexpr int NB = L / R;
+    constexpr int BPT = (NB + T - 1) / T;
+    float2 v[BPT][R], w[BPT][R];
+#pragma unroll
+    for (int m = 0; m < BPT; ++m) {
+        const int b = j + m * T;
+        if (NB % T == 0 || b < NB) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                v[m][t] = b0[spad(b + t * NB) * es];
+                w[m][t] = b1[spad(b + t * NB) * es];
+            }
+            twiddle<L, R, NS, S>(v[m], b, tw);
+            dft<R, S>(v[m]);
+            twiddle<L, R, NS, S>(w[m], b, tw);
+            dft<R, S>(w[m]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < BPT; ++m) {
+        const int b = j + m * T;
+        if (NB % T == 0 || b < NB) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                b0[spad(pass_out<R, NS>(b, t)) * es] = v[m][t];
+                b1[spad(pass_out<R, NS>(b, t)) * es] = w[m][t];
+            }
         }
     }
     __syncthreads();
@@ -228,30 +275,28 @@ __device__ __forceinline__ void fft_passes(float2* buf, int es, int j, bool acti
     if constexpr (sizeof...(Rest) > 0) fft_passes<L, T, S, NS * R, Rest...>(buf, es, j, active, tw);
 }
 
-// Radix plans: every length uses radix 16 first; T = threads per sequence.
+// Radix plans: every length uses radix 16 first; T = L/16 threads per sequence.  NP passes of
+// radices R1 = 16, R2 (, R3).  The column kernels that chain a forward transform, a pointwise
+// product and an inverse run the inverse in the reverse radix order: the forward's last pass and
+// the inverse's first pass then read and write the same butterfly positions, so the product
+// happens in registers between them.
 template <int L> struct FftPlan;
-template <> struct FftPlan<128> { static constexpr int T = 8; };
-template <> struct FftPlan<192> { static constexpr int T = 12; };
-template <> struct FftPlan<384> { static constexpr int T = 24; };
-template <> struct FftPlan<768> { static constexpr int T = 48; };
-template <> struct FftPlan<256> { static constexpr int T = 16; };
-template <> struct FftPlan<400> { static constexpr int T = 25; };
-template <> struct FftPlan<512> { static constexpr int T = 32; };
-template <> struct FftPlan<1024> { static constexpr int T = 64; };
+template <> struct FftPlan<128> { static constexpr int T = 8, NP = 2, R2 = 8, R3 = 1; };
+template <> struct FftPlan<192> { static constexpr int T = 12, NP = 3, R2 = 4, R3 = 3; };
+template <> struct FftPlan<256> { static constexpr int T = 16, NP = 2, R2 = 16, R3 = 1; };
+template <> struct FftPlan<384> { static constexpr int T = 24, NP = 3, R2 = 8, R3 = 3; };
+template <> struct FftPlan<400> { static constexpr int T = 25, NP = 3, R2 = 5, R3 = 5; };
+template <> struct FftPlan<512> { static constexpr int T = 32, NP = 3, R2 = 16, R3 = 2; };
+template <> struct FftPlan<768> { static constexpr int T = 48, NP = 3, R2 = 16, R3 = 3; };
+template <> struct FftPlan<1024> { static constexpr int T = 64, NP = 3, R2 = 16, R3 = 4; };
 
 // In-place FFT of one sequence (element i at buf[spad(i) * es]) by thread j < T of its group.
 // S = -1 forward, +1 inverse.  Threads with active = false only take part in the barriers.
 template <int L, int S>
 __device__ __forceinline__ void fft(float2* buf, int es, int j, bool active, const float2* __restrict__ tw) {
-    constexpr int T = FftPlan<L>::T;
-    if constexpr (L == 128) fft_passes<L, T, S, 1, 16, 8>(buf, es, j, active, tw);
-    else if constexpr (L == 256) fft_passes<L, T, S, 1, 16, 16>(buf, es, j, active, tw);
-    else if constexpr (L == 400) fft_passes<L, T, S, 1, 16, 5, 5>(buf, es, j, active, tw);
-    else if constexpr (L == 512) fft_passes<L, T, S, 1, 16, 16, 2>(buf, es, j, active, tw);
-    else if constexpr (L == 1024) fft_passes<L, T, S, 1, 16, 16, 4>(buf, es, j, active, tw);
-    else if constexpr (L == 192) fft_passes<L, T, S, 1, 16, 4, 3>(buf, es, j, active, tw);
-    else if constexpr (L == 384) fft_passes<L, T, S, 1, 16, 8, 3>(buf, es, j, active, tw);
-    else if constexpr (L == 768) fft_passes<L, T, S, 1, 16, 16, 3>(buf, es, j, active, tw);
+    using PL = FftPlan<L>;
+    if constexpr (PL::NP == 2) fft_passes<L, PL::T, S, 1, 16, PL::R2>(buf, es, j, active, tw);
+    else fft_passes<L, PL::T, S, 1, 16, PL::R2, PL::R3>(buf, es, j, active, tw);
 }
 
 // Threads of a CTA that runs several length-L sequences side by side: a multiple of both the

@@ -278,62 +278,132 @@ __global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long
 // Column pass of the correlation: FFT the columns of F' and G (rows >= N are the zero pad),
 // multiply conj(F') G (A1), inverse FFT, keep the N lag rows s_y in [-N/2, N/2).  Column 0 holds
 // the DC and Nyquist columns packed; their products are formed after separating them.
+//
+// Shared traffic is cut to what the middle passes need: the forward's first radix-16 pass reads
+// its inputs straight from global memory, the forward's last pass, the product and the inverse's
+// first pass (the inverse runs the radices in reverse order, so both touch the same butterfly
+// positions) happen in registers, and the inverse's last radix-16 pass stores the kept rows
+// straight to global memory.  Threads are column-fastest (c = tid mod C) over a tile of stride
+// C, which makes every shared access phase free of bank conflicts and every global access a run
+// of C consecutive columns.
 template <int N, int P>
 __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
                                                       float2* __restrict__ s3, int B) {
-    constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), C = TPB / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
-    constexpr int PER = P * C / TPB;
+    using PL = FftPlan<P>;
+    constexpr int T = PL::T, TPB = tpb_for(P), C = TPB / T, ES = C, W = P / 2, TILE = spad(P) * ES;
+    constexpr int RL = PL::NP == 3 ? PL::R3 : PL::R2;   // radix of the forward's last pass
+    constexpr int NBL = P / RL;                          // its butterflies (= its stride NS)
+    constexpr int BPL = (NBL + T - 1) / T;
     extern __shared__ float2 sm[];
     float2* tf = sm;
     float2* tg = sm + TILE;
     const int q = blockIdx.y, u0 = blockIdx.x * C;
-    const float2* inf = s2 + (size_t)q * N * W;
-    const float2* ing = s2 + (size_t)(B + q) * N * W;
-    for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
-        const int v = idx / C, c = idx % C;
-        if (v < N) {
-            cp_async8(&tf[spad(v) * ES + c], &inf[(size_t)v * W + u0 + c]);
-            cp_async8(&tg[spad(v) * ES + c], &ing[(size_t)v * W + u0 + c]);
-        } else {
-            tf[spad(v) * ES + c] = make_float2(0.f, 0.f);
-            tg[spad(v) * ES + c] = make_float2(0.f, 0.f);
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    const int c = threadIdx.x / T, j = threadIdx.x % T;
-    fft<P, -1>(tf + c, ES, j, true, p.tw_p);
-    fft<P, -1>(tg + c, ES, j, true, p.tw_p);
-    float2 qv[PER];
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const float2* __restrict__ tw = p.tw_p;
+    {   // forward pass 1 (radix 16, no twiddles) from global memory
+        const float2* inf = s2 + (size_t)q * N * W + u0 + c;
+        const float2* ing = s2 + (size_t)(B + q) * N * W + u0 + c;
+        float2 vf[16], vg[16];
 #pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-        const float2 F = tf[spad(v) * ES + cc], G = tg[spad(v) * ES + cc];
-        if (u0 + cc == 0) {
-            const int vm = (v == 0 ? 0 : P - v);
-            const float2 Fm = tf[spad(vm) * ES + cc], Gm = tg[spad(vm) * ES + cc];
-            const float2 af = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
-            const float2 bf = make_float2(0.5f * (F.y + Fm.y), -0.5f * (F.x - Fm.x));
-            const float2 ag = make_float2(0.5f * (G.x + Gm.x), 0.5f * (G.y - Gm.y));
-            const float2 bg = make_float2(0.5f * (G.y + Gm.y), -0.5f * (G.x - Gm.x));
-            const float2 p0 = c_cjmul(af, ag), pn = c_cjmul(bf, bg);
-            qv[m] = make_float2(p0.x - pn.y, p0.y + pn.x);
-        } else {
-            qv[m] = c_cjmul(F, G);
+        for (int t = 0; t < 16; ++t) {
+            const int row = j + t * T;
+            if (row < N) {
+                vf[t] = __ldg(inf + (size_t)row * W);
+                vg[t] = __ldg(ing + (size_t)row * W);
+            } else {
+                vf[t] = make_float2(0.f, 0.f);
+                vg[t] = make_float2(0.f, 0.f);
+            }
+        }
+        dft16<-1>(vf);
+        dft16<-1>(vg);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            tf[spad(16 * j + t) * ES + c] = vf[t];
+            tg[spad(16 * j + t) * ES + c] = vg[t];
         }
     }
     __syncthreads();
+    if constexpr (PL::NP == 3) fft_pass2<P, T, PL::R2, 16, -1>(tf + c, tg + c, ES, j, tw);
+    if (blockIdx.x != 0) {
+        // forward last pass, conj(F') G and the inverse's first pass (no twiddles) in registers
+        float2 o[BPL][RL];
 #pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-        tg[spad(v) * ES + cc] = qv[m];
+        for (int m = 0; m < BPL; ++m) {
+            const int b = j + m * T;
+            if (NBL % T == 0 || b < NBL) {
+                float2 a[RL], g[RL];
+#pragma unroll
+                for (int t = 0; t < RL; ++t) {
+                    a[t] = tf[spad(b + t * NBL) * ES + c];
+                    g[t] = tg[spad(b + t * NBL) * ES + c];
+                }
+                twiddle<P, RL, NBL, -1>(a, b, tw);
+                dft<RL, -1>(a);
+                twiddle<P, RL, NBL, -1>(g, b, tw);
+                dft<RL, -1>(g);
+#pragma unroll
+                for (int t = 0; t < RL; ++t) o[m][t] = c_cjmul(a[t], g[t]);
+                dft<RL, +1>(o[m]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < BPL; ++m) {
+            const int b = j + m * T;
+            if (NBL % T == 0 || b < NBL) {
+#pragma unroll
+                for (int t = 0; t < RL; ++t) tf[spad(RL * b + t) * ES + c] = o[m][t];
+            }
+        }
+        __syncthreads();
+    } else {
+        // the tile holding column 0: last forward pass in shared memory, then the products with
+        // the DC / Nyquist split (which pairs v with P - v), then the inverse's first pass
+        fft_pass2<P, T, RL, NBL, -1>(tf + c, tg + c, ES, j, tw);
+        constexpr int PER = P * C / TPB;
+        float2 qv[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
+            const float2 F = tf[spad(v) * ES + cc], G = tg[spad(v) * ES + cc];
+            if (cc == 0) {
+                const int vm = (v == 0 ? 0 : P - v);
+                const float2 Fm = tf[spad(vm) * ES + cc], Gm = tg[spad(vm) * ES + cc];
+                const float2 af = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
+                const float2 bf = make_float2(0.5f * (F.y + Fm.y), -0.5f * (F.x - Fm.x));
+                const float2 ag = make_float2(0.5f * (G.x + Gm.x), 0.5f * (G.y - Gm.y));
+                const float2 bg = make_float2(0.5f * (G.y + Gm.y), -0.5f * (G.x - Gm.x));
+                const float2 p0 = c_cjmul(af, ag), pn = c_cjmul(bf, bg);
+                qv[m] = make_float2(p0.x - pn.y, p0.y + pn.x);
+            } else {
+                qv[m] = c_cjmul(F, G);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
+            tf[spad(v) * ES + cc] = qv[m];
+        }
+        __syncthreads();
+        fft_pass<P, T, RL, 1, +1>(tf + c, ES, j, true, tw);
     }
-    __syncthreads();
-    fft<P, +1>(tg + c, ES, j, true, p.tw_p);
-    float2* out = s3 + (size_t)q * N * W;
-    for (int idx = threadIdx.x; idx < N * C; idx += TPB) {
-        const int i = idx / C, cc = idx % C, v = (i - N / 2 + P) % P;
-        out[(size_t)i * W + u0 + cc] = tg[spad(v) * ES + cc];
+    if constexpr (PL::NP == 3) fft_pass<P, T, PL::R2, RL, +1>(tf + c, ES, j, true, tw);
+    {   // inverse last pass (radix 16, stride T) straight to the N kept lag rows in global memory
+        float2 v[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) v[t] = tf[spad(j + t * T) * ES + c];
+        twiddle<P, 16, T, +1>(v, j, tw);
+        dft16<+1>(v);
+        float2* out = s3 + (size_t)q * N * W + u0 + c;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            // P-position j + t T holds lag s_y = pos (pos < P/2) or pos - P; lag row i = s_y + N/2
+            const int pos = j + t * T;
+            const int i = pos < P / 2 ? pos + N / 2 : pos - P + N / 2;
+            if (i >= 0 && i < N) out[(size_t)i * W] = v[t];
+        }
     }
 }
 
@@ -471,7 +541,7 @@ template <int N> constexpr size_t smem_cols1() {
     return (size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) * sizeof(float2);
 }
 template <int P> constexpr size_t smem_cols2() {
-    return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T + 1) * sizeof(float2);
+    return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T) * sizeof(float2);
 }
 template <int NT> constexpr size_t smem_angle() { return (size_t)spad(NT) * (kAngleRadii + 1) * sizeof(float2); }
 
