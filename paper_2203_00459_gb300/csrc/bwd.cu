@@ -177,74 +177,83 @@ __device__ __forceinline__ void split0(float2 z, float2 zm, float2& a, float2& b
 // Column pass of the correlation adjoint: FFT columns of D (lag rows placed at their P-rows) and
 // of G, Q1 = conj(D) G, inverse, keep the spatial rows y < N (-> d f'); then the same tile takes
 // F': FFT, Q2 = D F', inverse, keep y < N (-> d g).  The packed column 0 multiplies its DC and
-// Nyquist parts separately.  Two tiles are resident at a time.
+// Nyquist parts separately.  Two tiles are resident at a time.  As in the forward's column pass,
+// first passes read global memory, the forward's last pass, the product and the inverse's first
+// pass run in registers (D's transformed values stay in its tile for the second product), and the
+// inverse's last pass stores to global memory.
 template <int N, int P>
 __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_b_cols(DevPlan p, const float2* __restrict__ b1,
                                                                        const float2* __restrict__ s2,
                                                                        float2* __restrict__ b2, int B) {
-    constexpr int TPB = tpb_for(P), T = FftPlan<P>::T, C = TPB / T, ES = C + 1, W = P / 2, TILE = spad(P) * ES;
-    constexpr int PER = P * C / TPB;
+    using PL = FftPlan<P>;
+    constexpr int TPB = tpb_for(P), T = PL::T, C = TPB / T, ES = C, W = P / 2, TILE = spad(P) * ES;
+    constexpr int RL = last_radix<P>(), NBL = P / RL, PER = P * C / TPB;
     extern __shared__ float2 sm[];
     float2* tD = sm;
     float2* tX = sm + TILE;
     const int q = blockIdx.y, u0 = blockIdx.x * C;
-    const float2* inD = b1 + (size_t)q * N * W;
-    const float2* inF = s2 + (size_t)q * N * W;
-    const float2* inG = s2 + (size_t)(B + q) * N * W;
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const float2* __restrict__ tw = p.tw_p;
+    const float2* inD = b1 + (size_t)q * N * W + u0 + c;
+    const float2* inF = s2 + (size_t)q * N * W + u0 + c;
+    const float2* inG = s2 + (size_t)(B + q) * N * W + u0 + c;
     const float2 zero = make_float2(0.f, 0.f);
-    for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
-        const int v = idx / C, c = idx % C, i = (v + N / 2) % P;
-        if (i < N) cp_async8(&tD[spad(v) * ES + c], &inD[(size_t)i * W + u0 + c]);
-        else tD[spad(v) * ES + c] = zero;
-        if (v < N) cp_async8(&tX[spad(v) * ES + c], &inG[(size_t)v * W + u0 + c]);
-        else tX[spad(v) * ES + c] = zero;
-    }
-    cp_async_wait_all();
+    // P-row v of D holds lag row i = (v + N/2) mod P (zero when i >= N)
+    first_pass_global2<P>(
+        tD + c, tX + c, ES, j,
+        [&](int v) {
+            const int i = v + N / 2 < P ? v + N / 2 : v + N / 2 - P;
+            return i < N ? __ldg(inD + (size_t)i * W) : zero;
+        },
+        [&](int v) { return v < N ? __ldg(inG + (size_t)v * W) : zero; });
     __syncthreads();
-    const int c = threadIdx.x / T, j = threadIdx.x % T;
-    fft<P, -1>(tD + c, ES, j, true, p.tw_p);
+    if constexpr (PL::NP == 3) fft_pass2<P, T, PL::R2, 16, -1>(tD + c, tX + c, ES, j, tw);
+    const bool col0 = blockIdx.x == 0;
+    if (col0) fft_pass2<P, T, RL, NBL, -1>(tD + c, tX + c, ES, j, tw);
 #pragma unroll 1
     for (int phase = 0; phase < 2; ++phase) {
-        fft<P, -1>(tX + c, ES, j, true, p.tw_p);
-        float2 qv[PER];
+        if (!col0) {
+            if (phase == 0)
+                fused_turn<P, 1>(tD + c, tX + c, ES, j, tw, [](float2 D, float2 X) { return c_cjmul(D, X); });
+            else
+                fused_turn<P, 2>(tD + c, tX + c, ES, j, tw, [](float2 D, float2 X) { return c_mul(D, X); });
+        } else {
+            if (phase == 1) fft_pass<P, T, RL, NBL, -1>(tX + c, ES, j, true, tw);
+            float2 qv[PER];
 #pragma unroll
-        for (int m = 0; m < PER; ++m) {
-            const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-            const float2 D = tD[spad(v) * ES + cc], X = tX[spad(v) * ES + cc];
-            if (u0 + cc == 0) {
-                const int vm = v == 0 ? 0 : P - v;
-                float2 ad, bd, ax, bx;
-                split0(D, tD[spad(vm) * ES + cc], ad, bd);
-                split0(X, tX[spad(vm) * ES + cc], ax, bx);
-                const float2 q0 = phase == 0 ? c_cjmul(ad, ax) : c_mul(ad, ax);
-                const float2 qn = phase == 0 ? c_cjmul(bd, bx) : c_mul(bd, bx);
-                qv[m] = make_float2(q0.x - qn.y, q0.y + qn.x);
-            } else {
-                qv[m] = phase == 0 ? c_cjmul(D, X) : c_mul(D, X);
+            for (int m = 0; m < PER; ++m) {
+                const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
+                const float2 D = tD[spad(v) * ES + cc], X = tX[spad(v) * ES + cc];
+                if (cc == 0) {
+                    const int vm = v == 0 ? 0 : P - v;
+                    float2 ad, bd, ax, bx;
+                    split0(D, tD[spad(vm) * ES + cc], ad, bd);
+                    split0(X, tX[spad(vm) * ES + cc], ax, bx);
+                    const float2 q0 = phase == 0 ? c_cjmul(ad, ax) : c_mul(ad, ax);
+                    const float2 qn = phase == 0 ? c_cjmul(bd, bx) : c_mul(bd, bx);
+                    qv[m] = make_float2(q0.x - qn.y, q0.y + qn.x);
+                } else {
+                    qv[m] = phase == 0 ? c_cjmul(D, X) : c_mul(D, X);
+                }
             }
-        }
-        __syncthreads();
+            __syncthreads();
 #pragma unroll
-        for (int m = 0; m < PER; ++m) {
-            const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-            tX[spad(v) * ES + cc] = qv[m];
+            for (int m = 0; m < PER; ++m) {
+                const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
+                tX[spad(v) * ES + cc] = qv[m];
+            }
+            __syncthreads();
+            fft_pass<P, T, RL, 1, +1>(tX + c, ES, j, true, tw);
         }
-        __syncthreads();
-        fft<P, +1>(tX + c, ES, j, true, p.tw_p);
-        float2* o = b2 + (size_t)(phase * B + q) * N * W;
-        for (int idx = threadIdx.x; idx < N * C; idx += TPB) {
-            const int y = idx / C, cc = idx % C;
-            o[(size_t)y * W + u0 + cc] = tX[spad(y) * ES + cc];
-        }
+        float2* o = b2 + (size_t)(phase * B + q) * N * W + u0 + c;
+        inverse_rest_global<P>(tX + c, ES, j, tw, [&](int y, float2 v) {
+            if (y < N) o[(size_t)y * W] = v;
+        });
         if (phase == 0) {
+            __syncthreads();   // every thread has read tX
+            first_pass_global<P>(tX + c, ES, j, [&](int v) { return v < N ? __ldg(inF + (size_t)v * W) : zero; });
             __syncthreads();
-            for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
-                const int v = idx / C, cc = idx % C;
-                if (v < N) cp_async8(&tX[spad(v) * ES + cc], &inF[(size_t)v * W + u0 + cc]);
-                else tX[spad(v) * ES + cc] = zero;
-            }
-            cp_async_wait_all();
-            __syncthreads();
+            if constexpr (PL::NP == 3) fft_pass<P, T, PL::R2, 16, -1>(tX + c, ES, j, true, tw);
         }
     }
 }
@@ -705,7 +714,7 @@ cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, in
 
 template <int L> constexpr size_t b_smem_rows() { return (size_t)(tpb_for(L) / FftPlan<L>::T) * spad(L) * sizeof(float2); }
 template <int P> constexpr size_t b_smem_cols() {
-    return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T + 1) * sizeof(float2);
+    return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T) * sizeof(float2);
 }
 template <int N> constexpr size_t b_smem_s1cols() {
     return ((size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) + spad(N)) * sizeof(float2);

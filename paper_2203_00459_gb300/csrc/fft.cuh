@@ -299,6 +299,117 @@ __device__ __forceinline__ void fft(float2* buf, int es, int j, bool active, con
     else fft_passes<L, PL::T, S, 1, 16, PL::R2, PL::R3>(buf, es, j, active, tw);
 }
 
+// ---------------------------------------------------------------------------------------------
+// column transforms fed from and stored to global memory
+// ---------------------------------------------------------------------------------------------
+//
+// A tile holds C columns interleaved element by element (element i of column c at
+// buf[spad(i) * C + c]); thread (c, j) of the tile is column c's thread j < T.
+
+// The forward first pass (radix 16, no twiddles) of two columns whose inputs come from global
+// memory: thread j loads x[j + t T], t < 16, through load0(pos) and load1(pos) (all 32 loads in
+// flight before the first use) and writes the outputs to the tiles.
+template <int L, class Load0, class Load1>
+__device__ __forceinline__ void first_pass_global2(float2* b0, float2* b1, int es, int j, Load0 load0, Load1 load1) {
+    constexpr int T = FftPlan<L>::T;
+    float2 v[16], w[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        v[t] = load0(j + t * T);
+        w[t] = load1(j + t * T);
+    }
+    dft16<-1>(v);
+    dft16<-1>(w);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        b0[spad(16 * j + t) * es] = v[t];
+        b1[spad(16 * j + t) * es] = w[t];
+    }
+}
+
+template <int L, class Load>
+__device__ __forceinline__ void first_pass_global(float2* b0, int es, int j, Load load) {
+    constexpr int T = FftPlan<L>::T;
+    float2 v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = load(j + t * T);
+    dft16<-1>(v);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) b0[spad(16 * j + t) * es] = v[t];
+}
+
+// The forward transform's last pass of two columns, their pointwise product and the inverse
+// transform's first pass, in registers.  With the inverse in the reverse radix order, the forward's
+// last pass (radix RL, stride L / RL) writes exactly the positions b + t L/RL that it reads, and
+// the inverse's first pass (radix RL, no twiddles) reads them: one thread owns a butterfly from
+// the forward through the product to the inverse.  MODE_A = 0: a is transformed here; 1: a is
+// transformed here and its final values are stored back in place (same thread, same positions,
+// no barrier needed); 2: a already holds its final values.  prod(A, X) gives the product; the
+// inverse first pass's outputs go to tb.  Every thread of the CTA must call it.
+template <int L, int MODE_A, class Prod>
+__device__ __forceinline__ void fused_turn(float2* ta, float2* tb, int es, int j, const float2* __restrict__ tw,
+                                           Prod prod) {
+    using PL = FftPlan<L>;
+    constexpr int T = PL::T, RL = PL::NP == 3 ? PL::R3 : PL::R2, NBL = L / RL, BPL = (NBL + T - 1) / T;
+    float2 o[BPL][RL];
+#pragma unroll
+    for (int m = 0; m < BPL; ++m) {
+        const int b = j + m * T;
+        if (NBL % T == 0 || b < NBL) {
+            float2 a[RL], x[RL];
+#pragma unroll
+            for (int t = 0; t < RL; ++t) {
+                a[t] = ta[spad(b + t * NBL) * es];
+                x[t] = tb[spad(b + t * NBL) * es];
+            }
+            if constexpr (MODE_A != 2) {
+                twiddle<L, RL, NBL, -1>(a, b, tw);
+                dft<RL, -1>(a);
+                if constexpr (MODE_A == 1) {
+#pragma unroll
+                    for (int t = 0; t < RL; ++t) ta[spad(b + t * NBL) * es] = a[t];
+                }
+            }
+            twiddle<L, RL, NBL, -1>(x, b, tw);
+            dft<RL, -1>(x);
+#pragma unroll
+            for (int t = 0; t < RL; ++t) o[m][t] = prod(a[t], x[t]);
+            dft<RL, +1>(o[m]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < BPL; ++m) {
+        const int b = j + m * T;
+        if (NBL % T == 0 || b < NBL) {
+#pragma unroll
+            for (int t = 0; t < RL; ++t) tb[spad(RL * b + t) * es] = o[m][t];
+        }
+    }
+    __syncthreads();
+}
+
+// The inverse transform's remaining passes after fused_turn (or after its first pass): the middle
+// pass (three-pass plans), then the last pass (radix 16, stride T) with its outputs handed to
+// store(pos, value) instead of the tile.
+template <int L, class Store>
+__device__ __forceinline__ void inverse_rest_global(float2* buf, int es, int j, const float2* __restrict__ tw,
+                                                    Store store) {
+    using PL = FftPlan<L>;
+    constexpr int T = PL::T, RL = PL::NP == 3 ? PL::R3 : PL::R2;
+    if constexpr (PL::NP == 3) fft_pass<L, T, PL::R2, RL, +1>(buf, es, j, true, tw);
+    float2 v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = buf[spad(j + t * T) * es];
+    twiddle<L, 16, T, +1>(v, j, tw);
+    dft16<+1>(v);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) store(j + t * T, v[t]);
+}
+
+// Last radix of the forward plan and the stride of its pass.
+template <int L> __host__ __device__ constexpr int last_radix() { return FftPlan<L>::NP == 3 ? FftPlan<L>::R3 : FftPlan<L>::R2; }
+
 // Threads of a CTA that runs several length-L sequences side by side: a multiple of both the
 // group size and 32 (192 for the 3 * 2^k lengths, 256 otherwise).
 __host__ __device__ constexpr int tpb_for(int L) { return (L % 3 == 0) ? 192 : 256; }

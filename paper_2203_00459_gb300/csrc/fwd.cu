@@ -291,72 +291,24 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevP
                                                       float2* __restrict__ s3, int B) {
     using PL = FftPlan<P>;
     constexpr int T = PL::T, TPB = tpb_for(P), C = TPB / T, ES = C, W = P / 2, TILE = spad(P) * ES;
-    constexpr int RL = PL::NP == 3 ? PL::R3 : PL::R2;   // radix of the forward's last pass
-    constexpr int NBL = P / RL;                          // its butterflies (= its stride NS)
-    constexpr int BPL = (NBL + T - 1) / T;
+    constexpr int RL = last_radix<P>(), NBL = P / RL;
     extern __shared__ float2 sm[];
     float2* tf = sm;
     float2* tg = sm + TILE;
     const int q = blockIdx.y, u0 = blockIdx.x * C;
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const float2* __restrict__ tw = p.tw_p;
-    {   // forward pass 1 (radix 16, no twiddles) from global memory
-        const float2* inf = s2 + (size_t)q * N * W + u0 + c;
-        const float2* ing = s2 + (size_t)(B + q) * N * W + u0 + c;
-        float2 vf[16], vg[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            const int row = j + t * T;
-            if (row < N) {
-                vf[t] = __ldg(inf + (size_t)row * W);
-                vg[t] = __ldg(ing + (size_t)row * W);
-            } else {
-                vf[t] = make_float2(0.f, 0.f);
-                vg[t] = make_float2(0.f, 0.f);
-            }
-        }
-        dft16<-1>(vf);
-        dft16<-1>(vg);
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            tf[spad(16 * j + t) * ES + c] = vf[t];
-            tg[spad(16 * j + t) * ES + c] = vg[t];
-        }
-    }
+    const float2* inf = s2 + (size_t)q * N * W + u0 + c;
+    const float2* ing = s2 + (size_t)(B + q) * N * W + u0 + c;
+    // forward first pass from global memory (rows >= N are the zero pad)
+    first_pass_global2<P>(
+        tf + c, tg + c, ES, j,
+        [&](int v) { return v < N ? __ldg(inf + (size_t)v * W) : make_float2(0.f, 0.f); },
+        [&](int v) { return v < N ? __ldg(ing + (size_t)v * W) : make_float2(0.f, 0.f); });
     __syncthreads();
     if constexpr (PL::NP == 3) fft_pass2<P, T, PL::R2, 16, -1>(tf + c, tg + c, ES, j, tw);
     if (blockIdx.x != 0) {
-        // forward last pass, conj(F') G and the inverse's first pass (no twiddles) in registers
-        float2 o[BPL][RL];
-#pragma unroll
-        for (int m = 0; m < BPL; ++m) {
-            const int b = j + m * T;
-            if (NBL % T == 0 || b < NBL) {
-                float2 a[RL], g[RL];
-#pragma unroll
-                for (int t = 0; t < RL; ++t) {
-                    a[t] = tf[spad(b + t * NBL) * ES + c];
-                    g[t] = tg[spad(b + t * NBL) * ES + c];
-                }
-                twiddle<P, RL, NBL, -1>(a, b, tw);
-                dft<RL, -1>(a);
-                twiddle<P, RL, NBL, -1>(g, b, tw);
-                dft<RL, -1>(g);
-#pragma unroll
-                for (int t = 0; t < RL; ++t) o[m][t] = c_cjmul(a[t], g[t]);
-                dft<RL, +1>(o[m]);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < BPL; ++m) {
-            const int b = j + m * T;
-            if (NBL % T == 0 || b < NBL) {
-#pragma unroll
-                for (int t = 0; t < RL; ++t) tf[spad(RL * b + t) * ES + c] = o[m][t];
-            }
-        }
-        __syncthreads();
+        fused_turn<P, 0>(tf + c, tg + c, ES, j, tw, [](float2 F, float2 G) { return c_cjmul(F, G); });
     } else {
         // the tile holding column 0: last forward pass in shared memory, then the products with
         // the DC / Nyquist split (which pairs v with P - v), then the inverse's first pass
@@ -384,27 +336,18 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevP
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-            tf[spad(v) * ES + cc] = qv[m];
+            tg[spad(v) * ES + cc] = qv[m];
         }
         __syncthreads();
-        fft_pass<P, T, RL, 1, +1>(tf + c, ES, j, true, tw);
+        fft_pass<P, T, RL, 1, +1>(tg + c, ES, j, true, tw);
     }
-    if constexpr (PL::NP == 3) fft_pass<P, T, PL::R2, RL, +1>(tf + c, ES, j, true, tw);
-    {   // inverse last pass (radix 16, stride T) straight to the N kept lag rows in global memory
-        float2 v[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) v[t] = tf[spad(j + t * T) * ES + c];
-        twiddle<P, 16, T, +1>(v, j, tw);
-        dft16<+1>(v);
-        float2* out = s3 + (size_t)q * N * W + u0 + c;
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            // P-position j + t T holds lag s_y = pos (pos < P/2) or pos - P; lag row i = s_y + N/2
-            const int pos = j + t * T;
-            const int i = pos < P / 2 ? pos + N / 2 : pos - P + N / 2;
-            if (i >= 0 && i < N) out[(size_t)i * W] = v[t];
-        }
-    }
+    // inverse middle and last passes; P-position pos holds lag s_y = pos (pos < P/2) or pos - P,
+    // kept as lag row i = s_y + N/2 when 0 <= i < N
+    float2* out = s3 + (size_t)q * N * W + u0 + c;
+    inverse_rest_global<P>(tg + c, ES, j, tw, [&](int pos, float2 v) {
+        const int i = pos < P / 2 ? pos + N / 2 : pos - P + N / 2;
+        if (i >= 0 && i < N) out[(size_t)i * W] = v;
+    });
 }
 
 // Inverse real row FFTs (two lag rows per complex FFT, Hermitian extension of the packed half
