@@ -125,7 +125,8 @@ __device__ __forceinline__ float dcxy(const DevPlan& p, const float* r, float cv
 // ---------------------------------------------------------------------------------------------
 
 // Lag rows of D (row i holds s_y = i - N/2; column j sits at P-position (j - N/2) mod P), two
-// rows per complex FFT of length P, packed real-FFT output rows [N][P/2].
+// rows per complex FFT of length P, packed real-FFT output rows [N][P/2].  The first pass forms
+// d c_xy straight from global memory.
 template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long* __restrict__ tab,
                                                      const float* __restrict__ cxy, const float* __restrict__ bsc,
@@ -133,38 +134,29 @@ __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long*
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
+    const int k = threadIdx.x / T, jt = threadIdx.x % T, i = i0 + 2 * k;
     const long long pr = tab[3 * q + 2];
     const float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
     const float* r = bsc + (size_t)q * 16;
-    const float* c = cxy + (size_t)q * N * N;
-    #pragma unroll 4
-    for (int idx = threadIdx.x; idx < FPC * P; idx += TPB) {
-        const int k = idx / P, x = idx % P, j = (x + N / 2) % P, i = i0 + 2 * k;
+    const float* c = cxy + (size_t)q * N * N + (size_t)i * N;
+    first_pass_global<P>(sm + k * SL, 1, jt, [&](int x) {
+        const int j = x + N / 2 < P ? x + N / 2 : x + N / 2 - P;   // lag column at P-position x
         float2 v = make_float2(0.f, 0.f);
         if (j < N) {
-            v.x = dcxy(p, r, c[(size_t)i * N + j], i, j, N, dtx, dty);
-            v.y = dcxy(p, r, c[(size_t)(i + 1) * N + j], i + 1, j, N, dtx, dty);
+            v.x = dcxy(p, r, __ldg(c + j), i, j, N, dtx, dty);
+            v.y = dcxy(p, r, __ldg(c + N + j), i + 1, j, N, dtx, dty);
         }
-        sm[k * SL + spad(x)] = v;
-    }
+        return v;
+    });
     __syncthreads();
-    fft<P, -1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
+    fft_passes_from<P, -1, 2>(sm + k * SL, 1, jt, p.tw_p);
     float2* out = b1 + (size_t)q * N * W;
     for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
-        const int k = idx / W, u = idx % W, row = i0 + 2 * k;
-        const float2* Z = sm + k * SL;
-        float2 xa, xb;
-        if (u == 0) {
-            const float2 z0 = Z[0], zn = Z[spad(W)];
-            xa = make_float2(z0.x, zn.x);
-            xb = make_float2(z0.y, zn.y);
-        } else {
-            const float2 zu = Z[spad(u)], zm = Z[spad(P - u)];
-            xa = make_float2(0.5f * (zu.x + zm.x), 0.5f * (zu.y - zm.y));
-            xb = make_float2(0.5f * (zu.y + zm.y), -0.5f * (zu.x - zm.x));
-        }
-        out[(size_t)row * W + u] = xa;
-        out[(size_t)(row + 1) * W + u] = xb;
+        const int kk = idx / W, u = idx % W, row = i0 + 2 * kk;
+        const float2* Z = sm + kk * SL;
+        const float2 zu = Z[spad(u)], zm = Z[spad(u == 0 ? W : P - u)];
+        out[(size_t)row * W + u] = unpack_half(zu, zm, u == 0, false);
+        out[(size_t)(row + 1) * W + u] = unpack_half(zu, zm, u == 0, true);
     }
 }
 
@@ -259,7 +251,8 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_b_cols(DevPl
 }
 
 // Inverse row FFTs of the two adjoint spectra, keep x in [0, N), scale 1/P^2:
-// z = 0 -> d f' (workspace), z = 1 -> d g (stage-2 part, written to the caller's buffer).
+// z = 0 -> d f' (workspace), z = 1 -> d g (stage-2 part, written to the caller's buffer).  The
+// first pass builds its inputs from global memory and the last pass stores straight to it.
 template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* __restrict__ tab,
                                                     const float2* __restrict__ b2, float* __restrict__ gfr,
@@ -267,30 +260,18 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, i0 = blockIdx.x * FPC * 2;
-    const float2* in = b2 + (size_t)(s * B + q) * N * W;
-    #pragma unroll 4
-    for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
-        const int k = idx / W, u = idx % W;
-        const float2 a = in[(size_t)(i0 + 2 * k) * W + u], b = in[(size_t)(i0 + 2 * k + 1) * W + u];
-        float2* Z = sm + k * SL;
-        if (u == 0) {
-            Z[0] = make_float2(a.x, b.x);
-            Z[spad(W)] = make_float2(a.y, b.y);
-        } else {
-            Z[spad(u)] = make_float2(a.x - b.y, a.y + b.x);
-            Z[spad(P - u)] = make_float2(a.x + b.y, b.x - a.y);
-        }
-    }
+    const int k = threadIdx.x / T, j = threadIdx.x % T, y = i0 + 2 * k;
+    const float2* ra = b2 + ((size_t)(s * B + q) * N + y) * W;
+    first_pass_global<P, +1>(sm + k * SL, 1, j, [&](int x) { return pack_inverse(ra, ra + W, x, P); });
     __syncthreads();
-    fft<P, +1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
     const float scale = 1.f / ((float)P * (float)P);
-    float* out = s == 0 ? gfr + (size_t)q * N * N : dg + tab[3 * q];
-    for (int idx = threadIdx.x; idx < FPC * N; idx += TPB) {
-        const int k = idx / N, x = idx % N;
-        const float2 z = sm[k * SL + spad(x)];
-        out[(size_t)(i0 + 2 * k) * N + x] = z.x * scale;
-        out[(size_t)(i0 + 2 * k + 1) * N + x] = z.y * scale;
-    }
+    float* out = (s == 0 ? gfr + (size_t)q * N * N : dg + tab[3 * q]) + (size_t)y * N;
+    rest_global<P, +1>(sm + k * SL, 1, j, p.tw_p, [&](int x, float2 z) {
+        if (x < N) {
+            out[x] = z.x * scale;
+            out[N + x] = z.y * scale;
+        }
+    });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -640,35 +621,22 @@ __global__ void __launch_bounds__(kThreads) k_b_s1rows(DevPlan p, const long lon
     constexpr int T = FftPlan<N>::T, FPC = kThreads / T, SL = spad(N), W = N / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
-    const float2* in = gs1 + (size_t)(s * B + q) * N * W;
-    #pragma unroll 4
-    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
-        const int k = idx / W, u = idx % W;
-        const float2 a = in[(size_t)(r0 + 2 * k) * W + u], b = in[(size_t)(r0 + 2 * k + 1) * W + u];
-        float2* Z = sm + k * SL;
-        if (u == 0) {
-            Z[0] = make_float2(a.x, b.x);
-            Z[spad(W)] = make_float2(a.y, b.y);
-        } else {
-            Z[spad(u)] = make_float2(a.x - b.y, a.y + b.x);
-            Z[spad(N - u)] = make_float2(a.x + b.y, b.x - a.y);
-        }
-    }
+    const int k = threadIdx.x / T, j = threadIdx.x % T, y = r0 + 2 * k;
+    const float2* ra = gs1 + ((size_t)(s * B + q) * N + y) * W;
+    first_pass_global<N, +1>(sm + k * SL, 1, j, [&](int x) { return pack_inverse(ra, ra + W, x, N); });
     __syncthreads();
-    fft<N, +1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_n);
-    float* out = (s ? dg : df) + tab[3 * q];
-    for (int idx = threadIdx.x; idx < FPC * N; idx += kThreads) {
-        const int k = idx / N, x = idx % N, y = r0 + 2 * k;
-        const float2 z = sm[k * SL + spad(x)];
+    float* out = (s ? dg : df) + tab[3 * q] + (size_t)y * N;
+    const float wa = p.window ? __ldg(&p.win[y]) : 1.f, wb = p.window ? __ldg(&p.win[y + 1]) : 1.f;
+    rest_global<N, +1>(sm + k * SL, 1, j, p.tw_n, [&](int x, float2 z) {
         float va = z.x, vb = z.y;
         if (p.window) {
             const float wx = __ldg(&p.win[x]);
-            va *= __ldg(&p.win[y]) * wx;
-            vb *= __ldg(&p.win[y + 1]) * wx;
+            va *= wa * wx;
+            vb *= wb * wx;
         }
-        out[(size_t)y * N + x] += va;
-        out[(size_t)(y + 1) * N + x] += vb;
-    }
+        out[x] += va;
+        out[N + x] += vb;
+    });
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -309,7 +309,7 @@ __device__ __forceinline__ void fft(float2* buf, int es, int j, bool active, con
 // The forward first pass (radix 16, no twiddles) of two columns whose inputs come from global
 // memory: thread j loads x[j + t T], t < 16, through load0(pos) and load1(pos) (all 32 loads in
 // flight before the first use) and writes the outputs to the tiles.
-template <int L, class Load0, class Load1>
+template <int L, int S = -1, class Load0, class Load1>
 __device__ __forceinline__ void first_pass_global2(float2* b0, float2* b1, int es, int j, Load0 load0, Load1 load1) {
     constexpr int T = FftPlan<L>::T;
     float2 v[16], w[16];
@@ -318,8 +318,8 @@ __device__ __forceinline__ void first_pass_global2(float2* b0, float2* b1, int e
         v[t] = load0(j + t * T);
         w[t] = load1(j + t * T);
     }
-    dft16<-1>(v);
-    dft16<-1>(w);
+    dft16<S>(v);
+    dft16<S>(w);
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
         b0[spad(16 * j + t) * es] = v[t];
@@ -327,13 +327,13 @@ __device__ __forceinline__ void first_pass_global2(float2* b0, float2* b1, int e
     }
 }
 
-template <int L, class Load>
+template <int L, int S = -1, class Load>
 __device__ __forceinline__ void first_pass_global(float2* b0, int es, int j, Load load) {
     constexpr int T = FftPlan<L>::T;
     float2 v[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) v[t] = load(j + t * T);
-    dft16<-1>(v);
+    dft16<S>(v);
 #pragma unroll
     for (int t = 0; t < 16; ++t) b0[spad(16 * j + t) * es] = v[t];
 }
@@ -405,6 +405,66 @@ __device__ __forceinline__ void inverse_rest_global(float2* buf, int es, int j, 
     dft16<+1>(v);
 #pragma unroll
     for (int t = 0; t < 16; ++t) store(j + t * T, v[t]);
+}
+
+// The passes after the first (FIRST = 2), in the plan's own radix order, in shared memory.
+template <int L, int S, int FIRST>
+__device__ __forceinline__ void fft_passes_from(float2* buf, int es, int j, const float2* __restrict__ tw) {
+    using PL = FftPlan<L>;
+    static_assert(FIRST == 2, "only the passes after the first");
+    if constexpr (PL::NP == 2) fft_pass<L, PL::T, PL::R2, 16, S>(buf, es, j, true, tw);
+    else fft_passes<L, PL::T, S, 16, PL::R2, PL::R3>(buf, es, j, true, tw);
+}
+
+// The middle pass (three-pass plans) and the last pass of a transform in the plan's own radix
+// order after first_pass_global; the last pass (radix RL, stride L / RL) hands its outputs to
+// store(pos, value), pos in natural order.
+template <int L, int S, class Store>
+__device__ __forceinline__ void rest_global(float2* buf, int es, int j, const float2* __restrict__ tw, Store store) {
+    using PL = FftPlan<L>;
+    constexpr int T = PL::T, RL = PL::NP == 3 ? PL::R3 : PL::R2, NBL = L / RL, BPL = (NBL + T - 1) / T;
+    if constexpr (PL::NP == 3) fft_pass<L, T, PL::R2, 16, S>(buf, es, j, true, tw);
+#pragma unroll
+    for (int m = 0; m < BPL; ++m) {
+        const int b = j + m * T;
+        if (NBL % T == 0 || b < NBL) {
+            float2 v[RL];
+#pragma unroll
+            for (int t = 0; t < RL; ++t) v[t] = buf[spad(b + t * NBL) * es];
+            twiddle<L, RL, NBL, S>(v, b, tw);
+            dft<RL, S>(v);
+#pragma unroll
+            for (int t = 0; t < RL; ++t) store(b + t * NBL, v[t]);
+        }
+    }
+}
+
+// A packed pair of real rows, Z = FFT(x_a + i x_b) of length L, gives the half spectra
+// X_a[u] = (Z[u] + conj Z[L-u]) / 2 and X_b[u] = (Z[u] - conj Z[L-u]) / 2i.  Column u = 0 of the
+// half spectra packs the real DC and Nyquist values (X[0], X[L/2]) as one complex number.
+// zu = Z[u], zm = Z[u == 0 ? L/2 : L - u]; odd selects X_b.
+__device__ __forceinline__ float2 unpack_half(float2 zu, float2 zm, bool u0, bool odd) {
+    if (u0) return odd ? make_float2(zu.y, zm.y) : make_float2(zu.x, zm.x);
+    return odd ? make_float2(0.5f * (zu.y + zm.y), -0.5f * (zu.x - zm.x))
+               : make_float2(0.5f * (zu.x + zm.x), 0.5f * (zu.y - zm.y));
+}
+
+// Z[x] of the packed inverse transform of two half spectra A (row ra) and B (row rb), columns
+// u in [0, L/2) with column 0 holding (DC, Nyquist): Z[x] = A[x] + i B[x] under the Hermitian
+// extension A[L - u] = conj A[u], so that the inverse of Z is a + i b for the real rows a, b.
+__device__ __forceinline__ float2 pack_inverse(const float2* __restrict__ ra, const float2* __restrict__ rb, int x,
+                                               int L) {
+    const int W = L / 2;
+    if (x == 0 || x == W) {
+        const float2 a = __ldg(ra), b = __ldg(rb);
+        return x == 0 ? make_float2(a.x, b.x) : make_float2(a.y, b.y);
+    }
+    if (x < W) {
+        const float2 a = __ldg(ra + x), b = __ldg(rb + x);
+        return make_float2(a.x - b.y, a.y + b.x);
+    }
+    const float2 a = __ldg(ra + (L - x)), b = __ldg(rb + (L - x));
+    return make_float2(a.x + b.y, b.x - a.y);
 }
 
 // Last radix of the forward plan and the stride of its pass.

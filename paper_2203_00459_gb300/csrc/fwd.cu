@@ -24,50 +24,30 @@ namespace fmbym {
 
 // Hann-windowed real row FFTs of f (z = 0) and g (z = 1).  Rows 2k and 2k+1 share one complex
 // FFT; the output row keeps u in [0, N/2) with the real DC and Nyquist values packed in u = 0.
+// The first pass takes the windowed samples straight from global memory.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_s1_rows(DevPlan p, const long long* __restrict__ tab,
                                                       const float* __restrict__ f, const float* __restrict__ g,
                                                       float2* __restrict__ s1, int B) {
     constexpr int T = FftPlan<N>::T, FPC = kThreads / T, SL = spad(N), W = N / 2;
     extern __shared__ float2 sm[];
-    const int q = blockIdx.y, s = blockIdx.z;
-    const float* __restrict__ src = (s ? g : f) + tab[3 * q];
-    const int r0 = blockIdx.x * FPC * 2;
-    #pragma unroll 4
-    for (int idx = threadIdx.x; idx < FPC * 2 * (N / 4); idx += kThreads) {
-        const int rr = idx / (N / 4), x4 = (idx % (N / 4)) * 4, row = r0 + rr;
-        float4 v = __ldg(reinterpret_cast<const float4*>(src + (size_t)row * N + x4));
-        if (p.window) {
-            const float wr = __ldg(&p.win[row]);
-            v.x *= wr * __ldg(&p.win[x4]);
-            v.y *= wr * __ldg(&p.win[x4 + 1]);
-            v.z *= wr * __ldg(&p.win[x4 + 2]);
-            v.w *= wr * __ldg(&p.win[x4 + 3]);
-        }
-        float* base = reinterpret_cast<float*>(sm + (rr >> 1) * SL) + (rr & 1);
-        base[2 * spad(x4)] = v.x;
-        base[2 * spad(x4 + 1)] = v.y;
-        base[2 * spad(x4 + 2)] = v.z;
-        base[2 * spad(x4 + 3)] = v.w;
-    }
+    const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
+    const int k = threadIdx.x / T, j = threadIdx.x % T, r = r0 + 2 * k;
+    const float* __restrict__ rp = (s ? g : f) + tab[3 * q] + (size_t)r * N;
+    const float wa = p.window ? __ldg(&p.win[r]) : 1.f, wb = p.window ? __ldg(&p.win[r + 1]) : 1.f;
+    first_pass_global<N>(sm + k * SL, 1, j, [&](int x) {
+        const float wx = p.window ? __ldg(&p.win[x]) : 1.f;
+        return make_float2(__ldg(rp + x) * (wa * wx), __ldg(rp + N + x) * (wb * wx));
+    });
     __syncthreads();
-    fft<N, -1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_n);
+    fft_passes_from<N, -1, 2>(sm + k * SL, 1, j, p.tw_n);
     float2* out = s1 + (size_t)(s * B + q) * N * W;
     for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
-        const int k = idx / W, u = idx % W, row = r0 + 2 * k;
-        const float2* Z = sm + k * SL;
-        float2 xa, xb;
-        if (u == 0) {
-            const float2 z0 = Z[0], zn = Z[spad(W)];
-            xa = make_float2(z0.x, zn.x);
-            xb = make_float2(z0.y, zn.y);
-        } else {
-            const float2 zu = Z[spad(u)], zm = Z[spad(N - u)];
-            xa = make_float2(0.5f * (zu.x + zm.x), 0.5f * (zu.y - zm.y));
-            xb = make_float2(0.5f * (zu.y + zm.y), -0.5f * (zu.x - zm.x));
-        }
-        out[(size_t)row * W + u] = xa;
-        out[(size_t)(row + 1) * W + u] = xb;
+        const int kk = idx / W, u = idx % W, row = r0 + 2 * kk;
+        const float2* Z = sm + kk * SL;
+        const float2 zu = Z[spad(u)], zm = Z[spad(u == 0 ? W : N - u)];
+        out[(size_t)row * W + u] = unpack_half(zu, zm, u == 0, false);
+        out[(size_t)(row + 1) * W + u] = unpack_half(zu, zm, u == 0, true);
     }
 }
 
@@ -219,59 +199,40 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
 
 // Rows of the rotated source f' (z = 0, rotation on load) and of g (z = 1), zero-padded to P,
 // real row FFTs packed two rows per complex FFT, output u in [0, P/2) (DC/Nyquist packed in 0).
+// The first pass takes its inputs straight from the gather (no staging in shared memory).
 template <int N, int P>
-__global__ void __launch_bounds__(kThreads) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
-                                                      const float* __restrict__ f, const float* __restrict__ g,
-                                                      const float* __restrict__ th, float2* __restrict__ s2, int B) {
+__global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
+                                                        const float* __restrict__ f, const float* __restrict__ g,
+                                                        const float* __restrict__ th, float2* __restrict__ s2, int B) {
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
+    const int k = threadIdx.x / T, j = threadIdx.x % T;
+    const int r = r0 + 2 * k;                                 // rows r and r + 1
     const float* __restrict__ src = (s ? g : f) + tab[3 * q];
     if (s == 0) {
         const float* t = th + 8 * q;
         const float ch = t[1], cl = t[2], sh = t[3], sl = t[4];
-        #pragma unroll 4
-        for (int idx = threadIdx.x; idx < FPC * 2 * N; idx += TPB) {
-            const int rr = idx / N, x = idx % N;
-            const float v = rotated_sample(src, N, x, r0 + rr, ch, cl, sh, sl);
-            reinterpret_cast<float*>(sm + (rr >> 1) * SL + spad(x))[rr & 1] = v;
-        }
+        first_pass_global<P>(sm + k * SL, 1, j, [&](int x) {
+            return x < N ? make_float2(rotated_sample(src, N, x, r, ch, cl, sh, sl),
+                                       rotated_sample(src, N, x, r + 1, ch, cl, sh, sl))
+                         : make_float2(0.f, 0.f);
+        });
     } else {
-        #pragma unroll 4
-        for (int idx = threadIdx.x; idx < FPC * 2 * (N / 4); idx += TPB) {
-            const int rr = idx / (N / 4), x4 = (idx % (N / 4)) * 4;
-            const float4 v = __ldg(reinterpret_cast<const float4*>(src + (size_t)(r0 + rr) * N + x4));
-            float* base = reinterpret_cast<float*>(sm + (rr >> 1) * SL) + (rr & 1);
-            base[2 * spad(x4)] = v.x;
-            base[2 * spad(x4 + 1)] = v.y;
-            base[2 * spad(x4 + 2)] = v.z;
-            base[2 * spad(x4 + 3)] = v.w;
-        }
-    }
-    if constexpr (P > N) {
-        for (int idx = threadIdx.x; idx < FPC * (P - N); idx += TPB) {
-            const int k = idx / (P - N), x = N + idx % (P - N);
-            sm[k * SL + spad(x)] = make_float2(0.f, 0.f);
-        }
+        const float* rp = src + (size_t)r * N;
+        first_pass_global<P>(sm + k * SL, 1, j, [&](int x) {
+            return x < N ? make_float2(__ldg(rp + x), __ldg(rp + N + x)) : make_float2(0.f, 0.f);
+        });
     }
     __syncthreads();
-    fft<P, -1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
+    fft_passes_from<P, -1, 2>(sm + k * SL, 1, j, p.tw_p);
     float2* out = s2 + (size_t)(s * B + q) * N * W;
     for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
-        const int k = idx / W, u = idx % W, row = r0 + 2 * k;
-        const float2* Z = sm + k * SL;
-        float2 xa, xb;
-        if (u == 0) {
-            const float2 z0 = Z[0], zn = Z[spad(W)];
-            xa = make_float2(z0.x, zn.x);
-            xb = make_float2(z0.y, zn.y);
-        } else {
-            const float2 zu = Z[spad(u)], zm = Z[spad(P - u)];
-            xa = make_float2(0.5f * (zu.x + zm.x), 0.5f * (zu.y - zm.y));
-            xb = make_float2(0.5f * (zu.y + zm.y), -0.5f * (zu.x - zm.x));
-        }
-        out[(size_t)row * W + u] = xa;
-        out[(size_t)(row + 1) * W + u] = xb;
+        const int kk = idx / W, u = idx % W, row = r0 + 2 * kk;
+        const float2* Z = sm + kk * SL;
+        const float2 zu = Z[spad(u)], zm = Z[spad(u == 0 ? W : P - u)];
+        out[(size_t)row * W + u] = unpack_half(zu, zm, u == 0, false);
+        out[(size_t)(row + 1) * W + u] = unpack_half(zu, zm, u == 0, true);
     }
 }
 
@@ -352,7 +313,9 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevP
 
 // Inverse real row FFTs (two lag rows per complex FFT, Hermitian extension of the packed half
 // rows), keep the N lag columns s_x in [-N/2, N/2), scale by 1/P^2 -> c_xy.  Each block also
-// writes the mean, sum of squared deviations and maximum of its scores for the z-score.
+// writes the mean, sum of squared deviations and maximum of its scores for the z-score.  The
+// first pass builds its inputs from global memory and the last pass stores the kept columns
+// straight to global memory (and to the tile, for the second statistics pass).
 template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long* __restrict__ tab,
                                                      const float2* __restrict__ s3, float* __restrict__ cxy_ws,
@@ -361,42 +324,34 @@ __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long*
     extern __shared__ float2 sm[];
     __shared__ float red[32];
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
-    const float2* in = s3 + (size_t)q * N * W;
-    #pragma unroll 4
-    for (int idx = threadIdx.x; idx < FPC * W; idx += TPB) {
-        const int k = idx / W, u = idx % W;
-        const float2 a = in[(size_t)(i0 + 2 * k) * W + u], b = in[(size_t)(i0 + 2 * k + 1) * W + u];
-        float2* Z = sm + k * SL;
-        if (u == 0) {
-            Z[0] = make_float2(a.x, b.x);
-            Z[spad(W)] = make_float2(a.y, b.y);
-        } else {
-            Z[spad(u)] = make_float2(a.x - b.y, a.y + b.x);
-            Z[spad(P - u)] = make_float2(a.x + b.y, b.x - a.y);
-        }
-    }
+    const int k = threadIdx.x / T, j = threadIdx.x % T, i = i0 + 2 * k;
+    const float2* ra = s3 + ((size_t)q * N + i) * W;
+    float2* buf = sm + k * SL;
+    first_pass_global<P, +1>(buf, 1, j, [&](int x) { return pack_inverse(ra, ra + W, x, P); });
     __syncthreads();
-    fft<P, +1>(sm + (threadIdx.x / T) * SL, 1, threadIdx.x % T, true, p.tw_p);
     const float scale = 1.f / ((float)P * (float)P);
-    float* out = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N;
+    float* out = (cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N) + (size_t)i * N;
     float lsum = 0.f, lmax = -FLT_MAX;
-    for (int idx = threadIdx.x; idx < FPC * N; idx += TPB) {
-        const int k = idx / N, jj = idx % N, nn = (jj - N / 2 + P) % P;
-        const float2 z = sm[k * SL + spad(nn)];
-        const float va = z.x * scale, vb = z.y * scale;
-        out[(size_t)(i0 + 2 * k) * N + jj] = va;
-        out[(size_t)(i0 + 2 * k + 1) * N + jj] = vb;
-        lsum += va + vb;
-        lmax = fmaxf(lmax, fmaxf(va, vb));
-    }
+    // P-position pos holds lag s_x = pos (pos < P/2) or pos - P; column jj = s_x + N/2
+    rest_global<P, +1>(buf, 1, j, p.tw_p, [&](int pos, float2 z) {
+        if (pos < N / 2 || pos >= P - N / 2) {
+            const int jj = pos < N / 2 ? pos + N / 2 : pos - P + N / 2;
+            const float va = z.x * scale, vb = z.y * scale;
+            out[jj] = va;
+            out[N + jj] = vb;
+            lsum += va + vb;
+            lmax = fmaxf(lmax, fmaxf(va, vb));
+            buf[spad(pos)] = make_float2(va, vb);   // same position the last pass read: no race
+        }
+    });
     constexpr float cnt = (float)(FPC * 2 * N);
     const float mean = block_reduce<false>(lsum, red) * (1.f / cnt);
     const float bmax = block_reduce<true>(lmax, red);
     float lm2 = 0.f;
     for (int idx = threadIdx.x; idx < FPC * N; idx += TPB) {
-        const int k = idx / N, jj = idx % N, nn = (jj - N / 2 + P) % P;
-        const float2 z = sm[k * SL + spad(nn)];
-        const float da = z.x * scale - mean, db = z.y * scale - mean;
+        const int kk = idx / N, jj = idx % N, nn = (jj - N / 2 + P) % P;
+        const float2 z = sm[kk * SL + spad(nn)];
+        const float da = z.x - mean, db = z.y - mean;
         lm2 += da * da + db * db;
     }
     const float m2 = block_reduce<false>(lm2, red);
