@@ -295,58 +295,63 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
                                                     unsigned* __restrict__ cnt, float* __restrict__ bsc) {
     __shared__ float red[32];
     __shared__ bool last;
-    constexpr int NB = N * N / kThreads;
+    constexpr int NB = N * N / (kThreads * kRotPixels);
     const int q = blockIdx.y;
     const float* t = th + 8 * q;
     const float ch = t[1], cl = t[2], sh = t[3], sl = t[4];
     const float c = 0.5f * N;
     const float* src = f + tab[3 * q];
     const float* d = gfr + (size_t)q * N * N;
-    const int idx = blockIdx.x * kThreads + threadIdx.x;
-    const int Y = idx / N, X = idx % N;
-    // (a) d theta at output pixel X
-    float contrib;
-    {
-        int x0, y0;
-        float fx, fy;
-        rot_coord(ch, cl, (float)X - c, sh, sl, (float)Y - c, c, x0, fx);
-        rot_coord(ch, cl, (float)Y - c, -sh, -sl, (float)X - c, c, y0, fy);
-        auto at = [&](int yy, int xx) {
-            return ((unsigned)yy < (unsigned)N && (unsigned)xx < (unsigned)N) ? __ldg(src + (size_t)yy * N + xx) : 0.f;
-        };
-        const float v00 = at(y0, x0), v01 = at(y0, x0 + 1), v10 = at(y0 + 1, x0), v11 = at(y0 + 1, x0 + 1);
-        const float dvx = (1.f - fy) * (v01 - v00) + fy * (v11 - v10);
-        const float dvy = (1.f - fx) * (v10 - v00) + fx * (v11 - v01);
-        const float pxc = ((float)x0 - c) + fx, pyc = ((float)y0 - c) + fy;
-        contrib = d[idx] * (dvx * pyc - dvy * pxc);
-    }
-    // (b) d f at source pixel (X, Y).  Its image X0 = c + R(theta)(y - c) (error-free coordinates);
-    // a candidate output pixel M samples at y + R(-theta)(M - X0), so its bilinear weight on y is the
-    // tent (1 - |dx|)(1 - |dy|) of (dx, dy) = R(-theta)(M - X0), small numbers exact to ~1e-7
-    {
-        int ix, iy;
-        float fx, fy;
-        rot_coord(ch, cl, (float)X - c, -sh, -sl, (float)Y - c, c, ix, fx);  // c + cos dx - sin dy
-        rot_coord(sh, sl, (float)X - c, ch, cl, (float)Y - c, c, iy, fy);    // c + sin dx + cos dy
-        const int mx0 = ix + (fx >= 0.5f ? 1 : 0) - 1, my0 = iy + (fy >= 0.5f ? 1 : 0) - 1;
-        const float ct = ch + cl, stn = sh + sl;
-        float acc = 0.f;
+    float contrib = 0.f;
 #pragma unroll
-        for (int oy = 0; oy < 3; ++oy) {
-            const int my = my0 + oy;
-            if ((unsigned)my >= (unsigned)N) continue;
-            const float ey = (float)(my - iy) - fy;
-#pragma unroll
-            for (int ox = 0; ox < 3; ++ox) {
-                const int mx = mx0 + ox;
-                if ((unsigned)mx >= (unsigned)N) continue;
-                const float ex = (float)(mx - ix) - fx;
-                const float dx = fmaf(ct, ex, stn * ey), dy = fmaf(ct, ey, -stn * ex);
-                const float wx = 1.f - fabsf(dx), wy = 1.f - fabsf(dy);
-                if (wx > 0.f && wy > 0.f) acc += wy * wx * d[(size_t)my * N + mx];
-            }
+    for (int m = 0; m < kRotPixels; ++m) {
+        const int idx = (blockIdx.x * kRotPixels + m) * kThreads + threadIdx.x;
+        const int Y = idx / N, X = idx % N;
+        // (a) d theta at output pixel X
+        {
+            int x0, y0;
+            float fx, fy;
+            rot_coord(ch, cl, (float)X - c, sh, sl, (float)Y - c, c, x0, fx);
+            rot_coord(ch, cl, (float)Y - c, -sh, -sl, (float)X - c, c, y0, fy);
+            auto at = [&](int yy, int xx) {
+                return ((unsigned)yy < (unsigned)N && (unsigned)xx < (unsigned)N) ? __ldg(src + (size_t)yy * N + xx)
+                                                                                  : 0.f;
+            };
+            const float v00 = at(y0, x0), v01 = at(y0, x0 + 1), v10 = at(y0 + 1, x0), v11 = at(y0 + 1, x0 + 1);
+            const float dvx = (1.f - fy) * (v01 - v00) + fy * (v11 - v10);
+            const float dvy = (1.f - fx) * (v10 - v00) + fx * (v11 - v01);
+            const float pxc = ((float)x0 - c) + fx, pyc = ((float)y0 - c) + fy;
+            contrib += __ldg(d + idx) * (dvx * pyc - dvy * pxc);
         }
-        df[tab[3 * q] + idx] = acc;
+        // (b) d f at source pixel (X, Y).  Its image X0 = c + R(theta)(y - c) (error-free
+        // coordinates); a candidate output pixel M samples at y + R(-theta)(M - X0), so its
+        // bilinear weight on y is the tent (1 - |dx|)(1 - |dy|) of (dx, dy) = R(-theta)(M - X0),
+        // small numbers exact to ~1e-7
+        {
+            int ix, iy;
+            float fx, fy;
+            rot_coord(ch, cl, (float)X - c, -sh, -sl, (float)Y - c, c, ix, fx);  // c + cos dx - sin dy
+            rot_coord(sh, sl, (float)X - c, ch, cl, (float)Y - c, c, iy, fy);    // c + sin dx + cos dy
+            const int mx0 = ix + (fx >= 0.5f ? 1 : 0) - 1, my0 = iy + (fy >= 0.5f ? 1 : 0) - 1;
+            const float ct = ch + cl, stn = sh + sl;
+            float acc = 0.f;
+#pragma unroll
+            for (int oy = 0; oy < 3; ++oy) {
+                const int my = my0 + oy;
+                if ((unsigned)my >= (unsigned)N) continue;
+                const float ey = (float)(my - iy) - fy;
+#pragma unroll
+                for (int ox = 0; ox < 3; ++ox) {
+                    const int mx = mx0 + ox;
+                    if ((unsigned)mx >= (unsigned)N) continue;
+                    const float ex = (float)(mx - ix) - fx;
+                    const float dx = fmaf(ct, ex, stn * ey), dy = fmaf(ct, ey, -stn * ex);
+                    const float wx = 1.f - fabsf(dx), wy = 1.f - fabsf(dy);
+                    if (wx > 0.f && wy > 0.f) acc += wy * wx * __ldg(d + (size_t)my * N + mx);
+                }
+            }
+            df[tab[3 * q] + idx] = acc;
+        }
     }
     const float bs = block_reduce<false>(contrib, red);
     if (threadIdx.x == 0) {
@@ -716,7 +721,7 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     w.tr->before(K_B_C2R, st);
     k_b_c2r<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st>>>(p, tab, w.b2, w.gfr, dg, B);
     w.tr->before(K_B_ROT, st);
-    k_b_rot<N><<<dim3(N * N / kThreads, B), kThreads, 0, st>>>(p, tab, f, w.th, w.gfr, dpose, df, w.gpart, w.cnt,
+    k_b_rot<N><<<dim3(N * N / (kThreads * kRotPixels), B), kThreads, 0, st>>>(p, tab, f, w.th, w.gfr, dpose, df, w.gpart, w.cnt,
                                                               w.bsc);
     if (p.nt == 128) launch_stage1_adjoint<128>(p, w, B, st);
     else if (p.nt == 256) launch_stage1_adjoint<256>(p, w, B, st);

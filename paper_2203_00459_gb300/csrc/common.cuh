@@ -10,7 +10,8 @@
 namespace fmbym {
 
 constexpr int kThreads = 256;   // threads of the FFT kernels
-constexpr int kAngleRadii = 16; // radii per CTA of the angle-correlation kernel
+constexpr int kAngleRadii = 16;  // radii per CTA of the angle-correlation kernel
+constexpr int kRotPixels = 4;    // pixels per thread of the Rotate adjoint (one reduction per block)
 constexpr int kSplitXY = 8;     // CTAs per pair of the translation soft-argmax
 
 // One bilinear Cart2Pol sample: floor of the (u, v) frequency and the fractions.

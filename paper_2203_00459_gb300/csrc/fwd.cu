@@ -90,17 +90,23 @@ __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* _
 // Cart2Pol of both magnitudes for kAngleRadii radii, packed as z[a] = A_f[a] + i A_g[a], FFT along
 // angle, then S[k] = sum_r conj(A^_f[k, r]) A^_g[k, r] for this chunk of radii.  The inverse FFT of
 // S summed over chunks is the circular correlation along angle summed over radius (Eq. 7).
+// Threads are radius-fastest (rr = tid mod kAngleRadii): the polar table reads are contiguous, the
+// first FFT pass takes the bilinear samples straight from the gather, and the sum over radii is a
+// shuffle reduction over the kAngleRadii lanes that hold one k.
 template <int NT>
-__global__ void k_angle(DevPlan p, const float* __restrict__ mt, float2* __restrict__ sp, int B) {
-    constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC + 1;
+__global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_angle(DevPlan p, const float* __restrict__ mt,
+                                                                       float2* __restrict__ sp, int B) {
+    constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC;
+    static_assert(RC == 16, "the shuffle sum runs over aligned groups of 16 lanes");
     extern __shared__ float2 sm[];
-    const int q = blockIdx.y, ch = blockIdx.x, r0 = ch * RC, n = p.n, W = n / 2;
+    const int q = blockIdx.y, ch = blockIdx.x, n = p.n, W = n / 2;
+    const int rr = threadIdx.x % RC, j = threadIdx.x / RC, r = ch * RC + rr;
     const float* mf = mt + (size_t)q * (W + 1) * n;
     const float* mg = mt + (size_t)(B + q) * (W + 1) * n;
-    for (int idx = threadIdx.x; idx < NT * RC; idx += blockDim.x) {
-        const int a = idx / RC, rr = idx % RC, r = r0 + rr;
+    const bool live = r < p.nr;
+    first_pass_global<NT>(sm + rr, ES, j, [&](int a) {
         float2 z = make_float2(0.f, 0.f);
-        if (r < p.nr) {
+        if (live) {
             const PolarSample ps = p.polar[a * p.nr + r];
             const float w00 = (1.f - ps.fy) * (1.f - ps.fx), w01 = (1.f - ps.fy) * ps.fx;
             const float w10 = ps.fy * (1.f - ps.fx), w11 = ps.fy * ps.fx;
@@ -109,23 +115,25 @@ __global__ void k_angle(DevPlan p, const float* __restrict__ mt, float2* __restr
             z.y = w00 * mag_at(mg, n, ps.y0, ps.x0) + w01 * mag_at(mg, n, ps.y0, ps.x0 + 1) +
                   w10 * mag_at(mg, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mg, n, ps.y0 + 1, ps.x0 + 1);
         }
-        sm[spad(a) * ES + rr] = z;
-    }
+        return z;
+    });
     __syncthreads();
-    fft<NT, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, threadIdx.x < T * RC, p.tw_t);
+    fft_passes_from<NT, -1, 2>(sm + rr, ES, j, p.tw_t);
     float2* out = sp + ((size_t)q * gridDim.x + ch) * NT;
-    for (int k = threadIdx.x; k < NT; k += blockDim.x) {
-        const int km = k == 0 ? 0 : NT - k;
-        float sx = 0.f, sy = 0.f;
+    const unsigned grp = 0xffffu << (threadIdx.x & 16);   // the 16 lanes of this thread's k
 #pragma unroll 4
-        for (int rr = 0; rr < RC; ++rr) {
-            const float2 z = sm[spad(k) * ES + rr], zm = sm[spad(km) * ES + rr];
-            const float ax = 0.5f * (z.x + zm.x), ay = 0.5f * (z.y - zm.y);
-            const float bx = 0.5f * (z.y + zm.y), by = -0.5f * (z.x - zm.x);
-            sx += ax * bx + ay * by;
-            sy += ax * by - ay * bx;
+    for (int m = 0; m < 16; ++m) {
+        const int k = j + T * m, km = k == 0 ? 0 : NT - k;
+        const float2 z = sm[spad(k) * ES + rr], zm = sm[spad(km) * ES + rr];
+        const float ax = 0.5f * (z.x + zm.x), ay = 0.5f * (z.y - zm.y);
+        const float bx = 0.5f * (z.y + zm.y), by = -0.5f * (z.x - zm.x);
+        float sx = ax * bx + ay * by, sy = ax * by - ay * bx;
+#pragma unroll
+        for (int o = RC / 2; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(grp, sx, o);
+            sy += __shfl_xor_sync(grp, sy, o);
         }
-        out[k] = make_float2(sx, sy);
+        if (rr == 0) out[k] = make_float2(sx, sy);
     }
 }
 
@@ -441,7 +449,7 @@ template <int N> constexpr size_t smem_cols1() {
 template <int P> constexpr size_t smem_cols2() {
     return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T) * sizeof(float2);
 }
-template <int NT> constexpr size_t smem_angle() { return (size_t)spad(NT) * (kAngleRadii + 1) * sizeof(float2); }
+template <int NT> constexpr size_t smem_angle() { return (size_t)spad(NT) * kAngleRadii * sizeof(float2); }
 
 template <int NT>
 static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, const long long* tab, float* pose,
