@@ -272,9 +272,7 @@ def run_mixed(args):
         for net, st, cnt, n in nets:
             view = lambda t: t[st:st + cnt * n * n].view(cnt, n, n)
             net.forward(view(F), view(G), training=False, f_out=view(FM), g_out=view(GM))
-        search.pose(FM, GM, size_idx=si, offsets=offs, out=pose)
-        search.pose_loss(pose, gt, kind=1, loss=loss, dpose=dpose)
-        search.pose_backward(FM, GM, dpose, size_idx=si, offsets=offs)
+        search.pose_train(FM, GM, gt, kind=1, size_idx=si, offsets=offs, out=(pose, loss, dpose, dF, dG))
 
     for _ in range(args.warmup):
         step()
@@ -380,10 +378,17 @@ def main():
     df = torch.empty_like(fd)
     dg = torch.empty_like(gd)
 
-    def run_step(srch, fx, gx, gtx, px, dpx, lx, dfx, dgx, nb):
-        """One step through the library only: search, L2 pose loss (the 512^2 configuration's loss)
-        and its adjoint."""
+    def run_step(srch, fx, gx, gtx, px, dpx, lx, dfx, dgx, nb, separate=False):
+        """One step through the library only.  fwd: the search.  fwdbwd: the search, the L2 pose loss
+        (the 512^2 configuration's loss) and its adjoint in one training call, whose adjoint reads
+        the forward's intermediates; separate=True makes the same step from the three separate
+        calls, the adjoint then recomputing the forward."""
         st = torch.cuda.current_stream().cuda_stream
+        if args.mode == "fwdbwd" and not separate:
+            _lib.check(L.fmbym_pose_train(srch.handle, st, nb, None, None, fx.data_ptr(), gx.data_ptr(),
+                                          gtx.data_ptr(), 2, px.data_ptr(), lx.data_ptr(), dpx.data_ptr(),
+                                          dfx.data_ptr(), dgx.data_ptr()), srch.handle)
+            return
         _lib.check(L.fmbym_pose(srch.handle, st, nb, None, None, fx.data_ptr(), gx.data_ptr(), px.data_ptr(), None,
                                 None), srch.handle)
         if args.mode == "fwdbwd":
@@ -515,7 +520,7 @@ def main():
             dt = (time.perf_counter() - t0) / reps
             e2e = {"value": B / dt, "unit": "scan-pairs/s", "h2d_bytes_per_step": 2 * f.nbytes + B * 12,
                    "d2h_bytes_per_step": B * 12 + 4, "mode": "fwdbwd",
-                   "api": "fmbym_pose + fmbym_pose_loss + fmbym_pose_backward from pinned host buffers"}
+                   "api": "fmbym_pose_train from pinned host buffers (H2D of f, g, gt; D2H of pose, loss)"}
 
     # ---- forward-only rate and the plain one-pair-per-call path ----
     extra = {}
@@ -530,6 +535,18 @@ def main():
             torch.cuda.synchronize()
             fwd_ms.append(a.elapsed_time(b))
         extra["fwd_pairs_per_s"] = B / (statistics.mean(fwd_ms) * 1e-3)
+        if args.mode == "fwdbwd":
+            # the same step as three calls (pose, loss, backward with its forward recompute)
+            sep_ms = []
+            for _ in range(max(3, args.steps // 2)):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                run_step(search, fd, gd, gtd, pose, dpose, loss, df, dg, B, separate=True)
+                b.record()
+                torch.cuda.synchronize()
+                sep_ms.append(a.elapsed_time(b))
+            extra["separate_calls_pairs_per_s"] = B / (statistics.mean(sep_ms[1:]) * 1e-3)
         if not args.no_plain:
             one = PoseSearch([cfg], max_pairs=1)
             for label, mode in (("fwd", "fwd"), ("step", args.mode)):

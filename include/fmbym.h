@@ -137,6 +137,21 @@ int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* s
 int fmbym_pose_loss(fmbym_handle* h, void* stream, int n_pairs, const float* pose, const float* gt,
                     int kind, float* loss, float* dpose);
 
+/* One training step of the search (Sec. III-D, Eq. 12-13): the forward of fmbym_pose, the loss of
+ * fmbym_pose_loss against gt, and the adjoint of fmbym_pose_backward for that loss, in one call.
+ * The adjoint reads the forward's intermediates from the handle's workspace, where this call's
+ * forward left them, instead of recomputing them; the results equal those of the three separate
+ * calls.
+ *   f, g       device float32 scans (as fmbym_pose); gt device float32 [n_pairs][3]
+ *   loss_kind  1 (L1, Eq. 13) or 2 (L2), as fmbym_pose_loss's kind
+ *   pose       device float32 [n_pairs][3] out; loss device float32 [1] out
+ *   dpose      device float32 [n_pairs][3] out: dloss/dpose
+ *   df, dg     device float32 out, laid out like f and g (overwritten)
+ * f, g, df and dg must be 16-byte aligned; every buffer is required.  Errors as fmbym_pose. */
+int fmbym_pose_train(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx,
+                     const long long* offsets, const float* f, const float* g, const float* gt,
+                     int loss_kind, float* pose, float* loss, float* dpose, float* df, float* dg);
+
 /* fmbym_pose with HOST buffers: copies f and g (host float32, total elements as laid out by
  * offsets) into the handle's device staging area, runs the search on the stream, copies the
  * pose (host float32 [n_pairs][3]) back and synchronises the stream.  total_elems is the

@@ -317,7 +317,8 @@ int make_table(fmbym_handle* h, int n_pairs, const int* size_idx, const long lon
     return FMBYM_OK;
 }
 
-// Buffers of one forward (kind 0) or backward (kind 1) call.
+// Buffers of one forward (kind 0), backward (kind 1) or training (kind 2: forward, pose loss and
+// the adjoint of the loss without recomputing the forward) call.
 struct LaunchArgs {
     int kind;
     const float* f;
@@ -328,37 +329,60 @@ struct LaunchArgs {
     const float* dpose;
     float* df;
     float* dg;
+    const float* gt;      // kind 2: ground-truth poses
+    int loss_kind;        // kind 2: 1 = L1 (Eq. 13), 2 = L2
+    float* loss;          // kind 2: the loss (device scalar)
+    float* dpose_out;     // kind 2: dL/dpose, written by the loss and read by the adjoint
 };
 
+// phase 0 launches the forward of one size group, phase 1 its adjoint (after a forward recompute
+// unless the call is a training call, whose forward left its intermediates in the workspace).
 cudaError_t launch_group(fmbym_handle* h, const Group& gr, const long long* dtab, const LaunchArgs& a,
-                         cudaStream_t s) {
+                         cudaStream_t s, int phase) {
     const DevPlan& p = h->plans[gr.size_idx].dev;
     Ws w = ws_carve(p, gr.count, h->ws[gr.size_idx], true);
     w.tr = &h->tracer;
     w.cnt = h->d_cnt + (size_t)gr.size_idx * h->max_pairs;
     w.bpose = h->d_bpose;
-    if (a.kind == 0)
-        return launch_forward(p, w, gr.count, dtab + 3 * gr.first, a.f, a.g, a.pose, a.c_theta, a.c_xy, s);
-    return launch_backward(p, w, gr.count, dtab + 3 * gr.first, a.f, a.g, a.dpose, a.df, a.dg, s);
+    const long long* tab = dtab + 3 * gr.first;
+    if (phase == 0) {
+        const bool train = a.kind == 2;
+        return launch_forward(p, w, gr.count, tab, a.f, a.g, a.pose, train ? nullptr : a.c_theta,
+                              train ? nullptr : a.c_xy, s);
+    }
+    if (a.kind == 2) return launch_backward(p, w, gr.count, tab, a.f, a.g, a.dpose_out, a.df, a.dg, s, a.pose);
+    return launch_backward(p, w, gr.count, tab, a.f, a.g, a.dpose, a.df, a.dg, s, nullptr);
 }
 
-// Launches every size group: the first on the caller's stream, the others on the handle's side
-// streams forked from it and joined back, so that groups of different sizes run concurrently.
-// With more than one group the tracer only counts launches (its events assume one stream).
-cudaError_t enqueue(fmbym_handle* h, cudaStream_t st, const std::vector<Group>& groups, const long long* dtab,
-                    const LaunchArgs& a) {
-    if (groups.size() == 1) return launch_group(h, groups[0], dtab, a, st);
+// Launches one phase of every size group: the first on the caller's stream, the others on the
+// handle's side streams forked from it and joined back, so that groups of different sizes run
+// concurrently.  With more than one group the tracer only counts launches (its events assume one
+// stream).
+cudaError_t enqueue_phase(fmbym_handle* h, cudaStream_t st, const std::vector<Group>& groups, const long long* dtab,
+                          const LaunchArgs& a, int phase) {
+    if (groups.size() == 1) return launch_group(h, groups[0], dtab, a, st, phase);
     const bool tracing = h->tracer.on;
     h->tracer.on = false;
     cudaError_t e = cudaEventRecord(h->ev_fork, st);
     for (size_t k = 1; k < groups.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(h->side[k - 1], h->ev_fork, 0);
     for (size_t k = 0; k < groups.size() && e == cudaSuccess; ++k) {
         cudaStream_t s = k == 0 ? st : h->side[k - 1];
-        e = launch_group(h, groups[k], dtab, a, s);
+        e = launch_group(h, groups[k], dtab, a, s, phase);
         if (e == cudaSuccess && k > 0) e = cudaEventRecord(h->ev_join[k - 1], s);
         if (e == cudaSuccess && k > 0) e = cudaStreamWaitEvent(st, h->ev_join[k - 1], 0);
     }
     h->tracer.on = tracing;
+    return e;
+}
+
+// A forward call is phase 0, a backward call phase 1; a training call runs phase 0, the loss over
+// all pairs on the caller's stream (after every group's forward has joined it), then phase 1.
+cudaError_t enqueue(fmbym_handle* h, cudaStream_t st, const std::vector<Group>& groups, const long long* dtab,
+                    const LaunchArgs& a, int n_pairs) {
+    if (a.kind != 2) return enqueue_phase(h, st, groups, dtab, a, a.kind);
+    cudaError_t e = enqueue_phase(h, st, groups, dtab, a, 0);
+    if (e == cudaSuccess) e = launch_pose_loss(n_pairs, a.pose, a.gt, a.loss_kind, a.loss, a.dpose_out, &h->tracer, st);
+    if (e == cudaSuccess) e = enqueue_phase(h, st, groups, dtab, a, 1);
     return e;
 }
 
@@ -375,7 +399,9 @@ int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Gr
         std::vector<long long> key = {a.kind, n_pairs, (long long)(uintptr_t)a.f, (long long)(uintptr_t)a.g,
                                       (long long)(uintptr_t)a.pose, (long long)(uintptr_t)a.c_theta,
                                       (long long)(uintptr_t)a.c_xy, (long long)(uintptr_t)a.dpose,
-                                      (long long)(uintptr_t)a.df, (long long)(uintptr_t)a.dg};
+                                      (long long)(uintptr_t)a.df, (long long)(uintptr_t)a.dg,
+                                      (long long)(uintptr_t)a.gt, a.loss_kind, (long long)(uintptr_t)a.loss,
+                                      (long long)(uintptr_t)a.dpose_out};
         key.insert(key.end(), h->h_tab, h->h_tab + 3 * (size_t)n_pairs);
         GraphEntry* ge = nullptr;
         for (auto& x : h->graphs)
@@ -403,7 +429,7 @@ int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Gr
                 cudaFree(n.d_tab);
                 return cuda_fail(h, e, "cudaStreamBeginCapture");
             }
-            cudaError_t le = enqueue(h, h->cap, groups, n.d_tab, a);
+            cudaError_t le = enqueue(h, h->cap, groups, n.d_tab, a, n_pairs);
             e = cudaStreamEndCapture(h->cap, &graph);
             n.kernels = h->tracer.launches - before;
             h->tracer.launches = before;
@@ -430,7 +456,8 @@ int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Gr
         cudaSuccess)
         return cuda_fail(h, e, "pair table copy");
     if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
-    if ((e = enqueue(h, st, groups, h->d_tab, a)) != cudaSuccess) return cuda_fail(h, e, a.kind ? "backward launch" : "forward launch");
+    if ((e = enqueue(h, st, groups, h->d_tab, a, n_pairs)) != cudaSuccess)
+        return cuda_fail(h, e, a.kind == 0 ? "forward launch" : a.kind == 1 ? "backward launch" : "training launch");
     return FMBYM_OK;
 }
 
@@ -590,6 +617,33 @@ int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* s
     a.f = f;
     a.g = g;
     a.dpose = dpose;
+    a.df = df;
+    a.dg = dg;
+    return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
+}
+
+int fmbym_pose_train(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
+                     const float* f, const float* g, const float* gt, int loss_kind, float* pose, float* loss,
+                     float* dpose, float* df, float* dg) {
+    if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    h->err.clear();
+    if (n_pairs == 0) return FMBYM_OK;
+    if (loss_kind != 1 && loss_kind != 2) return fail(h, FMBYM_ERR_INVALID_ARG, "loss_kind not 1/2");
+    if (!f || !g || !gt || !pose || !loss || !dpose || !df || !dg) return fail(h, FMBYM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(f) || !aligned16(g) || !aligned16(df) || !aligned16(dg))
+        return fail(h, FMBYM_ERR_INVALID_ARG, "f, g, df and dg must be 16-byte aligned");
+    std::vector<Group> groups;
+    int rc = make_table(h, n_pairs, size_idx, offsets, groups, nullptr);
+    if (rc != FMBYM_OK) return rc;
+    LaunchArgs a{};
+    a.kind = 2;
+    a.f = f;
+    a.g = g;
+    a.pose = pose;
+    a.gt = gt;
+    a.loss_kind = loss_kind;
+    a.loss = loss;
+    a.dpose_out = dpose;
     a.df = df;
     a.dg = dg;
     return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);

@@ -705,13 +705,17 @@ static void launch_stage1_adjoint(const DevPlan& p, const Ws& w, int B, cudaStre
 
 template <int N, int P>
 static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
-                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st) {
-    cudaError_t e = launch_forward(p, w, B, tab, f, g, w.bpose, nullptr, nullptr, st);
-    if (e != cudaSuccess) return e;
+                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st,
+                            const float* fwd_pose) {
+    if (!fwd_pose) {
+        cudaError_t e = launch_forward(p, w, B, tab, f, g, w.bpose, nullptr, nullptr, st);
+        if (e != cudaSuccess) return e;
+        fwd_pose = w.bpose;
+    }
     constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T, TB2 = tpb_for(P);
     const int nblk = (N / 2) / (TB2 / T2);
     w.tr->before(K_B_SXY, st);
-    k_b_stats<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, w.st, nblk, w.sx, w.bpose, dpose, w.gxx,
+    k_b_stats<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, w.st, nblk, w.sx, fwd_pose, dpose, w.gxx,
                                                           w.cnt, w.bsc);
     w.tr->before(K_B_ROWS, st);
     k_b_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.bsc, dpose, w.b1,
@@ -741,14 +745,15 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
 }
 
 cudaError_t launch_backward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
-                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st) {
+                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st,
+                            const float* fwd_pose) {
     if (B <= 0) return cudaSuccess;
-    if (p.n == 128) return p.p == 192 ? launch_b<128, 192>(p, w, B, tab, f, g, dpose, df, dg, st)
-                                      : launch_b<128, 128>(p, w, B, tab, f, g, dpose, df, dg, st);
-    if (p.n == 256) return p.p == 384 ? launch_b<256, 384>(p, w, B, tab, f, g, dpose, df, dg, st)
-                                      : launch_b<256, 256>(p, w, B, tab, f, g, dpose, df, dg, st);
-    return p.p == 768 ? launch_b<512, 768>(p, w, B, tab, f, g, dpose, df, dg, st)
-                      : launch_b<512, 512>(p, w, B, tab, f, g, dpose, df, dg, st);
+    if (p.n == 128) return p.p == 192 ? launch_b<128, 192>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
+                                      : launch_b<128, 128>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+    if (p.n == 256) return p.p == 384 ? launch_b<256, 384>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
+                                      : launch_b<256, 256>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+    return p.p == 768 ? launch_b<512, 768>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
+                      : launch_b<512, 512>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
 }
 
 template <typename K>

@@ -113,8 +113,11 @@ Ws ws_carve(const DevPlan& p, int B, void* base, bool backward);
 // tab: device long long [B][3] = (scan offset, c_theta offset, pair index)
 cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                            const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st);
+// fwd_pose: NULL recomputes the forward into the workspace first (the stateless adjoint); otherwise
+// the workspace still holds this call's forward intermediates and fwd_pose is its pose output.
 cudaError_t launch_backward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
-                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st);
+                            const float* g, const float* dpose, float* df, float* dg, cudaStream_t st,
+                            const float* fwd_pose);
 cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, int kind, float* loss, float* dpose,
                              Tracer* tr, cudaStream_t st);
 cudaError_t prepare_kernels();

@@ -111,6 +111,27 @@ class PoseSearch:
         _lib.check(st, self.handle)
         return df, dg
 
+    def pose_train(self, f, g, gt, kind=1, size_idx=None, offsets=None, stream=None, out=None):
+        """One training step of the search: forward, the Eq. 13 loss against gt [B, 3] (kind 1 = L1,
+        2 = L2) and the adjoint of that loss, the adjoint reading the forward's intermediates instead
+        of recomputing them.  out: optional preallocated (pose, loss, dpose, df, dg).  Returns
+        (pose, loss, dpose, df, dg)."""
+        n_pairs, si, off, _, _ = self._layout(f, size_idx, offsets)
+        if out is None:
+            out = (torch.empty((n_pairs, 3), device=f.device, dtype=torch.float32),
+                   torch.empty(1, device=f.device, dtype=torch.float32),
+                   torch.empty((n_pairs, 3), device=f.device, dtype=torch.float32),
+                   torch.empty_like(f), torch.empty_like(g))
+        pose, loss, dpose, df, dg = out
+        gt = gt.contiguous().to(torch.float32)
+        st = _lib.lib().fmbym_pose_train(self.handle, _stream(stream), n_pairs,
+                                         None if si is None else si.ctypes.data_as(ctypes.c_void_p),
+                                         None if off is None else off.ctypes.data_as(ctypes.c_void_p),
+                                         _ptr(f), _ptr(g), _ptr(gt), int(kind), _ptr(pose), _ptr(loss),
+                                         _ptr(dpose), _ptr(df), _ptr(dg))
+        _lib.check(st, self.handle)
+        return pose, loss, dpose, df, dg
+
     def pose_loss(self, pose, gt, kind=1, loss=None, dpose=None, stream=None):
         """Eq. 13 loss (kind 1 = L1, 2 = L2; mean over pairs) and dloss/dpose, on the device."""
         n_pairs = pose.shape[0]

@@ -1,9 +1,9 @@
 """End-to-end training of the masking network through the decoupled search (Sec. III-D, Eq. 10-13).
 
-One step: masks and masked scans from the U-Net (Eq. 10-11), the pose from the search on the
-masked scans (Eq. 12, Alg. 1), the L1 pose loss of Eq. 13 and its gradient, the adjoint of the
-search down to the masked scans, the adjoint of the network, and an Adam step -- every stage a
-call into the CUDA library.
+One step: masks and masked scans from the U-Net (Eq. 10-11), then one training call of the search
+on the masked scans (the pose of Eq. 12 / Alg. 1, the L1 pose loss of Eq. 13 and the adjoint of
+the search down to the masked scans), the adjoint of the network, and an Adam step -- every stage
+a call into the CUDA library.
 """
 from __future__ import annotations
 
@@ -46,9 +46,7 @@ class MaskedSearch:
     def train_step(self, f, g, gt, lr=1e-3):
         """One Adam step on a batch (device tensors f, g [B, N, N], gt [B, 3]); returns the loss."""
         fo, go, _ = self.net.forward(f, g, training=True)
-        pose = self.search.pose(fo, go)["pose"]
-        loss, dpose = self.search.pose_loss(pose, gt, kind=self.loss_kind)
-        dfo, dgo = self.search.pose_backward(fo, go, dpose)
+        _, loss, _, dfo, dgo = self.search.pose_train(fo, go, gt, kind=self.loss_kind)
         self.net.backward(f, g, dfo, dgo)
         self.steps += 1
         self.net.adam(lr, self.steps)

@@ -151,3 +151,42 @@ def test_adjoint_mixed_sizes_in_one_call(lib):
         assert grad_err(df[offs[k]:offs[k] + n * n].reshape(n, n), odf) <= TOL_GRAD
         assert grad_err(dg[offs[k]:offs[k] + n * n].reshape(n, n), odg) <= TOL_GRAD
     s.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("kind", [1, 2])
+def test_training_call_equals_separate_calls(lib, graph, kind):
+    """fmbym_pose_train (forward, loss, adjoint reading the forward's intermediates) gives the same
+    bits as fmbym_pose + fmbym_pose_loss + fmbym_pose_backward (which recomputes the forward), for a
+    mixed-size call."""
+    from paper_2203_00459_gb300 import _lib
+    from paper_2203_00459_gb300.search import PoseSearch
+    cfgs = [lib.size_cfg(128, 128, 64), lib.size_cfg(512, 400, 256)]
+    names = ["single128", "batch512"]
+    order = [1, 0, 1, 0]
+    scans = [synth.make_batch(names[s], pairs=1, start=40 + k) for k, s in enumerate(order)]
+    offs, cur = [], 0
+    for f, _, _ in scans:
+        offs.append(cur)
+        cur += f.size
+    F = torch.from_numpy(np.concatenate([f.ravel() for f, _, _ in scans])).cuda()
+    G = torch.from_numpy(np.concatenate([g.ravel() for _, g, _ in scans])).cuda()
+    gt = torch.from_numpy(np.concatenate([p for _, _, p in scans]).astype(np.float32)).cuda()
+    s = PoseSearch(cfgs, max_pairs=4, flags=_lib.FLAG_GRAPH if graph else 0)
+    for _ in range(2):   # the second graph call replays the captured layout
+        pose, loss, dpose, df, dg = s.pose_train(F, G, gt, kind=kind, size_idx=order, offsets=offs)
+    pose2 = s.pose(F, G, size_idx=order, offsets=offs)["pose"]
+    loss2, dpose2 = s.pose_loss(pose2, gt, kind=kind)
+    df2, dg2 = s.pose_backward(F, G, dpose2, size_idx=order, offsets=offs)
+    torch.cuda.synchronize()
+    for a, b in ((pose, pose2), (loss, loss2), (dpose, dpose2), (df, df2), (dg, dg2)):
+        assert torch.equal(a, b)
+    # and the adjoint matches the oracle's adjoint for the loss gradient the call produced
+    if kind == 2:
+        k = 0
+        n = cfgs[order[k]]["n"]
+        f, g, _ = scans[k]
+        odf, odg, _ = O.pose_backward(f[0], g[0], oracle_cfg(cfgs[order[k]]), dpose.cpu().numpy()[k].astype(np.float64))
+        assert grad_err(df.cpu().numpy()[offs[k]:offs[k] + n * n].reshape(n, n), odf) <= TOL_GRAD
+        assert grad_err(dg.cpu().numpy()[offs[k]:offs[k] + n * n].reshape(n, n), odg) <= TOL_GRAD
+    s.close()
