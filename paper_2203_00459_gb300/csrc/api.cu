@@ -85,12 +85,12 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
     t.s3 = (float2*)take(b * n * Wp * sizeof(float2));
     t.cxy = (float*)take(b * n * n * sizeof(float));
     t.st = (float*)take(b * c2r_blocks(p) * 4 * sizeof(float));
-    t.sx = (float*)take(b * kSplitXY * 4 * sizeof(float));
+    t.sx = (float*)take(b * kSplitXY * 8 * sizeof(float));
+    t.xm = (float*)take(b * 8 * sizeof(float));
     t.ct = (float*)take(b * p.nt * sizeof(float));
     if (backward) {
         t.bsc = (float*)take(b * 16 * sizeof(float));
         t.gpart = (float*)take(b * (n * n / 256) * sizeof(float));
-        t.gxx = (float*)take(b * kSplitXY * 4 * sizeof(float));
         t.b1 = (float2*)take(b * n * Wp * sizeof(float2));
         t.b2 = (float2*)take(2 * b * n * Wp * sizeof(float2));
         t.gfr = (float*)take(b * n * n * sizeof(float));

@@ -2,10 +2,10 @@
 // through which the masking network of Sec. III-D is trained by Eq. 13).
 //
 // Given dL/d(theta, t_x, t_y) per pair, the kernels below produce dL/df and dL/dg.  The forward
-// intermediates are recomputed first (launch_forward into the workspace); nothing is kept between
-// calls.  Order of the adjoint, last forward step first:
-//   k_b_stats    translation soft-argmax adjoint: the two z-score reductions of dz
-//   k_b_rows     d c_xy formed on load, embedded in the P x P lag grid, real row FFTs
+// intermediates are recomputed first (launch_forward into the workspace), or, in a training call,
+// are still in the workspace from that call's own forward; nothing is kept between calls.  Order of the adjoint, last forward step first:
+//   k_b_rows     translation soft-argmax adjoint d c_xy (from the moments the forward kept),
+//                embedded in the P x P lag grid, real row FFTs
 //   k_b_cols     column FFTs of D, F' and G; conj(D) G (-> d f') and D F' (-> d g); inverse
 //   k_b_c2r      inverse row FFTs, keep x in [0, N): d f' and the stage-2 part of d g
 //   k_b_rot      Rotate adjoint: d f (transpose of the bilinear gather, in gather form) and
@@ -29,86 +29,25 @@ namespace fmbym {
 
 // With p = softmax(y), y = (c - mean)/(std T), t = delta E_p[s]: dL/dy = p (q - <p, q>) with
 // q_s = delta (dtx s_x + dty s_y) and <p, q> = dtx t_x + dty t_y; dz = dL/dy / T.  The z-score
-// adjoint needs mean(dz) and mean(dz z) over all lags: each block sums a slab of rows and the last
-// block of a pair adds the slabs in order.  bsc[q] receives (mean dz, mean dz z, mean, std, max,
-// 1/(std T), sum of exp, <p, q>).
-template <int N>
-__global__ void __launch_bounds__(kThreads) k_b_stats(DevPlan p, const long long* __restrict__ tab,
-                                                      const float* __restrict__ cxy, const float* __restrict__ st,
-                                                      int nblk, const float* __restrict__ sx,
-                                                      const float* __restrict__ bpose,
-                                                      const float* __restrict__ dpose, float* __restrict__ gxx,
-                                                      unsigned* __restrict__ cnt, float* __restrict__ bsc) {
-    __shared__ float red[32];
-    __shared__ float sh[8];
-    __shared__ bool last;
-    const int q = blockIdx.y;
-    const long long pr = tab[3 * q + 2];
-    if (threadIdx.x < 32) {
-        float mu, sd, cmax;
-        xy_stats_warp(st + (size_t)q * nblk * 4, nblk, (float)N * (float)N, mu, sd, cmax);
-        if (threadIdx.x == 0) {
-            const float* o = sx + (size_t)q * kSplitXY * 4;
-            float se = 0.f;
-            for (int i = 0; i < kSplitXY; ++i) se += o[4 * i];
-            sh[0] = mu;
-            sh[1] = sd;
-            sh[2] = cmax;
-            sh[3] = p.score_norm == 1 ? 1.f / p.temp_xy : (sd > 0.f ? 1.f / (sd * p.temp_xy) : 0.f);
-            sh[4] = se;
-        }
-    }
-    __syncthreads();
-    const float mu = sh[0], sd = sh[1], cmax = sh[2], inv = sh[3], se = sh[4];
-    const float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
-    const float pq = dtx * bpose[3 * pr + 1] + dty * bpose[3 * pr + 2];
-    const float dl = p.delta_xy, invT = 1.f / p.temp_xy, isd = sd > 0.f ? 1.f / sd : 0.f;
-    const float* c = cxy + (size_t)q * N * N;
-    constexpr int ROWS = N / kSplitXY;
-    const int y0 = blockIdx.x * ROWS;
-    float l1 = 0.f, l2 = 0.f;
-    for (int idx = threadIdx.x; idx < ROWS * N; idx += kThreads) {
-        const int yy = y0 + idx / N, xx = idx % N;
-        const float cv = c[(size_t)yy * N + xx];
-        const float pp = expf((cv - cmax) * inv) / se;
-        const float qq = dl * (dtx * (float)(xx - N / 2) + dty * (float)(yy - N / 2));
-        const float dz = pp * (qq - pq) * invT;
-        l1 += dz;
-        l2 += dz * (cv - mu) * isd;
-    }
-    const float s1 = block_reduce<false>(l1, red);
-    const float s2 = block_reduce<false>(l2, red);
-    if (threadIdx.x == 0) {
-        float* o = gxx + ((size_t)q * kSplitXY + blockIdx.x) * 4;
-        o[0] = s1;
-        o[1] = s2;
-        __threadfence();
-        last = atomicAdd(&cnt[q], 1u) == kSplitXY - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const volatile float* o = gxx + (size_t)q * kSplitXY * 4;
-        float a = 0.f, b = 0.f;
-        for (int i = 0; i < kSplitXY; ++i) {
-            a += o[4 * i];
-            b += o[4 * i + 1];
-        }
-        float* r = bsc + (size_t)q * 16;
-        const float inn = 1.f / ((float)N * (float)N);
-        r[0] = a * inn;
-        r[1] = b * inn;
-        r[2] = mu;
-        r[3] = sd;
-        r[4] = cmax;
-        r[5] = inv;
-        r[6] = se;
-        r[7] = pq;
-        cnt[q] = 0u;
-    }
+// adjoint needs mean(dz) and mean(dz z) over the n = N^2 lags.  Since sum p = 1 and
+// sum p q = <p, q>, mean(dz) = 0, and mean(dz z) = (delta (dtx S_zx + dty S_zy) - <p, q> S_z) /
+// (n T S) with S = sum e, S_z = sum e z, S_zx = sum e z s_x, S_zy = sum e z s_y, the sums the
+// forward's soft-argmax keeps (xm).  r receives (mean dz, mean dz z, mean, std, max, 1/(std T),
+// S, <p, q>).
+__device__ __forceinline__ void xy_adjoint_scalars(const DevPlan& p, const float* __restrict__ m, float tx,
+                                                   float ty, float dtx, float dty, int n, float* r) {
+    const float pq = dtx * tx + dty * ty;
+    r[0] = 0.f;
+    r[1] = (p.delta_xy * (dtx * m[6] + dty * m[7]) - pq * m[5]) / ((float)n * (float)n * p.temp_xy * m[4]);
+    r[2] = m[0];
+    r[3] = m[1];
+    r[4] = m[2];
+    r[5] = m[3];
+    r[6] = m[4];
+    r[7] = pq;
 }
 
-// d c_xy at lag (i, j) from the scores and the per-pair scalars of k_b_stats.
+// d c_xy at lag (i, j) from the scores and the per-pair scalars of xy_adjoint_scalars.
 __device__ __forceinline__ float dcxy(const DevPlan& p, const float* r, float cv, int i, int j, int n, float dtx,
                                       float dty) {
     const float pp = expf((cv - r[4]) * r[5]) / r[6];
@@ -129,15 +68,19 @@ __device__ __forceinline__ float dcxy(const DevPlan& p, const float* r, float cv
 // d c_xy straight from global memory.
 template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long* __restrict__ tab,
-                                                     const float* __restrict__ cxy, const float* __restrict__ bsc,
+                                                     const float* __restrict__ cxy, const float* __restrict__ xm,
+                                                     const float* __restrict__ fwd_pose,
                                                      const float* __restrict__ dpose, float2* __restrict__ b1, int B) {
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
+    __shared__ float r[8];
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
     const int k = threadIdx.x / T, jt = threadIdx.x % T, i = i0 + 2 * k;
     const long long pr = tab[3 * q + 2];
     const float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
-    const float* r = bsc + (size_t)q * 16;
+    if (threadIdx.x == 0)
+        xy_adjoint_scalars(p, xm + (size_t)q * 8, fwd_pose[3 * pr + 1], fwd_pose[3 * pr + 2], dtx, dty, N, r);
+    __syncthreads();
     const float* c = cxy + (size_t)q * N * N + (size_t)i * N;
     first_pass_global<P>(sm + k * SL, 1, jt, [&](int x) {
         const int j = x + N / 2 < P ? x + N / 2 : x + N / 2 - P;   // lag column at P-position x
@@ -713,13 +656,9 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
         fwd_pose = w.bpose;
     }
     constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T, TB2 = tpb_for(P);
-    const int nblk = (N / 2) / (TB2 / T2);
-    w.tr->before(K_B_SXY, st);
-    k_b_stats<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, w.st, nblk, w.sx, fwd_pose, dpose, w.gxx,
-                                                          w.cnt, w.bsc);
     w.tr->before(K_B_ROWS, st);
-    k_b_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.bsc, dpose, w.b1,
-                                                                                   B);
+    k_b_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.xm, fwd_pose,
+                                                                                   dpose, w.b1, B);
     w.tr->before(K_B_COLS, st);
     k_b_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, b_smem_cols<P>(), st>>>(p, w.b1, w.s2, w.b2, B);
     w.tr->before(K_B_C2R, st);

@@ -12,7 +12,7 @@ namespace fmbym {
 constexpr int kThreads = 256;   // threads of the FFT kernels
 constexpr int kAngleRadii = 16;  // radii per CTA of the angle-correlation kernel
 constexpr int kRotPixels = 4;    // pixels per thread of the Rotate adjoint (one reduction per block)
-constexpr int kSplitXY = 8;     // CTAs per pair of the translation soft-argmax
+constexpr int kSplitXY = 32;    // CTAs per pair of the translation soft-argmax
 
 // One bilinear Cart2Pol sample: floor of the (u, v) frequency and the fractions.
 struct PolarSample {
@@ -88,15 +88,15 @@ struct Ws {
     float2* s3;   // [B][N][P/2]      product after the inverse column pass, lag rows
     float* cxy;   // [B][N][N]        translation scores when the caller does not keep them
     float* st;    // [B][c2r blocks][4] per-block mean, M2, max of the translation scores
-    float* sx;    // [B][kSplitXY][4] soft-argmax partial sums
+    float* sx;    // [B][kSplitXY][8] soft-argmax partial sums
+    float* xm;    // [B][8]           translation soft-argmax statistics and moments kept for the adjoint
     unsigned* cnt;  // [B] completion counters of the last-block reductions: a handle-wide array that
                     // is zero between launches (the last block of a pair resets its counter)
     float* ct;    // [B][n_theta]     angle scores in lag order (kept for the adjoint)
     // adjoint
     float* bpose; // [pairs][3]       recomputed pose, indexed by pair (handle-wide)
-    float* bsc;   // [B][16]          per-pair scalars of the soft-argmax adjoints
+    float* bsc;   // [B][16]          per-pair scalars of the adjoint (d theta at 8)
     float* gpart; // [B][N*N/256]     per-block partial sums of d theta through Rotate
-    float* gxx;   // [B][kSplitXY][4] partial sums of the translation soft-argmax adjoint
     float2* b1;   // [B][N][P/2]      row spectra of the embedded d c_xy (lag rows)
     float2* b2;   // [2][B][N][P/2]   inverse column pass of conj(D) G and D F'
     float* gfr;   // [B][N][N]        d rotated source

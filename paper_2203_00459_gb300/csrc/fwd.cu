@@ -374,15 +374,18 @@ __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long*
 
 // Soft-argmax over the translation candidates (Alg. 1 stage 2): the blocks of a pair first
 // combine the per-block statistics of k_s2_c2r into the mean, population std and maximum, then
-// each sums exp((c - max) / (std T)) and its first moments over a slab of rows; the last block
-// of the pair adds the slabs in order and writes (t_x, t_y) = delta_xy E[s].
+// each sums e = exp((c - max) / (std T)) and its first moments over a slab of rows; the last block
+// of the pair adds the slabs in order and writes (t_x, t_y) = delta_xy E[s].  It also keeps, for
+// the adjoint, the statistics and the sums of e z, e z s_x and e z s_y with z = (c - mean) / std:
+// with them the z-score adjoint needs no second pass over the scores (see k_b_rows).
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __restrict__ tab,
                                                   const float* __restrict__ cxy_ws, const float* __restrict__ cxy_out,
                                                   const float* __restrict__ st, int nblk, float* __restrict__ sx,
-                                                  unsigned* __restrict__ cnt, float* __restrict__ pose) {
+                                                  unsigned* __restrict__ cnt, float* __restrict__ pose,
+                                                  float* __restrict__ xm) {
     __shared__ float red[32];
-    __shared__ float stat[2];
+    __shared__ float stat[4];
     __shared__ bool last;
     const int q = blockIdx.y;
     if (threadIdx.x < 32) {
@@ -391,49 +394,76 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
         if (threadIdx.x == 0) {
             stat[0] = cmax;
             stat[1] = p.score_norm == 1 ? 1.f / p.temp_xy : (sd > 0.f ? 1.f / (sd * p.temp_xy) : 0.f);
+            stat[2] = mu;
+            stat[3] = sd;
         }
     }
     __syncthreads();
-    const float cmax = stat[0], inv = stat[1];
+    const float cmax = stat[0], inv = stat[1], mu = stat[2], sd = stat[3];
+    const float isd = sd > 0.f ? 1.f / sd : 0.f;
     const float* c = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N;
     constexpr int ROWS = N / kSplitXY;
     const int y0 = blockIdx.x * ROWS;
-    float le = 0.f, lx = 0.f, ly = 0.f;
+    float le = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lzx = 0.f, lzy = 0.f;
     for (int idx = threadIdx.x; idx < ROWS * (N / 4); idx += kThreads) {
         const int yy = y0 + idx / (N / 4), x4 = (idx % (N / 4)) * 4;
         const float4 v = *reinterpret_cast<const float4*>(c + (size_t)yy * N + x4);
         const float e0 = expf((v.x - cmax) * inv), e1 = expf((v.y - cmax) * inv);
         const float e2 = expf((v.z - cmax) * inv), e3 = expf((v.w - cmax) * inv);
         const float es = (e0 + e1) + (e2 + e3);
-        const float sx0 = (float)(x4 - N / 2);
+        const float sx0 = (float)(x4 - N / 2), sy = (float)(yy - N / 2);
+        const float ex = e1 + 2.f * e2 + 3.f * e3;
         le += es;
-        lx += es * sx0 + (e1 + 2.f * e2 + 3.f * e3);
-        ly += es * (float)(yy - N / 2);
+        lx += es * sx0 + ex;
+        ly += es * sy;
+        const float z0 = (v.x - mu) * isd, z1 = (v.y - mu) * isd, z2 = (v.z - mu) * isd, z3 = (v.w - mu) * isd;
+        const float ez = (e0 * z0 + e1 * z1) + (e2 * z2 + e3 * z3);
+        lz += ez;
+        lzx += ez * sx0 + (e1 * z1 + 2.f * e2 * z2 + 3.f * e3 * z3);
+        lzy += ez * sy;
     }
     const float se = block_reduce<false>(le, red);
     const float sxx = block_reduce<false>(lx, red);
     const float syy = block_reduce<false>(ly, red);
+    const float sz = block_reduce<false>(lz, red);
+    const float szx = block_reduce<false>(lzx, red);
+    const float szy = block_reduce<false>(lzy, red);
     if (threadIdx.x == 0) {
-        float* o = sx + ((size_t)q * kSplitXY + blockIdx.x) * 4;
+        float* o = sx + ((size_t)q * kSplitXY + blockIdx.x) * 8;
         o[0] = se;
         o[1] = sxx;
         o[2] = syy;
+        o[3] = sz;
+        o[4] = szx;
+        o[5] = szy;
         __threadfence();
         last = atomicAdd(&cnt[q], 1u) == kSplitXY - 1;
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
-        const volatile float* o = sx + (size_t)q * kSplitXY * 4;
-        float a = 0.f, bx = 0.f, by = 0.f;
+        const volatile float* o = sx + (size_t)q * kSplitXY * 8;
+        float a = 0.f, bx = 0.f, by = 0.f, z = 0.f, zx = 0.f, zy = 0.f;
         for (int i = 0; i < kSplitXY; ++i) {
-            a += o[4 * i];
-            bx += o[4 * i + 1];
-            by += o[4 * i + 2];
+            a += o[8 * i];
+            bx += o[8 * i + 1];
+            by += o[8 * i + 2];
+            z += o[8 * i + 3];
+            zx += o[8 * i + 4];
+            zy += o[8 * i + 5];
         }
         const long long pr = tab[3 * q + 2];
         pose[3 * pr + 1] = p.delta_xy * (bx / a);
         pose[3 * pr + 2] = p.delta_xy * (by / a);
+        float* m = xm + (size_t)q * 8;
+        m[0] = mu;
+        m[1] = sd;
+        m[2] = cmax;
+        m[3] = inv;
+        m[4] = a;
+        m[5] = z;
+        m[6] = zx;
+        m[7] = zy;
         cnt[q] = 0u;
     }
 }
@@ -483,7 +513,7 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
     w.tr->before(K_S2_C2R, st);
     k_s2_c2r<N, P><<<dim3(nblk, B), TB2, smem_rows<P>(), st>>>(p, tab, w.s3, w.cxy, c_xy, w.st, B);
     w.tr->before(K_SXY, st);
-    k_sxy<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose);
+    k_sxy<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose, w.xm);
     w.tr->close(st);
     return cudaGetLastError();
 }
