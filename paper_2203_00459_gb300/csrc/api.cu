@@ -89,6 +89,8 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
     t.xm = (float*)take(b * 8 * sizeof(float));
     t.ct = (float*)take(b * p.nt * sizeof(float));
     if (backward) {
+        t.ahat = (float2*)take(b * p.nt * p.nr * sizeof(float2));
+        t.phs = (float2*)take(2 * b * (Wn + 1) * n * sizeof(float2));
         t.bsc = (float*)take(b * 16 * sizeof(float));
         t.gpart = (float*)take(b * (n * n / 256) * sizeof(float));
         t.b1 = (float2*)take(b * n * Wp * sizeof(float2));
@@ -347,6 +349,10 @@ cudaError_t launch_group(fmbym_handle* h, const Group& gr, const long long* dtab
     const long long* tab = dtab + 3 * gr.first;
     if (phase == 0) {
         const bool train = a.kind == 2;
+        if (!train) {   // a plain forward keeps nothing for an adjoint
+            w.ahat = nullptr;
+            w.phs = nullptr;
+        }
         return launch_forward(p, w, gr.count, tab, a.f, a.g, a.pose, train ? nullptr : a.c_theta,
                               train ? nullptr : a.c_xy, s);
     }

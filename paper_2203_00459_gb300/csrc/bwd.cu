@@ -3,7 +3,8 @@
 //
 // Given dL/d(theta, t_x, t_y) per pair, the kernels below produce dL/df and dL/dg.  The forward
 // intermediates are recomputed first (launch_forward into the workspace), or, in a training call,
-// are still in the workspace from that call's own forward; nothing is kept between calls.  Order of the adjoint, last forward step first:
+// are still in the workspace from that call's own forward; nothing is kept between calls.  Order
+// of the adjoint, last forward step first:
 //   k_b_rows     translation soft-argmax adjoint d c_xy (from the moments the forward kept),
 //                embedded in the P x P lag grid, real row FFTs
 //   k_b_cols     column FFTs of D, F' and G; conj(D) G (-> d f') and D F' (-> d g); inverse
@@ -381,70 +382,43 @@ __global__ void __launch_bounds__(256) k_b_theta(DevPlan p, const float* __restr
     for (int k = threadIdx.x; k < NT; k += blockDim.x) bdc[(size_t)q * NT + k] = z[spad(k)];
 }
 
-// Angle-correlation adjoint for a chunk of radii: recompute A^_f, A^_g (gather + FFT along angle as
-// in the forward), then d A_f = iFFT(conj(DC) A^_g) / n and d A_g = iFFT(DC A^_f) / n, both real,
-// packed as one inverse FFT of U_f + i U_g.
+// Angle-correlation adjoint for a chunk of radii: from the forward's Z = FFT along angle of
+// A_f + i A_g (kept in ahat), d A_f = iFFT(conj(DC) A^_g) / n and d A_g = iFFT(DC A^_f) / n, both
+// real, packed as one inverse FFT of U_f + i U_g.  Threads are radius-fastest; the first pass
+// forms U_f + i U_g straight from global memory (A^_f, A^_g from Z[k] and Z[n - k]) and the last
+// pass stores d A straight to global memory.
 template <int NT>
-__global__ void k_b_angle(DevPlan p, const float* __restrict__ mt, const float2* __restrict__ bdc,
-                          float* __restrict__ gpol, int B) {
-    constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC + 1;
+__global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_b_angle(DevPlan p, const float2* __restrict__ ahat,
+                                                                         const float2* __restrict__ bdc,
+                                                                         float* __restrict__ gpol, int B) {
+    constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC;
     extern __shared__ float2 sm[];
-    const int q = blockIdx.y, ch = blockIdx.x, r0 = ch * RC, n = p.n, W = n / 2;
-    const float* mf = mt + (size_t)q * (W + 1) * n;
-    const float* mg = mt + (size_t)(B + q) * (W + 1) * n;
-    for (int idx = threadIdx.x; idx < NT * RC; idx += blockDim.x) {
-        const int a = idx / RC, rr = idx % RC, r = r0 + rr;
-        float2 z = make_float2(0.f, 0.f);
-        if (r < p.nr) {
-            const PolarSample ps = p.polar[a * p.nr + r];
-            const float w00 = (1.f - ps.fy) * (1.f - ps.fx), w01 = (1.f - ps.fy) * ps.fx;
-            const float w10 = ps.fy * (1.f - ps.fx), w11 = ps.fy * ps.fx;
-            z.x = w00 * mag_at(mf, n, ps.y0, ps.x0) + w01 * mag_at(mf, n, ps.y0, ps.x0 + 1) +
-                  w10 * mag_at(mf, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mf, n, ps.y0 + 1, ps.x0 + 1);
-            z.y = w00 * mag_at(mg, n, ps.y0, ps.x0) + w01 * mag_at(mg, n, ps.y0, ps.x0 + 1) +
-                  w10 * mag_at(mg, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mg, n, ps.y0 + 1, ps.x0 + 1);
-        }
-        sm[spad(a) * ES + rr] = z;
-    }
-    __syncthreads();
-    const int rr0 = threadIdx.x / T, j = threadIdx.x % T;
-    const bool active = threadIdx.x < T * RC;
-    fft<NT, -1>(sm + rr0, ES, j, active, p.tw_t);
-    constexpr int PER = (NT * RC + T * RC - 1) / (T * RC);
-    float2 wv[PER];
+    const int q = blockIdx.y, ch = blockIdx.x;
+    const int rr = threadIdx.x % RC, j = threadIdx.x / RC, r = ch * RC + rr;
+    const bool live = r < p.nr;
+    const float2* Z = ahat + (size_t)q * NT * p.nr + r;
     const float2* DC = bdc + (size_t)q * NT;
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * blockDim.x;
-        if (idx < NT * RC) {
-            const int k = idx / RC, rr = idx % RC, km = k == 0 ? 0 : NT - k;
-            float2 af, ag;
-            split0(sm[spad(k) * ES + rr], sm[spad(km) * ES + rr], af, ag);
-            const float2 dc = __ldg(&DC[k]);
-            const float2 uf = c_cjmul(dc, ag), ug = c_mul(dc, af);
-            wv[m] = make_float2(uf.x - ug.y, uf.y + ug.x);
-        }
-    }
+    first_pass_global<NT, +1>(sm + rr, ES, j, [&](int k) {
+        if (!live) return make_float2(0.f, 0.f);
+        const int km = k == 0 ? 0 : NT - k;
+        float2 af, ag;
+        split0(__ldg(Z + (size_t)k * p.nr), __ldg(Z + (size_t)km * p.nr), af, ag);
+        const float2 dc = __ldg(&DC[k]);
+        const float2 uf = c_cjmul(dc, ag), ug = c_mul(dc, af);
+        return make_float2(uf.x - ug.y, uf.y + ug.x);
+    });
     __syncthreads();
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * blockDim.x;
-        if (idx < NT * RC) sm[spad(idx / RC) * ES + idx % RC] = wv[m];
-    }
-    __syncthreads();
-    fft<NT, +1>(sm + rr0, ES, j, active, p.tw_t);
     const float sc = 1.f / NT;
-    float* of = gpol + (size_t)q * NT * p.nr;
-    float* og = gpol + (size_t)(B + q) * NT * p.nr;
-    for (int idx = threadIdx.x; idx < NT * RC; idx += blockDim.x) {
-        const int a = idx / RC, rr = idx % RC, r = r0 + rr;
-        if (r < p.nr) {
-            const float2 v = sm[spad(a) * ES + rr];
-            of[a * p.nr + r] = v.x * sc;
-            og[a * p.nr + r] = v.y * sc;
+    float* of = gpol + (size_t)q * NT * p.nr + r;
+    float* og = gpol + (size_t)(B + q) * NT * p.nr + r;
+    rest_global<NT, +1>(sm + rr, ES, j, p.tw_t, [&](int a, float2 v) {
+        if (live) {
+            of[(size_t)a * p.nr] = v.x * sc;
+            og[(size_t)a * p.nr] = v.y * sc;
         }
-    }
+    });
 }
+
 
 // Transpose of the Cart2Pol gather: d a[e] = sum over the samples that read element e of the
 // half plane, with the forward's bilinear weights (precomputed CSR on the host).  Blocks below
@@ -476,88 +450,38 @@ __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float* __r
     if (lane == 0) out[e] = acc;
 }
 
-// |z| adjoint with the band-pass, then the column part of the half-plane DFT adjoint.  The
-// column FFT of the stage-1 row spectra is recomputed to get F; dF = d a band F/|F|.  The DFT
-// adjoint is d x[y,x] = Re sum_{v, u <= N/2} dF[v,u] exp(+2 pi i (v y + u x)/N): here the inverse
-// column transform, with interior columns halved (a real row transform counts them twice) and the
+// |z| adjoint with the band-pass, then the column part of the half-plane DFT adjoint:
+// dF = d a band F/|F| with the forward's kept phasors.  The DFT adjoint is
+// d x[y,x] = Re sum_{v, u <= N/2} dF[v,u] exp(+2 pi i (v y + u x)/N): here the inverse column
+// transform, with interior columns halved (a real row transform counts them twice) and the
 // DC/Nyquist columns made Hermitian (only the real part of their row sums counts) so that they
-// can share the packed column 0.
+// can share the packed column 0.  Threads are column-fastest; the first pass forms dF straight
+// from global memory and the last pass stores straight to it.
 template <int N>
-__global__ void __launch_bounds__(kThreads, 3) k_b_s1cols(DevPlan p, const float2* __restrict__ s1,
+__global__ void __launch_bounds__(kThreads) k_b_s1cols(DevPlan p, const float2* __restrict__ phs,
                                                        const float* __restrict__ gmt, float2* __restrict__ gs1,
                                                        int B) {
-    constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C + 1, W = N / 2, PER = C * N / kThreads;
+    constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C, W = N / 2;
     extern __shared__ float2 sm[];
-    float2* nyq = sm + spad(N) * ES;  // Nyquist column of the packed column 0
     const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
-    const float2* in = s1 + (size_t)(s * B + q) * N * W;
-    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
-        const int v = idx / C, c = idx % C;
-        cp_async8(&sm[spad(v) * ES + c], &in[(size_t)v * W + u0 + c]);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    fft<N, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
+    const int c = threadIdx.x % C, j = threadIdx.x / C, u = u0 + c;
     const float* dm = gmt + (size_t)(s * B + q) * (W + 1) * N;
-    auto unit = [](float2 z) {
-        const float a = sqrtf(fmaf(z.x, z.x, z.y * z.y));
-        return a > 0.f ? make_float2(z.x / a, z.y / a) : make_float2(0.f, 0.f);
-    };
-    float2 r0[PER], r1[PER];
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * kThreads, cc = idx / N, v = idx % N;
-        const int vs = v <= W ? v : v - N;
-        const float2 z = sm[spad(v) * ES + cc];
-        if (u0 + cc == 0) {
-            float2 a, b;
-            split0(z, sm[spad((N - v) & (N - 1)) * ES + cc], a, b);
-            const int m0 = vs * vs, mn = vs * vs + W * W;
-            const float g0 = (m0 >= p.m_lo && m0 <= p.m_hi) ? dm[v] : 0.f;
-            const float gn = (mn >= p.m_lo && mn <= p.m_hi) ? dm[(size_t)W * N + v] : 0.f;
-            r0[m] = c_scale(unit(a), g0);
-            r1[m] = c_scale(unit(b), gn);
-        } else {
-            const int u = u0 + cc, mm = vs * vs + u * u;
-            const float gv = (mm >= p.m_lo && mm <= p.m_hi) ? dm[(size_t)u * N + v] : 0.f;
-            r0[m] = c_scale(unit(z), 0.5f * gv);
-        }
-    }
+    const float2* ph = phs + (size_t)(s * B + q) * (W + 1) * N;
+    first_pass_global<N, +1>(sm + c, ES, j, [&](int v) {
+        if (u != 0) return c_scale(__ldg(ph + (size_t)u * N + v), 0.5f * __ldg(dm + (size_t)u * N + v));
+        // packed DC (u = 0) and Nyquist (u = N/2) columns, each made Hermitian
+        const int vm = (N - v) & (N - 1);
+        const float2 a = c_scale(__ldg(ph + v), __ldg(dm + v));
+        const float2 am = c_scale(__ldg(ph + vm), __ldg(dm + vm));
+        const float2 b = c_scale(__ldg(ph + (size_t)W * N + v), __ldg(dm + (size_t)W * N + v));
+        const float2 bm = c_scale(__ldg(ph + (size_t)W * N + vm), __ldg(dm + (size_t)W * N + vm));
+        const float2 sa = make_float2(0.5f * (a.x + am.x), 0.5f * (a.y - am.y));
+        const float2 sb = make_float2(0.5f * (b.x + bm.x), 0.5f * (b.y - bm.y));
+        return make_float2(sa.x - sb.y, sa.y + sb.x);
+    });
     __syncthreads();
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * kThreads, cc = idx / N, v = idx % N;
-        sm[spad(v) * ES + cc] = r0[m];
-        if (u0 + cc == 0) nyq[spad(v)] = r1[m];
-    }
-    __syncthreads();
-    if (u0 == 0) {  // uniform per block
-        float2 pk[(N + kThreads - 1) / kThreads];
-#pragma unroll
-        for (int m = 0; m < (N + kThreads - 1) / kThreads; ++m) {
-            const int v = threadIdx.x + m * kThreads;
-            if (v < N) {
-                const int vm = (N - v) & (N - 1);
-                const float2 a = sm[spad(v) * ES], am = sm[spad(vm) * ES], b = nyq[spad(v)], bm = nyq[spad(vm)];
-                const float2 sa = make_float2(0.5f * (a.x + am.x), 0.5f * (a.y - am.y));
-                const float2 sb = make_float2(0.5f * (b.x + bm.x), 0.5f * (b.y - bm.y));
-                pk[m] = make_float2(sa.x - sb.y, sa.y + sb.x);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < (N + kThreads - 1) / kThreads; ++m) {
-            const int v = threadIdx.x + m * kThreads;
-            if (v < N) sm[spad(v) * ES] = pk[m];
-        }
-        __syncthreads();
-    }
-    fft<N, +1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
-    float2* out = gs1 + (size_t)(s * B + q) * N * W;
-    for (int idx = threadIdx.x; idx < N * C; idx += kThreads) {
-        const int y = idx / C, cc = idx % C;
-        out[(size_t)y * W + u0 + cc] = sm[spad(y) * ES + cc];
-    }
+    float2* out = gs1 + (size_t)(s * B + q) * N * W + u;
+    rest_global<N, +1>(sm + c, ES, j, p.tw_n, [&](int y, float2 v) { out[(size_t)y * W] = v; });
 }
 
 // Row part of the half-plane DFT adjoint (a real inverse FFT of each row, two rows per complex
@@ -633,16 +557,16 @@ template <int P> constexpr size_t b_smem_cols() {
     return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T) * sizeof(float2);
 }
 template <int N> constexpr size_t b_smem_s1cols() {
-    return ((size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) + spad(N)) * sizeof(float2);
+    return (size_t)spad(N) * (kThreads / FftPlan<N>::T) * sizeof(float2);
 }
-template <int NT> constexpr size_t b_smem_angle() { return (size_t)spad(NT) * (kAngleRadii + 1) * sizeof(float2); }
+template <int NT> constexpr size_t b_smem_angle() { return (size_t)spad(NT) * kAngleRadii * sizeof(float2); }
 
 template <int NT>
 static void launch_stage1_adjoint(const DevPlan& p, const Ws& w, int B, cudaStream_t st) {
     w.tr->before(K_B_THETA, st);
     k_b_theta<NT><<<B, 256, 0, st>>>(p, w.ct, w.bsc, w.bdc);
     w.tr->before(K_B_ANGLE, st);
-    k_b_angle<NT><<<dim3(angle_chunks(p), B), FftPlan<NT>::T * kAngleRadii, b_smem_angle<NT>(), st>>>(p, w.mt, w.bdc,
+    k_b_angle<NT><<<dim3(angle_chunks(p), B), FftPlan<NT>::T * kAngleRadii, b_smem_angle<NT>(), st>>>(p, w.ahat, w.bdc,
                                                                                                     w.gpol, B);
 }
 
@@ -674,7 +598,7 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     const int hb = (p.n_heavy + kThreads / 32 - 1) / (kThreads / 32);
     k_b_polT<<<dim3(lb + hb, B, 2), kThreads, 0, st>>>(p, w.gpol, w.gmt, B, lb);
     w.tr->before(K_B_S1COLS, st);
-    k_b_s1cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st>>>(p, w.s1, w.gmt,
+    k_b_s1cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st>>>(p, w.phs, w.gmt,
                                                                                                  w.gs1, B);
     w.tr->before(K_B_S1ROWS, st);
     k_b_s1rows<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_rows<N>(), st>>>(p, tab, w.gs1, df, dg,

@@ -93,6 +93,9 @@ struct Ws {
     unsigned* cnt;  // [B] completion counters of the last-block reductions: a handle-wide array that
                     // is zero between launches (the last block of a pair resets its counter)
     float* ct;    // [B][n_theta]     angle scores in lag order (kept for the adjoint)
+    float2* ahat; // [B][n_theta][n_r] FFT along angle of A_f + i A_g, kept by the forward for the
+                  //                  adjoint (NULL: not kept)
+    float2* phs;  // [2][B][N/2+1][N] band-limited unit phasors F/|F| of stage 1, kept likewise
     // adjoint
     float* bpose; // [pairs][3]       recomputed pose, indexed by pair (handle-wide)
     float* bsc;   // [B][16]          per-pair scalars of the adjoint (d theta at 8)

@@ -53,10 +53,11 @@ __global__ void __launch_bounds__(kThreads) k_s1_rows(DevPlan p, const long long
 
 // Column FFTs of the packed row spectra, band-pass and magnitude.  Column 0 holds the DC and
 // Nyquist columns as one complex sequence; they are separated after the transform.  Output is
-// the u-major half plane m[u][v], u in [0, N/2], v in [0, N).
+// the u-major half plane m[u][v], u in [0, N/2], v in [0, N).  With ph non-NULL the band-limited
+// unit phasors F/|F| (0 outside the band or where F = 0) are kept for the adjoint, same layout.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* __restrict__ s1,
-                                                      float* __restrict__ mt, int B) {
+                                                      float* __restrict__ mt, float2* __restrict__ ph, int B) {
     constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C + 1, W = N / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
@@ -69,20 +70,25 @@ __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* _
     __syncthreads();
     fft<N, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
     float* out = mt + (size_t)(s * B + q) * (W + 1) * N;
+    float2* pho = ph ? ph + (size_t)(s * B + q) * (W + 1) * N : nullptr;
+    // |z| within the band (else 0), and the phasor z / |z| there
+    auto mag = [&](float2 z, int m2, size_t at) {
+        const bool in_band = m2 >= p.m_lo && m2 <= p.m_hi;
+        const float a = in_band ? sqrtf(fmaf(z.x, z.x, z.y * z.y)) : 0.f;
+        out[at] = a;
+        if (pho) pho[at] = a > 0.f ? make_float2(z.x / a, z.y / a) : make_float2(0.f, 0.f);
+    };
     for (int idx = threadIdx.x; idx < C * N; idx += kThreads) {
         const int cc = idx / N, v = idx % N;
         const int vs = v <= W ? v : v - N;
         const float2 z = sm[spad(v) * ES + cc];
         if (u0 + cc == 0) {
             const float2 zm = sm[spad((N - v) & (N - 1)) * ES + cc];
-            const float ax = 0.5f * (z.x + zm.x), ay = 0.5f * (z.y - zm.y);
-            const float bx = 0.5f * (z.y + zm.y), by = -0.5f * (z.x - zm.x);
-            const int m0 = vs * vs, mn = vs * vs + W * W;
-            out[v] = (m0 >= p.m_lo && m0 <= p.m_hi) ? sqrtf(fmaf(ax, ax, ay * ay)) : 0.f;
-            out[(size_t)W * N + v] = (mn >= p.m_lo && mn <= p.m_hi) ? sqrtf(fmaf(bx, bx, by * by)) : 0.f;
+            mag(make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y)), vs * vs, v);
+            mag(make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x)), vs * vs + W * W, (size_t)W * N + v);
         } else {
-            const int u = u0 + cc, m = vs * vs + u * u;
-            out[(size_t)u * N + v] = (m >= p.m_lo && m <= p.m_hi) ? sqrtf(fmaf(z.x, z.x, z.y * z.y)) : 0.f;
+            const int u = u0 + cc;
+            mag(z, vs * vs + u * u, (size_t)u * N + v);
         }
     }
 }
@@ -95,7 +101,8 @@ __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* _
 // shuffle reduction over the kAngleRadii lanes that hold one k.
 template <int NT>
 __global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_angle(DevPlan p, const float* __restrict__ mt,
-                                                                       float2* __restrict__ sp, int B) {
+                                                                       float2* __restrict__ sp,
+                                                                       float2* __restrict__ ahat, int B) {
     constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC;
     static_assert(RC == 16, "the shuffle sum runs over aligned groups of 16 lanes");
     extern __shared__ float2 sm[];
@@ -125,6 +132,7 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_angle(DevPlan 
     for (int m = 0; m < 16; ++m) {
         const int k = j + T * m, km = k == 0 ? 0 : NT - k;
         const float2 z = sm[spad(k) * ES + rr], zm = sm[spad(km) * ES + rr];
+        if (ahat && live) ahat[((size_t)q * NT + k) * p.nr + r] = z;   // kept for the adjoint
         const float ax = 0.5f * (z.x + zm.x), ay = 0.5f * (z.y - zm.y);
         const float bx = 0.5f * (z.y + zm.y), by = -0.5f * (z.x - zm.x);
         float sx = ax * bx + ay * by, sy = ax * by - ay * bx;
@@ -486,7 +494,7 @@ static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, con
                                        float* c_theta, cudaStream_t st) {
     const int nch = angle_chunks(p);
     w.tr->before(K_ANGLE, st);
-    k_angle<NT><<<dim3(nch, B), FftPlan<NT>::T * kAngleRadii, smem_angle<NT>(), st>>>(p, w.mt, w.sp, B);
+    k_angle<NT><<<dim3(nch, B), FftPlan<NT>::T * kAngleRadii, smem_angle<NT>(), st>>>(p, w.mt, w.sp, w.ahat, B);
     w.tr->before(K_THETA, st);
     k_theta<NT><<<B, 256, 0, st>>>(p, w.sp, nch, tab, w.th, pose, c_theta, w.ct);
     return cudaGetLastError();
@@ -499,7 +507,7 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
     w.tr->before(K_S1_ROWS, st);
     k_s1_rows<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st>>>(p, tab, f, g, w.s1, B);
     w.tr->before(K_S1_COLS, st);
-    k_s1_cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_cols1<N>(), st>>>(p, w.s1, w.mt, B);
+    k_s1_cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_cols1<N>(), st>>>(p, w.s1, w.mt, w.phs, B);
     cudaError_t e;
     if (p.nt == 128) e = launch_stage1_angle<128>(p, w, B, tab, pose, c_theta, st);
     else if (p.nt == 256) e = launch_stage1_angle<256>(p, w, B, tab, pose, c_theta, st);
