@@ -97,7 +97,7 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
         t.b2 = (float2*)take(2 * b * n * Wp * sizeof(float2));
         t.gfr = (float*)take(b * n * n * sizeof(float));
         t.bdc = (float2*)take(b * p.nt * sizeof(float2));
-        t.gpol = (float*)take(2 * b * p.nt * p.nr * sizeof(float));
+        t.gpol = (float2*)take(b * p.nt * p.nr * sizeof(float2));
         t.gmt = (float*)take(2 * b * (Wn + 1) * n * sizeof(float));
         t.gs1 = (float2*)take(2 * b * n * Wn * sizeof(float2));
     }

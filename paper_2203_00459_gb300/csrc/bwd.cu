@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(256) k_b_theta(DevPlan p, const float* __restr
 template <int NT>
 __global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_b_angle(DevPlan p, const float2* __restrict__ ahat,
                                                                          const float2* __restrict__ bdc,
-                                                                         float* __restrict__ gpol, int B) {
+                                                                         float2* __restrict__ gpol, int B) {
     constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, ch = blockIdx.x;
@@ -409,13 +409,9 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_b_angle(DevPla
     });
     __syncthreads();
     const float sc = 1.f / NT;
-    float* of = gpol + (size_t)q * NT * p.nr + r;
-    float* og = gpol + (size_t)(B + q) * NT * p.nr + r;
+    float2* o = gpol + (size_t)q * NT * p.nr + r;
     rest_global<NT, +1>(sm + rr, ES, j, p.tw_t, [&](int a, float2 v) {
-        if (live) {
-            of[(size_t)a * p.nr] = v.x * sc;
-            og[(size_t)a * p.nr] = v.y * sc;
-        }
+        if (live) o[(size_t)a * p.nr] = make_float2(v.x * sc, v.y * sc);
     });
 }
 
@@ -423,31 +419,50 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_b_angle(DevPla
 // Transpose of the Cart2Pol gather: d a[e] = sum over the samples that read element e of the
 // half plane, with the forward's bilinear weights (precomputed CSR on the host).  Blocks below
 // `light_blocks` give each element a thread and skip the heavy rows; the blocks after them give
-// each heavy row a warp (lane-strided taps, fixed-order warp sum).
-__global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float* __restrict__ gpol,
+// each heavy row a warp (lane-strided taps, fixed-order warp sum).  The f and g gradients of a
+// sample sit side by side, so one gathered sector serves both scans.
+__global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float2* __restrict__ gpol,
                                                      float* __restrict__ gmt, int B, int light_blocks) {
     const int n = p.n, E = (n / 2 + 1) * n;
-    const int q = blockIdx.y, s = blockIdx.z;
-    const float* da = gpol + (size_t)(s * B + q) * p.nt * p.nr;
-    float* out = gmt + (size_t)(s * B + q) * E;
+    const int q = blockIdx.y;
+    const float2* da = gpol + (size_t)q * p.nt * p.nr;   // (d A_f, d A_g) of each sample
+    float* of = gmt + (size_t)q * E;
+    float* og = gmt + (size_t)(B + q) * E;
     if ((int)blockIdx.x < light_blocks) {
         const int e = blockIdx.x * kThreads + threadIdx.x;
         if (e >= E) return;
         const int k0 = __ldg(&p.csr_ptr[e]), k1 = __ldg(&p.csr_ptr[e + 1]);
         if (k1 - k0 > kHeavyRow) return;
-        float acc = 0.f;
-        for (int k = k0; k < k1; ++k) acc += __ldg(&p.csr_w[k]) * __ldg(&da[__ldg(&p.csr_col[k])]);
-        out[e] = acc;
+        float af = 0.f, ag = 0.f;
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            const float w = __ldg(&p.csr_w[k]);
+            const float2 v = __ldg(&da[__ldg(&p.csr_col[k])]);
+            af += w * v.x;
+            ag += w * v.y;
+        }
+        of[e] = af;
+        og[e] = ag;
         return;
     }
     const int hw = ((int)blockIdx.x - light_blocks) * (kThreads / 32) + (threadIdx.x >> 5);
     if (hw >= p.n_heavy) return;
     const int e = __ldg(&p.heavy[hw]), lane = threadIdx.x & 31;
     const int k0 = __ldg(&p.csr_ptr[e]), k1 = __ldg(&p.csr_ptr[e + 1]);
-    float acc = 0.f;
-    for (int k = k0 + lane; k < k1; k += 32) acc += __ldg(&p.csr_w[k]) * __ldg(&da[__ldg(&p.csr_col[k])]);
-    acc = warp_sum(acc);
-    if (lane == 0) out[e] = acc;
+    float af = 0.f, ag = 0.f;
+#pragma unroll 4
+    for (int k = k0 + lane; k < k1; k += 32) {
+        const float w = __ldg(&p.csr_w[k]);
+        const float2 v = __ldg(&da[__ldg(&p.csr_col[k])]);
+        af += w * v.x;
+        ag += w * v.y;
+    }
+    af = warp_sum(af);
+    ag = warp_sum(ag);
+    if (lane == 0) {
+        of[e] = af;
+        og[e] = ag;
+    }
 }
 
 // |z| adjoint with the band-pass, then the column part of the half-plane DFT adjoint:
@@ -596,7 +611,7 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     w.tr->before(K_B_POLT, st);
     const int E = (N / 2 + 1) * N, lb = (E + kThreads - 1) / kThreads;
     const int hb = (p.n_heavy + kThreads / 32 - 1) / (kThreads / 32);
-    k_b_polT<<<dim3(lb + hb, B, 2), kThreads, 0, st>>>(p, w.gpol, w.gmt, B, lb);
+    k_b_polT<<<dim3(lb + hb, B), kThreads, 0, st>>>(p, w.gpol, w.gmt, B, lb);
     w.tr->before(K_B_S1COLS, st);
     k_b_s1cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st>>>(p, w.phs, w.gmt,
                                                                                                  w.gs1, B);

@@ -104,7 +104,7 @@ struct Ws {
     float2* b2;   // [2][B][N][P/2]   inverse column pass of conj(D) G and D F'
     float* gfr;   // [B][N][N]        d rotated source
     float2* bdc;  // [B][n_theta]     FFT of d c_theta along angle
-    float* gpol;  // [2][B][n_theta][n_r] d polar arrays
+    float2* gpol; // [B][n_theta][n_r] d polar arrays of (f, g)
     float* gmt;   // [2][B][N/2+1][N] d magnitudes
     float2* gs1;  // [2][B][N][N/2]   inverse column pass of the stage-1 adjoint
     Tracer* tr;   // launch tracer of the handle
