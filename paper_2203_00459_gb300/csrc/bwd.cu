@@ -222,15 +222,17 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
 // Rotate adjoint
 // ---------------------------------------------------------------------------------------------
 
-// One thread per pixel, which plays two roles:
+// One thread per pixel (kRotPixels pixels per thread), which plays two roles:
 //  (a) output pixel X of f': its d theta term d f'(X) (dv/dpx (py - c) - dv/dpy (px - c)), since
 //      d px / d theta = py - c and d py / d theta = -(px - c);
 //  (b) source pixel y of f: d f(y) = sum over the output pixels X whose bilinear sample reads y of
 //      weight * d f'(X).  Such X lie within sqrt 2 of X0 = c + R(theta)(y - c), i.e. in the 3 x 3
 //      box around its rounded position, and the bilinear weight of y in X's sample is the tent
 //      (1 - |dx|)(1 - |dy|) of the offset R(-theta)(X - X0) of that sample from y.
-// d theta is reduced per pair (last block adds the block sums in order) into bsc[q][8] together
-// with the direct term dL/dtheta.
+// The adjoint's coordinates are two fused multiply-adds (error ~ 1e-4 px at N = 512, which moves a
+// bilinear weight by as much; the forward's error-free coordinates decide the scores, these only
+// their gradient).  d theta is reduced per pair (last block adds the block sums in order) into
+// bsc[q][8] together with the direct term dL/dtheta.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* __restrict__ tab,
                                                     const float* __restrict__ f, const float* __restrict__ th,
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
     constexpr int NB = N * N / (kThreads * kRotPixels);
     const int q = blockIdx.y;
     const float* t = th + 8 * q;
-    const float ch = t[1], cl = t[2], sh = t[3], sl = t[4];
+    const float ct = t[1] + t[2], stn = t[3] + t[4];
     const float c = 0.5f * N;
     const float* src = f + tab[3 * q];
     const float* d = gfr + (size_t)q * N * N;
@@ -251,12 +253,13 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
     for (int m = 0; m < kRotPixels; ++m) {
         const int idx = (blockIdx.x * kRotPixels + m) * kThreads + threadIdx.x;
         const int Y = idx / N, X = idx % N;
-        // (a) d theta at output pixel X
+        const float dX = (float)X - c, dY = (float)Y - c;
+        // (a) d theta at output pixel X, sampled at c + R(-theta)(X - c)
         {
-            int x0, y0;
-            float fx, fy;
-            rot_coord(ch, cl, (float)X - c, sh, sl, (float)Y - c, c, x0, fx);
-            rot_coord(ch, cl, (float)Y - c, -sh, -sl, (float)X - c, c, y0, fy);
+            const float px = fmaf(ct, dX, fmaf(stn, dY, c)), py = fmaf(ct, dY, fmaf(-stn, dX, c));
+            const float fx0 = floorf(px), fy0 = floorf(py);
+            const int x0 = (int)fx0, y0 = (int)fy0;
+            const float fx = px - fx0, fy = py - fy0;
             auto at = [&](int yy, int xx) {
                 return ((unsigned)yy < (unsigned)N && (unsigned)xx < (unsigned)N) ? __ldg(src + (size_t)yy * N + xx)
                                                                                   : 0.f;
@@ -264,34 +267,27 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
             const float v00 = at(y0, x0), v01 = at(y0, x0 + 1), v10 = at(y0 + 1, x0), v11 = at(y0 + 1, x0 + 1);
             const float dvx = (1.f - fy) * (v01 - v00) + fy * (v11 - v10);
             const float dvy = (1.f - fx) * (v10 - v00) + fx * (v11 - v01);
-            const float pxc = ((float)x0 - c) + fx, pyc = ((float)y0 - c) + fy;
-            contrib += __ldg(d + idx) * (dvx * pyc - dvy * pxc);
+            contrib += __ldg(d + idx) * (dvx * (py - c) - dvy * (px - c));
         }
-        // (b) d f at source pixel (X, Y).  Its image X0 = c + R(theta)(y - c) (error-free
-        // coordinates); a candidate output pixel M samples at y + R(-theta)(M - X0), so its
-        // bilinear weight on y is the tent (1 - |dx|)(1 - |dy|) of (dx, dy) = R(-theta)(M - X0),
-        // small numbers exact to ~1e-7
+        // (b) d f at source pixel (X, Y): X0 = c + R(theta)(y - c); a candidate output pixel M
+        // samples at y + R(-theta)(M - X0), so its bilinear weight on y is the tent of
+        // (dx, dy) = R(-theta)(M - X0); the taps of the 3 x 3 box differ by constant steps
         {
-            int ix, iy;
-            float fx, fy;
-            rot_coord(ch, cl, (float)X - c, -sh, -sl, (float)Y - c, c, ix, fx);  // c + cos dx - sin dy
-            rot_coord(sh, sl, (float)X - c, ch, cl, (float)Y - c, c, iy, fy);    // c + sin dx + cos dy
-            const int mx0 = ix + (fx >= 0.5f ? 1 : 0) - 1, my0 = iy + (fy >= 0.5f ? 1 : 0) - 1;
-            const float ct = ch + cl, stn = sh + sl;
+            const float qx = fmaf(ct, dX, fmaf(-stn, dY, c)), qy = fmaf(stn, dX, fmaf(ct, dY, c));
+            const int mx0 = (int)floorf(qx + 0.5f) - 1, my0 = (int)floorf(qy + 0.5f) - 1;
+            const float ex0 = (float)mx0 - qx, ey0 = (float)my0 - qy;
+            const float dx0 = fmaf(ct, ex0, stn * ey0), dy0 = fmaf(ct, ey0, -stn * ex0);
             float acc = 0.f;
 #pragma unroll
             for (int oy = 0; oy < 3; ++oy) {
                 const int my = my0 + oy;
-                if ((unsigned)my >= (unsigned)N) continue;
-                const float ey = (float)(my - iy) - fy;
+                const float dxr = fmaf(stn, (float)oy, dx0), dyr = fmaf(ct, (float)oy, dy0);
 #pragma unroll
                 for (int ox = 0; ox < 3; ++ox) {
                     const int mx = mx0 + ox;
-                    if ((unsigned)mx >= (unsigned)N) continue;
-                    const float ex = (float)(mx - ix) - fx;
-                    const float dx = fmaf(ct, ex, stn * ey), dy = fmaf(ct, ey, -stn * ex);
-                    const float wx = 1.f - fabsf(dx), wy = 1.f - fabsf(dy);
-                    if (wx > 0.f && wy > 0.f) acc += wy * wx * __ldg(d + (size_t)my * N + mx);
+                    const float wx = 1.f - fabsf(fmaf(ct, (float)ox, dxr)), wy = 1.f - fabsf(fmaf(-stn, (float)ox, dyr));
+                    if (wx > 0.f && wy > 0.f && (unsigned)my < (unsigned)N && (unsigned)mx < (unsigned)N)
+                        acc = fmaf(wy * wx, __ldg(d + (size_t)my * N + mx), acc);
                 }
             }
             df[tab[3 * q] + idx] = acc;
