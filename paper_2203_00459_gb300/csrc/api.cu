@@ -91,6 +91,7 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
     if (backward) {
         t.ahat = (float2*)take(b * p.nt * p.nr * sizeof(float2));
         t.phs = (float2*)take(2 * b * (Wn + 1) * n * sizeof(float2));
+        t.s2hat = (float2*)take(2 * b * P * Wp * sizeof(float2));
         t.bsc = (float*)take(b * 16 * sizeof(float));
         t.gpart = (float*)take(b * (n * n / 256) * sizeof(float));
         t.b1 = (float2*)take(b * n * Wp * sizeof(float2));
@@ -352,6 +353,7 @@ cudaError_t launch_group(fmbym_handle* h, const Group& gr, const long long* dtab
         if (!train) {   // a plain forward keeps nothing for an adjoint
             w.ahat = nullptr;
             w.phs = nullptr;
+            w.s2hat = nullptr;
         }
         return launch_forward(p, w, gr.count, tab, a.f, a.g, a.pose, train ? nullptr : a.c_theta,
                               train ? nullptr : a.c_xy, s);

@@ -110,20 +110,19 @@ __device__ __forceinline__ void split0(float2 z, float2 zm, float2& a, float2& b
     b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
 }
 
-// Column pass of the correlation adjoint: FFT columns of D (lag rows placed at their P-rows) and
-// of G, Q1 = conj(D) G, inverse, keep the spatial rows y < N (-> d f'); then the same tile takes
-// F': FFT, Q2 = D F', inverse, keep y < N (-> d g).  The packed column 0 multiplies its DC and
-// Nyquist parts separately.  Two tiles are resident at a time.  As in the forward's column pass,
-// first passes read global memory, the forward's last pass, the product and the inverse's first
-// pass run in registers (D's transformed values stay in its tile for the second product), and the
-// inverse's last pass stores to global memory.
+// Column pass of the correlation adjoint: FFT the columns of D (lag rows placed at their P-rows),
+// Q1 = conj(D) G^ (-> d f') and Q2 = D F'^ (-> d g) with the column spectra F'^, G^ that the
+// forward kept (s2hat), inverse FFT both, keep the spatial rows y < N.  The packed column 0
+// multiplies its DC and Nyquist parts separately.  D's first pass reads global memory; its last
+// pass, both products and both inverses' first passes run in registers (the inverse in the
+// reverse radix order); both inverses' last passes store to global memory.
 template <int N, int P>
 __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_b_cols(DevPlan p, const float2* __restrict__ b1,
-                                                                       const float2* __restrict__ s2,
+                                                                       const float2* __restrict__ s2hat,
                                                                        float2* __restrict__ b2, int B) {
     using PL = FftPlan<P>;
     constexpr int TPB = tpb_for(P), T = PL::T, C = TPB / T, ES = C, W = P / 2, TILE = spad(P) * ES;
-    constexpr int RL = last_radix<P>(), NBL = P / RL, PER = P * C / TPB;
+    constexpr int RL = last_radix<P>(), NBL = P / RL, BPL = (NBL + T - 1) / T, PER = P * C / TPB;
     extern __shared__ float2 sm[];
     float2* tD = sm;
     float2* tX = sm + TILE;
@@ -131,67 +130,105 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_b_cols(DevPl
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const float2* __restrict__ tw = p.tw_p;
     const float2* inD = b1 + (size_t)q * N * W + u0 + c;
-    const float2* inF = s2 + (size_t)q * N * W + u0 + c;
-    const float2* inG = s2 + (size_t)(B + q) * N * W + u0 + c;
+    const float2* hF = s2hat + (size_t)q * P * W;          // F'^ [P][W]
+    const float2* hG = s2hat + (size_t)(B + q) * P * W;    // G^  [P][W]
     const float2 zero = make_float2(0.f, 0.f);
     // P-row v of D holds lag row i = (v + N/2) mod P (zero when i >= N)
-    first_pass_global2<P>(
-        tD + c, tX + c, ES, j,
-        [&](int v) {
-            const int i = v + N / 2 < P ? v + N / 2 : v + N / 2 - P;
-            return i < N ? __ldg(inD + (size_t)i * W) : zero;
-        },
-        [&](int v) { return v < N ? __ldg(inG + (size_t)v * W) : zero; });
+    first_pass_global<P>(tD + c, ES, j, [&](int v) {
+        const int i = v + N / 2 < P ? v + N / 2 : v + N / 2 - P;
+        return i < N ? __ldg(inD + (size_t)i * W) : zero;
+    });
     __syncthreads();
-    if constexpr (PL::NP == 3) fft_pass2<P, T, PL::R2, 16, -1>(tD + c, tX + c, ES, j, tw);
-    const bool col0 = blockIdx.x == 0;
-    if (col0) fft_pass2<P, T, RL, NBL, -1>(tD + c, tX + c, ES, j, tw);
-#pragma unroll 1
-    for (int phase = 0; phase < 2; ++phase) {
-        if (!col0) {
-            if (phase == 0)
-                fused_turn<P, 1>(tD + c, tX + c, ES, j, tw, [](float2 D, float2 X) { return c_cjmul(D, X); });
-            else
-                fused_turn<P, 2>(tD + c, tX + c, ES, j, tw, [](float2 D, float2 X) { return c_mul(D, X); });
-        } else {
-            if (phase == 1) fft_pass<P, T, RL, NBL, -1>(tX + c, ES, j, true, tw);
-            float2 qv[PER];
+    if constexpr (PL::NP == 3) fft_pass<P, T, PL::R2, 16, -1>(tD + c, ES, j, true, tw);
+    if (blockIdx.x != 0) {
+        const int u = u0 + c;
+        // D's last forward pass (final values back in place: same thread, same positions), then
+        // Q1 = conj(D) G^ and its inverse first pass straight into tX, which nothing reads here
 #pragma unroll
-            for (int m = 0; m < PER; ++m) {
-                const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-                const float2 D = tD[spad(v) * ES + cc], X = tX[spad(v) * ES + cc];
-                if (cc == 0) {
-                    const int vm = v == 0 ? 0 : P - v;
-                    float2 ad, bd, ax, bx;
-                    split0(D, tD[spad(vm) * ES + cc], ad, bd);
-                    split0(X, tX[spad(vm) * ES + cc], ax, bx);
-                    const float2 q0 = phase == 0 ? c_cjmul(ad, ax) : c_mul(ad, ax);
-                    const float2 qn = phase == 0 ? c_cjmul(bd, bx) : c_mul(bd, bx);
-                    qv[m] = make_float2(q0.x - qn.y, q0.y + qn.x);
-                } else {
-                    qv[m] = phase == 0 ? c_cjmul(D, X) : c_mul(D, X);
+        for (int m = 0; m < BPL; ++m) {
+            const int b = j + m * T;
+            if (NBL % T == 0 || b < NBL) {
+                float2 d[RL], o[RL];
+#pragma unroll
+                for (int t = 0; t < RL; ++t) d[t] = tD[spad(b + t * NBL) * ES + c];
+                twiddle<P, RL, NBL, -1>(d, b, tw);
+                dft<RL, -1>(d);
+#pragma unroll
+                for (int t = 0; t < RL; ++t) {
+                    tD[spad(b + t * NBL) * ES + c] = d[t];
+                    o[t] = c_cjmul(d[t], __ldg(hG + (size_t)(b + t * NBL) * W + u));
                 }
-            }
-            __syncthreads();
+                dft<RL, +1>(o);
 #pragma unroll
-            for (int m = 0; m < PER; ++m) {
-                const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
-                tX[spad(v) * ES + cc] = qv[m];
+                for (int t = 0; t < RL; ++t) tX[spad(RL * b + t) * ES + c] = o[t];
             }
-            __syncthreads();
-            fft_pass<P, T, RL, 1, +1>(tX + c, ES, j, true, tw);
         }
-        float2* o = b2 + (size_t)(phase * B + q) * N * W + u0 + c;
-        inverse_rest_global<P>(tX + c, ES, j, tw, [&](int y, float2 v) {
-            if (y < N) o[(size_t)y * W] = v;
-        });
-        if (phase == 0) {
-            __syncthreads();   // every thread has read tX
-            first_pass_global<P>(tX + c, ES, j, [&](int v) { return v < N ? __ldg(inF + (size_t)v * W) : zero; });
-            __syncthreads();
-            if constexpr (PL::NP == 3) fft_pass<P, T, PL::R2, 16, -1>(tX + c, ES, j, true, tw);
+        // Q2 = D F'^ from the thread's own final D values; written over tD once every thread
+        // has read its D
+        float2 o2[BPL][RL];
+#pragma unroll
+        for (int m = 0; m < BPL; ++m) {
+            const int b = j + m * T;
+            if (NBL % T == 0 || b < NBL) {
+#pragma unroll
+                for (int t = 0; t < RL; ++t)
+                    o2[m][t] = c_mul(tD[spad(b + t * NBL) * ES + c], __ldg(hF + (size_t)(b + t * NBL) * W + u));
+                dft<RL, +1>(o2[m]);
+            }
         }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < BPL; ++m) {
+            const int b = j + m * T;
+            if (NBL % T == 0 || b < NBL) {
+#pragma unroll
+                for (int t = 0; t < RL; ++t) tD[spad(RL * b + t) * ES + c] = o2[m][t];
+            }
+        }
+        __syncthreads();
+    } else {
+        // the tile holding column 0: D's last pass in shared memory, the products with the DC /
+        // Nyquist split (pairs v with P - v), then both inverses' first passes
+        fft_pass<P, T, RL, NBL, -1>(tD + c, ES, j, true, tw);
+        float2 q1[PER], q2[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C, u = u0 + cc;
+            const float2 D = tD[spad(v) * ES + cc];
+            const float2 G = __ldg(hG + (size_t)v * W + u), F = __ldg(hF + (size_t)v * W + u);
+            if (cc == 0) {
+                const int vm = v == 0 ? 0 : P - v;
+                float2 ad, bd, ag, bg, af, bf;
+                split0(D, tD[spad(vm) * ES + cc], ad, bd);
+                split0(G, __ldg(hG + (size_t)vm * W + u), ag, bg);
+                split0(F, __ldg(hF + (size_t)vm * W + u), af, bf);
+                const float2 g0 = c_cjmul(ad, ag), gn = c_cjmul(bd, bg);
+                const float2 f0 = c_mul(ad, af), fn = c_mul(bd, bf);
+                q1[m] = make_float2(g0.x - gn.y, g0.y + gn.x);
+                q2[m] = make_float2(f0.x - fn.y, f0.y + fn.x);
+            } else {
+                q1[m] = c_cjmul(D, G);
+                q2[m] = c_mul(D, F);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C;
+            tX[spad(v) * ES + cc] = q1[m];
+            tD[spad(v) * ES + cc] = q2[m];
+        }
+        __syncthreads();
+        fft_pass2<P, T, RL, 1, +1>(tX + c, tD + c, ES, j, tw);
     }
+    float2* o1 = b2 + (size_t)q * N * W + u0 + c;
+    float2* o2 = b2 + (size_t)(B + q) * N * W + u0 + c;
+    inverse_rest_global<P>(tX + c, ES, j, tw, [&](int y, float2 v) {
+        if (y < N) o1[(size_t)y * W] = v;
+    });
+    inverse_rest_global<P>(tD + c, ES, j, tw, [&](int y, float2 v) {
+        if (y < N) o2[(size_t)y * W] = v;
+    });
 }
 
 // Inverse row FFTs of the two adjoint spectra, keep x in [0, N), scale 1/P^2:
@@ -595,7 +632,7 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     k_b_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.xm, fwd_pose,
                                                                                    dpose, w.b1, B);
     w.tr->before(K_B_COLS, st);
-    k_b_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, b_smem_cols<P>(), st>>>(p, w.b1, w.s2, w.b2, B);
+    k_b_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, b_smem_cols<P>(), st>>>(p, w.b1, w.s2hat, w.b2, B);
     w.tr->before(K_B_C2R, st);
     k_b_c2r<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st>>>(p, tab, w.b2, w.gfr, dg, B);
     w.tr->before(K_B_ROT, st);

@@ -345,10 +345,11 @@ __device__ __forceinline__ void first_pass_global(float2* b0, int es, int j, Loa
 // the forward through the product to the inverse.  MODE_A = 0: a is transformed here; 1: a is
 // transformed here and its final values are stored back in place (same thread, same positions,
 // no barrier needed); 2: a already holds its final values.  prod(A, X) gives the product; the
-// inverse first pass's outputs go to tb.  Every thread of the CTA must call it.
-template <int L, int MODE_A, class Prod>
+// inverse first pass's outputs go to tb.  keep(pos, A, X) sees both transformed values at each
+// position (to store them for a later pass).  Every thread of the CTA must call it.
+template <int L, int MODE_A, class Prod, class Keep>
 __device__ __forceinline__ void fused_turn(float2* ta, float2* tb, int es, int j, const float2* __restrict__ tw,
-                                           Prod prod) {
+                                           Prod prod, Keep keep) {
     using PL = FftPlan<L>;
     constexpr int T = PL::T, RL = PL::NP == 3 ? PL::R3 : PL::R2, NBL = L / RL, BPL = (NBL + T - 1) / T;
     float2 o[BPL][RL];
@@ -373,7 +374,10 @@ __device__ __forceinline__ void fused_turn(float2* ta, float2* tb, int es, int j
             twiddle<L, RL, NBL, -1>(x, b, tw);
             dft<RL, -1>(x);
 #pragma unroll
-            for (int t = 0; t < RL; ++t) o[m][t] = prod(a[t], x[t]);
+            for (int t = 0; t < RL; ++t) {
+                keep(b + t * NBL, a[t], x[t]);
+                o[m][t] = prod(a[t], x[t]);
+            }
             dft<RL, +1>(o[m]);
         }
     }
@@ -387,6 +391,13 @@ __device__ __forceinline__ void fused_turn(float2* ta, float2* tb, int es, int j
         }
     }
     __syncthreads();
+}
+
+// fused_turn without keeping the transformed values.
+template <int L, int MODE_A, class Prod>
+__device__ __forceinline__ void fused_turn(float2* ta, float2* tb, int es, int j, const float2* __restrict__ tw,
+                                           Prod prod) {
+    fused_turn<L, MODE_A>(ta, tb, es, j, tw, prod, [](int, float2, float2) {});
 }
 
 // The inverse transform's remaining passes after fused_turn (or after its first pass): the middle

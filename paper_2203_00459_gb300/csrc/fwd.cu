@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long lo
 // of C consecutive columns.
 template <int N, int P>
 __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
-                                                      float2* __restrict__ s3, int B) {
+                                                      float2* __restrict__ s3, float2* __restrict__ s2hat, int B) {
     using PL = FftPlan<P>;
     constexpr int T = PL::T, TPB = tpb_for(P), C = TPB / T, ES = C, W = P / 2, TILE = spad(P) * ES;
     constexpr int RL = last_radix<P>(), NBL = P / RL;
@@ -284,12 +284,28 @@ __global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevP
         [&](int v) { return v < N ? __ldg(ing + (size_t)v * W) : make_float2(0.f, 0.f); });
     __syncthreads();
     if constexpr (PL::NP == 3) fft_pass2<P, T, PL::R2, 16, -1>(tf + c, tg + c, ES, j, tw);
+    // with s2hat the two transforms are kept for the adjoint ([2][B][P][P/2], row = P-position)
+    float2* kf = s2hat ? s2hat + (size_t)q * P * W : nullptr;
+    float2* kg = s2hat ? s2hat + (size_t)(B + q) * P * W : nullptr;
     if (blockIdx.x != 0) {
-        fused_turn<P, 0>(tf + c, tg + c, ES, j, tw, [](float2 F, float2 G) { return c_cjmul(F, G); });
+        fused_turn<P, 0>(tf + c, tg + c, ES, j, tw, [](float2 F, float2 G) { return c_cjmul(F, G); },
+                         [&](int pos, float2 F, float2 G) {
+                             if (kf) {
+                                 kf[(size_t)pos * W + u0 + c] = F;
+                                 kg[(size_t)pos * W + u0 + c] = G;
+                             }
+                         });
     } else {
         // the tile holding column 0: last forward pass in shared memory, then the products with
         // the DC / Nyquist split (which pairs v with P - v), then the inverse's first pass
         fft_pass2<P, T, RL, NBL, -1>(tf + c, tg + c, ES, j, tw);
+        if (kf) {
+            for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
+                const int v = idx / C, cc = idx % C;
+                kf[(size_t)v * W + u0 + cc] = tf[spad(v) * ES + cc];
+                kg[(size_t)v * W + u0 + cc] = tg[spad(v) * ES + cc];
+            }
+        }
         constexpr int PER = P * C / TPB;
         float2 qv[PER];
 #pragma unroll
@@ -516,7 +532,7 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
     w.tr->before(K_S2_ROWS, st);
     k_s2_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st>>>(p, tab, f, g, w.th, w.s2, B);
     w.tr->before(K_S2_COLS, st);
-    k_s2_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, smem_cols2<P>(), st>>>(p, w.s2, w.s3, B);
+    k_s2_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, smem_cols2<P>(), st>>>(p, w.s2, w.s3, w.s2hat, B);
     const int nblk = (N / 2) / (TB2 / T2);
     w.tr->before(K_S2_C2R, st);
     k_s2_c2r<N, P><<<dim3(nblk, B), TB2, smem_rows<P>(), st>>>(p, tab, w.s3, w.cxy, c_xy, w.st, B);
