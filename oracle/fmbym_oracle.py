@@ -251,6 +251,29 @@ def pose(f, g, cfg, keep=False):
     return out
 
 
+def pose_exhaustive(f, g, cfg, angles):
+    """The exhaustive rotate-then-correlate search that the decoupled search replaces (the
+    brute-force "raw" method of Tab. IIIa, Sec. I and III): every candidate heading theta_k is
+    tried by rotating the source (as stage 2 does) and correlating it with the target over the
+    same lags; the heading is the candidate with the highest correlation peak, the translation
+    that candidate's soft-argmax.  Returns dict(k, theta, tx, ty, peaks [len(angles)])."""
+    n = cfg["n"]
+    f = np.asarray(f, np.float64)
+    g = np.asarray(g, np.float64)
+    s = lags(n) * cfg["delta_xy"]
+    peaks = np.empty(len(angles))
+    best = None
+    for k, th in enumerate(angles):
+        c_xy = xcorr2d(rotate(f, float(th)), g, cfg["pad_mode"])
+        peaks[k] = c_xy.max()
+        if best is None or peaks[k] > peaks[best[0]]:
+            best = (k, c_xy)
+    k, c_xy = best
+    p_xy = soft_argmax(c_xy, cfg["temp_xy"], cfg["score_norm"])
+    return dict(k=k, theta=float(angles[k]), tx=float(np.sum(p_xy * s[None, :])),
+                ty=float(np.sum(p_xy * s[:, None])), peaks=peaks)
+
+
 def pose_batch(fs, gs, cfg):
     """Alg. 1 applied to each pair of a batch; returns (pose [B,3], c_theta [B,n_theta], c_xy [B,N,N])."""
     res = [pose(f, g, cfg) for f, g in zip(fs, gs)]

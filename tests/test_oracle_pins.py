@@ -382,3 +382,31 @@ def test_generator_is_deterministic_and_pairs_differ():
     assert not np.array_equal(f1[0], f1[1])
     f3, _, p3 = synth.make_batch("batch256", pairs=1, start=1)
     assert np.array_equal(f3[0], f1[1]) and np.array_equal(p3[0], p1[1])
+
+
+def test_exhaustive_search_recovers_a_grid_rotation_and_circular_shift():
+    # g is f turned by a quarter turn (an exact index permutation) and circularly shifted by an
+    # integer t: among headings 0, 45, ..., 315 degrees the exhaustive rotate-then-correlate
+    # search must pick 90 degrees, and its translation is t (a sharp soft-argmax, circular lags)
+    rng = np.random.default_rng(11)
+    n = 32
+    f = rng.random((n, n))
+    fr = O.rotate(f, np.pi / 2)
+    g = np.roll(fr, (-5, 3), axis=(0, 1))
+    cfg = O.make_cfg(n, 32, 16, temp_xy=0.01, pad_mode=1)
+    angles = np.arange(-4, 4) * (np.pi / 4)
+    r = O.pose_exhaustive(f, g, cfg, angles)
+    assert r["k"] == 6 and r["theta"] == np.pi / 2
+    assert abs(r["tx"] - 3) < 1e-6 and abs(r["ty"] + 5) < 1e-6
+    # the winning peak is the energy sum of the rotated source (Cauchy-Schwarz bound attained)
+    assert abs(r["peaks"][6] - np.sum(fr * fr)) <= 1e-9 * np.sum(fr * fr)
+    assert np.all(r["peaks"][np.arange(8) != 6] < r["peaks"][6])
+
+
+def test_exhaustive_search_of_identical_scans_is_the_identity():
+    f, _, _ = synth.make_batch("single128", pairs=1, start=3)
+    cfg = O.make_cfg(128, 128, 64)
+    r = O.pose_exhaustive(f[0], f[0], cfg, np.radians(np.arange(-10, 11)))
+    assert r["theta"] == 0.0
+    # (the unpaired -N/2 lag row and column leave a bias far below 1e-4 px)
+    assert abs(r["tx"]) < 1e-4 and abs(r["ty"]) < 1e-4
