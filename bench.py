@@ -297,6 +297,57 @@ def run_mixed(args):
     print(json.dumps(line), flush=True)
 
 
+def exhaustive_comparison(pairs=64, steps=3, warmup=1):
+    """The exhaustive rotate-then-correlate search against the decoupled search's forward on the
+    same 256^2 pairs of the batch256 workload: pairs/s of both (CUDA events, L2 flushed before each
+    timed call) and their mean absolute pose errors against the generator's ground truth.  The
+    exhaustive search runs once with 360 candidate headings 1 degree apart and once at equal
+    accuracy: a grid of step 4 e (e the decoupled search's mean heading error; a uniform grid of
+    step d errs by d / 4 on average), rounded to whole degrees."""
+    import numpy as np
+    import torch
+    from paper_2203_00459_gb300 import _lib, synth
+    from paper_2203_00459_gb300.search import PoseSearch, size_cfg
+    f, g, gt = synth.make_batch("batch256", pairs=pairs, start=1000)
+    cfg = size_cfg(256, 400, 128)
+    s = PoseSearch([cfg], max_pairs=pairs, flags=_lib.FLAG_GRAPH)
+    fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    pe = torch.empty((pairs, 3), device="cuda")
+    pd = torch.empty((pairs, 3), device="cuda")
+
+    def timed(fn, reps):
+        for _ in range(warmup):
+            fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms)
+
+    def err(p):
+        e = np.mean(np.abs(p.cpu().numpy().astype(np.float64) - gt), axis=0)
+        return {"theta_deg": float(np.degrees(e[0])), "tx_px": float(e[1]), "ty_px": float(e[2])}
+
+    ms_d = timed(lambda: s.pose(fd, gd, out=pd), max(10, steps))
+    out = {"workload": f"batch256, {pairs} pairs", "decoupled_fwd_pairs_per_s": pairs / (ms_d * 1e-3),
+           "mean_abs_err_decoupled": err(pd)}
+    step_eq = max(1, int(round(4.0 * out["mean_abs_err_decoupled"]["theta_deg"])))
+    for label, step in (("grid_1deg", 1), ("equal_accuracy", step_eq)):
+        angles = np.radians(np.arange(-180, 180, step, dtype=np.float64)).astype(np.float32)
+        ms_e = timed(lambda: s.pose_exhaustive(fd, gd, angles, out=pe), steps)
+        out[label] = {"step_deg": step, "candidates": int(angles.size),
+                      "exhaustive_pairs_per_s": pairs / (ms_e * 1e-3), "speedup_of_decoupled": ms_e / ms_d,
+                      "mean_abs_err_exhaustive": err(pe)}
+    s.close()
+    return out
+
+
 def run_masked256(args):
     """The learned-mask training step at 256^2, batch 64: U-Net forward, masked search, L1 pose loss,
     search adjoint, U-Net adjoint and Adam."""
@@ -568,6 +619,9 @@ def main():
             extra["batched_vs_plain_fwd"] = extra["fwd_pairs_per_s"] / extra["plain_fwd_pairs_per_s"]
             extra["batched_vs_plain_step"] = value / extra["plain_step_pairs_per_s"]
             one.close()
+
+    if rank == 0 and args.workload == WORKLOAD:
+        extra["exhaustive_256"] = exhaustive_comparison()
 
     cpu = None
     if pool is not None:

@@ -137,6 +137,23 @@ int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* s
 int fmbym_pose_loss(fmbym_handle* h, void* stream, int n_pairs, const float* pose, const float* gt,
                     int kind, float* loss, float* dpose);
 
+/* Exhaustive rotate-then-correlate search, the brute-force method the decoupled search replaces
+ * (the "raw" rows of Tab. IIIa; Sec. I and III).  For every candidate heading angles[k] the source
+ * is rotated and correlated with the target by the stage-2 steps of Alg. 1 (Rotate, ZeroPad and
+ * correlation, soft-argmax); the heading is the candidate with the highest correlation peak (the
+ * first on ties) and the translation that candidate's soft-argmax.
+ *   size      index into cfg->sizes; every pair of the call has this size
+ *   offsets   host long long[n_pairs] or NULL (packed), as fmbym_pose
+ *   f, g      device float32 scans, 16-byte aligned
+ *   n_angles  number of candidates (>= 1); angles host float[n_angles], radians
+ *   pose      device float32 [n_pairs][3] out: (theta, t_x, t_y)
+ *   peaks     device float32 [n_pairs][n_angles] out, or NULL: every candidate's correlation peak
+ * Runs n_angles stage-2 passes over the batch, launched directly.  Returns FMBYM_ERR_WORKSPACE
+ * if n_pairs exceeds max_pairs. */
+int fmbym_pose_exhaustive(fmbym_handle* h, void* stream, int n_pairs, int size, const long long* offsets,
+                          const float* f, const float* g, int n_angles, const float* angles, float* pose,
+                          float* peaks);
+
 /* One training step of the search (Sec. III-D, Eq. 12-13): the forward of fmbym_pose, the loss of
  * fmbym_pose_loss against gt, and the adjoint of fmbym_pose_backward for that loss, in one call.
  * The adjoint reads the forward's intermediates from the handle's workspace, where this call's

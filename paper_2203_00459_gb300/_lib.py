@@ -48,6 +48,7 @@ SIGNATURES = {
     "fmbym_pose_host": (_I, [_P, _P, _I, _P, _P, _LL, _P, _P, _P]),
     "fmbym_pose_loss": (_I, [_P, _P, _I, _P, _P, _I, _P, _P]),
     "fmbym_pose_train": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
+    "fmbym_pose_exhaustive": (_I, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P]),
     "fmbym_set_tracing": (_I, [_P, _I]),
     "fmbym_trace_summary": (_I, [_P, _I, _P, _P, _P]),
     "fmbym_trace_kind_name": (ctypes.c_char_p, [_I]),

@@ -60,6 +60,7 @@ struct fmbym_handle {
     float* d_stage_pose = nullptr;
     unsigned* d_cnt = nullptr;    // [max_pairs] completion counters, zero between launches
     float* d_bpose = nullptr;     // [max_pairs][3] pose recomputed by the adjoint
+    float4* d_best = nullptr;     // [max_pairs] running best of the exhaustive search
     long long stage_elems = 0;
     Tracer tracer;
     std::string err;
@@ -500,6 +501,7 @@ void fmbym_destroy(fmbym_handle* h) {
     cudaFree(h->d_stage_pose);
     cudaFree(h->d_cnt);
     cudaFree(h->d_bpose);
+    cudaFree(h->d_best);
     if (h->h_tab) cudaFreeHost(h->h_tab);
     for (cudaEvent_t e : h->tracer.ev) cudaEventDestroy(e);
     if (h->tab_free) cudaEventDestroy(h->tab_free);
@@ -580,7 +582,8 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
         (e = cudaMalloc(&h->d_stage_pose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_bpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess) {
+        (e = cudaMalloc(&h->d_bpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_best, sizeof(float4) * cfg->max_pairs)) != cudaSuccess) {
         fmbym_destroy(h);
         return cuda_fail(nullptr, e, "staging allocation");
     }
@@ -655,6 +658,40 @@ int fmbym_pose_train(fmbym_handle* h, void* stream, int n_pairs, const int* size
     a.df = df;
     a.dg = dg;
     return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
+}
+
+int fmbym_pose_exhaustive(fmbym_handle* h, void* stream, int n_pairs, int size, const long long* offsets,
+                          const float* f, const float* g, int n_angles, const float* angles, float* pose,
+                          float* peaks) {
+    if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    h->err.clear();
+    if (n_pairs == 0) return FMBYM_OK;
+    if (size < 0 || size >= (int)h->plans.size()) return fail(h, FMBYM_ERR_INVALID_ARG, "size index out of range");
+    if (n_angles < 1 || !angles) return fail(h, FMBYM_ERR_INVALID_ARG, "need n_angles >= 1 host angles");
+    if (!f || !g || !pose) return fail(h, FMBYM_ERR_INVALID_ARG, "f, g and pose must not be NULL");
+    if (!aligned16(f) || !aligned16(g)) return fail(h, FMBYM_ERR_INVALID_ARG, "f and g must be 16-byte aligned");
+    if (n_pairs < 0 || n_pairs > h->max_pairs) return fail(h, FMBYM_ERR_WORKSPACE, "n_pairs exceeds max_pairs");
+    std::vector<int> si((size_t)n_pairs, size);
+    std::vector<Group> groups;
+    int rc = make_table(h, n_pairs, si.data(), offsets, groups, nullptr);
+    if (rc != FMBYM_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaEventRecord(h->tab_free, st)) != cudaSuccess)
+        return cuda_fail(h, e, "pair table copy");
+    const Group& gr = groups[0];
+    const DevPlan& p = h->plans[size].dev;
+    Ws w = ws_carve(p, gr.count, h->ws[size], true);
+    w.tr = &h->tracer;
+    w.cnt = h->d_cnt + (size_t)size * h->max_pairs;
+    w.bpose = h->d_bpose;
+    w.s2hat = nullptr;   // nothing is kept for an adjoint
+    if ((e = launch_exhaustive(p, w, gr.count, h->d_tab, f, g, n_angles, angles, h->d_bpose, h->d_best, peaks, pose,
+                               st)) != cudaSuccess)
+        return cuda_fail(h, e, "exhaustive search launch");
+    return FMBYM_OK;
 }
 
 int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,

@@ -115,6 +115,13 @@ size_t ws_bytes(const DevPlan& p, int B, bool backward);
 Ws ws_carve(const DevPlan& p, int B, void* base, bool backward);
 
 // tab: device long long [B][3] = (scan offset, c_theta offset, pair index)
+// Stage 2 only, for the headings already in w.th (the exhaustive search's inner step).
+cudaError_t launch_forward_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                                  const float* g, float* pose, float* c_xy, cudaStream_t st);
+// Exhaustive rotate-then-correlate search over n_angles host headings (exhaustive.cu).
+cudaError_t launch_exhaustive(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                              const float* g, int n_angles, const float* angles, float* cand, float4* best,
+                              float* peaks, float* pose, cudaStream_t st);
 cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                            const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st);
 // fwd_pose: NULL recomputes the forward into the workspace first (the stateless adjoint); otherwise

@@ -505,6 +505,10 @@ template <int P> constexpr size_t smem_cols2() {
 }
 template <int NT> constexpr size_t smem_angle() { return (size_t)spad(NT) * kAngleRadii * sizeof(float2); }
 
+template <int N, int P>
+static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                                 const float* g, float* pose, float* c_xy, cudaStream_t st);
+
 template <int NT>
 static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, const long long* tab, float* pose,
                                        float* c_theta, cudaStream_t st) {
@@ -519,7 +523,7 @@ static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, con
 template <int N, int P>
 static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                              const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
-    constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T, TB2 = tpb_for(P);
+    constexpr int T1 = FftPlan<N>::T;
     w.tr->before(K_S1_ROWS, st);
     k_s1_rows<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st>>>(p, tab, f, g, w.s1, B);
     w.tr->before(K_S1_COLS, st);
@@ -529,6 +533,15 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
     else if (p.nt == 256) e = launch_stage1_angle<256>(p, w, B, tab, pose, c_theta, st);
     else e = launch_stage1_angle<400>(p, w, B, tab, pose, c_theta, st);
     if (e != cudaSuccess) return e;
+    return launch_stage2<N, P>(p, w, B, tab, f, g, pose, c_xy, st);
+}
+
+// Stage 2 of Alg. 1 for the headings in w.th: Rotate, the padded correlation and the translation
+// soft-argmax -> pose[.][1..2], block statistics of c_xy in w.st.
+template <int N, int P>
+static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                                 const float* g, float* pose, float* c_xy, cudaStream_t st) {
+    constexpr int T2 = FftPlan<P>::T, TB2 = tpb_for(P);
     w.tr->before(K_S2_ROWS, st);
     k_s2_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st>>>(p, tab, f, g, w.th, w.s2, B);
     w.tr->before(K_S2_COLS, st);
@@ -551,6 +564,17 @@ cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long
                                       : launch_np<256, 256>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
     return p.p == 768 ? launch_np<512, 768>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
                       : launch_np<512, 512>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+}
+
+cudaError_t launch_forward_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                                  const float* g, float* pose, float* c_xy, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    if (p.n == 128) return p.p == 192 ? launch_stage2<128, 192>(p, w, B, tab, f, g, pose, c_xy, st)
+                                      : launch_stage2<128, 128>(p, w, B, tab, f, g, pose, c_xy, st);
+    if (p.n == 256) return p.p == 384 ? launch_stage2<256, 384>(p, w, B, tab, f, g, pose, c_xy, st)
+                                      : launch_stage2<256, 256>(p, w, B, tab, f, g, pose, c_xy, st);
+    return p.p == 768 ? launch_stage2<512, 768>(p, w, B, tab, f, g, pose, c_xy, st)
+                      : launch_stage2<512, 512>(p, w, B, tab, f, g, pose, c_xy, st);
 }
 
 template <typename K>

@@ -132,6 +132,25 @@ class PoseSearch:
         _lib.check(st, self.handle)
         return pose, loss, dpose, df, dg
 
+    def pose_exhaustive(self, f, g, angles, size=0, offsets=None, want_peaks=False, stream=None, out=None):
+        """Exhaustive rotate-then-correlate search over the candidate headings `angles` (radians):
+        returns dict(pose [B, 3], peaks [B, len(angles)] or None).  Every pair has size `size`."""
+        if offsets is None:
+            n_pairs = f.shape[0]
+            off = None
+        else:
+            off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+            n_pairs = off.size
+        ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float32))
+        pose = out if out is not None else torch.empty((n_pairs, 3), device=f.device, dtype=torch.float32)
+        peaks = torch.empty((n_pairs, ang.size), device=f.device, dtype=torch.float32) if want_peaks else None
+        st = _lib.lib().fmbym_pose_exhaustive(self.handle, _stream(stream), n_pairs, int(size),
+                                              None if off is None else off.ctypes.data_as(ctypes.c_void_p),
+                                              _ptr(f), _ptr(g), int(ang.size), ang.ctypes.data_as(ctypes.c_void_p),
+                                              _ptr(pose), _ptr(peaks))
+        _lib.check(st, self.handle)
+        return dict(pose=pose, peaks=peaks)
+
     def pose_loss(self, pose, gt, kind=1, loss=None, dpose=None, stream=None):
         """Eq. 13 loss (kind 1 = L1, 2 = L2; mean over pairs) and dloss/dpose, on the device."""
         n_pairs = pose.shape[0]
