@@ -68,12 +68,26 @@ typedef struct fmbym_size_cfg {
 } fmbym_size_cfg;
 
 /* Handle flags.
- *   FMBYM_FLAG_GRAPH  capture each distinct call layout (forward or backward; pair count, sizes
- *                     and offsets; buffer pointers) into a CUDA graph on first use and replay it
- *                     with one launch afterwards (up to 16 layouts are kept, least recently used
- *                     released).  The first call of a layout must not happen while the caller's
- *                     stream is being captured.  Ignored while tracing is on. */
-enum fmbym_flags { FMBYM_FLAG_GRAPH = 1 };
+ *   FMBYM_FLAG_GRAPH     capture each distinct call layout (forward or backward; pair count, sizes
+ *                        and offsets; buffer pointers) into a CUDA graph on first use and replay it
+ *                        with one launch afterwards (up to 16 layouts are kept, least recently used
+ *                        released).  The first call of a layout must not happen while the caller's
+ *                        stream is being captured.  Ignored while tracing is on.
+ *   FMBYM_FLAG_AUTOTUNE  at creation, pick each size's launch schedules (fmbym_tune_knob) by
+ *                        timing a training call (fmbym_pose_train) of max_pairs synthetic pairs
+ *                        under every candidate, one schedule after another; the defaults are
+ *                        used otherwise.  Every schedule computes the same results up to float
+ *                        rounding order. */
+enum fmbym_flags { FMBYM_FLAG_GRAPH = 1, FMBYM_FLAG_AUTOTUNE = 2 };
+
+/* Launch schedules of a size (values for fmbym_get_tuning / fmbym_set_tuning):
+ *   FMBYM_TUNE_COL_TILE     columns per CTA of the stage-2 column passes: for the zero-padded
+ *                           lengths P = 3N/2 one of {C/2, C, 2C} with C = 192 / (P/16) (default C);
+ *                           otherwise C = 256 / (P/16) only
+ *   FMBYM_TUNE_ANGLE_RADII  radii per CTA of the angle correlation and its adjoint: 16 (default) or 8
+ *   FMBYM_TUNE_ROT_PIXELS   pixels per thread of the Rotate adjoint: 4 (default), 1, 2 or 8 */
+enum fmbym_tune_knob { FMBYM_TUNE_COL_TILE = 0, FMBYM_TUNE_ANGLE_RADII = 1, FMBYM_TUNE_ROT_PIXELS = 2,
+                       FMBYM_TUNE_COUNT = 3 };
 
 /* Handle configuration: n_sizes size configurations (host array, copied by fmbym_create),
  * the largest number of pairs one call may carry, and flags (fmbym_flags).  Pairs of different
@@ -153,6 +167,15 @@ int fmbym_pose_loss(fmbym_handle* h, void* stream, int n_pairs, const float* pos
 int fmbym_pose_exhaustive(fmbym_handle* h, void* stream, int n_pairs, int size, const long long* offsets,
                           const float* f, const float* g, int n_angles, const float* angles, float* pose,
                           float* peaks);
+
+/* The launch schedules of size `size` (host int[FMBYM_TUNE_COUNT] out, indexed by
+ * fmbym_tune_knob). */
+int fmbym_get_tuning(const fmbym_handle* h, int size, int* values);
+
+/* Sets the launch schedules of size `size` (host int[FMBYM_TUNE_COUNT]); every value must be one
+ * of its knob's candidates, else FMBYM_ERR_INVALID_ARG and nothing changes.  Releases the
+ * handle's captured graphs (they hold the previous schedules); synchronises the device. */
+int fmbym_set_tuning(fmbym_handle* h, int size, const int* values);
 
 /* One training step of the search (Sec. III-D, Eq. 12-13): the forward of fmbym_pose, the loss of
  * fmbym_pose_loss against gt, and the adjoint of fmbym_pose_backward for that loss, in one call.

@@ -13,6 +13,8 @@ LIB_PATH = os.path.join(HERE, "libfmbym.so")
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT = range(6)
 FLAG_GRAPH = 1
+FLAG_AUTOTUNE = 2
+TUNE_KNOBS = ("col_tile", "angle_radii", "rot_pixels")   # fmbym_tune_knob order
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE", 4: "CUDA", 5: "TIMEOUT"}
 
 
@@ -49,6 +51,8 @@ SIGNATURES = {
     "fmbym_pose_loss": (_I, [_P, _P, _I, _P, _P, _I, _P, _P]),
     "fmbym_pose_train": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
     "fmbym_pose_exhaustive": (_I, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P]),
+    "fmbym_get_tuning": (_I, [_P, _I, _P]),
+    "fmbym_set_tuning": (_I, [_P, _I, _P]),
     "fmbym_set_tracing": (_I, [_P, _I]),
     "fmbym_trace_summary": (_I, [_P, _I, _P, _P, _P]),
     "fmbym_trace_kind_name": (ctypes.c_char_p, [_I]),

@@ -80,7 +80,7 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
     Ws t{};
     t.s1 = (float2*)take(2 * b * n * Wn * sizeof(float2));
     t.mt = (float*)take(2 * b * (Wn + 1) * n * sizeof(float));
-    t.sp = (float2*)take(b * angle_chunks(p) * p.nt * sizeof(float2));
+    t.sp = (float2*)take(b * angle_chunks_max(p) * p.nt * sizeof(float2));
     t.th = (float*)take(b * 8 * sizeof(float));
     t.s2 = (float2*)take(2 * b * n * Wp * sizeof(float2));
     t.s3 = (float2*)take(b * n * Wp * sizeof(float2));
@@ -162,6 +162,9 @@ cudaError_t build_plan(HostPlan& hp) {
     DevPlan& d = hp.dev;
     d.n = c.n;
     d.p = c.pad_mode == 1 ? c.n : 3 * c.n / 2;  // zero pad to 1.5 N: lags |s| <= N/2 never alias
+    d.col_tile = tpb_for(d.p) / fft_threads(d.p);
+    d.angle_rc = kAngleRadii;
+    d.rot_px = kRotPixels;
     d.nt = c.n_theta;
     d.nr = c.n_r;
     d.window = c.window;
@@ -472,6 +475,115 @@ int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Gr
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
+// ---------------------------------------------------------------------------------------------
+// launch-schedule autotuner
+// ---------------------------------------------------------------------------------------------
+
+// Candidate values of one launch schedule of a size; the first is the default.
+std::vector<int> tune_candidates(const DevPlan& d, int knob) {
+    const int c0 = tpb_for(d.p) / fft_threads(d.p);
+    if (knob == FMBYM_TUNE_COL_TILE) return d.p % 3 == 0 ? std::vector<int>{c0, c0 / 2, 2 * c0} : std::vector<int>{c0};
+    if (knob == FMBYM_TUNE_ANGLE_RADII) return {kAngleRadii, kAngleRadiiMin};
+    return {kRotPixels, 1, 2, 8};
+}
+
+int& tune_field(DevPlan& d, int knob) {
+    return knob == FMBYM_TUNE_COL_TILE ? d.col_tile : knob == FMBYM_TUNE_ANGLE_RADII ? d.angle_rc : d.rot_px;
+}
+
+void release_graphs(fmbym_handle* h) {
+    for (auto& x : h->graphs) {
+        cudaGraphExecDestroy(x.exec);
+        cudaFree(x.d_tab);
+    }
+    h->graphs.clear();
+}
+
+// Scan-like test data for timing: a counter-based hash of (seed, index) mapped to [0, 1), cubed so
+// that most pixels are dim and a few bright (the timings do not depend on the values).
+__global__ void k_tune_fill(float* __restrict__ x, long long n, unsigned seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)i * 0x9E3779B1u ^ seed;
+        h ^= h >> 16;
+        h *= 0x85EBCA6Bu;
+        h ^= h >> 13;
+        h *= 0xC2B2AE35u;
+        h ^= h >> 16;
+        const float u = (float)(h >> 8) * (1.f / 16777216.f);
+        x[i] = u * u * u;
+    }
+}
+
+// Times a training call of max_pairs pairs of each size under every candidate of every schedule
+// (coordinate descent, one pass in knob order) and keeps the fastest.
+int autotune(fmbym_handle* h) {
+    const int saved_flags = h->flags;
+    h->flags &= ~FMBYM_FLAG_GRAPH;
+    cudaStream_t st = h->cap;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    int rc = e == cudaSuccess ? FMBYM_OK : FMBYM_ERR_CUDA;
+    for (size_t s = 0; s < h->plans.size() && rc == FMBYM_OK; ++s) {
+        const int n = h->plans[s].cfg.n, B = h->max_pairs;
+        const long long elems = (long long)B * n * n;
+        float *f = nullptr, *g = nullptr, *df = nullptr, *dg = nullptr, *small = nullptr;
+        if ((e = cudaMalloc(&f, sizeof(float) * elems)) != cudaSuccess || (e = cudaMalloc(&g, sizeof(float) * elems)) != cudaSuccess ||
+            (e = cudaMalloc(&df, sizeof(float) * elems)) != cudaSuccess || (e = cudaMalloc(&dg, sizeof(float) * elems)) != cudaSuccess ||
+            (e = cudaMalloc(&small, sizeof(float) * (9 * (size_t)B + 1))) != cudaSuccess ||
+            (e = cudaMemsetAsync(small, 0, sizeof(float) * (9 * (size_t)B + 1), st)) != cudaSuccess) {
+            rc = FMBYM_ERR_CUDA;
+        } else {
+            k_tune_fill<<<1024, 256, 0, st>>>(f, elems, 12345u + (unsigned)s);
+            k_tune_fill<<<1024, 256, 0, st>>>(g, elems, 67890u + (unsigned)s);
+            const std::vector<int> si((size_t)B, (int)s);
+            float *gt = small, *pose = small + 3 * B, *dpose = small + 6 * B, *loss = small + 9 * B;
+            auto timed = [&](float& ms) -> int {
+                float best = 1e30f;
+                for (int rep = 0; rep < 4 && rc == FMBYM_OK; ++rep) {
+                    if ((e = cudaEventRecord(a, st)) != cudaSuccess) return FMBYM_ERR_CUDA;
+                    const int r = fmbym_pose_train(h, st, B, si.data(), nullptr, f, g, gt, 2, pose, loss, dpose, df, dg);
+                    if (r != FMBYM_OK) return r;
+                    if ((e = cudaEventRecord(b, st)) != cudaSuccess || (e = cudaEventSynchronize(b)) != cudaSuccess)
+                        return FMBYM_ERR_CUDA;
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, a, b);
+                    if (rep > 0) best = std::min(best, t);   // the first call warms up
+                }
+                ms = best;
+                return FMBYM_OK;
+            };
+            DevPlan& d = h->plans[s].dev;
+            for (int knob = 0; knob < FMBYM_TUNE_COUNT && rc == FMBYM_OK; ++knob) {
+                const std::vector<int> cand = tune_candidates(d, knob);
+                int best_v = tune_field(d, knob);
+                float best_ms = 1e30f;
+                for (int v : cand) {
+                    tune_field(d, knob) = v;
+                    float ms = 0.f;
+                    if ((rc = timed(ms)) != FMBYM_OK) break;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best_v = v;
+                    }
+                }
+                tune_field(d, knob) = best_v;
+            }
+        }
+        cudaStreamSynchronize(st);
+        cudaFree(f);
+        cudaFree(g);
+        cudaFree(df);
+        cudaFree(dg);
+        cudaFree(small);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    h->flags = saved_flags;
+    if (rc != FMBYM_OK && h->err.empty()) h->err = std::string("autotune: ") + cudaGetErrorString(e);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -587,7 +699,43 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
         fmbym_destroy(h);
         return cuda_fail(nullptr, e, "staging allocation");
     }
+    if (cfg->flags & FMBYM_FLAG_AUTOTUNE) {
+        const int rc = autotune(h);
+        if (rc != FMBYM_OK) {
+            g_create_error = h->err;
+            fmbym_destroy(h);
+            return rc;
+        }
+    }
     *out = h;
+    return FMBYM_OK;
+}
+
+int fmbym_get_tuning(const fmbym_handle* h, int size, int* values) {
+    if (!h || !values) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle or values is NULL");
+    if (size < 0 || size >= (int)h->plans.size()) return FMBYM_ERR_INVALID_ARG;
+    const DevPlan& d = h->plans[size].dev;
+    values[FMBYM_TUNE_COL_TILE] = d.col_tile;
+    values[FMBYM_TUNE_ANGLE_RADII] = d.angle_rc;
+    values[FMBYM_TUNE_ROT_PIXELS] = d.rot_px;
+    return FMBYM_OK;
+}
+
+int fmbym_set_tuning(fmbym_handle* h, int size, const int* values) {
+    if (!h || !values) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle or values is NULL");
+    h->err.clear();
+    if (size < 0 || size >= (int)h->plans.size()) return fail(h, FMBYM_ERR_INVALID_ARG, "size index out of range");
+    DevPlan& d = h->plans[size].dev;
+    for (int knob = 0; knob < FMBYM_TUNE_COUNT; ++knob) {
+        const std::vector<int> cand = tune_candidates(d, knob);
+        if (std::find(cand.begin(), cand.end(), values[knob]) == cand.end())
+            return fail(h, FMBYM_ERR_INVALID_ARG, "schedule value " + std::to_string(values[knob]) + " of knob " +
+                                                      std::to_string(knob) + " is not a candidate");
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+    release_graphs(h);
+    for (int knob = 0; knob < FMBYM_TUNE_COUNT; ++knob) tune_field(d, knob) = values[knob];
     return FMBYM_OK;
 }
 

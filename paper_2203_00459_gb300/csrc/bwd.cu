@@ -116,12 +116,12 @@ __device__ __forceinline__ void split0(float2 z, float2 zm, float2& a, float2& b
 // multiplies its DC and Nyquist parts separately.  D's first pass reads global memory; its last
 // pass, both products and both inverses' first passes run in registers (the inverse in the
 // reverse radix order); both inverses' last passes store to global memory.
-template <int N, int P>
-__global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_b_cols(DevPlan p, const float2* __restrict__ b1,
+template <int N, int P, int C>
+__global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_cols(DevPlan p, const float2* __restrict__ b1,
                                                                        const float2* __restrict__ s2hat,
                                                                        float2* __restrict__ b2, int B) {
     using PL = FftPlan<P>;
-    constexpr int TPB = tpb_for(P), T = PL::T, C = TPB / T, ES = C, W = P / 2, TILE = spad(P) * ES;
+    constexpr int T = PL::T, TPB = C * T, ES = C, W = P / 2, TILE = spad(P) * ES;
     constexpr int RL = last_radix<P>(), NBL = P / RL, BPL = (NBL + T - 1) / T, PER = P * C / TPB;
     extern __shared__ float2 sm[];
     float2* tD = sm;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
 // Rotate adjoint
 // ---------------------------------------------------------------------------------------------
 
-// One thread per pixel (kRotPixels pixels per thread), which plays two roles:
+// One thread per pixel (PX pixels per thread), which plays two roles:
 //  (a) output pixel X of f': its d theta term d f'(X) (dv/dpx (py - c) - dv/dpy (px - c)), since
 //      d px / d theta = py - c and d py / d theta = -(px - c);
 //  (b) source pixel y of f: d f(y) = sum over the output pixels X whose bilinear sample reads y of
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
 // bilinear weight by as much; the forward's error-free coordinates decide the scores, these only
 // their gradient).  d theta is reduced per pair (last block adds the block sums in order) into
 // bsc[q][8] together with the direct term dL/dtheta.
-template <int N>
+template <int N, int PX>
 __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* __restrict__ tab,
                                                     const float* __restrict__ f, const float* __restrict__ th,
                                                     const float* __restrict__ gfr, const float* __restrict__ dpose,
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
                                                     unsigned* __restrict__ cnt, float* __restrict__ bsc) {
     __shared__ float red[32];
     __shared__ bool last;
-    constexpr int NB = N * N / (kThreads * kRotPixels);
+    constexpr int NB = N * N / (kThreads * PX);
     const int q = blockIdx.y;
     const float* t = th + 8 * q;
     const float ct = t[1] + t[2], stn = t[3] + t[4];
@@ -287,8 +287,8 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
     const float* d = gfr + (size_t)q * N * N;
     float contrib = 0.f;
 #pragma unroll
-    for (int m = 0; m < kRotPixels; ++m) {
-        const int idx = (blockIdx.x * kRotPixels + m) * kThreads + threadIdx.x;
+    for (int m = 0; m < PX; ++m) {
+        const int idx = (blockIdx.x * PX + m) * kThreads + threadIdx.x;
         const int Y = idx / N, X = idx % N;
         const float dX = (float)X - c, dY = (float)Y - c;
         // (a) d theta at output pixel X, sampled at c + R(-theta)(X - c)
@@ -420,11 +420,11 @@ __global__ void __launch_bounds__(256) k_b_theta(DevPlan p, const float* __restr
 // real, packed as one inverse FFT of U_f + i U_g.  Threads are radius-fastest; the first pass
 // forms U_f + i U_g straight from global memory (A^_f, A^_g from Z[k] and Z[n - k]) and the last
 // pass stores d A straight to global memory.
-template <int NT>
-__global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_b_angle(DevPlan p, const float2* __restrict__ ahat,
+template <int NT, int RC>
+__global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_b_angle(DevPlan p, const float2* __restrict__ ahat,
                                                                          const float2* __restrict__ bdc,
                                                                          float2* __restrict__ gpol, int B) {
-    constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC;
+    constexpr int T = FftPlan<NT>::T, ES = RC;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, ch = blockIdx.x;
     const int rr = threadIdx.x % RC, j = threadIdx.x / RC, r = ch * RC + rr;
@@ -601,21 +601,30 @@ cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, in
 // ---------------------------------------------------------------------------------------------
 
 template <int L> constexpr size_t b_smem_rows() { return (size_t)(tpb_for(L) / FftPlan<L>::T) * spad(L) * sizeof(float2); }
-template <int P> constexpr size_t b_smem_cols() {
-    return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T) * sizeof(float2);
-}
+template <int P, int C> constexpr size_t b_smem_cols() { return 2 * (size_t)spad(P) * C * sizeof(float2); }
 template <int N> constexpr size_t b_smem_s1cols() {
     return (size_t)spad(N) * (kThreads / FftPlan<N>::T) * sizeof(float2);
 }
-template <int NT> constexpr size_t b_smem_angle() { return (size_t)spad(NT) * kAngleRadii * sizeof(float2); }
+template <int NT, int RC> constexpr size_t b_smem_angle() { return (size_t)spad(NT) * RC * sizeof(float2); }
 
 template <int NT>
 static void launch_stage1_adjoint(const DevPlan& p, const Ws& w, int B, cudaStream_t st) {
     w.tr->before(K_B_THETA, st);
     k_b_theta<NT><<<B, 256, 0, st>>>(p, w.ct, w.bsc, w.bdc);
     w.tr->before(K_B_ANGLE, st);
-    k_b_angle<NT><<<dim3(angle_chunks(p), B), FftPlan<NT>::T * kAngleRadii, b_smem_angle<NT>(), st>>>(p, w.ahat, w.bdc,
-                                                                                                    w.gpol, B);
+    if (p.angle_rc == 8)
+        k_b_angle<NT, 8><<<dim3(angle_chunks(p), B), FftPlan<NT>::T * 8, b_smem_angle<NT, 8>(), st>>>(p, w.ahat, w.bdc,
+                                                                                                     w.gpol, B);
+    else
+        k_b_angle<NT, 16><<<dim3(angle_chunks(p), B), FftPlan<NT>::T * 16, b_smem_angle<NT, 16>(), st>>>(
+            p, w.ahat, w.bdc, w.gpol, B);
+}
+
+template <int N, int PX>
+static void launch_b_rot(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                         const float* dpose, float* df, cudaStream_t st) {
+    k_b_rot<N, PX><<<dim3(N * N / (kThreads * PX), B), kThreads, 0, st>>>(p, tab, f, w.th, w.gfr, dpose, df, w.gpart,
+                                                                          w.cnt, w.bsc);
 }
 
 template <int N, int P>
@@ -632,12 +641,28 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     k_b_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.xm, fwd_pose,
                                                                                    dpose, w.b1, B);
     w.tr->before(K_B_COLS, st);
-    k_b_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, b_smem_cols<P>(), st>>>(p, w.b1, w.s2hat, w.b2, B);
+    constexpr int C0 = TB2 / T2;   // the default tile; the 3 * 2^k lengths also have half and double
+    if constexpr (P % 3 == 0) {
+        if (p.col_tile == C0 / 2)
+            k_b_cols<N, P, C0 / 2><<<dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, b_smem_cols<P, C0 / 2>(), st>>>(
+                p, w.b1, w.s2hat, w.b2, B);
+        else if (p.col_tile == 2 * C0)
+            k_b_cols<N, P, 2 * C0><<<dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, b_smem_cols<P, 2 * C0>(), st>>>(
+                p, w.b1, w.s2hat, w.b2, B);
+        else
+            k_b_cols<N, P, C0><<<dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st>>>(p, w.b1, w.s2hat, w.b2, B);
+    } else {
+        k_b_cols<N, P, C0><<<dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st>>>(p, w.b1, w.s2hat, w.b2, B);
+    }
     w.tr->before(K_B_C2R, st);
     k_b_c2r<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st>>>(p, tab, w.b2, w.gfr, dg, B);
     w.tr->before(K_B_ROT, st);
-    k_b_rot<N><<<dim3(N * N / (kThreads * kRotPixels), B), kThreads, 0, st>>>(p, tab, f, w.th, w.gfr, dpose, df, w.gpart, w.cnt,
-                                                              w.bsc);
+    switch (p.rot_px) {
+        case 1: launch_b_rot<N, 1>(p, w, B, tab, f, dpose, df, st); break;
+        case 2: launch_b_rot<N, 2>(p, w, B, tab, f, dpose, df, st); break;
+        case 8: launch_b_rot<N, 8>(p, w, B, tab, f, dpose, df, st); break;
+        default: launch_b_rot<N, 4>(p, w, B, tab, f, dpose, df, st); break;
+    }
     if (p.nt == 128) launch_stage1_adjoint<128>(p, w, B, st);
     else if (p.nt == 256) launch_stage1_adjoint<256>(p, w, B, st);
     else launch_stage1_adjoint<400>(p, w, B, st);
@@ -676,7 +701,12 @@ template <int N, int P>
 static cudaError_t prepare_b() {
     cudaError_t e;
     if ((e = allow(k_b_rows<N, P>, b_smem_rows<P>())) != cudaSuccess) return e;
-    if ((e = allow(k_b_cols<N, P>, b_smem_cols<P>())) != cudaSuccess) return e;
+    constexpr int C0 = tpb_for(P) / FftPlan<P>::T;
+    if ((e = allow(k_b_cols<N, P, C0>, b_smem_cols<P, C0>())) != cudaSuccess) return e;
+    if constexpr (P % 3 == 0) {
+        if ((e = allow(k_b_cols<N, P, C0 / 2>, b_smem_cols<P, C0 / 2>())) != cudaSuccess) return e;
+        if ((e = allow(k_b_cols<N, P, 2 * C0>, b_smem_cols<P, 2 * C0>())) != cudaSuccess) return e;
+    }
     if ((e = allow(k_b_c2r<N, P>, b_smem_rows<P>())) != cudaSuccess) return e;
     if ((e = allow(k_b_s1cols<N>, b_smem_s1cols<N>())) != cudaSuccess) return e;
     return allow(k_b_s1rows<N>, b_smem_rows<N>());
@@ -690,9 +720,12 @@ cudaError_t prepare_backward_kernels() {
     if ((e = prepare_b<256, 256>()) != cudaSuccess) return e;
     if ((e = prepare_b<512, 768>()) != cudaSuccess) return e;
     if ((e = prepare_b<512, 512>()) != cudaSuccess) return e;
-    if ((e = allow(k_b_angle<128>, b_smem_angle<128>())) != cudaSuccess) return e;
-    if ((e = allow(k_b_angle<256>, b_smem_angle<256>())) != cudaSuccess) return e;
-    return allow(k_b_angle<400>, b_smem_angle<400>());
+    if ((e = allow(k_b_angle<128, 8>, b_smem_angle<128, 8>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_angle<256, 8>, b_smem_angle<256, 8>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_angle<400, 8>, b_smem_angle<400, 8>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_angle<128, 16>, b_smem_angle<128, 16>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_angle<256, 16>, b_smem_angle<256, 16>())) != cudaSuccess) return e;
+    return allow(k_b_angle<400, 16>, b_smem_angle<400, 16>());
 }
 
 }  // namespace fmbym

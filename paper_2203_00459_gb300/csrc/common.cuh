@@ -10,8 +10,11 @@
 namespace fmbym {
 
 constexpr int kThreads = 256;   // threads of the FFT kernels
-constexpr int kAngleRadii = 16;  // radii per CTA of the angle-correlation kernel
-constexpr int kRotPixels = 4;    // pixels per thread of the Rotate adjoint (one reduction per block)
+// Launch schedules with more than one compiled variant; each size's DevPlan names the variant its
+// launches use (the defaults below, or the autotuner's measured choice).
+constexpr int kAngleRadiiMin = 8;   // radii per CTA of the angle correlation and its adjoint: 8 or 16
+constexpr int kAngleRadii = 16;
+constexpr int kRotPixels = 4;       // pixels per thread of the Rotate adjoint: 1, 2, 4 or 8
 constexpr int kSplitXY = 32;    // CTAs per pair of the translation soft-argmax
 
 // One bilinear Cart2Pol sample: floor of the (u, v) frequency and the fractions.
@@ -40,11 +43,15 @@ struct DevPlan {
     // same few elements); the adjoint gives each of them a warp instead of a thread
     const int* heavy;
     int n_heavy;
+    // launch schedules: columns per CTA of the stage-2 column passes (half, the default, or twice
+    // tpb_for(P) / T), radii per CTA of the angle kernels, pixels per thread of the Rotate adjoint
+    int col_tile, angle_rc, rot_px;
 };
 
 constexpr int kHeavyRow = 32;
 
-inline int angle_chunks(const DevPlan& p) { return (p.nr + kAngleRadii - 1) / kAngleRadii; }
+inline int angle_chunks(const DevPlan& p) { return (p.nr + p.angle_rc - 1) / p.angle_rc; }
+inline int angle_chunks_max(const DevPlan& p) { return (p.nr + kAngleRadiiMin - 1) / kAngleRadiiMin; }
 inline int fft_threads(int L) { return L / 16 == 25 ? 25 : L / 16; }
 inline int c2r_blocks(const DevPlan& p) { return (p.n / 2) / (tpb_for(p.p) / fft_threads(p.p)); }
 

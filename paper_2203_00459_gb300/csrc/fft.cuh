@@ -485,4 +485,10 @@ template <int L> __host__ __device__ constexpr int last_radix() { return FftPlan
 // group size and 32 (192 for the 3 * 2^k lengths, 256 otherwise).
 __host__ __device__ constexpr int tpb_for(int L) { return (L % 3 == 0) ? 192 : 256; }
 
+// Minimum resident CTAs asked of the compiler for a column pass of length L with C columns per
+// CTA: the 3 * 2^k lengths keep 576 threads per SM (96 registers a thread), the others 512.
+__host__ __device__ constexpr int col_min_blocks(int L, int C) {
+    return (L % 3 == 0 ? 576 : 512) / (C * (L / 16)) > 0 ? (L % 3 == 0 ? 576 : 512) / (C * (L / 16)) : 1;
+}
+
 }  // namespace fmbym

@@ -93,18 +93,18 @@ __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* _
     }
 }
 
-// Cart2Pol of both magnitudes for kAngleRadii radii, packed as z[a] = A_f[a] + i A_g[a], FFT along
+// Cart2Pol of both magnitudes for RC radii, packed as z[a] = A_f[a] + i A_g[a], FFT along
 // angle, then S[k] = sum_r conj(A^_f[k, r]) A^_g[k, r] for this chunk of radii.  The inverse FFT of
 // S summed over chunks is the circular correlation along angle summed over radius (Eq. 7).
-// Threads are radius-fastest (rr = tid mod kAngleRadii): the polar table reads are contiguous, the
-// first FFT pass takes the bilinear samples straight from the gather, and the sum over radii is a
-// shuffle reduction over the kAngleRadii lanes that hold one k.
-template <int NT>
-__global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_angle(DevPlan p, const float* __restrict__ mt,
+// Threads are radius-fastest (rr = tid mod RC): the polar table reads are contiguous, the first FFT
+// pass takes the bilinear samples straight from the gather, and the sum over radii is a shuffle
+// reduction over the RC lanes that hold one k.
+template <int NT, int RC>
+__global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_angle(DevPlan p, const float* __restrict__ mt,
                                                                        float2* __restrict__ sp,
                                                                        float2* __restrict__ ahat, int B) {
-    constexpr int T = FftPlan<NT>::T, RC = kAngleRadii, ES = RC;
-    static_assert(RC == 16, "the shuffle sum runs over aligned groups of 16 lanes");
+    constexpr int T = FftPlan<NT>::T, ES = RC;
+    static_assert(RC == 8 || RC == 16, "the shuffle sum runs over aligned groups of RC lanes");
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, ch = blockIdx.x, n = p.n, W = n / 2;
     const int rr = threadIdx.x % RC, j = threadIdx.x / RC, r = ch * RC + rr;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * kAngleRadii) k_angle(DevPlan 
     __syncthreads();
     fft_passes_from<NT, -1, 2>(sm + rr, ES, j, p.tw_t);
     float2* out = sp + ((size_t)q * gridDim.x + ch) * NT;
-    const unsigned grp = 0xffffu << (threadIdx.x & 16);   // the 16 lanes of this thread's k
+    const unsigned grp = ((1u << RC) - 1u) << (threadIdx.x & (32 - RC));   // the RC lanes of this thread's k
 #pragma unroll 4
     for (int m = 0; m < 16; ++m) {
         const int k = j + T * m, km = k == 0 ? 0 : NT - k;
@@ -263,11 +263,11 @@ __global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long lo
 // straight to global memory.  Threads are column-fastest (c = tid mod C) over a tile of stride
 // C, which makes every shared access phase free of bank conflicts and every global access a run
 // of C consecutive columns.
-template <int N, int P>
-__global__ void __launch_bounds__(tpb_for(P), P % 3 == 0 ? 3 : 2) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
+template <int N, int P, int C>
+__global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
                                                       float2* __restrict__ s3, float2* __restrict__ s2hat, int B) {
     using PL = FftPlan<P>;
-    constexpr int T = PL::T, TPB = tpb_for(P), C = TPB / T, ES = C, W = P / 2, TILE = spad(P) * ES;
+    constexpr int T = PL::T, TPB = C * T, ES = C, W = P / 2, TILE = spad(P) * ES;
     constexpr int RL = last_radix<P>(), NBL = P / RL;
     extern __shared__ float2 sm[];
     float2* tf = sm;
@@ -500,10 +500,8 @@ template <int L> constexpr size_t smem_rows() { return (size_t)(tpb_for(L) / Fft
 template <int N> constexpr size_t smem_cols1() {
     return (size_t)spad(N) * (kThreads / FftPlan<N>::T + 1) * sizeof(float2);
 }
-template <int P> constexpr size_t smem_cols2() {
-    return 2 * (size_t)spad(P) * (tpb_for(P) / FftPlan<P>::T) * sizeof(float2);
-}
-template <int NT> constexpr size_t smem_angle() { return (size_t)spad(NT) * kAngleRadii * sizeof(float2); }
+template <int P, int C> constexpr size_t smem_cols2() { return 2 * (size_t)spad(P) * C * sizeof(float2); }
+template <int NT, int RC> constexpr size_t smem_angle() { return (size_t)spad(NT) * RC * sizeof(float2); }
 
 template <int N, int P>
 static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
@@ -514,7 +512,10 @@ static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, con
                                        float* c_theta, cudaStream_t st) {
     const int nch = angle_chunks(p);
     w.tr->before(K_ANGLE, st);
-    k_angle<NT><<<dim3(nch, B), FftPlan<NT>::T * kAngleRadii, smem_angle<NT>(), st>>>(p, w.mt, w.sp, w.ahat, B);
+    if (p.angle_rc == 8)
+        k_angle<NT, 8><<<dim3(nch, B), FftPlan<NT>::T * 8, smem_angle<NT, 8>(), st>>>(p, w.mt, w.sp, w.ahat, B);
+    else
+        k_angle<NT, 16><<<dim3(nch, B), FftPlan<NT>::T * 16, smem_angle<NT, 16>(), st>>>(p, w.mt, w.sp, w.ahat, B);
     w.tr->before(K_THETA, st);
     k_theta<NT><<<B, 256, 0, st>>>(p, w.sp, nch, tab, w.th, pose, c_theta, w.ct);
     return cudaGetLastError();
@@ -545,7 +546,19 @@ static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const lon
     w.tr->before(K_S2_ROWS, st);
     k_s2_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st>>>(p, tab, f, g, w.th, w.s2, B);
     w.tr->before(K_S2_COLS, st);
-    k_s2_cols<N, P><<<dim3((P / 2) / (TB2 / T2), B), TB2, smem_cols2<P>(), st>>>(p, w.s2, w.s3, w.s2hat, B);
+    constexpr int C0 = TB2 / T2;   // the default tile; the 3 * 2^k lengths also have half and double
+    if constexpr (P % 3 == 0) {
+        if (p.col_tile == C0 / 2)
+            k_s2_cols<N, P, C0 / 2><<<dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, smem_cols2<P, C0 / 2>(), st>>>(
+                p, w.s2, w.s3, w.s2hat, B);
+        else if (p.col_tile == 2 * C0)
+            k_s2_cols<N, P, 2 * C0><<<dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, smem_cols2<P, 2 * C0>(), st>>>(
+                p, w.s2, w.s3, w.s2hat, B);
+        else
+            k_s2_cols<N, P, C0><<<dim3((P / 2) / C0, B), TB2, smem_cols2<P, C0>(), st>>>(p, w.s2, w.s3, w.s2hat, B);
+    } else {
+        k_s2_cols<N, P, C0><<<dim3((P / 2) / C0, B), TB2, smem_cols2<P, C0>(), st>>>(p, w.s2, w.s3, w.s2hat, B);
+    }
     const int nblk = (N / 2) / (TB2 / T2);
     w.tr->before(K_S2_C2R, st);
     k_s2_c2r<N, P><<<dim3(nblk, B), TB2, smem_rows<P>(), st>>>(p, tab, w.s3, w.cxy, c_xy, w.st, B);
@@ -588,7 +601,12 @@ static cudaError_t prepare_np() {
     if ((e = allow_smem(k_s1_rows<N>, smem_rows<N>())) != cudaSuccess) return e;
     if ((e = allow_smem(k_s1_cols<N>, smem_cols1<N>())) != cudaSuccess) return e;
     if ((e = allow_smem(k_s2_rows<N, P>, smem_rows<P>())) != cudaSuccess) return e;
-    if ((e = allow_smem(k_s2_cols<N, P>, smem_cols2<P>())) != cudaSuccess) return e;
+    constexpr int C0 = tpb_for(P) / FftPlan<P>::T;
+    if ((e = allow_smem(k_s2_cols<N, P, C0>, smem_cols2<P, C0>())) != cudaSuccess) return e;
+    if constexpr (P % 3 == 0) {
+        if ((e = allow_smem(k_s2_cols<N, P, C0 / 2>, smem_cols2<P, C0 / 2>())) != cudaSuccess) return e;
+        if ((e = allow_smem(k_s2_cols<N, P, 2 * C0>, smem_cols2<P, 2 * C0>())) != cudaSuccess) return e;
+    }
     return allow_smem(k_s2_c2r<N, P>, smem_rows<P>());
 }
 
@@ -605,9 +623,12 @@ cudaError_t prepare_forward_kernels() {
     if ((e = prepare_np<256, 256>()) != cudaSuccess) return e;
     if ((e = prepare_np<512, 768>()) != cudaSuccess) return e;
     if ((e = prepare_np<512, 512>()) != cudaSuccess) return e;
-    if ((e = allow_smem(k_angle<128>, smem_angle<128>())) != cudaSuccess) return e;
-    if ((e = allow_smem(k_angle<256>, smem_angle<256>())) != cudaSuccess) return e;
-    return allow_smem(k_angle<400>, smem_angle<400>());
+    if ((e = allow_smem(k_angle<128, 8>, smem_angle<128, 8>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_angle<256, 8>, smem_angle<256, 8>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_angle<400, 8>, smem_angle<400, 8>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_angle<128, 16>, smem_angle<128, 16>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_angle<256, 16>, smem_angle<256, 16>())) != cudaSuccess) return e;
+    return allow_smem(k_angle<400, 16>, smem_angle<400, 16>());
 }
 
 }  // namespace fmbym

@@ -161,6 +161,9 @@ int fmbym_pose_noalloc(void* stream, const fmbym_size_cfg* cfg, int n_pairs, con
     p.temp_theta = cfg->temp_theta;
     p.temp_xy = cfg->temp_xy;
     p.delta_xy = cfg->delta_xy;
+    p.col_tile = tpb_for(p.p) / fft_threads(p.p);   // the default launch schedules
+    p.angle_rc = kAngleRadii;
+    p.rot_px = kRotPixels;
     const int mmax = (cfg->n / 2) * (cfg->n / 2) * 2;
     p.m_lo = mmax + 1;
     p.m_hi = -1;

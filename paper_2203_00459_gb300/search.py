@@ -65,6 +65,19 @@ class PoseSearch:
         except Exception:
             pass
 
+    def tuning(self, size=0):
+        """The launch schedules of a size: dict(col_tile, angle_radii, rot_pixels)."""
+        v = (ctypes.c_int * len(_lib.TUNE_KNOBS))()
+        _lib.check(_lib.lib().fmbym_get_tuning(self.handle, int(size), v), self.handle)
+        return dict(zip(_lib.TUNE_KNOBS, list(v)))
+
+    def set_tuning(self, size=0, **values):
+        """Sets launch schedules of a size (unnamed knobs keep their values)."""
+        cur = self.tuning(size)
+        cur.update(values)
+        v = (ctypes.c_int * len(_lib.TUNE_KNOBS))(*[int(cur[k]) for k in _lib.TUNE_KNOBS])
+        _lib.check(_lib.lib().fmbym_set_tuning(self.handle, int(size), v), self.handle)
+
     def workspace_bytes(self):
         return int(_lib.lib().fmbym_workspace_bytes(self.handle))
 
