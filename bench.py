@@ -416,8 +416,10 @@ def main():
     n, nt, nr = spec["n"], spec["n_theta"], spec["n_r"]
     f, g, gt = synth.make_batch(args.workload, pairs=B, start=rank * B)
     cfg = size_cfg(n, nt, nr)
-    search = PoseSearch([cfg], max_pairs=B, flags=_lib.FLAG_GRAPH)   # production path: graph replays
+    # production path: graph replays, launch schedules picked by the library's autotuner
+    search = PoseSearch([cfg], max_pairs=B, flags=_lib.FLAG_GRAPH | _lib.FLAG_AUTOTUNE)
     traced = PoseSearch([cfg], max_pairs=B)                          # direct launches, per-kernel events
+    traced.set_tuning(0, **search.tuning(0))
     L = _lib.lib()
     fd = torch.from_numpy(f).cuda()
     gd = torch.from_numpy(g).cuda()
@@ -635,7 +637,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "mode": args.mode,
                 "config": {"workload": args.workload, "n": n, "n_theta": nt, "n_r": nr, "pairs_per_gpu": B,
-                           "pad": "zero to 1.5N (same lags as 2N)", "l2": "flushed (256 MB write) between timed steps"},
+                           "pad": "zero to 1.5N (same lags as 2N)", "l2": "flushed (256 MB write) between timed steps",
+                           "schedules": search.tuning(0)},
                 "roofline": roof, "kernel_shares": shares, "ms_per_step_direct_launch": ms_traced,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, **extra}
