@@ -387,9 +387,8 @@ def main():
     if args.workload == "masked256" and args.impl == "ours":
         return run_masked256(args)
     spec = dict(synth.WORKLOADS[args.workload if args.workload in synth.WORKLOADS else "batch256"])
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2203_00459_gb300 import replicas
+    world, rank, local = replicas.world()
     if args.impl == "reference":
         run_reference(args, spec, rank)
         return
@@ -407,14 +406,12 @@ def main():
     from paper_2203_00459_gb300.search import PoseSearch, size_cfg
 
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = replicas.init("nccl")
 
     B = spec["pairs"]
     n, nt, nr = spec["n"], spec["n_theta"], spec["n_r"]
-    f, g, gt = synth.make_batch(args.workload, pairs=B, start=rank * B)
+    first, _ = replicas.shard(B, rank)
+    f, g, gt = synth.make_batch(args.workload, pairs=B, start=first)
     cfg = size_cfg(n, nt, nr)
     # production path: graph replays, launch schedules picked by the library's autotuner
     search = PoseSearch([cfg], max_pairs=B, flags=_lib.FLAG_GRAPH | _lib.FLAG_AUTOTUNE)
@@ -467,8 +464,7 @@ def main():
     clocks.start()
     time.sleep(0.3)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.zero_()
@@ -476,16 +472,11 @@ def main():
         step()
         evs[k][1].record()
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     clk = clocks.stop()
     launches = L.fmbym_launch_count(search.handle) - launches0
     ms = [a.elapsed_time(b) for a, b in evs]
-    ms_step = sum(ms) / len(ms)
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = replicas.max_over_ranks(sum(ms) / len(ms), dist, device="cuda")
 
     # ---- second timed region, same K steps launched directly with the library's tracer on: the
     # event before each launch gives every kernel's device time on the launching stream ----
@@ -512,7 +503,7 @@ def main():
         if cnt[k]:
             kernels[L.fmbym_trace_kind_name(k).decode()] = (tot[k], cnt[k])
 
-    value = world * B / (ms_step * 1e-3)
+    value = replicas.job_rate(world, B, ms_step)
 
     # ---- dominant kernel roofline ----
     chunks = (nr + 15) // 16
