@@ -46,27 +46,30 @@ def parse():
 # ---------------------------------------------------------------------------------------------
 
 def kernel_model(n, p, nt, nr, chunks):
+    """Compulsory HBM bytes and nominal FFT FLOPs per pair of every kernel of the training step
+    (each input read once, each output written once; the training call's forward also writes the
+    arrays it keeps for the adjoint: phasors, angle spectra, column spectra)."""
     w, wp = n // 2, p // 2
     c = 8  # bytes of a complex float
     fft = lambda L: 5.0 * L * math.log2(L)  # nominal FLOPs of one complex length-L FFT
+    half = (w + 1) * n                      # elements of a half plane
     m = {
         "s1_rows": (2 * n * n * 4 + 2 * n * w * c, 2 * (n // 2) * fft(n)),
-        "s1_cols": (2 * n * w * c + 2 * (w + 1) * n * 4, 2 * w * fft(n)),
-        "angle": (2 * (w + 1) * n * 4 + chunks * nt * c, nr * fft(nt)),
+        "s1_cols": (2 * n * w * c + 2 * half * 4 + 2 * half * c, 2 * w * fft(n)),
+        "angle": (2 * half * 4 + chunks * nt * c + nt * nr * c, nr * fft(nt)),
         "theta": (chunks * nt * c + nt * 4, fft(nt)),
         "s2_rows": (2 * n * n * 4 + 2 * n * wp * c, 2 * (n // 2) * fft(p)),
-        "s2_cols": (2 * n * wp * c + n * wp * c, 3 * wp * fft(p)),
+        "s2_cols": (2 * n * wp * c + n * wp * c + 2 * p * wp * c, 3 * wp * fft(p)),
         "s2_c2r": (n * wp * c + n * n * 4, (n // 2) * fft(p)),
         "sxy": (n * n * 4, 0.0),
-        "b_sxy": (n * n * 4, 0.0),
         "b_rows": (n * n * 4 + n * wp * c, (n // 2) * fft(p)),
-        "b_cols": (3 * n * wp * c + 2 * n * wp * c, 5 * wp * fft(p)),
+        "b_cols": (n * wp * c + 2 * p * wp * c + 2 * n * wp * c, 3 * wp * fft(p)),
         "b_c2r": (2 * n * wp * c + 2 * n * n * 4, n * fft(p)),
         "b_rot": (3 * n * n * 4, 0.0),
         "b_theta": (nt * 4 + nt * c, fft(nt)),
-        "b_angle": (2 * (w + 1) * n * 4 + 2 * nt * nr * 4, 2 * nr * fft(nt)),
-        "b_polT": (2 * nt * nr * 4 + 2 * (w + 1) * n * 4, 0.0),
-        "b_s1cols": (2 * n * w * c + 2 * (w + 1) * n * 4 + 2 * n * w * c, 4 * w * fft(n)),
+        "b_angle": (nt * nr * c + nt * nr * c, nr * fft(nt)),
+        "b_polT": (nt * nr * c + 2 * half * 4, 0.0),
+        "b_s1cols": (2 * half * c + 2 * half * 4 + 2 * n * w * c, 2 * w * fft(n)),
         "b_s1rows": (2 * n * w * c + 4 * n * n * 4, n * fft(n)),
     }
     return m
@@ -525,6 +528,13 @@ def main():
                 "peak_source": peak_src, "alg_bytes_per_launch": byts, "avg_launch_ms": round(avg_ms, 5),
                 "fp32_tflops": round(flops / (avg_ms * 1e-3) / 1e12, 2)}
 
+    # the whole step against the same roofline: every kernel's compulsory bytes over the step time
+    step_roof = None
+    if args.mode == "fwdbwd":
+        step_bytes = sum(model[k][0] for k in model if k in kernels) * B
+        step_roof = {"alg_bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (ms_step * 1e-3) / 1e9, 1),
+                     "peak_gbs": peaks["hbm_gbs"], "frac": round(step_bytes / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+
     # ---- end to end with host buffers ----
     e2e = None
     if rank == 0:
@@ -630,7 +640,8 @@ def main():
                 "config": {"workload": args.workload, "n": n, "n_theta": nt, "n_r": nr, "pairs_per_gpu": B,
                            "pad": "zero to 1.5N (same lags as 2N)", "l2": "flushed (256 MB write) between timed steps",
                            "schedules": search.tuning(0)},
-                "roofline": roof, "kernel_shares": shares, "ms_per_step_direct_launch": ms_traced,
+                "roofline": roof, "step_roofline": step_roof, "kernel_shares": shares,
+                "ms_per_step_direct_launch": ms_traced,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, **extra}
         print(json.dumps(line), flush=True)
