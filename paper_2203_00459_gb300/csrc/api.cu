@@ -100,7 +100,7 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
         t.gfr = (float*)take(b * n * n * sizeof(float));
         t.bdc = (float2*)take(b * p.nt * sizeof(float2));
         t.gpol = (float2*)take(b * p.nt * p.nr * sizeof(float2));
-        t.gmt = (float*)take(2 * b * (Wn + 1) * n * sizeof(float));
+        t.gmt = (float2*)take(b * (Wn + 1) * n * sizeof(float2));
         t.gs1 = (float2*)take(2 * b * n * Wn * sizeof(float2));
     }
     if (w) *w = t;

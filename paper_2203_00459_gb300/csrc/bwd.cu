@@ -34,7 +34,7 @@ namespace fmbym {
 // sum p q = <p, q>, mean(dz) = 0, and mean(dz z) = (delta (dtx S_zx + dty S_zy) - <p, q> S_z) /
 // (n T S) with S = sum e, S_z = sum e z, S_zx = sum e z s_x, S_zy = sum e z s_y, the sums the
 // forward's soft-argmax keeps (xm).  r receives (mean dz, mean dz z, mean, std, max, 1/(std T),
-// S, <p, q>).
+// S, <p, q>, 1/S, 1/T, 1/std).
 __device__ __forceinline__ void xy_adjoint_scalars(const DevPlan& p, const float* __restrict__ m, float tx,
                                                    float ty, float dtx, float dty, int n, float* r) {
     const float pq = dtx * tx + dty * ty;
@@ -46,18 +46,21 @@ __device__ __forceinline__ void xy_adjoint_scalars(const DevPlan& p, const float
     r[5] = m[3];
     r[6] = m[4];
     r[7] = pq;
+    r[8] = 1.f / m[4];
+    r[9] = 1.f / p.temp_xy;
+    r[10] = m[1] > 0.f ? 1.f / m[1] : 0.f;
 }
 
 // d c_xy at lag (i, j) from the scores and the per-pair scalars of xy_adjoint_scalars.
 __device__ __forceinline__ float dcxy(const DevPlan& p, const float* r, float cv, int i, int j, int n, float dtx,
                                       float dty) {
-    const float pp = expf((cv - r[4]) * r[5]) / r[6];
+    const float pp = expf((cv - r[4]) * r[5]) * r[8];
     const float qq = p.delta_xy * (dtx * (float)(j - n / 2) + dty * (float)(i - n / 2));
-    const float dz = pp * (qq - r[7]) / p.temp_xy;
+    const float dz = pp * (qq - r[7]) * r[9];
     if (p.score_norm == 1) return dz;
     if (!(r[3] > 0.f)) return 0.f;
-    const float z = (cv - r[2]) / r[3];
-    return (dz - r[0] - z * r[1]) / r[3];
+    const float z = (cv - r[2]) * r[10];
+    return (dz - r[0] - z * r[1]) * r[10];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long*
                                                      const float* __restrict__ dpose, float2* __restrict__ b1, int B) {
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
-    __shared__ float r[8];
+    __shared__ float r[11];
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
     const int k = threadIdx.x / T, jt = threadIdx.x % T, i = i0 + 2 * k;
     const long long pr = tab[3 * q + 2];
@@ -455,12 +458,11 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_b_angle(DevPlan p, cons
 // each heavy row a warp (lane-strided taps, fixed-order warp sum).  The f and g gradients of a
 // sample sit side by side, so one gathered sector serves both scans.
 __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float2* __restrict__ gpol,
-                                                     float* __restrict__ gmt, int B, int light_blocks) {
+                                                     float2* __restrict__ gmt, int B, int light_blocks) {
     const int n = p.n, E = (n / 2 + 1) * n;
     const int q = blockIdx.y;
     const float2* da = gpol + (size_t)q * p.nt * p.nr;   // (d A_f, d A_g) of each sample
-    float* of = gmt + (size_t)q * E;
-    float* og = gmt + (size_t)(B + q) * E;
+    float2* o = gmt + (size_t)q * E;   // (d a_f, d a_g) pairs
     if ((int)blockIdx.x < light_blocks) {
         const int e = blockIdx.x * kThreads + threadIdx.x;
         if (e >= E) return;
@@ -474,8 +476,7 @@ __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float2* __
             af += w * v.x;
             ag += w * v.y;
         }
-        of[e] = af;
-        og[e] = ag;
+        o[e] = make_float2(af, ag);
         return;
     }
     const int hw = ((int)blockIdx.x - light_blocks) * (kThreads / 32) + (threadIdx.x >> 5);
@@ -492,10 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float2* __
     }
     af = warp_sum(af);
     ag = warp_sum(ag);
-    if (lane == 0) {
-        of[e] = af;
-        og[e] = ag;
-    }
+    if (lane == 0) o[e] = make_float2(af, ag);
 }
 
 // |z| adjoint with the band-pass, then the column part of the half-plane DFT adjoint:
@@ -507,22 +505,22 @@ __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float2* __
 // from global memory and the last pass stores straight to it.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_b_s1cols(DevPlan p, const float2* __restrict__ phs,
-                                                       const float* __restrict__ gmt, float2* __restrict__ gs1,
+                                                       const float2* __restrict__ gmt, float2* __restrict__ gs1,
                                                        int B) {
     constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C, W = N / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
     const int c = threadIdx.x % C, j = threadIdx.x / C, u = u0 + c;
-    const float* dm = gmt + (size_t)(s * B + q) * (W + 1) * N;
+    const float* dm = reinterpret_cast<const float*>(gmt + (size_t)q * (W + 1) * N) + s;   // stride 2
     const float2* ph = phs + (size_t)(s * B + q) * (W + 1) * N;
     first_pass_global<N, +1>(sm + c, ES, j, [&](int v) {
-        if (u != 0) return c_scale(__ldg(ph + (size_t)u * N + v), 0.5f * __ldg(dm + (size_t)u * N + v));
+        if (u != 0) return c_scale(__ldg(ph + (size_t)u * N + v), 0.5f * __ldg(dm + 2 * ((size_t)u * N + v)));
         // packed DC (u = 0) and Nyquist (u = N/2) columns, each made Hermitian
         const int vm = (N - v) & (N - 1);
-        const float2 a = c_scale(__ldg(ph + v), __ldg(dm + v));
-        const float2 am = c_scale(__ldg(ph + vm), __ldg(dm + vm));
-        const float2 b = c_scale(__ldg(ph + (size_t)W * N + v), __ldg(dm + (size_t)W * N + v));
-        const float2 bm = c_scale(__ldg(ph + (size_t)W * N + vm), __ldg(dm + (size_t)W * N + vm));
+        const float2 a = c_scale(__ldg(ph + v), __ldg(dm + 2 * v));
+        const float2 am = c_scale(__ldg(ph + vm), __ldg(dm + 2 * vm));
+        const float2 b = c_scale(__ldg(ph + (size_t)W * N + v), __ldg(dm + 2 * ((size_t)W * N + v)));
+        const float2 bm = c_scale(__ldg(ph + (size_t)W * N + vm), __ldg(dm + 2 * ((size_t)W * N + vm)));
         const float2 sa = make_float2(0.5f * (a.x + am.x), 0.5f * (a.y - am.y));
         const float2 sb = make_float2(0.5f * (b.x + bm.x), 0.5f * (b.y - bm.y));
         return make_float2(sa.x - sb.y, sa.y + sb.x);

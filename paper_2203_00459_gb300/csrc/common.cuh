@@ -88,7 +88,7 @@ struct Tracer {
 // Workspace of one size group of B pairs (pointers into the handle's workspace).
 struct Ws {
     float2* s1;   // [2][B][N][N/2]   stage-1 row spectra (packed real FFT rows)
-    float* mt;    // [2][B][N/2+1][N] stage-1 band-passed magnitudes, u-major
+    float* mt;    // [B][N/2+1][N][2] stage-1 band-passed magnitudes of (f, g), u-major, interleaved
     float2* sp;   // [B][chunks][n_theta] per-chunk sums of conj(A_f) A_g along angle
     float* th;    // [B][8] theta, cos hi/lo, sin hi/lo
     float2* s2;   // [2][B][N][P/2]   stage-2 row spectra of the rotated source and the target
@@ -113,7 +113,7 @@ struct Ws {
     float* gfr;   // [B][N][N]        d rotated source
     float2* bdc;  // [B][n_theta]     FFT of d c_theta along angle
     float2* gpol; // [B][n_theta][n_r] d polar arrays of (f, g)
-    float* gmt;   // [2][B][N/2+1][N] d magnitudes
+    float2* gmt;  // [B][N/2+1][N]    d magnitudes of (f, g)
     float2* gs1;  // [2][B][N][N/2]   inverse column pass of the stage-1 adjoint
     Tracer* tr;   // launch tracer of the handle
 };

@@ -41,6 +41,39 @@ __device__ __forceinline__ float block_reduce(float v, float* red) {
 
 // |F| at integer frequency (vi, ui) of the N-periodic spectrum, read from the u-major half plane
 // m[u][v] (u <= N/2) through |F(-v,-u)| = |F(v,u)|.
+// Block-wide sums of K values at once (two barriers in all); red holds 32 K floats.  Every thread
+// receives the sums in v.  Fixed order, so the result does not depend on timing.
+template <int K>
+__device__ __forceinline__ void block_sum_n(float (&v)[K], float* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[wid * K + k] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float t = 0.f;
+        for (int w = 0; w < nw; ++w) t += red[w * K + k];
+        v[k] = t;
+    }
+}
+
+// The (f, g) magnitude pair at (vi, ui) of the N-periodic spectrum from the u-major half plane of
+// interleaved pairs (the Hermitian mirror for ui > N/2).
+__device__ __forceinline__ float2 mag2_at(const float2* __restrict__ m, int n, int vi, int ui) {
+    vi &= n - 1;
+    ui &= n - 1;
+    if (ui > (n >> 1)) {
+        vi = (n - vi) & (n - 1);
+        ui = n - ui;
+    }
+    return __ldg(&m[ui * n + vi]);
+}
+
 __device__ __forceinline__ float mag_at(const float* __restrict__ m, int n, int vi, int ui) {
     vi &= n - 1;
     ui &= n - 1;

@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(kThreads) k_s1_rows(DevPlan p, const long long
 
 // Column FFTs of the packed row spectra, band-pass and magnitude.  Column 0 holds the DC and
 // Nyquist columns as one complex sequence; they are separated after the transform.  Output is
-// the u-major half plane m[u][v], u in [0, N/2], v in [0, N).  With ph non-NULL the band-limited
+// the u-major half plane m[u][v], u in [0, N/2], v in [0, N), with the magnitudes of f and g of a
+// pair interleaved (float2 per element) for the Cart2Pol gather.  With ph non-NULL the band-limited
 // unit phasors F/|F| (0 outside the band or where F = 0) are kept for the adjoint, same layout.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* __restrict__ s1,
@@ -69,13 +70,13 @@ __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* _
     cp_async_wait_all();
     __syncthreads();
     fft<N, -1>(sm + threadIdx.x / T, ES, threadIdx.x % T, true, p.tw_n);
-    float* out = mt + (size_t)(s * B + q) * (W + 1) * N;
+    float* out = mt + (size_t)q * (W + 1) * N * 2 + s;   // (f, g) pairs: this scan's half of each
     float2* pho = ph ? ph + (size_t)(s * B + q) * (W + 1) * N : nullptr;
     // |z| within the band (else 0), and the phasor z / |z| there
     auto mag = [&](float2 z, int m2, size_t at) {
         const bool in_band = m2 >= p.m_lo && m2 <= p.m_hi;
         const float a = in_band ? sqrtf(fmaf(z.x, z.x, z.y * z.y)) : 0.f;
-        out[at] = a;
+        out[2 * at] = a;
         if (pho) pho[at] = a > 0.f ? make_float2(z.x / a, z.y / a) : make_float2(0.f, 0.f);
     };
     for (int idx = threadIdx.x; idx < C * N; idx += kThreads) {
@@ -108,8 +109,7 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_angle(DevPlan p, const 
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, ch = blockIdx.x, n = p.n, W = n / 2;
     const int rr = threadIdx.x % RC, j = threadIdx.x / RC, r = ch * RC + rr;
-    const float* mf = mt + (size_t)q * (W + 1) * n;
-    const float* mg = mt + (size_t)(B + q) * (W + 1) * n;
+    const float2* m2 = reinterpret_cast<const float2*>(mt) + (size_t)q * (W + 1) * n;   // (f, g) pairs
     const bool live = r < p.nr;
     first_pass_global<NT>(sm + rr, ES, j, [&](int a) {
         float2 z = make_float2(0.f, 0.f);
@@ -117,10 +117,10 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_angle(DevPlan p, const 
             const PolarSample ps = p.polar[a * p.nr + r];
             const float w00 = (1.f - ps.fy) * (1.f - ps.fx), w01 = (1.f - ps.fy) * ps.fx;
             const float w10 = ps.fy * (1.f - ps.fx), w11 = ps.fy * ps.fx;
-            z.x = w00 * mag_at(mf, n, ps.y0, ps.x0) + w01 * mag_at(mf, n, ps.y0, ps.x0 + 1) +
-                  w10 * mag_at(mf, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mf, n, ps.y0 + 1, ps.x0 + 1);
-            z.y = w00 * mag_at(mg, n, ps.y0, ps.x0) + w01 * mag_at(mg, n, ps.y0, ps.x0 + 1) +
-                  w10 * mag_at(mg, n, ps.y0 + 1, ps.x0) + w11 * mag_at(mg, n, ps.y0 + 1, ps.x0 + 1);
+            const float2 v00 = mag2_at(m2, n, ps.y0, ps.x0), v01 = mag2_at(m2, n, ps.y0, ps.x0 + 1);
+            const float2 v10 = mag2_at(m2, n, ps.y0 + 1, ps.x0), v11 = mag2_at(m2, n, ps.y0 + 1, ps.x0 + 1);
+            z.x = w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x;
+            z.y = w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y;
         }
         return z;
     });
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
                                                   const float* __restrict__ st, int nblk, float* __restrict__ sx,
                                                   unsigned* __restrict__ cnt, float* __restrict__ pose,
                                                   float* __restrict__ xm) {
-    __shared__ float red[32];
+    __shared__ float red[32 * 6];
     __shared__ float stat[4];
     __shared__ bool last;
     const int q = blockIdx.y;
@@ -446,20 +446,12 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
         lzx += ez * sx0 + (e1 * z1 + 2.f * e2 * z2 + 3.f * e3 * z3);
         lzy += ez * sy;
     }
-    const float se = block_reduce<false>(le, red);
-    const float sxx = block_reduce<false>(lx, red);
-    const float syy = block_reduce<false>(ly, red);
-    const float sz = block_reduce<false>(lz, red);
-    const float szx = block_reduce<false>(lzx, red);
-    const float szy = block_reduce<false>(lzy, red);
+    float sums[6] = {le, lx, ly, lz, lzx, lzy};
+    block_sum_n<6>(sums, red);
     if (threadIdx.x == 0) {
         float* o = sx + ((size_t)q * kSplitXY + blockIdx.x) * 8;
-        o[0] = se;
-        o[1] = sxx;
-        o[2] = syy;
-        o[3] = sz;
-        o[4] = szx;
-        o[5] = szy;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k] = sums[k];
         __threadfence();
         last = atomicAdd(&cnt[q], 1u) == kSplitXY - 1;
     }
