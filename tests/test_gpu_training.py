@@ -30,7 +30,7 @@ def test_trained_mask_lowers_translation_error():
     plain = ms.poses(Fe_t, Ge_t, masked=False).cpu().numpy()
     rng = np.random.default_rng(0)
     nb = F.shape[0] // 64
-    for step in range(240):
+    for step in range(400):   # 12.5 epochs of the 2048 pairs
         if step % nb == 0:
             perm = torch.from_numpy(rng.permutation(F.shape[0])).cuda()
         idx = perm[(step % nb) * 64:(step % nb + 1) * 64]
