@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long*
                                                      const float* __restrict__ cxy, const float* __restrict__ xm,
                                                      const float* __restrict__ fwd_pose,
                                                      const float* __restrict__ dpose, float2* __restrict__ b1, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     __shared__ float r[11];
@@ -123,6 +124,7 @@ template <int N, int P, int C>
 __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_cols(DevPlan p, const float2* __restrict__ b1,
                                                                        const float2* __restrict__ s2hat,
                                                                        float2* __restrict__ b2, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     using PL = FftPlan<P>;
     constexpr int T = PL::T, TPB = C * T, ES = C, W = P / 2, TILE = spad(P) * ES;
     constexpr int RL = last_radix<P>(), NBL = P / RL, BPL = (NBL + T - 1) / T, PER = P * C / TPB;
@@ -241,6 +243,7 @@ template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* __restrict__ tab,
                                                     const float2* __restrict__ b2, float* __restrict__ gfr,
                                                     float* __restrict__ dg, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, i0 = blockIdx.x * FPC * 2;
@@ -279,6 +282,7 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
                                                     const float* __restrict__ gfr, const float* __restrict__ dpose,
                                                     float* __restrict__ df, float* __restrict__ gpart,
                                                     unsigned* __restrict__ cnt, float* __restrict__ bsc) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     __shared__ float red[32];
     __shared__ bool last;
     constexpr int NB = N * N / (kThreads * PX);
@@ -362,6 +366,7 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
 template <int NT>
 __global__ void __launch_bounds__(256) k_b_theta(DevPlan p, const float* __restrict__ ct,
                                                  const float* __restrict__ bsc, float2* __restrict__ bdc) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<NT>::T;
     __shared__ float2 z[spad(NT)];
     __shared__ float c[NT];
@@ -427,6 +432,7 @@ template <int NT, int RC>
 __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_b_angle(DevPlan p, const float2* __restrict__ ahat,
                                                                          const float2* __restrict__ bdc,
                                                                          float2* __restrict__ gpol, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<NT>::T, ES = RC;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, ch = blockIdx.x;
@@ -459,6 +465,7 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_b_angle(DevPlan p, cons
 // sample sit side by side, so one gathered sector serves both scans.
 __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float2* __restrict__ gpol,
                                                      float2* __restrict__ gmt, int B, int light_blocks) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     const int n = p.n, E = (n / 2 + 1) * n;
     const int q = blockIdx.y;
     const float2* da = gpol + (size_t)q * p.nt * p.nr;   // (d A_f, d A_g) of each sample
@@ -507,6 +514,7 @@ template <int N>
 __global__ void __launch_bounds__(kThreads) k_b_s1cols(DevPlan p, const float2* __restrict__ phs,
                                                        const float2* __restrict__ gmt, float2* __restrict__ gs1,
                                                        int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C, W = N / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
@@ -536,6 +544,7 @@ template <int N>
 __global__ void __launch_bounds__(kThreads) k_b_s1rows(DevPlan p, const long long* __restrict__ tab,
                                                        const float2* __restrict__ gs1, float* __restrict__ df,
                                                        float* __restrict__ dg, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<N>::T, FPC = kThreads / T, SL = spad(N), W = N / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
@@ -566,6 +575,7 @@ __global__ void __launch_bounds__(kThreads) k_b_s1rows(DevPlan p, const long lon
 __global__ void __launch_bounds__(256) k_pose_loss(int n_pairs, const float* __restrict__ pose,
                                                    const float* __restrict__ gt, int kind, float* __restrict__ loss,
                                                    float* __restrict__ dpose) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     __shared__ float red[32];
     const float inv = 1.f / (float)n_pairs;
     float acc = 0.f;
@@ -589,7 +599,7 @@ __global__ void __launch_bounds__(256) k_pose_loss(int n_pairs, const float* __r
 cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, int kind, float* loss, float* dpose,
                              Tracer* tr, cudaStream_t st) {
     tr->before(K_LOSS, st);
-    k_pose_loss<<<1, 256, 0, st>>>(n_pairs, pose, gt, kind, loss, dpose);
+    launch_pdl(k_pose_loss, 1, 256, 0, st, n_pairs, pose, gt, kind, loss, dpose);
     tr->close(st);
     return cudaGetLastError();
 }
@@ -608,20 +618,20 @@ template <int NT, int RC> constexpr size_t b_smem_angle() { return (size_t)spad(
 template <int NT>
 static void launch_stage1_adjoint(const DevPlan& p, const Ws& w, int B, cudaStream_t st) {
     w.tr->before(K_B_THETA, st);
-    k_b_theta<NT><<<B, 256, 0, st>>>(p, w.ct, w.bsc, w.bdc);
+    launch_pdl(k_b_theta<NT>, B, 256, 0, st, p, w.ct, w.bsc, w.bdc);
     w.tr->before(K_B_ANGLE, st);
     if (p.angle_rc == 8)
-        k_b_angle<NT, 8><<<dim3(angle_chunks(p), B), FftPlan<NT>::T * 8, b_smem_angle<NT, 8>(), st>>>(p, w.ahat, w.bdc,
+        launch_pdl(k_b_angle<NT, 8>, dim3(angle_chunks(p), B), FftPlan<NT>::T * 8, b_smem_angle<NT, 8>(), st, p, w.ahat, w.bdc,
                                                                                                      w.gpol, B);
     else
-        k_b_angle<NT, 16><<<dim3(angle_chunks(p), B), FftPlan<NT>::T * 16, b_smem_angle<NT, 16>(), st>>>(
+        launch_pdl(k_b_angle<NT, 16>, dim3(angle_chunks(p), B), FftPlan<NT>::T * 16, b_smem_angle<NT, 16>(), st, 
             p, w.ahat, w.bdc, w.gpol, B);
 }
 
 template <int N, int PX>
 static void launch_b_rot(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                          const float* dpose, float* df, cudaStream_t st) {
-    k_b_rot<N, PX><<<dim3(N * N / (kThreads * PX), B), kThreads, 0, st>>>(p, tab, f, w.th, w.gfr, dpose, df, w.gpart,
+    launch_pdl(k_b_rot<N, PX>, dim3(N * N / (kThreads * PX), B), kThreads, 0, st, p, tab, f, w.th, w.gfr, dpose, df, w.gpart,
                                                                           w.cnt, w.bsc);
 }
 
@@ -636,24 +646,24 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     }
     constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T, TB2 = tpb_for(P);
     w.tr->before(K_B_ROWS, st);
-    k_b_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st>>>(p, tab, w.cxy, w.xm, fwd_pose,
+    launch_pdl(k_b_rows<N, P>, dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st, p, tab, w.cxy, w.xm, fwd_pose,
                                                                                    dpose, w.b1, B);
     w.tr->before(K_B_COLS, st);
     constexpr int C0 = TB2 / T2;   // the default tile; the 3 * 2^k lengths also have half and double
     if constexpr (P % 3 == 0) {
         if (p.col_tile == C0 / 2)
-            k_b_cols<N, P, C0 / 2><<<dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, b_smem_cols<P, C0 / 2>(), st>>>(
+            launch_pdl(k_b_cols<N, P, C0 / 2>, dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, b_smem_cols<P, C0 / 2>(), st, 
                 p, w.b1, w.s2hat, w.b2, B);
         else if (p.col_tile == 2 * C0)
-            k_b_cols<N, P, 2 * C0><<<dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, b_smem_cols<P, 2 * C0>(), st>>>(
+            launch_pdl(k_b_cols<N, P, 2 * C0>, dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, b_smem_cols<P, 2 * C0>(), st, 
                 p, w.b1, w.s2hat, w.b2, B);
         else
-            k_b_cols<N, P, C0><<<dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st>>>(p, w.b1, w.s2hat, w.b2, B);
+            launch_pdl(k_b_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2, B);
     } else {
-        k_b_cols<N, P, C0><<<dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st>>>(p, w.b1, w.s2hat, w.b2, B);
+        launch_pdl(k_b_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2, B);
     }
     w.tr->before(K_B_C2R, st);
-    k_b_c2r<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st>>>(p, tab, w.b2, w.gfr, dg, B);
+    launch_pdl(k_b_c2r<N, P>, dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st, p, tab, w.b2, w.gfr, dg, B);
     w.tr->before(K_B_ROT, st);
     switch (p.rot_px) {
         case 1: launch_b_rot<N, 1>(p, w, B, tab, f, dpose, df, st); break;
@@ -667,12 +677,12 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     w.tr->before(K_B_POLT, st);
     const int E = (N / 2 + 1) * N, lb = (E + kThreads - 1) / kThreads;
     const int hb = (p.n_heavy + kThreads / 32 - 1) / (kThreads / 32);
-    k_b_polT<<<dim3(lb + hb, B), kThreads, 0, st>>>(p, w.gpol, w.gmt, B, lb);
+    launch_pdl(k_b_polT, dim3(lb + hb, B), kThreads, 0, st, p, w.gpol, w.gmt, B, lb);
     w.tr->before(K_B_S1COLS, st);
-    k_b_s1cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st>>>(p, w.phs, w.gmt,
+    launch_pdl(k_b_s1cols<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st, p, w.phs, w.gmt,
                                                                                                  w.gs1, B);
     w.tr->before(K_B_S1ROWS, st);
-    k_b_s1rows<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_rows<N>(), st>>>(p, tab, w.gs1, df, dg,
+    launch_pdl(k_b_s1rows<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_rows<N>(), st, p, tab, w.gs1, df, dg,
                                                                                                B);
     w.tr->close(st);
     return cudaGetLastError();

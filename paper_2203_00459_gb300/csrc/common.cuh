@@ -10,6 +10,30 @@
 namespace fmbym {
 
 constexpr int kThreads = 256;   // threads of the FFT kernels
+// Device side of a programmatic dependent launch: waits until the kernel launched before this one
+// on the stream has completed and its writes are visible (returns at once without such a
+// predecessor).  Every kernel of the search calls it before its first global memory access.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// Launches a kernel that may be scheduled while its predecessor on the stream drains (programmatic
+// stream serialization).  Because the kernel's grid_dep_wait() orders all of its reads and writes
+// after the predecessor's completion, only the launch and the scheduling of its blocks overlap.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Launch schedules with more than one compiled variant; each size's DevPlan names the variant its
 // launches use (the defaults below, or the autotuner's measured choice).
 constexpr int kAngleRadiiMin = 8;   // radii per CTA of the angle correlation and its adjoint: 8 or 16

@@ -14,6 +14,7 @@ namespace fmbym {
 
 // The heading of every pair for this candidate: theta and the float splits of its cosine and sine.
 __global__ void k_ex_theta(float* __restrict__ th, int B, float theta, float ch, float cl, float sh, float sl) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= B) return;
     float* t = th + 8 * q;
@@ -29,6 +30,7 @@ __global__ void k_ex_theta(float* __restrict__ th, int B, float theta, float ch,
 __global__ void k_ex_update(const long long* __restrict__ tab, const float* __restrict__ st, int nblk,
                             const float* __restrict__ cand, int B, int k, float theta, float4* __restrict__ best,
                             float* __restrict__ peaks, int n_angles) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= B) return;
     float m = -FLT_MAX;
@@ -40,6 +42,7 @@ __global__ void k_ex_update(const long long* __restrict__ tab, const float* __re
 
 __global__ void k_ex_write(const long long* __restrict__ tab, const float4* __restrict__ best, int B,
                            float* __restrict__ pose) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= B) return;
     const long long pr = tab[3 * q + 2];
@@ -59,12 +62,12 @@ cudaError_t launch_exhaustive(const DevPlan& p, const Ws& w, int B, const long l
         const float theta = angles[k];
         const double cd = std::cos((double)theta), sd = std::sin((double)theta);
         const float ch = (float)cd, sh = (float)sd;
-        k_ex_theta<<<nb, 256, 0, st>>>(w.th, B, theta, ch, (float)(cd - (double)ch), sh, (float)(sd - (double)sh));
+        launch_pdl(k_ex_theta, nb, 256, 0, st, w.th, B, theta, ch, (float)(cd - (double)ch), sh, (float)(sd - (double)sh));
         cudaError_t e = launch_forward_stage2(p, w, B, tab, f, g, cand, nullptr, st);
         if (e != cudaSuccess) return e;
-        k_ex_update<<<nb, 256, 0, st>>>(tab, w.st, nblk, cand, B, k, theta, best, peaks, n_angles);
+        launch_pdl(k_ex_update, nb, 256, 0, st, tab, w.st, nblk, cand, B, k, theta, best, peaks, n_angles);
     }
-    k_ex_write<<<nb, 256, 0, st>>>(tab, best, B, pose);
+    launch_pdl(k_ex_write, nb, 256, 0, st, tab, best, B, pose);
     return cudaGetLastError();
 }
 

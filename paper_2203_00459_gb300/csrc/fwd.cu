@@ -29,6 +29,7 @@ template <int N>
 __global__ void __launch_bounds__(kThreads) k_s1_rows(DevPlan p, const long long* __restrict__ tab,
                                                       const float* __restrict__ f, const float* __restrict__ g,
                                                       float2* __restrict__ s1, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<N>::T, FPC = kThreads / T, SL = spad(N), W = N / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(kThreads) k_s1_rows(DevPlan p, const long long
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* __restrict__ s1,
                                                       float* __restrict__ mt, float2* __restrict__ ph, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C + 1, W = N / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
@@ -104,6 +106,7 @@ template <int NT, int RC>
 __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_angle(DevPlan p, const float* __restrict__ mt,
                                                                        float2* __restrict__ sp,
                                                                        float2* __restrict__ ahat, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<NT>::T, ES = RC;
     static_assert(RC == 8 || RC == 16, "the shuffle sum runs over aligned groups of RC lanes");
     extern __shared__ float2 sm[];
@@ -152,6 +155,7 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
                                                const long long* __restrict__ tab, float* __restrict__ th,
                                                float* __restrict__ pose, float* __restrict__ c_theta,
                                                float* __restrict__ ct) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<NT>::T;
     __shared__ float2 z[spad(NT)];
     __shared__ float c[NT];
@@ -220,6 +224,7 @@ template <int N, int P>
 __global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
                                                         const float* __restrict__ f, const float* __restrict__ g,
                                                         const float* __restrict__ th, float2* __restrict__ s2, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
@@ -266,6 +271,7 @@ __global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long lo
 template <int N, int P, int C>
 __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
                                                       float2* __restrict__ s3, float2* __restrict__ s2hat, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     using PL = FftPlan<P>;
     constexpr int T = PL::T, TPB = C * T, ES = C, W = P / 2, TILE = spad(P) * ES;
     constexpr int RL = last_radix<P>(), NBL = P / RL;
@@ -352,6 +358,7 @@ template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long* __restrict__ tab,
                                                      const float2* __restrict__ s3, float* __restrict__ cxy_ws,
                                                      float* __restrict__ cxy_out, float* __restrict__ st, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
     __shared__ float red[32];
@@ -408,6 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
                                                   const float* __restrict__ st, int nblk, float* __restrict__ sx,
                                                   unsigned* __restrict__ cnt, float* __restrict__ pose,
                                                   float* __restrict__ xm) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     __shared__ float red[32 * 6];
     __shared__ float stat[4];
     __shared__ bool last;
@@ -505,11 +513,11 @@ static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, con
     const int nch = angle_chunks(p);
     w.tr->before(K_ANGLE, st);
     if (p.angle_rc == 8)
-        k_angle<NT, 8><<<dim3(nch, B), FftPlan<NT>::T * 8, smem_angle<NT, 8>(), st>>>(p, w.mt, w.sp, w.ahat, B);
+        launch_pdl(k_angle<NT, 8>, dim3(nch, B), FftPlan<NT>::T * 8, smem_angle<NT, 8>(), st, p, w.mt, w.sp, w.ahat, B);
     else
-        k_angle<NT, 16><<<dim3(nch, B), FftPlan<NT>::T * 16, smem_angle<NT, 16>(), st>>>(p, w.mt, w.sp, w.ahat, B);
+        launch_pdl(k_angle<NT, 16>, dim3(nch, B), FftPlan<NT>::T * 16, smem_angle<NT, 16>(), st, p, w.mt, w.sp, w.ahat, B);
     w.tr->before(K_THETA, st);
-    k_theta<NT><<<B, 256, 0, st>>>(p, w.sp, nch, tab, w.th, pose, c_theta, w.ct);
+    launch_pdl(k_theta<NT>, B, 256, 0, st, p, w.sp, nch, tab, w.th, pose, c_theta, w.ct);
     return cudaGetLastError();
 }
 
@@ -518,9 +526,9 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
                              const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
     constexpr int T1 = FftPlan<N>::T;
     w.tr->before(K_S1_ROWS, st);
-    k_s1_rows<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st>>>(p, tab, f, g, w.s1, B);
+    launch_pdl(k_s1_rows<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st, p, tab, f, g, w.s1, B);
     w.tr->before(K_S1_COLS, st);
-    k_s1_cols<N><<<dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_cols1<N>(), st>>>(p, w.s1, w.mt, w.phs, B);
+    launch_pdl(k_s1_cols<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_cols1<N>(), st, p, w.s1, w.mt, w.phs, B);
     cudaError_t e;
     if (p.nt == 128) e = launch_stage1_angle<128>(p, w, B, tab, pose, c_theta, st);
     else if (p.nt == 256) e = launch_stage1_angle<256>(p, w, B, tab, pose, c_theta, st);
@@ -536,26 +544,26 @@ static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const lon
                                  const float* g, float* pose, float* c_xy, cudaStream_t st) {
     constexpr int T2 = FftPlan<P>::T, TB2 = tpb_for(P);
     w.tr->before(K_S2_ROWS, st);
-    k_s2_rows<N, P><<<dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st>>>(p, tab, f, g, w.th, w.s2, B);
+    launch_pdl(k_s2_rows<N, P>, dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st, p, tab, f, g, w.th, w.s2, B);
     w.tr->before(K_S2_COLS, st);
     constexpr int C0 = TB2 / T2;   // the default tile; the 3 * 2^k lengths also have half and double
     if constexpr (P % 3 == 0) {
         if (p.col_tile == C0 / 2)
-            k_s2_cols<N, P, C0 / 2><<<dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, smem_cols2<P, C0 / 2>(), st>>>(
+            launch_pdl(k_s2_cols<N, P, C0 / 2>, dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, smem_cols2<P, C0 / 2>(), st, 
                 p, w.s2, w.s3, w.s2hat, B);
         else if (p.col_tile == 2 * C0)
-            k_s2_cols<N, P, 2 * C0><<<dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, smem_cols2<P, 2 * C0>(), st>>>(
+            launch_pdl(k_s2_cols<N, P, 2 * C0>, dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, smem_cols2<P, 2 * C0>(), st, 
                 p, w.s2, w.s3, w.s2hat, B);
         else
-            k_s2_cols<N, P, C0><<<dim3((P / 2) / C0, B), TB2, smem_cols2<P, C0>(), st>>>(p, w.s2, w.s3, w.s2hat, B);
+            launch_pdl(k_s2_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, smem_cols2<P, C0>(), st, p, w.s2, w.s3, w.s2hat, B);
     } else {
-        k_s2_cols<N, P, C0><<<dim3((P / 2) / C0, B), TB2, smem_cols2<P, C0>(), st>>>(p, w.s2, w.s3, w.s2hat, B);
+        launch_pdl(k_s2_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, smem_cols2<P, C0>(), st, p, w.s2, w.s3, w.s2hat, B);
     }
     const int nblk = (N / 2) / (TB2 / T2);
     w.tr->before(K_S2_C2R, st);
-    k_s2_c2r<N, P><<<dim3(nblk, B), TB2, smem_rows<P>(), st>>>(p, tab, w.s3, w.cxy, c_xy, w.st, B);
+    launch_pdl(k_s2_c2r<N, P>, dim3(nblk, B), TB2, smem_rows<P>(), st, p, tab, w.s3, w.cxy, c_xy, w.st, B);
     w.tr->before(K_SXY, st);
-    k_sxy<N><<<dim3(kSplitXY, B), kThreads, 0, st>>>(p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose, w.xm);
+    launch_pdl(k_sxy<N>, dim3(kSplitXY, B), kThreads, 0, st, p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose, w.xm);
     w.tr->close(st);
     return cudaGetLastError();
 }
