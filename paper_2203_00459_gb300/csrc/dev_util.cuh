@@ -132,6 +132,48 @@ __device__ __forceinline__ float rotated_sample(const float* __restrict__ src, i
     return v;
 }
 
+// Exact fixed-point sampling coordinates of the Rotate step: with C = cos(theta) 2^40 and
+// S = sin(theta) 2^40 rounded to integers (from the double cosine and sine the splits carry), the
+// sample of output pixel (X, Y) sits at p = c + R(-theta)((X, Y) - c), i.e.
+//   px 2^40 = c 2^40 + C (X - c) + S (Y - c),   py 2^40 = c 2^40 - S (X - c) + C (Y - c),
+// integers below 2^50 for N <= 512, so every pixel's coordinates are exact to 2^-40 px and cost
+// one 64-bit multiply-add each.
+struct RotFixed {
+    long long C, S, px0, py0;   // px0, py0: the coordinates of (X, Y) = (0, 0)
+};
+
+__device__ __forceinline__ RotFixed rot_fixed(float ch, float cl, float sh, float sl, int n) {
+    const double one = 1099511627776.0;   // 2^40
+    RotFixed r;
+    r.C = __double2ll_rn(((double)ch + (double)cl) * one);
+    r.S = __double2ll_rn(((double)sh + (double)sl) * one);
+    const long long c = (long long)(n / 2) << 40, h = n / 2;
+    r.px0 = c - r.C * h - r.S * h;
+    r.py0 = c + r.S * h - r.C * h;
+    return r;
+}
+
+// Bilinear f at fixed-point (px, py), zero outside the scan (Alg. 1 Rotate).
+__device__ __forceinline__ float rotated_sample_fixed(const float* __restrict__ src, int n, long long px,
+                                                      long long py) {
+    const int x0 = (int)(px >> 40), y0 = (int)(py >> 40);
+    const float fx = (float)(int)((px >> 16) & 0xFFFFFF) * (1.f / 16777216.f);
+    const float fy = (float)(int)((py >> 16) & 0xFFFFFF) * (1.f / 16777216.f);
+    float v = 0.f;
+    const bool xin0 = (unsigned)x0 < (unsigned)n, xin1 = (unsigned)(x0 + 1) < (unsigned)n;
+    if ((unsigned)y0 < (unsigned)n) {
+        const float* r = src + (size_t)y0 * n;
+        if (xin0) v += (1.f - fy) * (1.f - fx) * __ldg(r + x0);
+        if (xin1) v += (1.f - fy) * fx * __ldg(r + x0 + 1);
+    }
+    if ((unsigned)(y0 + 1) < (unsigned)n) {
+        const float* r = src + (size_t)(y0 + 1) * n;
+        if (xin0) v += fy * (1.f - fx) * __ldg(r + x0);
+        if (xin1) v += fy * fx * __ldg(r + x0 + 1);
+    }
+    return v;
+}
+
 // Combines per-block (mean, M2, max, count) statistics of the translation scores into the mean,
 // population std and maximum over all `total` scores (equal block counts; Chan's update).  Run by
 // one full warp; every lane returns the results.

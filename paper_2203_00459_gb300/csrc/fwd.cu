@@ -233,11 +233,13 @@ __global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long lo
     const float* __restrict__ src = (s ? g : f) + tab[3 * q];
     if (s == 0) {
         const float* t = th + 8 * q;
-        const float ch = t[1], cl = t[2], sh = t[3], sl = t[4];
+        const RotFixed rf = rot_fixed(t[1], t[2], t[3], t[4], N);
+        // rows r and r + 1: (Y - c) steps add S to px and C to py
+        const long long pxr = rf.px0 + rf.S * r, pyr = rf.py0 + rf.C * r;
         first_pass_global<P>(sm + k * SL, 1, j, [&](int x) {
-            return x < N ? make_float2(rotated_sample(src, N, x, r, ch, cl, sh, sl),
-                                       rotated_sample(src, N, x, r + 1, ch, cl, sh, sl))
-                         : make_float2(0.f, 0.f);
+            if (x >= N) return make_float2(0.f, 0.f);
+            const long long px = pxr + rf.C * x, py = pyr - rf.S * x;
+            return make_float2(rotated_sample_fixed(src, N, px, py), rotated_sample_fixed(src, N, px + rf.S, py + rf.C));
         });
     } else {
         const float* rp = src + (size_t)r * N;
