@@ -84,54 +84,6 @@ __device__ __forceinline__ float mag_at(const float* __restrict__ m, int n, int 
     return __ldg(&m[ui * n + vi]);
 }
 
-// p = c + a d1 + b d2 with a = ah + al and b = bh + bl (float splits of double values) and small
-// integer d1, d2.  Error-free products and sums keep p to ~1e-7 px so that the rotation does not
-// add error beyond the rounding of theta itself.  Returns floor(p) and p - floor(p).
-__device__ __forceinline__ void rot_coord(float ah, float al, float d1, float bh, float bl, float d2, float c,
-                                          int& i0, float& fr) {
-    const float p1 = __fmul_rn(ah, d1), e1 = fmaf(ah, d1, -p1);
-    const float p2 = __fmul_rn(bh, d2), e2 = fmaf(bh, d2, -p2);
-    const float s = __fadd_rn(p1, p2), t = __fsub_rn(s, p1);
-    const float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, t)), __fsub_rn(p2, t));
-    const float h = __fadd_rn(c, s), t2 = __fsub_rn(h, c);
-    const float eh = __fadd_rn(__fsub_rn(c, __fsub_rn(h, t2)), __fsub_rn(s, t2));
-    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(es, eh)), fmaf(al, d1, __fmul_rn(bl, d2)));
-    float fl = floorf(h);
-    float f = __fadd_rn(__fsub_rn(h, fl), lo);
-    if (f < 0.f) {
-        f += 1.f;
-        fl -= 1.f;
-    } else if (f >= 1.f) {
-        f -= 1.f;
-        fl += 1.f;
-    }
-    i0 = (int)fl;
-    fr = f;
-}
-
-// f'(X, Y) = bilinear(f, c + R(-theta)([X, Y] - c)), zero outside the scan (Alg. 1 Rotate).
-__device__ __forceinline__ float rotated_sample(const float* __restrict__ src, int n, int X, int Y, float ch,
-                                                float cl, float sh, float sl) {
-    const float c = 0.5f * n, dx = (float)X - c, dy = (float)Y - c;
-    int x0, y0;
-    float fx, fy;
-    rot_coord(ch, cl, dx, sh, sl, dy, c, x0, fx);    // px = c + cos dx + sin dy
-    rot_coord(ch, cl, dy, -sh, -sl, dx, c, y0, fy);  // py = c - sin dx + cos dy
-    float v = 0.f;
-    const bool xin0 = (unsigned)x0 < (unsigned)n, xin1 = (unsigned)(x0 + 1) < (unsigned)n;
-    if ((unsigned)y0 < (unsigned)n) {
-        const float* r = src + (size_t)y0 * n;
-        if (xin0) v += (1.f - fy) * (1.f - fx) * __ldg(r + x0);
-        if (xin1) v += (1.f - fy) * fx * __ldg(r + x0 + 1);
-    }
-    if ((unsigned)(y0 + 1) < (unsigned)n) {
-        const float* r = src + (size_t)(y0 + 1) * n;
-        if (xin0) v += fy * (1.f - fx) * __ldg(r + x0);
-        if (xin1) v += fy * fx * __ldg(r + x0 + 1);
-    }
-    return v;
-}
-
 // Exact fixed-point sampling coordinates of the Rotate step: with C = cos(theta) 2^40 and
 // S = sin(theta) 2^40 rounded to integers (from the double cosine and sine the splits carry), the
 // sample of output pixel (X, Y) sits at p = c + R(-theta)((X, Y) - c), i.e.
