@@ -37,12 +37,13 @@ import numpy as np
 # ----------------------------------------------------------------------------------------------
 
 def make_cfg(n, n_theta, n_r, temp_theta=1.0, temp_xy=1.0, delta_xy=1.0, window=1, pad_mode=0,
-             score_norm=0, band_lo=2.0, band_hi=None):
-    """Alg. 1 parameters (n_theta, T_theta, n_xy = n, delta_xy, T_xy) plus the A3-A7 switches."""
+             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0):
+    """Alg. 1 parameters (n_theta, T_theta, n_xy = n, delta_xy, T_xy) plus the A3-A7 switches;
+    angle_score 0 is Eq. 7 (reading A2), 1 the mean over radial lags that Alg. 1 prints."""
     return dict(n=int(n), n_theta=int(n_theta), n_r=int(n_r), temp_theta=float(temp_theta),
                 temp_xy=float(temp_xy), delta_xy=float(delta_xy), window=int(window),
                 pad_mode=int(pad_mode), score_norm=int(score_norm), band_lo=float(band_lo),
-                band_hi=float(n / 2 if band_hi is None else band_hi))
+                band_hi=float(n / 2 if band_hi is None else band_hi), angle_score=int(angle_score))
 
 
 def lags(n):
@@ -135,6 +136,20 @@ def angle_scores(af, ag):
     for i, k in enumerate(lags(n)):
         c[i] = np.sum(af * np.roll(ag, -k, axis=0))
     return c
+
+
+def angle_scores_marginal(af, ag):
+    """The rotation score Alg. 1 prints: the 2D correlation of the (angle x radius) polar arrays,
+    circular in both (WrapPad), averaged over the radial lags.  Summing a circular correlation over
+    all radial lags pairs every radius with every other once, so it is the circular correlation
+    along angle of the radial sums, divided by n_r:
+    c[k] = (1/n_r) sum_a m_f[a] m_g[(a + k) mod n_theta], m = sum over radius."""
+    n_r = af.shape[1]
+    return angle_scores(af.sum(axis=1, keepdims=True), ag.sum(axis=1, keepdims=True)) / n_r
+
+
+def angle_scores_any(af, ag, cfg):
+    return angle_scores_marginal(af, ag) if cfg.get("angle_score", 0) == 1 else angle_scores(af, ag)
 
 
 def normalise_scores(c, score_norm):
@@ -234,7 +249,7 @@ def pose(f, g, cfg, keep=False):
     Ff, Fg = spectrum(f, cfg), spectrum(g, cfg)
     af, ag = magnitude(Ff, cfg), magnitude(Fg, cfg)
     pf, pg = cart2pol(af, cfg), cart2pol(ag, cfg)
-    c_theta = angle_scores(pf, pg)
+    c_theta = angle_scores_any(pf, pg, cfg)
     p_theta = soft_argmax(c_theta, cfg["temp_theta"], cfg["score_norm"])
     d_theta = np.pi / nt
     theta = float(np.sum(p_theta * lags(nt) * d_theta))
@@ -370,6 +385,13 @@ def angle_scores_backward(af, ag, dc):
     return daf, dag
 
 
+def angle_scores_marginal_backward(af, ag, dc):
+    """Adjoint of angle_scores_marginal(): the radial sums' adjoint, spread back over radius."""
+    n_r = af.shape[1]
+    dmf, dmg = angle_scores_backward(af.sum(axis=1, keepdims=True), ag.sum(axis=1, keepdims=True), dc)
+    return np.repeat(dmf / n_r, n_r, axis=1), np.repeat(dmg / n_r, n_r, axis=1)
+
+
 def cart2pol_backward(dp, cfg):
     """Transpose of the bilinear polar gather onto the [N, N/2+1] half spectrum."""
     n = cfg["n"]
@@ -423,7 +445,10 @@ def pose_backward(f, g, cfg, dpose):
     dth = dth_out + dth_rot
     q_t = dth * lags(nt) * (np.pi / nt)
     dc_t = soft_argmax_backward(r["c_theta"], r["p_theta"], q_t, cfg["temp_theta"], cfg["score_norm"])
-    dpf, dpg = angle_scores_backward(r["pf"], r["pg"], dc_t)
+    if cfg.get("angle_score", 0) == 1:
+        dpf, dpg = angle_scores_marginal_backward(r["pf"], r["pg"], dc_t)
+    else:
+        dpf, dpg = angle_scores_backward(r["pf"], r["pg"], dc_t)
     df = df + spectrum_backward(magnitude_backward(r["Ff"], cart2pol_backward(dpf, cfg), cfg), cfg)
     dg = dg + spectrum_backward(magnitude_backward(r["Fg"], cart2pol_backward(dpg, cfg), cfg), cfg)
     return df, dg, dict(dtheta_total=dth, dtheta_rot=dth_rot, dc_xy=dc_xy, dc_theta=dc_t)

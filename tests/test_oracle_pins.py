@@ -410,3 +410,51 @@ def test_exhaustive_search_of_identical_scans_is_the_identity():
     assert r["theta"] == 0.0
     # (the unpaired -N/2 lag row and column leave a bias far below 1e-4 px)
     assert abs(r["tx"]) < 1e-4 and abs(r["ty"]) < 1e-4
+
+
+def test_marginal_angle_score_is_the_radial_mean_of_the_2d_circular_correlation():
+    # Alg. 1 literally: 2D correlation of the wrap-padded (circular) polar arrays, then the mean
+    # over the radial lag dimension -- computed here by brute force over both lags
+    rng = np.random.default_rng(21)
+    nt, nr = 12, 5
+    af, ag = rng.random((nt, nr)), rng.random((nt, nr))
+    c2 = np.zeros((nt, nr))
+    for k in range(nt):
+        for ll in range(nr):
+            c2[k, ll] = np.sum(af * np.roll(np.roll(ag, -k, axis=0), -ll, axis=1))
+    want = np.array([c2[k % nt].mean() for k in O.lags(nt)])
+    got = O.angle_scores_marginal(af, ag)
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+    # it differs from Eq. 7's radial lag 0 in general
+    assert not np.allclose(got, O.angle_scores(af, ag) / nr)
+
+
+def test_marginal_angle_score_adjoint_dot_product():
+    rng = np.random.default_rng(22)
+    af, ag = rng.random((16, 6)), rng.random((16, 6))
+    dc = rng.standard_normal(16)
+    daf, dag = O.angle_scores_marginal_backward(af, ag, dc)
+    u, v = rng.standard_normal(af.shape), rng.standard_normal(ag.shape)
+    h = 1e-6
+    lhs = (np.dot(dc, O.angle_scores_marginal(af + h * u, ag + h * v))
+           - np.dot(dc, O.angle_scores_marginal(af - h * u, ag - h * v))) / (2 * h)
+    assert abs(lhs - (np.sum(daf * u) + np.sum(dag * v))) <= 1e-7 * max(1.0, abs(lhs))
+
+
+def test_pose_gradient_matches_central_differences_marginal_score():
+    f, g, _ = synth.make_batch("single128", pairs=1, start=5)
+    cfg = O.make_cfg(128, 128, 64, angle_score=1)
+    dpose = np.array([0.6, -0.3, 0.8])
+    df, dg, _ = O.pose_backward(f[0], g[0], cfg, dpose)
+    rng = np.random.default_rng(9)
+    h = 1e-4
+    for _ in range(4):
+        y, x = rng.integers(8, 120, 2)
+        for img, grad, which in ((f[0].astype(np.float64), df, 0), (g[0].astype(np.float64), dg, 1)):
+            e = np.zeros_like(img)
+            e[y, x] = h
+            a = (img + e, g[0]) if which == 0 else (f[0], img + e)
+            b = (img - e, g[0]) if which == 0 else (f[0], img - e)
+            ra, rb = O.pose(*a, cfg), O.pose(*b, cfg)
+            fd = sum(dpose[i] * (ra[k] - rb[k]) / (2 * h) for i, k in enumerate(("theta", "tx", "ty")))
+            assert abs(fd - grad[y, x]) <= 1e-6 * max(1.0, np.max(np.abs(grad))), (which, y, x, fd, grad[y, x])
