@@ -65,6 +65,9 @@ typedef struct fmbym_size_cfg {
     int score_norm;
     float band_lo;
     float band_hi;
+    int angle_score;   /* 0: Eq. 7, the angle correlation at radial lag 0, summed over radius (reading
+                          A2); 1: the mean over radial lags of the circular 2D polar correlation that
+                          Alg. 1 prints, i.e. the angle correlation of the radial sums over n_r */
 } fmbym_size_cfg;
 
 /* Handle flags.

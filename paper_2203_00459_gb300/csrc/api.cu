@@ -152,6 +152,7 @@ std::string validate(const fmbym_size_cfg& c) {
     if (c.window != 0 && c.window != 1) return "window must be 0 or 1";
     if (c.pad_mode != 0 && c.pad_mode != 1) return "pad_mode must be 0 or 1";
     if (c.score_norm != 0 && c.score_norm != 1) return "score_norm must be 0 or 1";
+    if (c.angle_score != 0 && c.angle_score != 1) return "angle_score must be 0 or 1";
     if (!(c.band_lo >= 0.f) || !(c.band_hi >= c.band_lo)) return "need 0 <= band_lo <= band_hi";
     return "";
 }
@@ -169,6 +170,7 @@ cudaError_t build_plan(HostPlan& hp) {
     d.nr = c.n_r;
     d.window = c.window;
     d.score_norm = c.score_norm;
+    d.angle_score = c.angle_score;
     d.temp_theta = c.temp_theta;
     d.temp_xy = c.temp_xy;
     d.delta_xy = c.delta_xy;

@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(256) k_b_theta(DevPlan p, const float* __restr
 
 // Angle-correlation adjoint for a chunk of radii: from the forward's Z = FFT along angle of
 // A_f + i A_g (kept in ahat), d A_f = iFFT(conj(DC) A^_g) / n and d A_g = iFFT(DC A^_f) / n, both
-// real, packed as one inverse FFT of U_f + i U_g.  Threads are radius-fastest; the first pass
+// real, packed as one inverse FFT of U_f + i U_g.  With the radial-mean score the same holds for
+// the radial sums M (their transform kept at radius 0), and every radius receives d M / n_r.  Threads are radius-fastest; the first pass
 // forms U_f + i U_g straight from global memory (A^_f, A^_g from Z[k] and Z[n - k]) and the last
 // pass stores d A straight to global memory.
 template <int NT, int RC>
@@ -438,7 +439,10 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_b_angle(DevPlan p, cons
     const int q = blockIdx.y, ch = blockIdx.x;
     const int rr = threadIdx.x % RC, j = threadIdx.x / RC, r = ch * RC + rr;
     const bool live = r < p.nr;
-    const float2* Z = ahat + (size_t)q * NT * p.nr + r;
+    // per-radius score: this radius' transform; radial-mean score: the transform of the radial sums
+    // (kept at radius 0), the same for every radius
+    const bool marginal = p.angle_score == 1;
+    const float2* Z = ahat + (size_t)q * NT * p.nr + (marginal ? 0 : r);
     const float2* DC = bdc + (size_t)q * NT;
     first_pass_global<NT, +1>(sm + rr, ES, j, [&](int k) {
         if (!live) return make_float2(0.f, 0.f);
@@ -450,7 +454,7 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_b_angle(DevPlan p, cons
         return make_float2(uf.x - ug.y, uf.y + ug.x);
     });
     __syncthreads();
-    const float sc = 1.f / NT;
+    const float sc = marginal ? 1.f / ((float)NT * (float)p.nr) : 1.f / NT;
     float2* o = gpol + (size_t)q * NT * p.nr + r;
     rest_global<NT, +1>(sm + rr, ES, j, p.tw_t, [&](int a, float2 v) {
         if (live) o[(size_t)a * p.nr] = make_float2(v.x * sc, v.y * sc);

@@ -131,6 +131,22 @@ __global__ void __launch_bounds__(FftPlan<NT>::T * RC) k_angle(DevPlan p, const 
     fft_passes_from<NT, -1, 2>(sm + rr, ES, j, p.tw_t);
     float2* out = sp + ((size_t)q * gridDim.x + ch) * NT;
     const unsigned grp = ((1u << RC) - 1u) << (threadIdx.x & (32 - RC));   // the RC lanes of this thread's k
+    if (p.angle_score == 1) {
+        // radial-mean score: the transform is linear, so the chunk's share of the transform of the
+        // radial sums is the sum of its columns' transforms
+#pragma unroll 4
+        for (int m = 0; m < 16; ++m) {
+            const int k = j + T * m;
+            float2 z = sm[spad(k) * ES + rr];
+#pragma unroll
+            for (int o = RC / 2; o > 0; o >>= 1) {
+                z.x += __shfl_xor_sync(grp, z.x, o);
+                z.y += __shfl_xor_sync(grp, z.y, o);
+            }
+            if (rr == 0) out[k] = z;
+        }
+        return;
+    }
 #pragma unroll 4
     for (int m = 0; m < 16; ++m) {
         const int k = j + T * m, km = k == 0 ? 0 : NT - k;
@@ -154,7 +170,7 @@ template <int NT>
 __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restrict__ sp, int nch,
                                                const long long* __restrict__ tab, float* __restrict__ th,
                                                float* __restrict__ pose, float* __restrict__ c_theta,
-                                               float* __restrict__ ct) {
+                                               float* __restrict__ ct, float2* __restrict__ ahat) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<NT>::T;
     __shared__ float2 z[spad(NT)];
@@ -171,6 +187,30 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
         z[spad(k)] = make_float2(sx, sy);
     }
     __syncthreads();
+    if (p.angle_score == 1) {
+        // z holds Z = M^_f + i M^_g, the transform of the radial sums of A_f + i A_g: keep it for the
+        // adjoint, separate the two with the mirror k <-> n - k and form conj(M^_f) M^_g / n_r
+        float2 sk[(NT + 255) / 256];
+#pragma unroll
+        for (int m = 0; m < (NT + 255) / 256; ++m) {
+            const int k = threadIdx.x + 256 * m;
+            if (k < NT) {
+                const float2 a = z[spad(k)], b = z[spad(k == 0 ? 0 : NT - k)];
+                if (ahat) ahat[((size_t)q * NT + k) * p.nr] = a;
+                const float ax = 0.5f * (a.x + b.x), ay = 0.5f * (a.y - b.y);
+                const float bx = 0.5f * (a.y + b.y), by = -0.5f * (a.x - b.x);
+                const float inr = 1.f / (float)p.nr;
+                sk[m] = make_float2((ax * bx + ay * by) * inr, (ax * by - ay * bx) * inr);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < (NT + 255) / 256; ++m) {
+            const int k = threadIdx.x + 256 * m;
+            if (k < NT) z[spad(k)] = sk[m];
+        }
+        __syncthreads();
+    }
     fft<NT, +1>(z, 1, threadIdx.x, threadIdx.x < T, p.tw_t);
     float lsum = 0.f, lmax = -FLT_MAX;
     for (int i = threadIdx.x; i < NT; i += blockDim.x) {
@@ -519,7 +559,7 @@ static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, con
     else
         launch_pdl(k_angle<NT, 16>, dim3(nch, B), FftPlan<NT>::T * 16, smem_angle<NT, 16>(), st, p, w.mt, w.sp, w.ahat, B);
     w.tr->before(K_THETA, st);
-    launch_pdl(k_theta<NT>, B, 256, 0, st, p, w.sp, nch, tab, w.th, pose, c_theta, w.ct);
+    launch_pdl(k_theta<NT>, B, 256, 0, st, p, w.sp, nch, tab, w.th, pose, c_theta, w.ct, w.ahat);
     return cudaGetLastError();
 }
 

@@ -122,7 +122,8 @@ std::string check_cfg(const fmbym_size_cfg& c) {
     if (c.n_r < 1 || c.n_r > c.n / 2) return "n_r must be in [1, n/2]";
     if (!(c.temp_theta > 0.f) || !(c.temp_xy > 0.f) || !(c.delta_xy > 0.f))
         return "temperatures and delta_xy must be positive";
-    if ((c.window | c.pad_mode | c.score_norm) & ~1) return "window, pad_mode and score_norm must be 0 or 1";
+    if ((c.window | c.pad_mode | c.score_norm | c.angle_score) & ~1)
+        return "window, pad_mode, score_norm and angle_score must be 0 or 1";
     if (!(c.band_lo >= 0.f) || !(c.band_hi >= c.band_lo)) return "need 0 <= band_lo <= band_hi";
     return "";
 }
@@ -158,6 +159,7 @@ int fmbym_pose_noalloc(void* stream, const fmbym_size_cfg* cfg, int n_pairs, con
     p.nr = cfg->n_r;
     p.window = cfg->window;
     p.score_norm = cfg->score_norm;
+    p.angle_score = cfg->angle_score;
     p.temp_theta = cfg->temp_theta;
     p.temp_xy = cfg->temp_xy;
     p.delta_xy = cfg->delta_xy;

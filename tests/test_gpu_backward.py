@@ -190,3 +190,10 @@ def test_training_call_equals_separate_calls(lib, graph, kind):
         assert grad_err(df.cpu().numpy()[offs[k]:offs[k] + n * n].reshape(n, n), odf) <= TOL_GRAD
         assert grad_err(dg.cpu().numpy()[offs[k]:offs[k] + n * n].reshape(n, n), odg) <= TOL_GRAD
     s.close()
+
+
+def test_adjoint_radial_mean_angle_score(lib):
+    f, g, _ = synth.make_batch("batch256", pairs=2, start=61)
+    cfg = lib.size_cfg(256, 400, 128, temp_theta=2.0, angle_score=1)
+    df, dg = gpu_backward(lib, cfg, f, g, DP[:2])
+    check_against_oracle(cfg, f, g, DP[:2], df, dg, "marginal")

@@ -160,3 +160,16 @@ def test_empty_batch_and_errors(lib):
         s.pose(flat, flat, size_idx=[0, 0], offsets=[0, 128 * 128 + 2])
     assert ei.value.status == _lib.ERR_INVALID_ARG
     s.close()
+
+
+@pytest.mark.parametrize("name,n,nt,nr,score_norm,temp", [("batch256", 256, 400, 128, 0, 2.0),
+                                                          ("single128", 128, 128, 50, 1, 1.0e7)])
+def test_radial_mean_angle_score(lib, name, n, nt, nr, score_norm, temp):
+    """The angle score Alg. 1 prints (mean over radial lags of the 2D polar correlation) with the
+    T_theta = 2 of Alg. 1 (z-scores), and with raw scores and a ragged chunk of radii."""
+    f, g, _ = synth.make_batch(name, pairs=2, start=60)
+    cfg = lib.size_cfg(n, nt, nr, temp_theta=temp, score_norm=score_norm, angle_score=1,
+                       temp_xy=1.0 if score_norm == 0 else 1.0e4)
+    o = run(lib, cfg, f, g)
+    for i in range(2):
+        check_pair(f[i], g[i], cfg, o["pose"][i], o["c_theta"][nt * i:nt * (i + 1)], o["c_xy"][i], f"marg{i}")
