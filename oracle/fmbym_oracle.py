@@ -37,13 +37,15 @@ import numpy as np
 # ----------------------------------------------------------------------------------------------
 
 def make_cfg(n, n_theta, n_r, temp_theta=1.0, temp_xy=1.0, delta_xy=1.0, window=1, pad_mode=0,
-             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0):
+             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0, full_circle=0):
     """Alg. 1 parameters (n_theta, T_theta, n_xy = n, delta_xy, T_xy) plus the A3-A7 switches;
-    angle_score 0 is Eq. 7 (reading A2), 1 the mean over radial lags that Alg. 1 prints."""
+    angle_score 0 is Eq. 7 (reading A2), 1 the mean over radial lags that Alg. 1 prints;
+    full_circle 1 resolves the heading over the full circle (see pose())."""
     return dict(n=int(n), n_theta=int(n_theta), n_r=int(n_r), temp_theta=float(temp_theta),
                 temp_xy=float(temp_xy), delta_xy=float(delta_xy), window=int(window),
                 pad_mode=int(pad_mode), score_norm=int(score_norm), band_lo=float(band_lo),
-                band_hi=float(n / 2 if band_hi is None else band_hi), angle_score=int(angle_score))
+                band_hi=float(n / 2 if band_hi is None else band_hi), angle_score=int(angle_score),
+                full_circle=int(full_circle))
 
 
 def lags(n):
@@ -256,6 +258,14 @@ def pose(f, g, cfg, keep=False):
     # stage 2 (Alg. 1 stage 2)
     fr = rotate(f, theta)
     c_xy = xcorr2d(fr, g, cfg["pad_mode"])
+    if cfg.get("full_circle", 0) == 1:
+        # |F| cannot tell theta from theta + pi (Sec. V suggests the decoupled search for arbitrary
+        # headings): correlate at both and keep the one whose translation peak is higher
+        theta_b = theta + np.pi if theta < 0 else theta - np.pi
+        fr_b = rotate(f, theta_b)
+        c_b = xcorr2d(fr_b, g, cfg["pad_mode"])
+        if c_b.max() > c_xy.max():
+            theta, fr, c_xy = theta_b, fr_b, c_b
     p_xy = soft_argmax(c_xy, cfg["temp_xy"], cfg["score_norm"])
     s = lags(n) * cfg["delta_xy"]
     tx = float(np.sum(p_xy * s[None, :]))

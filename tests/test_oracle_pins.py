@@ -458,3 +458,44 @@ def test_pose_gradient_matches_central_differences_marginal_score():
             ra, rb = O.pose(*a, cfg), O.pose(*b, cfg)
             fd = sum(dpose[i] * (ra[k] - rb[k]) / (2 * h) for i, k in enumerate(("theta", "tx", "ty")))
             assert abs(fd - grad[y, x]) <= 1e-6 * max(1.0, np.max(np.abs(grad))), (which, y, x, fd, grad[y, x])
+
+
+@pytest.mark.parametrize("deg,flip", [(170.0, True), (-125.0, True), (12.0, False)])
+def test_full_circle_heading(deg, flip):
+    # a scene turned by more than a quarter turn: the half-circle search reports the heading less
+    # half a turn; the full-circle search finds it, with the translation
+    n = 128
+    th, tx, ty = math.radians(deg), 3.0, -2.0
+    f, g = synth.make_pair(n, 60, 8, th, tx, ty, seed=777, index=int(deg) + 500)
+    # a sharp angle soft-argmax (T = 0.2 on z-scores) so that stage 1 resolves large headings
+    half = O.pose(f, g, O.make_cfg(n, 128, 64, temp_theta=0.2))
+    full = O.pose(f, g, O.make_cfg(n, 128, 64, temp_theta=0.2, full_circle=1))
+    wrap = lambda a: (a + math.pi) % (2 * math.pi) - math.pi
+    assert abs(wrap(full["theta"] - th)) < math.radians(1.5)
+    assert abs(full["tx"] - tx) < 0.5 and abs(full["ty"] - ty) < 0.5
+    assert abs(wrap(half["theta"] - th + (math.pi if flip else 0.0))) < math.radians(1.5)
+    if not flip:
+        assert full["theta"] == half["theta"] and full["tx"] == half["tx"]
+
+
+def test_pose_gradient_matches_central_differences_full_circle():
+    n = 128
+    f, g = synth.make_pair(n, 40, 6, math.radians(160.0), 2.0, 1.0, seed=778, index=1)
+    cfg = O.make_cfg(n, 128, 64, temp_theta=0.2, full_circle=1)
+    dpose = np.array([0.5, 0.7, -0.4])
+    assert abs(O.pose(f, g, cfg)["theta"]) > math.pi / 2      # the flipped branch
+    df, dg, _ = O.pose_backward(f, g, cfg, dpose)
+    rng = np.random.default_rng(10)
+    h = 1e-4
+    for _ in range(3):
+        y, x = rng.integers(20, 108, 2)
+        for which in (0, 1):
+            img = (f if which == 0 else g).astype(np.float64)
+            e = np.zeros_like(img)
+            e[y, x] = h
+            a = (img + e, g) if which == 0 else (f, img + e)
+            b = (img - e, g) if which == 0 else (f, img - e)
+            ra, rb = O.pose(*a, cfg), O.pose(*b, cfg)
+            fd = sum(dpose[i] * (ra[k] - rb[k]) / (2 * h) for i, k in enumerate(("theta", "tx", "ty")))
+            grad = (df if which == 0 else dg)
+            assert abs(fd - grad[y, x]) <= 1e-6 * max(1.0, np.max(np.abs(grad))), (which, y, x, fd, grad[y, x])
