@@ -68,6 +68,10 @@ typedef struct fmbym_size_cfg {
     int angle_score;   /* 0: Eq. 7, the angle correlation at radial lag 0, summed over radius (reading
                           A2); 1: the mean over radial lags of the circular 2D polar correlation that
                           Alg. 1 prints, i.e. the angle correlation of the radial sums over n_r */
+    int full_circle;   /* 0: heading in [-pi/2, pi/2) (|F| of a real scan is centrosymmetric, reading
+                          A9); 1: the full circle, stage 2 run at theta and theta + pi and the one
+                          with the higher translation peak kept (the extension of Sec. V for
+                          arbitrary headings; three stage-2 passes) */
 } fmbym_size_cfg;
 
 /* Handle flags.

@@ -22,7 +22,8 @@ class SizeCfg(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_r", ctypes.c_int),
                 ("temp_theta", ctypes.c_float), ("temp_xy", ctypes.c_float), ("delta_xy", ctypes.c_float),
                 ("window", ctypes.c_int), ("pad_mode", ctypes.c_int), ("score_norm", ctypes.c_int),
-                ("band_lo", ctypes.c_float), ("band_hi", ctypes.c_float), ("angle_score", ctypes.c_int)]
+                ("band_lo", ctypes.c_float), ("band_hi", ctypes.c_float), ("angle_score", ctypes.c_int),
+                ("full_circle", ctypes.c_int)]
 
 
 class Config(ctypes.Structure):

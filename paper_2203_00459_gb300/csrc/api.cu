@@ -61,6 +61,7 @@ struct fmbym_handle {
     unsigned* d_cnt = nullptr;    // [max_pairs] completion counters, zero between launches
     float* d_bpose = nullptr;     // [max_pairs][3] pose recomputed by the adjoint
     float4* d_best = nullptr;     // [max_pairs] running best of the exhaustive search
+    float* d_fcpose = nullptr;    // [max_pairs][3] full-circle candidate translations
     long long stage_elems = 0;
     Tracer tracer;
     std::string err;
@@ -88,6 +89,8 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
     t.st = (float*)take(b * c2r_blocks(p) * 4 * sizeof(float));
     t.sx = (float*)take(b * kSplitXY * 8 * sizeof(float));
     t.xm = (float*)take(b * 8 * sizeof(float));
+    t.fc = (float*)take(b * 8 * sizeof(float));
+    t.fcpose = (float*)take(b * 3 * sizeof(float));
     t.ct = (float*)take(b * p.nt * sizeof(float));
     if (backward) {
         t.ahat = (float2*)take(b * p.nt * p.nr * sizeof(float2));
@@ -153,6 +156,7 @@ std::string validate(const fmbym_size_cfg& c) {
     if (c.pad_mode != 0 && c.pad_mode != 1) return "pad_mode must be 0 or 1";
     if (c.score_norm != 0 && c.score_norm != 1) return "score_norm must be 0 or 1";
     if (c.angle_score != 0 && c.angle_score != 1) return "angle_score must be 0 or 1";
+    if (c.full_circle != 0 && c.full_circle != 1) return "full_circle must be 0 or 1";
     if (!(c.band_lo >= 0.f) || !(c.band_hi >= c.band_lo)) return "need 0 <= band_lo <= band_hi";
     return "";
 }
@@ -171,6 +175,7 @@ cudaError_t build_plan(HostPlan& hp) {
     d.window = c.window;
     d.score_norm = c.score_norm;
     d.angle_score = c.angle_score;
+    d.full_circle = c.full_circle;
     d.temp_theta = c.temp_theta;
     d.temp_xy = c.temp_xy;
     d.delta_xy = c.delta_xy;
@@ -353,6 +358,7 @@ cudaError_t launch_group(fmbym_handle* h, const Group& gr, const long long* dtab
     w.tr = &h->tracer;
     w.cnt = h->d_cnt + (size_t)gr.size_idx * h->max_pairs;
     w.bpose = h->d_bpose;
+    w.fcpose = h->d_fcpose;   // indexed by the call's pair index, which spans every group
     const long long* tab = dtab + 3 * gr.first;
     if (phase == 0) {
         const bool train = a.kind == 2;
@@ -616,6 +622,7 @@ void fmbym_destroy(fmbym_handle* h) {
     cudaFree(h->d_cnt);
     cudaFree(h->d_bpose);
     cudaFree(h->d_best);
+    cudaFree(h->d_fcpose);
     if (h->h_tab) cudaFreeHost(h->h_tab);
     for (cudaEvent_t e : h->tracer.ev) cudaEventDestroy(e);
     if (h->tab_free) cudaEventDestroy(h->tab_free);
@@ -697,7 +704,8 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
         (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_bpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_best, sizeof(float4) * cfg->max_pairs)) != cudaSuccess) {
+        (e = cudaMalloc(&h->d_best, sizeof(float4) * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fcpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess) {
         fmbym_destroy(h);
         return cuda_fail(nullptr, e, "staging allocation");
     }

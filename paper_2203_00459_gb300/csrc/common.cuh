@@ -51,7 +51,7 @@ struct PolarSample {
 struct DevPlan {
     int n, p, nt, nr;      // scan side, padded side (2N or N), angle bins, radii
     int m_lo, m_hi;        // band-pass: keep integer rho^2 in [m_lo, m_hi]
-    int window, score_norm, angle_score;
+    int window, score_norm, angle_score, full_circle;
     float temp_theta, temp_xy, delta_xy;
     const float* win;      // [N] periodic Hann
     const float2* tw_n;    // [N]  exp(-2 pi i k / N)
@@ -121,6 +121,8 @@ struct Ws {
     float* st;    // [B][c2r blocks][4] per-block mean, M2, max of the translation scores
     float* sx;    // [B][kSplitXY][8] soft-argmax partial sums
     float* xm;    // [B][8]           translation soft-argmax statistics and moments kept for the adjoint
+    float* fc;    // [B][8]           full circle: stage 1's heading splits, the theta + pi peak
+    float* fcpose;  // [pairs][3]     full circle: the theta + pi candidate's translation, by pair index
     unsigned* cnt;  // [B] completion counters of the last-block reductions: a handle-wide array that
                     // is zero between launches (the last block of a pair resets its counter)
     float* ct;    // [B][n_theta]     angle scores in lag order (kept for the adjoint)

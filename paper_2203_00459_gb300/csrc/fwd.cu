@@ -535,6 +535,59 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
 }
 
 // ---------------------------------------------------------------------------------------------
+// full-circle heading (the extension of Sec. V): stage 2 at theta and at theta + pi
+// ---------------------------------------------------------------------------------------------
+
+// Keeps stage 1's heading splits and turns every pair's heading by pi: theta' = theta + pi for
+// theta < 0, theta - pi otherwise (in (-pi, pi]); its cosine and sine are the negated splits.
+__global__ void k_fc_flip(float* __restrict__ th, float* __restrict__ fc, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= B) return;
+    float* t = th + 8 * q;
+    float* k = fc + 8 * q;
+    const float pi = 3.14159265358979323846f;
+    for (int i = 0; i < 5; ++i) k[i] = t[i];
+    t[0] = t[0] < 0.f ? t[0] + pi : t[0] - pi;
+    for (int i = 1; i < 5; ++i) t[i] = -t[i];
+}
+
+// The highest translation score of each pair (the maximum of the block maxima of k_s2_c2r).
+__device__ __forceinline__ float fc_peak(const float* __restrict__ st, int nblk, int q) {
+    float m = -FLT_MAX;
+    for (int b = 0; b < nblk; ++b) m = fmaxf(m, st[((size_t)q * nblk + b) * 4 + 2]);
+    return m;
+}
+
+// After the theta + pi pass: records its peak and puts stage 1's heading back.
+__global__ void k_fc_restore(const float* __restrict__ st, int nblk, float* __restrict__ th, float* __restrict__ fc,
+                             int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= B) return;
+    float* k = fc + 8 * q;
+    k[5] = fc_peak(st, nblk, q);
+    for (int i = 0; i < 5; ++i) th[8 * q + i] = k[i];
+}
+
+// After the theta pass: where the theta + pi peak is higher (strictly), the heading turns by pi
+// (th and the pose's theta); the last stage-2 pass then runs at every pair's winner.
+__global__ void k_fc_select(const long long* __restrict__ tab, const float* __restrict__ st, int nblk,
+                            float* __restrict__ th, const float* __restrict__ fc, float* __restrict__ pose, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= B) return;
+    const float* k = fc + 8 * q;
+    if (k[5] > fc_peak(st, nblk, q)) {
+        float* t = th + 8 * q;
+        const float pi = 3.14159265358979323846f;
+        t[0] = k[0] < 0.f ? k[0] + pi : k[0] - pi;
+        for (int i = 1; i < 5; ++i) t[i] = -k[i];
+        pose[3 * tab[3 * q + 2]] = t[0];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
 
@@ -576,6 +629,17 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
     else if (p.nt == 256) e = launch_stage1_angle<256>(p, w, B, tab, pose, c_theta, st);
     else e = launch_stage1_angle<400>(p, w, B, tab, pose, c_theta, st);
     if (e != cudaSuccess) return e;
+    if (!p.full_circle) return launch_stage2<N, P>(p, w, B, tab, f, g, pose, c_xy, st);
+    // full circle: the two candidate passes keep nothing for the adjoint and write no scores for
+    // the caller; the third pass runs at each pair's winner
+    Ws wc = w;
+    wc.s2hat = nullptr;
+    const int nb = (B + 127) / 128, nblk = c2r_blocks(p);
+    launch_pdl(k_fc_flip, nb, 128, 0, st, w.th, w.fc, B);
+    if ((e = launch_stage2<N, P>(p, wc, B, tab, f, g, w.fcpose, nullptr, st)) != cudaSuccess) return e;
+    launch_pdl(k_fc_restore, nb, 128, 0, st, (const float*)w.st, nblk, w.th, w.fc, B);
+    if ((e = launch_stage2<N, P>(p, wc, B, tab, f, g, pose, nullptr, st)) != cudaSuccess) return e;
+    launch_pdl(k_fc_select, nb, 128, 0, st, tab, (const float*)w.st, nblk, w.th, (const float*)w.fc, pose, B);
     return launch_stage2<N, P>(p, w, B, tab, f, g, pose, c_xy, st);
 }
 

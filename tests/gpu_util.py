@@ -27,7 +27,7 @@ def argmax_ok(gpu, ref):
 def oracle_cfg(c):
     return O.make_cfg(c["n"], c["n_theta"], c["n_r"], c["temp_theta"], c["temp_xy"], c["delta_xy"],
                       c["window"], c["pad_mode"], c["score_norm"], c["band_lo"], c["band_hi"],
-                      c.get("angle_score", 0))
+                      c.get("angle_score", 0), c.get("full_circle", 0))
 
 
 def check_pair(f, g, cfg, pose, c_theta=None, c_xy=None, tag=""):

@@ -197,3 +197,14 @@ def test_adjoint_radial_mean_angle_score(lib):
     cfg = lib.size_cfg(256, 400, 128, temp_theta=2.0, angle_score=1)
     df, dg = gpu_backward(lib, cfg, f, g, DP[:2])
     check_against_oracle(cfg, f, g, DP[:2], df, dg, "marginal")
+
+
+def test_adjoint_full_circle(lib):
+    import math
+    pairs = [synth.make_pair(128, 40, 6, math.radians(d), 2.0, 1.0, seed=780, index=i)
+             for i, d in enumerate((160.0, -20.0))]
+    f = np.stack([a for a, _ in pairs])
+    g = np.stack([b for _, b in pairs])
+    cfg = lib.size_cfg(128, 128, 64, temp_theta=0.2, full_circle=1)
+    df, dg = gpu_backward(lib, cfg, f, g, DP[:2])
+    check_against_oracle(cfg, f, g, DP[:2], df, dg, "full_circle")

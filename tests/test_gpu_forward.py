@@ -173,3 +173,20 @@ def test_radial_mean_angle_score(lib, name, n, nt, nr, score_norm, temp):
     o = run(lib, cfg, f, g)
     for i in range(2):
         check_pair(f[i], g[i], cfg, o["pose"][i], o["c_theta"][nt * i:nt * (i + 1)], o["c_xy"][i], f"marg{i}")
+
+
+@pytest.mark.parametrize("n,nt,nr", [(128, 128, 64), (256, 400, 128)])
+def test_full_circle_heading(lib, n, nt, nr):
+    """Headings beyond a quarter turn: stage 2 at theta and theta + pi, the higher peak kept."""
+    import math
+    degs = [170.0, -125.0, 12.0]
+    pairs = [synth.make_pair(n, n * n // 300, n // 16, math.radians(d), 3.0, -2.0, seed=779, index=i)
+             for i, d in enumerate(degs)]
+    f = np.stack([a for a, _ in pairs])
+    g = np.stack([b for _, b in pairs])
+    cfg = lib.size_cfg(n, nt, nr, temp_theta=0.2, full_circle=1)
+    o = run(lib, cfg, f, g)
+    for i in range(len(degs)):
+        check_pair(f[i], g[i], cfg, o["pose"][i], o["c_theta"][nt * i:nt * (i + 1)], o["c_xy"][i], f"fc{i}")
+        err = (o["pose"][i][0] - math.radians(degs[i]) + math.pi) % (2 * math.pi) - math.pi
+        assert abs(err) < math.radians(1.5), (degs[i], o["pose"][i])
