@@ -300,6 +300,12 @@ float* fmbym_unet_running(fmbym_unet* u);
 int fmbym_unet_load(fmbym_unet* u, void* stream, const float* params, const float* running);
 int fmbym_unet_store(fmbym_unet* u, void* stream, float* params, float* running, float* grads);
 
+/* The optimiser state for checkpoint / resume: copies the Adam first and second moments (device
+ * float32 [param_count] each, in the parameter layout) out of (store) or into (load) the handle;
+ * a NULL pointer skips that moment.  Load after fmbym_unet_load, which resets them. */
+int fmbym_unet_store_adam(fmbym_unet* u, void* stream, float* m, float* v);
+int fmbym_unet_load_adam(fmbym_unet* u, void* stream, const float* m, const float* v);
+
 /* Inspection: copies one tensor of convolution layer `layer` (0-based, in the parameter order) for
  * the first n pairs of the last call, widened to float32 NHWC, into dst (device): which = 0 the
  * convolution output y (pre-BN), 1 the bf16 activation a (post-ReLU), 2 dL/da, 3 the bf16 dL/dy.

@@ -76,6 +76,8 @@ SIGNATURES = {
     "fmbym_unet_load": (_I, [_P, _P, _P, _P]),
     "fmbym_unet_layer_tensor": (_I, [_P, _P, _I, _I, _I, _P]),
     "fmbym_unet_store": (_I, [_P, _P, _P, _P, _P]),
+    "fmbym_unet_store_adam": (_I, [_P, _P, _P, _P]),
+    "fmbym_unet_load_adam": (_I, [_P, _P, _P, _P]),
 }
 
 _lib = None

@@ -643,6 +643,7 @@ template <int N, int P>
 static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                             const float* g, const float* dpose, float* df, float* dg, cudaStream_t st,
                             const float* fwd_pose) {
+    StageRange range("fmbym adjoint");
     if (!fwd_pose) {
         cudaError_t e = launch_forward(p, w, B, tab, f, g, w.bpose, nullptr, nullptr, st);
         if (e != cudaSuccess) return e;

@@ -2,6 +2,7 @@
 // size group, and the launchers of the forward and backward kernel sequences.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -33,6 +34,13 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
+
+// An NVTX range over the launches of one stage (visible to Nsight tools on the host timeline;
+// costs nothing measurable without a tool attached).
+struct StageRange {
+    explicit StageRange(const char* name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+};
 
 // Launch schedules with more than one compiled variant; each size's DevPlan names the variant its
 // launches use (the defaults below, or the autotuner's measured choice).

@@ -620,6 +620,7 @@ template <int N, int P>
 static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                              const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
     constexpr int T1 = FftPlan<N>::T;
+    StageRange range("fmbym forward");
     w.tr->before(K_S1_ROWS, st);
     launch_pdl(k_s1_rows<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st, p, tab, f, g, w.s1, B);
     w.tr->before(K_S1_COLS, st);

@@ -370,6 +370,26 @@ int fmbym_unet_store(fmbym_unet* u, void* stream, float* params, float* running,
     return FMBYM_OK;
 }
 
+int fmbym_unet_store_adam(fmbym_unet* u, void* stream, float* m, float* v) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (m) e = cudaMemcpyAsync(m, u->adam_m, u->n_params * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, u->adam_v, u->n_params * 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return ucuda(u, e, "store_adam");
+    return FMBYM_OK;
+}
+
+int fmbym_unet_load_adam(fmbym_unet* u, void* stream, const float* m, const float* v) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (m) e = cudaMemcpyAsync(u->adam_m, m, u->n_params * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(u->adam_v, v, u->n_params * 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return ucuda(u, e, "load_adam");
+    return FMBYM_OK;
+}
+
 int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const float* g, int training,
                        float* f_out, float* g_out, float* masks) {
     if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");

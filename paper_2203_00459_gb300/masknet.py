@@ -110,6 +110,16 @@ class MaskNet:
         _lib.check_unet(_lib.lib().fmbym_unet_store(self._h, _st(), _p(p), _p(r), _p(g)), self._h)
         return p, r, g
 
+    def adam_state(self):
+        """(first, second) Adam moments as new device tensors."""
+        m = torch.empty(self.n_params, device="cuda")
+        v = torch.empty(self.n_params, device="cuda")
+        _lib.check_unet(_lib.lib().fmbym_unet_store_adam(self._h, _st(), _p(m), _p(v)), self._h)
+        return m, v
+
+    def load_adam(self, m=None, v=None):
+        _lib.check_unet(_lib.lib().fmbym_unet_load_adam(self._h, _st(), _p(m), _p(v)), self._h)
+
     def forward(self, f, g, training=True, want_masks=False, f_out=None, g_out=None):
         n = f.shape[0]
         fo = torch.empty_like(f) if f_out is None else f_out

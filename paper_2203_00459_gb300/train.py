@@ -52,6 +52,25 @@ class MaskedSearch:
         self.net.adam(lr, self.steps)
         return loss
 
+    def save(self, path):
+        """Checkpoint: float32 master parameters, BN running statistics, both Adam moments and the
+        step count (the state a resumed run needs to continue bit for bit), as an .npz file."""
+        p, r, _ = self.net.store()
+        m, v = self.net.adam_state()
+        torch.cuda.synchronize()
+        np.savez(path, params=p.cpu().numpy(), running=r.cpu().numpy(), adam_m=m.cpu().numpy(),
+                 adam_v=v.cpu().numpy(), steps=np.int64(self.steps), loss_kind=np.int64(self.loss_kind))
+
+    def load(self, path):
+        """Resumes from a checkpoint written by save()."""
+        z = np.load(path)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        self.net.load(dev(z["params"]), dev(z["running"]))
+        self.net.load_adam(dev(z["adam_m"]), dev(z["adam_v"]))
+        self.steps = int(z["steps"])
+        self.loss_kind = int(z["loss_kind"])
+        torch.cuda.synchronize()
+
     def poses(self, f, g, masked=True):
         """Poses with the trained masks (evaluation statistics), or of the raw scans, computed in
         chunks of the handle's batch size."""

@@ -56,3 +56,31 @@ def test_trained_mask_lowers_translation_error():
     # the summed L1 loss of Eq. 13 is dominated by the translation (pixels against radians), so the
     # mask is judged on translation; the heading must not get materially worse
     assert e_mask[0] <= 1.2 * e_plain[0]
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    """Training 6 steps, checkpointing, then 6 more equals loading the checkpoint into a fresh model
+    and running the same 6 steps: parameters, running statistics and Adam moments bit for bit."""
+    from paper_2203_00459_gb300 import build
+    build.build()
+    from paper_2203_00459_gb300 import train
+    F, G, P = train.trajectory_data(2, 13, 20221111)          # 24 pairs
+    Ft, Gt = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
+    Pt = torch.from_numpy(P.astype(np.float32)).cuda()
+    batches = [slice(8 * (k % 3), 8 * (k % 3) + 8) for k in range(12)]
+    a = train.MaskedSearch(batch=8, seed=3)
+    for k in range(6):
+        a.train_step(Ft[batches[k]].contiguous(), Gt[batches[k]].contiguous(), Pt[batches[k]].contiguous())
+    ck = str(tmp_path / "ck.npz")
+    a.save(ck)
+    for k in range(6, 12):
+        a.train_step(Ft[batches[k]].contiguous(), Gt[batches[k]].contiguous(), Pt[batches[k]].contiguous())
+    b = train.MaskedSearch(batch=8, seed=99)   # different initial weights, overwritten by the checkpoint
+    b.load(ck)
+    assert b.steps == 6
+    for k in range(6, 12):
+        b.train_step(Ft[batches[k]].contiguous(), Gt[batches[k]].contiguous(), Pt[batches[k]].contiguous())
+    for x, y in zip(a.net.store()[:2] + a.net.adam_state(), b.net.store()[:2] + b.net.adam_state()):
+        assert torch.equal(x, y)
+    a.close()
+    b.close()
