@@ -59,6 +59,8 @@ struct fmbym_unet {
     float* wpart = nullptr;             // wgrad partials
     float* hpart = nullptr;             // head partials
     size_t stats_cap = 0, bnpart_cap = 0, wpart_cap = 0, hpart_cap = 0;
+    int wslots[5] = {0};                // resident CTAs of the wgrad variants (CIB 8/16/32/64, planes)
+    int nsm = 0;
     std::vector<void*> allocs;
     long long launches = 0;
     int last_batch = -1;
@@ -131,6 +133,57 @@ cudaError_t conv_dispatch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cuda
         case 128: return conv_launch<128>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// BN adjoint slabs: about four CTAs per SM, each a whole number of the reduce kernel's pixel rows.
+int bn_pix_per_cta(const fmbym_unet* u, long long px, int C) {
+    const long long rows = 256 / (C / 4), target = 4LL * u->nsm;
+    const long long per = (px + target - 1) / target;
+    return (int)std::max(rows, (per + rows - 1) / rows * rows);
+}
+
+// Partials of the head adjoint: a grid of eight CTAs per SM, grid-stride over the pixels.
+int head_grid(const fmbym_unet* u) { return 8 * u->nsm; }
+
+// Weight-gradient launch geometry: CIB input channels per CTA (the smallest of 8, 16, 32, 64 that
+// holds the layer's inputs), gy x gz channel blocks, and the pixel tiles cut into one wave of
+// chunks over the resident CTAs of that variant.
+int wgrad_variant(const Layer& l) {
+    if (l.planes) return 4;
+    return l.cin <= 8 ? 0 : l.cin <= 16 ? 1 : l.cin <= 32 ? 2 : 3;
+}
+
+struct WgradGeom {
+    int gy, gz, chunks, tpc, used;
+};
+
+WgradGeom wgrad_geom(const fmbym_unet* u, const Layer& l, int B) {
+    const int v = wgrad_variant(l), cib = v == 4 ? 8 : 8 << v;
+    WgradGeom w;
+    w.gy = (l.cout + 15) / 16;
+    w.gz = (l.cin + cib - 1) / cib;
+    const int ntiles = B * (l.H / kTH) * (l.W / kTW);
+    w.chunks = std::max(1, std::min(ntiles, u->wslots[v] / (w.gy * w.gz)));
+    w.tpc = (ntiles + w.chunks - 1) / w.chunks;
+    w.used = (ntiles + w.tpc - 1) / w.tpc;
+    return w;
+}
+
+template <int CIB, bool PLANES>
+cudaError_t wgrad_prepare(fmbym_unet* u, int v) {
+    const size_t smem = wgrad_smem<CIB>();
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad<CIB, PLANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wgrad<CIB, PLANES>, 256, smem);
+    u->wslots[v] = std::max(1, occ) * u->nsm;
+    return e;
+}
+
+template <int CIB, bool PLANES>
+void wgrad_run(const Layer& l, const WgradGeom& w, int n, const float* f, const float* g, float* part,
+               cudaStream_t st) {
+    k_wgrad<CIB, PLANES><<<dim3(w.used, w.gy, w.gz), 256, wgrad_smem<CIB>(), st>>>(
+        l.dy, l.cout, PLANES ? nullptr : l.in0, PLANES ? 0 : l.c0, l.in1, l.c1, f, g, n, l.H, l.W, w.tpc, part);
 }
 
 // Inputs of layer k for a batch of B (planes for the first layer are set per call).
@@ -248,6 +301,14 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     chk(ualloc(u, &u->adam_m, off));
     chk(ualloc(u, &u->adam_v, off));
     chk(ualloc(u, &u->running, roff));
+    int dev = 0;
+    chk(cudaGetDevice(&dev));
+    chk(cudaDeviceGetAttribute(&u->nsm, cudaDevAttrMultiProcessorCount, dev));
+    chk(wgrad_prepare<8, false>(u, 0));
+    chk(wgrad_prepare<16, false>(u, 1));
+    chk(wgrad_prepare<32, false>(u, 2));
+    chk(wgrad_prepare<64, false>(u, 3));
+    chk(wgrad_prepare<8, true>(u, 4));
     size_t stats_cap = 0, bn_cap = 0, w_cap = 0;
     for (Layer& l : u->layers) {
         const size_t px = (size_t)B * l.H * l.W;
@@ -260,8 +321,8 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         chk(ualloc(u, &l.bn, l.cout));
         chk(ualloc(u, &l.bsums, l.cout));
         stats_cap = std::max(stats_cap, px / (kTH * kTW) * l.cout);
-        bn_cap = std::max(bn_cap, (px / 1024 + 1) * l.cout);
-        w_cap = std::max(w_cap, (size_t)600 * l.cout * 9 * l.cin);
+        bn_cap = std::max(bn_cap, (size_t)4 * u->nsm * l.cout);   // bn_pix_per_cta keeps the slabs at most 4 per SM
+        w_cap = std::max(w_cap, (size_t)wgrad_geom(u, l, B).chunks * l.cout * 9 * l.cin);
     }
     u->pooled.assign(L, nullptr);
     u->upped.assign(L, nullptr);
@@ -280,7 +341,7 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     u->stats_cap = stats_cap;
     u->bnpart_cap = bn_cap;
     u->wpart_cap = w_cap;
-    u->hpart_cap = ((size_t)B * H * W / kBlock + 1) * (2 * u->ch[0] + 2);
+    u->hpart_cap = (size_t)head_grid(u) * (2 * u->ch[0] + 2);
     chk(ualloc(u, &u->stats, stats_cap));
     chk(ualloc(u, &u->bnpart, bn_cap));
     chk(ualloc(u, &u->wpart, w_cap));
@@ -298,7 +359,6 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         chk(cudaMemset(u->grads, 0, off * 4));
         chk(cudaMemset(u->adam_m, 0, off * 4));
         chk(cudaMemset(u->adam_v, 0, off * 4));
-        chk(cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgradSmem));
     }
     if (e != cudaSuccess) {
         fmbym_unet_destroy(u);
@@ -441,7 +501,7 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
         const Layer& deep = (j == 0) ? u->layers[2 * L - 1] : u->layers[2 * L + 2 * (j - 1) + 1];
         const long long nu = (long long)n * (deep.H * 2) * (deep.W * 2) * deep.cout;
         ++u->launches;
-        k_upsample<<<blocks(nu), kBlock, 0, st>>>(deep.a, u->upped[i], n, deep.H, deep.W, deep.cout);
+        k_upsample<<<blocks(nu / 8), kBlock, 0, st>>>(deep.a, u->upped[i], n, deep.H, deep.W, deep.cout, nu / 8);
         e = conv_bn(u->layers[2 * L + 2 * j]);
         if (e == cudaSuccess) e = conv_bn(u->layers[2 * L + 2 * j + 1]);
     }
@@ -475,7 +535,7 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
     // head
     {
         const Layer& last = u->layers.back();
-        const int nb = blocks(npix), width = 2 * C0 + 2;
+        const int nb = (int)std::min<long long>(blocks(npix), head_grid(u)), width = 2 * C0 + 2;
         ++u->launches;
         switch (C0) {
             case 8: k_head_bwd<8><<<nb, kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, df_out, dg_out, last.da, u->hpart, npix); break;
@@ -484,32 +544,32 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
             default: k_head_bwd<64><<<nb, kBlock, 0, st>>>(last.a, u->params + u->head_w, u->params + u->head_b, f, g, df_out, dg_out, last.da, u->hpart, npix); break;
         }
         ++u->launches;
-        k_sum_parts<<<1, 256, 0, st>>>(u->hpart, nb, width, u->grads + u->head_w);
+        k_sum_parts<<<width, 256, 0, st>>>(u->hpart, nb, width, u->grads + u->head_w);
     }
     // one layer: BN/ReLU adjoint, weight gradient, and (unless first) dgrad into out0/out1
     auto layer_bwd = [&](Layer& l, float* out0, float* out1, int split, int acc0, int acc1) -> cudaError_t {
         const long long px = (long long)n * l.H * l.W;
-        const int C = l.cout, pix_per_cta = 1024;
+        const int C = l.cout, pix_per_cta = bn_pix_per_cta(u, px, C);
         const int nparts = (int)((px + pix_per_cta - 1) / pix_per_cta);
         u->launches += 3;
         k_bn_bwd_reduce<<<nparts, 256, 0, st>>>(l.y, l.da, l.bn, u->params + l.g_off, u->params + l.b_off, px, C,
                                                 pix_per_cta, u->bnpart);
-        k_bn_bwd_finalize<<<1, 64, 0, st>>>(u->bnpart, nparts, C, 1.f / (float)px, u->grads + l.g_off,
-                                            u->grads + l.b_off, l.bsums);
-        k_bn_bwd_dy<<<blocks(px * C), kBlock, 0, st>>>(l.y, l.da, l.bn, u->params + l.g_off, u->params + l.b_off,
-                                                       l.bsums, l.dy, px * C, C);
+        k_bn_bwd_finalize<<<C, 256, 0, st>>>(u->bnpart, nparts, C, 1.f / (float)px, u->grads + l.g_off,
+                                             u->grads + l.b_off, l.bsums);
+        k_bn_bwd_dy<<<blocks(px * C / 4), kBlock, 0, st>>>(l.y, l.da, l.bn, u->params + l.g_off,
+                                                           u->params + l.b_off, l.bsums, l.dy, px * C / 4, C);
         // weight gradient
-        const int ntiles = (int)(px / (kTH * kTW));
-        const int gy = (C + 15) / 16, gz = (l.cin + 63) / 64;
-        const int nchunks = std::max(1, std::min(ntiles, 600 / (gy * gz)));
-        const int tpc = (ntiles + nchunks - 1) / nchunks;
-        const int used = (ntiles + tpc - 1) / tpc;
+        const WgradGeom w = wgrad_geom(u, l, n);
         u->launches += 2;
-        k_wgrad<<<dim3(used, gy, gz), 256, kWgradSmem, st>>>(
-            l.dy, C, l.planes ? nullptr : l.in0, l.planes ? 0 : l.c0, l.in1, l.c1, l.planes ? f : nullptr,
-            l.planes ? g : nullptr, n, l.H, l.W, tpc, u->wpart);
+        switch (wgrad_variant(l)) {
+            case 0: wgrad_run<8, false>(l, w, n, f, g, u->wpart, st); break;
+            case 1: wgrad_run<16, false>(l, w, n, f, g, u->wpart, st); break;
+            case 2: wgrad_run<32, false>(l, w, n, f, g, u->wpart, st); break;
+            case 3: wgrad_run<64, false>(l, w, n, f, g, u->wpart, st); break;
+            default: wgrad_run<8, true>(l, w, n, f, g, u->wpart, st); break;
+        }
         const int total = C * 9 * l.cin;
-        k_wgrad_reduce<<<blocks(total), kBlock, 0, st>>>(u->wpart, used, C, l.cin, u->grads + l.w_off);
+        k_wgrad_reduce<<<(total + 31) / 32, 256, 0, st>>>(u->wpart, w.used, C, l.cin, u->grads + l.w_off);
         cudaError_t r = cudaGetLastError();
         if (r != cudaSuccess || !out0) return r;
         return conv_dispatch(u, l, n, true, st, out0, out1, split, acc0, acc1, nullptr);
@@ -527,7 +587,7 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         Layer& deep = (j == 0) ? u->layers[2 * L - 1] : u->layers[2 * L + 2 * (j - 1) + 1];
         const long long nl = (long long)n * deep.H * deep.W * deep.cout;
         ++u->launches;
-        k_upsample_bwd<<<blocks(nl), kBlock, 0, st>>>(u->dup[i], deep.da, n, deep.H, deep.W, deep.cout);
+        k_upsample_bwd<<<blocks(nl / 4), kBlock, 0, st>>>(u->dup[i], deep.da, n, deep.H, deep.W, deep.cout, nl / 4);
         e = cudaGetLastError();
     }
     // encoder, deepest first

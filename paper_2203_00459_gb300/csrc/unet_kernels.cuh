@@ -213,40 +213,39 @@ inline size_t conv_smem(int cout, int cinp) {
 // BatchNorm
 // ---------------------------------------------------------------------------------------------
 
-// Combines the per-CTA (mean, M2) partials of one channel (equal counts, fixed-order Chan
-// updates), updates the running statistics (momentum 0.1, unbiased variance) and writes
+// Combines the per-CTA (mean, M2) partials of one channel, all over the same count m: the batch
+// mean is the mean of the CTA means and M2 = sum M2_i + m sum (mean_i - mean)^2 (two passes, each a
+// fixed-order sum).  Updates the running statistics (momentum 0.1, unbiased variance) and writes
 // bn[c] = (mean, 1/sqrt(var + eps)) for the batch statistics.  One block per channel.
 __global__ void __launch_bounds__(256) k_bn_finalize(const float2* __restrict__ stats, int ncta, int C,
                                                      float cnt_per_cta, float* __restrict__ run_mean,
                                                      float* __restrict__ run_var, float2* __restrict__ bn) {
-    __shared__ double sn[256], sm[256], sq[256];
+    __shared__ double r[256];
     const int c = blockIdx.x;
-    double n = 0.0, mu = 0.0, m2 = 0.0;
-    for (int i = threadIdx.x; i < ncta; i += 256) {
-        const float2 s = stats[(size_t)i * C + c];
-        const double nb = cnt_per_cta, d = (double)s.x - mu, tot = n + nb;
-        mu += d * nb / tot;
-        m2 += (double)s.y + d * d * n * nb / tot;
-        n = tot;
-    }
-    sn[threadIdx.x] = n;
-    sm[threadIdx.x] = mu;
-    sq[threadIdx.x] = m2;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            const double na = sn[threadIdx.x], nb = sn[threadIdx.x + o], tot = na + nb;
-            if (nb > 0) {
-                const double d = sm[threadIdx.x + o] - sm[threadIdx.x];
-                sm[threadIdx.x] += d * nb / tot;
-                sq[threadIdx.x] += sq[threadIdx.x + o] + d * d * na * nb / tot;
-                sn[threadIdx.x] = tot;
-            }
-        }
+    auto block_sum = [&](double v) {
+        r[threadIdx.x] = v;
         __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
+            __syncthreads();
+        }
+        const double t = r[0];
+        __syncthreads();
+        return t;
+    };
+    double s = 0.0;
+    for (int i = threadIdx.x; i < ncta; i += 256) s += (double)stats[(size_t)i * C + c].x;
+    const double mean = block_sum(s) / ncta;
+    double q = 0.0, e = 0.0;
+    for (int i = threadIdx.x; i < ncta; i += 256) {
+        const float2 v = stats[(size_t)i * C + c];
+        const double d = (double)v.x - mean;
+        q += (double)v.y;
+        e += d * d;
     }
+    const double m2 = block_sum(q) + (double)cnt_per_cta * block_sum(e);
     if (threadIdx.x == 0) {
-        const double N = sn[0], mean = sm[0], var = sq[0] / N;
+        const double N = (double)cnt_per_cta * ncta, var = m2 / N;
         run_mean[c] = (float)((1.0 - kMomentum) * run_mean[c] + kMomentum * mean);
         run_var[c] = (float)((1.0 - kMomentum) * run_var[c] + kMomentum * var * N / (N > 1 ? N - 1 : 1));
         bn[c] = make_float2((float)mean, (float)(1.0 / sqrt(var + kEps)));
@@ -284,73 +283,115 @@ __global__ void k_bn_relu(const float* __restrict__ y, const float2* __restrict_
 }
 
 // Adjoint of a = relu(xhat gamma + beta) with batch statistics, part 1: per-CTA partial sums over a
-// slab of pixels of dpre = da [pre > 0] and dpre xhat per channel (fixed order).  C <= 64.
+// slab of pixel_per_cta pixels of dpre = da [pre > 0] and dpre xhat per channel.  A thread takes
+// four channels (float4) of every (256 / (C / 4))-th pixel; the CTA adds its rows in order.
+// C in {8, 16, 32, 64}; pix_per_cta a multiple of 256 / (C / 4).
 __global__ void __launch_bounds__(256) k_bn_bwd_reduce(const float* __restrict__ y, const float* __restrict__ da,
                                                        const float2* __restrict__ bn,
                                                        const float* __restrict__ gamma,
                                                        const float* __restrict__ beta, long long npix, int C,
                                                        int pix_per_cta, float2* __restrict__ part) {
-    __shared__ float s1[256], s2[256];
-    const int lanes = 256 / C * C;  // threads used: a multiple of C
-    const int c = threadIdx.x % C, r = threadIdx.x / C, rows = 256 / C;
-    float a1 = 0.f, a2 = 0.f;
-    if ((int)threadIdx.x < lanes) {
-        const float2 s = bn[c];
-        const float gm = gamma[c], bt = beta[c];
-        const long long p0 = (long long)blockIdx.x * pix_per_cta;
-        for (long long p = p0 + r; p < p0 + pix_per_cta && p < npix; p += rows) {
-            const float yv = y[p * C + c];
-            const float xh = (yv - s.x) * s.y;
-            const float pre = fmaf(xh, gm, bt);
-            const float dp = pre > 0.f ? da[p * C + c] : 0.f;
-            a1 += dp;
-            a2 += dp * xh;
+    __shared__ float4 s1[256], s2[256];
+    const int q = C / 4, rows = 256 / q;
+    const int cq = threadIdx.x % q, r = threadIdx.x / q;
+    float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), a2 = a1;
+    float mu[4], is[4], gm[4], bt[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 st = bn[4 * cq + j];
+        mu[j] = st.x;
+        is[j] = st.y;
+        gm[j] = gamma[4 * cq + j];
+        bt[j] = beta[4 * cq + j];
+    }
+    const long long p0 = (long long)blockIdx.x * pix_per_cta;
+    const long long p1 = min(p0 + pix_per_cta, npix);
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    const float4* d4 = reinterpret_cast<const float4*>(da);
+#pragma unroll 4
+    for (long long p = p0 + r; p < p1; p += rows) {
+        const float4 yv = y4[p * q + cq], dv = d4[p * q + cq];
+        const float yy[4] = {yv.x, yv.y, yv.z, yv.w}, dd[4] = {dv.x, dv.y, dv.z, dv.w};
+        float o1[4], o2[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float xh = (yy[j] - mu[j]) * is[j];
+            const float dp = fmaf(xh, gm[j], bt[j]) > 0.f ? dd[j] : 0.f;
+            o1[j] = dp;
+            o2[j] = dp * xh;
         }
+        a1.x += o1[0]; a1.y += o1[1]; a1.z += o1[2]; a1.w += o1[3];
+        a2.x += o2[0]; a2.y += o2[1]; a2.z += o2[2]; a2.w += o2[3];
     }
     s1[threadIdx.x] = a1;
     s2[threadIdx.x] = a2;
     __syncthreads();
     if ((int)threadIdx.x < C) {
+        const int c = threadIdx.x, qq = c / 4, j = c % 4;
+        const float* f1 = reinterpret_cast<const float*>(s1);
+        const float* f2 = reinterpret_cast<const float*>(s2);
         float t1 = 0.f, t2 = 0.f;
         for (int k = 0; k < rows; ++k) {
-            t1 += s1[k * C + threadIdx.x];
-            t2 += s2[k * C + threadIdx.x];
+            t1 += f1[(k * q + qq) * 4 + j];
+            t2 += f2[(k * q + qq) * 4 + j];
         }
-        part[(size_t)blockIdx.x * C + threadIdx.x] = make_float2(t1, t2);
+        part[(size_t)blockIdx.x * C + c] = make_float2(t1, t2);
     }
 }
 
-// Part 2: sums the partials in order -> d beta = sum dpre, d gamma = sum dpre xhat (written to the
-// gradient array) and the per-channel means used by the dy kernel: sums[c] = (mean dpre, mean dpre xhat).
-__global__ void k_bn_bwd_finalize(const float2* __restrict__ part, int nparts, int C, float inv_n,
-                                  float* __restrict__ dgamma, float* __restrict__ dbeta, float2* __restrict__ sums) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+// Part 2, one block per channel: the partials summed in a fixed order -> d beta = sum dpre,
+// d gamma = sum dpre xhat (written to the gradient array) and the means used by the dy kernel,
+// sums[c] = (mean dpre, mean dpre xhat).
+__global__ void __launch_bounds__(256) k_bn_bwd_finalize(const float2* __restrict__ part, int nparts, int C,
+                                                         float inv_n, float* __restrict__ dgamma,
+                                                         float* __restrict__ dbeta, float2* __restrict__ sums) {
+    __shared__ double r1[256], r2[256];
+    const int c = blockIdx.x;
     double t1 = 0.0, t2 = 0.0;
-    for (int i = 0; i < nparts; ++i) {
+    for (int i = threadIdx.x; i < nparts; i += 256) {
         const float2 v = part[(size_t)i * C + c];
         t1 += v.x;
         t2 += v.y;
     }
-    dbeta[c] = (float)t1;
-    dgamma[c] = (float)t2;
-    sums[c] = make_float2((float)(t1 * inv_n), (float)(t2 * inv_n));
+    r1[threadIdx.x] = t1;
+    r2[threadIdx.x] = t2;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            r1[threadIdx.x] += r1[threadIdx.x + o];
+            r2[threadIdx.x] += r2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        dbeta[c] = (float)r1[0];
+        dgamma[c] = (float)r2[0];
+        sums[c] = make_float2((float)(r1[0] * inv_n), (float)(r2[0] * inv_n));
+    }
 }
 
 // Part 3: dy = gamma invstd (dpre - mean dpre - xhat mean(dpre xhat)), rounded to bf16 for the
-// tensor-core dgrad and wgrad.
+// tensor-core dgrad and wgrad.  Four channels per thread; n4 = pixels * C / 4.
 __global__ void k_bn_bwd_dy(const float* __restrict__ y, const float* __restrict__ da, const float2* __restrict__ bn,
                             const float* __restrict__ gamma, const float* __restrict__ beta,
-                            const float2* __restrict__ sums, bf16* __restrict__ dy, long long n, int C) {
+                            const float2* __restrict__ sums, bf16* __restrict__ dy, long long n4, int C) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = (int)(i % C);
-    const float2 s = bn[c];
-    const float xh = (y[i] - s.x) * s.y;
-    const float pre = fmaf(xh, gamma[c], beta[c]);
-    const float dp = pre > 0.f ? da[i] : 0.f;
-    const float2 m = sums[c];
-    dy[i] = __float2bfloat16_rn(gamma[c] * s.y * (dp - m.x - xh * m.y));
+    if (i >= n4) return;
+    const int c0 = (int)((i * 4) % C);
+    const float4 yv = reinterpret_cast<const float4*>(y)[i], dv = reinterpret_cast<const float4*>(da)[i];
+    const float yy[4] = {yv.x, yv.y, yv.z, yv.w}, dd[4] = {dv.x, dv.y, dv.z, dv.w};
+    bf16 o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = c0 + j;
+        const float2 s = bn[c];
+        const float gm = gamma[c];
+        const float xh = (yy[j] - s.x) * s.y;
+        const float dp = fmaf(xh, gm, beta[c]) > 0.f ? dd[j] : 0.f;
+        const float2 m = sums[c];
+        o[j] = __float2bfloat16_rn(gm * s.y * (dp - m.x - xh * m.y));
+    }
+    reinterpret_cast<uint2*>(dy)[i] = make_uint2(pack2(o[0], o[1]), pack2(o[2], o[3]));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -414,12 +455,14 @@ __device__ __forceinline__ void up_src(int o, int n, int& i0, int& i1, float& l0
     l0 = 1.f - l1;
 }
 
-__global__ void k_upsample(const bf16* __restrict__ a, bf16* __restrict__ u, int B, int h, int w, int C) {
+// Eight channels (16 bytes) of one output pixel per thread; n8 = B * 2h * 2w * C / 8.
+__global__ void k_upsample(const bf16* __restrict__ a, bf16* __restrict__ u, int B, int h, int w, int C,
+                           long long n8) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int H = 2 * h, W = 2 * w;
-    if (i >= (long long)B * H * W * C) return;
-    const int c = (int)(i % C);
-    long long r = i / C;
+    if (i >= n8) return;
+    const int H = 2 * h, W = 2 * w, q = C / 8;
+    const int c = (int)(i % q) * 8;
+    long long r = i / q;
     const int X = (int)(r % W);
     r /= W;
     const int Y = (int)(r % H);
@@ -429,9 +472,26 @@ __global__ void k_upsample(const bf16* __restrict__ a, bf16* __restrict__ u, int
     up_src(Y, h, y0, y1, ly0, ly1);
     up_src(X, w, x0, x1, lx0, lx1);
     const bf16* base = a + (size_t)b * h * w * C + c;
-    auto at = [&](int yy, int xx) { return __bfloat162float(base[((size_t)yy * w + xx) * C]); };
-    const float v = ly0 * (lx0 * at(y0, x0) + lx1 * at(y0, x1)) + ly1 * (lx0 * at(y1, x0) + lx1 * at(y1, x1));
-    u[i] = __float2bfloat16_rn(v);
+    const uint4 v00 = *reinterpret_cast<const uint4*>(base + ((size_t)y0 * w + x0) * C);
+    const uint4 v01 = *reinterpret_cast<const uint4*>(base + ((size_t)y0 * w + x1) * C);
+    const uint4 v10 = *reinterpret_cast<const uint4*>(base + ((size_t)y1 * w + x0) * C);
+    const uint4 v11 = *reinterpret_cast<const uint4*>(base + ((size_t)y1 * w + x1) * C);
+    const uint32_t* p00 = &v00.x;
+    const uint32_t* p01 = &v01.x;
+    const uint32_t* p10 = &v10.x;
+    const uint32_t* p11 = &v11.x;
+    uint32_t o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float res[2];
+#pragma unroll
+        for (int hlf = 0; hlf < 2; ++hlf) {
+            auto f = [&](uint32_t wd) { return __uint_as_float(hlf ? (wd & 0xffff0000u) : (wd << 16)); };
+            res[hlf] = ly0 * (lx0 * f(p00[k]) + lx1 * f(p01[k])) + ly1 * (lx0 * f(p10[k]) + lx1 * f(p11[k]));
+        }
+        o[k] = pack2(__float2bfloat16_rn(res[0]), __float2bfloat16_rn(res[1]));
+    }
+    *reinterpret_cast<uint4*>(u + i * 8) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 // Weight that the forward assigns from input index k to output index o (both taps if clamped).
@@ -442,29 +502,45 @@ __device__ __forceinline__ float up_w(int o, int k, int n) {
     return (i0 == k ? l0 : 0.f) + (i1 == k ? l1 : 0.f);
 }
 
-// Transpose of the upsampling in gather form: d a[k] = sum over outputs o in [2k-2, 2k+2] of the
-// forward weights times d u[o]; written (not added) to da.
-__global__ void k_upsample_bwd(const float* __restrict__ du, float* __restrict__ da, int B, int h, int w, int C) {
+// Transpose of the upsampling in gather form: d a[k] = sum over the outputs o in [2k-1, 2k+2] (the
+// only ones whose two taps can reach k) of the forward weights times d u[o]; written (not added)
+// to da.  Four channels per thread; n4 = B * h * w * C / 4.
+__global__ void k_upsample_bwd(const float* __restrict__ du, float* __restrict__ da, int B, int h, int w, int C,
+                               long long n4) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int H = 2 * h, W = 2 * w;
-    if (i >= (long long)B * h * w * C) return;
-    const int c = (int)(i % C);
-    long long r = i / C;
+    if (i >= n4) return;
+    const int H = 2 * h, W = 2 * w, q = C / 4;
+    const int c = (int)(i % q) * 4;
+    long long r = i / q;
     const int x = (int)(r % w);
     r /= w;
     const int y = (int)(r % h);
     const int b = (int)(r / h);
-    float s = 0.f;
-    for (int Y = max(0, 2 * y - 2); Y <= min(H - 1, 2 * y + 2); ++Y) {
-        const float wy = up_w(Y, y, h);
-        if (wy == 0.f) continue;
-        for (int X = max(0, 2 * x - 2); X <= min(W - 1, 2 * x + 2); ++X) {
-            const float wx = up_w(X, x, w);
-            if (wx == 0.f) continue;
-            s += wy * wx * du[(((size_t)b * H + Y) * W + X) * C + c];
+    float wy[4], wx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int Y = 2 * y - 1 + k, X = 2 * x - 1 + k;
+        wy[k] = (Y >= 0 && Y < H) ? up_w(Y, y, h) : 0.f;
+        wx[k] = (X >= 0 && X < W) ? up_w(X, x, w) : 0.f;
+    }
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int ky = 0; ky < 4; ++ky) {
+        if (wy[ky] == 0.f) continue;
+        const int Y = 2 * y - 1 + ky;
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) {
+            if (wx[kx] == 0.f) continue;
+            const int X = 2 * x - 1 + kx;
+            const float wt = wy[ky] * wx[kx];
+            const float4 v = *reinterpret_cast<const float4*>(du + (((size_t)b * H + Y) * W + X) * C + c);
+            s.x += wt * v.x;
+            s.y += wt * v.y;
+            s.z += wt * v.z;
+            s.w += wt * v.w;
         }
     }
-    da[i] = s;
+    *reinterpret_cast<float4*>(da + i * 4) = s;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -495,7 +571,8 @@ __global__ void k_head(const bf16* __restrict__ a, const float* __restrict__ hw,
 }
 
 // d z_o = d(out_o) scan_o m_o (1 - m_o); d a[c] = sum_o W[o][c] d z_o; per-block partial sums of
-// d W[o][c] = sum d z_o a[c] and d b[o] = sum d z_o (2 C + 2 values, fixed order).
+// d W[o][c] = sum d z_o a[c] and d b[o] = sum d z_o (2 C + 2 values, fixed order).  Grid-stride
+// over pixels, so the number of partials is the grid size.
 template <int C>
 __global__ void __launch_bounds__(256) k_head_bwd(const bf16* __restrict__ a, const float* __restrict__ hw,
                                                   const float* __restrict__ hb, const float* __restrict__ f,
@@ -503,31 +580,48 @@ __global__ void __launch_bounds__(256) k_head_bwd(const bf16* __restrict__ a, co
                                                   const float* __restrict__ dgo, float* __restrict__ da,
                                                   float* __restrict__ part, long long npix) {
     __shared__ float red[8][2 * C + 2];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float w0[C], w1[C];   // the bf16-rounded head weights
     float loc[2 * C + 2];
 #pragma unroll
     for (int k = 0; k < 2 * C + 2; ++k) loc[k] = 0.f;
-    if (i < npix) {
-        float av[C], w0[C], w1[C];
+    if ((int)threadIdx.x < C) {
+        w0[threadIdx.x] = __bfloat162float(__float2bfloat16_rn(hw[threadIdx.x]));
+        w1[threadIdx.x] = __bfloat162float(__float2bfloat16_rn(hw[C + threadIdx.x]));
+    }
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix;
+         i += (long long)gridDim.x * blockDim.x) {
+        float av[C];
         float z0 = hb[0], z1 = hb[1];
 #pragma unroll
+        for (int c = 0; c < C; c += 8) {
+            const uint4 v = *reinterpret_cast<const uint4*>(a + i * C + c);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                av[c + 2 * k] = __uint_as_float(w[k] << 16);
+                av[c + 2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+            }
+        }
+#pragma unroll
         for (int c = 0; c < C; ++c) {
-            av[c] = __bfloat162float(a[i * C + c]);
-            w0[c] = __bfloat162float(__float2bfloat16_rn(hw[c]));
-            w1[c] = __bfloat162float(__float2bfloat16_rn(hw[C + c]));
             z0 = fmaf(w0[c], av[c], z0);
             z1 = fmaf(w1[c], av[c], z1);
         }
         const float m0 = 1.f / (1.f + expf(-z0)), m1 = 1.f / (1.f + expf(-z1));
         const float d0 = dfo[i] * f[i] * m0 * (1.f - m0), d1 = dgo[i] * g[i] * m1 * (1.f - m1);
 #pragma unroll
+        for (int c = 0; c < C; c += 4)
+            *reinterpret_cast<float4*>(da + i * C + c) =
+                make_float4(w0[c] * d0 + w1[c] * d1, w0[c + 1] * d0 + w1[c + 1] * d1, w0[c + 2] * d0 + w1[c + 2] * d1,
+                            w0[c + 3] * d0 + w1[c + 3] * d1);
+#pragma unroll
         for (int c = 0; c < C; ++c) {
-            da[i * C + c] = w0[c] * d0 + w1[c] * d1;
-            loc[c] = d0 * av[c];
-            loc[C + c] = d1 * av[c];
+            loc[c] = fmaf(d0, av[c], loc[c]);
+            loc[C + c] = fmaf(d1, av[c], loc[C + c]);
         }
-        loc[2 * C] = d0;
-        loc[2 * C + 1] = d1;
+        loc[2 * C] += d0;
+        loc[2 * C + 1] += d1;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -545,124 +639,200 @@ __global__ void __launch_bounds__(256) k_head_bwd(const bf16* __restrict__ a, co
     }
 }
 
-// Sums per-block partials column by column in a fixed order into out (added to out if acc).
-__global__ void k_sum_parts(const float* __restrict__ part, int nparts, int width, float* __restrict__ out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= width) return;
+// Sums per-block partials column by column into out, one block per column: every thread adds a
+// fixed stride of partials, then a fixed-order tree.
+__global__ void __launch_bounds__(256) k_sum_parts(const float* __restrict__ part, int nparts, int width,
+                                                   float* __restrict__ out) {
+    __shared__ double r[256];
+    const int k = blockIdx.x;
     double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += part[(size_t)i * width + k];
-    out[k] = (float)s;
+    for (int i = threadIdx.x; i < nparts; i += 256) s += part[(size_t)i * width + k];
+    r[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = (float)r[0];
 }
 
 // ---------------------------------------------------------------------------------------------
 // weight gradient of a 3x3 convolution
 // ---------------------------------------------------------------------------------------------
 //
-// dW[co][tap][ci] = sum over pixels of dy[p][co] in[p + tap][ci], an implicit GEMM with M = 16
-// output channels, N = 8 input channels, K = 16 pixels of a tile row.  A CTA owns one block of 16
-// output channels and up to 64 input channels (one block of 8 per warp, all 9 taps in registers)
-// and walks a chunk of 8 x 32 pixel tiles; its partial dW goes to part[chunk] and k_wgrad_reduce
-// sums the chunks in order.  Tiles are stored channel-major in shared memory.
+// dW[co][tap][ci] = sum over pixels p of dy[p][co] in[p + tap][ci]: an implicit GEMM with
+// M = 16 output channels, N = 8 input channels, K = 16 pixels of one tile row, on
+// mma.sync.m16n8k16.  A CTA owns 16 output channels and CIB input channels and walks a chunk of
+// 8 x 32 pixel tiles.  Both operands are staged pixel-major, one 16-byte row per pixel and group
+// of 8 channels -- exactly the NHWC bytes -- by cp.async (double-buffered, zero-filled outside the
+// image), and ldmatrix.trans turns those rows into the channel-by-pixel fragments, so a 3x3 tap
+// is only a shifted row address.  Warps split into CIB / 8 channel groups times 64 / CIB row
+// groups; the row groups' partial sums are added in a fixed order at the end and the CTA's dW
+// goes to part[chunk], which k_wgrad_reduce sums over chunks in order (bitwise deterministic).
+// Requires cout and every input channel count to be multiples of 8 (the planes of the first
+// layer are staged by plain loads instead).
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const void* row_addr) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(row_addr);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(s));
+}
+
+constexpr int kTilePx = kTH * kTW, kHaloPx = kTileH * kTileW;
+
+template <int CIB>
+__host__ __device__ constexpr size_t wgrad_buf_bytes() { return (size_t)(2 * kTilePx + (CIB / 8) * kHaloPx) * 16; }
+template <int CIB>
+__host__ __device__ constexpr size_t wgrad_smem() {
+    return 2 * wgrad_buf_bytes<CIB>() > (size_t)8 * 36 * 32 * 4 ? 2 * wgrad_buf_bytes<CIB>() : (size_t)8 * 36 * 32 * 4;
+}
+
+template <int CIB, bool PLANES>
 __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int cout, const bf16* __restrict__ in0,
                                                int c0, const bf16* __restrict__ in1, int c1,
                                                const float* __restrict__ pf, const float* __restrict__ pg, int B,
                                                int H, int W, int tiles_per_chunk, float* __restrict__ part) {
-    constexpr int DS = kTH * kTW + 8;          // channel stride of the dy tile
-    constexpr int IS = kTileH * kTileW + 4;    // channel stride of the input tile
-    extern __shared__ __align__(16) unsigned char smem_w[];
-    bf16* dys = reinterpret_cast<bf16*>(smem_w);
-    bf16* ins = dys + 16 * DS;
-    const int cin = pf ? 2 : c0 + c1;
-    const int co0 = blockIdx.y * 16, ci_base = blockIdx.z * 64;
+    constexpr int NG = CIB / 8, NRG = 8 / NG;
+    constexpr size_t BUF = wgrad_buf_bytes<CIB>();
+    extern __shared__ __align__(128) unsigned char smem_w[];
+    const int cin = PLANES ? 2 : c0 + c1;
+    const int co0 = blockIdx.y * 16, ci_base = blockIdx.z * CIB;
+    const int ngr = PLANES ? 1 : min(NG, (cin - ci_base) / 8);   // channel groups present
+    const int cog = min(2, (cout - co0) / 8);                     // output groups present (1 or 2)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const int ci0 = ci_base + warp * 8;
+    const int wc = warp % NG, wr = warp / NG;
+    const int tiles_x = W / kTW, tiles_y = H / kTH, ntiles = B * tiles_x * tiles_y;
+    const int first = blockIdx.x * tiles_per_chunk, n = min(tiles_per_chunk, ntiles - first);
+
+    if (cog == 1)  // the upper 8 rows of the A operand stay zero in both buffers
+        for (int i = tid; i < kTilePx; i += 256)
+#pragma unroll
+            for (int bsel = 0; bsel < 2; ++bsel)
+                *reinterpret_cast<uint4*>(smem_w + bsel * BUF + (size_t)(kTilePx + i) * 16) = make_uint4(0, 0, 0, 0);
+
+    auto stage = [&](int tile, int bsel) {
+        unsigned char* buf = smem_w + bsel * BUF;
+        const int b = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
+        const int ty0 = (rem / tiles_x) * kTH, tx0 = (rem % tiles_x) * kTW;
+        for (int i = tid; i < cog * kTilePx; i += 256) {
+            const int grp = i / kTilePx, pix = i % kTilePx;
+            const size_t p = ((size_t)b * H + ty0 + pix / kTW) * W + tx0 + pix % kTW;
+            cp_async16(buf + (size_t)(grp * kTilePx + pix) * 16, dy + p * cout + co0 + grp * 8, true);
+        }
+        unsigned char* ins = buf + 2 * kTilePx * 16;
+        if constexpr (PLANES) {
+            for (int pix = tid; pix < kHaloPx; pix += 256) {
+                const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (y >= 0 && y < H && x >= 0 && x < W) {
+                    const size_t p = ((size_t)b * H + y) * W + x;
+                    v.x = pack2(__float2bfloat16_rn(pf[p]), __float2bfloat16_rn(pg[p]));
+                }
+                *reinterpret_cast<uint4*>(ins + (size_t)pix * 16) = v;
+            }
+        } else {
+            for (int i = tid; i < ngr * kHaloPx; i += 256) {
+                const int grp = i / kHaloPx, pix = i % kHaloPx;
+                const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
+                const bool inside = y >= 0 && y < H && x >= 0 && x < W;
+                const size_t p = inside ? ((size_t)b * H + y) * W + x : 0;
+                const int c = ci_base + grp * 8;
+                const bf16* src = c < c0 ? in0 + p * c0 + c : in1 + p * c1 + (c - c0);
+                cp_async16(ins + (size_t)(grp * kHaloPx + pix) * 16, src, inside);
+            }
+        }
+    };
+
     float acc[9][4];
 #pragma unroll
     for (int k = 0; k < 9; ++k)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[k][j] = 0.f;
-    const int tiles_x = W / kTW, tiles_y = H / kTH, ntiles = B * tiles_x * tiles_y;
-    const uint16_t* dys16 = reinterpret_cast<const uint16_t*>(dys);
-    const uint16_t* ins16 = reinterpret_cast<const uint16_t*>(ins);
-    for (int tt = 0; tt < tiles_per_chunk; ++tt) {
-        const int tile = blockIdx.x * tiles_per_chunk + tt;
-        if (tile >= ntiles) break;
-        const int b = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
-        const int ty0 = (rem / tiles_x) * kTH, tx0 = (rem % tiles_x) * kTW;
+
+    // ldmatrix row addresses: A matrices (out group lane/8 & 1, pixels + 8 (lane/8 >> 1)); B: pixel lane
+    const int a_row = ((lane >> 3) & 1) * kTilePx + ((lane >> 4) << 3) + (lane & 7);
+    stage(first, 0);
+    cp_async_commit();
+    for (int it = 0; it < n; ++it) {
+        if (it + 1 < n) stage(first + it + 1, (it + 1) & 1);
+        cp_async_commit();
+        cp_async_wait1();
         __syncthreads();
-        for (int idx = tid; idx < 16 * kTH * kTW; idx += 256) {
-            const int co = idx % 16, pix = idx / 16, y = ty0 + pix / kTW, x = tx0 + pix % kTW;
-            bf16 v = __float2bfloat16_rn(0.f);
-            if (co0 + co < cout) v = dy[(((size_t)b * H + y) * W + x) * cout + co0 + co];
-            dys[co * DS + pix] = v;
-        }
-        for (int idx = tid; idx < 64 * kTileH * kTileW; idx += 256) {
-            const int ci = idx % 64, pix = idx / 64, y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
-            const int c = ci_base + ci;
-            bf16 v = __float2bfloat16_rn(0.f);
-            if (c < cin && y >= 0 && y < H && x >= 0 && x < W) {
-                const size_t p = ((size_t)b * H + y) * W + x;
-                if (pf) v = __float2bfloat16_rn(c == 0 ? pf[p] : pg[p]);
-                else if (c < c0) v = in0[p * c0 + c];
-                else v = in1[p * c1 + (c - c0)];
-            }
-            ins[ci * IS + pix] = v;
-        }
-        __syncthreads();
-        if (ci0 < cin) {
-            for (int row = 0; row < kTH; ++row) {
-                for (int xs = 0; xs < kTW; xs += 16) {
-                    const int p0 = row * kTW + xs;
-                    uint32_t a[4];
-                    const uint32_t* d32 = reinterpret_cast<const uint32_t*>(dys16 + g * DS + p0);
-                    const uint32_t* d32b = reinterpret_cast<const uint32_t*>(dys16 + (g + 8) * DS + p0);
-                    a[0] = d32[t];
-                    a[1] = d32b[t];
-                    a[2] = d32[t + 4];
-                    a[3] = d32b[t + 4];
+        const unsigned char* buf = smem_w + (it & 1) * BUF;
+        const unsigned char* ins = buf + 2 * kTilePx * 16 + (size_t)wc * kHaloPx * 16;
+        if (wc < ngr) {
+            for (int row = wr; row < kTH; row += NRG) {
+                uint32_t a0[4], a1[4];
+                ldsm_x4_trans(a0, buf + (size_t)(a_row + row * kTW) * 16);
+                ldsm_x4_trans(a1, buf + (size_t)(a_row + row * kTW + 16) * 16);
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int ky = tap / 3, kx = tap % 3;
-                        const uint16_t* ib = ins16 + (warp * 8 + g) * IS + (row + ky) * kTileW + xs + kx;
-                        uint32_t bb[2];
-                        bb[0] = (uint32_t)ib[2 * t] | ((uint32_t)ib[2 * t + 1] << 16);
-                        bb[1] = (uint32_t)ib[2 * t + 8] | ((uint32_t)ib[2 * t + 9] << 16);
-                        mma16816(acc[tap], a, bb);
-                    }
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap % 3;
+                    uint32_t bb[4];
+                    ldsm_x4_trans(bb, ins + (size_t)((row + ky) * kTileW + kx + lane) * 16);
+                    mma16816(acc[tap], a0, bb);
+                    mma16816(acc[tap], a1, bb + 2);
                 }
             }
         }
+        __syncthreads();
     }
-    // acc[tap]: rows co0 + g (+8), columns ci0 + 2t (+1)
-    if (ci0 < cin) {
-        float* o = part + (size_t)blockIdx.x * cout * 9 * cin;
+    // acc[tap][2 h + j]: output channel co0 + g + 8 h, input channel ci0 + 2 t + j.  With several
+    // row groups, their accumulators meet in shared memory and are added in row-group order.
+    float* o = part + (size_t)blockIdx.x * cout * 9 * cin;
+    if constexpr (NRG == 1) {
+        if (wc < ngr) {
+            const int ci0 = ci_base + wc * 8;
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
+            for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int co = co0 + g + 8 * h;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int ci = ci0 + 2 * t + j;
-                    if (co < cout && ci < cin) o[((size_t)co * 9 + tap) * cin + ci] = acc[tap][2 * h + j];
+                for (int k = 0; k < 4; ++k) {
+                    const int co = co0 + g + 8 * (k >> 1), ci = ci0 + 2 * t + (k & 1);
+                    if (co < cout && ci < cin) o[((size_t)co * 9 + tap) * cin + ci] = acc[tap][k];
                 }
-            }
+        }
+    } else {
+        float* red = reinterpret_cast<float*>(smem_w);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) red[(warp * 36 + k) * 32 + lane] = acc[k / 4][k % 4];
+        __syncthreads();
+        for (int e = tid; e < ngr * 36 * 32; e += 256) {
+            const int gi = e / (36 * 32), k = (e / 32) % 36, ln = e % 32;
+            float sum = 0.f;
+            for (int r = 0; r < NRG; ++r) sum += red[((r * NG + gi) * 36 + k) * 32 + ln];
+            const int co = co0 + (ln >> 2) + 8 * ((k & 3) >> 1), ci = ci_base + gi * 8 + 2 * (ln & 3) + (k & 1);
+            if (co < cout && ci < cin) o[((size_t)co * 9 + (k >> 2)) * cin + ci] = sum;
         }
     }
 }
 
-constexpr size_t kWgradSmem = (size_t)(16 * (kTH * kTW + 8) + 64 * (kTileH * kTileW + 4)) * sizeof(bf16);
-
-// dW (PyTorch layout [co][ci][3][3]) = sum over chunks of part[chunk][co][tap][ci], fixed order.
-__global__ void k_wgrad_reduce(const float* __restrict__ part, int nchunks, int cout, int cin,
-                               float* __restrict__ dw) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// dW (PyTorch layout [co][ci][3][3]) = sum over chunks of part[chunk][co][tap][ci] in chunk order.
+// A block covers 32 consecutive entries; its 8 warps take every 8th chunk and are added in order.
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ part, int nchunks, int cout,
+                                                      int cin, float* __restrict__ dw) {
+    __shared__ float red[8][33];
     const int total = cout * 9 * cin;
-    if (k >= total) return;
-    const int ci = k % cin, tap = (k / cin) % 9, co = k / (9 * cin);
-    float s = 0.f;
-    for (int i = 0; i < nchunks; ++i) s += part[(size_t)i * total + k];
-    dw[((size_t)co * cin + ci) * 9 + tap] = s;
+    const int k = blockIdx.x * 32 + (threadIdx.x & 31), s = threadIdx.x >> 5;
+    float acc = 0.f;
+    if (k < total)
+        for (int i = s; i < nchunks; i += 8) acc += part[(size_t)i * total + k];
+    red[s][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32 && k < total) {
+        float r = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) r += red[w][threadIdx.x];
+        const int ci = k % cin, tap = (k / cin) % 9, co = k / (9 * cin);
+        dw[((size_t)co * cin + ci) * 9 + tap] = r;
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
