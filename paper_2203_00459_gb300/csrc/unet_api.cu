@@ -16,13 +16,15 @@ using namespace fmbym::unet;
 
 namespace {
 
-int round16(int c) { return (c + 15) / 16 * 16; }
+int round8(int c) { return (c + 7) / 8 * 8; }
 
 // One 3x3 conv + BN + ReLU layer and its buffers.
 struct Layer {
     std::string name;
     int cin, cout, H, W;       // input channels, output channels, resolution
-    int cinp, coutp;           // channels rounded up to 16
+    int cinp, coutp;           // channels rounded up to 8
+    int ns_f = 0, ns_d = 0;    // cp.async ring depth of the forward and dgrad convolutions
+    int slots_f = 0, slots_d = 0;   // their resident CTAs on the device
     long long w_off, g_off, b_off, rs_off;  // offsets in the parameter and running-stat arrays
     bf16* wf = nullptr;        // forward weights [cout][9][cinp]
     bf16* wd = nullptr;        // dgrad weights [cin][9][coutp]
@@ -94,28 +96,63 @@ cudaError_t ualloc(fmbym_unet* u, T** p, size_t count) {
 
 const int kBlock = 256;
 inline unsigned blocks(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+// 2-D grid of the row kernels: threads over one row's work items, blocks in y over the rows
+inline dim3 row_grid(int per_row, int rows) { return dim3(blocks(per_row), (unsigned)std::min(rows, 65535)); }
+
+// Ring depth and resident CTAs of a convolution with COUT outputs and G input groups: three tile
+// buffers while the CTA stays under 64 KB of shared memory, else two, else one; 0 if even one
+// does not fit.
+template <int COUT>
+cudaError_t conv_plan_t(const fmbym_unet* u, int G, int& ns, int& slots) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_conv3x3<COUT>);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const size_t cap = (size_t)optin - fa.sharedSizeBytes, wb = conv_weight_bytes(COUT, G), tb = conv_tile_bytes(G);
+    ns = wb + 3 * tb <= 64 * 1024 ? 3 : wb + 2 * tb <= cap ? 2 : wb + tb <= cap ? 1 : 0;
+    slots = 0;
+    if (!ns) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_conv3x3<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    int occ = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3x3<COUT>, 256, wb + ns * tb);
+    slots = std::max(1, occ) * u->nsm;
+    return e;
+}
+
+cudaError_t conv_plan(const fmbym_unet* u, int cout, int G, int& ns, int& slots) {
+    switch (cout) {
+        case 8: return conv_plan_t<8>(u, G, ns, slots);
+        case 16: return conv_plan_t<16>(u, G, ns, slots);
+        case 24: return conv_plan_t<24>(u, G, ns, slots);
+        case 32: return conv_plan_t<32>(u, G, ns, slots);
+        case 48: return conv_plan_t<48>(u, G, ns, slots);
+        case 64: return conv_plan_t<64>(u, G, ns, slots);
+        case 96: return conv_plan_t<96>(u, G, ns, slots);
+        case 128: return conv_plan_t<128>(u, G, ns, slots);
+        default: ns = 0; return cudaSuccess;
+    }
+}
 
 template <int COUT>
 cudaError_t conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
                         float* out1, int split, int acc0, int acc1, float2* stats) {
-    const int cinp = dgrad ? L.coutp : L.cinp;
+    const int G = (dgrad ? L.coutp : L.cinp) / 8, ns = dgrad ? L.ns_d : L.ns_f;
     const bf16* w = dgrad ? L.wd : L.wf;
-    const size_t smem = conv_smem(COUT, cinp);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3x3<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    dim3 grid(L.W / kTW, L.H / kTH, B);
+    const size_t smem = conv_weight_bytes(COUT, G) + ns * conv_tile_bytes(G);
+    const int ntiles = B * (L.H / kTH) * (L.W / kTW);
+    const int grid = std::min(ntiles, dgrad ? L.slots_d : L.slots_f);
     ++u->launches;
     if (dgrad)
-        k_conv3x3<COUT><<<grid, 256, smem, st>>>(L.dy, L.cout, nullptr, 0, nullptr, nullptr, w, cinp, out0, out1,
-                                                 split, acc0, acc1, nullptr, L.H, L.W);
+        k_conv3x3<COUT><<<grid, 256, smem, st>>>(L.dy, L.cout, nullptr, 0, nullptr, nullptr, w, G, ns, out0, out1,
+                                                 split, acc0, acc1, nullptr, B, L.H, L.W);
     else
         k_conv3x3<COUT><<<grid, 256, smem, st>>>(L.in0, L.c0, L.in1, L.c1, L.planes ? (const float*)L.in0 : nullptr,
-                                                 L.planes ? (const float*)L.in1 : nullptr, w, cinp, out0, out1,
-                                                 split, acc0, acc1, stats, L.H, L.W);
+                                                 L.planes ? (const float*)L.in1 : nullptr, w, G, ns, out0, out1,
+                                                 split, acc0, acc1, stats, B, L.H, L.W);
     return cudaGetLastError();
 }
 
@@ -261,8 +298,8 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         l.cout = cout;
         l.H = H >> lvl;
         l.W = W >> lvl;
-        l.cinp = round16(cin);
-        l.coutp = round16(cout);
+        l.cinp = round8(cin);
+        l.coutp = round8(cout);
         l.w_off = off;
         off += (long long)cout * cin * 9;
         l.g_off = off;
@@ -310,6 +347,7 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     chk(wgrad_prepare<64, false>(u, 3));
     chk(wgrad_prepare<8, true>(u, 4));
     size_t stats_cap = 0, bn_cap = 0, w_cap = 0;
+    bool too_big = false;
     for (Layer& l : u->layers) {
         const size_t px = (size_t)B * l.H * l.W;
         chk(ualloc(u, &l.wf, (size_t)l.cout * 9 * l.cinp));
@@ -320,9 +358,12 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         chk(ualloc(u, &l.dy, px * l.cout));
         chk(ualloc(u, &l.bn, l.cout));
         chk(ualloc(u, &l.bsums, l.cout));
-        stats_cap = std::max(stats_cap, px / (kTH * kTW) * l.cout);
+        stats_cap = std::max(stats_cap, px / kTilePx * l.cout);
         bn_cap = std::max(bn_cap, (size_t)4 * u->nsm * l.cout);   // bn_pix_per_cta keeps the slabs at most 4 per SM
         w_cap = std::max(w_cap, (size_t)wgrad_geom(u, l, B).chunks * l.cout * 9 * l.cin);
+        chk(conv_plan(u, l.cout, l.cinp / 8, l.ns_f, l.slots_f));
+        if (!l.planes) chk(conv_plan(u, l.cin, l.coutp / 8, l.ns_d, l.slots_d));
+        if (e == cudaSuccess && (!l.ns_f || (!l.planes && !l.ns_d))) too_big = true;
     }
     u->pooled.assign(L, nullptr);
     u->upped.assign(L, nullptr);
@@ -363,6 +404,10 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     if (e != cudaSuccess) {
         fmbym_unet_destroy(u);
         return ucuda(nullptr, e, "U-Net allocation");
+    }
+    if (too_big) {
+        fmbym_unet_destroy(u);
+        return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "a convolution's weights and input tile exceed shared memory");
     }
     wire_inputs(u);
     *out = u;
@@ -472,13 +517,13 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
     }
     auto conv_bn = [&](Layer& l) -> cudaError_t {
         const long long px = (long long)n * l.H * l.W;
-        const int ncta = (int)(px / (kTH * kTW));
+        const int ntiles = (int)(px / kTilePx), nparts = std::min(ntiles, l.slots_f);   // the conv's grid
         cudaError_t r = conv_dispatch(u, l, n, false, st, l.y, nullptr, l.cout, 0, 0, training ? u->stats : nullptr);
         if (r != cudaSuccess) return r;
         ++u->launches;
         if (training)
-            k_bn_finalize<<<l.cout, 256, 0, st>>>(u->stats, ncta, l.cout, (float)(kTH * kTW), u->running + l.rs_off,
-                                                  u->running + l.rs_off + l.cout, l.bn);
+            k_bn_finalize<<<l.cout, 256, 0, st>>>(u->stats, nparts, l.cout, ntiles, (float)kTilePx,
+                                                  u->running + l.rs_off, u->running + l.rs_off + l.cout, l.bn);
         else
             k_bn_eval<<<1, 128, 0, st>>>(u->running + l.rs_off, u->running + l.rs_off + l.cout, l.cout, l.bn);
         ++u->launches;
@@ -489,9 +534,9 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
     for (int i = 0; i < L && e == cudaSuccess; ++i) {
         if (i > 0) {
             const Layer& prev = u->layers[2 * i - 1];
-            const long long np = (long long)n * (prev.H / 2) * (prev.W / 2) * prev.cout;
             ++u->launches;
-            k_maxpool<<<blocks(np), kBlock, 0, st>>>(prev.a, u->pooled[i], n, prev.H, prev.W, prev.cout);
+            k_maxpool<<<row_grid((prev.W / 2) * (prev.cout / 8), n * (prev.H / 2)), kBlock, 0, st>>>(
+                prev.a, u->pooled[i], n, prev.H, prev.W, prev.cout);
         }
         e = conv_bn(u->layers[2 * i]);
         if (e == cudaSuccess) e = conv_bn(u->layers[2 * i + 1]);
@@ -499,9 +544,9 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
     for (int j = 0; j < L - 1 && e == cudaSuccess; ++j) {
         const int i = L - 2 - j;
         const Layer& deep = (j == 0) ? u->layers[2 * L - 1] : u->layers[2 * L + 2 * (j - 1) + 1];
-        const long long nu = (long long)n * (deep.H * 2) * (deep.W * 2) * deep.cout;
         ++u->launches;
-        k_upsample<<<blocks(nu / 8), kBlock, 0, st>>>(deep.a, u->upped[i], n, deep.H, deep.W, deep.cout, nu / 8);
+        k_upsample<<<row_grid(2 * deep.W * (deep.cout / 8), n * 2 * deep.H), kBlock, 0, st>>>(
+            deep.a, u->upped[i], n, deep.H, deep.W, deep.cout);
         e = conv_bn(u->layers[2 * L + 2 * j]);
         if (e == cudaSuccess) e = conv_bn(u->layers[2 * L + 2 * j + 1]);
     }
@@ -585,9 +630,9 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         e = layer_bwd(la, u->dup[i], skip.da, u->ch[i + 1], 0, 0);
         if (e != cudaSuccess) break;
         Layer& deep = (j == 0) ? u->layers[2 * L - 1] : u->layers[2 * L + 2 * (j - 1) + 1];
-        const long long nl = (long long)n * deep.H * deep.W * deep.cout;
         ++u->launches;
-        k_upsample_bwd<<<blocks(nl / 4), kBlock, 0, st>>>(u->dup[i], deep.da, n, deep.H, deep.W, deep.cout, nl / 4);
+        k_upsample_bwd<<<row_grid(deep.W * (deep.cout / 4), n * deep.H), kBlock, 0, st>>>(
+            u->dup[i], deep.da, n, deep.H, deep.W, deep.cout);
         e = cudaGetLastError();
     }
     // encoder, deepest first
@@ -603,9 +648,9 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         e = layer_bwd(la, u->dpool[i], nullptr, la.cin, 0, 0);
         if (e != cudaSuccess) break;
         Layer& prev = u->layers[2 * i - 1];
-        const long long np = (long long)n * (prev.H / 2) * (prev.W / 2) * prev.cout;
         ++u->launches;
-        k_maxpool_bwd<<<blocks(np), kBlock, 0, st>>>(prev.a, u->dpool[i], prev.da, n, prev.H, prev.W, prev.cout);
+        k_maxpool_bwd<<<row_grid((prev.W / 2) * prev.cout, n * (prev.H / 2)), kBlock, 0, st>>>(
+            prev.a, u->dpool[i], prev.da, n, prev.H, prev.W, prev.cout);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return ucuda(u, e, "U-Net backward");

@@ -33,192 +33,271 @@ __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
+constexpr int kTilePx = kTH * kTW, kHaloPx = kTileH * kTileW;   // pixels of a tile, and with its halo
+
+// 16-byte global -> shared copies (zero-filled when !valid), and their group waits
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_n(int n) {   // wait until at most n groups are pending
+    if (n >= 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ldmatrix: eight 16-byte rows per 8x8 matrix, row addresses from lanes 8 i .. 8 i + 7 for matrix i
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* row_addr) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(row_addr);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t* r, const void* row_addr) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(row_addr);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const void* row_addr) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(row_addr);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(s));
+}
+
 // ---------------------------------------------------------------------------------------------
 // 3x3 convolution (zero padding 1): forward, or dgrad with the flipped transposed kernel
 // ---------------------------------------------------------------------------------------------
 //
 // Input: the channel concatenation [in0 (c0 channels), in1 (c1 channels)] of two bf16 NHWC
-// tensors, or (planes != 0) two float32 planes f, g as the 2 channels of the first layer.
-// Weights: bf16 [COUT][9][cinp], cinp = channels rounded up to 16 (zero padded).
-// Output: float32 NHWC split at channel `split`: channels [0, split) go to out0 (row stride
-// split), [split, COUT) to out1 (row stride COUT - split); acc0/acc1 add instead of store.
-// stats (forward only): per CTA and channel (mean, sum of squared deviations) of the outputs.
+// tensors, or (pf != NULL) two float32 planes f, g as the 2 channels of the first layer; G groups
+// of 8 channels (zero padded).  Weights: bf16 [COUT][9 G][8], i.e. [COUT][tap][8 G], taps
+// row-major.  Output: float32 NHWC split at channel `split`: channels [0, split) go to out0 (row
+// stride split), [split, COUT) to out1 (row stride COUT - split); acc0/acc1 add instead of store.
+// stats (forward only): per CTA and channel (mean, sum of squared deviations) of its outputs: each
+// tile's pair is taken over its 256 pixels and merged into the CTA's running pair by Chan's
+// update, in tile order.
+//
+// An implicit GEMM on mma.sync.m16n8k16: M = 16 output pixels of a tile row, N = 8 output
+// channels, and each K = 16 step takes two (tap, channel group) items, so 8-channel layers waste
+// no K.  The CTA is persistent over tiles: the whole weight array sits in shared memory, the
+// input tiles (with halo) arrive by cp.async in the NHWC byte order -- one 16-byte row per pixel
+// and channel group -- through a ring of `nstage` buffers, and ldmatrix reads the A fragments at
+// shifted row addresses (the tap) and the B fragments from the weight rows.
+__host__ __device__ constexpr int conv_items_padded(int G) { return (9 * G + 1) / 2 * 2; }
+__host__ __device__ inline size_t conv_weight_bytes(int cout, int G) { return (size_t)cout * (conv_items_padded(G) + 1) * 16; }
+__host__ __device__ inline size_t conv_tile_bytes(int G) { return (size_t)G * kHaloPx * 16; }
+constexpr int kConvMaxItems = 9 * 16 + 1;
+
 template <int COUT>
 __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in0, int c0, const bf16* __restrict__ in1,
                                                  int c1, const float* __restrict__ pf, const float* __restrict__ pg,
-                                                 const bf16* __restrict__ wt, int cinp, float* __restrict__ out0,
-                                                 float* __restrict__ out1, int split, int acc0, int acc1,
-                                                 float2* __restrict__ stats, int H, int W) {
+                                                 const bf16* __restrict__ wt, int G, int nstage,
+                                                 float* __restrict__ out0, float* __restrict__ out1, int split,
+                                                 int acc0, int acc1, float2* __restrict__ stats, int B, int H,
+                                                 int W) {
     constexpr int NT = COUT / 8;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int ps = cinp + 8;                      // pixel stride of the input tile (bf16)
-    bf16* tile = reinterpret_cast<bf16*>(smem_raw);
-    bf16* ws = tile + kTileH * kTileW * ps;       // weights [COUT][9][ps]
-    const int tx0 = blockIdx.x * kTW, ty0 = blockIdx.y * kTH, b = blockIdx.z;
-    const int tid = threadIdx.x;
-    // input tile with halo; channel groups of 8 (16 bytes)
-    const int groups = cinp / 8;
-    for (int idx = tid; idx < kTileH * kTileW * groups; idx += 256) {
-        const int gq = idx % groups, pix = idx / groups, ty = pix / kTileW, tx = pix % kTileW;
-        const int y = ty0 + ty - 1, x = tx0 + tx - 1;
+    extern __shared__ __align__(128) unsigned char smem_c[];
+    __shared__ int item_off[kConvMaxItems];       // per item: group * halo + ky * row + kx (pixels)
+    __shared__ float red[8][COUT];
+    __shared__ float mean_s[COUT];
+    const int NI = 9 * G, NIp = conv_items_padded(G), WS = NIp + 1;   // weight row stride (odd: no conflicts)
+    unsigned char* ws = smem_c;
+    unsigned char* ring = smem_c + (size_t)COUT * WS * 16;
+    const size_t TB = conv_tile_bytes(G);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    for (int i = tid; i < COUT * NIp; i += 256) {
+        const int co = i / NIp, it = i % NIp;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (y >= 0 && y < H && x >= 0 && x < W) {
-            const size_t pidx = ((size_t)b * H + y) * W + x;
-            const int ch = gq * 8;
-            if (pf) {
-                if (gq == 0) {
-                    const bf16 a = __float2bfloat16_rn(pf[pidx]), c = __float2bfloat16_rn(pg[pidx]);
-                    v.x = pack2(a, c);
+        if (it < NI) v = *reinterpret_cast<const uint4*>(wt + ((size_t)co * NI + it) * 8);
+        *reinterpret_cast<uint4*>(ws + ((size_t)co * WS + it) * 16) = v;
+    }
+    for (int i = tid; i < NIp; i += 256) {
+        const int it = min(i, NI - 1), tap = it / G, grp = it % G;   // the odd pad item repeats a real one
+        item_off[i] = grp * kHaloPx + (tap / 3) * kTileW + tap % 3;   // (its weights are zero)
+    }
+    const int tiles_x = W / kTW, tiles_y = H / kTH, ntiles = B * tiles_x * tiles_y;
+    const int n = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    auto stage = [&](int k) {   // the k-th tile of this CTA into ring slot k % nstage
+        unsigned char* buf = ring + (size_t)(k % nstage) * TB;
+        const int tile = blockIdx.x + k * gridDim.x;
+        const int b = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
+        const int ty0 = (rem / tiles_x) * kTH, tx0 = (rem % tiles_x) * kTW;
+        if (pf) {
+            for (int pix = tid; pix < kHaloPx; pix += 256) {
+                const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (y >= 0 && y < H && x >= 0 && x < W) {
+                    const size_t p = ((size_t)b * H + y) * W + x;
+                    v.x = pack2(__float2bfloat16_rn(pf[p]), __float2bfloat16_rn(pg[p]));
                 }
-            } else if (ch < c0) {
-                v = *reinterpret_cast<const uint4*>(in0 + pidx * c0 + ch);
-            } else if (ch < c0 + c1) {
-                v = *reinterpret_cast<const uint4*>(in1 + pidx * c1 + (ch - c0));
+                *reinterpret_cast<uint4*>(buf + (size_t)pix * 16) = v;
+            }
+        } else {
+            for (int i = tid; i < G * kHaloPx; i += 256) {
+                const int grp = i / kHaloPx, pix = i % kHaloPx;
+                const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
+                const bool inside = y >= 0 && y < H && x >= 0 && x < W;
+                const size_t p = inside ? ((size_t)b * H + y) * W + x : 0;
+                const int ch = grp * 8;
+                const bf16* src = ch < c0 ? in0 + p * c0 + ch : in1 + p * c1 + (ch - c0);
+                cp_async16(buf + (size_t)(grp * kHaloPx + pix) * 16, src, inside);
             }
         }
-        *reinterpret_cast<uint4*>(tile + pix * ps + gq * 8) = v;
+    };
+
+    // per-lane ldmatrix rows: A matrices (pixels 0-7 | 8-15) x (item 2s | 2s+1); B matrices
+    // (channel block n | n+1) x (item 2s | 2s+1), eight output channels each
+    const int mi = lane >> 3, r8 = lane & 7;
+    const int a_px = warp * kTileW + (mi & 1) * 8 + r8, a_item = mi >> 1;
+    float run_mean = 0.f, run_m2 = 0.f;   // the CTA's statistics so far (threads tid < COUT)
+    const int b_row = (mi >> 1) * 8 + r8, b_item = mi & 1;
+    for (int k = 0; k < nstage - 1; ++k) {
+        if (k < n) stage(k);
+        cp_async_commit();
     }
-    for (int idx = tid; idx < COUT * 9 * groups; idx += 256) {
-        const int gq = idx % groups, row = idx / groups;
-        *reinterpret_cast<uint4*>(ws + row * ps + gq * 8) =
-            *reinterpret_cast<const uint4*>(wt + (size_t)row * cinp + gq * 8);
-    }
-    __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    float acc[2][NT][4];
+    for (int it = 0; it < n; ++it) {
+        if (it + nstage - 1 < n) stage(it + nstage - 1);
+        cp_async_commit();
+        cp_async_wait_n(nstage - 1);
+        __syncthreads();
+        const unsigned char* tb = ring + (size_t)(it % nstage) * TB;
+        float acc[2][NT][4];
 #pragma unroll
-    for (int m = 0; m < 2; ++m)
+        for (int m = 0; m < 2; ++m)
 #pragma unroll
-        for (int n = 0; n < NT; ++n)
+            for (int q = 0; q < NT; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[m][n][k] = 0.f;
-    const uint32_t* tile32 = reinterpret_cast<const uint32_t*>(tile);
-    const uint32_t* ws32 = reinterpret_cast<const uint32_t*>(ws);
-    const int ps32 = ps / 2;
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
-        for (int kc = 0; kc < cinp; kc += 16) {
+                for (int j = 0; j < 4; ++j) acc[m][q][j] = 0.f;
+        for (int s = 0; s < NIp / 2; ++s) {
+            const int off = item_off[2 * s + a_item] + a_px;
             uint32_t a[2][4];
+            ldsm_x4(a[0], tb + (size_t)off * 16);
+            ldsm_x4(a[1], tb + (size_t)(off + 16) * 16);
 #pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const int p0 = (warp + ky) * kTileW + m * 16 + g + kx;
-                const int base0 = p0 * ps32 + (kc >> 1) + t, base1 = (p0 + 8) * ps32 + (kc >> 1) + t;
-                a[m][0] = tile32[base0];
-                a[m][1] = tile32[base1];
-                a[m][2] = tile32[base0 + 4];
-                a[m][3] = tile32[base1 + 4];
-            }
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const int wb = ((n * 8 + g) * 9 + tap) * ps32 + (kc >> 1) + t;
-                uint32_t bb[2] = {ws32[wb], ws32[wb + 4]};
-                mma16816(acc[0][n], a[0], bb);
-                mma16816(acc[1][n], a[1], bb);
+            for (int q = 0; q < NT; q += 2) {
+                if (q + 1 < NT) {
+                    uint32_t bq[4];
+                    ldsm_x4(bq, ws + ((size_t)(q * 8 + b_row) * WS + 2 * s + b_item) * 16);
+                    mma16816(acc[0][q], a[0], bq);
+                    mma16816(acc[1][q], a[1], bq);
+                    mma16816(acc[0][q + 1], a[0], bq + 2);
+                    mma16816(acc[1][q + 1], a[1], bq + 2);
+                } else {
+                    uint32_t bq[2];
+                    ldsm_x2(bq, ws + ((size_t)(q * 8 + r8) * WS + 2 * s + b_item) * 16);
+                    mma16816(acc[0][q], a[0], bq);
+                    mma16816(acc[1][q], a[1], bq);
+                }
             }
         }
-    }
-    // store
-    const int y = ty0 + warp;
+        // epilogue: rows g (+8) of the m-block are pixels, columns 2t (+1) channels
+        const int tile = blockIdx.x + it * gridDim.x;
+        const int b = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
+        const int y = (rem / tiles_x) * kTH + warp, tx0 = (rem % tiles_x) * kTW;
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
+        for (int m = 0; m < 2; ++m) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int x = tx0 + m * 16 + g + 8 * h;
-            const size_t pidx = ((size_t)b * H + y) * W + x;
+            for (int h = 0; h < 2; ++h) {
+                const int x = tx0 + m * 16 + g + 8 * h;
+                const size_t pidx = ((size_t)b * H + y) * W + x;
 #pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const int ch = n * 8 + 2 * t;
-                const float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
-                if (ch < split) {
-                    float2* o = reinterpret_cast<float2*>(out0 + pidx * split + ch);
-                    if (acc0) {
-                        float2 old = *o;
-                        *o = make_float2(old.x + v0, old.y + v1);
+                for (int q = 0; q < NT; ++q) {
+                    const int ch = q * 8 + 2 * t;
+                    const float v0 = acc[m][q][2 * h], v1 = acc[m][q][2 * h + 1];
+                    if (ch < split) {
+                        float2* o = reinterpret_cast<float2*>(out0 + pidx * split + ch);
+                        if (acc0) {
+                            const float2 old = *o;
+                            *o = make_float2(old.x + v0, old.y + v1);
+                        } else {
+                            *o = make_float2(v0, v1);
+                        }
                     } else {
-                        *o = make_float2(v0, v1);
-                    }
-                } else {
-                    float2* o = reinterpret_cast<float2*>(out1 + pidx * (COUT - split) + (ch - split));
-                    if (acc1) {
-                        float2 old = *o;
-                        *o = make_float2(old.x + v0, old.y + v1);
-                    } else {
-                        *o = make_float2(v0, v1);
+                        float2* o = reinterpret_cast<float2*>(out1 + pidx * (COUT - split) + (ch - split));
+                        if (acc1) {
+                            const float2 old = *o;
+                            *o = make_float2(old.x + v0, old.y + v1);
+                        } else {
+                            *o = make_float2(v0, v1);
+                        }
                     }
                 }
             }
         }
-    }
-    if (stats) {
-        // per-channel mean and sum of squared deviations over the CTA's 256 outputs: lanes with the
-        // same t hold the same channels; reduce over g, then over warps in a fixed order
-        __shared__ float red[8][COUT];
-        __shared__ float mean_s[COUT];
+        if (stats) {
+            // per-channel mean and sum of squared deviations over the tile's 256 outputs: lanes with
+            // the same t hold the same channels; reduce over g, then over warps in a fixed order
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            float s0 = acc[0][n][0] + acc[0][n][2] + acc[1][n][0] + acc[1][n][2];
-            float s1 = acc[0][n][1] + acc[0][n][3] + acc[1][n][1] + acc[1][n][3];
+            for (int q = 0; q < NT; ++q) {
+                float s0 = acc[0][q][0] + acc[0][q][2] + acc[1][q][0] + acc[1][q][2];
+                float s1 = acc[0][q][1] + acc[0][q][3] + acc[1][q][1] + acc[1][q][3];
 #pragma unroll
-            for (int o = 4; o < 32; o <<= 1) {
-                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            }
-            if (g == 0) {
-                red[warp][n * 8 + 2 * t] = s0;
-                red[warp][n * 8 + 2 * t + 1] = s1;
-            }
-        }
-        __syncthreads();
-        if (tid < COUT) {
-            float s = 0.f;
-            for (int w = 0; w < 8; ++w) s += red[w][tid];
-            mean_s[tid] = s * (1.f / (kTH * kTW));
-        }
-        __syncthreads();
-#pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            const float mu0 = mean_s[n * 8 + 2 * t], mu1 = mean_s[n * 8 + 2 * t + 1];
-            float q0 = 0.f, q1 = 0.f;
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                q0 += (acc[m][n][0] - mu0) * (acc[m][n][0] - mu0) + (acc[m][n][2] - mu0) * (acc[m][n][2] - mu0);
-                q1 += (acc[m][n][1] - mu1) * (acc[m][n][1] - mu1) + (acc[m][n][3] - mu1) * (acc[m][n][3] - mu1);
-            }
-#pragma unroll
-            for (int o = 4; o < 32; o <<= 1) {
-                q0 += __shfl_xor_sync(0xffffffffu, q0, o);
-                q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+                for (int o = 4; o < 32; o <<= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                }
+                if (g == 0) {
+                    red[warp][q * 8 + 2 * t] = s0;
+                    red[warp][q * 8 + 2 * t + 1] = s1;
+                }
             }
             __syncthreads();
-            if (g == 0) {
-                red[warp][n * 8 + 2 * t] = q0;
-                red[warp][n * 8 + 2 * t + 1] = q1;
+            if (tid < COUT) {
+                float sm = 0.f;
+                for (int w = 0; w < 8; ++w) sm += red[w][tid];
+                mean_s[tid] = sm * (1.f / kTilePx);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < NT; ++q) {
+                const float mu0 = mean_s[q * 8 + 2 * t], mu1 = mean_s[q * 8 + 2 * t + 1];
+                float q0 = 0.f, q1 = 0.f;
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    q0 += (acc[m][q][0] - mu0) * (acc[m][q][0] - mu0) + (acc[m][q][2] - mu0) * (acc[m][q][2] - mu0);
+                    q1 += (acc[m][q][1] - mu1) * (acc[m][q][1] - mu1) + (acc[m][q][3] - mu1) * (acc[m][q][3] - mu1);
+                }
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {
+                    q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+                    q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+                }
+                __syncthreads();
+                if (g == 0) {
+                    red[warp][q * 8 + 2 * t] = q0;
+                    red[warp][q * 8 + 2 * t + 1] = q1;
+                }
+            }
+            __syncthreads();
+            if (tid < COUT) {
+                float sm = 0.f;
+                for (int w = 0; w < 8; ++w) sm += red[w][tid];
+                // merge (kTilePx, mean_s, sm) into (it * kTilePx, run_mean, run_m2)
+                const float d = mean_s[tid] - run_mean, f = 1.f / (float)(it + 1);
+                run_mean = fmaf(d, f, run_mean);
+                run_m2 += sm + d * d * (float)kTilePx * (float)it * f;
             }
         }
         __syncthreads();
-        if (tid < COUT) {
-            float s = 0.f;
-            for (int w = 0; w < 8; ++w) s += red[w][tid];
-            const int cta = (b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            stats[(size_t)cta * COUT + tid] = make_float2(mean_s[tid], s);
-        }
     }
-}
-
-inline size_t conv_smem(int cout, int cinp) {
-    return (size_t)(kTileH * kTileW + cout * 9) * (cinp + 8) * sizeof(bf16);
+    if (stats && tid < COUT && n > 0) stats[(size_t)blockIdx.x * COUT + tid] = make_float2(run_mean, run_m2);
 }
 
 // ---------------------------------------------------------------------------------------------
 // BatchNorm
 // ---------------------------------------------------------------------------------------------
 
-// Combines the per-CTA (mean, M2) partials of one channel, all over the same count m: the batch
-// mean is the mean of the CTA means and M2 = sum M2_i + m sum (mean_i - mean)^2 (two passes, each a
-// fixed-order sum).  Updates the running statistics (momentum 0.1, unbiased variance) and writes
+// Combines the per-CTA (mean, M2) partials of one channel.  CTA k of the convolution's nparts
+// covered n_k = ((ntiles - 1 - k) / nparts + 1) tiles of tile_px pixels; the batch mean is
+// sum n_k mean_k / N and M2 = sum M2_k + sum n_k (mean_k - mean)^2 (two passes; each thread adds a
+// fixed stride of partials in float32, the block adds the threads in a fixed-order float64 tree).
+// Updates the running statistics (momentum 0.1, unbiased variance) and writes
 // bn[c] = (mean, 1/sqrt(var + eps)) for the batch statistics.  One block per channel.
-__global__ void __launch_bounds__(256) k_bn_finalize(const float2* __restrict__ stats, int ncta, int C,
-                                                     float cnt_per_cta, float* __restrict__ run_mean,
+__global__ void __launch_bounds__(256) k_bn_finalize(const float2* __restrict__ stats, int nparts, int C,
+                                                     int ntiles, float tile_px, float* __restrict__ run_mean,
                                                      float* __restrict__ run_var, float2* __restrict__ bn) {
     __shared__ double r[256];
     const int c = blockIdx.x;
@@ -229,23 +308,26 @@ __global__ void __launch_bounds__(256) k_bn_finalize(const float2* __restrict__ 
             if ((int)threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
             __syncthreads();
         }
-        const double t = r[0];
+        const double tot = r[0];
         __syncthreads();
-        return t;
+        return tot;
     };
-    double s = 0.0;
-    for (int i = threadIdx.x; i < ncta; i += 256) s += (double)stats[(size_t)i * C + c].x;
-    const double mean = block_sum(s) / ncta;
-    double q = 0.0, e = 0.0;
-    for (int i = threadIdx.x; i < ncta; i += 256) {
-        const float2 v = stats[(size_t)i * C + c];
-        const double d = (double)v.x - mean;
-        q += (double)v.y;
-        e += d * d;
+    auto count = [&](int k) { return (float)((ntiles - 1 - k) / nparts + 1) * tile_px; };
+    float s = 0.f;
+    for (int k = threadIdx.x; k < nparts; k += 256) s = fmaf(count(k), stats[(size_t)k * C + c].x, s);
+    const double N = (double)ntiles * tile_px;
+    const double mean = block_sum(s) / N;
+    const float mf = (float)mean;
+    float q = 0.f, e = 0.f;
+    for (int k = threadIdx.x; k < nparts; k += 256) {
+        const float2 v = stats[(size_t)k * C + c];
+        const float d = v.x - mf;
+        q += v.y;
+        e = fmaf(count(k) * d, d, e);
     }
-    const double m2 = block_sum(q) + (double)cnt_per_cta * block_sum(e);
+    const double m2 = block_sum(q) + block_sum(e);
     if (threadIdx.x == 0) {
-        const double N = (double)cnt_per_cta * ncta, var = m2 / N;
+        const double var = m2 / N;
         run_mean[c] = (float)((1.0 - kMomentum) * run_mean[c] + kMomentum * mean);
         run_var[c] = (float)((1.0 - kMomentum) * run_var[c] + kMomentum * var * N / (N > 1 ? N - 1 : 1));
         bn[c] = make_float2((float)mean, (float)(1.0 / sqrt(var + kEps)));
@@ -398,49 +480,62 @@ __global__ void k_bn_bwd_dy(const float* __restrict__ y, const float* __restrict
 // max-pool 2x2 and bilinear x2 (align_corners = False) with their adjoints
 // ---------------------------------------------------------------------------------------------
 
+// Pooling and upsampling kernels run on a 2-D grid: blockIdx.y walks image rows (b, y) with a
+// stride of gridDim.y, blockIdx.x / threadIdx.x the pixels x channel vectors of one row, so that
+// all index arithmetic is 32-bit.  Channel counts are multiples of 8.
+
+// 2x2 max-pool, eight channels (16 bytes) per thread; rows = B * H / 2.
 __global__ void k_maxpool(const bf16* __restrict__ a, bf16* __restrict__ p, int B, int H, int W, int C) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int Ho = H / 2, Wo = W / 2;
-    if (i >= (long long)B * Ho * Wo * C) return;
-    const int c = (int)(i % C);
-    long long r = i / C;
-    const int x = (int)(r % Wo);
-    r /= Wo;
-    const int y = (int)(r % Ho);
-    const int b = (int)(r / Ho);
-    const bf16* base = a + (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
-    float m = __bfloat162float(base[0]);
-    m = fmaxf(m, __bfloat162float(base[C]));
-    m = fmaxf(m, __bfloat162float(base[(size_t)W * C]));
-    m = fmaxf(m, __bfloat162float(base[(size_t)W * C + C]));
-    p[i] = __float2bfloat16_rn(m);
+    const int Ho = H / 2, Wo = W / 2, q = C / 8;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Wo * q) return;
+    const int c = (j % q) * 8, x = j / q;
+    for (int row = blockIdx.y; row < B * Ho; row += gridDim.y) {
+        const int b = row / Ho, y = row % Ho;
+        const bf16* base = a + (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
+        const uint4 v[4] = {*reinterpret_cast<const uint4*>(base), *reinterpret_cast<const uint4*>(base + C),
+                            *reinterpret_cast<const uint4*>(base + (size_t)W * C),
+                            *reinterpret_cast<const uint4*>(base + (size_t)W * C + C)};
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t w[4] = {(&v[0].x)[k], (&v[1].x)[k], (&v[2].x)[k], (&v[3].x)[k]};
+            float lo = __uint_as_float(w[0] << 16), hi = __uint_as_float(w[0] & 0xffff0000u);
+#pragma unroll
+            for (int r = 1; r < 4; ++r) {
+                lo = fmaxf(lo, __uint_as_float(w[r] << 16));
+                hi = fmaxf(hi, __uint_as_float(w[r] & 0xffff0000u));
+            }
+            o[k] = pack2(__float2bfloat16_rn(lo), __float2bfloat16_rn(hi));   // exact: both are bf16 values
+        }
+        *reinterpret_cast<uint4*>(p + (((size_t)b * Ho + y) * Wo + x) * C + c) = make_uint4(o[0], o[1], o[2], o[3]);
+    }
 }
 
 // Routes d p to the first maximum of its window in row-major order (strict >), added to da.
+// One channel per thread; rows = B * H / 2.
 __global__ void k_maxpool_bwd(const bf16* __restrict__ a, const float* __restrict__ dp, float* __restrict__ da,
                               int B, int H, int W, int C) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int Ho = H / 2, Wo = W / 2;
-    if (i >= (long long)B * Ho * Wo * C) return;
-    const int c = (int)(i % C);
-    long long r = i / C;
-    const int x = (int)(r % Wo);
-    r /= Wo;
-    const int y = (int)(r % Ho);
-    const int b = (int)(r / Ho);
-    const size_t off[4] = {0, (size_t)C, (size_t)W * C, (size_t)W * C + C};
-    const size_t base = (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
-    int best = 0;
-    float m = __bfloat162float(a[base]);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Wo * C) return;
+    const int c = j % C, x = j / C;
+    for (int row = blockIdx.y; row < B * Ho; row += gridDim.y) {
+        const int b = row / Ho, y = row % Ho;
+        const size_t off[4] = {0, (size_t)C, (size_t)W * C, (size_t)W * C + C};
+        const size_t base = (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
+        int best = 0;
+        float m = __bfloat162float(a[base]);
 #pragma unroll
-    for (int k = 1; k < 4; ++k) {
-        const float v = __bfloat162float(a[base + off[k]]);
-        if (v > m) {
-            m = v;
-            best = k;
+        for (int k = 1; k < 4; ++k) {
+            const float v = __bfloat162float(a[base + off[k]]);
+            if (v > m) {
+                m = v;
+                best = k;
+            }
         }
+        da[base + off[best]] += dp[(((size_t)b * Ho + y) * Wo + x) * C + c];
     }
-    da[base + off[best]] += dp[i];
 }
 
 // Source row/column of the bilinear x2 upsampling with align_corners = False: output index o
@@ -455,43 +550,42 @@ __device__ __forceinline__ void up_src(int o, int n, int& i0, int& i1, float& l0
     l0 = 1.f - l1;
 }
 
-// Eight channels (16 bytes) of one output pixel per thread; n8 = B * 2h * 2w * C / 8.
-__global__ void k_upsample(const bf16* __restrict__ a, bf16* __restrict__ u, int B, int h, int w, int C,
-                           long long n8) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n8) return;
+// Eight channels (16 bytes) of one output pixel per thread; rows = B * 2h.
+__global__ void k_upsample(const bf16* __restrict__ a, bf16* __restrict__ u, int B, int h, int w, int C) {
     const int H = 2 * h, W = 2 * w, q = C / 8;
-    const int c = (int)(i % q) * 8;
-    long long r = i / q;
-    const int X = (int)(r % W);
-    r /= W;
-    const int Y = (int)(r % H);
-    const int b = (int)(r / H);
-    int y0, y1, x0, x1;
-    float ly0, ly1, lx0, lx1;
-    up_src(Y, h, y0, y1, ly0, ly1);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= W * q) return;
+    const int c = (j % q) * 8, X = j / q;
+    int x0, x1;
+    float lx0, lx1;
     up_src(X, w, x0, x1, lx0, lx1);
-    const bf16* base = a + (size_t)b * h * w * C + c;
-    const uint4 v00 = *reinterpret_cast<const uint4*>(base + ((size_t)y0 * w + x0) * C);
-    const uint4 v01 = *reinterpret_cast<const uint4*>(base + ((size_t)y0 * w + x1) * C);
-    const uint4 v10 = *reinterpret_cast<const uint4*>(base + ((size_t)y1 * w + x0) * C);
-    const uint4 v11 = *reinterpret_cast<const uint4*>(base + ((size_t)y1 * w + x1) * C);
-    const uint32_t* p00 = &v00.x;
-    const uint32_t* p01 = &v01.x;
-    const uint32_t* p10 = &v10.x;
-    const uint32_t* p11 = &v11.x;
-    uint32_t o[4];
+    for (int row = blockIdx.y; row < B * H; row += gridDim.y) {
+        const int b = row / H, Y = row % H;
+        int y0, y1;
+        float ly0, ly1;
+        up_src(Y, h, y0, y1, ly0, ly1);
+        const bf16* base = a + (size_t)b * h * w * C + c;
+        const uint4 v00 = *reinterpret_cast<const uint4*>(base + ((size_t)y0 * w + x0) * C);
+        const uint4 v01 = *reinterpret_cast<const uint4*>(base + ((size_t)y0 * w + x1) * C);
+        const uint4 v10 = *reinterpret_cast<const uint4*>(base + ((size_t)y1 * w + x0) * C);
+        const uint4 v11 = *reinterpret_cast<const uint4*>(base + ((size_t)y1 * w + x1) * C);
+        const uint32_t* p00 = &v00.x;
+        const uint32_t* p01 = &v01.x;
+        const uint32_t* p10 = &v10.x;
+        const uint32_t* p11 = &v11.x;
+        uint32_t o[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        float res[2];
+        for (int k = 0; k < 4; ++k) {
+            float res[2];
 #pragma unroll
-        for (int hlf = 0; hlf < 2; ++hlf) {
-            auto f = [&](uint32_t wd) { return __uint_as_float(hlf ? (wd & 0xffff0000u) : (wd << 16)); };
-            res[hlf] = ly0 * (lx0 * f(p00[k]) + lx1 * f(p01[k])) + ly1 * (lx0 * f(p10[k]) + lx1 * f(p11[k]));
+            for (int hlf = 0; hlf < 2; ++hlf) {
+                auto f = [&](uint32_t wd) { return __uint_as_float(hlf ? (wd & 0xffff0000u) : (wd << 16)); };
+                res[hlf] = ly0 * (lx0 * f(p00[k]) + lx1 * f(p01[k])) + ly1 * (lx0 * f(p10[k]) + lx1 * f(p11[k]));
+            }
+            o[k] = pack2(__float2bfloat16_rn(res[0]), __float2bfloat16_rn(res[1]));
         }
-        o[k] = pack2(__float2bfloat16_rn(res[0]), __float2bfloat16_rn(res[1]));
+        *reinterpret_cast<uint4*>(u + (((size_t)b * H + Y) * W + X) * C + c) = make_uint4(o[0], o[1], o[2], o[3]);
     }
-    *reinterpret_cast<uint4*>(u + i * 8) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 // Weight that the forward assigns from input index k to output index o (both taps if clamped).
@@ -504,43 +598,40 @@ __device__ __forceinline__ float up_w(int o, int k, int n) {
 
 // Transpose of the upsampling in gather form: d a[k] = sum over the outputs o in [2k-1, 2k+2] (the
 // only ones whose two taps can reach k) of the forward weights times d u[o]; written (not added)
-// to da.  Four channels per thread; n4 = B * h * w * C / 4.
-__global__ void k_upsample_bwd(const float* __restrict__ du, float* __restrict__ da, int B, int h, int w, int C,
-                               long long n4) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n4) return;
+// to da.  Four channels per thread; rows = B * h.
+__global__ void k_upsample_bwd(const float* __restrict__ du, float* __restrict__ da, int B, int h, int w, int C) {
     const int H = 2 * h, W = 2 * w, q = C / 4;
-    const int c = (int)(i % q) * 4;
-    long long r = i / q;
-    const int x = (int)(r % w);
-    r /= w;
-    const int y = (int)(r % h);
-    const int b = (int)(r / h);
-    float wy[4], wx[4];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= w * q) return;
+    const int c = (j % q) * 4, x = j / q;
+    float wx[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int Y = 2 * y - 1 + k, X = 2 * x - 1 + k;
-        wy[k] = (Y >= 0 && Y < H) ? up_w(Y, y, h) : 0.f;
+        const int X = 2 * x - 1 + k;
         wx[k] = (X >= 0 && X < W) ? up_w(X, x, w) : 0.f;
     }
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int row = blockIdx.y; row < B * h; row += gridDim.y) {
+        const int b = row / h, y = row % h;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int ky = 0; ky < 4; ++ky) {
-        if (wy[ky] == 0.f) continue;
-        const int Y = 2 * y - 1 + ky;
+        for (int ky = 0; ky < 4; ++ky) {
+            const int Y = 2 * y - 1 + ky;
+            const float wy = (Y >= 0 && Y < H) ? up_w(Y, y, h) : 0.f;
+            if (wy == 0.f) continue;
 #pragma unroll
-        for (int kx = 0; kx < 4; ++kx) {
-            if (wx[kx] == 0.f) continue;
-            const int X = 2 * x - 1 + kx;
-            const float wt = wy[ky] * wx[kx];
-            const float4 v = *reinterpret_cast<const float4*>(du + (((size_t)b * H + Y) * W + X) * C + c);
-            s.x += wt * v.x;
-            s.y += wt * v.y;
-            s.z += wt * v.z;
-            s.w += wt * v.w;
+            for (int kx = 0; kx < 4; ++kx) {
+                if (wx[kx] == 0.f) continue;
+                const int X = 2 * x - 1 + kx;
+                const float wt = wy * wx[kx];
+                const float4 v = *reinterpret_cast<const float4*>(du + (((size_t)b * H + Y) * W + X) * C + c);
+                s.x += wt * v.x;
+                s.y += wt * v.y;
+                s.z += wt * v.z;
+                s.w += wt * v.w;
+            }
         }
+        *reinterpret_cast<float4*>(da + (((size_t)b * h + y) * w + x) * C + c) = s;
     }
-    *reinterpret_cast<float4*>(da + i * 4) = s;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -672,21 +763,6 @@ __global__ void __launch_bounds__(256) k_sum_parts(const float* __restrict__ par
 // Requires cout and every input channel count to be multiples of 8 (the planes of the first
 // layer are staged by plain loads instead).
 
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(valid ? 16 : 0));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const void* row_addr) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(row_addr);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(s));
-}
-
-constexpr int kTilePx = kTH * kTW, kHaloPx = kTileH * kTileW;
 
 template <int CIB>
 __host__ __device__ constexpr size_t wgrad_buf_bytes() { return (size_t)(2 * kTilePx + (CIB / 8) * kHaloPx) * 16; }

@@ -30,11 +30,14 @@ def test_trained_mask_lowers_translation_error():
     plain = ms.poses(Fe_t, Ge_t, masked=False).cpu().numpy()
     rng = np.random.default_rng(0)
     nb = F.shape[0] // 64
+    # lr 2e-3: the held-out translation error stays at 0.6-0.7 of the unmasked search's from step
+    # 240 to 640 of this schedule, so the bound below does not hinge on rounding-level differences
+    # in the trajectory (at 1e-3 it wanders between 0.79 and 0.91)
     for step in range(400):   # 12.5 epochs of the 2048 pairs
         if step % nb == 0:
             perm = torch.from_numpy(rng.permutation(F.shape[0])).cuda()
         idx = perm[(step % nb) * 64:(step % nb + 1) * 64]
-        ms.train_step(Ft[idx].contiguous(), Gt[idx].contiguous(), Pt[idx].contiguous(), lr=1e-3)
+        ms.train_step(Ft[idx].contiguous(), Gt[idx].contiguous(), Pt[idx].contiguous(), lr=2e-3)
     masked = ms.poses(Fe_t, Ge_t, masked=True).cpu().numpy()
     torch.cuda.synchronize()
     ms.close()
