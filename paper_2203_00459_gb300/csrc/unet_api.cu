@@ -24,6 +24,7 @@ struct Layer {
     int cin, cout, H, W;       // input channels, output channels, resolution
     int cinp, coutp;           // channels rounded up to 8
     int ns_f = 0, ns_d = 0;    // cp.async ring depth of the forward and dgrad convolutions
+    int R_f = 1, R_d = 1;      // their rows per warp (CTA tile 8 R x 32)
     int slots_f = 0, slots_d = 0;   // their resident CTAs on the device
     long long w_off, g_off, b_off, rs_off;  // offsets in the parameter and running-stat arrays
     bf16* wf = nullptr;        // forward weights [cout][9][cinp]
@@ -62,6 +63,7 @@ struct fmbym_unet {
     float* hpart = nullptr;             // head partials
     size_t stats_cap = 0, bnpart_cap = 0, wpart_cap = 0, hpart_cap = 0;
     int wslots[5] = {0};                // resident CTAs of the wgrad variants (CIB 8/16/32/64, planes)
+    int wns[5] = {0};                   // and their cp.async ring depths
     int nsm = 0;
     std::vector<void*> allocs;
     long long launches = 0;
@@ -99,77 +101,92 @@ inline unsigned blocks(long long n) { return (unsigned)((n + kBlock - 1) / kBloc
 // 2-D grid of the row kernels: threads over one row's work items, blocks in y over the rows
 inline dim3 row_grid(int per_row, int rows) { return dim3(blocks(per_row), (unsigned)std::min(rows, 65535)); }
 
-// Ring depth and resident CTAs of a convolution with COUT outputs and G input groups: three tile
-// buffers while the CTA stays under 64 KB of shared memory, else two, else one; 0 if even one
-// does not fit.
-template <int COUT>
+// Ring depth and resident CTAs of a convolution with COUT outputs, G input groups and R-row warps:
+// three tile buffers while the CTA stays under 64 KB of shared memory, else two, else one; 0 if
+// even one does not fit.
+template <int COUT, int R>
 cudaError_t conv_plan_t(const fmbym_unet* u, int G, int& ns, int& slots) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_conv3x3<COUT>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_conv3x3<COUT, R>);
     if (e != cudaSuccess) return e;
     int dev = 0, optin = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const size_t cap = (size_t)optin - fa.sharedSizeBytes, wb = conv_weight_bytes(COUT, G), tb = conv_tile_bytes(G);
+    const size_t cap = (size_t)optin - fa.sharedSizeBytes, wb = conv_weight_bytes(COUT, G),
+                 tb = conv_tile_bytes(G, R);
     ns = wb + 3 * tb <= 64 * 1024 ? 3 : wb + 2 * tb <= cap ? 2 : wb + tb <= cap ? 1 : 0;
     slots = 0;
     if (!ns) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_conv3x3<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    e = cudaFuncSetAttribute(k_conv3x3<COUT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
     int occ = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3x3<COUT>, 256, wb + ns * tb);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3x3<COUT, R>, 256, wb + ns * tb);
     slots = std::max(1, occ) * u->nsm;
     return e;
 }
 
-cudaError_t conv_plan(const fmbym_unet* u, int cout, int G, int& ns, int& slots) {
+// Tile height of a convolution: narrow outputs (8, 16, 24 channels) take the tallest CTA tile
+// (R = 4, 2, 1 rows per warp) that divides the image height and keeps two input tiles and the
+// weights within 64 KB; everything else R = 1.
+cudaError_t conv_plan(const fmbym_unet* u, int cout, int G, int H, int& R, int& ns, int& slots) {
+    ns = 0;
+    slots = 0;
+    if (cout == 8 || cout == 16 || cout == 24) {
+        for (R = 4; R > 1; R /= 2) {
+            if (H % (8 * R) || conv_weight_bytes(cout, G) + 2 * conv_tile_bytes(G, R) > 64 * 1024) continue;
+            cudaError_t e;
+            if (R == 4) e = cout == 8 ? conv_plan_t<8, 4>(u, G, ns, slots) : cout == 16 ? conv_plan_t<16, 4>(u, G, ns, slots)
+                                                                                       : conv_plan_t<24, 4>(u, G, ns, slots);
+            else e = cout == 8 ? conv_plan_t<8, 2>(u, G, ns, slots) : cout == 16 ? conv_plan_t<16, 2>(u, G, ns, slots)
+                                                                                 : conv_plan_t<24, 2>(u, G, ns, slots);
+            return e;
+        }
+    }
+    R = 1;
     switch (cout) {
-        case 8: return conv_plan_t<8>(u, G, ns, slots);
-        case 16: return conv_plan_t<16>(u, G, ns, slots);
-        case 24: return conv_plan_t<24>(u, G, ns, slots);
-        case 32: return conv_plan_t<32>(u, G, ns, slots);
-        case 48: return conv_plan_t<48>(u, G, ns, slots);
-        case 64: return conv_plan_t<64>(u, G, ns, slots);
-        case 96: return conv_plan_t<96>(u, G, ns, slots);
-        case 128: return conv_plan_t<128>(u, G, ns, slots);
-        default: ns = 0; return cudaSuccess;
+        case 8: return conv_plan_t<8, 1>(u, G, ns, slots);
+        case 16: return conv_plan_t<16, 1>(u, G, ns, slots);
+        case 24: return conv_plan_t<24, 1>(u, G, ns, slots);
+        case 32: return conv_plan_t<32, 1>(u, G, ns, slots);
+        case 48: return conv_plan_t<48, 1>(u, G, ns, slots);
+        case 64: return conv_plan_t<64, 1>(u, G, ns, slots);
+        case 96: return conv_plan_t<96, 1>(u, G, ns, slots);
+        case 128: return conv_plan_t<128, 1>(u, G, ns, slots);
+        default: return cudaSuccess;
     }
 }
 
-template <int COUT>
+template <int COUT, int R>
 cudaError_t conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
                         float* out1, int split, int acc0, int acc1, float2* stats) {
     const int G = (dgrad ? L.coutp : L.cinp) / 8, ns = dgrad ? L.ns_d : L.ns_f;
     const bf16* w = dgrad ? L.wd : L.wf;
-    const size_t smem = conv_weight_bytes(COUT, G) + ns * conv_tile_bytes(G);
-    const int ntiles = B * (L.H / kTH) * (L.W / kTW);
+    const size_t smem = conv_weight_bytes(COUT, G) + ns * conv_tile_bytes(G, R);
+    const int ntiles = B * (L.H / (8 * R)) * (L.W / kTW);
     const int grid = std::min(ntiles, dgrad ? L.slots_d : L.slots_f);
     ++u->launches;
     if (dgrad)
-        k_conv3x3<COUT><<<grid, 256, smem, st>>>(L.dy, L.cout, nullptr, 0, nullptr, nullptr, w, G, ns, out0, out1,
-                                                 split, acc0, acc1, nullptr, B, L.H, L.W);
+        k_conv3x3<COUT, R><<<grid, 256, smem, st>>>(L.dy, L.cout, nullptr, 0, nullptr, nullptr, w, G, ns, out0,
+                                                    out1, split, acc0, acc1, nullptr, B, L.H, L.W);
     else
-        k_conv3x3<COUT><<<grid, 256, smem, st>>>(L.in0, L.c0, L.in1, L.c1, L.planes ? (const float*)L.in0 : nullptr,
-                                                 L.planes ? (const float*)L.in1 : nullptr, w, G, ns, out0, out1,
-                                                 split, acc0, acc1, stats, B, L.H, L.W);
+        k_conv3x3<COUT, R><<<grid, 256, smem, st>>>(L.in0, L.c0, L.in1, L.c1,
+                                                    L.planes ? (const float*)L.in0 : nullptr,
+                                                    L.planes ? (const float*)L.in1 : nullptr, w, G, ns, out0, out1,
+                                                    split, acc0, acc1, stats, B, L.H, L.W);
     return cudaGetLastError();
 }
 
 cudaError_t conv_dispatch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
                           float* out1, int split, int acc0, int acc1, float2* stats) {
-    const int co = dgrad ? L.cin : L.cout;
-    switch (co) {
-        case 8: return conv_launch<8>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
-        case 16: return conv_launch<16>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
-        case 24: return conv_launch<24>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
-        case 32: return conv_launch<32>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
-        case 48: return conv_launch<48>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
-        case 64: return conv_launch<64>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
-        case 96: return conv_launch<96>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
-        case 128: return conv_launch<128>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
-        default: return cudaErrorInvalidValue;
-    }
+    const int co = dgrad ? L.cin : L.cout, R = dgrad ? L.R_d : L.R_f;
+#define FMBYM_CONV(C, RR) \
+    if (co == C && R == RR) return conv_launch<C, RR>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
+    FMBYM_CONV(8, 4) FMBYM_CONV(16, 4) FMBYM_CONV(24, 4) FMBYM_CONV(8, 2) FMBYM_CONV(16, 2) FMBYM_CONV(24, 2)
+    FMBYM_CONV(8, 1) FMBYM_CONV(16, 1) FMBYM_CONV(24, 1) FMBYM_CONV(32, 1) FMBYM_CONV(48, 1) FMBYM_CONV(64, 1)
+    FMBYM_CONV(96, 1) FMBYM_CONV(128, 1)
+#undef FMBYM_CONV
+    return cudaErrorInvalidValue;
 }
 
 // BN adjoint slabs: about four CTAs per SM, each a whole number of the reduce kernel's pixel rows.
@@ -206,9 +223,11 @@ WgradGeom wgrad_geom(const fmbym_unet* u, const Layer& l, int B) {
     return w;
 }
 
+// Three ring slots while they stay under 100 KB of shared memory, else two.
 template <int CIB, bool PLANES>
 cudaError_t wgrad_prepare(fmbym_unet* u, int v) {
-    const size_t smem = wgrad_smem<CIB>();
+    u->wns[v] = 3 * wgrad_buf_bytes<CIB>() <= 100 * 1024 ? 3 : 2;
+    const size_t smem = wgrad_smem<CIB>(u->wns[v]);
     cudaError_t e = cudaFuncSetAttribute(k_wgrad<CIB, PLANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wgrad<CIB, PLANES>, 256, smem);
@@ -217,10 +236,11 @@ cudaError_t wgrad_prepare(fmbym_unet* u, int v) {
 }
 
 template <int CIB, bool PLANES>
-void wgrad_run(const Layer& l, const WgradGeom& w, int n, const float* f, const float* g, float* part,
-               cudaStream_t st) {
-    k_wgrad<CIB, PLANES><<<dim3(w.used, w.gy, w.gz), 256, wgrad_smem<CIB>(), st>>>(
-        l.dy, l.cout, PLANES ? nullptr : l.in0, PLANES ? 0 : l.c0, l.in1, l.c1, f, g, n, l.H, l.W, w.tpc, part);
+void wgrad_run(const fmbym_unet* u, int v, const Layer& l, const WgradGeom& w, int n, const float* f,
+               const float* g, float* part, cudaStream_t st) {
+    k_wgrad<CIB, PLANES><<<dim3(w.used, w.gy, w.gz), 256, wgrad_smem<CIB>(u->wns[v]), st>>>(
+        l.dy, l.cout, PLANES ? nullptr : l.in0, PLANES ? 0 : l.c0, l.in1, l.c1, f, g, n, l.H, l.W, w.tpc,
+        u->wns[v], part);
 }
 
 // Inputs of layer k for a batch of B (planes for the first layer are set per call).
@@ -361,8 +381,8 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         stats_cap = std::max(stats_cap, px / kTilePx * l.cout);
         bn_cap = std::max(bn_cap, (size_t)4 * u->nsm * l.cout);   // bn_pix_per_cta keeps the slabs at most 4 per SM
         w_cap = std::max(w_cap, (size_t)wgrad_geom(u, l, B).chunks * l.cout * 9 * l.cin);
-        chk(conv_plan(u, l.cout, l.cinp / 8, l.ns_f, l.slots_f));
-        if (!l.planes) chk(conv_plan(u, l.cin, l.coutp / 8, l.ns_d, l.slots_d));
+        chk(conv_plan(u, l.cout, l.cinp / 8, l.H, l.R_f, l.ns_f, l.slots_f));
+        if (!l.planes) chk(conv_plan(u, l.cin, l.coutp / 8, l.H, l.R_d, l.ns_d, l.slots_d));
         if (e == cudaSuccess && (!l.ns_f || (!l.planes && !l.ns_d))) too_big = true;
     }
     u->pooled.assign(L, nullptr);
@@ -517,12 +537,13 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
     }
     auto conv_bn = [&](Layer& l) -> cudaError_t {
         const long long px = (long long)n * l.H * l.W;
-        const int ntiles = (int)(px / kTilePx), nparts = std::min(ntiles, l.slots_f);   // the conv's grid
+        const int tile_px = kTilePx * l.R_f, ntiles = (int)(px / tile_px);
+        const int nparts = std::min(ntiles, l.slots_f);   // the conv's grid
         cudaError_t r = conv_dispatch(u, l, n, false, st, l.y, nullptr, l.cout, 0, 0, training ? u->stats : nullptr);
         if (r != cudaSuccess) return r;
         ++u->launches;
         if (training)
-            k_bn_finalize<<<l.cout, 256, 0, st>>>(u->stats, nparts, l.cout, ntiles, (float)kTilePx,
+            k_bn_finalize<<<l.cout, 256, 0, st>>>(u->stats, nparts, l.cout, ntiles, (float)tile_px,
                                                   u->running + l.rs_off, u->running + l.rs_off + l.cout, l.bn);
         else
             k_bn_eval<<<1, 128, 0, st>>>(u->running + l.rs_off, u->running + l.rs_off + l.cout, l.cout, l.bn);
@@ -607,11 +628,11 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         const WgradGeom w = wgrad_geom(u, l, n);
         u->launches += 2;
         switch (wgrad_variant(l)) {
-            case 0: wgrad_run<8, false>(l, w, n, f, g, u->wpart, st); break;
-            case 1: wgrad_run<16, false>(l, w, n, f, g, u->wpart, st); break;
-            case 2: wgrad_run<32, false>(l, w, n, f, g, u->wpart, st); break;
-            case 3: wgrad_run<64, false>(l, w, n, f, g, u->wpart, st); break;
-            default: wgrad_run<8, true>(l, w, n, f, g, u->wpart, st); break;
+            case 0: wgrad_run<8, false>(u, 0, l, w, n, f, g, u->wpart, st); break;
+            case 1: wgrad_run<16, false>(u, 1, l, w, n, f, g, u->wpart, st); break;
+            case 2: wgrad_run<32, false>(u, 2, l, w, n, f, g, u->wpart, st); break;
+            case 3: wgrad_run<64, false>(u, 3, l, w, n, f, g, u->wpart, st); break;
+            default: wgrad_run<8, true>(u, 4, l, w, n, f, g, u->wpart, st); break;
         }
         const int total = C * 9 * l.cin;
         k_wgrad_reduce<<<(total + 31) / 32, 256, 0, st>>>(u->wpart, w.used, C, l.cin, u->grads + l.w_off);

@@ -76,7 +76,7 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const void* row_addr)
 // row-major.  Output: float32 NHWC split at channel `split`: channels [0, split) go to out0 (row
 // stride split), [split, COUT) to out1 (row stride COUT - split); acc0/acc1 add instead of store.
 // stats (forward only): per CTA and channel (mean, sum of squared deviations) of its outputs: each
-// tile's pair is taken over its 256 pixels and merged into the CTA's running pair by Chan's
+// tile's pair is taken over its 256 R pixels and merged into the CTA's running pair by Chan's
 // update, in tile order.
 //
 // An implicit GEMM on mma.sync.m16n8k16: M = 16 output pixels of a tile row, N = 8 output
@@ -84,28 +84,32 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const void* row_addr)
 // no K.  The CTA is persistent over tiles: the whole weight array sits in shared memory, the
 // input tiles (with halo) arrive by cp.async in the NHWC byte order -- one 16-byte row per pixel
 // and channel group -- through a ring of `nstage` buffers, and ldmatrix reads the A fragments at
-// shifted row addresses (the tap) and the B fragments from the weight rows.
+// shifted row addresses (the tap) and the B fragments from the weight rows.  A CTA tile is 8 R rows
+// x 32 columns (each warp R rows), R = 4 for narrow layers so that the per-tile work outweighs the
+// per-tile bookkeeping.
 __host__ __device__ constexpr int conv_items_padded(int G) { return (9 * G + 1) / 2 * 2; }
-__host__ __device__ inline size_t conv_weight_bytes(int cout, int G) { return (size_t)cout * (conv_items_padded(G) + 1) * 16; }
-__host__ __device__ inline size_t conv_tile_bytes(int G) { return (size_t)G * kHaloPx * 16; }
+__host__ __device__ inline size_t conv_weight_bytes(int cout, int G) {
+    return (size_t)cout * (conv_items_padded(G) + 1) * 16;
+}
+// input tile with halo of a CTA tile of 8 R rows x 32 columns
+__host__ __device__ inline size_t conv_tile_bytes(int G, int R) { return (size_t)G * (8 * R + 2) * kTileW * 16; }
 constexpr int kConvMaxItems = 9 * 16 + 1;
 
-template <int COUT>
+template <int COUT, int R>
 __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in0, int c0, const bf16* __restrict__ in1,
                                                  int c1, const float* __restrict__ pf, const float* __restrict__ pg,
                                                  const bf16* __restrict__ wt, int G, int nstage,
                                                  float* __restrict__ out0, float* __restrict__ out1, int split,
                                                  int acc0, int acc1, float2* __restrict__ stats, int B, int H,
                                                  int W) {
-    constexpr int NT = COUT / 8;
+    constexpr int NT = COUT / 8, TH = 8 * R, HALO = (TH + 2) * kTileW;
     extern __shared__ __align__(128) unsigned char smem_c[];
     __shared__ int item_off[kConvMaxItems];       // per item: group * halo + ky * row + kx (pixels)
-    __shared__ float red[8][COUT];
-    __shared__ float mean_s[COUT];
+    __shared__ float2 wstat[8][COUT];            // per warp (R tile rows): (mean, M2) of each channel
     const int NI = 9 * G, NIp = conv_items_padded(G), WS = NIp + 1;   // weight row stride (odd: no conflicts)
     unsigned char* ws = smem_c;
     unsigned char* ring = smem_c + (size_t)COUT * WS * 16;
-    const size_t TB = conv_tile_bytes(G);
+    const size_t TB = conv_tile_bytes(G, R);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
     for (int i = tid; i < COUT * NIp; i += 256) {
         const int co = i / NIp, it = i % NIp;
@@ -115,35 +119,33 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in0, i
     }
     for (int i = tid; i < NIp; i += 256) {
         const int it = min(i, NI - 1), tap = it / G, grp = it % G;   // the odd pad item repeats a real one
-        item_off[i] = grp * kHaloPx + (tap / 3) * kTileW + tap % 3;   // (its weights are zero)
+        item_off[i] = grp * HALO + (tap / 3) * kTileW + tap % 3;      // (its weights are zero)
     }
-    const int tiles_x = W / kTW, tiles_y = H / kTH, ntiles = B * tiles_x * tiles_y;
+    const int tiles_x = W / kTW, tiles_y = H / TH, tiles_img = tiles_x * tiles_y, ntiles = B * tiles_img;
     const int n = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     auto stage = [&](int k) {   // the k-th tile of this CTA into ring slot k % nstage
         unsigned char* buf = ring + (size_t)(k % nstage) * TB;
         const int tile = blockIdx.x + k * gridDim.x;
-        const int b = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
-        const int ty0 = (rem / tiles_x) * kTH, tx0 = (rem % tiles_x) * kTW;
-        if (pf) {
-            for (int pix = tid; pix < kHaloPx; pix += 256) {
-                const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
+        const int b = tile / tiles_img, rem = tile - b * tiles_img;
+        const int ty = rem / tiles_x;
+        const int ty0 = ty * TH, tx0 = (rem - ty * tiles_x) * kTW;
+        for (int pix = tid; pix < HALO; pix += 256) {
+            const int hy = pix / kTileW;
+            const int y = ty0 + hy - 1, x = tx0 + (pix - hy * kTileW) - 1;
+            const bool inside = y >= 0 && y < H && x >= 0 && x < W;
+            const size_t p = inside ? ((size_t)b * H + y) * W + x : 0;
+            if (pf) {
                 uint4 v = make_uint4(0, 0, 0, 0);
-                if (y >= 0 && y < H && x >= 0 && x < W) {
-                    const size_t p = ((size_t)b * H + y) * W + x;
-                    v.x = pack2(__float2bfloat16_rn(pf[p]), __float2bfloat16_rn(pg[p]));
-                }
+                if (inside) v.x = pack2(__float2bfloat16_rn(pf[p]), __float2bfloat16_rn(pg[p]));
                 *reinterpret_cast<uint4*>(buf + (size_t)pix * 16) = v;
-            }
-        } else {
-            for (int i = tid; i < G * kHaloPx; i += 256) {
-                const int grp = i / kHaloPx, pix = i % kHaloPx;
-                const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
-                const bool inside = y >= 0 && y < H && x >= 0 && x < W;
-                const size_t p = inside ? ((size_t)b * H + y) * W + x : 0;
-                const int ch = grp * 8;
-                const bf16* src = ch < c0 ? in0 + p * c0 + ch : in1 + p * c1 + (ch - c0);
-                cp_async16(buf + (size_t)(grp * kHaloPx + pix) * 16, src, inside);
+            } else {
+                const bf16* s0 = in0 + p * c0;
+                const bf16* s1 = in1 + p * c1 - c0;
+                for (int grp = 0; grp < G; ++grp) {
+                    const int ch = grp * 8;
+                    cp_async16(buf + (size_t)(grp * HALO + pix) * 16, ch < c0 ? s0 + ch : s1 + ch, inside);
+                }
             }
         }
     };
@@ -151,9 +153,9 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in0, i
     // per-lane ldmatrix rows: A matrices (pixels 0-7 | 8-15) x (item 2s | 2s+1); B matrices
     // (channel block n | n+1) x (item 2s | 2s+1), eight output channels each
     const int mi = lane >> 3, r8 = lane & 7;
-    const int a_px = warp * kTileW + (mi & 1) * 8 + r8, a_item = mi >> 1;
-    float run_mean = 0.f, run_m2 = 0.f;   // the CTA's statistics so far (threads tid < COUT)
+    const int a_px = warp * R * kTileW + (mi & 1) * 8 + r8, a_item = mi >> 1;
     const int b_row = (mi >> 1) * 8 + r8, b_item = mi & 1;
+    float run_mean = 0.f, run_m2 = 0.f;   // the CTA's statistics so far (threads tid < COUT)
     for (int k = 0; k < nstage - 1; ++k) {
         if (k < n) stage(k);
         cp_async_commit();
@@ -164,121 +166,131 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in0, i
         cp_async_wait_n(nstage - 1);
         __syncthreads();
         const unsigned char* tb = ring + (size_t)(it % nstage) * TB;
-        float acc[2][NT][4];
+        float acc[R][2][NT][4];
 #pragma unroll
-        for (int m = 0; m < 2; ++m)
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int q = 0; q < NT; ++q)
+            for (int m = 0; m < 2; ++m)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[m][q][j] = 0.f;
+                for (int q = 0; q < NT; ++q)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[r][m][q][j] = 0.f;
         for (int s = 0; s < NIp / 2; ++s) {
-            const int off = item_off[2 * s + a_item] + a_px;
-            uint32_t a[2][4];
-            ldsm_x4(a[0], tb + (size_t)off * 16);
-            ldsm_x4(a[1], tb + (size_t)(off + 16) * 16);
+            const unsigned char* ab = tb + (size_t)(item_off[2 * s + a_item] + a_px) * 16;
+            uint32_t a[R][2][4];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ldsm_x4(a[r][0], ab + (size_t)r * kTileW * 16);
+                ldsm_x4(a[r][1], ab + (size_t)(r * kTileW + 16) * 16);
+            }
 #pragma unroll
             for (int q = 0; q < NT; q += 2) {
                 if (q + 1 < NT) {
                     uint32_t bq[4];
                     ldsm_x4(bq, ws + ((size_t)(q * 8 + b_row) * WS + 2 * s + b_item) * 16);
-                    mma16816(acc[0][q], a[0], bq);
-                    mma16816(acc[1][q], a[1], bq);
-                    mma16816(acc[0][q + 1], a[0], bq + 2);
-                    mma16816(acc[1][q + 1], a[1], bq + 2);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        mma16816(acc[r][0][q], a[r][0], bq);
+                        mma16816(acc[r][1][q], a[r][1], bq);
+                        mma16816(acc[r][0][q + 1], a[r][0], bq + 2);
+                        mma16816(acc[r][1][q + 1], a[r][1], bq + 2);
+                    }
                 } else {
                     uint32_t bq[2];
                     ldsm_x2(bq, ws + ((size_t)(q * 8 + r8) * WS + 2 * s + b_item) * 16);
-                    mma16816(acc[0][q], a[0], bq);
-                    mma16816(acc[1][q], a[1], bq);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        mma16816(acc[r][0][q], a[r][0], bq);
+                        mma16816(acc[r][1][q], a[r][1], bq);
+                    }
                 }
             }
         }
         // epilogue: rows g (+8) of the m-block are pixels, columns 2t (+1) channels
         const int tile = blockIdx.x + it * gridDim.x;
-        const int b = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
-        const int y = (rem / tiles_x) * kTH + warp, tx0 = (rem % tiles_x) * kTW;
+        const int b = tile / tiles_img, rem = tile - b * tiles_img;
+        const int ty = rem / tiles_x;
+        const int y0 = ty * TH + warp * R, tx0 = (rem - ty * tiles_x) * kTW;
 #pragma unroll
-        for (int m = 0; m < 2; ++m) {
+        for (int r = 0; r < R; ++r) {
+            const size_t prow = ((size_t)b * H + y0 + r) * W + tx0;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int x = tx0 + m * 16 + g + 8 * h;
-                const size_t pidx = ((size_t)b * H + y) * W + x;
+            for (int m = 0; m < 2; ++m) {
 #pragma unroll
-                for (int q = 0; q < NT; ++q) {
-                    const int ch = q * 8 + 2 * t;
-                    const float v0 = acc[m][q][2 * h], v1 = acc[m][q][2 * h + 1];
-                    if (ch < split) {
-                        float2* o = reinterpret_cast<float2*>(out0 + pidx * split + ch);
-                        if (acc0) {
-                            const float2 old = *o;
-                            *o = make_float2(old.x + v0, old.y + v1);
+                for (int h = 0; h < 2; ++h) {
+                    const size_t pidx = prow + m * 16 + g + 8 * h;
+#pragma unroll
+                    for (int q = 0; q < NT; ++q) {
+                        const int ch = q * 8 + 2 * t;
+                        const float v0 = acc[r][m][q][2 * h], v1 = acc[r][m][q][2 * h + 1];
+                        if (ch < split) {
+                            float2* o = reinterpret_cast<float2*>(out0 + pidx * split + ch);
+                            if (acc0) {
+                                const float2 old = *o;
+                                *o = make_float2(old.x + v0, old.y + v1);
+                            } else {
+                                *o = make_float2(v0, v1);
+                            }
                         } else {
-                            *o = make_float2(v0, v1);
-                        }
-                    } else {
-                        float2* o = reinterpret_cast<float2*>(out1 + pidx * (COUT - split) + (ch - split));
-                        if (acc1) {
-                            const float2 old = *o;
-                            *o = make_float2(old.x + v0, old.y + v1);
-                        } else {
-                            *o = make_float2(v0, v1);
+                            float2* o = reinterpret_cast<float2*>(out1 + pidx * (COUT - split) + (ch - split));
+                            if (acc1) {
+                                const float2 old = *o;
+                                *o = make_float2(old.x + v0, old.y + v1);
+                            } else {
+                                *o = make_float2(v0, v1);
+                            }
                         }
                     }
                 }
             }
         }
         if (stats) {
-            // per-channel mean and sum of squared deviations over the tile's 256 outputs: lanes with
-            // the same t hold the same channels; reduce over g, then over warps in a fixed order
+            // per channel: each warp's 32 R outputs (its tile rows) give a (mean, M2) pair by
+            // shuffles over g; the 8 warps' pairs (equal counts) give the tile's, which is merged
+            // into the CTA's running pair by Chan's update
+            constexpr float kWarpPx = 32.f * R;
 #pragma unroll
             for (int q = 0; q < NT; ++q) {
-                float s0 = acc[0][q][0] + acc[0][q][2] + acc[1][q][0] + acc[1][q][2];
-                float s1 = acc[0][q][1] + acc[0][q][3] + acc[1][q][1] + acc[1][q][3];
 #pragma unroll
-                for (int o = 4; o < 32; o <<= 1) {
-                    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                }
-                if (g == 0) {
-                    red[warp][q * 8 + 2 * t] = s0;
-                    red[warp][q * 8 + 2 * t + 1] = s1;
+                for (int j = 0; j < 2; ++j) {
+                    float sm = 0.f;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        sm += acc[r][0][q][j] + acc[r][0][q][j + 2] + acc[r][1][q][j] + acc[r][1][q][j + 2];
+#pragma unroll
+                    for (int o = 4; o < 32; o <<= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+                    const float mu = sm * (1.f / kWarpPx);
+                    float m2 = 0.f;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int m = 0; m < 2; ++m)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const float d = acc[r][m][q][2 * h + j] - mu;
+                                m2 = fmaf(d, d, m2);
+                            }
+#pragma unroll
+                    for (int o = 4; o < 32; o <<= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+                    if (g == 0) wstat[warp][q * 8 + 2 * t + j] = make_float2(mu, m2);
                 }
             }
             __syncthreads();
             if (tid < COUT) {
-                float sm = 0.f;
-                for (int w = 0; w < 8; ++w) sm += red[w][tid];
-                mean_s[tid] = sm * (1.f / kTilePx);
-            }
-            __syncthreads();
+                float mu = 0.f;
 #pragma unroll
-            for (int q = 0; q < NT; ++q) {
-                const float mu0 = mean_s[q * 8 + 2 * t], mu1 = mean_s[q * 8 + 2 * t + 1];
-                float q0 = 0.f, q1 = 0.f;
+                for (int w = 0; w < 8; ++w) mu += wstat[w][tid].x;
+                mu *= 0.125f;
+                float m2 = 0.f;
 #pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    q0 += (acc[m][q][0] - mu0) * (acc[m][q][0] - mu0) + (acc[m][q][2] - mu0) * (acc[m][q][2] - mu0);
-                    q1 += (acc[m][q][1] - mu1) * (acc[m][q][1] - mu1) + (acc[m][q][3] - mu1) * (acc[m][q][3] - mu1);
+                for (int w = 0; w < 8; ++w) {
+                    const float d = wstat[w][tid].x - mu;
+                    m2 += wstat[w][tid].y + kWarpPx * d * d;
                 }
-#pragma unroll
-                for (int o = 4; o < 32; o <<= 1) {
-                    q0 += __shfl_xor_sync(0xffffffffu, q0, o);
-                    q1 += __shfl_xor_sync(0xffffffffu, q1, o);
-                }
-                __syncthreads();
-                if (g == 0) {
-                    red[warp][q * 8 + 2 * t] = q0;
-                    red[warp][q * 8 + 2 * t + 1] = q1;
-                }
-            }
-            __syncthreads();
-            if (tid < COUT) {
-                float sm = 0.f;
-                for (int w = 0; w < 8; ++w) sm += red[w][tid];
-                // merge (kTilePx, mean_s, sm) into (it * kTilePx, run_mean, run_m2)
-                const float d = mean_s[tid] - run_mean, f = 1.f / (float)(it + 1);
+                // merge (8 kWarpPx, mu, m2) into (it * 8 kWarpPx, run_mean, run_m2)
+                const float d = mu - run_mean, f = 1.f / (float)(it + 1);
                 run_mean = fmaf(d, f, run_mean);
-                run_m2 += sm + d * d * (float)kTilePx * (float)it * f;
+                run_m2 += m2 + d * d * (8.f * kWarpPx) * (float)it * f;
             }
         }
         __syncthreads();
@@ -767,15 +779,17 @@ __global__ void __launch_bounds__(256) k_sum_parts(const float* __restrict__ par
 template <int CIB>
 __host__ __device__ constexpr size_t wgrad_buf_bytes() { return (size_t)(2 * kTilePx + (CIB / 8) * kHaloPx) * 16; }
 template <int CIB>
-__host__ __device__ constexpr size_t wgrad_smem() {
-    return 2 * wgrad_buf_bytes<CIB>() > (size_t)8 * 36 * 32 * 4 ? 2 * wgrad_buf_bytes<CIB>() : (size_t)8 * 36 * 32 * 4;
+__host__ __device__ constexpr size_t wgrad_smem(int nstage) {   // the ring, or the row-group sums
+    return nstage * wgrad_buf_bytes<CIB>() > (size_t)8 * 36 * 32 * 4 ? nstage * wgrad_buf_bytes<CIB>()
+                                                                      : (size_t)8 * 36 * 32 * 4;
 }
 
 template <int CIB, bool PLANES>
 __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int cout, const bf16* __restrict__ in0,
                                                int c0, const bf16* __restrict__ in1, int c1,
                                                const float* __restrict__ pf, const float* __restrict__ pg, int B,
-                                               int H, int W, int tiles_per_chunk, float* __restrict__ part) {
+                                               int H, int W, int tiles_per_chunk, int nstage,
+                                               float* __restrict__ part) {
     constexpr int NG = CIB / 8, NRG = 8 / NG;
     constexpr size_t BUF = wgrad_buf_bytes<CIB>();
     extern __shared__ __align__(128) unsigned char smem_w[];
@@ -788,14 +802,14 @@ __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int 
     const int tiles_x = W / kTW, tiles_y = H / kTH, ntiles = B * tiles_x * tiles_y;
     const int first = blockIdx.x * tiles_per_chunk, n = min(tiles_per_chunk, ntiles - first);
 
-    if (cog == 1)  // the upper 8 rows of the A operand stay zero in both buffers
+    if (cog == 1)  // the upper 8 rows of the A operand stay zero in every ring slot
         for (int i = tid; i < kTilePx; i += 256)
-#pragma unroll
-            for (int bsel = 0; bsel < 2; ++bsel)
+            for (int bsel = 0; bsel < nstage; ++bsel)
                 *reinterpret_cast<uint4*>(smem_w + bsel * BUF + (size_t)(kTilePx + i) * 16) = make_uint4(0, 0, 0, 0);
 
-    auto stage = [&](int tile, int bsel) {
-        unsigned char* buf = smem_w + bsel * BUF;
+    auto stage = [&](int k) {   // the k-th tile of this CTA's chunk into ring slot k % nstage
+        const int tile = first + k;
+        unsigned char* buf = smem_w + (k % nstage) * BUF;
         const int b = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
         const int ty0 = (rem / tiles_x) * kTH, tx0 = (rem % tiles_x) * kTW;
         for (int i = tid; i < cog * kTilePx; i += 256) {
@@ -815,14 +829,16 @@ __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int 
                 *reinterpret_cast<uint4*>(ins + (size_t)pix * 16) = v;
             }
         } else {
-            for (int i = tid; i < ngr * kHaloPx; i += 256) {
-                const int grp = i / kHaloPx, pix = i % kHaloPx;
+            for (int pix = tid; pix < kHaloPx; pix += 256) {
                 const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
                 const bool inside = y >= 0 && y < H && x >= 0 && x < W;
                 const size_t p = inside ? ((size_t)b * H + y) * W + x : 0;
-                const int c = ci_base + grp * 8;
-                const bf16* src = c < c0 ? in0 + p * c0 + c : in1 + p * c1 + (c - c0);
-                cp_async16(ins + (size_t)(grp * kHaloPx + pix) * 16, src, inside);
+                const bf16* s0 = in0 + p * c0;
+                const bf16* s1 = in1 + p * c1 - c0;
+                for (int grp = 0; grp < ngr; ++grp) {
+                    const int c = ci_base + grp * 8;
+                    cp_async16(ins + (size_t)(grp * kHaloPx + pix) * 16, c < c0 ? s0 + c : s1 + c, inside);
+                }
             }
         }
     };
@@ -835,14 +851,16 @@ __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int 
 
     // ldmatrix row addresses: A matrices (out group lane/8 & 1, pixels + 8 (lane/8 >> 1)); B: pixel lane
     const int a_row = ((lane >> 3) & 1) * kTilePx + ((lane >> 4) << 3) + (lane & 7);
-    stage(first, 0);
-    cp_async_commit();
-    for (int it = 0; it < n; ++it) {
-        if (it + 1 < n) stage(first + it + 1, (it + 1) & 1);
+    for (int k = 0; k < nstage - 1; ++k) {
+        if (k < n) stage(k);
         cp_async_commit();
-        cp_async_wait1();
+    }
+    for (int it = 0; it < n; ++it) {
+        if (it + nstage - 1 < n) stage(it + nstage - 1);
+        cp_async_commit();
+        cp_async_wait_n(nstage - 1);
         __syncthreads();
-        const unsigned char* buf = smem_w + (it & 1) * BUF;
+        const unsigned char* buf = smem_w + (it % nstage) * BUF;
         const unsigned char* ins = buf + 2 * kTilePx * 16 + (size_t)wc * kHaloPx * 16;
         if (wc < ngr) {
             for (int row = wr; row < kTH; row += NRG) {
