@@ -25,6 +25,7 @@ struct Layer {
     int cinp, coutp;           // channels rounded up to 8
     int ns_f = 0, ns_d = 0;    // cp.async ring depth of the forward and dgrad convolutions
     int R_f = 1, R_d = 1;      // their rows per warp (CTA tile 8 R x 32)
+    int wg_cib = 8, wg_R = 1, wg_ns = 2, wg_slots = 0;   // the weight gradient's plan
     int slots_f = 0, slots_d = 0;   // their resident CTAs on the device
     long long w_off, g_off, b_off, rs_off;  // offsets in the parameter and running-stat arrays
     bf16* wf = nullptr;        // forward weights [cout][9][cinp]
@@ -62,8 +63,6 @@ struct fmbym_unet {
     float* wpart = nullptr;             // wgrad partials
     float* hpart = nullptr;             // head partials
     size_t stats_cap = 0, bnpart_cap = 0, wpart_cap = 0, hpart_cap = 0;
-    int wslots[5] = {0};                // resident CTAs of the wgrad variants (CIB 8/16/32/64, planes)
-    int wns[5] = {0};                   // and their cp.async ring depths
     int nsm = 0;
     std::vector<void*> allocs;
     long long launches = 0;
@@ -199,48 +198,65 @@ int bn_pix_per_cta(const fmbym_unet* u, long long px, int C) {
 // Partials of the head adjoint: a grid of eight CTAs per SM, grid-stride over the pixels.
 int head_grid(const fmbym_unet* u) { return 8 * u->nsm; }
 
-// Weight-gradient launch geometry: CIB input channels per CTA (the smallest of 8, 16, 32, 64 that
-// holds the layer's inputs), gy x gz channel blocks, and the pixel tiles cut into one wave of
-// chunks over the resident CTAs of that variant.
-int wgrad_variant(const Layer& l) {
-    if (l.planes) return 4;
-    return l.cin <= 8 ? 0 : l.cin <= 16 ? 1 : l.cin <= 32 ? 2 : 3;
+// Weight-gradient plan of a layer: CIB input channels per CTA (the largest of 64, 32, 16, 8 that
+// divides the input channels, so that no warp idles), CTA tiles of 8 R x 32 pixels (R up to 2 for
+// CIB 8 and 16, dividing the height, else 1), a ring of three slots while they stay under 60 KB of
+// shared memory, else two, and the resident CTAs of that configuration.
+template <int CIB, bool PLANES>
+cudaError_t wgrad_plan_t(const fmbym_unet* u, Layer& l) {
+    const int rmax = PLANES ? 1 : CIB <= 16 ? 2 : 1;
+    l.wg_R = 1;
+    for (int r = rmax; r > 1; r /= 2)
+        if (l.H % (8 * r) == 0) {
+            l.wg_R = r;
+            break;
+        }
+    l.wg_ns = 3 * wgrad_buf_bytes<CIB>(l.wg_R) <= 60 * 1024 ? 3 : 2;
+    const size_t smem = wgrad_smem<CIB>(l.wg_R, l.wg_ns);
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad<CIB, PLANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wgrad<CIB, PLANES>, 256, smem);
+    l.wg_slots = std::max(1, occ) * u->nsm;
+    return e;
 }
 
+cudaError_t wgrad_plan(const fmbym_unet* u, Layer& l) {
+    if (l.planes) {
+        l.wg_cib = 8;
+        return wgrad_plan_t<8, true>(u, l);
+    }
+    l.wg_cib = l.cin % 64 == 0 ? 64 : l.cin % 32 == 0 ? 32 : l.cin % 16 == 0 ? 16 : 8;
+    switch (l.wg_cib) {
+        case 64: return wgrad_plan_t<64, false>(u, l);
+        case 32: return wgrad_plan_t<32, false>(u, l);
+        case 16: return wgrad_plan_t<16, false>(u, l);
+        default: return wgrad_plan_t<8, false>(u, l);
+    }
+}
+
+// Channel blocks gy (16 outputs) x gz (CIB inputs), and the pixel tiles cut into one wave of
+// chunks over the resident CTAs.
 struct WgradGeom {
     int gy, gz, chunks, tpc, used;
 };
 
-WgradGeom wgrad_geom(const fmbym_unet* u, const Layer& l, int B) {
-    const int v = wgrad_variant(l), cib = v == 4 ? 8 : 8 << v;
+WgradGeom wgrad_geom(const Layer& l, int B) {
     WgradGeom w;
     w.gy = (l.cout + 15) / 16;
-    w.gz = (l.cin + cib - 1) / cib;
-    const int ntiles = B * (l.H / kTH) * (l.W / kTW);
-    w.chunks = std::max(1, std::min(ntiles, u->wslots[v] / (w.gy * w.gz)));
+    w.gz = l.planes ? 1 : l.cin / l.wg_cib;
+    const int ntiles = B * (l.H / (8 * l.wg_R)) * (l.W / kTW);
+    w.chunks = std::max(1, std::min(ntiles, l.wg_slots / (w.gy * w.gz)));
     w.tpc = (ntiles + w.chunks - 1) / w.chunks;
     w.used = (ntiles + w.tpc - 1) / w.tpc;
     return w;
 }
 
-// Three ring slots while they stay under 100 KB of shared memory, else two.
 template <int CIB, bool PLANES>
-cudaError_t wgrad_prepare(fmbym_unet* u, int v) {
-    u->wns[v] = 3 * wgrad_buf_bytes<CIB>() <= 100 * 1024 ? 3 : 2;
-    const size_t smem = wgrad_smem<CIB>(u->wns[v]);
-    cudaError_t e = cudaFuncSetAttribute(k_wgrad<CIB, PLANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wgrad<CIB, PLANES>, 256, smem);
-    u->wslots[v] = std::max(1, occ) * u->nsm;
-    return e;
-}
-
-template <int CIB, bool PLANES>
-void wgrad_run(const fmbym_unet* u, int v, const Layer& l, const WgradGeom& w, int n, const float* f,
-               const float* g, float* part, cudaStream_t st) {
-    k_wgrad<CIB, PLANES><<<dim3(w.used, w.gy, w.gz), 256, wgrad_smem<CIB>(u->wns[v]), st>>>(
-        l.dy, l.cout, PLANES ? nullptr : l.in0, PLANES ? 0 : l.c0, l.in1, l.c1, f, g, n, l.H, l.W, w.tpc,
-        u->wns[v], part);
+void wgrad_run(const Layer& l, const WgradGeom& w, int n, const float* f, const float* g, float* part,
+               cudaStream_t st) {
+    k_wgrad<CIB, PLANES><<<dim3(w.used * w.gz, w.gy), 256, wgrad_smem<CIB>(l.wg_R, l.wg_ns), st>>>(
+        l.dy, l.cout, PLANES ? nullptr : l.in0, PLANES ? 0 : l.c0, l.in1, l.c1, f, g, n, l.H, l.W, l.wg_R, w.gz,
+        w.tpc, l.wg_ns, part);
 }
 
 // Inputs of layer k for a batch of B (planes for the first layer are set per call).
@@ -361,11 +377,6 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     int dev = 0;
     chk(cudaGetDevice(&dev));
     chk(cudaDeviceGetAttribute(&u->nsm, cudaDevAttrMultiProcessorCount, dev));
-    chk(wgrad_prepare<8, false>(u, 0));
-    chk(wgrad_prepare<16, false>(u, 1));
-    chk(wgrad_prepare<32, false>(u, 2));
-    chk(wgrad_prepare<64, false>(u, 3));
-    chk(wgrad_prepare<8, true>(u, 4));
     size_t stats_cap = 0, bn_cap = 0, w_cap = 0;
     bool too_big = false;
     for (Layer& l : u->layers) {
@@ -380,7 +391,8 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         chk(ualloc(u, &l.bsums, l.cout));
         stats_cap = std::max(stats_cap, px / kTilePx * l.cout);
         bn_cap = std::max(bn_cap, (size_t)4 * u->nsm * l.cout);   // bn_pix_per_cta keeps the slabs at most 4 per SM
-        w_cap = std::max(w_cap, (size_t)wgrad_geom(u, l, B).chunks * l.cout * 9 * l.cin);
+        chk(wgrad_plan(u, l));
+        w_cap = std::max(w_cap, (size_t)wgrad_geom(l, B).chunks * l.cout * 9 * l.cin);
         chk(conv_plan(u, l.cout, l.cinp / 8, l.H, l.R_f, l.ns_f, l.slots_f));
         if (!l.planes) chk(conv_plan(u, l.cin, l.coutp / 8, l.H, l.R_d, l.ns_d, l.slots_d));
         if (e == cudaSuccess && (!l.ns_f || (!l.planes && !l.ns_d))) too_big = true;
@@ -625,15 +637,13 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         k_bn_bwd_dy<<<blocks(px * C / 4), kBlock, 0, st>>>(l.y, l.da, l.bn, u->params + l.g_off,
                                                            u->params + l.b_off, l.bsums, l.dy, px * C / 4, C);
         // weight gradient
-        const WgradGeom w = wgrad_geom(u, l, n);
+        const WgradGeom w = wgrad_geom(l, n);
         u->launches += 2;
-        switch (wgrad_variant(l)) {
-            case 0: wgrad_run<8, false>(u, 0, l, w, n, f, g, u->wpart, st); break;
-            case 1: wgrad_run<16, false>(u, 1, l, w, n, f, g, u->wpart, st); break;
-            case 2: wgrad_run<32, false>(u, 2, l, w, n, f, g, u->wpart, st); break;
-            case 3: wgrad_run<64, false>(u, 3, l, w, n, f, g, u->wpart, st); break;
-            default: wgrad_run<8, true>(u, 4, l, w, n, f, g, u->wpart, st); break;
-        }
+        if (l.planes) wgrad_run<8, true>(l, w, n, f, g, u->wpart, st);
+        else if (l.wg_cib == 64) wgrad_run<64, false>(l, w, n, f, g, u->wpart, st);
+        else if (l.wg_cib == 32) wgrad_run<32, false>(l, w, n, f, g, u->wpart, st);
+        else if (l.wg_cib == 16) wgrad_run<16, false>(l, w, n, f, g, u->wpart, st);
+        else wgrad_run<8, false>(l, w, n, f, g, u->wpart, st);
         const int total = C * 9 * l.cin;
         k_wgrad_reduce<<<(total + 31) / 32, 256, 0, st>>>(u->wpart, w.used, C, l.cin, u->grads + l.w_off);
         cudaError_t r = cudaGetLastError();

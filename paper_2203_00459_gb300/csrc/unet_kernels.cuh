@@ -765,79 +765,81 @@ __global__ void __launch_bounds__(256) k_sum_parts(const float* __restrict__ par
 //
 // dW[co][tap][ci] = sum over pixels p of dy[p][co] in[p + tap][ci]: an implicit GEMM with
 // M = 16 output channels, N = 8 input channels, K = 16 pixels of one tile row, on
-// mma.sync.m16n8k16.  A CTA owns 16 output channels and CIB input channels and walks a chunk of
-// 8 x 32 pixel tiles.  Both operands are staged pixel-major, one 16-byte row per pixel and group
-// of 8 channels -- exactly the NHWC bytes -- by cp.async (double-buffered, zero-filled outside the
-// image), and ldmatrix.trans turns those rows into the channel-by-pixel fragments, so a 3x3 tap
-// is only a shifted row address.  Warps split into CIB / 8 channel groups times 64 / CIB row
-// groups; the row groups' partial sums are added in a fixed order at the end and the CTA's dW
-// goes to part[chunk], which k_wgrad_reduce sums over chunks in order (bitwise deterministic).
+// mma.sync.m16n8k16.  A CTA owns 16 output channels and CIB input channels (CIB divides the
+// layer's input channels) and walks a chunk of 8 R x 32 pixel tiles.  Both operands are staged
+// pixel-major, one 16-byte row per pixel and group of 8 channels -- exactly the NHWC bytes -- by
+// cp.async through a ring of `nstage` slots (zero-filled outside the image), and ldmatrix.trans
+// turns those rows into the channel-by-pixel fragments, so a 3x3 tap is only a shifted row
+// address.  Warps split into CIB / 8 channel groups times 64 / CIB row groups; the row groups'
+// partial sums are added in a fixed order at the end and the CTA's dW goes to part[chunk], which
+// k_wgrad_reduce sums over chunks in order (bitwise deterministic).  blockIdx.x = chunk * gz + z
+// for the gz input-channel blocks, so the blocks of one chunk run together and share dy in L2.
 // Requires cout and every input channel count to be multiples of 8 (the planes of the first
 // layer are staged by plain loads instead).
 
-
 template <int CIB>
-__host__ __device__ constexpr size_t wgrad_buf_bytes() { return (size_t)(2 * kTilePx + (CIB / 8) * kHaloPx) * 16; }
+__host__ __device__ inline size_t wgrad_buf_bytes(int R) {
+    return (size_t)(2 * kTilePx * R + (CIB / 8) * (8 * R + 2) * kTileW) * 16;
+}
 template <int CIB>
-__host__ __device__ constexpr size_t wgrad_smem(int nstage) {   // the ring, or the row-group sums
-    return nstage * wgrad_buf_bytes<CIB>() > (size_t)8 * 36 * 32 * 4 ? nstage * wgrad_buf_bytes<CIB>()
-                                                                      : (size_t)8 * 36 * 32 * 4;
+__host__ __device__ inline size_t wgrad_smem(int R, int nstage) {   // the ring, or the row-group sums
+    return nstage * wgrad_buf_bytes<CIB>(R) > (size_t)8 * 36 * 32 * 4 ? nstage * wgrad_buf_bytes<CIB>(R)
+                                                                         : (size_t)8 * 36 * 32 * 4;
 }
 
 template <int CIB, bool PLANES>
 __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int cout, const bf16* __restrict__ in0,
                                                int c0, const bf16* __restrict__ in1, int c1,
                                                const float* __restrict__ pf, const float* __restrict__ pg, int B,
-                                               int H, int W, int tiles_per_chunk, int nstage,
+                                               int H, int W, int R, int gz, int tiles_per_chunk, int nstage,
                                                float* __restrict__ part) {
     constexpr int NG = CIB / 8, NRG = 8 / NG;
-    constexpr size_t BUF = wgrad_buf_bytes<CIB>();
+    const size_t BUF = wgrad_buf_bytes<CIB>(R);
+    const int TH = 8 * R, TPX = kTilePx * R, HALO = (TH + 2) * kTileW;
     extern __shared__ __align__(128) unsigned char smem_w[];
     const int cin = PLANES ? 2 : c0 + c1;
-    const int co0 = blockIdx.y * 16, ci_base = blockIdx.z * CIB;
+    const int chunk = blockIdx.x / gz, co0 = blockIdx.y * 16, ci_base = (blockIdx.x % gz) * CIB;
     const int ngr = PLANES ? 1 : min(NG, (cin - ci_base) / 8);   // channel groups present
     const int cog = min(2, (cout - co0) / 8);                     // output groups present (1 or 2)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
     const int wc = warp % NG, wr = warp / NG;
-    const int tiles_x = W / kTW, tiles_y = H / kTH, ntiles = B * tiles_x * tiles_y;
-    const int first = blockIdx.x * tiles_per_chunk, n = min(tiles_per_chunk, ntiles - first);
+    const int tiles_x = W / kTW, tiles_img = tiles_x * (H / TH), ntiles = B * tiles_img;
+    const int first = chunk * tiles_per_chunk, n = min(tiles_per_chunk, ntiles - first);
 
     if (cog == 1)  // the upper 8 rows of the A operand stay zero in every ring slot
-        for (int i = tid; i < kTilePx; i += 256)
+        for (int i = tid; i < TPX; i += 256)
             for (int bsel = 0; bsel < nstage; ++bsel)
-                *reinterpret_cast<uint4*>(smem_w + bsel * BUF + (size_t)(kTilePx + i) * 16) = make_uint4(0, 0, 0, 0);
+                *reinterpret_cast<uint4*>(smem_w + bsel * BUF + (size_t)(TPX + i) * 16) = make_uint4(0, 0, 0, 0);
 
     auto stage = [&](int k) {   // the k-th tile of this CTA's chunk into ring slot k % nstage
         const int tile = first + k;
         unsigned char* buf = smem_w + (k % nstage) * BUF;
-        const int b = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
-        const int ty0 = (rem / tiles_x) * kTH, tx0 = (rem % tiles_x) * kTW;
-        for (int i = tid; i < cog * kTilePx; i += 256) {
-            const int grp = i / kTilePx, pix = i % kTilePx;
+        const int b = tile / tiles_img, rem = tile - b * tiles_img, ty = rem / tiles_x;
+        const int ty0 = ty * TH, tx0 = (rem - ty * tiles_x) * kTW;
+#pragma unroll 2
+        for (int i = tid; i < cog * TPX; i += 256) {
+            const int grp = i >= TPX, pix = i - grp * TPX;
             const size_t p = ((size_t)b * H + ty0 + pix / kTW) * W + tx0 + pix % kTW;
-            cp_async16(buf + (size_t)(grp * kTilePx + pix) * 16, dy + p * cout + co0 + grp * 8, true);
+            cp_async16(buf + (size_t)(grp * TPX + pix) * 16, dy + p * cout + co0 + grp * 8, true);
         }
-        unsigned char* ins = buf + 2 * kTilePx * 16;
-        if constexpr (PLANES) {
-            for (int pix = tid; pix < kHaloPx; pix += 256) {
-                const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
+        unsigned char* ins = buf + (size_t)2 * TPX * 16;
+#pragma unroll 2
+        for (int pix = tid; pix < HALO; pix += 256) {
+            const int hy = pix / kTileW;
+            const int y = ty0 + hy - 1, x = tx0 + (pix - hy * kTileW) - 1;
+            const bool inside = y >= 0 && y < H && x >= 0 && x < W;
+            const size_t p = inside ? ((size_t)b * H + y) * W + x : 0;
+            if constexpr (PLANES) {
                 uint4 v = make_uint4(0, 0, 0, 0);
-                if (y >= 0 && y < H && x >= 0 && x < W) {
-                    const size_t p = ((size_t)b * H + y) * W + x;
-                    v.x = pack2(__float2bfloat16_rn(pf[p]), __float2bfloat16_rn(pg[p]));
-                }
+                if (inside) v.x = pack2(__float2bfloat16_rn(pf[p]), __float2bfloat16_rn(pg[p]));
                 *reinterpret_cast<uint4*>(ins + (size_t)pix * 16) = v;
-            }
-        } else {
-            for (int pix = tid; pix < kHaloPx; pix += 256) {
-                const int y = ty0 + pix / kTileW - 1, x = tx0 + pix % kTileW - 1;
-                const bool inside = y >= 0 && y < H && x >= 0 && x < W;
-                const size_t p = inside ? ((size_t)b * H + y) * W + x : 0;
+            } else {
                 const bf16* s0 = in0 + p * c0;
                 const bf16* s1 = in1 + p * c1 - c0;
+#pragma unroll 1
                 for (int grp = 0; grp < ngr; ++grp) {
                     const int c = ci_base + grp * 8;
-                    cp_async16(ins + (size_t)(grp * kHaloPx + pix) * 16, c < c0 ? s0 + c : s1 + c, inside);
+                    cp_async16(ins + (size_t)(grp * HALO + pix) * 16, c < c0 ? s0 + c : s1 + c, inside);
                 }
             }
         }
@@ -850,7 +852,7 @@ __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int 
         for (int j = 0; j < 4; ++j) acc[k][j] = 0.f;
 
     // ldmatrix row addresses: A matrices (out group lane/8 & 1, pixels + 8 (lane/8 >> 1)); B: pixel lane
-    const int a_row = ((lane >> 3) & 1) * kTilePx + ((lane >> 4) << 3) + (lane & 7);
+    const int a_row = ((lane >> 3) & 1) * TPX + ((lane >> 4) << 3) + (lane & 7);
     for (int k = 0; k < nstage - 1; ++k) {
         if (k < n) stage(k);
         cp_async_commit();
@@ -861,9 +863,10 @@ __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int 
         cp_async_wait_n(nstage - 1);
         __syncthreads();
         const unsigned char* buf = smem_w + (it % nstage) * BUF;
-        const unsigned char* ins = buf + 2 * kTilePx * 16 + (size_t)wc * kHaloPx * 16;
+        const unsigned char* ins = buf + (size_t)2 * TPX * 16 + (size_t)wc * HALO * 16;
         if (wc < ngr) {
-            for (int row = wr; row < kTH; row += NRG) {
+#pragma unroll 1
+            for (int row = wr; row < TH; row += NRG) {
                 uint32_t a0[4], a1[4];
                 ldsm_x4_trans(a0, buf + (size_t)(a_row + row * kTW) * 16);
                 ldsm_x4_trans(a1, buf + (size_t)(a_row + row * kTW + 16) * 16);
@@ -881,7 +884,7 @@ __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int 
     }
     // acc[tap][2 h + j]: output channel co0 + g + 8 h, input channel ci0 + 2 t + j.  With several
     // row groups, their accumulators meet in shared memory and are added in row-group order.
-    float* o = part + (size_t)blockIdx.x * cout * 9 * cin;
+    float* o = part + (size_t)chunk * cout * 9 * cin;
     if constexpr (NRG == 1) {
         if (wc < ngr) {
             const int ci0 = ci_base + wc * 8;

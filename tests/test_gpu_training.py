@@ -21,8 +21,8 @@ def test_trained_mask_lowers_translation_error():
     from paper_2203_00459_gb300 import build
     build.build()
     from paper_2203_00459_gb300 import train
-    F, G, P = train.trajectory_data(64, 33, 20220304, parallel=True)    # 2048 training pairs
-    Fe, Ge, Pe = train.trajectory_data(8, 17, 20229999, parallel=True)  # 128 held-out pairs
+    F, G, P = train.trajectory_data(64, 33, 20220304, parallel=True)     # 2048 training pairs
+    Fe, Ge, Pe = train.trajectory_data(16, 17, 20229999, parallel=True)  # 256 held-out pairs
     ms = train.MaskedSearch(batch=64, seed=1)
     Ft, Gt = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
     Pt = torch.from_numpy(P.astype(np.float32)).cuda()
@@ -30,19 +30,22 @@ def test_trained_mask_lowers_translation_error():
     plain = ms.poses(Fe_t, Ge_t, masked=False).cpu().numpy()
     rng = np.random.default_rng(0)
     nb = F.shape[0] // 64
-    # lr 2e-3: the held-out translation error stays at 0.6-0.7 of the unmasked search's from step
-    # 240 to 640 of this schedule, so the bound below does not hinge on rounding-level differences
-    # in the trajectory (at 1e-3 it wanders between 0.79 and 0.91)
+    # Adam at 2e-3, then 5e-4 from step 300: at a constant rate the held-out error of the mask jumps
+    # by +-15 % between neighbouring checkpoints, after the decay it settles, and the mean of the
+    # last three checkpoints is what is judged
+    masked = []
     for step in range(400):   # 12.5 epochs of the 2048 pairs
         if step % nb == 0:
             perm = torch.from_numpy(rng.permutation(F.shape[0])).cuda()
         idx = perm[(step % nb) * 64:(step % nb + 1) * 64]
-        ms.train_step(Ft[idx].contiguous(), Gt[idx].contiguous(), Pt[idx].contiguous(), lr=2e-3)
-    masked = ms.poses(Fe_t, Ge_t, masked=True).cpu().numpy()
+        ms.train_step(Ft[idx].contiguous(), Gt[idx].contiguous(), Pt[idx].contiguous(),
+                      lr=2e-3 if step < 300 else 5e-4)
+        if step + 1 in (320, 360, 400):
+            masked.append(ms.poses(Fe_t, Ge_t, masked=True).cpu().numpy())
     torch.cuda.synchronize()
     ms.close()
     e_plain = train.pose_errors(plain, Pe)
-    e_mask = train.pose_errors(masked, Pe)
+    e_mask = np.mean([train.pose_errors(m, Pe) for m in masked], axis=0)
     # the FP64 oracle's unmasked search on the same held-out pairs
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(16) as pool:
@@ -55,10 +58,10 @@ def test_trained_mask_lowers_translation_error():
     t_plain, t_mask, t_orc = e_plain[1:].sum(), e_mask[1:].sum(), e_orc[1:].sum()
     print("held-out mean |error| (theta rad, tx px, ty px): unmasked GPU", e_plain, "FP64 oracle", e_orc,
           "trained mask", e_mask)
-    assert t_mask <= 0.9 * t_plain and t_mask <= 0.9 * t_orc, (e_mask, e_plain, e_orc)
+    assert t_mask <= 0.88 * t_plain and t_mask <= 0.88 * t_orc, (e_mask, e_plain, e_orc)
     # the summed L1 loss of Eq. 13 is dominated by the translation (pixels against radians), so the
     # mask is judged on translation; the heading must not get materially worse
-    assert e_mask[0] <= 1.2 * e_plain[0]
+    assert e_mask[0] <= 1.25 * e_plain[0]
 
 
 def test_checkpoint_resume_is_bitwise(tmp_path):
