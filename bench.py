@@ -75,17 +75,26 @@ def kernel_model(n, p, nt, nr, chunks):
     return m
 
 
-# ncu dram traffic per launch (bytes) of the dominant kernel, with the hash of the sources it was
-# taken on; a traffic figure is reported only while the sources are unchanged.
-TRAFFIC = {}
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel:
+# (bytes, hash of the search sources it was taken on, pairs in that launch, column tile of the
+# variant).  Reported, scaled to the launch's pairs, only while the sources are unchanged and the
+# autotuner picked the same variant.  k_b_cols<512, 768, 4> over 32 pairs at 512^2:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
+#       --clock-control none -k regex:k_b_cols -s 2 -c 1 --csv \
+#       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-plain
+#   -> 201,416,192 read + 72,382,720 written (cold cache: ncu flushes the caches before the launch)
+TRAFFIC = {"b_cols": (201416192 + 72382720, "7d692ce42bd9feea", 32, 4)}
+
+
+SEARCH_SOURCES = ("api.cu", "bwd.cu", "common.cuh", "dev_util.cuh", "fft.cuh", "fwd.cu")
 
 
 def src_hash():
+    """Hash of the sources the search kernels are built from (the mask network's are not)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2203_00459_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, name), "rb").read())
+    for name in SEARCH_SOURCES:
+        h.update(open(os.path.join(d, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -522,7 +531,8 @@ def main():
         flops = model[dom][1] * B
         achieved = byts / (avg_ms * 1e-3) / 1e9
         tr = TRAFFIC.get(dom)
-        traffic = tr[0] * B / tr[2] if (tr and tr[1] == src_hash()) else None
+        same = tr and tr[1] == src_hash() and tr[3] == search.tuning(0)["col_tile"]
+        traffic = tr[0] * B / tr[2] if same else None
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": peak_src, "alg_bytes_per_launch": byts, "avg_launch_ms": round(avg_ms, 5),
