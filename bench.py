@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwd", "fwdbwd"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "mixed", "masked256"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "mixed", "masked256", "masked256_tab2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     return ap.parse_args()
@@ -362,14 +362,16 @@ def exhaustive_comparison(pairs=64, steps=3, warmup=1):
 
 def run_masked256(args):
     """The learned-mask training step at 256^2, batch 64: U-Net forward, masked search, L1 pose loss,
-    search adjoint, U-Net adjoint and Adam."""
+    search adjoint, U-Net adjoint and Adam.  `masked256` uses the 4-level 8..64-channel net,
+    `masked256_tab2` the paper's 6-level 8..256-channel net of Tab. II."""
     import numpy as np
     import torch
     from paper_2203_00459_gb300 import build
     build.build()
     from paper_2203_00459_gb300 import train
     F, G, P = train.trajectory_data(2, 33, 20220304)
-    ms = train.MaskedSearch(batch=64)
+    channels = (8, 16, 32, 64, 128, 256) if args.workload == "masked256_tab2" else (8, 16, 32, 64)
+    ms = train.MaskedSearch(batch=64, channels=channels)
     Ft, Gt = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
     Pt = torch.from_numpy(P.astype(np.float32)).cuda()
     for _ in range(args.warmup):
@@ -386,7 +388,7 @@ def run_masked256(args):
             "value": 64 / (ms_step * 1e-3), "unit": "scan-pairs/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 mask, f32 search", "data": "synthetic",
-            "config": {"workload": "masked256", "n": 256, "batch": 64, "mask_channels": [8, 16, 32, 64]}}
+            "config": {"workload": args.workload, "n": 256, "batch": 64, "mask_channels": list(channels)}}
     ms.close()
     print(json.dumps(line), flush=True)
 
@@ -396,7 +398,7 @@ def main():
     from paper_2203_00459_gb300 import synth
     if args.workload == "mixed" and args.impl == "ours":
         return run_mixed(args)
-    if args.workload == "masked256" and args.impl == "ours":
+    if args.workload in ("masked256", "masked256_tab2") and args.impl == "ours":
         return run_masked256(args)
     spec = dict(synth.WORKLOADS[args.workload if args.workload in synth.WORKLOADS else "batch256"])
     from paper_2203_00459_gb300 import replicas

@@ -269,9 +269,11 @@ const char* fmbym_noalloc_last_error(void);
  * --------------------------------------------------------------------------------------------- */
 typedef struct fmbym_unet fmbym_unet;
 
-/* levels L in [2, 8]; channels c_1..c_L each 8, 16, 32 or 64, non-decreasing, with
- * c_i + c_{i+1} <= 128; height a multiple of 8 * 2^(L-1) and width of 32 * 2^(L-1);
- * max_batch = the largest number of scan pairs per call. */
+/* levels L in [2, 8]; channels c_1..c_L each 8, 16, 32, 64, 128 or 256, non-decreasing, c_1 <= 64
+ * (Tab. II is L = 6 with 8, 16, 32, 64, 128, 256); height and width multiples of 8 * 2^(L-1), the
+ * width also of 32; max_batch = the largest number of scan pairs per call.  Levels whose images
+ * are narrower than 32 pixels, and layers whose weights do not fit in shared memory, run on the
+ * flat-GEMM convolution kernels. */
 typedef struct fmbym_unet_config {
     int levels;
     int channels[8];

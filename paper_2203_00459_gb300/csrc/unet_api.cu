@@ -26,6 +26,7 @@ struct Layer {
     int ns_f = 0, ns_d = 0;    // cp.async ring depth of the forward and dgrad convolutions
     int R_f = 1, R_d = 1;      // their rows per warp (CTA tile 8 R x 32)
     int wg_cib = 8, wg_R = 1, wg_ns = 2, wg_slots = 0;   // the weight gradient's plan
+    bool gemm_f = false, gemm_d = false, gemm_w = false;  // forward / dgrad / wgrad on the flat-GEMM kernels
     int slots_f = 0, slots_d = 0;   // their resident CTAs on the device
     long long w_off, g_off, b_off, rs_off;  // offsets in the parameter and running-stat arrays
     bf16* wf = nullptr;        // forward weights [cout][9][cinp]
@@ -64,6 +65,7 @@ struct fmbym_unet {
     float* hpart = nullptr;             // head partials
     size_t stats_cap = 0, bnpart_cap = 0, wpart_cap = 0, hpart_cap = 0;
     int nsm = 0;
+    int gw_slots = 0;                   // resident CTAs of the flat-GEMM weight gradient
     std::vector<void*> allocs;
     long long launches = 0;
     int last_batch = -1;
@@ -179,6 +181,20 @@ cudaError_t conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaSt
 cudaError_t conv_dispatch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
                           float* out1, int split, int acc0, int acc1, float2* stats) {
     const int co = dgrad ? L.cin : L.cout, R = dgrad ? L.R_d : L.R_f;
+    if (dgrad ? L.gemm_d : L.gemm_f) {
+        const int G = (dgrad ? L.coutp : L.cinp) / 8;
+        const dim3 grid((unsigned)((long long)B * L.H * L.W / kGM), (unsigned)(co / kGN));
+        ++u->launches;
+        if (dgrad)
+            k_conv3x3_gemm<<<grid, 256, kGemmConvSmem, st>>>(L.dy, L.cout, nullptr, 0, nullptr, nullptr, L.wd, G, co,
+                                                           out0, out1, split, acc0, acc1, nullptr, B, L.H, L.W);
+        else
+            k_conv3x3_gemm<<<grid, 256, kGemmConvSmem, st>>>(
+                L.in0, L.c0, L.in1, L.c1, L.planes ? (const float*)L.in0 : nullptr,
+                L.planes ? (const float*)L.in1 : nullptr, L.wf, G, co, out0, out1, split, acc0, acc1, stats, B, L.H,
+                L.W);
+        return cudaGetLastError();
+    }
 #define FMBYM_CONV(C, RR) \
     if (co == C && R == RR) return conv_launch<C, RR>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
     FMBYM_CONV(8, 4) FMBYM_CONV(16, 4) FMBYM_CONV(24, 4) FMBYM_CONV(8, 2) FMBYM_CONV(16, 2) FMBYM_CONV(24, 2)
@@ -259,6 +275,19 @@ void wgrad_run(const Layer& l, const WgradGeom& w, int n, const float* f, const 
         w.tpc, l.wg_ns, part);
 }
 
+// Flat-GEMM weight gradient: kWM output channels x kWI items per CTA, pixel tiles of kWP cut
+// into one wave of chunks over the resident CTAs.
+WgradGeom gemm_wgrad_geom(const fmbym_unet* u, const Layer& l, int B) {
+    WgradGeom w;
+    w.gy = l.cout / kWM;
+    w.gz = (9 * (l.cin / 8) + kWI - 1) / kWI;
+    const int ntiles = (int)((long long)B * l.H * l.W / kWP);
+    w.chunks = std::max(1, std::min(ntiles, u->gw_slots / (w.gy * w.gz)));
+    w.tpc = (ntiles + w.chunks - 1) / w.chunks;
+    w.used = (ntiles + w.tpc - 1) / w.tpc;
+    return w;
+}
+
 // Inputs of layer k for a batch of B (planes for the first layer are set per call).
 void wire_inputs(fmbym_unet* u) {
     const int L = u->levels;
@@ -306,18 +335,16 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     if (L < 2 || L > 8) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "levels must be in [2, 8]");
     for (int i = 0; i < L; ++i) {
         const int c = cfg->channels[i];
-        if (c != 8 && c != 16 && c != 32 && c != 64)
-            return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "channels must be 8, 16, 32 or 64");
+        if (c != 8 && c != 16 && c != 32 && c != 64 && c != 128 && c != 256)
+            return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "channels must be 8, 16, 32, 64, 128 or 256");
         if (i > 0 && c < cfg->channels[i - 1]) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "channels must not decrease");
     }
-    for (int i = 0; i + 1 < L; ++i)
-        if (cfg->channels[i] + cfg->channels[i + 1] > 128)
-            return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "decoder concatenation wider than 128 channels");
+    if (cfg->channels[0] > 64) return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "the first level has at most 64 channels");
     if (cfg->max_batch < 1) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "max_batch must be >= 1");
     const int H = cfg->height, W = cfg->width;
-    if (H <= 0 || W <= 0 || H % (kTH << (L - 1)) || W % (kTW << (L - 1)))
+    if (H <= 0 || W <= 0 || H % (8 << (L - 1)) || W % (8 << (L - 1)) || W % kTW)
         return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE,
-                     "height must be a multiple of 8*2^(L-1) and width of 32*2^(L-1)");
+                     "height and width must be multiples of 8*2^(L-1), and width of 32");
     fmbym_unet* u = new fmbym_unet();
     u->levels = L;
     for (int i = 0; i < L; ++i) u->ch[i] = cfg->channels[i];
@@ -377,6 +404,13 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     int dev = 0;
     chk(cudaGetDevice(&dev));
     chk(cudaDeviceGetAttribute(&u->nsm, cudaDevAttrMultiProcessorCount, dev));
+    {
+        int occ = 0;
+        chk(cudaFuncSetAttribute(k_wgrad_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmWgradSmem));
+        chk(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wgrad_gemm, 256, kGemmWgradSmem));
+        u->gw_slots = std::max(1, occ) * u->nsm;
+        chk(cudaFuncSetAttribute(k_conv3x3_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmConvSmem));
+    }
     size_t stats_cap = 0, bn_cap = 0, w_cap = 0;
     bool too_big = false;
     for (Layer& l : u->layers) {
@@ -391,11 +425,22 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         chk(ualloc(u, &l.bsums, l.cout));
         stats_cap = std::max(stats_cap, px / kTilePx * l.cout);
         bn_cap = std::max(bn_cap, (size_t)4 * u->nsm * l.cout);   // bn_pix_per_cta keeps the slabs at most 4 per SM
-        chk(wgrad_plan(u, l));
-        w_cap = std::max(w_cap, (size_t)wgrad_geom(l, B).chunks * l.cout * 9 * l.cin);
-        chk(conv_plan(u, l.cout, l.cinp / 8, l.H, l.R_f, l.ns_f, l.slots_f));
-        if (!l.planes) chk(conv_plan(u, l.cin, l.coutp / 8, l.H, l.R_d, l.ns_d, l.slots_d));
-        if (e == cudaSuccess && (!l.ns_f || (!l.planes && !l.ns_d))) too_big = true;
+        // tile kernels where the image is at least a tile wide and the weights fit in shared memory,
+        // the flat-GEMM kernels otherwise
+        const bool wide = l.W % kTW == 0;
+        if (wide) {
+            chk(wgrad_plan(u, l));
+            w_cap = std::max(w_cap, (size_t)wgrad_geom(l, B).chunks * l.cout * 9 * l.cin);
+            chk(conv_plan(u, l.cout, l.cinp / 8, l.H, l.R_f, l.ns_f, l.slots_f));
+            if (!l.planes) chk(conv_plan(u, l.cin, l.coutp / 8, l.H, l.R_d, l.ns_d, l.slots_d));
+        }
+        l.gemm_w = !wide;
+        l.gemm_f = !wide || !l.ns_f;
+        l.gemm_d = !l.planes && (!wide || !l.ns_d);
+        if (l.gemm_w) w_cap = std::max(w_cap, (size_t)gemm_wgrad_geom(u, l, B).chunks * l.cout * 9 * l.cin);
+        if (l.gemm_f) stats_cap = std::max(stats_cap, px / kGM * l.cout);
+        if ((l.gemm_f && l.cout % kGN) || (l.gemm_d && l.cin % kGN) || (l.gemm_w && (l.planes || l.cout % kWM)))
+            too_big = true;
     }
     u->pooled.assign(L, nullptr);
     u->upped.assign(L, nullptr);
@@ -439,7 +484,7 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     }
     if (too_big) {
         fmbym_unet_destroy(u);
-        return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "a convolution's weights and input tile exceed shared memory");
+        return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "a layer fits neither the tile nor the flat-GEMM convolution");
     }
     wire_inputs(u);
     *out = u;
@@ -549,8 +594,8 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
     }
     auto conv_bn = [&](Layer& l) -> cudaError_t {
         const long long px = (long long)n * l.H * l.W;
-        const int tile_px = kTilePx * l.R_f, ntiles = (int)(px / tile_px);
-        const int nparts = std::min(ntiles, l.slots_f);   // the conv's grid
+        const int tile_px = l.gemm_f ? kGM : kTilePx * l.R_f, ntiles = (int)(px / tile_px);
+        const int nparts = l.gemm_f ? ntiles : std::min(ntiles, l.slots_f);   // the conv's grid
         cudaError_t r = conv_dispatch(u, l, n, false, st, l.y, nullptr, l.cout, 0, 0, training ? u->stats : nullptr);
         if (r != cudaSuccess) return r;
         ++u->launches;
@@ -558,7 +603,7 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
             k_bn_finalize<<<l.cout, 256, 0, st>>>(u->stats, nparts, l.cout, ntiles, (float)tile_px,
                                                   u->running + l.rs_off, u->running + l.rs_off + l.cout, l.bn);
         else
-            k_bn_eval<<<1, 128, 0, st>>>(u->running + l.rs_off, u->running + l.rs_off + l.cout, l.cout, l.bn);
+            k_bn_eval<<<(l.cout + 127) / 128, 128, 0, st>>>(u->running + l.rs_off, u->running + l.rs_off + l.cout, l.cout, l.bn);
         ++u->launches;
         k_bn_relu<<<blocks(px * l.cout / 8), kBlock, 0, st>>>(l.y, l.bn, u->params + l.g_off, u->params + l.b_off,
                                                               l.a, px * l.cout / 8, l.cout);
@@ -637,9 +682,12 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         k_bn_bwd_dy<<<blocks(px * C / 4), kBlock, 0, st>>>(l.y, l.da, l.bn, u->params + l.g_off,
                                                            u->params + l.b_off, l.bsums, l.dy, px * C / 4, C);
         // weight gradient
-        const WgradGeom w = wgrad_geom(l, n);
+        const WgradGeom w = l.gemm_w ? gemm_wgrad_geom(u, l, n) : wgrad_geom(l, n);
         u->launches += 2;
-        if (l.planes) wgrad_run<8, true>(l, w, n, f, g, u->wpart, st);
+        if (l.gemm_w)
+            k_wgrad_gemm<<<dim3(w.used, w.gy, w.gz), 256, kGemmWgradSmem, st>>>(l.dy, l.cout, l.in0, l.c0, l.in1, l.c1,
+                                                                             n, l.H, l.W, w.tpc, u->wpart);
+        else if (l.planes) wgrad_run<8, true>(l, w, n, f, g, u->wpart, st);
         else if (l.wg_cib == 64) wgrad_run<64, false>(l, w, n, f, g, u->wpart, st);
         else if (l.wg_cib == 32) wgrad_run<32, false>(l, w, n, f, g, u->wpart, st);
         else if (l.wg_cib == 16) wgrad_run<16, false>(l, w, n, f, g, u->wpart, st);

@@ -299,6 +299,156 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in0, i
 }
 
 // ---------------------------------------------------------------------------------------------
+// 3x3 convolution as a flat GEMM over pixels: the deep levels of the network, whose images are
+// narrower than a tile or whose weights do not fit in shared memory
+// ---------------------------------------------------------------------------------------------
+//
+// out[p][co] = sum_k A[p][k] W[co][k] over the flattened pixels p = (b, y, x) and k = (tap, ci),
+// A the im2col of the input, gathered on the fly.  A CTA owns kGM pixels and kGN output channels
+// (blockIdx.y) and walks K in chunks of kGK items (tap, 8-channel group); each chunk's A rows
+// (pixel, item) and B rows (output channel, item) arrive by cp.async, 16 bytes each (zero-filled
+// outside the image and past the last item), through a ring of kGStages slots, and ldmatrix
+// reads both.  Warps: 4 along pixels x 2 along output channels, 16 x 16 each.  Inputs, weights,
+// the output split and the statistics are those of k_conv3x3; the statistics are per CTA (kGM
+// pixels) and channel.  Requires B H W to be a multiple of kGM and cout of kGN.
+constexpr int kGM = 64, kGN = 32, kGK = 8, kGStages = 4;
+constexpr size_t kGemmConvSlot = (size_t)(kGM + kGN) * kGK * 16;
+constexpr size_t kGemmConvSmem = kGStages * kGemmConvSlot;
+
+__global__ void __launch_bounds__(256) k_conv3x3_gemm(const bf16* __restrict__ in0, int c0,
+                                                      const bf16* __restrict__ in1, int c1,
+                                                      const float* __restrict__ pf, const float* __restrict__ pg,
+                                                      const bf16* __restrict__ wt, int G, int cout,
+                                                      float* __restrict__ out0, float* __restrict__ out1, int split,
+                                                      int acc0, int acc1, float2* __restrict__ stats, int B, int H,
+                                                      int W) {
+    extern __shared__ __align__(128) unsigned char smem_g[];
+    __shared__ float2 wstat[4][kGN];
+    const int NI = 9 * G, nchunk = (NI + kGK - 1) / kGK, HW = H * W;
+    const int p0 = blockIdx.x * kGM, co0 = blockIdx.y * kGN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int wm = warp & 3, wn = warp >> 2;
+
+    auto stage = [&](int kc) {   // K chunk kc into ring slot kc % kGStages
+        unsigned char* As = smem_g + (size_t)(kc % kGStages) * kGemmConvSlot;
+        unsigned char* Bs = As + (size_t)kGK * kGM * 16;
+        const int it0 = kc * kGK;
+        for (int e = tid; e < kGK * kGM; e += 256) {
+            const int li = e / kGM, px = e - li * kGM, item = it0 + li;
+            const int p = p0 + px, b = p / HW, r = p - b * HW, y = r / W, x = r - y * W;
+            const int tap = item < NI ? item / G : 0, grp = item - tap * G;
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            const bool inside = item < NI && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const size_t q = inside ? ((size_t)b * H + yy) * W + xx : 0;
+            unsigned char* dst = As + (size_t)e * 16;
+            if (pf) {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (inside) v.x = pack2(__float2bfloat16_rn(pf[q]), __float2bfloat16_rn(pg[q]));
+                *reinterpret_cast<uint4*>(dst) = v;
+            } else {
+                const int ch = inside ? grp * 8 : 0;
+                cp_async16(dst, ch < c0 ? in0 + q * c0 + ch : in1 + q * c1 + (ch - c0), inside);
+            }
+        }
+        for (int e = tid; e < kGK * kGN; e += 256) {
+            const int li = e / kGN, co = e - li * kGN, item = it0 + li;
+            const bool ok = item < NI;
+            cp_async16(Bs + (size_t)e * 16, wt + ((size_t)(co0 + co) * NI + (ok ? item : 0)) * 8, ok);
+        }
+    };
+
+    float acc[2][4];
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[nb][j] = 0.f;
+    const int mi = lane >> 3, r8 = lane & 7;
+    const int a_px = wm * 16 + (mi & 1) * 8 + r8, a_item = mi >> 1;
+    const int b_co = wn * 16 + (mi >> 1) * 8 + r8, b_item = mi & 1;
+    for (int k = 0; k < kGStages - 1; ++k) {
+        if (k < nchunk) stage(k);
+        cp_async_commit();
+    }
+    for (int kc = 0; kc < nchunk; ++kc) {
+        if (kc + kGStages - 1 < nchunk) stage(kc + kGStages - 1);
+        cp_async_commit();
+        cp_async_wait_n(kGStages - 1);
+        __syncthreads();
+        const unsigned char* As = smem_g + (size_t)(kc % kGStages) * kGemmConvSlot;
+        const unsigned char* Bs = As + (size_t)kGK * kGM * 16;
+#pragma unroll
+        for (int s = 0; s < kGK / 2; ++s) {
+            uint32_t a[4], bq[4];
+            ldsm_x4(a, As + (size_t)((2 * s + a_item) * kGM + a_px) * 16);
+            ldsm_x4(bq, Bs + (size_t)((2 * s + b_item) * kGN + b_co) * 16);
+            mma16816(acc[0], a, bq);
+            mma16816(acc[1], a, bq + 2);
+        }
+        __syncthreads();
+    }
+    // acc[nb][j]: pixel p0 + 16 wm + g (+8 for j >= 2), channel co0 + 16 wn + 8 nb + 2 t + (j & 1)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const size_t p = (size_t)p0 + wm * 16 + g + 8 * h;
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+            const int ch = co0 + wn * 16 + nb * 8 + 2 * t;
+            const float v0 = acc[nb][2 * h], v1 = acc[nb][2 * h + 1];
+            if (ch < split) {
+                float2* o = reinterpret_cast<float2*>(out0 + p * split + ch);
+                if (acc0) {
+                    const float2 old = *o;
+                    *o = make_float2(old.x + v0, old.y + v1);
+                } else {
+                    *o = make_float2(v0, v1);
+                }
+            } else {
+                float2* o = reinterpret_cast<float2*>(out1 + p * (cout - split) + (ch - split));
+                if (acc1) {
+                    const float2 old = *o;
+                    *o = make_float2(old.x + v0, old.y + v1);
+                } else {
+                    *o = make_float2(v0, v1);
+                }
+            }
+        }
+    }
+    if (stats) {
+        // per channel: each warp's 16 pixels give a (mean, M2) pair by shuffles over g; the 4 pixel
+        // warps' pairs (equal counts) give the CTA's
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                float sm = acc[nb][j] + acc[nb][j + 2];
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+                const float mu = sm * (1.f / 16.f);
+                const float d0 = acc[nb][j] - mu, d1 = acc[nb][j + 2] - mu;
+                float m2 = d0 * d0 + d1 * d1;
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+                if (g == 0) wstat[wm][wn * 16 + nb * 8 + 2 * t + j] = make_float2(mu, m2);
+            }
+        }
+        __syncthreads();
+        if (tid < kGN) {
+            float mu = 0.f;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) mu += wstat[w][tid].x;
+            mu *= 0.25f;
+            float m2 = 0.f;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const float d = wstat[w][tid].x - mu;
+                m2 += wstat[w][tid].y + 16.f * d * d;
+            }
+            stats[(size_t)blockIdx.x * cout + co0 + tid] = make_float2(mu, m2);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // BatchNorm
 // ---------------------------------------------------------------------------------------------
 
@@ -907,6 +1057,98 @@ __global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int 
             for (int r = 0; r < NRG; ++r) sum += red[((r * NG + gi) * 36 + k) * 32 + ln];
             const int co = co0 + (ln >> 2) + 8 * ((k & 3) >> 1), ci = ci_base + gi * 8 + 2 * (ln & 3) + (k & 1);
             if (co < cout && ci < cin) o[((size_t)co * 9 + (k >> 2)) * cin + ci] = sum;
+        }
+    }
+}
+
+// Weight gradient as a flat GEMM over pixels (the layers k_conv3x3_gemm serves): dW[co][k] =
+// sum_p dy[p][co] A[p][k], A the im2col of the layer input.  M = 16 output channels, N = 8 k (one
+// item), K = 16 pixels.  A CTA owns kWM output channels (blockIdx.y), kWI items (blockIdx.z) and a
+// chunk of kWP-pixel tiles (blockIdx.x); per tile, dy (kWP pixels x kWM channels) and the im2col
+// block (kWI items x kWP pixels) arrive by cp.async through a ring of kWStages slots, and
+// ldmatrix.trans gives the channel-by-pixel fragments.  Warps: 2 along output channels x 4 along
+// items (4 items each).  The CTA's sums go to part[chunk] in the layout of k_wgrad, which
+// k_wgrad_reduce adds in chunk order.  Requires B H W to be a multiple of kWP and cout of kWM.
+constexpr int kWM = 32, kWI = 16, kWP = 64, kWStages = 3;
+constexpr size_t kGemmWgradSlot = (size_t)(kWM / 8 + kWI) * kWP * 16;
+constexpr size_t kGemmWgradSmem = kWStages * kGemmWgradSlot;
+
+__global__ void __launch_bounds__(256) k_wgrad_gemm(const bf16* __restrict__ dy, int cout,
+                                                    const bf16* __restrict__ in0, int c0,
+                                                    const bf16* __restrict__ in1, int c1, int B, int H, int W,
+                                                    int tiles_per_chunk, float* __restrict__ part) {
+    extern __shared__ __align__(128) unsigned char smem_gw[];
+    const int cin = c0 + c1, G = cin / 8, NI = 9 * G, HW = H * W, ntiles = B * HW / kWP;
+    const int co0 = blockIdx.y * kWM, it0 = blockIdx.z * kWI;
+    const int first = blockIdx.x * tiles_per_chunk, n = min(tiles_per_chunk, ntiles - first);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int wm = warp & 1, wi = warp >> 1;
+
+    auto stage = [&](int k) {   // the k-th tile of this CTA's chunk into ring slot k % kWStages
+        unsigned char* Ds = smem_gw + (size_t)(k % kWStages) * kGemmWgradSlot;   // [co group][px][16 B]
+        unsigned char* As = Ds + (size_t)(kWM / 8) * kWP * 16;                    // [item][px][16 B]
+        const int p0 = (first + k) * kWP;
+        for (int e = tid; e < (kWM / 8) * kWP; e += 256) {
+            const int cg = e / kWP, px = e - cg * kWP;
+            cp_async16(Ds + (size_t)e * 16, dy + (size_t)(p0 + px) * cout + co0 + cg * 8, true);
+        }
+        for (int e = tid; e < kWI * kWP; e += 256) {
+            const int li = e / kWP, px = e - li * kWP, item = it0 + li;
+            const int p = p0 + px, b = p / HW, r = p - b * HW, y = r / W, x = r - y * W;
+            const int tap = item < NI ? item / G : 0, grp = item - tap * G;
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            const bool inside = item < NI && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const size_t q = inside ? ((size_t)b * H + yy) * W + xx : 0;
+            const int ch = inside ? grp * 8 : 0;
+            cp_async16(As + (size_t)e * 16, ch < c0 ? in0 + q * c0 + ch : in1 + q * c1 + (ch - c0), inside);
+        }
+    };
+
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const int mi = lane >> 3, r8 = lane & 7;
+    // A (dy^T): matrices (channels 0-7 | 8-15) x (pixels 0-7 | 8-15); B: (pixels 0-7 | 8-15) x (item a | a+1)
+    const int a_off = (wm * 2 + (mi & 1)) * kWP + (mi >> 1) * 8 + r8;
+    const int b_off = (4 * wi + (mi >> 1)) * kWP + (mi & 1) * 8 + r8;
+    for (int k = 0; k < kWStages - 1; ++k) {
+        if (k < n) stage(k);
+        cp_async_commit();
+    }
+    for (int it = 0; it < n; ++it) {
+        if (it + kWStages - 1 < n) stage(it + kWStages - 1);
+        cp_async_commit();
+        cp_async_wait_n(kWStages - 1);
+        __syncthreads();
+        const unsigned char* Ds = smem_gw + (size_t)(it % kWStages) * kGemmWgradSlot;
+        const unsigned char* As = Ds + (size_t)(kWM / 8) * kWP * 16;
+#pragma unroll
+        for (int s = 0; s < kWP / 16; ++s) {
+            uint32_t a[4], b01[4], b23[4];
+            ldsm_x4_trans(a, Ds + (size_t)(a_off + 16 * s) * 16);
+            ldsm_x4_trans(b01, As + (size_t)(b_off + 16 * s) * 16);
+            ldsm_x4_trans(b23, As + (size_t)(b_off + 2 * kWP + 16 * s) * 16);
+            mma16816(acc[0], a, b01);
+            mma16816(acc[1], a, b01 + 2);
+            mma16816(acc[2], a, b23);
+            mma16816(acc[3], a, b23 + 2);
+        }
+        __syncthreads();
+    }
+    // acc[i][j]: output channel co0 + 16 wm + g (+8 for j >= 2), item it0 + 4 wi + i, channel
+    // 2 t + (j & 1) of that item's group
+    float* o = part + (size_t)blockIdx.x * cout * 9 * cin;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int item = it0 + 4 * wi + i;
+        if (item >= NI) continue;
+        const int tap = item / G, ci0 = (item - tap * G) * 8;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int co = co0 + wm * 16 + g + 8 * (j >> 1), ci = ci0 + 2 * t + (j & 1);
+            o[((size_t)co * 9 + tap) * cin + ci] = acc[i][j];
         }
     }
 }

@@ -13,6 +13,9 @@ pytestmark = pytest.mark.gpu
 # bf16 activations: the oracle rounds at the same points, so differences come from float32 vs
 # float64 accumulation and the rare bf16 rounding flips they cause (one bf16 ulp, 2^-8 relative).
 TOL_MASK_MAX = 2e-2      # max |m_gpu - m_oracle| (masks lie in (0, 1))
+TOL_MASK_MAX_DEEP = 4e-2  # the same through the 6-level net's 22 bf16 layers (14 in the 4-level
+                          # net): more rounding flips compound; every layer is pinned on its own
+                          # by the teacher-forced test below
 TOL_MASK_MEAN = 1e-3     # mean |m_gpu - m_oracle|
 TOL_GRAD = 5e-2          # max |dW_gpu - dW_oracle| / max |dW_oracle| per parameter tensor
 TOL_RUN = 1e-3           # running statistics: |d| <= TOL_RUN (|ref| + std of the channel's statistic)
@@ -52,7 +55,8 @@ def scans(hw, b, start=0):
     return f, g
 
 
-@pytest.mark.parametrize("channels,hw,b", [((8, 16, 32, 64), 256, 2), ((8, 16), 64, 3)])
+@pytest.mark.parametrize("channels,hw,b", [((8, 16, 32, 64), 256, 2), ((8, 16), 64, 3),
+                                            ((8, 16, 32, 64, 128, 256), 256, 2)])
 def test_forward_and_running_stats_match_oracle(mn, channels, hw, b):
     net, p = setup(mn, channels, hw, b)
     f, g = scans(hw, b)
@@ -62,8 +66,9 @@ def test_forward_and_running_stats_match_oracle(mn, channels, hw, b):
     st = U.init_state(channels)
     of, og, om = U.masked(p, st, torch.from_numpy(f).double(), torch.from_numpy(g).double(), channels, True)
     d = np.abs(m.cpu().numpy() - om.numpy())
-    assert d.max() <= TOL_MASK_MAX and d.mean() <= TOL_MASK_MEAN, (d.max(), d.mean())
-    assert np.max(np.abs(fo.cpu().numpy() - of.numpy())) <= TOL_MASK_MAX * np.max(np.abs(f))
+    tol_max = TOL_MASK_MAX if len(channels) <= 4 else TOL_MASK_MAX_DEEP
+    assert d.max() <= tol_max and d.mean() <= TOL_MASK_MEAN, (d.max(), d.mean())
+    assert np.max(np.abs(fo.cpu().numpy() - of.numpy())) <= tol_max * np.max(np.abs(f))
     _, run, _ = net.store()
     torch.cuda.synchronize()
     ref = mn.flatten_running(st, channels).double().numpy()
@@ -77,7 +82,7 @@ def test_forward_and_running_stats_match_oracle(mn, channels, hw, b):
     torch.cuda.synchronize()
     _, _, om2 = U.masked(p, st, torch.from_numpy(f).double(), torch.from_numpy(g).double(), channels, False)
     d2 = np.abs(m2.cpu().numpy() - om2.numpy())
-    assert d2.max() <= TOL_MASK_MAX and d2.mean() <= TOL_MASK_MEAN, (d2.max(), d2.mean())
+    assert d2.max() <= tol_max and d2.mean() <= TOL_MASK_MEAN, (d2.max(), d2.mean())
     net.close()
 
 
@@ -151,14 +156,20 @@ def _rel(a, b):
     return float(torch.max(torch.abs(a - b)) / max(1e-30, float(torch.max(torch.abs(b)))))
 
 
-def test_every_layer_forward_and_adjoint_from_gpu_inputs(mn):
-    """Teacher-forced check of the 4-level 256^2 network: for every layer the float64 reference
-    recomputes the convolution, BN + ReLU, the BN/ReLU adjoint, the weight gradient, d gamma,
-    d beta and the input gradient (through concatenation, upsampling and max-pool) from the
-    GPU's own saved inputs, so that bf16 divergence between independent runs does not enter."""
+TAB2 = (8, 16, 32, 64, 128, 256)   # the paper's network (Tab. II): six levels, 8..256 channels
+
+
+@pytest.mark.parametrize("channels,hw,b", [((8, 16, 32, 64), 256, 2), (TAB2, 256, 2)],
+                         ids=["4-level", "tab2-6-level"])
+def test_every_layer_forward_and_adjoint_from_gpu_inputs(mn, channels, hw, b):
+    """Teacher-forced check of the 4-level and of the paper's 6-level 256^2 network: for every layer
+    the float64 reference recomputes the convolution, BN + ReLU, the BN/ReLU adjoint, the weight
+    gradient, d gamma, d beta and the input gradient (through concatenation, upsampling and
+    max-pool) from the GPU's own saved inputs, so that bf16 divergence between independent runs
+    does not enter.  In the 6-level net the 16^2 and 8^2 levels, and the 32^2 decoder layer whose
+    weights exceed shared memory, run on the flat-GEMM kernels; the rest on the tile kernels."""
     import torch.nn.functional as F
     from torch.nn.grad import conv2d_input, conv2d_weight
-    channels, hw, b = (8, 16, 32, 64), 256, 2
     net, p = setup(mn, channels, hw, b, seed=4)
     f, g = scans(hw, b, start=13)
     rng = np.random.default_rng(10)
@@ -243,3 +254,10 @@ def test_every_layer_forward_and_adjoint_from_gpu_inputs(mn):
             ref = ref + src.grad
         assert _rel(T[name]["da"], ref) <= TOL_STEP, (name, "da")
     net.close()
+
+
+def test_create_rejects_unsupported_networks(mn):
+    from paper_2203_00459_gb300 import _lib
+    for channels, hw in (((8, 24), 64), ((128, 256), 64), ((16, 8), 64), ((8, 16, 32), 48)):
+        with pytest.raises(_lib.FmbymError):
+            mn.MaskNet(channels, hw, hw, max_batch=1)
