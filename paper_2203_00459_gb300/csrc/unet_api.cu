@@ -178,22 +178,37 @@ cudaError_t conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaSt
     return cudaGetLastError();
 }
 
+// Flat-GEMM convolution tile: 128 pixels x 64 output channels while that still gives a CTA per SM,
+// else 64 x 32.
+bool gemm_big(const fmbym_unet* u, int co, long long npix) {
+    return co % 64 == 0 && npix % 128 == 0 && (npix / 128) * (co / 64) >= u->nsm;
+}
+
+template <int MT, int NT>
+cudaError_t gemm_conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
+                             float* out1, int split, int acc0, int acc1, float2* stats) {
+    const int co = dgrad ? L.cin : L.cout, G = (dgrad ? L.coutp : L.cinp) / 8;
+    const dim3 grid((unsigned)((long long)B * L.H * L.W / MT), (unsigned)(co / NT));
+    const size_t smem = gemm_conv_smem(MT, NT);
+    ++u->launches;
+    if (dgrad)
+        k_conv3x3_gemm<MT, NT><<<grid, 256, smem, st>>>(L.dy, L.cout, nullptr, 0, nullptr, nullptr, L.wd, G, co, out0,
+                                                         out1, split, acc0, acc1, nullptr, B, L.H, L.W);
+    else
+        k_conv3x3_gemm<MT, NT><<<grid, 256, smem, st>>>(L.in0, L.c0, L.in1, L.c1,
+                                                         L.planes ? (const float*)L.in0 : nullptr,
+                                                         L.planes ? (const float*)L.in1 : nullptr, L.wf, G, co, out0,
+                                                         out1, split, acc0, acc1, stats, B, L.H, L.W);
+    return cudaGetLastError();
+}
+
 cudaError_t conv_dispatch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
                           float* out1, int split, int acc0, int acc1, float2* stats) {
     const int co = dgrad ? L.cin : L.cout, R = dgrad ? L.R_d : L.R_f;
     if (dgrad ? L.gemm_d : L.gemm_f) {
-        const int G = (dgrad ? L.coutp : L.cinp) / 8;
-        const dim3 grid((unsigned)((long long)B * L.H * L.W / kGM), (unsigned)(co / kGN));
-        ++u->launches;
-        if (dgrad)
-            k_conv3x3_gemm<<<grid, 256, kGemmConvSmem, st>>>(L.dy, L.cout, nullptr, 0, nullptr, nullptr, L.wd, G, co,
-                                                           out0, out1, split, acc0, acc1, nullptr, B, L.H, L.W);
-        else
-            k_conv3x3_gemm<<<grid, 256, kGemmConvSmem, st>>>(
-                L.in0, L.c0, L.in1, L.c1, L.planes ? (const float*)L.in0 : nullptr,
-                L.planes ? (const float*)L.in1 : nullptr, L.wf, G, co, out0, out1, split, acc0, acc1, stats, B, L.H,
-                L.W);
-        return cudaGetLastError();
+        const long long npix = (long long)B * L.H * L.W;
+        return gemm_big(u, co, npix) ? gemm_conv_launch<128, 64>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats)
+                                     : gemm_conv_launch<64, 32>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
     }
 #define FMBYM_CONV(C, RR) \
     if (co == C && R == RR) return conv_launch<C, RR>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
@@ -409,7 +424,10 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         chk(cudaFuncSetAttribute(k_wgrad_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmWgradSmem));
         chk(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wgrad_gemm, 256, kGemmWgradSmem));
         u->gw_slots = std::max(1, occ) * u->nsm;
-        chk(cudaFuncSetAttribute(k_conv3x3_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmConvSmem));
+        chk(cudaFuncSetAttribute(k_conv3x3_gemm<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gemm_conv_smem(64, 32)));
+        chk(cudaFuncSetAttribute(k_conv3x3_gemm<128, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gemm_conv_smem(128, 64)));
     }
     size_t stats_cap = 0, bn_cap = 0, w_cap = 0;
     bool too_big = false;
@@ -438,8 +456,8 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
         l.gemm_f = !wide || !l.ns_f;
         l.gemm_d = !l.planes && (!wide || !l.ns_d);
         if (l.gemm_w) w_cap = std::max(w_cap, (size_t)gemm_wgrad_geom(u, l, B).chunks * l.cout * 9 * l.cin);
-        if (l.gemm_f) stats_cap = std::max(stats_cap, px / kGM * l.cout);
-        if ((l.gemm_f && l.cout % kGN) || (l.gemm_d && l.cin % kGN) || (l.gemm_w && (l.planes || l.cout % kWM)))
+        if (l.gemm_f) stats_cap = std::max(stats_cap, px / 64 * l.cout);
+        if ((l.gemm_f && l.cout % 32) || (l.gemm_d && l.cin % 32) || (l.gemm_w && (l.planes || l.cout % kWM)))
             too_big = true;
     }
     u->pooled.assign(L, nullptr);
@@ -594,7 +612,8 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
     }
     auto conv_bn = [&](Layer& l) -> cudaError_t {
         const long long px = (long long)n * l.H * l.W;
-        const int tile_px = l.gemm_f ? kGM : kTilePx * l.R_f, ntiles = (int)(px / tile_px);
+        const int tile_px = l.gemm_f ? (gemm_big(u, l.cout, px) ? 128 : 64) : kTilePx * l.R_f;
+        const int ntiles = (int)(px / tile_px);
         const int nparts = l.gemm_f ? ntiles : std::min(ntiles, l.slots_f);   // the conv's grid
         cudaError_t r = conv_dispatch(u, l, n, false, st, l.y, nullptr, l.cout, 0, 0, training ? u->stats : nullptr);
         if (r != cudaSuccess) return r;

@@ -304,17 +304,18 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in0, i
 // ---------------------------------------------------------------------------------------------
 //
 // out[p][co] = sum_k A[p][k] W[co][k] over the flattened pixels p = (b, y, x) and k = (tap, ci),
-// A the im2col of the input, gathered on the fly.  A CTA owns kGM pixels and kGN output channels
+// A the im2col of the input, gathered on the fly.  A CTA owns MT pixels and NT output channels
 // (blockIdx.y) and walks K in chunks of kGK items (tap, 8-channel group); each chunk's A rows
 // (pixel, item) and B rows (output channel, item) arrive by cp.async, 16 bytes each (zero-filled
 // outside the image and past the last item), through a ring of kGStages slots, and ldmatrix
-// reads both.  Warps: 4 along pixels x 2 along output channels, 16 x 16 each.  Inputs, weights,
-// the output split and the statistics are those of k_conv3x3; the statistics are per CTA (kGM
-// pixels) and channel.  Requires B H W to be a multiple of kGM and cout of kGN.
-constexpr int kGM = 64, kGN = 32, kGK = 8, kGStages = 4;
-constexpr size_t kGemmConvSlot = (size_t)(kGM + kGN) * kGK * 16;
-constexpr size_t kGemmConvSmem = kGStages * kGemmConvSlot;
+// reads both.  Each thread gathers for one pixel, decoded once.  Warps: 4 along pixels x 2 along
+// output channels, (MT / 4) x (NT / 2) each.  Inputs, weights, the output split and the
+// statistics are those of k_conv3x3; the statistics are per CTA (MT pixels) and channel.
+// Requires B H W to be a multiple of MT and cout of NT.
+constexpr int kGK = 8, kGStages = 4;
+__host__ __device__ constexpr size_t gemm_conv_smem(int MT, int NT) { return kGStages * (size_t)(MT + NT) * kGK * 16; }
 
+template <int MT, int NT>
 __global__ void __launch_bounds__(256) k_conv3x3_gemm(const bf16* __restrict__ in0, int c0,
                                                       const bf16* __restrict__ in1, int c1,
                                                       const float* __restrict__ pf, const float* __restrict__ pg,
@@ -322,25 +323,38 @@ __global__ void __launch_bounds__(256) k_conv3x3_gemm(const bf16* __restrict__ i
                                                       float* __restrict__ out0, float* __restrict__ out1, int split,
                                                       int acc0, int acc1, float2* __restrict__ stats, int B, int H,
                                                       int W) {
+    constexpr int MB = MT / 64, NB = NT / 16;          // m-blocks and n-blocks per warp
+    constexpr int TPP = 256 / MT;                       // threads per pixel in the gather
+    constexpr size_t SLOT = (size_t)(MT + NT) * kGK * 16;
     extern __shared__ __align__(128) unsigned char smem_g[];
-    __shared__ float2 wstat[4][kGN];
+    __shared__ float2 wstat[4][NT];
     const int NI = 9 * G, nchunk = (NI + kGK - 1) / kGK, HW = H * W;
-    const int p0 = blockIdx.x * kGM, co0 = blockIdx.y * kGN;
+    const int p0 = blockIdx.x * MT, co0 = blockIdx.y * NT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
     const int wm = warp & 3, wn = warp >> 2;
+    // this thread's gather pixel and first item slot
+    const int gpx = tid % MT, gli = tid / MT;
+    int gb, gy, gx;
+    {
+        const int p = p0 + gpx;
+        gb = p / HW;
+        const int r = p - gb * HW;
+        gy = r / W;
+        gx = r - gy * W;
+    }
 
     auto stage = [&](int kc) {   // K chunk kc into ring slot kc % kGStages
-        unsigned char* As = smem_g + (size_t)(kc % kGStages) * kGemmConvSlot;
-        unsigned char* Bs = As + (size_t)kGK * kGM * 16;
+        unsigned char* As = smem_g + (size_t)(kc % kGStages) * SLOT;
+        unsigned char* Bs = As + (size_t)kGK * MT * 16;
         const int it0 = kc * kGK;
-        for (int e = tid; e < kGK * kGM; e += 256) {
-            const int li = e / kGM, px = e - li * kGM, item = it0 + li;
-            const int p = p0 + px, b = p / HW, r = p - b * HW, y = r / W, x = r - y * W;
+#pragma unroll
+        for (int li = gli; li < kGK; li += TPP) {
+            const int item = it0 + li;
             const int tap = item < NI ? item / G : 0, grp = item - tap * G;
-            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            const int yy = gy + tap / 3 - 1, xx = gx + tap % 3 - 1;
             const bool inside = item < NI && yy >= 0 && yy < H && xx >= 0 && xx < W;
-            const size_t q = inside ? ((size_t)b * H + yy) * W + xx : 0;
-            unsigned char* dst = As + (size_t)e * 16;
+            const size_t q = inside ? ((size_t)gb * H + yy) * W + xx : 0;
+            unsigned char* dst = As + (size_t)(li * MT + gpx) * 16;
             if (pf) {
                 uint4 v = make_uint4(0, 0, 0, 0);
                 if (inside) v.x = pack2(__float2bfloat16_rn(pf[q]), __float2bfloat16_rn(pg[q]));
@@ -350,21 +364,23 @@ __global__ void __launch_bounds__(256) k_conv3x3_gemm(const bf16* __restrict__ i
                 cp_async16(dst, ch < c0 ? in0 + q * c0 + ch : in1 + q * c1 + (ch - c0), inside);
             }
         }
-        for (int e = tid; e < kGK * kGN; e += 256) {
-            const int li = e / kGN, co = e - li * kGN, item = it0 + li;
+        for (int e = tid; e < kGK * NT; e += 256) {
+            const int li = e / NT, co = e - li * NT, item = it0 + li;
             const bool ok = item < NI;
             cp_async16(Bs + (size_t)e * 16, wt + ((size_t)(co0 + co) * NI + (ok ? item : 0)) * 8, ok);
         }
     };
 
-    float acc[2][4];
+    float acc[MB][NB][4];
 #pragma unroll
-    for (int nb = 0; nb < 2; ++nb)
+    for (int m = 0; m < MB; ++m)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[nb][j] = 0.f;
+        for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[m][nb][j] = 0.f;
     const int mi = lane >> 3, r8 = lane & 7;
-    const int a_px = wm * 16 + (mi & 1) * 8 + r8, a_item = mi >> 1;
-    const int b_co = wn * 16 + (mi >> 1) * 8 + r8, b_item = mi & 1;
+    const int a_px = wm * (MT / 4) + (mi & 1) * 8 + r8, a_item = mi >> 1;
+    const int b_co = wn * (NT / 2) + (mi >> 1) * 8 + r8, b_item = mi & 1;
     for (int k = 0; k < kGStages - 1; ++k) {
         if (k < nchunk) stage(k);
         cp_async_commit();
@@ -374,65 +390,84 @@ __global__ void __launch_bounds__(256) k_conv3x3_gemm(const bf16* __restrict__ i
         cp_async_commit();
         cp_async_wait_n(kGStages - 1);
         __syncthreads();
-        const unsigned char* As = smem_g + (size_t)(kc % kGStages) * kGemmConvSlot;
-        const unsigned char* Bs = As + (size_t)kGK * kGM * 16;
+        const unsigned char* As = smem_g + (size_t)(kc % kGStages) * SLOT;
+        const unsigned char* Bs = As + (size_t)kGK * MT * 16;
 #pragma unroll
         for (int s = 0; s < kGK / 2; ++s) {
-            uint32_t a[4], bq[4];
-            ldsm_x4(a, As + (size_t)((2 * s + a_item) * kGM + a_px) * 16);
-            ldsm_x4(bq, Bs + (size_t)((2 * s + b_item) * kGN + b_co) * 16);
-            mma16816(acc[0], a, bq);
-            mma16816(acc[1], a, bq + 2);
+            uint32_t a[MB][4];
+#pragma unroll
+            for (int m = 0; m < MB; ++m)
+                ldsm_x4(a[m], As + (size_t)((2 * s + a_item) * MT + a_px + 16 * m) * 16);
+#pragma unroll
+            for (int nb = 0; nb < NB; nb += 2) {
+                uint32_t bq[4];
+                ldsm_x4(bq, Bs + (size_t)((2 * s + b_item) * NT + b_co + 8 * nb) * 16);
+#pragma unroll
+                for (int m = 0; m < MB; ++m) {
+                    mma16816(acc[m][nb], a[m], bq);
+                    mma16816(acc[m][nb + 1], a[m], bq + 2);
+                }
+            }
         }
         __syncthreads();
     }
-    // acc[nb][j]: pixel p0 + 16 wm + g (+8 for j >= 2), channel co0 + 16 wn + 8 nb + 2 t + (j & 1)
+    // acc[m][nb][j]: pixel p0 + wm MT/4 + 16 m + g (+8 for j >= 2), channel co0 + wn NT/2 + 8 nb + 2 t + (j & 1)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const size_t p = (size_t)p0 + wm * 16 + g + 8 * h;
+    for (int m = 0; m < MB; ++m) {
 #pragma unroll
-        for (int nb = 0; nb < 2; ++nb) {
-            const int ch = co0 + wn * 16 + nb * 8 + 2 * t;
-            const float v0 = acc[nb][2 * h], v1 = acc[nb][2 * h + 1];
-            if (ch < split) {
-                float2* o = reinterpret_cast<float2*>(out0 + p * split + ch);
-                if (acc0) {
-                    const float2 old = *o;
-                    *o = make_float2(old.x + v0, old.y + v1);
+        for (int h = 0; h < 2; ++h) {
+            const size_t p = (size_t)p0 + wm * (MT / 4) + 16 * m + g + 8 * h;
+#pragma unroll
+            for (int nb = 0; nb < NB; ++nb) {
+                const int ch = co0 + wn * (NT / 2) + nb * 8 + 2 * t;
+                const float v0 = acc[m][nb][2 * h], v1 = acc[m][nb][2 * h + 1];
+                if (ch < split) {
+                    float2* o = reinterpret_cast<float2*>(out0 + p * split + ch);
+                    if (acc0) {
+                        const float2 old = *o;
+                        *o = make_float2(old.x + v0, old.y + v1);
+                    } else {
+                        *o = make_float2(v0, v1);
+                    }
                 } else {
-                    *o = make_float2(v0, v1);
-                }
-            } else {
-                float2* o = reinterpret_cast<float2*>(out1 + p * (cout - split) + (ch - split));
-                if (acc1) {
-                    const float2 old = *o;
-                    *o = make_float2(old.x + v0, old.y + v1);
-                } else {
-                    *o = make_float2(v0, v1);
+                    float2* o = reinterpret_cast<float2*>(out1 + p * (cout - split) + (ch - split));
+                    if (acc1) {
+                        const float2 old = *o;
+                        *o = make_float2(old.x + v0, old.y + v1);
+                    } else {
+                        *o = make_float2(v0, v1);
+                    }
                 }
             }
         }
     }
     if (stats) {
-        // per channel: each warp's 16 pixels give a (mean, M2) pair by shuffles over g; the 4 pixel
-        // warps' pairs (equal counts) give the CTA's
+        // per channel: each warp's MT / 4 pixels give a (mean, M2) pair by shuffles over g; the 4
+        // pixel warps' pairs (equal counts) give the CTA's
+        constexpr float kWarpPx = MT / 4;
 #pragma unroll
-        for (int nb = 0; nb < 2; ++nb) {
+        for (int nb = 0; nb < NB; ++nb) {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                float sm = acc[nb][j] + acc[nb][j + 2];
+                float sm = 0.f;
+#pragma unroll
+                for (int m = 0; m < MB; ++m) sm += acc[m][nb][j] + acc[m][nb][j + 2];
 #pragma unroll
                 for (int o = 4; o < 32; o <<= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
-                const float mu = sm * (1.f / 16.f);
-                const float d0 = acc[nb][j] - mu, d1 = acc[nb][j + 2] - mu;
-                float m2 = d0 * d0 + d1 * d1;
+                const float mu = sm * (1.f / kWarpPx);
+                float m2 = 0.f;
+#pragma unroll
+                for (int m = 0; m < MB; ++m) {
+                    const float d0 = acc[m][nb][j] - mu, d1 = acc[m][nb][j + 2] - mu;
+                    m2 += d0 * d0 + d1 * d1;
+                }
 #pragma unroll
                 for (int o = 4; o < 32; o <<= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-                if (g == 0) wstat[wm][wn * 16 + nb * 8 + 2 * t + j] = make_float2(mu, m2);
+                if (g == 0) wstat[wm][wn * (NT / 2) + nb * 8 + 2 * t + j] = make_float2(mu, m2);
             }
         }
         __syncthreads();
-        if (tid < kGN) {
+        if (tid < NT) {
             float mu = 0.f;
 #pragma unroll
             for (int w = 0; w < 4; ++w) mu += wstat[w][tid].x;
@@ -441,7 +476,7 @@ __global__ void __launch_bounds__(256) k_conv3x3_gemm(const bf16* __restrict__ i
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const float d = wstat[w][tid].x - mu;
-                m2 += wstat[w][tid].y + 16.f * d * d;
+                m2 += wstat[w][tid].y + kWarpPx * d * d;
             }
             stats[(size_t)blockIdx.x * cout + co0 + tid] = make_float2(mu, m2);
         }
@@ -1092,15 +1127,18 @@ __global__ void __launch_bounds__(256) k_wgrad_gemm(const bf16* __restrict__ dy,
             const int cg = e / kWP, px = e - cg * kWP;
             cp_async16(Ds + (size_t)e * 16, dy + (size_t)(p0 + px) * cout + co0 + cg * 8, true);
         }
-        for (int e = tid; e < kWI * kWP; e += 256) {
-            const int li = e / kWP, px = e - li * kWP, item = it0 + li;
-            const int p = p0 + px, b = p / HW, r = p - b * HW, y = r / W, x = r - y * W;
+        // each thread gathers for one pixel (decoded once per tile) and every (256 / kWP)-th item
+        const int px = tid % kWP, p = p0 + px, b = p / HW, r = p - b * HW, y = r / W, x = r - y * W;
+#pragma unroll
+        for (int li = tid / kWP; li < kWI; li += 256 / kWP) {
+            const int item = it0 + li;
             const int tap = item < NI ? item / G : 0, grp = item - tap * G;
             const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
             const bool inside = item < NI && yy >= 0 && yy < H && xx >= 0 && xx < W;
             const size_t q = inside ? ((size_t)b * H + yy) * W + xx : 0;
             const int ch = inside ? grp * 8 : 0;
-            cp_async16(As + (size_t)e * 16, ch < c0 ? in0 + q * c0 + ch : in1 + q * c1 + (ch - c0), inside);
+            cp_async16(As + (size_t)(li * kWP + px) * 16, ch < c0 ? in0 + q * c0 + ch : in1 + q * c1 + (ch - c0),
+                       inside);
         }
     };
 
