@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwd", "fwdbwd"])
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "mixed", "masked256", "masked256_tab2"])
+    ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1],
+                    help="masked workloads: the mask network's flat-GEMM convolutions on mma.sync (0) or tcgen05 (1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     return ap.parse_args()
@@ -372,6 +374,7 @@ def run_masked256(args):
     F, G, P = train.trajectory_data(2, 33, 20220304)
     channels = (8, 16, 32, 64, 128, 256) if args.workload == "masked256_tab2" else (8, 16, 32, 64)
     ms = train.MaskedSearch(batch=64, channels=channels)
+    ms.net.set_conv_path(args.conv_path)
     Ft, Gt = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
     Pt = torch.from_numpy(P.astype(np.float32)).cuda()
     for _ in range(args.warmup):
@@ -388,7 +391,8 @@ def run_masked256(args):
             "value": 64 / (ms_step * 1e-3), "unit": "scan-pairs/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 mask, f32 search", "data": "synthetic",
-            "config": {"workload": args.workload, "n": 256, "batch": 64, "mask_channels": list(channels)}}
+            "config": {"workload": args.workload, "n": 256, "batch": 64, "mask_channels": list(channels),
+                       "conv_path": ["mma.sync", "tcgen05"][args.conv_path]}}
     ms.close()
     print(json.dumps(line), flush=True)
 

@@ -333,6 +333,17 @@ int fmbym_unet_adam(fmbym_unet* u, void* stream, float lr, float beta1, float be
 /* Number of kernels the network handle has launched. */
 long long fmbym_unet_launch_count(const fmbym_unet* u);
 
+/* Tensor-core path of the flat-GEMM convolutions (the layers that do not fit the tile kernels,
+ * e.g. the 16^2 and 8^2 levels of Tab. II's network at 256^2): 0 = mma.sync (the default),
+ * 1 = tcgen05 with the accumulator in tensor memory, for layers whose output channels are a
+ * multiple of 64 (the others stay on mma.sync).  Results agree to float32 summation order.
+ * FMBYM_ERR_INVALID_ARG for another value. */
+int fmbym_unet_set_conv_path(fmbym_unet* u, int path);
+
+/* Number of tcgen05 convolution CTAs whose bounded mbarrier wait gave up since creation (their
+ * outputs are not written); 0 in a healthy run.  Synchronous. */
+long long fmbym_unet_tc_timeouts(fmbym_unet* u);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int fmbym_version(void);
 

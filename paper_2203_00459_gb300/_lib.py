@@ -78,6 +78,8 @@ SIGNATURES = {
     "fmbym_unet_store": (_I, [_P, _P, _P, _P, _P]),
     "fmbym_unet_store_adam": (_I, [_P, _P, _P, _P]),
     "fmbym_unet_load_adam": (_I, [_P, _P, _P, _P]),
+    "fmbym_unet_set_conv_path": (_I, [_P, _I]),
+    "fmbym_unet_tc_timeouts": (_LL, [_P]),
 }
 
 _lib = None

@@ -66,6 +66,8 @@ struct fmbym_unet {
     size_t stats_cap = 0, bnpart_cap = 0, wpart_cap = 0, hpart_cap = 0;
     int nsm = 0;
     int gw_slots = 0;                   // resident CTAs of the flat-GEMM weight gradient
+    int conv_path = 0;                  // flat-GEMM convolutions: 0 mma.sync, 1 tcgen05
+    unsigned* tc_timeouts = nullptr;    // device counter of tcgen05 CTAs whose wait gave up
     std::vector<void*> allocs;
     long long launches = 0;
     int last_batch = -1;
@@ -179,9 +181,26 @@ cudaError_t conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaSt
 }
 
 // Flat-GEMM convolution tile: 128 pixels x 64 output channels while that still gives a CTA per SM,
-// else 64 x 32.
+// else 64 x 32; on the tcgen05 path always 128 pixels.
 bool gemm_big(const fmbym_unet* u, int co, long long npix) {
-    return co % 64 == 0 && npix % 128 == 0 && (npix / 128) * (co / 64) >= u->nsm;
+    return co % 64 == 0 && npix % 128 == 0 && (u->conv_path == 1 || (npix / 128) * (co / 64) >= u->nsm);
+}
+
+template <int NT>
+cudaError_t tc_conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cudaStream_t st, float* out0,
+                           float* out1, int split, int acc0, int acc1, float2* stats) {
+    const int co = dgrad ? L.cin : L.cout, G = (dgrad ? L.coutp : L.cinp) / 8;
+    const dim3 grid((unsigned)((long long)B * L.H * L.W / 128), (unsigned)(co / NT));
+    ++u->launches;
+    if (dgrad)
+        k_conv3x3_tc<NT><<<grid, 256, tc_conv_smem(NT), st>>>(L.dy, L.cout, nullptr, 0, L.wd, G, co, out0, out1,
+                                                              split, acc0, acc1, nullptr, B, L.H, L.W,
+                                                              u->tc_timeouts);
+    else
+        k_conv3x3_tc<NT><<<grid, 256, tc_conv_smem(NT), st>>>(L.in0, L.c0, L.in1, L.c1, L.wf, G, co, out0, out1,
+                                                              split, acc0, acc1, stats, B, L.H, L.W,
+                                                              u->tc_timeouts);
+    return cudaGetLastError();
 }
 
 template <int MT, int NT>
@@ -207,6 +226,10 @@ cudaError_t conv_dispatch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cuda
     const int co = dgrad ? L.cin : L.cout, R = dgrad ? L.R_d : L.R_f;
     if (dgrad ? L.gemm_d : L.gemm_f) {
         const long long npix = (long long)B * L.H * L.W;
+        if (u->conv_path == 1 && !L.planes && gemm_big(u, co, npix))
+            return co % 128 == 0 && (npix / 128) * (co / 128) >= u->nsm
+                       ? tc_conv_launch<128>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats)
+                       : tc_conv_launch<64>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
         return gemm_big(u, co, npix) ? gemm_conv_launch<128, 64>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats)
                                      : gemm_conv_launch<64, 32>(u, L, B, dgrad, st, out0, out1, split, acc0, acc1, stats);
     }
@@ -428,6 +451,11 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
                                  (int)gemm_conv_smem(64, 32)));
         chk(cudaFuncSetAttribute(k_conv3x3_gemm<128, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)gemm_conv_smem(128, 64)));
+        chk(cudaFuncSetAttribute(k_conv3x3_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_conv_smem(64)));
+        chk(cudaFuncSetAttribute(k_conv3x3_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_conv_smem(128)));
+        chk(ualloc(u, &u->tc_timeouts, 1));
+        chk(cudaMemset(u->tc_timeouts, 0, sizeof(unsigned)));
     }
     size_t stats_cap = 0, bn_cap = 0, w_cap = 0;
     bool too_big = false;
@@ -515,6 +543,20 @@ float* fmbym_unet_params(fmbym_unet* u) { return u ? u->params : nullptr; }
 float* fmbym_unet_grads(fmbym_unet* u) { return u ? u->grads : nullptr; }
 float* fmbym_unet_running(fmbym_unet* u) { return u ? u->running : nullptr; }
 long long fmbym_unet_launch_count(const fmbym_unet* u) { return u ? u->launches : 0; }
+
+int fmbym_unet_set_conv_path(fmbym_unet* u, int path) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    if (path != 0 && path != 1) return ufail(u, FMBYM_ERR_INVALID_ARG, "conv path must be 0 (mma.sync) or 1 (tcgen05)");
+    u->conv_path = path;
+    return FMBYM_OK;
+}
+
+long long fmbym_unet_tc_timeouts(fmbym_unet* u) {
+    if (!u || !u->tc_timeouts) return 0;
+    unsigned v = 0;
+    if (cudaMemcpy(&v, u->tc_timeouts, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return (long long)v;
+}
 
 int fmbym_unet_layer_tensor(fmbym_unet* u, void* stream, int layer, int which, int n, float* dst) {
     if (!u || layer < 0 || layer >= (int)u->layers.size() || which < 0 || which > 3 || !dst || n < 1 ||

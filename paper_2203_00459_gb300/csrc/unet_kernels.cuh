@@ -484,6 +484,225 @@ __global__ void __launch_bounds__(256) k_conv3x3_gemm(const bf16* __restrict__ i
 }
 
 // ---------------------------------------------------------------------------------------------
+// The flat-GEMM convolution on the 5th-generation tensor cores (tcgen05, accumulator in TMEM)
+// ---------------------------------------------------------------------------------------------
+//
+// Same product, operands and ring as k_conv3x3_gemm<128, NT>: the im2col rows (pixel, item) and
+// weight rows (output channel, item) land by cp.async in the canonical K-major, no-swizzle layout
+// of tcgen05 -- a core matrix is 8 consecutive 16-byte rows, so [item][pixel][16 B] puts the 8-row
+// groups 128 B apart (SBO) and the K-adjacent core matrices 128 * 16 B apart (LBO).  One thread
+// issues tcgen05.mma (M = 128 pixels, N = NT channels, K = 16) for each K step of a chunk and
+// commits it to the slot's mbarrier, which the producers wait on before refilling the slot; the
+// accumulator lives in NT TMEM columns.  The epilogue reads TMEM with tcgen05.ld (warp w: lanes
+// 32 (w % 4) .., columns (w / 4) NT / 2 ..), stores, and forms the statistics as k_conv3x3_gemm
+// does.  Every mbarrier wait is bounded: on a timeout the CTA counts it in *timeouts, stops
+// issuing, waits (bounded) for what it issued, frees its TMEM and returns.
+__host__ __device__ constexpr size_t tc_conv_smem(int NT) { return kGStages * (size_t)(128 + NT) * kGK * 16; }
+constexpr unsigned kTcSpin = 1u << 22;   // mbarrier polls before a wait gives up
+
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    unsigned done = 0;
+    for (unsigned it = 0; it < kTcSpin && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+    return done != 0;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(256) k_conv3x3_tc(const bf16* __restrict__ in0, int c0, const bf16* __restrict__ in1,
+                                                    int c1, const bf16* __restrict__ wt, int G, int cout,
+                                                    float* __restrict__ out0, float* __restrict__ out1, int split,
+                                                    int acc0, int acc1, float2* __restrict__ stats, int B, int H,
+                                                    int W, unsigned* __restrict__ timeouts) {
+    constexpr int MT = 128;
+    constexpr size_t SLOT = (size_t)(MT + NT) * kGK * 16;
+    extern __shared__ __align__(1024) unsigned char smem_t[];
+    __shared__ __align__(8) unsigned long long mbar[kGStages];
+    __shared__ unsigned tmem_base;
+    __shared__ int failed;
+    __shared__ float2 wstat[4][NT];
+    const int NI = 9 * G, nchunk = (NI + kGK - 1) / kGK, HW = H * W;
+    const int p0 = blockIdx.x * MT, co0 = blockIdx.y * NT;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(smem_t);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         (unsigned)__cvta_generic_to_shared(&tmem_base)),
+                     "r"(NT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        failed = 0;
+        for (int s = 0; s < kGStages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"((unsigned)__cvta_generic_to_shared(&mbar[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    const int gpx = tid % MT, gli = tid / MT;
+    int gb, gy, gx;
+    {
+        const int p = p0 + gpx;
+        gb = p / HW;
+        const int r = p - gb * HW;
+        gy = r / W;
+        gx = r - gy * W;
+    }
+    auto stage = [&](int kc) {
+        unsigned char* As = smem_t + (size_t)(kc % kGStages) * SLOT;
+        unsigned char* Bs = As + (size_t)kGK * MT * 16;
+        const int it0 = kc * kGK;
+#pragma unroll
+        for (int li = gli; li < kGK; li += 256 / MT) {
+            const int item = it0 + li;
+            const int tap = item < NI ? item / G : 0, grp = item - tap * G;
+            const int yy = gy + tap / 3 - 1, xx = gx + tap % 3 - 1;
+            const bool inside = item < NI && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const size_t q = inside ? ((size_t)gb * H + yy) * W + xx : 0;
+            const int ch = inside ? grp * 8 : 0;
+            cp_async16(As + (size_t)(li * MT + gpx) * 16, ch < c0 ? in0 + q * c0 + ch : in1 + q * c1 + (ch - c0),
+                       inside);
+        }
+        for (int e = tid; e < kGK * NT; e += 256) {
+            const int li = e / NT, co = e - li * NT, item = it0 + li;
+            const bool ok = item < NI;
+            cp_async16(Bs + (size_t)e * 16, wt + ((size_t)(co0 + co) * NI + (ok ? item : 0)) * 8, ok);
+        }
+    };
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const unsigned tmem = tmem_base;
+    // kind::f16: D f32, A and B bf16, both K-major, N = NT, M = 128
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NT >> 3) << 17) | ((unsigned)(MT >> 4) << 24);
+    for (int k = 0; k < kGStages - 1; ++k) {
+        if (k < nchunk) stage(k);
+        cp_async_commit();
+    }
+    int issued = 0;   // chunks whose MMAs were committed (thread 0's count; others follow via failed)
+    for (int kc = 0; kc < nchunk; ++kc) {
+        const int nk = kc + kGStages - 1;
+        if (nk < nchunk) {
+            if (nk >= kGStages) {   // the slot's previous chunk (kc - 1) must have been consumed
+                const unsigned bar = (unsigned)__cvta_generic_to_shared(&mbar[nk % kGStages]);
+                if (!mbar_wait(bar, (unsigned)(((nk - kGStages) / kGStages) & 1))) failed = 1;
+            }
+            __syncthreads();
+            if (failed) break;
+            stage(nk);
+        }
+        cp_async_commit();
+        cp_async_wait_n(kGStages - 1);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        if (tid == 0) {
+            const unsigned As = sbase + (unsigned)((kc % kGStages) * SLOT), Bs = As + kGK * MT * 16;
+#pragma unroll
+            for (int s = 0; s < kGK / 2; ++s) {
+                const unsigned long long ad = tc_desc(As + s * 2 * MT * 16, MT * 16, 128);
+                const unsigned long long bd = tc_desc(Bs + s * 2 * NT * 16, NT * 16, 128);
+                const unsigned accum = (kc > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                (unsigned)__cvta_generic_to_shared(&mbar[kc % kGStages])));
+        }
+        issued = kc + 1;
+    }
+    cp_async_wait_n(0);
+    // the last committed chunk's barrier covers every MMA issued before it; the verdict is shared
+    // so that the whole CTA takes the same branch around the warp-collective TMEM loads
+    if (issued > 0) {
+        const int last = issued - 1;
+        const unsigned bar = (unsigned)__cvta_generic_to_shared(&mbar[last % kGStages]);
+        if (!mbar_wait(bar, (unsigned)((last / kGStages) & 1))) failed = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const bool ok = !failed && issued == nchunk;
+    if (!ok && tid == 0) atomicAdd(timeouts, 1u);
+    if (ok) {
+        // epilogue: warp w holds pixels 32 (w % 4) + lane, channels (w / 4) NT / 2 + [0, NT / 2)
+        const int wq = warp & 3, half = warp >> 2;
+        const size_t p = (size_t)p0 + 32 * wq + lane;
+#pragma unroll
+        for (int cc = 0; cc < NT / 2; cc += 16) {
+            const int cb = half * (NT / 2) + cc;
+            unsigned r[16];
+            const unsigned addr = tmem + ((unsigned)(32 * wq) << 16) + (unsigned)cb;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                         : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                const int ch = co0 + cb + j;
+                if (ch < split) {
+                    float2* o = reinterpret_cast<float2*>(out0 + p * split + ch);
+                    if (acc0) {
+                        const float2 old = *o;
+                        *o = make_float2(old.x + v[j], old.y + v[j + 1]);
+                    } else {
+                        *o = make_float2(v[j], v[j + 1]);
+                    }
+                } else {
+                    float2* o = reinterpret_cast<float2*>(out1 + p * (cout - split) + (ch - split));
+                    if (acc1) {
+                        const float2 old = *o;
+                        *o = make_float2(old.x + v[j], old.y + v[j + 1]);
+                    } else {
+                        *o = make_float2(v[j], v[j + 1]);
+                    }
+                }
+            }
+            if (stats) {
+                // per channel: the warp's 32 pixels give a (mean, M2) pair by shuffles
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float sm = v[j];
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+                    const float mu = sm * (1.f / 32.f), d = v[j] - mu;
+                    float m2 = d * d;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+                    if (lane == 0) wstat[wq][cb + j] = make_float2(mu, m2);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NT));
+    if (ok && stats && tid < NT) {
+        float mu = 0.f;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) mu += wstat[w][tid].x;
+        mu *= 0.25f;
+        float m2 = 0.f;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float d = wstat[w][tid].x - mu;
+            m2 += wstat[w][tid].y + 32.f * d * d;
+        }
+        stats[(size_t)blockIdx.x * cout + co0 + tid] = make_float2(mu, m2);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // BatchNorm
 // ---------------------------------------------------------------------------------------------
 

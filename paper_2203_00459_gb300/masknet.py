@@ -146,3 +146,10 @@ class MaskNet:
 
     def launch_count(self):
         return int(_lib.lib().fmbym_unet_launch_count(self._h))
+
+    def set_conv_path(self, path):
+        """0: the flat-GEMM convolutions on mma.sync; 1: on tcgen05 (output channels a multiple of 64)."""
+        _lib.check_unet(_lib.lib().fmbym_unet_set_conv_path(self._h, int(path)), self._h)
+
+    def tc_timeouts(self):
+        return int(_lib.lib().fmbym_unet_tc_timeouts(self._h))

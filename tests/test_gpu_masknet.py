@@ -159,18 +159,20 @@ def _rel(a, b):
 TAB2 = (8, 16, 32, 64, 128, 256)   # the paper's network (Tab. II): six levels, 8..256 channels
 
 
-@pytest.mark.parametrize("channels,hw,b", [((8, 16, 32, 64), 256, 2), (TAB2, 256, 2)],
-                         ids=["4-level", "tab2-6-level"])
-def test_every_layer_forward_and_adjoint_from_gpu_inputs(mn, channels, hw, b):
+@pytest.mark.parametrize("channels,hw,b,path", [((8, 16, 32, 64), 256, 2, 0), (TAB2, 256, 2, 0), (TAB2, 256, 2, 1)],
+                         ids=["4-level", "tab2-6-level", "tab2-6-level-tcgen05"])
+def test_every_layer_forward_and_adjoint_from_gpu_inputs(mn, channels, hw, b, path):
     """Teacher-forced check of the 4-level and of the paper's 6-level 256^2 network: for every layer
     the float64 reference recomputes the convolution, BN + ReLU, the BN/ReLU adjoint, the weight
     gradient, d gamma, d beta and the input gradient (through concatenation, upsampling and
     max-pool) from the GPU's own saved inputs, so that bf16 divergence between independent runs
     does not enter.  In the 6-level net the 16^2 and 8^2 levels, and the 32^2 decoder layer whose
-    weights exceed shared memory, run on the flat-GEMM kernels; the rest on the tile kernels."""
+    weights exceed shared memory, run on the flat-GEMM kernels (path 1: their convolutions on
+    tcgen05 with the accumulator in tensor memory); the rest on the tile kernels."""
     import torch.nn.functional as F
     from torch.nn.grad import conv2d_input, conv2d_weight
     net, p = setup(mn, channels, hw, b, seed=4)
+    net.set_conv_path(path)
     f, g = scans(hw, b, start=13)
     rng = np.random.default_rng(10)
     dfo = rng.standard_normal(f.shape).astype(np.float32)
@@ -253,6 +255,7 @@ def test_every_layer_forward_and_adjoint_from_gpu_inputs(mn, channels, hw, b):
             F.interpolate(src, scale_factor=2, mode="bilinear", align_corners=False).backward(d_up)
             ref = ref + src.grad
         assert _rel(T[name]["da"], ref) <= TOL_STEP, (name, "da")
+    assert net.tc_timeouts() == 0
     net.close()
 
 
@@ -261,3 +264,39 @@ def test_create_rejects_unsupported_networks(mn):
     for channels, hw in (((8, 24), 64), ((128, 256), 64), ((16, 8), 64), ((8, 16, 32), 48)):
         with pytest.raises(_lib.FmbymError):
             mn.MaskNet(channels, hw, hw, max_batch=1)
+
+
+def test_tcgen05_and_mma_paths_agree(mn):
+    """The flat-GEMM convolutions on tcgen05 against the same kernels on mma.sync: one training
+    forward of the Tab. II net from the same parameters and inputs (only the float32 summation
+    order differs, then bf16 rounding flips through 22 layers), no timed-out tcgen05 CTA in a
+    forward and adjoint, and the conv path rejected outside {0, 1}.  The adjoint of each path is
+    pinned layer by layer by the teacher-forced test above: end to end, the parameter gradients
+    of two runs of this depth drift apart by rounding flips amplified through BatchNorm."""
+    from paper_2203_00459_gb300 import _lib
+    f, g = scans(256, 2, start=21)
+    ft, gt = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    d1 = torch.randn_like(ft)
+    d2 = torch.randn_like(gt)
+    out = []
+    for path in (0, 1):
+        net, _ = setup(mn, TAB2, 256, 2, seed=6)
+        net.set_conv_path(path)
+        fo, go, m = net.forward(ft, gt, training=True, want_masks=True)
+        net.backward(ft, gt, d1, d2)
+        _, run, _ = net.store()
+        torch.cuda.synchronize()
+        out.append((m.cpu().double(), run.cpu().double()))
+        assert net.tc_timeouts() == 0
+        if path == 1:
+            with pytest.raises(_lib.FmbymError):
+                net.set_conv_path(2)
+        net.close()
+    (m0, r0), (m1, r1) = out
+    assert float(torch.max(torch.abs(m0 - m1))) <= TOL_MASK_MAX_DEEP
+    assert float(torch.mean(torch.abs(m0 - m1))) <= TOL_MASK_MEAN
+    # running statistics on the scale of each channel's variance (as against the oracle above)
+    ref = r0.numpy()
+    scale = np.concatenate([np.concatenate([np.sqrt(np.abs(ref[k + co:k + 2 * co])), np.abs(ref[k + co:k + 2 * co])])
+                            for k, co in _running_blocks(TAB2)])
+    assert np.max(np.abs(r1.numpy() - ref) / (np.abs(ref) + scale + 1e-6)) <= 1e-2
