@@ -113,6 +113,25 @@ def test_layer_list_follows_the_unet_pattern():
     assert names[0][1:] == (2, 8) and names[8][1:] == (64 + 32, 32) and names[12][1:] == (16 + 8, 8)
 
 
+def test_six_level_layer_list_reproduces_tab2():
+    """The oracle's layer list for channels (8, 16, 32, 64, 128, 256) against every (c_i, c_o) that
+    Tab. II prints, including the 384/192/96/48/24-channel decoder concatenations, and the head."""
+    import os
+    rows = [ln.split() for ln in open(os.path.join(os.path.dirname(__file__), "golden", "tab2_network.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    layers = U.conv_layers((8, 16, 32, 64, 128, 256))
+    enc = [(int(r[1]), int(r[2]), int(r[3]), int(r[4])) for r in rows if r[0] == "enc"]
+    dec = [(int(r[1]), int(r[2]), int(r[3]), int(r[4])) for r in rows if r[0] == "dec"]
+    head = [(int(r[1]), int(r[2])) for r in rows if r[0] == "head"]
+    assert len(layers) == 2 * (len(enc) + len(dec))
+    got = [(a[1], a[2], b[1], b[2]) for a, b in zip(layers[0::2], layers[1::2])]
+    assert got == enc + dec
+    p = U.init_params((8, 16, 32, 64, 128, 256), seed=1)
+    assert tuple(p["head.w"].shape[:2]) == (head[0][1], head[0][0])
+    for name, ci, co in layers:
+        assert tuple(p[name + ".w"].shape) == (co, ci, 3, 3)
+
+
 def test_decoder_concatenates_up_then_skip():
     # with the weights on the first (upsampled) input channels of every decoder conv zeroed, the
     # masks no longer depend on the deepest level; zeroing the skip channels instead keeps the
