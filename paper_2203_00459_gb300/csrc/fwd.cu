@@ -175,10 +175,11 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
     constexpr int T = FftPlan<NT>::T;
     __shared__ float2 z[spad(NT)];
     __shared__ float c[NT];
-    __shared__ float red[32];
+    __shared__ float red[32], red2[64];
     const int q = blockIdx.x;
     for (int k = threadIdx.x; k < NT; k += blockDim.x) {
         float sx = 0.f, sy = 0.f;
+#pragma unroll 8
         for (int h = 0; h < nch; ++h) {
             const float2 v = sp[((size_t)q * nch + h) * NT + k];
             sx += v.x;
@@ -219,8 +220,32 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
         lsum += v;
         lmax = fmaxf(lmax, v);
     }
-    const float mean = block_reduce<false>(lsum, red) * (1.f / NT);
-    const float cmax = block_reduce<true>(lmax, red);
+    // sum and maximum in one block reduction
+    {
+        lsum = warp_sum(lsum);
+        lmax = warp_max(lmax);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        if (lane == 0) {
+            red[wid] = lsum;
+            red2[wid] = lmax;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            float a = lane < nw ? red[lane] : 0.f, b = lane < nw ? red2[lane] : -FLT_MAX;
+            a = warp_sum(a);
+            b = warp_max(b);
+            if (lane == 0) {
+                red[0] = a;
+                red2[0] = b;
+            }
+        }
+        __syncthreads();
+        lsum = red[0];
+        lmax = red2[0];
+        __syncthreads();
+    }
+    const float mean = lsum * (1.f / NT);
+    const float cmax = lmax;
     float lvar = 0.f;
     for (int i = threadIdx.x; i < NT; i += blockDim.x) lvar += (c[i] - mean) * (c[i] - mean);
     const float sd = sqrtf(block_reduce<false>(lvar, red) * (1.f / NT));
@@ -231,8 +256,9 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
         le += e;
         lek += e * (float)(i - NT / 2);
     }
-    const float se = block_reduce<false>(le, red);
-    const float sek = block_reduce<false>(lek, red);
+    float sums[2] = {le, lek};
+    block_sum_n<2>(sums, red2);
+    const float se = sums[0], sek = sums[1];
     for (int i = threadIdx.x; i < NT; i += blockDim.x) ct[(size_t)q * NT + i] = c[i];
     if (c_theta) {
         float* out = c_theta + tab[3 * q + 1];
@@ -462,6 +488,18 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
     __shared__ float stat[4];
     __shared__ bool last;
     const int q = blockIdx.y;
+    constexpr int ROWS = N / kSplitXY, TOT = ROWS * (N / 4), PER = (TOT + kThreads - 1) / kThreads;
+    const int y0 = blockIdx.x * ROWS;
+    const float* c = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N;
+    // the scores first (they do not depend on the statistics), so their loads overlap the
+    // statistics' reduction below
+    float4 vv[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * kThreads;
+        if (TOT % kThreads == 0 || idx < TOT)
+            vv[m] = *reinterpret_cast<const float4*>(c + (size_t)(y0 + idx / (N / 4)) * N + (idx % (N / 4)) * 4);
+    }
     if (threadIdx.x < 32) {
         float mu, sd, cmax;
         xy_stats_warp(st + (size_t)q * nblk * 4, nblk, (float)N * (float)N, mu, sd, cmax);
@@ -475,13 +513,13 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
     __syncthreads();
     const float cmax = stat[0], inv = stat[1], mu = stat[2], sd = stat[3];
     const float isd = sd > 0.f ? 1.f / sd : 0.f;
-    const float* c = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N;
-    constexpr int ROWS = N / kSplitXY;
-    const int y0 = blockIdx.x * ROWS;
     float le = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lzx = 0.f, lzy = 0.f;
-    for (int idx = threadIdx.x; idx < ROWS * (N / 4); idx += kThreads) {
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int idx = threadIdx.x + m * kThreads;
+        if (TOT % kThreads != 0 && idx >= TOT) break;
         const int yy = y0 + idx / (N / 4), x4 = (idx % (N / 4)) * 4;
-        const float4 v = *reinterpret_cast<const float4*>(c + (size_t)yy * N + x4);
+        const float4 v = vv[m];
         const float e0 = expf((v.x - cmax) * inv), e1 = expf((v.y - cmax) * inv);
         const float e2 = expf((v.z - cmax) * inv), e3 = expf((v.w - cmax) * inv);
         const float es = (e0 + e1) + (e2 + e3);
