@@ -37,15 +37,19 @@ import numpy as np
 # ----------------------------------------------------------------------------------------------
 
 def make_cfg(n, n_theta, n_r, temp_theta=1.0, temp_xy=1.0, delta_xy=1.0, window=1, pad_mode=0,
-             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0, full_circle=0):
+             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0, full_circle=0, rotate_target=0):
     """Alg. 1 parameters (n_theta, T_theta, n_xy = n, delta_xy, T_xy) plus the A3-A7 switches;
     angle_score 0 is Eq. 7 (reading A2), 1 the mean over radial lags that Alg. 1 prints;
-    full_circle 1 resolves the heading over the full circle (see pose())."""
+    full_circle 1 resolves the heading over the full circle (see pose()); rotate_target 0 rotates
+    the source f by theta (reading A8), 1 is Alg. 1's own stage 2: g turned back by theta, then the
+    translation found between f and it turned by theta (see pose())."""
+    if int(rotate_target) == 1 and int(full_circle) == 1:
+        raise ValueError("rotate_target 1 is defined for the half-circle search only")
     return dict(n=int(n), n_theta=int(n_theta), n_r=int(n_r), temp_theta=float(temp_theta),
                 temp_xy=float(temp_xy), delta_xy=float(delta_xy), window=int(window),
                 pad_mode=int(pad_mode), score_norm=int(score_norm), band_lo=float(band_lo),
                 band_hi=float(n / 2 if band_hi is None else band_hi), angle_score=int(angle_score),
-                full_circle=int(full_circle))
+                full_circle=int(full_circle), rotate_target=int(rotate_target))
 
 
 def lags(n):
@@ -256,6 +260,22 @@ def pose(f, g, cfg, keep=False):
     d_theta = np.pi / nt
     theta = float(np.sum(p_theta * lags(nt) * d_theta))
     # stage 2 (Alg. 1 stage 2)
+    if cfg.get("rotate_target", 0) == 1:
+        # Alg. 1 as printed: Rotate g, correlate f with it, then BuildSO2 / MatMul on the translation.
+        # With g(x) = f'(x - t) and f' = rotate(f, theta) (reading A8), g turned back by theta is f
+        # shifted by t' = R(-theta) t, so the scores peak at t' and t = R(theta) t'
+        gr = rotate(g, -theta)
+        c_xy = xcorr2d(f, gr, cfg["pad_mode"])
+        p_xy = soft_argmax(c_xy, cfg["temp_xy"], cfg["score_norm"])
+        s = lags(n) * cfg["delta_xy"]
+        tpx = float(np.sum(p_xy * s[None, :]))
+        tpy = float(np.sum(p_xy * s[:, None]))
+        ct, st = np.cos(theta), np.sin(theta)
+        out = dict(theta=theta, tx=float(ct * tpx - st * tpy), ty=float(st * tpx + ct * tpy), c_theta=c_theta,
+                   c_xy=c_xy, tpx=tpx, tpy=tpy)
+        if keep:
+            out.update(Ff=Ff, Fg=Fg, af=af, ag=ag, pf=pf, pg=pg, p_theta=p_theta, gr=gr, p_xy=p_xy)
+        return out
     fr = rotate(f, theta)
     c_xy = xcorr2d(fr, g, cfg["pad_mode"])
     if cfg.get("full_circle", 0) == 1:
@@ -448,10 +468,23 @@ def pose_backward(f, g, cfg, dpose):
     r = pose(f, g, cfg, keep=True)
     dth_out, dtx, dty = (float(v) for v in dpose)
     s = lags(n) * cfg["delta_xy"]
-    q_xy = dtx * s[None, :] + dty * s[:, None]
-    dc_xy = soft_argmax_backward(r["c_xy"], r["p_xy"], q_xy, cfg["temp_xy"], cfg["score_norm"])
-    dfr, dg = xcorr2d_backward(r["fr"], g, dc_xy, cfg["pad_mode"])
-    df, dth_rot = rotate_backward(f, r["theta"], dfr)
+    if cfg.get("rotate_target", 0) == 1:
+        # t = R(theta) t': dt' = R(theta)^T dt, and d theta gains dt . (dR/dtheta) t'; the
+        # scores' adjoint reaches f directly and g through Rotate(., -theta)
+        th = r["theta"]
+        ct, st = np.cos(th), np.sin(th)
+        dtpx, dtpy = ct * dtx + st * dty, -st * dtx + ct * dty
+        dth_t = dtx * (-st * r["tpx"] - ct * r["tpy"]) + dty * (ct * r["tpx"] - st * r["tpy"])
+        q_xy = dtpx * s[None, :] + dtpy * s[:, None]
+        dc_xy = soft_argmax_backward(r["c_xy"], r["p_xy"], q_xy, cfg["temp_xy"], cfg["score_norm"])
+        df, dgr = xcorr2d_backward(np.asarray(f, np.float64), r["gr"], dc_xy, cfg["pad_mode"])
+        dg, dth_rot_arg = rotate_backward(g, -th, dgr)
+        dth_rot = dth_t - dth_rot_arg
+    else:
+        q_xy = dtx * s[None, :] + dty * s[:, None]
+        dc_xy = soft_argmax_backward(r["c_xy"], r["p_xy"], q_xy, cfg["temp_xy"], cfg["score_norm"])
+        dfr, dg = xcorr2d_backward(r["fr"], g, dc_xy, cfg["pad_mode"])
+        df, dth_rot = rotate_backward(f, r["theta"], dfr)
     dth = dth_out + dth_rot
     q_t = dth * lags(nt) * (np.pi / nt)
     dc_t = soft_argmax_backward(r["c_theta"], r["p_theta"], q_t, cfg["temp_theta"], cfg["score_norm"])

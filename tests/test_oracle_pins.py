@@ -499,3 +499,46 @@ def test_pose_gradient_matches_central_differences_full_circle():
             fd = sum(dpose[i] * (ra[k] - rb[k]) / (2 * h) for i, k in enumerate(("theta", "tx", "ty")))
             grad = (df if which == 0 else dg)
             assert abs(fd - grad[y, x]) <= 1e-6 * max(1.0, np.max(np.abs(grad))), (which, y, x, fd, grad[y, x])
+
+
+@pytest.mark.parametrize("deg,tx,ty", [(20.0, 6.0, -3.0), (-14.0, -4.0, 5.0)])
+def test_rotate_target_g_recovers_the_pose(deg, tx, ty):
+    # Alg. 1's own stage 2 (g turned back by theta, then t = R(theta) t'): on a scene with a known
+    # pose the scores peak at t' = R(-theta) t -- more than a pixel away from t at these angles, so
+    # a wrong sign in either rotation shows -- and the reported translation is t
+    n = 128
+    th = math.radians(deg)
+    f, g = synth.make_pair(n, 60, 8, th, tx, ty, seed=781, index=int(deg) + 900)
+    lit = O.pose(f, g, O.make_cfg(n, 128, 64, temp_theta=0.2, rotate_target=1))
+    src = O.pose(f, g, O.make_cfg(n, 128, 64, temp_theta=0.2))
+    assert lit["theta"] == src["theta"]                          # stage 1 is the same
+    assert abs(lit["theta"] - th) < math.radians(1.0)
+    ct, st = math.cos(th), math.sin(th)
+    tp = (ct * tx + st * ty, -st * tx + ct * ty)
+    assert math.hypot(tp[0] - tx, tp[1] - ty) > 1.0
+    assert abs(lit["tpx"] - tp[0]) < 0.5 and abs(lit["tpy"] - tp[1]) < 0.5
+    assert abs(lit["tx"] - tx) < 0.5 and abs(lit["ty"] - ty) < 0.5
+    with pytest.raises(ValueError):
+        O.make_cfg(n, 128, 64, rotate_target=1, full_circle=1)
+
+
+def test_pose_gradient_matches_central_differences_rotate_target_g():
+    n = 128
+    f, g = synth.make_pair(n, 40, 6, math.radians(15.0), 3.0, -2.0, seed=782, index=2)
+    cfg = O.make_cfg(n, 128, 64, temp_theta=0.5, rotate_target=1)
+    dpose = np.array([0.4, -0.6, 0.9])
+    df, dg, _ = O.pose_backward(f, g, cfg, dpose)
+    rng = np.random.default_rng(11)
+    h = 1e-4
+    for _ in range(3):
+        y, x = rng.integers(20, 108, 2)
+        for which in (0, 1):
+            img = (f if which == 0 else g).astype(np.float64)
+            e = np.zeros_like(img)
+            e[y, x] = h
+            a = (img + e, g) if which == 0 else (f, img + e)
+            b = (img - e, g) if which == 0 else (f, img - e)
+            ra, rb = O.pose(*a, cfg), O.pose(*b, cfg)
+            fd = sum(dpose[i] * (ra[k] - rb[k]) / (2 * h) for i, k in enumerate(("theta", "tx", "ty")))
+            grad = (df if which == 0 else dg)
+            assert abs(fd - grad[y, x]) <= 1e-6 * max(1.0, np.max(np.abs(grad))), (which, y, x, fd, grad[y, x])
