@@ -72,6 +72,10 @@ typedef struct fmbym_size_cfg {
                           A9); 1: the full circle, stage 2 run at theta and theta + pi and the one
                           with the higher translation peak kept (the extension of Sec. V for
                           arbitrary headings; three stage-2 passes) */
+    int rotate_target; /* 0: stage 2 rotates the source, f' = Rotate(f, theta), and t is the
+                          translation's soft-argmax (reading A8); 1: Alg. 1's own stage 2, g turned
+                          back by theta, f correlated with it, and t = R(theta) t' from that
+                          soft-argmax t' (BuildSO2 / MatMul); half circle only (full_circle 0) */
 } fmbym_size_cfg;
 
 /* Handle flags.

@@ -23,7 +23,7 @@ class SizeCfg(ctypes.Structure):
                 ("temp_theta", ctypes.c_float), ("temp_xy", ctypes.c_float), ("delta_xy", ctypes.c_float),
                 ("window", ctypes.c_int), ("pad_mode", ctypes.c_int), ("score_norm", ctypes.c_int),
                 ("band_lo", ctypes.c_float), ("band_hi", ctypes.c_float), ("angle_score", ctypes.c_int),
-                ("full_circle", ctypes.c_int)]
+                ("full_circle", ctypes.c_int), ("rotate_target", ctypes.c_int)]
 
 
 class Config(ctypes.Structure):

@@ -157,6 +157,8 @@ std::string validate(const fmbym_size_cfg& c) {
     if (c.score_norm != 0 && c.score_norm != 1) return "score_norm must be 0 or 1";
     if (c.angle_score != 0 && c.angle_score != 1) return "angle_score must be 0 or 1";
     if (c.full_circle != 0 && c.full_circle != 1) return "full_circle must be 0 or 1";
+    if (c.rotate_target != 0 && c.rotate_target != 1) return "rotate_target must be 0 or 1";
+    if (c.rotate_target == 1 && c.full_circle == 1) return "rotate_target 1 needs full_circle 0";
     if (!(c.band_lo >= 0.f) || !(c.band_hi >= c.band_lo)) return "need 0 <= band_lo <= band_hi";
     return "";
 }
@@ -176,6 +178,7 @@ cudaError_t build_plan(HostPlan& hp) {
     d.score_norm = c.score_norm;
     d.angle_score = c.angle_score;
     d.full_circle = c.full_circle;
+    d.rotate_target = c.rotate_target;
     d.temp_theta = c.temp_theta;
     d.temp_xy = c.temp_xy;
     d.delta_xy = c.delta_xy;
@@ -826,6 +829,8 @@ int fmbym_pose_exhaustive(fmbym_handle* h, void* stream, int n_pairs, int size, 
     if (n_pairs == 0) return FMBYM_OK;
     if (size < 0 || size >= (int)h->plans.size()) return fail(h, FMBYM_ERR_INVALID_ARG, "size index out of range");
     if (n_angles < 1 || !angles) return fail(h, FMBYM_ERR_INVALID_ARG, "need n_angles >= 1 host angles");
+    if (h->plans[size].cfg.rotate_target != 0)
+        return fail(h, FMBYM_ERR_INVALID_ARG, "the exhaustive search rotates the source (rotate_target 0)");
     if (!f || !g || !pose) return fail(h, FMBYM_ERR_INVALID_ARG, "f, g and pose must not be NULL");
     if (!aligned16(f) || !aligned16(g)) return fail(h, FMBYM_ERR_INVALID_ARG, "f and g must be 16-byte aligned");
     if (n_pairs < 0 || n_pairs > h->max_pairs) return fail(h, FMBYM_ERR_WORKSPACE, "n_pairs exceeds max_pairs");

@@ -82,9 +82,19 @@ __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long*
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
     const int k = threadIdx.x / T, jt = threadIdx.x % T, i = i0 + 2 * k;
     const long long pr = tab[3 * q + 2];
-    const float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
-    if (threadIdx.x == 0)
-        xy_adjoint_scalars(p, xm + (size_t)q * 8, fwd_pose[3 * pr + 1], fwd_pose[3 * pr + 2], dtx, dty, N, r);
+    float dtx = dpose[3 * pr + 1], dty = dpose[3 * pr + 2];
+    float tx = fwd_pose[3 * pr + 1], ty = fwd_pose[3 * pr + 2];
+    if (p.rotate_target) {   // t = R(theta) t': the soft-argmax sees t' and dt' = R(theta)^T dt
+        float sn, cs;
+        sincosf(fwd_pose[3 * pr], &sn, &cs);
+        const float a = cs * dtx + sn * dty, b = -sn * dtx + cs * dty;
+        const float c = cs * tx + sn * ty, d = -sn * tx + cs * ty;
+        dtx = a;
+        dty = b;
+        tx = c;
+        ty = d;
+    }
+    if (threadIdx.x == 0) xy_adjoint_scalars(p, xm + (size_t)q * 8, tx, ty, dtx, dty, N, r);
     __syncthreads();
     const float* c = cxy + (size_t)q * N * N + (size_t)i * N;
     first_pass_global<P>(sm + k * SL, 1, jt, [&](int x) {
@@ -237,12 +247,13 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
 }
 
 // Inverse row FFTs of the two adjoint spectra, keep x in [0, N), scale 1/P^2:
-// z = 0 -> d f' (workspace), z = 1 -> d g (stage-2 part, written to the caller's buffer).  The
+// z = 0 -> d f' (workspace), z = 1 -> d g (stage-2 part, written to the caller's buffer); under
+// rotate_target 1, z = 0 -> d f (caller) and z = 1 -> d g' (workspace).  The
 // first pass builds its inputs from global memory and the last pass stores straight to it.
 template <int N, int P>
 __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* __restrict__ tab,
                                                     const float2* __restrict__ b2, float* __restrict__ gfr,
-                                                    float* __restrict__ dg, int B) {
+                                                    float* __restrict__ df, float* __restrict__ dg, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
     extern __shared__ float2 sm[];
@@ -252,7 +263,9 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
     first_pass_global<P, +1>(sm + k * SL, 1, j, [&](int x) { return pack_inverse(ra, ra + W, x, P); });
     __syncthreads();
     const float scale = 1.f / ((float)P * (float)P);
-    float* out = (s == 0 ? gfr + (size_t)q * N * N : dg + tab[3 * q]) + (size_t)y * N;
+    // the rotated operand's gradient goes to the workspace for the Rotate adjoint, the other one
+    // straight to the caller (f' and g by default; f and g' under rotate_target 1)
+    float* out = (s == p.rotate_target ? gfr + (size_t)q * N * N : (s == 0 ? df : dg) + tab[3 * q]) + (size_t)y * N;
     rest_global<P, +1>(sm + k * SL, 1, j, p.tw_p, [&](int x, float2 z) {
         if (x < N) {
             out[x] = z.x * scale;
@@ -276,19 +289,24 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
 // bilinear weight by as much; the forward's error-free coordinates decide the scores, these only
 // their gradient).  d theta is reduced per pair (last block adds the block sums in order) into
 // bsc[q][8] together with the direct term dL/dtheta.
+// Under rotate_target 1 the rotated scan is g, turned by -theta: f and df here are g and dg, the
+// sine changes sign, d theta takes the rotation term with the opposite sign, and the translation
+// t = R(theta) t' adds dt . (dR/dtheta) t' = t_x dt_y - t_y dt_x (fwd_pose holds t).
 template <int N, int PX>
 __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* __restrict__ tab,
                                                     const float* __restrict__ f, const float* __restrict__ th,
                                                     const float* __restrict__ gfr, const float* __restrict__ dpose,
                                                     float* __restrict__ df, float* __restrict__ gpart,
-                                                    unsigned* __restrict__ cnt, float* __restrict__ bsc) {
+                                                    unsigned* __restrict__ cnt, float* __restrict__ bsc,
+                                                    const float* __restrict__ fwd_pose) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     __shared__ float red[32];
     __shared__ bool last;
     constexpr int NB = N * N / (kThreads * PX);
     const int q = blockIdx.y;
     const float* t = th + 8 * q;
-    const float ct = t[1] + t[2], stn = t[3] + t[4];
+    const float sg = p.rotate_target ? -1.f : 1.f;
+    const float ct = t[1] + t[2], stn = sg * (t[3] + t[4]);
     const float c = 0.5f * N;
     const float* src = f + tab[3 * q];
     const float* d = gfr + (size_t)q * N * N;
@@ -351,7 +369,11 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
         for (int i = threadIdx.x; i < NB; i += kThreads) s += g[i];
         s = block_reduce<false>(s, red);
         if (threadIdx.x == 0) {
-            bsc[(size_t)q * 16 + 8] = dpose[3 * tab[3 * q + 2]] + s;
+            const long long pr = tab[3 * q + 2];
+            float dth = dpose[3 * pr] + sg * s;
+            if (p.rotate_target)
+                dth += fwd_pose[3 * pr + 1] * dpose[3 * pr + 2] - fwd_pose[3 * pr + 2] * dpose[3 * pr + 1];
+            bsc[(size_t)q * 16 + 8] = dth;
             cnt[q] = 0u;
         }
     }
@@ -634,9 +656,9 @@ static void launch_stage1_adjoint(const DevPlan& p, const Ws& w, int B, cudaStre
 
 template <int N, int PX>
 static void launch_b_rot(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
-                         const float* dpose, float* df, cudaStream_t st) {
+                         const float* dpose, float* df, cudaStream_t st, const float* fwd_pose) {
     launch_pdl(k_b_rot<N, PX>, dim3(N * N / (kThreads * PX), B), kThreads, 0, st, p, tab, f, w.th, w.gfr, dpose, df, w.gpart,
-                                                                          w.cnt, w.bsc);
+                                                                          w.cnt, w.bsc, fwd_pose);
 }
 
 template <int N, int P>
@@ -668,13 +690,13 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
         launch_pdl(k_b_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2, B);
     }
     w.tr->before(K_B_C2R, st);
-    launch_pdl(k_b_c2r<N, P>, dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st, p, tab, w.b2, w.gfr, dg, B);
+    launch_pdl(k_b_c2r<N, P>, dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st, p, tab, w.b2, w.gfr, df, dg, B);
     w.tr->before(K_B_ROT, st);
     switch (p.rot_px) {
-        case 1: launch_b_rot<N, 1>(p, w, B, tab, f, dpose, df, st); break;
-        case 2: launch_b_rot<N, 2>(p, w, B, tab, f, dpose, df, st); break;
-        case 8: launch_b_rot<N, 8>(p, w, B, tab, f, dpose, df, st); break;
-        default: launch_b_rot<N, 4>(p, w, B, tab, f, dpose, df, st); break;
+        case 1: launch_b_rot<N, 1>(p, w, B, tab, p.rotate_target ? g : f, dpose, p.rotate_target ? dg : df, st, fwd_pose); break;
+        case 2: launch_b_rot<N, 2>(p, w, B, tab, p.rotate_target ? g : f, dpose, p.rotate_target ? dg : df, st, fwd_pose); break;
+        case 8: launch_b_rot<N, 8>(p, w, B, tab, p.rotate_target ? g : f, dpose, p.rotate_target ? dg : df, st, fwd_pose); break;
+        default: launch_b_rot<N, 4>(p, w, B, tab, p.rotate_target ? g : f, dpose, p.rotate_target ? dg : df, st, fwd_pose); break;
     }
     if (p.nt == 128) launch_stage1_adjoint<128>(p, w, B, st);
     else if (p.nt == 256) launch_stage1_adjoint<256>(p, w, B, st);

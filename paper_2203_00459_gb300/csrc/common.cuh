@@ -59,7 +59,7 @@ struct PolarSample {
 struct DevPlan {
     int n, p, nt, nr;      // scan side, padded side (2N or N), angle bins, radii
     int m_lo, m_hi;        // band-pass: keep integer rho^2 in [m_lo, m_hi]
-    int window, score_norm, angle_score, full_circle;
+    int window, score_norm, angle_score, full_circle, rotate_target;
     float temp_theta, temp_xy, delta_xy;
     const float* win;      // [N] periodic Hann
     const float2* tw_n;    // [N]  exp(-2 pi i k / N)

@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
 
 // Rows of the rotated source f' (z = 0, rotation on load) and of g (z = 1), zero-padded to P,
 // real row FFTs packed two rows per complex FFT, output u in [0, P/2) (DC/Nyquist packed in 0).
+// Under Alg. 1's own stage 2 (rotate_target 1) f is read as it is and g is turned back by theta.
 // The first pass takes its inputs straight from the gather (no staging in shared memory).
 template <int N, int P>
 __global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
@@ -297,9 +298,10 @@ __global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long lo
     const int k = threadIdx.x / T, j = threadIdx.x % T;
     const int r = r0 + 2 * k;                                 // rows r and r + 1
     const float* __restrict__ src = (s ? g : f) + tab[3 * q];
-    if (s == 0) {
+    if (s == p.rotate_target) {
         const float* t = th + 8 * q;
-        const RotFixed rf = rot_fixed(t[1], t[2], t[3], t[4], N);
+        const float sg = p.rotate_target ? -1.f : 1.f;   // g turns by -theta
+        const RotFixed rf = rot_fixed(t[1], t[2], sg * t[3], sg * t[4], N);
         // rows r and r + 1: (Y - c) steps add S to px and C to py
         const long long pxr = rf.px0 + rf.S * r, pyr = rf.py0 + rf.C * r;
         first_pass_global<P>(sm + k * SL, 1, j, [&](int x) {
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
                                                   const float* __restrict__ cxy_ws, const float* __restrict__ cxy_out,
                                                   const float* __restrict__ st, int nblk, float* __restrict__ sx,
                                                   unsigned* __restrict__ cnt, float* __restrict__ pose,
-                                                  float* __restrict__ xm) {
+                                                  float* __restrict__ xm, const float* __restrict__ th) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     __shared__ float red[32 * 6];
     __shared__ float stat[4];
@@ -557,8 +559,16 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
             zy += o[8 * i + 5];
         }
         const long long pr = tab[3 * q + 2];
-        pose[3 * pr + 1] = p.delta_xy * (bx / a);
-        pose[3 * pr + 2] = p.delta_xy * (by / a);
+        const float tpx = p.delta_xy * (bx / a), tpy = p.delta_xy * (by / a);
+        if (p.rotate_target) {   // BuildSO2 / MatMul of Alg. 1: t = R(theta) t'
+            const float* t = th + 8 * q;
+            const float ct = t[1] + t[2], sn = t[3] + t[4];
+            pose[3 * pr + 1] = ct * tpx - sn * tpy;
+            pose[3 * pr + 2] = sn * tpx + ct * tpy;
+        } else {
+            pose[3 * pr + 1] = tpx;
+            pose[3 * pr + 2] = tpy;
+        }
         float* m = xm + (size_t)q * 8;
         m[0] = mu;
         m[1] = sd;
@@ -708,7 +718,7 @@ static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const lon
     w.tr->before(K_S2_C2R, st);
     launch_pdl(k_s2_c2r<N, P>, dim3(nblk, B), TB2, smem_rows<P>(), st, p, tab, w.s3, w.cxy, c_xy, w.st, B);
     w.tr->before(K_SXY, st);
-    launch_pdl(k_sxy<N>, dim3(kSplitXY, B), kThreads, 0, st, p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose, w.xm);
+    launch_pdl(k_sxy<N>, dim3(kSplitXY, B), kThreads, 0, st, p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose, w.xm, w.th);
     w.tr->close(st);
     return cudaGetLastError();
 }

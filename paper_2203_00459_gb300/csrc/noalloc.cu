@@ -122,8 +122,9 @@ std::string check_cfg(const fmbym_size_cfg& c) {
     if (c.n_r < 1 || c.n_r > c.n / 2) return "n_r must be in [1, n/2]";
     if (!(c.temp_theta > 0.f) || !(c.temp_xy > 0.f) || !(c.delta_xy > 0.f))
         return "temperatures and delta_xy must be positive";
-    if ((c.window | c.pad_mode | c.score_norm | c.angle_score | c.full_circle) & ~1)
-        return "window, pad_mode, score_norm, angle_score and full_circle must be 0 or 1";
+    if ((c.window | c.pad_mode | c.score_norm | c.angle_score | c.full_circle | c.rotate_target) & ~1)
+        return "window, pad_mode, score_norm, angle_score, full_circle and rotate_target must be 0 or 1";
+    if (c.rotate_target == 1 && c.full_circle == 1) return "rotate_target 1 needs full_circle 0";
     if (!(c.band_lo >= 0.f) || !(c.band_hi >= c.band_lo)) return "need 0 <= band_lo <= band_hi";
     return "";
 }
@@ -161,6 +162,7 @@ int fmbym_pose_noalloc(void* stream, const fmbym_size_cfg* cfg, int n_pairs, con
     p.score_norm = cfg->score_norm;
     p.angle_score = cfg->angle_score;
     p.full_circle = cfg->full_circle;
+    p.rotate_target = cfg->rotate_target;
     p.temp_theta = cfg->temp_theta;
     p.temp_xy = cfg->temp_xy;
     p.delta_xy = cfg->delta_xy;

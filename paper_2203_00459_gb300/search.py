@@ -14,13 +14,13 @@ from . import _lib
 
 
 def size_cfg(n, n_theta, n_r, temp_theta=1.0, temp_xy=1.0, delta_xy=1.0, window=1, pad_mode=0,
-             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0, full_circle=0):
+             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0, full_circle=0, rotate_target=0):
     """Parameters of one scan size (fmbym_size_cfg); band_hi defaults to N/2."""
     return dict(n=int(n), n_theta=int(n_theta), n_r=int(n_r), temp_theta=float(temp_theta),
                 temp_xy=float(temp_xy), delta_xy=float(delta_xy), window=int(window), pad_mode=int(pad_mode),
                 score_norm=int(score_norm), band_lo=float(band_lo),
                 band_hi=float(n / 2 if band_hi is None else band_hi), angle_score=int(angle_score),
-                full_circle=int(full_circle))
+                full_circle=int(full_circle), rotate_target=int(rotate_target))
 
 
 def _ptr(t):

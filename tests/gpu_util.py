@@ -27,7 +27,7 @@ def argmax_ok(gpu, ref):
 def oracle_cfg(c):
     return O.make_cfg(c["n"], c["n_theta"], c["n_r"], c["temp_theta"], c["temp_xy"], c["delta_xy"],
                       c["window"], c["pad_mode"], c["score_norm"], c["band_lo"], c["band_hi"],
-                      c.get("angle_score", 0), c.get("full_circle", 0))
+                      c.get("angle_score", 0), c.get("full_circle", 0), c.get("rotate_target", 0))
 
 
 def check_pair(f, g, cfg, pose, c_theta=None, c_xy=None, tag=""):
@@ -43,7 +43,11 @@ def check_pair(f, g, cfg, pose, c_theta=None, c_xy=None, tag=""):
         assert surf_err(c_theta, r["c_theta"]) <= TOL_SURF, (tag, "c_theta", surf_err(c_theta, r["c_theta"]))
         assert argmax_ok(c_theta, r["c_theta"]), (tag, "argmax c_theta")
     if c_xy is not None:
-        ref = O.xcorr2d(O.rotate(f, float(np.float32(pose[0]))), g, oc["pad_mode"])
+        th = float(np.float32(pose[0]))
+        if oc.get("rotate_target", 0) == 1:   # Alg. 1's own stage 2 correlates f with g turned back
+            ref = O.xcorr2d(f, O.rotate(g, -th), oc["pad_mode"])
+        else:
+            ref = O.xcorr2d(O.rotate(f, th), g, oc["pad_mode"])
         assert surf_err(c_xy, ref) <= TOL_SURF, (tag, "c_xy", surf_err(c_xy, ref))
         assert argmax_ok(c_xy, ref), (tag, "argmax c_xy")
     return r

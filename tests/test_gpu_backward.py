@@ -208,3 +208,31 @@ def test_adjoint_full_circle(lib):
     cfg = lib.size_cfg(128, 128, 64, temp_theta=0.2, full_circle=1)
     df, dg = gpu_backward(lib, cfg, f, g, DP[:2])
     check_against_oracle(cfg, f, g, DP[:2], df, dg, "full_circle")
+
+
+def test_adjoint_rotate_target_g(lib):
+    """The adjoint of Alg. 1's own stage 2 (g turned back by theta, t = R(theta) t') against the
+    oracle's, and the training call bitwise equal to the three separate calls under it."""
+    import math
+    from paper_2203_00459_gb300 import _lib
+    from paper_2203_00459_gb300.search import PoseSearch
+    pairs = [synth.make_pair(128, 40, 6, math.radians(d), 3.0, -2.0, seed=784, index=i)
+             for i, d in enumerate((15.0, -9.0))]
+    f = np.stack([a for a, _ in pairs])
+    g = np.stack([b for _, b in pairs])
+    cfg = lib.size_cfg(128, 128, 64, temp_theta=0.5, rotate_target=1)
+    df, dg = gpu_backward(lib, cfg, f, g, DP[:2])
+    check_against_oracle(cfg, f, g, DP[:2], df, dg, "rotate_target")
+    s = PoseSearch([cfg], max_pairs=2, flags=_lib.FLAG_GRAPH)
+    F, G = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    gt = torch.tensor([[0.25, 3.0, -2.0], [-0.15, 3.0, -2.0]], dtype=torch.float32).cuda()
+    pose, loss, dpose, dF, dG = s.pose_train(F, G, gt, kind=1)
+    pose2 = s.pose(F, G)["pose"]
+    loss2, dpose2 = s.pose_loss(pose2, gt, kind=1)
+    dF2, dG2 = s.pose_backward(F, G, dpose2)
+    torch.cuda.synchronize()
+    for a, b in ((pose, pose2), (dpose, dpose2), (dF, dF2), (dG, dG2)):
+        assert torch.equal(a, b)
+    with pytest.raises(_lib.FmbymError):
+        PoseSearch([lib.size_cfg(128, 128, 64, rotate_target=1, full_circle=1)], max_pairs=1)
+    s.close()

@@ -55,3 +55,8 @@ def test_exhaustive_rejects_bad_arguments(search):
     with pytest.raises(_lib.FmbymError):
         s.pose_exhaustive(f2, f2, np.zeros(3, np.float32))
     s.close()
+    # the comparator rotates the source; Alg. 1's g-rotating stage 2 is refused there
+    s = search.PoseSearch([search.size_cfg(128, 128, 64, rotate_target=1)], max_pairs=1)
+    with pytest.raises(_lib.FmbymError):
+        s.pose_exhaustive(f, f, np.zeros(3, np.float32))
+    s.close()

@@ -190,3 +190,21 @@ def test_full_circle_heading(lib, n, nt, nr):
         check_pair(f[i], g[i], cfg, o["pose"][i], o["c_theta"][nt * i:nt * (i + 1)], o["c_xy"][i], f"fc{i}")
         err = (o["pose"][i][0] - math.radians(degs[i]) + math.pi) % (2 * math.pi) - math.pi
         assert abs(err) < math.radians(1.5), (degs[i], o["pose"][i])
+
+
+@pytest.mark.parametrize("n,nt,nr", [(128, 128, 64), (256, 400, 128)])
+def test_rotate_target_g(lib, n, nt, nr):
+    """Alg. 1's own stage 2 (rotate_target 1): g turned back by theta, f correlated with it, and
+    t = R(theta) t'; the scores and the pose against the oracle's, and the pose against the truth."""
+    import math
+    poses = [(20.0, 6.0, -3.0), (-14.0, -4.0, 5.0), (3.0, 2.0, 1.0)]
+    pairs = [synth.make_pair(n, n * n // 300, n // 16, math.radians(d), tx, ty, seed=783, index=i)
+             for i, (d, tx, ty) in enumerate(poses)]
+    f = np.stack([a for a, _ in pairs])
+    g = np.stack([b for _, b in pairs])
+    cfg = lib.size_cfg(n, nt, nr, temp_theta=0.2, rotate_target=1)
+    o = run(lib, cfg, f, g)
+    for i, (d, tx, ty) in enumerate(poses):
+        check_pair(f[i], g[i], cfg, o["pose"][i], o["c_theta"][nt * i:nt * (i + 1)], o["c_xy"][i], f"rg{i}")
+        assert abs(o["pose"][i][0] - math.radians(d)) < math.radians(1.0)
+        assert abs(o["pose"][i][1] - tx) < 0.5 and abs(o["pose"][i][2] - ty) < 0.5, (poses[i], o["pose"][i])
