@@ -684,7 +684,7 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
         const int i = L - 2 - j;
         const Layer& deep = (j == 0) ? u->layers[2 * L - 1] : u->layers[2 * L + 2 * (j - 1) + 1];
         ++u->launches;
-        k_upsample<<<row_grid(2 * deep.W * (deep.cout / 8), n * 2 * deep.H), kBlock, 0, st>>>(
+        k_upsample<<<row_grid(deep.W * (deep.cout / 8), n * deep.H), kBlock, 0, st>>>(
             deep.a, u->upped[i], n, deep.H, deep.W, deep.cout);
         e = conv_bn(u->layers[2 * L + 2 * j]);
         if (e == cudaSuccess) e = conv_bn(u->layers[2 * L + 2 * j + 1]);
@@ -771,7 +771,7 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         if (e != cudaSuccess) break;
         Layer& deep = (j == 0) ? u->layers[2 * L - 1] : u->layers[2 * L + 2 * (j - 1) + 1];
         ++u->launches;
-        k_upsample_bwd<<<row_grid(deep.W * (deep.cout / 4), n * deep.H), kBlock, 0, st>>>(
+        k_upsample_bwd<<<row_grid((deep.W / 2) * (deep.cout / 4), n * (deep.H / 2)), kBlock, 0, st>>>(
             u->dup[i], deep.da, n, deep.H, deep.W, deep.cout);
         e = cudaGetLastError();
     }

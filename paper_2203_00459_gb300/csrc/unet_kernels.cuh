@@ -966,41 +966,52 @@ __device__ __forceinline__ void up_src(int o, int n, int& i0, int& i1, float& l0
     l0 = 1.f - l1;
 }
 
-// Eight channels (16 bytes) of one output pixel per thread; rows = B * 2h.
+// Eight channels (16 bytes) of one input pixel (y, x) per thread, which writes its 2 x 2 output
+// pixels (2y + dy, 2x + dx): with align_corners = False at scale 2 each of them is the bilinear
+// mix of rows y - 1 + dy, y + dy and columns x - 1 + dx, x + dx with weights (1/4, 3/4) for
+// d = 0 and (3/4, 1/4) for d = 1, and the edge clamping of the source index is the clamping of
+// those rows and columns to the image (up_src gives the same weights, and the same arithmetic
+// order is kept).  rows = B * h.
 __global__ void k_upsample(const bf16* __restrict__ a, bf16* __restrict__ u, int B, int h, int w, int C) {
     const int H = 2 * h, W = 2 * w, q = C / 8;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= W * q) return;
-    const int c = (j % q) * 8, X = j / q;
-    int x0, x1;
-    float lx0, lx1;
-    up_src(X, w, x0, x1, lx0, lx1);
-    for (int row = blockIdx.y; row < B * H; row += gridDim.y) {
-        const int b = row / H, Y = row % H;
-        int y0, y1;
-        float ly0, ly1;
-        up_src(Y, h, y0, y1, ly0, ly1);
+    if (j >= w * q) return;
+    const int c = (j % q) * 8, x = j / q;
+    const int xs[3] = {max(x - 1, 0), x, min(x + 1, w - 1)};
+    for (int row = blockIdx.y; row < B * h; row += gridDim.y) {
+        const int b = row / h, y = row % h;
+        const int ys[3] = {max(y - 1, 0), y, min(y + 1, h - 1)};
         const bf16* base = a + (size_t)b * h * w * C + c;
-        const uint4 v00 = *reinterpret_cast<const uint4*>(base + ((size_t)y0 * w + x0) * C);
-        const uint4 v01 = *reinterpret_cast<const uint4*>(base + ((size_t)y0 * w + x1) * C);
-        const uint4 v10 = *reinterpret_cast<const uint4*>(base + ((size_t)y1 * w + x0) * C);
-        const uint4 v11 = *reinterpret_cast<const uint4*>(base + ((size_t)y1 * w + x1) * C);
-        const uint32_t* p00 = &v00.x;
-        const uint32_t* p01 = &v01.x;
-        const uint32_t* p10 = &v10.x;
-        const uint32_t* p11 = &v11.x;
-        uint32_t o[4];
+        uint4 v[3][3];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float res[2];
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int hlf = 0; hlf < 2; ++hlf) {
-                auto f = [&](uint32_t wd) { return __uint_as_float(hlf ? (wd & 0xffff0000u) : (wd << 16)); };
-                res[hlf] = ly0 * (lx0 * f(p00[k]) + lx1 * f(p01[k])) + ly1 * (lx0 * f(p10[k]) + lx1 * f(p11[k]));
+            for (int k = 0; k < 3; ++k) v[i][k] = *reinterpret_cast<const uint4*>(base + ((size_t)ys[i] * w + xs[k]) * C);
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const float ly0 = dy ? 0.75f : 0.25f, ly1 = 1.f - ly0;
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const float lx0 = dx ? 0.75f : 0.25f, lx1 = 1.f - lx0;
+                const uint32_t* p00 = &v[dy][dx].x;
+                const uint32_t* p01 = &v[dy][dx + 1].x;
+                const uint32_t* p10 = &v[dy + 1][dx].x;
+                const uint32_t* p11 = &v[dy + 1][dx + 1].x;
+                uint32_t o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float res[2];
+#pragma unroll
+                    for (int hlf = 0; hlf < 2; ++hlf) {
+                        auto f = [&](uint32_t wd) { return __uint_as_float(hlf ? (wd & 0xffff0000u) : (wd << 16)); };
+                        res[hlf] = ly0 * (lx0 * f(p00[k]) + lx1 * f(p01[k])) + ly1 * (lx0 * f(p10[k]) + lx1 * f(p11[k]));
+                    }
+                    o[k] = pack2(__float2bfloat16_rn(res[0]), __float2bfloat16_rn(res[1]));
+                }
+                *reinterpret_cast<uint4*>(u + (((size_t)b * H + 2 * y + dy) * W + 2 * x + dx) * C + c) =
+                    make_uint4(o[0], o[1], o[2], o[3]);
             }
-            o[k] = pack2(__float2bfloat16_rn(res[0]), __float2bfloat16_rn(res[1]));
         }
-        *reinterpret_cast<uint4*>(u + (((size_t)b * H + Y) * W + X) * C + c) = make_uint4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -1014,39 +1025,59 @@ __device__ __forceinline__ float up_w(int o, int k, int n) {
 
 // Transpose of the upsampling in gather form: d a[k] = sum over the outputs o in [2k-1, 2k+2] (the
 // only ones whose two taps can reach k) of the forward weights times d u[o]; written (not added)
-// to da.  Four channels per thread; rows = B * h.
+// to da.  A thread takes a 2 x 2 block of input pixels (y0, y0 + 1) x (x0, x0 + 1) and four
+// channels: their outputs are the 6 x 6 window of rows 2 y0 - 1 .. 2 y0 + 4 and columns
+// 2 x0 - 1 .. 2 x0 + 4, each read once.  h and w even; rows = B * h / 2.
 __global__ void k_upsample_bwd(const float* __restrict__ du, float* __restrict__ da, int B, int h, int w, int C) {
     const int H = 2 * h, W = 2 * w, q = C / 4;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= w * q) return;
-    const int c = (j % q) * 4, x = j / q;
-    float wx[4];
+    if (j >= (w / 2) * q) return;
+    const int c = (j % q) * 4, x0 = 2 * (j / q);
+    // wx[i][k]: weight of output column 2 x0 - 1 + k on input column x0 + i (zero outside)
+    float wx[2][6];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int X = 2 * x - 1 + k;
-        wx[k] = (X >= 0 && X < W) ? up_w(X, x, w) : 0.f;
+    for (int k = 0; k < 6; ++k) {
+        const int X = 2 * x0 - 1 + k;
+        wx[0][k] = (k < 4 && X >= 0 && X < W) ? up_w(X, x0, w) : 0.f;
+        wx[1][k] = (k >= 2 && X < W) ? up_w(X, x0 + 1, w) : 0.f;
     }
-    for (int row = blockIdx.y; row < B * h; row += gridDim.y) {
-        const int b = row / h, y = row % h;
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int row = blockIdx.y; row < B * (h / 2); row += gridDim.y) {
+        const int b = row / (h / 2), y0 = 2 * (row % (h / 2));
+        float4 s[2][2];
 #pragma unroll
-        for (int ky = 0; ky < 4; ++ky) {
-            const int Y = 2 * y - 1 + ky;
-            const float wy = (Y >= 0 && Y < H) ? up_w(Y, y, h) : 0.f;
-            if (wy == 0.f) continue;
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int kx = 0; kx < 4; ++kx) {
-                if (wx[kx] == 0.f) continue;
-                const int X = 2 * x - 1 + kx;
-                const float wt = wy * wx[kx];
-                const float4 v = *reinterpret_cast<const float4*>(du + (((size_t)b * H + Y) * W + X) * C + c);
-                s.x += wt * v.x;
-                s.y += wt * v.y;
-                s.z += wt * v.z;
-                s.w += wt * v.w;
+            for (int k = 0; k < 2; ++k) s[i][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            const int Y = 2 * y0 - 1 + r;
+            if (Y < 0 || Y >= H) continue;
+            const float wy0 = r < 4 ? up_w(Y, y0, h) : 0.f, wy1 = r >= 2 ? up_w(Y, y0 + 1, h) : 0.f;
+            const float* rowp = du + ((size_t)b * H + Y) * W * C + c;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int X = 2 * x0 - 1 + k;
+                if (X < 0 || X >= W) continue;
+                const float4 v = *reinterpret_cast<const float4*>(rowp + (size_t)X * C);
+#pragma unroll
+                for (int iy = 0; iy < 2; ++iy) {
+                    const float wy = iy ? wy1 : wy0;
+#pragma unroll
+                    for (int ix = 0; ix < 2; ++ix) {
+                        const float wt = wy * wx[ix][k];
+                        s[iy][ix].x += wt * v.x;
+                        s[iy][ix].y += wt * v.y;
+                        s[iy][ix].z += wt * v.z;
+                        s[iy][ix].w += wt * v.w;
+                    }
+                }
             }
         }
-        *reinterpret_cast<float4*>(da + (((size_t)b * h + y) * w + x) * C + c) = s;
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < 2; ++ix)
+                *reinterpret_cast<float4*>(da + (((size_t)b * h + y0 + iy) * w + x0 + ix) * C + c) = s[iy][ix];
     }
 }
 
