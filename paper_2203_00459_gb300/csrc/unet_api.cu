@@ -383,6 +383,8 @@ int fmbym_unet_create(fmbym_unet** out, const fmbym_unet_config* cfg) {
     if (H <= 0 || W <= 0 || H % (8 << (L - 1)) || W % (8 << (L - 1)) || W % kTW)
         return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE,
                      "height and width must be multiples of 8*2^(L-1), and width of 32");
+    if ((long long)cfg->max_batch * H * W * cfg->channels[L - 1] / 4 >= (1LL << 31))
+        return ufail(nullptr, FMBYM_ERR_UNSUPPORTED_SIZE, "max_batch * height * width * channels too large");
     fmbym_unet* u = new fmbym_unet();
     u->levels = L;
     for (int i = 0; i < L; ++i) u->ch[i] = cfg->channels[i];
@@ -674,7 +676,7 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
         if (i > 0) {
             const Layer& prev = u->layers[2 * i - 1];
             ++u->launches;
-            k_maxpool<<<row_grid((prev.W / 2) * (prev.cout / 8), n * (prev.H / 2)), kBlock, 0, st>>>(
+            k_maxpool<<<blocks((long long)n * (prev.H / 2) * (prev.W / 2) * (prev.cout / 8)), kBlock, 0, st>>>(
                 prev.a, u->pooled[i], n, prev.H, prev.W, prev.cout);
         }
         e = conv_bn(u->layers[2 * i]);
@@ -789,7 +791,7 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         if (e != cudaSuccess) break;
         Layer& prev = u->layers[2 * i - 1];
         ++u->launches;
-        k_maxpool_bwd<<<row_grid((prev.W / 2) * prev.cout, n * (prev.H / 2)), kBlock, 0, st>>>(
+        k_maxpool_bwd<<<blocks((long long)n * (prev.H / 2) * (prev.W / 2) * (prev.cout / 4)), kBlock, 0, st>>>(
             prev.a, u->dpool[i], prev.da, n, prev.H, prev.W, prev.cout);
         e = cudaGetLastError();
     }

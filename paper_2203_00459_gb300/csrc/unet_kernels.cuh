@@ -900,57 +900,78 @@ __global__ void k_bn_bwd_dy(const float* __restrict__ y, const float* __restrict
 // stride of gridDim.y, blockIdx.x / threadIdx.x the pixels x channel vectors of one row, so that
 // all index arithmetic is 32-bit.  Channel counts are multiples of 8.
 
-// 2x2 max-pool, eight channels (16 bytes) per thread; rows = B * H / 2.
+// 2x2 max-pool, eight channels (16 bytes) per thread, flat 32-bit index over B * H/2 * W/2 * C/8.
 __global__ void k_maxpool(const bf16* __restrict__ a, bf16* __restrict__ p, int B, int H, int W, int C) {
     const int Ho = H / 2, Wo = W / 2, q = C / 8;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= Wo * q) return;
-    const int c = (j % q) * 8, x = j / q;
-    for (int row = blockIdx.y; row < B * Ho; row += gridDim.y) {
-        const int b = row / Ho, y = row % Ho;
-        const bf16* base = a + (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
-        const uint4 v[4] = {*reinterpret_cast<const uint4*>(base), *reinterpret_cast<const uint4*>(base + C),
-                            *reinterpret_cast<const uint4*>(base + (size_t)W * C),
-                            *reinterpret_cast<const uint4*>(base + (size_t)W * C + C)};
-        uint32_t o[4];
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (unsigned)B * Ho * Wo * q) return;
+    const int c = (int)(i % q) * 8;
+    unsigned r = i / q;
+    const int x = (int)(r % Wo);
+    r /= Wo;
+    const int y = (int)(r % Ho), b = (int)(r / Ho);
+    const bf16* base = a + (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
+    const uint4 v[4] = {*reinterpret_cast<const uint4*>(base), *reinterpret_cast<const uint4*>(base + C),
+                        *reinterpret_cast<const uint4*>(base + (size_t)W * C),
+                        *reinterpret_cast<const uint4*>(base + (size_t)W * C + C)};
+    uint32_t o[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t w[4] = {(&v[0].x)[k], (&v[1].x)[k], (&v[2].x)[k], (&v[3].x)[k]};
-            float lo = __uint_as_float(w[0] << 16), hi = __uint_as_float(w[0] & 0xffff0000u);
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t w[4] = {(&v[0].x)[k], (&v[1].x)[k], (&v[2].x)[k], (&v[3].x)[k]};
+        float lo = __uint_as_float(w[0] << 16), hi = __uint_as_float(w[0] & 0xffff0000u);
 #pragma unroll
-            for (int r = 1; r < 4; ++r) {
-                lo = fmaxf(lo, __uint_as_float(w[r] << 16));
-                hi = fmaxf(hi, __uint_as_float(w[r] & 0xffff0000u));
-            }
-            o[k] = pack2(__float2bfloat16_rn(lo), __float2bfloat16_rn(hi));   // exact: both are bf16 values
+        for (int t = 1; t < 4; ++t) {
+            lo = fmaxf(lo, __uint_as_float(w[t] << 16));
+            hi = fmaxf(hi, __uint_as_float(w[t] & 0xffff0000u));
         }
-        *reinterpret_cast<uint4*>(p + (((size_t)b * Ho + y) * Wo + x) * C + c) = make_uint4(o[0], o[1], o[2], o[3]);
+        o[k] = pack2(__float2bfloat16_rn(lo), __float2bfloat16_rn(hi));   // exact: both are bf16 values
     }
+    *reinterpret_cast<uint4*>(p + (((size_t)b * Ho + y) * Wo + x) * C + c) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 // Routes d p to the first maximum of its window in row-major order (strict >), added to da.
-// One channel per thread; rows = B * H / 2.
+// Four channels per thread (each window's da is touched by this thread only), flat 32-bit index
+// over B * H/2 * W/2 * C/4.
 __global__ void k_maxpool_bwd(const bf16* __restrict__ a, const float* __restrict__ dp, float* __restrict__ da,
                               int B, int H, int W, int C) {
-    const int Ho = H / 2, Wo = W / 2;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= Wo * C) return;
-    const int c = j % C, x = j / C;
-    for (int row = blockIdx.y; row < B * Ho; row += gridDim.y) {
-        const int b = row / Ho, y = row % Ho;
-        const size_t off[4] = {0, (size_t)C, (size_t)W * C, (size_t)W * C + C};
-        const size_t base = (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
-        int best = 0;
-        float m = __bfloat162float(a[base]);
+    const int Ho = H / 2, Wo = W / 2, q = C / 4;
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (unsigned)B * Ho * Wo * q) return;
+    const int c = (int)(i % q) * 4;
+    unsigned r = i / q;
+    const int x = (int)(r % Wo);
+    r /= Wo;
+    const int y = (int)(r % Ho), b = (int)(r / Ho);
+    const size_t off[4] = {0, (size_t)C, (size_t)W * C, (size_t)W * C + C};
+    const size_t base = (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
+    float m[4];
+    int best[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int k = 1; k < 4; ++k) {
-            const float v = __bfloat162float(a[base + off[k]]);
-            if (v > m) {
-                m = v;
-                best = k;
+    for (int t = 0; t < 4; ++t) {
+        const uint2 v = *reinterpret_cast<const uint2*>(a + base + off[t]);
+        const float e[4] = {__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                            __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (t == 0) m[k] = e[k];
+            else if (e[k] > m[k]) {
+                m[k] = e[k];
+                best[k] = t;
             }
         }
-        da[base + off[best]] += dp[(((size_t)b * Ho + y) * Wo + x) * C + c];
+    }
+    const float4 g = *reinterpret_cast<const float4*>(dp + (((size_t)b * Ho + y) * Wo + x) * C + c);
+    const float gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (best[0] != t && best[1] != t && best[2] != t && best[3] != t) continue;
+        float4* dst = reinterpret_cast<float4*>(da + base + off[t]);
+        float4 d = *dst;
+        if (best[0] == t) d.x += gv[0];
+        if (best[1] == t) d.y += gv[1];
+        if (best[2] == t) d.z += gv[2];
+        if (best[3] == t) d.w += gv[3];
+        *dst = d;
     }
 }
 
