@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
 // Under Alg. 1's own stage 2 (rotate_target 1) f is read as it is and g is turned back by theta.
 // The first pass takes its inputs straight from the gather (no staging in shared memory).
 template <int N, int P>
-__global__ void __launch_bounds__(tpb_for(P)) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
+__global__ void __launch_bounds__(tpb_for(P), P == 768 ? 6 : 65536 / (tpb_for(P) * 64)) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
                                                         const float* __restrict__ f, const float* __restrict__ g,
                                                         const float* __restrict__ th, float2* __restrict__ s2, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
