@@ -34,7 +34,7 @@ extern "C" {
 enum fmbym_status {
     FMBYM_OK = 0,
     FMBYM_ERR_INVALID_ARG = 1,      /* NULL or out-of-range argument                         */
-    FMBYM_ERR_UNSUPPORTED_SIZE = 2, /* N not in {128,256,512} or n_theta not in {128,256,400} */
+    FMBYM_ERR_UNSUPPORTED_SIZE = 2, /* N not in {128,256,512} or n_theta not in 8..1024   */
     FMBYM_ERR_WORKSPACE = 3,        /* more pairs than the handle was created for            */
     FMBYM_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed                  */
     FMBYM_ERR_TIMEOUT = 5           /* a bounded device-side wait ran out                    */
@@ -44,7 +44,8 @@ enum fmbym_status {
  * the places the paper leaves open.
  *   n           scan side N (n_xy of Alg. 1); supported: 128, 256, 512
  *   n_theta     number of angle candidates over a half turn (delta_theta = pi / n_theta,
- *               Alg. 1 first Linspace); supported: 128, 256, 400
+ *               Alg. 1 first Linspace); 8..1024: 128, 256 and 400 take the FFT correlation,
+ *               any other count (Alg. 1's default 733 among them) direct circular sums
  *   n_r         radii of the polar grid, rho_j = j * (N/2) / n_r, 1 <= n_r <= N/2 (Cart2Pol)
  *   temp_theta  T_theta > 0, temp_xy  T_xy > 0 (SoftArgMax temperatures of Alg. 1)
  *   delta_xy    translation bin size > 0 (the pose's t is lag * delta_xy)

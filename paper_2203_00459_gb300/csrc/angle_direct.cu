@@ -1,0 +1,271 @@
+// The angle stage of Alg. 1 for angle counts without an FFT plan -- Alg. 1's own n_theta = 733
+// among them: the same Cart2Pol samples, angle scores (Eq. 7, or the radial mean that Alg. 1
+// prints), soft-argmax and their adjoint as the FFT route of fwd.cu / bwd.cu, with the circular
+// correlation along angle evaluated as its direct sum.  Per pair n_theta^2 n_r multiply-adds
+// (1.4e8 at 733 x 256), spread over chunks of radii.
+//
+//   k_polar_direct  bilinear Cart2Pol of |F_f| and |F_g| -> pol[q][r][a] = (A_f, A_g)
+//   k_angle_direct  c partials per chunk of radii: sum_r sum_a A_f[a,r] A_g[(a + l) mod n, r]
+//   k_theta_direct  chunk sum, z-score, softmax, expectation -> theta (as k_theta)
+//   k_b_theta_direct  soft-argmax adjoint -> d c (as k_b_theta, without the transform)
+//   k_b_angle_direct  d A_f[a,r] = sum_l dc_l A_g[a + l, r], d A_g[b,r] = sum_l dc_l A_f[b - l, r]
+#include <cfloat>
+
+#include "common.cuh"
+#include "dev_util.cuh"
+
+namespace fmbym {
+
+constexpr int kDirectMaxNT = 1024;   // lags per CTA: one thread each
+constexpr int kDirectRadii = 16;     // radii per CTA of the per-radius score
+
+bool fft_angle_count(int nt) { return nt == 128 || nt == 256 || nt == 400; }
+
+int angle_direct_chunks(const DevPlan& p) { return p.angle_score == 1 ? 1 : (p.nr + kDirectRadii - 1) / kDirectRadii; }
+
+// Cart2Pol of both magnitude spectra (the gather of k_angle), radius-major: pol[q][r][a].
+__global__ void __launch_bounds__(256) k_polar_direct(DevPlan p, const float* __restrict__ mt,
+                                                      float2* __restrict__ pol, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    const int q = blockIdx.y, n = p.n, W = n / 2;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= p.nt * p.nr) return;
+    const int r = idx / p.nt, a = idx - r * p.nt;
+    const float2* m2 = reinterpret_cast<const float2*>(mt) + (size_t)q * (W + 1) * n;
+    const PolarSample ps = p.polar[a * p.nr + r];
+    const float w00 = (1.f - ps.fy) * (1.f - ps.fx), w01 = (1.f - ps.fy) * ps.fx;
+    const float w10 = ps.fy * (1.f - ps.fx), w11 = ps.fy * ps.fx;
+    const float2 v00 = mag2_at(m2, n, ps.y0, ps.x0), v01 = mag2_at(m2, n, ps.y0, ps.x0 + 1);
+    const float2 v10 = mag2_at(m2, n, ps.y0 + 1, ps.x0), v11 = mag2_at(m2, n, ps.y0 + 1, ps.x0 + 1);
+    pol[(size_t)q * p.nt * p.nr + idx] = make_float2(w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x,
+                                                     w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y);
+}
+
+// Thread i holds lag l = i - n/2 (lag index i of c_theta); A_g is kept twice over so that
+// A_g[(a + l) mod n] is a plain shared read.  Per-radius score: CTA x takes radii
+// [16 x, 16 x + 16); radial mean: one CTA correlates the radial sums and scales by 1/n_r.
+__global__ void __launch_bounds__(kDirectMaxNT) k_angle_direct(DevPlan p, const float2* __restrict__ pol,
+                                                               float* __restrict__ part, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    __shared__ float af[kDirectMaxNT], ag[2 * kDirectMaxNT];
+    const int q = blockIdx.y, nt = p.nt, i = threadIdx.x;
+    const int lp = (i - nt / 2 + nt) % nt;   // the lag as a shift in [0, n)
+    const float2* P = pol + (size_t)q * nt * p.nr;
+    float acc = 0.f;
+    auto correlate = [&]() {
+        __syncthreads();
+        if (i < nt) {
+            float s = 0.f;
+            for (int a = 0; a < nt; ++a) s = fmaf(af[a], ag[a + lp], s);
+            acc += s;
+        }
+        __syncthreads();
+    };
+    if (p.angle_score == 1) {
+        if (i < nt) {
+            float mf = 0.f, mg = 0.f;
+            for (int r = 0; r < p.nr; ++r) {
+                const float2 v = P[(size_t)r * nt + i];
+                mf += v.x;
+                mg += v.y;
+            }
+            af[i] = mf;
+            ag[i] = ag[i + nt] = mg;
+        }
+        correlate();
+        acc *= 1.f / (float)p.nr;
+    } else {
+        const int r0 = blockIdx.x * kDirectRadii, r1 = min(r0 + kDirectRadii, p.nr);
+        for (int r = r0; r < r1; ++r) {
+            if (i < nt) {
+                const float2 v = P[(size_t)r * nt + i];
+                af[i] = v.x;
+                ag[i] = ag[i + nt] = v.y;
+            }
+            correlate();
+        }
+    }
+    if (i < nt) part[((size_t)q * gridDim.x + blockIdx.x) * nt + i] = acc;
+}
+
+__device__ __forceinline__ void block_sum_max(float& s, float& m, float* red) {   // red: 64 floats
+    s = warp_sum(s);
+    m = warp_max(m);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        red[wid] = s;
+        red[32 + wid] = m;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        float a = lane < nw ? red[lane] : 0.f, b = lane < nw ? red[32 + lane] : -FLT_MAX;
+        a = warp_sum(a);
+        b = warp_max(b);
+        if (lane == 0) {
+            red[0] = a;
+            red[32] = b;
+        }
+    }
+    __syncthreads();
+    s = red[0];
+    m = red[32];
+    __syncthreads();
+}
+
+// Sum of the chunk partials -> c_theta (lag order), then the soft-argmax of Alg. 1 over the angle
+// candidates k delta_theta, delta_theta = pi / n_theta (the tail of k_theta).  One CTA per pair.
+__global__ void __launch_bounds__(kDirectMaxNT) k_theta_direct(DevPlan p, const float* __restrict__ part, int nch,
+                                                               const long long* __restrict__ tab, float* __restrict__ th,
+                                                               float* __restrict__ pose, float* __restrict__ c_theta,
+                                                               float* __restrict__ ct) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    __shared__ float red[64];
+    const int q = blockIdx.x, nt = p.nt, i = threadIdx.x;
+    float v = 0.f;
+    if (i < nt)
+        for (int h = 0; h < nch; ++h) v += part[((size_t)q * nch + h) * nt + i];
+    float s = i < nt ? v : 0.f, m = i < nt ? v : -FLT_MAX;
+    block_sum_max(s, m, red);
+    const float mean = s / nt, cmax = m;
+    const float sd = sqrtf(block_reduce<false>(i < nt ? (v - mean) * (v - mean) : 0.f, red) / nt);
+    const float inv = p.score_norm == 1 ? 1.f / p.temp_theta : (sd > 0.f ? 1.f / (sd * p.temp_theta) : 0.f);
+    const float e = i < nt ? expf((v - cmax) * inv) : 0.f;
+    float sums[2] = {e, e * (float)(i - nt / 2)};
+    block_sum_n<2>(sums, red);
+    if (i < nt) {
+        ct[(size_t)q * nt + i] = v;
+        if (c_theta) c_theta[tab[3 * q + 1] + i] = v;
+    }
+    if (i == 0) {
+        const float theta = (float)((double)sums[1] / (double)sums[0] * (3.14159265358979323846 / nt));
+        pose[3 * tab[3 * q + 2]] = theta;
+        double sd_, cd_;
+        sincos((double)theta, &sd_, &cd_);
+        const float chh = (float)cd_, shh = (float)sd_;
+        float* t = th + 8 * q;
+        t[0] = theta;
+        t[1] = chh;
+        t[2] = (float)(cd_ - (double)chh);
+        t[3] = shh;
+        t[4] = (float)(sd_ - (double)shh);
+    }
+}
+
+// Angle soft-argmax adjoint (the math of k_b_theta): d c_theta in lag order, from dL/dtheta in
+// bsc[q][8] and the scores kept in ct.
+__global__ void __launch_bounds__(kDirectMaxNT) k_b_theta_direct(DevPlan p, const float* __restrict__ ct,
+                                                                 const float* __restrict__ bsc,
+                                                                 float* __restrict__ dcout) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    __shared__ float red[64];
+    const int q = blockIdx.x, nt = p.nt, i = threadIdx.x;
+    const float c = i < nt ? ct[(size_t)q * nt + i] : 0.f;
+    float s = i < nt ? c : 0.f, m = i < nt ? c : -FLT_MAX;
+    block_sum_max(s, m, red);
+    const float mean = s / nt, cmax = m;
+    const float sd = sqrtf(block_reduce<false>(i < nt ? (c - mean) * (c - mean) : 0.f, red) / nt);
+    const float inv = p.score_norm == 1 ? 1.f / p.temp_theta : (sd > 0.f ? 1.f / (sd * p.temp_theta) : 0.f);
+    const float e = i < nt ? expf((c - cmax) * inv) : 0.f;
+    const float se = block_reduce<false>(e, red);
+    const float dth = bsc[(size_t)q * 16 + 8];
+    const float dl = 3.14159265358979323846f / nt;
+    const float pp = e / se, qk = dth * (float)(i - nt / 2) * dl;
+    const float pq = block_reduce<false>(i < nt ? pp * qk : 0.f, red);
+    const float dz = i < nt ? pp * (qk - pq) / p.temp_theta : 0.f;
+    const float z = sd > 0.f ? (c - mean) / sd : 0.f;
+    float sums[2] = {dz, dz * z};
+    block_sum_n<2>(sums, red);
+    const float m1 = sums[0] / nt, m2 = sums[1] / nt;
+    if (i < nt) {
+        float dc = dz;
+        if (p.score_norm != 1) dc = sd > 0.f ? (dz - m1 - z * m2) / sd : 0.f;
+        dcout[(size_t)q * nt + i] = dc;
+    }
+}
+
+// Correlation adjoint: thread a gives d A_f[a] = sum_i dc_i A_g[(a + l_i) mod n] and
+// d A_g[a] = sum_i dc_i A_f[(a - l_i) mod n] for each radius of its chunk (both operands kept
+// twice over); with the radial mean, d M / n_r goes to every radius.  gpol[q][a][r] as the FFT
+// route leaves it for k_b_polT.
+__global__ void __launch_bounds__(kDirectMaxNT) k_b_angle_direct(DevPlan p, const float2* __restrict__ pol,
+                                                                 const float* __restrict__ dc,
+                                                                 float2* __restrict__ gpol, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    __shared__ float af[2 * kDirectMaxNT], ag[2 * kDirectMaxNT], dcs[kDirectMaxNT];
+    __shared__ int lps[kDirectMaxNT];
+    const int q = blockIdx.y, nt = p.nt, a = threadIdx.x;
+    const float2* P = pol + (size_t)q * nt * p.nr;
+    float2* G = gpol + (size_t)q * nt * p.nr;
+    if (a < nt) {
+        dcs[a] = dc[(size_t)q * nt + a];
+        lps[a] = (a - nt / 2 + nt) % nt;
+    }
+    auto adjoint = [&](float& dfa, float& dga) {
+        __syncthreads();
+        dfa = 0.f;
+        dga = 0.f;
+        if (a < nt)
+            for (int i = 0; i < nt; ++i) {
+                const int l = lps[i];
+                dfa = fmaf(dcs[i], ag[a + l], dfa);
+                dga = fmaf(dcs[i], af[a - l + nt], dga);
+            }
+        __syncthreads();
+    };
+    if (p.angle_score == 1) {
+        if (a < nt) {
+            float mf = 0.f, mg = 0.f;
+            for (int r = 0; r < p.nr; ++r) {
+                const float2 v = P[(size_t)r * nt + a];
+                mf += v.x;
+                mg += v.y;
+            }
+            af[a] = af[a + nt] = mf;
+            ag[a] = ag[a + nt] = mg;
+        }
+        float dfa, dga;
+        adjoint(dfa, dga);
+        const float s = 1.f / (float)p.nr;
+        if (a < nt)
+            for (int r = 0; r < p.nr; ++r) G[(size_t)a * p.nr + r] = make_float2(dfa * s, dga * s);
+    } else {
+        const int r0 = blockIdx.x * kDirectRadii, r1 = min(r0 + kDirectRadii, p.nr);
+        for (int r = r0; r < r1; ++r) {
+            if (a < nt) {
+                const float2 v = P[(size_t)r * nt + a];
+                af[a] = af[a + nt] = v.x;
+                ag[a] = ag[a + nt] = v.y;
+            }
+            float dfa, dga;
+            adjoint(dfa, dga);
+            if (a < nt) G[(size_t)a * p.nr + r] = make_float2(dfa, dga);
+        }
+    }
+}
+
+cudaError_t launch_stage1_direct(const DevPlan& p, const Ws& w, int B, const long long* tab, float* pose,
+                                 float* c_theta, cudaStream_t st) {
+    const int nch = angle_direct_chunks(p);
+    float* part = reinterpret_cast<float*>(w.sp);
+    // the samples stay in ahat for the adjoint; a plain forward keeps nothing and borrows the
+    // adjoint's polar-gradient buffer (same size)
+    float2* pol = w.ahat ? w.ahat : w.gpol;
+    w.tr->before(K_ANGLE, st);
+    launch_pdl(k_polar_direct, dim3((p.nt * p.nr + 255) / 256, B), 256, 0, st, p, w.mt, pol, B);
+    launch_pdl(k_angle_direct, dim3(nch, B), kDirectMaxNT, 0, st, p, (const float2*)pol, part, B);
+    w.tr->before(K_THETA, st);
+    launch_pdl(k_theta_direct, B, kDirectMaxNT, 0, st, p, (const float*)part, nch, tab, w.th, pose, c_theta, w.ct);
+    return cudaGetLastError();
+}
+
+void launch_stage1_adjoint_direct(const DevPlan& p, const Ws& w, int B, cudaStream_t st) {
+    float* dc = reinterpret_cast<float*>(w.bdc);
+    w.tr->before(K_B_THETA, st);
+    launch_pdl(k_b_theta_direct, B, kDirectMaxNT, 0, st, p, (const float*)w.ct, (const float*)w.bsc, dc);
+    w.tr->before(K_B_ANGLE, st);
+    launch_pdl(k_b_angle_direct, dim3(angle_direct_chunks(p), B), kDirectMaxNT, 0, st, p, (const float2*)w.ahat,
+               (const float*)dc, w.gpol, B);
+}
+
+}  // namespace fmbym

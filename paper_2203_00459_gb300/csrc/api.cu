@@ -26,7 +26,9 @@ struct HostPlan {
 thread_local std::string g_create_error;
 
 bool supported_n(int n) { return n == 128 || n == 256 || n == 512; }
-bool supported_nt(int nt) { return nt == 128 || nt == 256 || nt == 400; }
+// 128, 256 and 400 angles take the FFT route; any other count up to 1024 (Alg. 1's 733 among them)
+// the direct sums of angle_direct.cu
+bool supported_nt(int nt) { return nt >= 8 && nt <= 1024; }
 
 }  // namespace
 
@@ -146,7 +148,7 @@ std::string validate(const fmbym_size_cfg& c) {
         return buf;
     }
     if (!supported_nt(c.n_theta)) {
-        snprintf(buf, sizeof buf, "n_theta=%d not supported (128, 256, 400)", c.n_theta);
+        snprintf(buf, sizeof buf, "n_theta=%d not supported (8..1024)", c.n_theta);
         return buf;
     }
     if (c.n_r < 1 || c.n_r > c.n / 2) return "n_r must be in [1, n/2]";

@@ -700,7 +700,8 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     }
     if (p.nt == 128) launch_stage1_adjoint<128>(p, w, B, st);
     else if (p.nt == 256) launch_stage1_adjoint<256>(p, w, B, st);
-    else launch_stage1_adjoint<400>(p, w, B, st);
+    else if (p.nt == 400) launch_stage1_adjoint<400>(p, w, B, st);
+    else launch_stage1_adjoint_direct(p, w, B, st);   // no FFT plan: direct sums
     w.tr->before(K_B_POLT, st);
     const int E = (N / 2 + 1) * N, lb = (E + kThreads - 1) / kThreads;
     const int hb = (p.n_heavy + kThreads / 32 - 1) / (kThreads / 32);

@@ -160,6 +160,11 @@ Ws ws_carve(const DevPlan& p, int B, void* base, bool backward);
 cudaError_t launch_forward_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                                   const float* g, float* pose, float* c_xy, cudaStream_t st);
 // Exhaustive rotate-then-correlate search over n_angles host headings (exhaustive.cu).
+// The angle stage by direct circular sums, for angle counts without an FFT plan (angle_direct.cu).
+bool fft_angle_count(int nt);
+cudaError_t launch_stage1_direct(const DevPlan& p, const Ws& w, int B, const long long* tab, float* pose,
+                                 float* c_theta, cudaStream_t st);
+void launch_stage1_adjoint_direct(const DevPlan& p, const Ws& w, int B, cudaStream_t st);
 cudaError_t launch_exhaustive(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                               const float* g, int n_angles, const float* angles, float* cand, float4* best,
                               float* peaks, float* pose, cudaStream_t st);

@@ -676,7 +676,8 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
     cudaError_t e;
     if (p.nt == 128) e = launch_stage1_angle<128>(p, w, B, tab, pose, c_theta, st);
     else if (p.nt == 256) e = launch_stage1_angle<256>(p, w, B, tab, pose, c_theta, st);
-    else e = launch_stage1_angle<400>(p, w, B, tab, pose, c_theta, st);
+    else if (p.nt == 400) e = launch_stage1_angle<400>(p, w, B, tab, pose, c_theta, st);
+    else e = launch_stage1_direct(p, w, B, tab, pose, c_theta, st);   // no FFT plan: direct sums
     if (e != cudaSuccess) return e;
     if (!p.full_circle) return launch_stage2<N, P>(p, w, B, tab, f, g, pose, c_xy, st);
     // full circle: the two candidate passes keep nothing for the adjoint and write no scores for

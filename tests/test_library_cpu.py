@@ -50,7 +50,7 @@ def _create(L, **over):
 
 
 @pytest.mark.parametrize("over,status", [
-    (dict(n=100), 2), (dict(n=1024), 2), (dict(n_theta=733), 2), (dict(n_r=0), 1), (dict(n_r=65), 1),
+    (dict(n=100), 2), (dict(n=1024), 2), (dict(n_theta=7), 2), (dict(n_theta=1025), 2), (dict(n_r=0), 1), (dict(n_r=65), 1),
     (dict(temp_theta=0.0), 1), (dict(delta_xy=-1.0), 1), (dict(pad_mode=2), 1), (dict(score_norm=3), 1),
     (dict(window=7), 1), (dict(band_lo=5.0, band_hi=4.0), 1)])
 def test_create_rejects_bad_sizes_before_any_cuda_call(L, over, status):

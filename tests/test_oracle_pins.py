@@ -154,20 +154,22 @@ def test_quarter_turn_shifts_polar_spectrum_by_half_the_angle_bins():
     assert int(np.argmax(c)) == 0
 
 
-def test_angle_scores_match_fft_correlation():
-    af = RNG.random((30, 7))
-    ag = RNG.random((30, 7))
+@pytest.mark.parametrize("nt,nr", [(30, 7), (733, 5)])   # 733: Alg. 1's n_theta, odd and prime
+def test_angle_scores_match_fft_correlation(nt, nr):
+    af = RNG.random((nt, nr))
+    ag = RNG.random((nt, nr))
     c = O.angle_scores(af, ag)
     viafft = np.real(np.fft.ifft(np.conj(np.fft.fft(af, axis=0)) * np.fft.fft(ag, axis=0), axis=0)).sum(1)
-    assert rel(c, viafft[np.mod(O.lags(30), 30)]) < 1e-13
+    assert rel(c, viafft[np.mod(O.lags(nt), nt)]) < 1e-13
 
 
-def test_angle_scores_peak_at_the_roll():
-    af = RNG.random((40, 9))
-    for k0 in (-20, -3, 0, 5, 19):
+@pytest.mark.parametrize("nt", [40, 41])
+def test_angle_scores_peak_at_the_roll(nt):
+    af = RNG.random((nt, 9))
+    for k0 in (-(nt // 2), -3, 0, 5, nt - 1 - nt // 2):
         c = O.angle_scores(af, np.roll(af, k0, axis=0))
         i = int(np.argmax(c))
-        assert O.lags(40)[i] == k0
+        assert O.lags(nt)[i] == k0
         assert abs(c[i] - np.sum(af * af)) < 1e-12 * c[i]
 
 
@@ -182,11 +184,16 @@ def test_soft_argmax_two_scores_closed_form():
 
 
 def test_soft_argmax_scale_invariance_and_hard_limit():
-    c = RNG.random(50)
+    """softmax(zscore(c) / T) ignores affine rescaling of c, and as T -> 0 it tends to the one-hot
+    argmax: the mass off the top score is at most (n - 1) exp(-(z_1 - z_2) / T)."""
+    c = np.random.default_rng(4).random(50)
     p = O.soft_argmax(c, 1.0, 0)
     assert rel(O.soft_argmax(7.0 * c + 3.0, 1.0, 0), p) < 1e-12
-    assert int(np.argmax(O.soft_argmax(c, 1e-4, 0))) == int(np.argmax(c))
-    assert abs(O.soft_argmax(c, 1e-4, 0).max() - 1.0) < 1e-9
+    T = 1e-4
+    hard = O.soft_argmax(c, T, 0)
+    assert int(np.argmax(hard)) == int(np.argmax(c))
+    z = np.sort((c - c.mean()) / c.std())[::-1]
+    assert 1.0 - hard.max() <= 49 * np.exp(-(z[0] - z[1]) / T) + 1e-15
 
 
 # ---------------------------------------------------------------------------------------------
