@@ -363,6 +363,90 @@ def exhaustive_comparison(pairs=64, steps=3, warmup=1):
     return out
 
 
+def angle_count_comparison(pairs=64, steps=10, warmup=3):
+    """Alg. 1's own angle count n_theta = 733 (no FFT plan: the angle correlation and its adjoint
+    as direct circular sums) beside n_theta = 400 (FFT route) on the same 256^2 pairs of the
+    batch256 workload, n_r = 128: pairs/s of the forward and of the training step (CUDA events,
+    L2 flushed before each timed call), and the device time of the angle stage from the library's
+    tracer.  The direct sums are bound by FP32 multiply-adds: n_theta^2 n_r per pair forward,
+    twice that in the adjoint, against 152 SMs x 128 lanes x the SM clock."""
+    import ctypes
+    import torch
+    from paper_2203_00459_gb300 import _lib, synth
+    from paper_2203_00459_gb300.search import PoseSearch, size_cfg
+    L = _lib.lib()
+    f, g, gt = synth.make_batch("batch256", pairs=pairs, start=2000)
+    fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    gtd = torch.from_numpy(gt.astype("float32")).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    pose = torch.empty((pairs, 3), device="cuda")
+    dpose = torch.empty((pairs, 3), device="cuda")
+    loss = torch.empty(1, device="cuda")
+    df, dg = torch.empty_like(fd), torch.empty_like(gd)
+    out = {"workload": f"batch256, {pairs} pairs, n_r 128"}
+
+    def fwd(srch):
+        st = torch.cuda.current_stream().cuda_stream
+        _lib.check(L.fmbym_pose(srch.handle, st, pairs, None, None, fd.data_ptr(), gd.data_ptr(), pose.data_ptr(),
+                                None, None), srch.handle)
+
+    def train(srch):
+        st = torch.cuda.current_stream().cuda_stream
+        _lib.check(L.fmbym_pose_train(srch.handle, st, pairs, None, None, fd.data_ptr(), gd.data_ptr(),
+                                      gtd.data_ptr(), 2, pose.data_ptr(), loss.data_ptr(), dpose.data_ptr(),
+                                      df.data_ptr(), dg.data_ptr()), srch.handle)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms)
+
+    fma_peak = 152 * 128 * 2070e6   # FP32 multiply-adds per second at the maximum SM clock
+    for nt in (400, 733):
+        cfg = size_cfg(256, nt, 128)
+        srch = PoseSearch([cfg], max_pairs=pairs, flags=_lib.FLAG_GRAPH)
+        ms_f = timed(lambda: fwd(srch))
+        ms_t = timed(lambda: train(srch))
+        srch.close()
+        traced = PoseSearch([cfg], max_pairs=pairs)
+        for _ in range(warmup):
+            train(traced)
+        torch.cuda.synchronize()
+        _lib.check(L.fmbym_set_tracing(traced.handle, 1), traced.handle)
+        for _ in range(steps):
+            flush.zero_()
+            train(traced)
+        torch.cuda.synchronize()
+        K = 32
+        tot, cnt, nk = (ctypes.c_double * K)(), (ctypes.c_longlong * K)(), ctypes.c_int()
+        _lib.check(L.fmbym_trace_summary(traced.handle, K, tot, cnt, ctypes.byref(nk)), traced.handle)
+        kern = {L.fmbym_trace_kind_name(k).decode(): tot[k] / cnt[k] for k in range(nk.value) if cnt[k]}
+        traced.close()
+        row = {"fwd_pairs_per_s": pairs / (ms_f * 1e-3), "step_pairs_per_s": pairs / (ms_t * 1e-3),
+               "angle_ms": kern.get("angle"), "b_angle_ms": kern.get("b_angle"),
+               "route": "fft" if nt == 400 else "direct sums"}
+        if nt != 400 and kern.get("angle") and kern.get("b_angle"):
+            fmas = nt * nt * 128 * pairs
+            row["direct_roofline"] = {
+                "bound": "alu", "unit": "TFMA/s", "peak": round(fma_peak / 1e12, 2),
+                "achieved_fwd": round(fmas / (kern["angle"] * 1e-3) / 1e12, 2),
+                "achieved_adjoint": round(2 * fmas / (kern["b_angle"] * 1e-3) / 1e12, 2),
+                "frac_fwd": round(fmas / (kern["angle"] * 1e-3) / fma_peak, 4),
+                "frac_adjoint": round(2 * fmas / (kern["b_angle"] * 1e-3) / fma_peak, 4),
+                "note": "angle_ms includes the Cart2Pol gather launched with it"}
+        out[f"n_theta_{nt}"] = row
+    return out
+
+
 def run_masked256(args):
     """The learned-mask training step at 256^2, batch 64: U-Net forward, masked search, L1 pose loss,
     search adjoint, U-Net adjoint and Adam.  `masked256` uses the 4-level 8..64-channel net,
@@ -642,6 +726,7 @@ def main():
 
     if rank == 0 and args.workload == WORKLOAD:
         extra["exhaustive_256"] = exhaustive_comparison()
+        extra["alg1_n_theta_733"] = angle_count_comparison()
 
     cpu = None
     if pool is not None:

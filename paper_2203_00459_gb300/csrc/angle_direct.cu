@@ -5,7 +5,8 @@
 // (1.4e8 at 733 x 256), spread over chunks of radii.
 //
 //   k_polar_direct  bilinear Cart2Pol of |F_f| and |F_g| -> pol[q][r][a] = (A_f, A_g)
-//   k_angle_direct  c partials per chunk of radii: sum_r sum_a A_f[a,r] A_g[(a + l) mod n, r]
+//   k_angle_direct  c partials per chunk of radii: sum_r sum_a A_f[a,r] A_g[(a + l) mod n, r],
+//                   four lags per thread over a shifted copy of A_g (register-blocked sums)
 //   k_theta_direct  chunk sum, z-score, softmax, expectation -> theta (as k_theta)
 //   k_b_theta_direct  soft-argmax adjoint -> d c (as k_b_theta, without the transform)
 //   k_b_angle_direct  d A_f[a,r] = sum_l dc_l A_g[a + l, r], d A_g[b,r] = sum_l dc_l A_f[b - l, r]
@@ -16,8 +17,8 @@
 
 namespace fmbym {
 
-constexpr int kDirectMaxNT = 1024;   // lags per CTA: one thread each
-constexpr int kDirectRadii = 16;     // radii per CTA of the per-radius score
+constexpr int kDirectMaxNT = 1024;   // largest angle count: one CTA holds every lag, four per thread
+constexpr int kDirectRadii = 8;      // radii per CTA of the per-radius score
 
 bool fft_angle_count(int nt) { return nt == 128 || nt == 256 || nt == 400; }
 
@@ -41,51 +42,117 @@ __global__ void __launch_bounds__(256) k_polar_direct(DevPlan p, const float* __
                                                      w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y);
 }
 
-// Thread i holds lag l = i - n/2 (lag index i of c_theta); A_g is kept twice over so that
-// A_g[(a + l) mod n] is a plain shared read.  Per-radius score: CTA x takes radii
-// [16 x, 16 x + 16); radial mean: one CTA correlates the radial sums and scales by 1/n_r.
-__global__ void __launch_bounds__(kDirectMaxNT) k_angle_direct(DevPlan p, const float2* __restrict__ pol,
-                                                               float* __restrict__ part, int B) {
+// 16 multiply-adds of one step: o[j] += u[4k + kk] v[x0 + 4k + kk + j], the window of v in (a, b).
+__device__ __forceinline__ void circ_step(const float4 uu, const float4 a, const float4 b, float o[4]) {
+    const float uv[4] = {uu.x, uu.y, uu.z, uu.w};
+    const float wv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = fmaf(uv[kk], wv[kk + j], o[j]);
+}
+
+// out[x] = sum_k u[k] v[x + k] for the four outputs x = x0 .. x0 + 3 of this thread (x0 a multiple
+// of 4): u zero-padded to ntp (a multiple of 4), v long enough for x0 + ntp + 3.  Each step takes
+// four u at once (one broadcast float4) and slides a window of v by one float4, so 16 multiply-adds
+// cost two shared loads; two steps per iteration keep the window in place (no register moves).
+__device__ __forceinline__ void circ_sum4(const float* __restrict__ u, const float* __restrict__ v, int ntp,
+                                          int x0, float o[4]) {
+    const float4* u4 = reinterpret_cast<const float4*>(u);
+    const float4* v4 = reinterpret_cast<const float4*>(v + x0);
+    const int K = ntp / 4;
+    float4 w0 = v4[0];
+    o[0] = o[1] = o[2] = o[3] = 0.f;
+    int k = 0;
+#pragma unroll 1
+    for (; k + 1 < K; k += 2) {
+        const float4 u0 = u4[k], u1 = u4[k + 1], w1 = v4[k + 1], w2 = v4[k + 2];
+        circ_step(u0, w0, w1, o);
+        circ_step(u1, w1, w2, o);
+        w0 = w2;
+    }
+    if (k < K) circ_step(u4[k], w0, v4[k + 1], o);
+}
+
+__host__ __device__ constexpr int direct_pad(int nt) { return (nt + 3) & ~3; }
+inline int direct_threads(int nt) { return ((direct_pad(nt) / 4 + 31) / 32) * 32; }
+
+// c[i] = sum_r sum_a A_f[a, r] A_g[(a + l_i) mod n, r], l_i = i - n/2, as sum_a u[a] v[a + i] with
+// u = A_f (zero-padded) and v[m] = A_g[(m - n/2) mod n] over 2 ntp entries.  Thread t holds lags
+// 4t .. 4t + 3.  Per-radius score: CTA x takes radii [8x, 8x + 8); radial mean: one CTA
+// correlates the radial sums and scales by 1/n_r.
+__global__ void __launch_bounds__(kDirectMaxNT / 4) k_angle_direct(DevPlan p, const float2* __restrict__ pol,
+                                                                   float* __restrict__ part, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
-    __shared__ float af[kDirectMaxNT], ag[2 * kDirectMaxNT];
-    const int q = blockIdx.y, nt = p.nt, i = threadIdx.x;
-    const int lp = (i - nt / 2 + nt) % nt;   // the lag as a shift in [0, n)
+    __shared__ __align__(16) float u[kDirectMaxNT], v[2 * kDirectMaxNT], mg[kDirectMaxNT];
+    const int q = blockIdx.y, nt = p.nt, ntp = direct_pad(nt), tid = threadIdx.x, T = blockDim.x;
+    const int sh = nt - nt / 2, x0 = 4 * tid;
     const float2* P = pol + (size_t)q * nt * p.nr;
-    float acc = 0.f;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, o[4];
     auto correlate = [&]() {
         __syncthreads();
-        if (i < nt) {
-            float s = 0.f;
-            for (int a = 0; a < nt; ++a) s = fmaf(af[a], ag[a + lp], s);
-            acc += s;
+        if (x0 < ntp) {
+            circ_sum4(u, v, ntp, x0, o);
+            for (int j = 0; j < 4; ++j) acc[j] += o[j];
         }
         __syncthreads();
     };
     if (p.angle_score == 1) {
-        if (i < nt) {
-            float mf = 0.f, mg = 0.f;
-            for (int r = 0; r < p.nr; ++r) {
-                const float2 v = P[(size_t)r * nt + i];
-                mf += v.x;
-                mg += v.y;
-            }
-            af[i] = mf;
-            ag[i] = ag[i + nt] = mg;
+        for (int a = tid; a < ntp; a += T) {
+            float mf = 0.f, m = 0.f;
+            if (a < nt)
+                for (int r = 0; r < p.nr; ++r) {
+                    const float2 w = P[(size_t)r * nt + a];
+                    mf += w.x;
+                    m += w.y;
+                }
+            u[a] = mf;
+            mg[a] = m;
         }
+        __syncthreads();
+        for (int m = tid; m < 2 * ntp; m += T) v[m] = mg[(m + sh) % nt];
         correlate();
-        acc *= 1.f / (float)p.nr;
+        for (int j = 0; j < 4; ++j) acc[j] *= 1.f / (float)p.nr;
     } else {
+        // the next radius is fetched into registers while the current one is summed
         const int r0 = blockIdx.x * kDirectRadii, r1 = min(r0 + kDirectRadii, p.nr);
-        for (int r = r0; r < r1; ++r) {
-            if (i < nt) {
-                const float2 v = P[(size_t)r * nt + i];
-                af[i] = v.x;
-                ag[i] = ag[i + nt] = v.y;
+        const int tm = T % nt, i0 = (tid + sh) % nt;
+        float pu[4], pv[8];
+        auto fetch = [&](int r) {
+            const float2* row = P + (size_t)r * nt;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int a = tid + i * T;
+                pu[i] = a < nt ? row[a].x : 0.f;
             }
-            correlate();
+            int idx = i0;   // (m + n - n/2) mod n for m = tid + i T
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                pv[i] = tid + i * T < 2 * ntp ? row[idx].y : 0.f;
+                idx += tm;
+                if (idx >= nt) idx -= nt;
+            }
+        };
+        if (r0 < r1) fetch(r0);
+        for (int r = r0; r < r1; ++r) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (tid + i * T < ntp) u[tid + i * T] = pu[i];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (tid + i * T < 2 * ntp) v[tid + i * T] = pv[i];
+            __syncthreads();
+            if (r + 1 < r1) fetch(r + 1);
+            if (x0 < ntp) {
+                circ_sum4(u, v, ntp, x0, o);
+                for (int j = 0; j < 4; ++j) acc[j] += o[j];
+            }
+            __syncthreads();
         }
     }
-    if (i < nt) part[((size_t)q * gridDim.x + blockIdx.x) * nt + i] = acc;
+    float* out = part + ((size_t)q * gridDim.x + blockIdx.x) * nt;
+    for (int j = 0; j < 4; ++j)
+        if (x0 + j < nt) out[x0 + j] = acc[j];
 }
 
 __device__ __forceinline__ void block_sum_max(float& s, float& m, float* red) {   // red: 64 floats
@@ -184,62 +251,92 @@ __global__ void __launch_bounds__(kDirectMaxNT) k_b_theta_direct(DevPlan p, cons
     }
 }
 
-// Correlation adjoint: thread a gives d A_f[a] = sum_i dc_i A_g[(a + l_i) mod n] and
-// d A_g[a] = sum_i dc_i A_f[(a - l_i) mod n] for each radius of its chunk (both operands kept
-// twice over); with the radial mean, d M / n_r goes to every radius.  gpol[q][a][r] as the FFT
-// route leaves it for k_b_polT.
-__global__ void __launch_bounds__(kDirectMaxNT) k_b_angle_direct(DevPlan p, const float2* __restrict__ pol,
-                                                                 const float* __restrict__ dc,
-                                                                 float2* __restrict__ gpol, int B) {
+// Correlation adjoint for each radius of the CTA's chunk:
+//   d A_f[a] = sum_i dc_i A_g[(a + l_i) mod n] = sum_i dc[i] v[a + i],    v[m] = A_g[(m - n/2) mod n]
+//   d A_g[b] = sum_i dc_i A_f[(b - l_i) mod n] = sum_i' dcr[i'] w[b + i'], dcr[i'] = dc[n - 1 - i'],
+//                                                                        w[m] = A_f[(m + n/2 + 1) mod n]
+// (both the sums of circ_sum4); with the radial mean, d M / n_r goes to every radius.  gpol[q][a][r]
+// as the FFT route leaves it for k_b_polT.
+__global__ void __launch_bounds__(kDirectMaxNT / 4) k_b_angle_direct(DevPlan p, const float2* __restrict__ pol,
+                                                                     const float* __restrict__ dc,
+                                                                     float2* __restrict__ gpol, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
-    __shared__ float af[2 * kDirectMaxNT], ag[2 * kDirectMaxNT], dcs[kDirectMaxNT];
-    __shared__ int lps[kDirectMaxNT];
-    const int q = blockIdx.y, nt = p.nt, a = threadIdx.x;
+    __shared__ __align__(16) float dcs[kDirectMaxNT], dcr[kDirectMaxNT], v[2 * kDirectMaxNT], w[2 * kDirectMaxNT];
+    const int q = blockIdx.y, nt = p.nt, ntp = direct_pad(nt), tid = threadIdx.x, T = blockDim.x;
+    const int shg = nt - nt / 2, shf = nt / 2 + 1, x0 = 4 * tid;
     const float2* P = pol + (size_t)q * nt * p.nr;
     float2* G = gpol + (size_t)q * nt * p.nr;
-    if (a < nt) {
-        dcs[a] = dc[(size_t)q * nt + a];
-        lps[a] = (a - nt / 2 + nt) % nt;
+    for (int i = tid; i < ntp; i += T) {
+        dcs[i] = i < nt ? dc[(size_t)q * nt + i] : 0.f;
+        dcr[i] = i < nt ? dc[(size_t)q * nt + nt - 1 - i] : 0.f;
     }
-    auto adjoint = [&](float& dfa, float& dga) {
+    float dfa[4], dga[4];
+    auto adjoint = [&]() {
         __syncthreads();
-        dfa = 0.f;
-        dga = 0.f;
-        if (a < nt)
-            for (int i = 0; i < nt; ++i) {
-                const int l = lps[i];
-                dfa = fmaf(dcs[i], ag[a + l], dfa);
-                dga = fmaf(dcs[i], af[a - l + nt], dga);
-            }
+        if (x0 < ntp) {
+            circ_sum4(dcs, v, ntp, x0, dfa);
+            circ_sum4(dcr, w, ntp, x0, dga);
+        }
         __syncthreads();
     };
     if (p.angle_score == 1) {
-        if (a < nt) {
+        __shared__ float mfs[kDirectMaxNT], mgs[kDirectMaxNT];   // radial sums M_f, M_g
+        for (int a = tid; a < nt; a += T) {
             float mf = 0.f, mg = 0.f;
             for (int r = 0; r < p.nr; ++r) {
-                const float2 v = P[(size_t)r * nt + a];
-                mf += v.x;
-                mg += v.y;
+                const float2 x = P[(size_t)r * nt + a];
+                mf += x.x;
+                mg += x.y;
             }
-            af[a] = af[a + nt] = mf;
-            ag[a] = ag[a + nt] = mg;
+            mfs[a] = mf;
+            mgs[a] = mg;
         }
-        float dfa, dga;
-        adjoint(dfa, dga);
+        __syncthreads();
+        for (int m = tid; m < 2 * ntp; m += T) {
+            v[m] = mgs[(m + shg) % nt];
+            w[m] = mfs[(m + shf) % nt];
+        }
+        adjoint();
         const float s = 1.f / (float)p.nr;
-        if (a < nt)
-            for (int r = 0; r < p.nr; ++r) G[(size_t)a * p.nr + r] = make_float2(dfa * s, dga * s);
+        for (int j = 0; j < 4; ++j)
+            if (x0 + j < nt)
+                for (int r = 0; r < p.nr; ++r) G[(size_t)(x0 + j) * p.nr + r] = make_float2(dfa[j] * s, dga[j] * s);
     } else {
+        // the next radius is fetched into registers while the current one is summed
         const int r0 = blockIdx.x * kDirectRadii, r1 = min(r0 + kDirectRadii, p.nr);
-        for (int r = r0; r < r1; ++r) {
-            if (a < nt) {
-                const float2 v = P[(size_t)r * nt + a];
-                af[a] = af[a + nt] = v.x;
-                ag[a] = ag[a + nt] = v.y;
+        const int tm = T % nt, ig = (tid + shg) % nt, jf = (tid + shf) % nt;
+        float pv[8], pw[8];
+        auto fetch = [&](int r) {
+            const float2* row = P + (size_t)r * nt;
+            int a = ig, b = jf;   // (m + shg) mod n and (m + shf) mod n for m = tid + i T
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const bool in = tid + i * T < 2 * ntp;
+                pv[i] = in ? row[a].y : 0.f;
+                pw[i] = in ? row[b].x : 0.f;
+                a += tm;
+                if (a >= nt) a -= nt;
+                b += tm;
+                if (b >= nt) b -= nt;
             }
-            float dfa, dga;
-            adjoint(dfa, dga);
-            if (a < nt) G[(size_t)a * p.nr + r] = make_float2(dfa, dga);
+        };
+        if (r0 < r1) fetch(r0);
+        for (int r = r0; r < r1; ++r) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (tid + i * T < 2 * ntp) {
+                    v[tid + i * T] = pv[i];
+                    w[tid + i * T] = pw[i];
+                }
+            __syncthreads();
+            if (r + 1 < r1) fetch(r + 1);
+            if (x0 < ntp) {
+                circ_sum4(dcs, v, ntp, x0, dfa);
+                circ_sum4(dcr, w, ntp, x0, dga);
+            }
+            __syncthreads();
+            for (int j = 0; j < 4; ++j)
+                if (x0 + j < nt) G[(size_t)(x0 + j) * p.nr + r] = make_float2(dfa[j], dga[j]);
         }
     }
 }
@@ -253,7 +350,7 @@ cudaError_t launch_stage1_direct(const DevPlan& p, const Ws& w, int B, const lon
     float2* pol = w.ahat ? w.ahat : w.gpol;
     w.tr->before(K_ANGLE, st);
     launch_pdl(k_polar_direct, dim3((p.nt * p.nr + 255) / 256, B), 256, 0, st, p, w.mt, pol, B);
-    launch_pdl(k_angle_direct, dim3(nch, B), kDirectMaxNT, 0, st, p, (const float2*)pol, part, B);
+    launch_pdl(k_angle_direct, dim3(nch, B), direct_threads(p.nt), 0, st, p, (const float2*)pol, part, B);
     w.tr->before(K_THETA, st);
     launch_pdl(k_theta_direct, B, kDirectMaxNT, 0, st, p, (const float*)part, nch, tab, w.th, pose, c_theta, w.ct);
     return cudaGetLastError();
@@ -264,7 +361,7 @@ void launch_stage1_adjoint_direct(const DevPlan& p, const Ws& w, int B, cudaStre
     w.tr->before(K_B_THETA, st);
     launch_pdl(k_b_theta_direct, B, kDirectMaxNT, 0, st, p, (const float*)w.ct, (const float*)w.bsc, dc);
     w.tr->before(K_B_ANGLE, st);
-    launch_pdl(k_b_angle_direct, dim3(angle_direct_chunks(p), B), kDirectMaxNT, 0, st, p, (const float2*)w.ahat,
+    launch_pdl(k_b_angle_direct, dim3(angle_direct_chunks(p), B), direct_threads(p.nt), 0, st, p, (const float2*)w.ahat,
                (const float*)dc, w.gpol, B);
 }
 

@@ -88,8 +88,12 @@ def test_counts_outside_the_range_are_rejected(lib):
 
 @pytest.mark.parametrize("angle_score", [0, 1])
 def test_adjoint_733(lib, angle_score):
+    """n_r = 92 leaves a partial chunk of radii.  The Rotate adjoint's d theta term takes the
+    bilinear cell of each fp32 sample point, so it jumps where a sample crosses a cell edge; these
+    pairs have no such edge within 6 fp32 ulps of the oracle's theta (at n_r = 100 pair 0 has one
+    2 ulps away, where a one-ulp change of theta moves d theta by 4 %)."""
     f, g = turned_pairs(256, (12.0, -7.0), 913)
-    cfg = lib.size_cfg(256, 733, 100, temp_theta=0.5, angle_score=angle_score)
+    cfg = lib.size_cfg(256, 733, 92, temp_theta=0.5, angle_score=angle_score)
     s = lib.PoseSearch([cfg], max_pairs=2)
     df, dg = s.pose_backward(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(),
                              torch.from_numpy(DP[:2].astype(np.float32)).cuda())
