@@ -24,22 +24,40 @@ bool fft_angle_count(int nt) { return nt == 128 || nt == 256 || nt == 400; }
 
 int angle_direct_chunks(const DevPlan& p) { return p.angle_score == 1 ? 1 : (p.nr + kDirectRadii - 1) / kDirectRadii; }
 
-// Cart2Pol of both magnitude spectra (the gather of k_angle), radius-major: pol[q][r][a].
+// Cart2Pol of both magnitude spectra (the gather of k_angle), radius-major: pol[q][r][a].  A CTA
+// takes a tile of 32 angles x 32 radii: the sample table (angle-major, a n_r + r) is read along
+// radius, the bilinear values go through shared memory, and the output is written along angle.
+constexpr int kPolTile = 32;
 __global__ void __launch_bounds__(256) k_polar_direct(DevPlan p, const float* __restrict__ mt,
                                                       float2* __restrict__ pol, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
-    const int q = blockIdx.y, n = p.n, W = n / 2;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= p.nt * p.nr) return;
-    const int r = idx / p.nt, a = idx - r * p.nt;
+    __shared__ float2 tile[kPolTile][kPolTile + 1];
+    const int q = blockIdx.z, n = p.n, W = n / 2, nt = p.nt, nr = p.nr;
+    const int a0 = blockIdx.x * kPolTile, r0 = blockIdx.y * kPolTile;
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;   // 8 rows of 32
     const float2* m2 = reinterpret_cast<const float2*>(mt) + (size_t)q * (W + 1) * n;
-    const PolarSample ps = p.polar[a * p.nr + r];
-    const float w00 = (1.f - ps.fy) * (1.f - ps.fx), w01 = (1.f - ps.fy) * ps.fx;
-    const float w10 = ps.fy * (1.f - ps.fx), w11 = ps.fy * ps.fx;
-    const float2 v00 = mag2_at(m2, n, ps.y0, ps.x0), v01 = mag2_at(m2, n, ps.y0, ps.x0 + 1);
-    const float2 v10 = mag2_at(m2, n, ps.y0 + 1, ps.x0), v11 = mag2_at(m2, n, ps.y0 + 1, ps.x0 + 1);
-    pol[(size_t)q * p.nt * p.nr + idx] = make_float2(w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x,
-                                                     w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y);
+#pragma unroll
+    for (int k = 0; k < kPolTile / 8; ++k) {
+        const int al = row + 8 * k, a = a0 + al, r = r0 + lane;
+        float2 val = make_float2(0.f, 0.f);
+        if (a < nt && r < nr) {
+            const PolarSample ps = p.polar[a * nr + r];
+            const float w00 = (1.f - ps.fy) * (1.f - ps.fx), w01 = (1.f - ps.fy) * ps.fx;
+            const float w10 = ps.fy * (1.f - ps.fx), w11 = ps.fy * ps.fx;
+            const float2 v00 = mag2_at(m2, n, ps.y0, ps.x0), v01 = mag2_at(m2, n, ps.y0, ps.x0 + 1);
+            const float2 v10 = mag2_at(m2, n, ps.y0 + 1, ps.x0), v11 = mag2_at(m2, n, ps.y0 + 1, ps.x0 + 1);
+            val = make_float2(w00 * v00.x + w01 * v01.x + w10 * v10.x + w11 * v11.x,
+                              w00 * v00.y + w01 * v01.y + w10 * v10.y + w11 * v11.y);
+        }
+        tile[al][lane] = val;
+    }
+    __syncthreads();
+    float2* out = pol + (size_t)q * nt * nr;
+#pragma unroll
+    for (int k = 0; k < kPolTile / 8; ++k) {
+        const int rl = row + 8 * k, r = r0 + rl, a = a0 + lane;
+        if (a < nt && r < nr) out[(size_t)r * nt + a] = tile[lane][rl];
+    }
 }
 
 // 16 multiply-adds of one step: o[j] += u[4k + kk] v[x0 + 4k + kk + j], the window of v in (a, b).
@@ -349,7 +367,8 @@ cudaError_t launch_stage1_direct(const DevPlan& p, const Ws& w, int B, const lon
     // adjoint's polar-gradient buffer (same size)
     float2* pol = w.ahat ? w.ahat : w.gpol;
     w.tr->before(K_ANGLE, st);
-    launch_pdl(k_polar_direct, dim3((p.nt * p.nr + 255) / 256, B), 256, 0, st, p, w.mt, pol, B);
+    launch_pdl(k_polar_direct, dim3((p.nt + kPolTile - 1) / kPolTile, (p.nr + kPolTile - 1) / kPolTile, B), 256, 0, st,
+               p, w.mt, pol, B);
     launch_pdl(k_angle_direct, dim3(nch, B), direct_threads(p.nt), 0, st, p, (const float2*)pol, part, B);
     w.tr->before(K_THETA, st);
     launch_pdl(k_theta_direct, B, kDirectMaxNT, 0, st, p, (const float*)part, nch, tab, w.th, pose, c_theta, w.ct);
