@@ -447,6 +447,51 @@ def angle_count_comparison(pairs=64, steps=10, warmup=3):
     return out
 
 
+def frontend_rate(scans=64, n=256, delta_xy=0.4, steps=20, warmup=3):
+    """Radar front end (fmbym_polar_to_cartesian) on Navtech-sized synthetic scans (400 azimuths x
+    3768 range bins of 0.0438 m) to n x n Cartesian scans of delta_xy metres: scans/s (CUDA events,
+    L2 flushed before each timed call) and its HBM roofline.  The compulsory bytes of a scan are
+    the scan cells its bilinear taps touch, read once, plus the image written once."""
+    import numpy as np
+    import torch
+    from paper_2203_00459_gb300 import synth
+    from paper_2203_00459_gb300.search import polar_to_cartesian
+    n_az, n_range, res = 400, 3768, 0.0438
+    polar = torch.from_numpy(synth.make_polar_scans(scans, seed=9)).cuda()
+    out = torch.empty((scans, n, n), device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    for _ in range(warmup):
+        polar_to_cartesian(polar, n, delta_xy, res, out=out)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        polar_to_cartesian(polar, n, delta_xy, res, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = sum(ms) / len(ms)
+    # cells touched by the taps (the same for every scan)
+    idx = (np.arange(n) - n // 2) * delta_xy
+    Y, X = np.meshgrid(idx, idx, indexing="ij")
+    fa = np.mod(np.arctan2(Y, X), 2 * np.pi) * n_az / (2 * np.pi)
+    fk = np.maximum(np.hypot(X, Y) / res - 0.5, 0.0)
+    ok = fk <= n_range - 1
+    a0 = np.floor(fa[ok]).astype(np.int64) % n_az
+    k0 = np.minimum(np.floor(fk[ok]).astype(np.int64), n_range - 1)
+    cells = np.unique(np.concatenate([((a0 + da) % n_az) * n_range + np.minimum(k0 + dk, n_range - 1)
+                                      for da in (0, 1) for dk in (0, 1)])).size
+    byts = scans * (cells * 4 + n * n * 4)
+    peaks, src = measured_peaks()
+    gbs = byts / (t * 1e-3) / 1e9
+    return {"workload": f"{scans} polar scans {n_az} x {n_range} (0.0438 m) -> {n}^2 at {delta_xy} m",
+            "scans_per_s": scans / (t * 1e-3), "ms": round(t, 4),
+            "roofline": {"bound": "hbm", "alg_bytes_per_launch": int(byts), "achieved": round(gbs, 1),
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
+                         "peak_source": src}}
+
+
 def run_masked256(args):
     """The learned-mask training step at 256^2, batch 64: U-Net forward, masked search, L1 pose loss,
     search adjoint, U-Net adjoint and Adam.  `masked256` uses the 4-level 8..64-channel net,
@@ -727,6 +772,7 @@ def main():
     if rank == 0 and args.workload == WORKLOAD:
         extra["exhaustive_256"] = exhaustive_comparison()
         extra["alg1_n_theta_733"] = angle_count_comparison()
+        extra["radar_frontend"] = frontend_rate()
 
     cpu = None
     if pool is not None:

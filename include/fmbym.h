@@ -257,6 +257,26 @@ unsigned long long fmbym_noalloc_capacity(void);
 const char* fmbym_noalloc_last_error(void);
 
 /* ---------------------------------------------------------------------------------------------
+ * Radar front end.  The search takes Cartesian scans of side N and cell size delta_xy (Alg. 1),
+ * recorded by a rotating FMCW radar (Sec. IV-A, Navtech CTS350-X: 400 azimuths, 3768 range bins
+ * of 0.0438 m).  The paper does not state the polar-to-Cartesian conversion; this one is bilinear:
+ * azimuth a looks along phi_a = 2 pi a / n_azimuths, from +x (column) toward +y (row); range bin
+ * k is centred at (k + 1/2) range_res; pixel (y, x) sits at ((x - n/2) delta_xy, (y - n/2)
+ * delta_xy), the sensor at the rotation centre of fmbym_pose; its value interpolates the scan
+ * at (phi / (2 pi / n_azimuths), rho / range_res - 1/2), periodic in azimuth, held at range index
+ * 0 inside the first bin centre and 0 beyond the last bin centre; the sensor pixel takes azimuth 0.
+ *   stream      cudaStream_t or NULL; the call is asynchronous on it
+ *   n_scans     number of scans (>= 0; 0 does nothing)
+ *   polar       device float32 [n_scans][n_azimuths][n_range], row-major, caller-owned
+ *   n_azimuths  >= 1;  n_range >= 1;  range_res > 0 (metres per range bin)
+ *   n           side of the Cartesian images (>= 1, any size);  delta_xy > 0 (metres per pixel)
+ *   cart        device float32 [n_scans][n][n] out, caller-owned, overwritten
+ * Returns FMBYM_ERR_INVALID_ARG for an out-of-range size or a NULL buffer with n_scans > 0, and
+ * FMBYM_ERR_CUDA when the launch fails.  Needs no handle and allocates nothing. */
+int fmbym_polar_to_cartesian(void* stream, int n_scans, const float* polar, int n_azimuths, int n_range,
+                             float range_res, int n, float delta_xy, float* cart);
+
+/* ---------------------------------------------------------------------------------------------
  * Masking network h_alpha (Sec. III-D, Eq. 10-12; layout of Tab. II).  A U-Net over the two-channel
  * image [f, g]: per level two 3x3 convolutions (no bias) each followed by BatchNorm and ReLU,
  * 2x2 max-pool down, bilinear x2 up (align_corners = False) concatenated before the skip

@@ -61,6 +61,7 @@ SIGNATURES = {
     "fmbym_pose_noalloc": (_I, [_P, _P, _I, _P, _P, _P, _P, _P]),
     "fmbym_noalloc_capacity": (ctypes.c_ulonglong, []),
     "fmbym_noalloc_last_error": (ctypes.c_char_p, []),
+    "fmbym_polar_to_cartesian": (_I, [_P, _I, _P, _I, _I, ctypes.c_float, _I, ctypes.c_float, _P]),
     "fmbym_unet_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(UnetConfig)]),
     "fmbym_unet_destroy": (None, [_P]),
     "fmbym_unet_last_error": (ctypes.c_char_p, [_P]),

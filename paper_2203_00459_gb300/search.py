@@ -213,3 +213,20 @@ class PoseFunction(torch.autograd.Function):
 def scan_match(f, g, search, size_idx=None, offsets=None):
     """Differentiable batched ScanMatch (Alg. 1): pose [B, 3] = (theta, t_x, t_y)."""
     return PoseFunction.apply(f, g, search, size_idx, offsets)
+
+
+def polar_to_cartesian(polar, n, delta_xy, range_res, out=None, stream=None):
+    """Radar front end (fmbym_polar_to_cartesian): polar scans [B, n_az, n_range] (CUDA float32,
+    contiguous) -> Cartesian scans [B, n, n] for the search."""
+    if polar.dim() == 2:
+        polar = polar.unsqueeze(0)
+    if not (polar.is_cuda and polar.dtype == torch.float32 and polar.is_contiguous()):
+        raise ValueError("polar must be a contiguous CUDA float32 tensor [B, n_az, n_range]")
+    b, n_az, n_range = polar.shape
+    if out is None:
+        out = torch.empty((b, n, n), dtype=torch.float32, device=polar.device)
+    st = _lib.lib().fmbym_polar_to_cartesian(_stream(stream), b, _ptr(polar), n_az, n_range, float(range_res), int(n),
+                                            float(delta_xy), _ptr(out))
+    if st != 0:
+        raise _lib.FmbymError(st, "fmbym_polar_to_cartesian")
+    return out

@@ -218,3 +218,27 @@ def trajectory_pairs_parallel(n_traj, n_frames, seed, processes=None, **kw):
         parts = pool.map(_trajectory_job, [(n_frames, seed, j, kw) for j in range(n_traj)])
     return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
             np.concatenate([p[2] for p in parts]))
+
+
+def make_polar_scans(b, n_az=400, n_range=3768, n_targets=300, seed=0):
+    """Seeded polar (azimuth x range) radar scans [b, n_az, n_range] float32, shaped like the
+    Navtech CTS350-X scans of the Oxford Radar RobotCar data (Sec. IV-A: 400 azimuths, 3768 range
+    bins): an |N(0, 0.3)| noise floor plus n_targets returns at uniform (azimuth, range), amplitude
+    U(5, 20) x Exp(1) speckle, each a Gaussian footprint of sigma 1 azimuth bin (wrapped) by
+    2 range bins."""
+    out = np.empty((b, n_az, n_range), np.float32)
+    da, dk = np.arange(-3, 4), np.arange(-6, 7)
+    shape = np.exp(-0.5 * da[:, None] ** 2) * np.exp(-0.5 * (dk[None, :] / 2.0) ** 2)
+    for i in range(b):
+        rng = _rng(seed, 1000 + i)
+        s = _abs_normal(rng, (n_az, n_range), 0.3)
+        a = np.floor(rng.random(n_targets) * n_az).astype(np.int64)
+        k = np.floor(rng.random(n_targets) * n_range).astype(np.int64)
+        amp = (5.0 + 15.0 * rng.random(n_targets)) * _exp1(rng, n_targets)
+        for t in range(n_targets):
+            rows = np.mod(a[t] + da, n_az)
+            cols = k[t] + dk
+            ok = (cols >= 0) & (cols < n_range)
+            s[np.ix_(rows, cols[ok])] += amp[t] * shape[:, ok]
+        out[i] = s
+    return out

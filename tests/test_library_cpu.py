@@ -65,3 +65,17 @@ def test_null_arguments(L):
     assert L.fmbym_pose(None, None, 1, None, None, None, None, None, None, None) == 1
     assert L.fmbym_pose_backward(None, None, 1, None, None, None, None, None, None, None) == 1
     L.fmbym_destroy(None)
+
+
+def test_polar_to_cartesian_validates_before_any_cuda_call(L):
+    f = L.fmbym_polar_to_cartesian
+    good = dict(n_scans=1, n_az=400, n_range=3768, res=0.0438, n=256, dxy=0.4)
+    def call(**kw):
+        a = dict(good, **kw)
+        return f(None, a["n_scans"], ctypes.c_void_p(16), a["n_az"], a["n_range"], a["res"], a["n"], a["dxy"],
+                 ctypes.c_void_p(16))
+    for bad in (dict(n_scans=-1), dict(n_az=0), dict(n_range=0), dict(res=0.0), dict(res=float("nan")), dict(n=0),
+                dict(dxy=-0.4)):
+        assert call(**bad) == 1, bad
+    assert f(None, 1, None, 400, 3768, 0.0438, 256, 0.4, None) == 1          # NULL buffers
+    assert f(None, 0, None, 400, 3768, 0.0438, 256, 0.4, None) == 0          # nothing to do

@@ -1,0 +1,57 @@
+"""The KITTI-style drift of Sec. IV-C against closed forms on planar trajectories."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2203_00459_gb300 import odometry as od
+
+T = 1000   # frames of 1 m
+
+
+def straight(theta=0.0, scale=1.0):
+    return np.tile([theta, scale * 1.0, 0.0], (T, 1))
+
+
+def test_perfect_estimate_has_no_drift():
+    rng = np.random.default_rng(3)
+    gt = np.column_stack([rng.normal(0, 0.01, T), 1.0 + rng.random(T), rng.normal(0, 0.1, T)])
+    d = od.drift(gt, gt)
+    assert d["translation_pct"] < 1e-9 and d["rotation_deg_per_km"] < 1e-6 and d["segments"] > 0
+
+
+def test_scale_error_on_a_straight_path():
+    """Every step 1 m, estimated (1 + s) m: a segment of L frames is off by s L, so s of L."""
+    s = 0.02
+    d = od.drift(straight(), straight(scale=1.0 + s))
+    assert abs(d["translation_pct"] - 100 * s) < 1e-9 and d["rotation_deg_per_km"] < 1e-9
+    assert d["by_length"][800.0][2] == T - 800 + 1   # segments from frames 0 .. T - 800
+
+
+def test_heading_bias_on_a_straight_path():
+    """A bias of b rad per 1 m frame turns the estimate by b L over L frames: b rad/m."""
+    b = 1e-4
+    d = od.drift(straight(), straight(theta=b))
+    assert abs(d["rotation_deg_per_km"] - math.degrees(b) * 1e3) < 1e-6
+
+
+def test_scaled_circle_measures_the_chord():
+    """On a circle of radius R (1 m steps, constant turn) the relative rotations are exact and the
+    steps are (1 + s) long, so the estimate is the circle scaled by (1 + s) and a segment's
+    residual translation is s times its chord 2 R sin(L / 2R); L = 100 m only."""
+    R, s = 150.0, 0.05
+    dth = 1.0 / R                        # arc of 1 m
+    chord1 = 2 * R * math.sin(dth / 2)   # straight step between frames
+    gt = np.tile([dth, chord1 * math.cos(dth / 2), chord1 * math.sin(dth / 2)], (400, 1))
+    est = gt * np.array([1.0, 1.0 + s, 1.0 + s])
+    d = od.drift(gt, est, lengths=(100.0,))
+    D = od.travelled(od.chain(gt))
+    j = int(np.searchsorted(D, 100.0))
+    arc = j * dth                         # angle swept by the first frame reaching 100 m
+    expect = s * 2 * R * math.sin(arc / 2) / 100.0
+    assert abs(d["translation_pct"] - 100 * expect) < 1e-9 and d["rotation_deg_per_km"] < 1e-9
+
+
+def test_short_trajectories_have_no_segments():
+    d = od.drift(straight()[:50], straight()[:50])
+    assert d["segments"] == 0 and math.isnan(d["translation_pct"])
