@@ -53,7 +53,7 @@ def test_alg1_defaults_fix_the_angle_span():
 # stage 1 pieces
 # ---------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n", [8, 128, 512])
+@pytest.mark.parametrize("n", [8, 128, 512, 127, 255])   # 127, 255: the paper's odd sizes
 def test_hann_is_periodic_hann(n):
     assert rel(O.hann(n), np.hanning(n + 1)[:n]) < 1e-15
 
@@ -68,8 +68,9 @@ def test_band_mask_hand_values():
     assert m[6, 5] == 1 and m[10, 5] == 1                         # rho = 7.81 (v = 6 and -6)
 
 
-def test_spectrum_of_delta_is_a_phase_ramp():
-    n, y0, x0 = 16, 3, 5
+@pytest.mark.parametrize("n", [16, 15])
+def test_spectrum_of_delta_is_a_phase_ramp(n):
+    y0, x0 = 3, 5
     x = np.zeros((n, n))
     x[y0, x0] = 1.0
     F = O.spectrum(x, O.make_cfg(n, 8, 4, window=0))
@@ -111,7 +112,7 @@ def test_magnitude_is_translation_invariant():
     assert rel(a2, a1) < 1e-12
 
 
-@pytest.mark.parametrize("n,nt,nr", [(32, 16, 8), (64, 50, 32), (128, 128, 64)])
+@pytest.mark.parametrize("n,nt,nr", [(32, 16, 8), (64, 50, 32), (128, 128, 64), (33, 20, 8), (127, 733, 16)])
 def test_cart2pol_matches_scipy_bilinear_on_full_periodic_spectrum(n, nt, nr):
     x = RNG.random((n, n))
     cfg = O.make_cfg(n, nt, nr, window=1, band_lo=0, band_hi=1e9)
@@ -205,8 +206,8 @@ def test_rotate_zero_is_identity():
     assert rel(O.rotate(x, 0.0), x) < 1e-15
 
 
-def test_rotate_quarter_turn_is_the_index_permutation():
-    n = 32
+@pytest.mark.parametrize("n", [32, 31])
+def test_rotate_quarter_turn_is_the_index_permutation(n):
     x = RNG.random((n, n))
     r = O.rotate(x, np.pi / 2)
     expect = rot90_about_centre(x)
@@ -226,7 +227,7 @@ def test_rotate_matches_scipy_bilinear_with_zero_fill(theta):
     assert rel(O.rotate(x, theta), ref.reshape(n, n)) < 1e-12
 
 
-@pytest.mark.parametrize("n", [8, 16, 24])
+@pytest.mark.parametrize("n", [8, 16, 24, 9, 15])
 def test_xcorr2d_matches_scipy_correlate(n):
     fr = RNG.random((n, n))
     g = RNG.random((n, n))
@@ -246,10 +247,10 @@ def test_xcorr2d_fft_route_equals_direct_sum():
             assert abs(c[sy + n // 2, sx + n // 2] - d) < 1e-11 * abs(d)
 
 
-def test_circular_integer_shift_peaks_at_the_shift():
-    n = 64
+@pytest.mark.parametrize("n", [64, 63])
+def test_circular_integer_shift_peaks_at_the_shift(n):
     f = RNG.random((n, n))
-    for ty, tx in [(3, -5), (-4, 4), (0, 0), (-32, 31)]:
+    for ty, tx in [(3, -5), (-4, 4), (0, 0), (-(n // 2), n - 1 - n // 2)]:
         c = O.xcorr2d(f, np.roll(f, (ty, tx), axis=(0, 1)), 1)
         iy, ix = np.unravel_index(np.argmax(c), c.shape)
         assert (iy - n // 2, ix - n // 2) == (ty, tx)
@@ -549,3 +550,13 @@ def test_pose_gradient_matches_central_differences_rotate_target_g():
             fd = sum(dpose[i] * (ra[k] - rb[k]) / (2 * h) for i, k in enumerate(("theta", "tx", "ty")))
             grad = (df if which == 0 else dg)
             assert abs(fd - grad[y, x]) <= 1e-6 * max(1.0, np.max(np.abs(grad))), (which, y, x, fd, grad[y, x])
+
+
+@pytest.mark.parametrize("n", [127, 255])
+def test_paper_odd_sizes_recover_a_known_pose(n):
+    """Alg. 1 at the paper's own odd scan sizes and n_theta = 733 (Sec. IV-B, Alg. 1): a pair
+    rendered with a continuous pose comes back within 0.05 deg and 0.05 px."""
+    f, g = synth.make_pair(n, n * n // 300, n // 16, math.radians(10.0), 3.0, -2.0, seed=77, index=0)
+    r = O.pose(f, g, O.make_cfg(n, 733, n // 2, temp_theta=0.2))
+    assert abs(math.degrees(r["theta"]) - 10.0) < 0.05, r["theta"]
+    assert abs(r["tx"] - 3.0) < 0.05 and abs(r["ty"] + 2.0) < 0.05, (r["tx"], r["ty"])
