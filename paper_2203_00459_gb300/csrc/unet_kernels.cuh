@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(const bf16* __restrict__ in0
         issued = kc + 1;
     }
     cp_async_wait_n(0);
-    // the last committed chunk's barrier covers every MMA issued before it; the verdict is shared
+    // the last committed chunk's barrier covers every MMA issued before it; the outcome is shared
     // so that the whole CTA takes the same branch around the warp-collective TMEM loads
     if (issued > 0) {
         const int last = issued - 1;
