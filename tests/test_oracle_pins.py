@@ -79,6 +79,24 @@ def test_spectrum_of_delta_is_a_phase_ramp(n):
     assert rel(F, np.exp(-2j * np.pi * (v * y0 + u * x0) / n)) < 1e-13
 
 
+@pytest.mark.parametrize("n,window", [(12, 1), (15, 1), (8, 0)])
+def test_spectrum_matches_the_direct_dft_sum(n, window):
+    """Eq. 4 written out: F[v, u] = sum_y sum_x w[y] w[x] f[y, x] exp(-2 pi i (v y + u x) / N) for
+    u <= N/2, by plain loops on a tiny scan."""
+    x = RNG.random((n, n))
+    w = O.hann(n) if window else np.ones(n)
+    ref = np.zeros((n, n // 2 + 1), complex)
+    for v in range(n):
+        for u in range(n // 2 + 1):
+            acc = 0j
+            for yy in range(n):
+                for xx in range(n):
+                    acc += w[yy] * w[xx] * x[yy, xx] * complex(math.cos(-2 * math.pi * (v * yy + u * xx) / n),
+                                                               math.sin(-2 * math.pi * (v * yy + u * xx) / n))
+            ref[v, u] = acc
+    assert rel(O.spectrum(x, O.make_cfg(n, 8, 4, window=window)), ref) < 1e-12
+
+
 def test_spectrum_of_plane_wave():
     n, u0, v0 = 32, 3, 5
     Y, X = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
