@@ -55,3 +55,22 @@ def test_scaled_circle_measures_the_chord():
 def test_short_trajectories_have_no_segments():
     d = od.drift(straight()[:50], straight()[:50])
     assert d["segments"] == 0 and math.isnan(d["translation_pct"])
+
+
+def test_chain_of_an_l_shaped_path():
+    """100 steps of 1 m along x, a +90 deg turn in place (+x toward +y), 100 steps along the new
+    heading: the last frame sits at (100, 100) facing +y after 200 m, and a segment error seen
+    from the turned leg is expressed in that leg's frame."""
+    rel = np.array([[0.0, 1.0, 0.0]] * 100 + [[math.pi / 2, 0.0, 0.0]] + [[0.0, 1.0, 0.0]] * 100)
+    T = od.chain(rel)
+    assert np.allclose(T[-1][:2, 2], [100.0, 100.0], atol=1e-9)
+    assert abs(math.atan2(T[-1][1, 0], T[-1][0, 0]) - math.pi / 2) < 1e-12
+    assert abs(od.travelled(T)[-1] - 200.0) < 1e-9
+    # an estimate 1 m short on the first step only: the one 100 m segment that contains step 0
+    # (from frame 0) is off by exactly 1 m, the others by nothing; segments start at frames
+    # 0 .. 101 (the turn frame adds no distance)
+    est = rel.copy()
+    est[0, 1] = 0.0
+    d = od.drift(rel, est, lengths=(100.0,))
+    assert d["by_length"][100.0][2] == 102
+    assert abs(d["translation_pct"] - 100.0 * (1.0 / 100.0) / 102) < 1e-12

@@ -55,12 +55,25 @@ def test_quarter_turn_of_the_scan_turns_the_image():
     assert rel(c2[x, N - y][off], c[y, x][off]) < 1e-12
 
 
-def test_matches_scipy_bilinear_with_wrapped_azimuth():
+@pytest.mark.parametrize("n_az", [NAZ, 16])   # 16: a 22.5 deg sector before the seam holds many pixels
+def test_matches_scipy_bilinear_with_wrapped_azimuth(n_az):
     ndimage = pytest.importorskip("scipy.ndimage")
-    p = RNG.random((NAZ, NRANGE))
+    p = RNG.random((n_az, NRANGE))
     c = R.polar_to_cartesian(p, N, DXY, RES)
-    fa, fk = R.polar_indices(N, DXY, NAZ, RES)
+    fa, fk = R.polar_indices(N, DXY, n_az, RES)
     wrapped = np.vstack([p, p[:1]])                               # row n_az = row 0
     ref = ndimage.map_coordinates(wrapped, [fa.ravel(), fk.ravel()], order=1, mode="nearest").reshape(N, N)
     inside = fk <= NRANGE - 1
     assert rel(c[inside], ref[inside]) < 1e-12
+    assert np.count_nonzero(inside & (fa > n_az - 1)) > (10 if n_az == 16 else -1)
+
+
+def test_seam_sector_interpolates_back_to_azimuth_zero():
+    """P[a] = a with 16 azimuths: past the last azimuth the value falls linearly from 15 to the 0
+    of azimuth 0, i.e. 15 (16 - fa) in the sector fa in [15, 16)."""
+    p = np.tile(np.arange(16, dtype=np.float64)[:, None], (1, NRANGE))
+    c = R.polar_to_cartesian(p, N, DXY, RES)
+    fa, _ = R.polar_indices(N, DXY, 16, RES)
+    seam = fa > 15
+    assert seam.sum() > 10
+    assert np.max(np.abs(c[seam] - 15.0 * (16.0 - fa[seam]))) < 1e-9
