@@ -77,3 +77,13 @@ def test_seam_sector_interpolates_back_to_azimuth_zero():
     seam = fa > 15
     assert seam.sum() > 10
     assert np.max(np.abs(c[seam] - 15.0 * (16.0 - fa[seam]))) < 1e-9
+
+
+def test_polar_generator_is_seeded_and_navtech_shaped():
+    from paper_2203_00459_gb300 import synth
+    a = synth.make_polar_scans(2, seed=5)
+    b = synth.make_polar_scans(2, seed=5)
+    assert a.shape == (2, 400, 3768) and a.dtype == np.float32
+    assert np.array_equal(a, b) and not np.array_equal(a[0], a[1])
+    assert not np.array_equal(a, synth.make_polar_scans(2, seed=6))
+    assert a.min() >= 0.0 and a.max() > 5.0   # |noise| floor plus returns of amplitude >= 5 x speckle
