@@ -79,3 +79,15 @@ def test_polar_to_cartesian_validates_before_any_cuda_call(L):
         assert call(**bad) == 1, bad
     assert f(None, 1, None, 400, 3768, 0.0438, 256, 0.4, None) == 1          # NULL buffers
     assert f(None, 0, None, 400, 3768, 0.0438, 256, 0.4, None) == 0          # nothing to do
+
+
+@pytest.mark.parametrize("n_theta,status", [(733, 2), (129, 2), (7, 2)])
+def test_noalloc_keeps_the_fft_angle_counts(L, n_theta, status):
+    """The allocation-free entry point takes only the angle counts with an FFT plan; the direct
+    sums of other counts need the handle's workspace.  Rejected before any CUDA call."""
+    from paper_2203_00459_gb300 import _lib
+    from paper_2203_00459_gb300.search import size_cfg
+    c = _lib.SizeCfg(**size_cfg(256, n_theta, 128))
+    st = L.fmbym_pose_noalloc(None, ctypes.byref(c), 1, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                              ctypes.c_void_p(16), None, None)
+    assert st == status and L.fmbym_noalloc_last_error().decode()
