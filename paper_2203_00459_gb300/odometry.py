@@ -61,3 +61,15 @@ def drift(gt_rel, est_rel, lengths=LENGTHS, step=1):
               len(per[L])) for L in lengths if per[L]}
     return {"translation_pct": 100.0 * float(t), "rotation_deg_per_km": float(np.degrees(r)) * 1e3,
             "segments": len(allv), "by_length": by}
+
+
+def motion_from_pose(pose, delta_xy):
+    """Vehicle motion (frame k+1 in frame k: theta, x, y in radians and metres) from the search's
+    pose between scans k and k+1 (theta, t_x, t_y in pixels; scan k+1 holds scan k's returns at
+    c + R(theta)(p - c) + t): the scene turning by theta is the vehicle turning by -theta, and the
+    vehicle's displacement is -delta_xy R(-theta) t."""
+    p = np.asarray(pose, np.float64).reshape(-1, 3)
+    th = -p[:, 0]
+    c, s = np.cos(th), np.sin(th)
+    tx, ty = p[:, 1], p[:, 2]
+    return np.column_stack([th, -delta_xy * (c * tx - s * ty), -delta_xy * (s * tx + c * ty)])

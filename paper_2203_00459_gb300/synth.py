@@ -242,3 +242,55 @@ def make_polar_scans(b, n_az=400, n_range=3768, n_targets=300, seed=0):
             s[np.ix_(rows, cols[ok])] += amp[t] * shape[:, ok]
         out[i] = s
     return out
+
+
+def make_drive(n, n_frames, speed_px=1.0, yaw_deg=0.5, period=80, n_points=None, n_walls=None, seed=0,
+               noise_sd=0.3, reach=0.45):
+    """A vehicle driving through one static, non-periodic world: frames [n_frames + 1, N, N]
+    float32 and the search pose between consecutive frames [n_frames, 3] = (theta, t_x, t_y) in the
+    convention of make_pair (frame k+1 holds frame k's returns at c + R(theta)(p - c) + t).
+
+    Step k moves the vehicle speed_px pixels along its heading and then turns it by
+    yaw_deg sin(2 pi k / period) degrees.  The world holds the point scatterers and walls of
+    make_pair's recipe at the same density per N x N area, spread over the path's bounding box
+    grown by N.  Frame k renders the returns within reach * N of the vehicle (a radar sees a disc
+    around itself) at p_k = c + R_k^T (p - T_k), with fresh |N(0, noise_sd)| noise."""
+    rng = _rng(seed, 7)
+    n_points = n * n // 300 if n_points is None else n_points
+    n_walls = n // 16 if n_walls is None else n_walls
+    # the path first: vehicle poses (phi_k, T_k), world origin at the start
+    phis, Ts = [0.0], [np.zeros(2)]
+    for k in range(n_frames):
+        T1 = Ts[-1] + speed_px * np.array([math.cos(phis[-1]), math.sin(phis[-1])])
+        phis.append(phis[-1] + math.radians(yaw_deg) * math.sin(2.0 * math.pi * k / period))
+        Ts.append(T1)
+    P = np.array(Ts)
+    lo, hi = P.min(axis=0) - n, P.max(axis=0) + n
+    area = float(np.prod(hi - lo)) / (n * n)
+    x, y, a = scene(rng, 1, int(round(n_points * area)), 0)   # points in the unit square
+    x, y = lo[0] + x * (hi[0] - lo[0]), lo[1] + y * (hi[1] - lo[1])
+    xs, ys, amps = [x], [y], [a]
+    for _ in range(int(round(n_walls * area))):
+        cx, cy = lo[0] + rng.random() * (hi[0] - lo[0]), lo[1] + rng.random() * (hi[1] - lo[1])
+        length = (0.1 + 0.4 * rng.random()) * n
+        ang = rng.random() * np.pi
+        m = max(2, int(length / 0.5) + 1)
+        sv = np.linspace(-0.5 * length, 0.5 * length, m)
+        xs.append(cx + sv * math.cos(ang))
+        ys.append(cy + sv * math.sin(ang))
+        amps.append(np.full(m, 2.0 + 6.0 * rng.random()) * _exp1(rng, m))
+    x, y, a = np.concatenate(xs), np.concatenate(ys), np.concatenate(amps)
+    c = n / 2.0
+    frames = np.empty((n_frames + 1, n, n), np.float32)
+    poses = np.empty((n_frames, 3))
+    for k in range(n_frames + 1):
+        cp, sp = math.cos(phis[k]), math.sin(phis[k])
+        dx, dy = x - Ts[k][0], y - Ts[k][1]
+        u, v = cp * dx + sp * dy, -sp * dx + cp * dy
+        seen = u * u + v * v < (reach * n) ** 2
+        frames[k] = render(n, c + u[seen], c + v[seen], a[seen]) + _abs_normal(rng, (n, n), noise_sd)
+        if k < n_frames:
+            c1, s1 = math.cos(phis[k + 1]), math.sin(phis[k + 1])
+            d = Ts[k] - Ts[k + 1]
+            poses[k] = (phis[k] - phis[k + 1], c1 * d[0] + s1 * d[1], -s1 * d[0] + c1 * d[1])
+    return frames, poses

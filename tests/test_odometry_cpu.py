@@ -74,3 +74,32 @@ def test_chain_of_an_l_shaped_path():
     d = od.drift(rel, est, lengths=(100.0,))
     assert d["by_length"][100.0][2] == 102
     assert abs(d["translation_pct"] - 100.0 * (1.0 / 100.0) / 102) < 1e-12
+
+
+def test_drive_ground_truth_converts_to_the_commanded_motion():
+    """make_drive's step k moves the vehicle speed pixels forward and then turns it by
+    yaw sin(2 pi k / period); motion_from_pose of the scan-to-scan pose gives back exactly that,
+    in metres."""
+    from paper_2203_00459_gb300 import synth
+    _, poses = synth.make_drive(64, 12, speed_px=3.0, yaw_deg=2.0, period=10, seed=2)
+    m = od.motion_from_pose(poses, 0.4)
+    k = np.arange(12)
+    w = np.radians(2.0) * np.sin(2 * np.pi * k / 10)
+    assert np.max(np.abs(m - np.column_stack([w, np.full(12, 3.0 * 0.4), np.zeros(12)]))) < 1e-12
+
+
+def test_oracle_odometry_on_a_synthetic_drive():
+    """Scan-to-scan poses of the FP64 oracle (the plain search, Alg. 1) chained over a 180 m
+    synthetic drive score a few percent of drift; the same poses with the heading's sign flipped
+    in the conversion score several times worse, so the check sees the convention."""
+    import oracle as O
+    from paper_2203_00459_gb300 import synth
+    frames, poses = synth.make_drive(128, 45, speed_px=4.0, yaw_deg=1.0, period=30, seed=1)
+    cfg = O.make_cfg(128, 256, 64, temp_theta=0.2)
+    est = np.array([[r["theta"], r["tx"], r["ty"]] for r in (O.pose(frames[k], frames[k + 1], cfg) for k in range(45))])
+    gt = od.motion_from_pose(poses, 1.0)
+    d = od.drift(gt, od.motion_from_pose(est, 1.0), lengths=(100.0,))
+    assert d["segments"] > 15 and d["translation_pct"] < 4.0 and d["rotation_deg_per_km"] < 40.0, d
+    flipped = est * np.array([-1.0, 1.0, 1.0])
+    bad = od.drift(gt, od.motion_from_pose(flipped, 1.0), lengths=(100.0,))
+    assert bad["translation_pct"] > 3 * d["translation_pct"], (d, bad)
