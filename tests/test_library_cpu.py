@@ -91,3 +91,12 @@ def test_noalloc_keeps_the_fft_angle_counts(L, n_theta, status):
     st = L.fmbym_pose_noalloc(None, ctypes.byref(c), 1, ctypes.c_void_p(16), ctypes.c_void_p(16),
                               ctypes.c_void_p(16), None, None)
     assert st == status and L.fmbym_noalloc_last_error().decode()
+
+
+def test_polar_wrapper_rejects_host_tensors():
+    torch = pytest.importorskip("torch")
+    from paper_2203_00459_gb300.search import polar_to_cartesian
+    with pytest.raises(ValueError):
+        polar_to_cartesian(torch.zeros((1, 400, 100)), 64, 0.4, 0.0438)
+    with pytest.raises(ValueError):
+        polar_to_cartesian(torch.zeros((1, 400, 100), dtype=torch.float64), 64, 0.4, 0.0438)
