@@ -498,6 +498,8 @@ def test_full_circle_heading(deg, flip):
     full = O.pose(f, g, O.make_cfg(n, 128, 64, temp_theta=0.2, full_circle=1))
     wrap = lambda a: (a + math.pi) % (2 * math.pi) - math.pi
     assert abs(wrap(full["theta"] - th)) < math.radians(1.5)
+    assert -math.pi < full["theta"] <= math.pi       # the flipped heading is reported in (-pi, pi]
+    assert abs(full["theta"] - th) < math.radians(1.5) or abs(th) > math.pi - math.radians(1.5)
     assert abs(full["tx"] - tx) < 0.5 and abs(full["ty"] - ty) < 0.5
     assert abs(wrap(half["theta"] - th + (math.pi if flip else 0.0))) < math.radians(1.5)
     if not flip:
