@@ -93,6 +93,17 @@ def conv_bn_relu(x, p, state, name, training):
     return bf16(torch.relu(xhat * p[name + ".gamma"][None, :, None, None] + p[name + ".beta"][None, :, None, None]))
 
 
+def down2(x):
+    """Encoder step down: 2 x 2 max-pool, stride 2 (Tab. II)."""
+    return F.max_pool2d(x, 2)
+
+
+def up2(x):
+    """Decoder step up: bilinear x2 with align_corners=False, rounded to bf16 like every
+    post-activation tensor (Tab. II)."""
+    return bf16(F.interpolate(x, scale_factor=2, mode="bilinear", align_corners=False))
+
+
 def forward(p, state, f, g, channels=(8, 16, 32, 64), training=True):
     """Masks [B, 2, H, W] (float64) of Eq. 10 for scans f, g [B, H, W]."""
     x = bf16(torch.stack([f, g], dim=1))
@@ -100,12 +111,12 @@ def forward(p, state, f, g, channels=(8, 16, 32, 64), training=True):
     L = len(channels)
     for i in range(L):
         if i > 0:
-            x = F.max_pool2d(x, 2)
+            x = down2(x)
         x = conv_bn_relu(x, p, state, f"enc{i}a", training)
         x = conv_bn_relu(x, p, state, f"enc{i}b", training)
         skips.append(x)
     for i in range(L - 2, -1, -1):
-        up = bf16(F.interpolate(x, scale_factor=2, mode="bilinear", align_corners=False))
+        up = up2(x)
         x = torch.cat([up, skips[i]], dim=1)
         x = conv_bn_relu(x, p, state, f"dec{i}a", training)
         x = conv_bn_relu(x, p, state, f"dec{i}b", training)

@@ -42,9 +42,10 @@ def _conv3x3_bruteforce(x, w):
     return out
 
 
-def test_conv_bn_relu_is_bruteforce_conv_then_numpy_batchnorm():
+@pytest.mark.parametrize("scale", [1.0, 1e-3])   # 1e-3: batch variance near eps, where its place shows
+def test_conv_bn_relu_is_bruteforce_conv_then_numpy_batchnorm(scale):
     rng = np.random.default_rng(3)
-    x = rng.standard_normal((2, 3, 6, 5))
+    x = scale * rng.standard_normal((2, 3, 6, 5))
     p = {"l.w": torch.from_numpy(rng.standard_normal((4, 3, 3, 3))),
          "l.gamma": torch.from_numpy(rng.uniform(0.5, 1.5, 4)), "l.beta": torch.from_numpy(rng.uniform(-.3, .3, 4))}
     st = {"l.mean": torch.zeros(4, dtype=torch.float64), "l.var": torch.ones(4, dtype=torch.float64)}
@@ -78,14 +79,14 @@ def test_bilinear_x2_weights_by_hand():
     want = np.array([1.0, 0.75 * 1 + 0.25 * 4, 0.25 * 1 + 0.75 * 4, 0.75 * 4 + 0.25 * 2, 0.25 * 4 + 0.75 * 2,
                      0.75 * 2 + 0.25 * 8, 0.25 * 2 + 0.75 * 8, 8.0])
     x = torch.from_numpy(np.outer([1.0, 1.0], a))[None, None]          # [1, 1, 2, 4], constant along y
-    got = F.interpolate(x, scale_factor=2, mode="bilinear", align_corners=False)[0, 0].numpy()
+    got = U.up2(x)[0, 0].numpy()   # the oracle's own step (these values are exact in bf16)
     assert got.shape == (4, 8)
     assert np.allclose(got, want[None, :], rtol=0, atol=1e-15)
 
 
 def test_maxpool_routes_the_gradient_to_the_window_maximum():
     x = torch.tensor([[[[1.0, 5.0, 2.0, 2.0], [3.0, 0.0, 7.0, 1.0]]]], dtype=torch.float64, requires_grad=True)
-    y = F.max_pool2d(x, 2)
+    y = U.down2(x)
     assert y.detach().numpy().ravel().tolist() == [5.0, 7.0]
     (y * torch.tensor([[[[10.0, 20.0]]]], dtype=torch.float64)).sum().backward()
     assert x.grad.numpy().ravel().tolist() == [0, 10, 0, 0, 0, 0, 20, 0]
@@ -203,3 +204,16 @@ def test_network_gradient_matches_central_differences_without_bf16(monkeypatch):
         fd = (loss(qp) - loss(qm)) / (2 * h)
         an = float(gr[name][idx])
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, fd, an)
+
+
+def test_first_convolution_sees_bf16_scans():
+    """The two scans enter the network rounded to bf16 (the CUDA path's operand type): scans that
+    differ only below bf16's resolution give identical masks."""
+    ch = (4, 8)
+    p = U.init_params(ch, seed=4)
+    rng = np.random.default_rng(5)
+    f = torch.from_numpy(rng.random((2, 8, 8)))
+    g = torch.from_numpy(rng.random((2, 8, 8)))
+    m1 = U.forward(p, U.init_state(ch), f, g, ch, training=True)
+    m2 = U.forward(p, U.init_state(ch), U.bf16(f), U.bf16(g), ch, training=True)
+    assert torch.equal(m1, m2) and not torch.equal(f, U.bf16(f))
