@@ -2,7 +2,7 @@
 // among them: the same Cart2Pol samples, angle scores (Eq. 7, or the radial mean that Alg. 1
 // prints), soft-argmax and their adjoint as the FFT route of fwd.cu / bwd.cu, with the circular
 // correlation along angle evaluated as its direct sum.  Per pair n_theta^2 n_r multiply-adds
-// (1.4e8 at 733 x 256), spread over chunks of radii.
+// (6.9e7 at 733 x 128), twice that in the adjoint, spread over chunks of 8 radii.
 //
 //   k_polar_direct  bilinear Cart2Pol of |F_f| and |F_g| -> pol[q][r][a] = (A_f, A_g)
 //   k_angle_direct  c partials per chunk of radii: sum_r sum_a A_f[a,r] A_g[(a + l) mod n, r],
