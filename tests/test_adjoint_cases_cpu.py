@@ -42,3 +42,41 @@ def test_fft_route_adjoint_cases(monkeypatch, name, pairs):
     dps = np.array([[0.8, -0.35, 0.6], [-0.5, 1.0, 0.25], [0.3, 0.2, -0.9], [1.0, 0.0, 0.0], [0.0, 1.0, 1.0]])
     for i in range(pairs):
         assert dtheta_kink_margin(f[i], g[i], cfg, dps[i], monkeypatch) < 1e-3, (name, i)
+
+
+def _pairs(n, pts, walls, degs, tx, ty, seed):
+    ps = [synth.make_pair(n, pts, walls, math.radians(d), tx, ty, seed=seed, index=i) for i, d in enumerate(degs)]
+    return [a for a, _ in ps], [b for _, b in ps]
+
+
+def _batch(name, pairs, start):
+    f, g, _ = synth.make_batch(name, pairs=pairs, start=start)
+    return list(f), list(g)
+
+
+CASES = {
+    "raw scores, ragged radii": (lambda: _batch("batch256", 2, 0),
+                                 dict(n=256, n_theta=256, n_r=100, temp_theta=2.0e8, temp_xy=1.0e4, window=0,
+                                      score_norm=1, band_lo=3.5, band_hi=100.0)),
+    "circular padding": (lambda: _batch("single128", 2, 11), dict(n=128, n_theta=128, n_r=64, pad_mode=1, temp_xy=0.5)),
+    "radial mean": (lambda: _batch("batch256", 2, 61), dict(n=256, n_theta=400, n_r=128, temp_theta=2.0, angle_score=1)),
+    "full circle": (lambda: _pairs(128, 40, 6, (160.0, -20.0), 2.0, 1.0, 780),
+                    dict(n=128, n_theta=128, n_r=64, temp_theta=0.2, full_circle=1)),
+    "Alg. 1 stage 2": (lambda: _pairs(128, 40, 6, (15.0, -9.0), 3.0, -2.0, 784),
+                       dict(n=128, n_theta=128, n_r=64, temp_theta=0.5, rotate_target=1)),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_option_adjoint_cases(monkeypatch, case):
+    make, kw = CASES[case]
+    f, g = make()
+    cfg = O.make_cfg(**kw)
+    for i in range(2):
+        assert dtheta_kink_margin(f[i], g[i], cfg, DP[i], monkeypatch) < 1e-3, (case, i)
+
+
+def test_schedule_variant_case(monkeypatch):
+    f, g = _batch("batch256", 2, 31)
+    cfg = O.make_cfg(256, 400, 128)
+    assert dtheta_kink_margin(f[0], g[0], cfg, np.array([0.7, -0.4, 0.5]), monkeypatch) < 1e-3
