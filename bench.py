@@ -538,6 +538,11 @@ def main():
     from paper_2203_00459_gb300 import replicas
     world, rank, local = replicas.world()
     if args.impl == "reference":
+        if args.workload not in synth.WORKLOADS:
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": f"the FP64 oracle arm times the search workloads "
+                                  f"({', '.join(synth.WORKLOADS)}); {args.workload} has no timed oracle arm"}))
+            return
         run_reference(args, spec, rank)
         return
 
