@@ -269,7 +269,7 @@ const char* fmbym_noalloc_last_error(void);
  *   n_scans     number of scans (>= 0; 0 does nothing)
  *   polar       device float32 [n_scans][n_azimuths][n_range], row-major, caller-owned
  *   n_azimuths  >= 1;  n_range >= 1;  range_res > 0 (metres per range bin)
- *   n           side of the Cartesian images (>= 1, any size);  delta_xy > 0 (metres per pixel)
+ *   n           side of the Cartesian images (1..16384);  delta_xy > 0 (metres per pixel)
  *   cart        device float32 [n_scans][n][n] out, caller-owned, overwritten
  * Returns FMBYM_ERR_INVALID_ARG for an out-of-range size or a NULL buffer with n_scans > 0, and
  * FMBYM_ERR_CUDA when the launch fails.  Needs no handle and allocates nothing. */

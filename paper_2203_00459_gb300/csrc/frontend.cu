@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(kFrontThreads) k_polar_to_cart(const float* __
 
 extern "C" int fmbym_polar_to_cartesian(void* stream, int n_scans, const float* polar, int n_azimuths, int n_range,
                                         float range_res, int n, float delta_xy, float* cart) {
-    if (n_scans < 0 || n_azimuths < 1 || n_range < 1 || n < 1 || !(range_res > 0.f) || !(delta_xy > 0.f))
+    // n <= 16384 keeps a scan's pixel index in 32 bits
+    if (n_scans < 0 || n_azimuths < 1 || n_range < 1 || n < 1 || n > 16384 || !(range_res > 0.f) || !(delta_xy > 0.f))
         return FMBYM_ERR_INVALID_ARG;
     if (n_scans == 0) return FMBYM_OK;
     if (!polar || !cart) return FMBYM_ERR_INVALID_ARG;

@@ -75,7 +75,7 @@ def test_polar_to_cartesian_validates_before_any_cuda_call(L):
         return f(None, a["n_scans"], ctypes.c_void_p(16), a["n_az"], a["n_range"], a["res"], a["n"], a["dxy"],
                  ctypes.c_void_p(16))
     for bad in (dict(n_scans=-1), dict(n_az=0), dict(n_range=0), dict(res=0.0), dict(res=float("nan")), dict(n=0),
-                dict(dxy=-0.4)):
+                dict(n=16385), dict(dxy=-0.4)):
         assert call(**bad) == 1, bad
     assert f(None, 1, None, 400, 3768, 0.0438, 256, 0.4, None) == 1          # NULL buffers
     assert f(None, 0, None, 400, 3768, 0.0438, 256, 0.4, None) == 0          # nothing to do
