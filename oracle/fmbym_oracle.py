@@ -4,9 +4,15 @@ TEST INFRASTRUCTURE ONLY. Nothing on the product path imports this module: only 
 tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference`` legs
 of ``bench.py`` may call it.  It shares no code with the CUDA library.
 
-Every function follows one step of Alg. 1 in the paper's order, in float64, with the
-numpy FFT as the only library primitive (Alg. 1 itself computes its correlations with
-FFT2d / iFFT2d).  Readings of the places where the paper is silent or ambiguous:
+Every function follows one step of Alg. 1 in the paper's order, in float64.  Every 2D DFT is the
+direct sum of its definition (Eq. 4), F[v, u] = sum_y sum_x x[y, x] exp(-2 pi i (v y + u x) / N),
+evaluated separably as a product with explicit DFT matrices whose exponents are reduced modulo N
+in integers (a matrix product is the only library primitive).  The translation scores are the
+correlation theorem over those direct DFTs, as Alg. 1 computes them; xcorr2d_brute is the sum of
+the definition itself, sum_x f'(x) g(x + s), lag by lag, and the angle scores are the
+brute-force circular double sum.  numpy's FFT survives only behind cfg["route"] = "fft", a faster
+route of the same sums kept as a cross-check and for the central-difference loops.  Readings of
+the places where the paper is silent or ambiguous:
 
 * A1  correlations conjugate the first operand: c = iFFT(conj(FFT a) * FFT b)  (Eq. 3, 7, 8
       define correlation; Alg. 1 prints the product without the conjugate).
@@ -37,19 +43,23 @@ import numpy as np
 # ----------------------------------------------------------------------------------------------
 
 def make_cfg(n, n_theta, n_r, temp_theta=1.0, temp_xy=1.0, delta_xy=1.0, window=1, pad_mode=0,
-             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0, full_circle=0, rotate_target=0):
+             score_norm=0, band_lo=2.0, band_hi=None, angle_score=0, full_circle=0, rotate_target=0,
+             route="direct"):
     """Alg. 1 parameters (n_theta, T_theta, n_xy = n, delta_xy, T_xy) plus the A3-A7 switches;
     angle_score 0 is Eq. 7 (reading A2), 1 the mean over radial lags that Alg. 1 prints;
     full_circle 1 resolves the heading over the full circle (see pose()); rotate_target 0 rotates
     the source f by theta (reading A8), 1 is Alg. 1's own stage 2: g turned back by theta, then the
-    translation found between f and it turned by theta (see pose())."""
+    translation found between f and it turned by theta (see pose()); route "direct" evaluates the
+    DFTs as their direct sums, "fft" through numpy's FFT (the same sums, faster)."""
     if int(rotate_target) == 1 and int(full_circle) == 1:
         raise ValueError("rotate_target 1 is defined for the half-circle search only")
+    if route not in ("direct", "fft"):
+        raise ValueError("route must be 'direct' or 'fft'")
     return dict(n=int(n), n_theta=int(n_theta), n_r=int(n_r), temp_theta=float(temp_theta),
                 temp_xy=float(temp_xy), delta_xy=float(delta_xy), window=int(window),
                 pad_mode=int(pad_mode), score_norm=int(score_norm), band_lo=float(band_lo),
                 band_hi=float(n / 2 if band_hi is None else band_hi), angle_score=int(angle_score),
-                full_circle=int(full_circle), rotate_target=int(rotate_target))
+                full_circle=int(full_circle), rotate_target=int(rotate_target), route=route)
 
 
 def lags(n):
@@ -76,16 +86,28 @@ def band_mask(n, band_lo, band_hi):
     return ((rho >= band_lo) & (rho <= band_hi)).astype(np.float64)
 
 
+def dft_matrix(n, rows=None, sign=-1):
+    """The kernel of the length-n DFT sum: W[k, j] = exp(sign 2 pi i k j / n) for frequency (or lag)
+    k in `rows` (default 0..n-1) and sample j < n.  The product k j is reduced modulo n in integers
+    first, so every entry is a root of unity rounded once."""
+    k = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
+    kj = np.mod(np.outer(k, np.arange(n, dtype=np.int64)), n)
+    return np.exp(sign * 2j * np.pi * kj.astype(np.float64) / n)
+
+
 def spectrum(x, cfg):
     """Windowed 2D DFT of a real scan, half plane u in [0, N/2] (Alg. 1 FFT2d; Eq. 4).
 
-    F[v, u] = sum_y sum_x w[y] w[x] x[y, x] exp(-2 pi i (v y + u x) / N)."""
+    F[v, u] = sum_y sum_x w[y] w[x] x[y, x] exp(-2 pi i (v y + u x) / N), the direct sum done as
+    the separable matrix product W_N X W_half^T."""
     n = cfg["n"]
     x = np.asarray(x, dtype=np.float64)
     if cfg["window"]:
         w = hann(n)
         x = x * w[:, None] * w[None, :]
-    return np.fft.rfft2(x)
+    if cfg.get("route", "direct") == "fft":
+        return np.fft.rfft2(x)
+    return dft_matrix(n) @ x @ dft_matrix(n, np.arange(n // 2 + 1)).T
 
 
 def magnitude(F, cfg):
@@ -211,17 +233,45 @@ def rotate(x, theta):
     return out
 
 
-def xcorr2d(fr, g, pad_mode):
-    """Translation scores c[s] = sum_x fr(x) g(x + s), s in [-N/2, N/2)^2 (Eq. 3 and 8),
-    through the correlation theorem as in Alg. 1: ZeroPad to P = 2N, then
-    iFFT2d(conj(FFT2d(fr)) o FFT2d(g)) (A1, A7).  pad_mode=1: N-periodic correlation."""
+def xcorr2d(fr, g, pad_mode, route="direct"):
+    """Translation scores c[s] = sum_x fr(x) g(x + s), s in lags(N)^2 (Eq. 3 and 8), through the
+    correlation theorem as in Alg. 1: ZeroPad to P = 2N, then iDFT2d(conj(DFT2d(fr)) o DFT2d(g))
+    at the kept lags (A1, A7).  pad_mode=1: N-periodic correlation (P = N).
+
+    route "direct": each DFT is its direct sum.  The padded entries are zero, so the forward sums
+    run over the N x N scan, Fp = W_P[:, :N] fr W_P[:, :N]^T, and the inverse sum
+    c[s] = P^-2 sum_k sum_l conj(Fp) Gp exp(+2 pi i (k s_y + l s_x) / P) is evaluated only at the
+    kept lags s mod P."""
     n = fr.shape[0]
     p = n if pad_mode == 1 else 2 * n
-    Fp = np.fft.fft2(np.asarray(fr, np.float64), s=(p, p))
-    Gp = np.fft.fft2(np.asarray(g, np.float64), s=(p, p))
-    full = np.real(np.fft.ifft2(np.conj(Fp) * Gp))
+    fr = np.asarray(fr, np.float64)
+    g = np.asarray(g, np.float64)
     s = np.mod(lags(n), p)
-    return full[np.ix_(s, s)]
+    if route == "fft":
+        Fp = np.fft.fft2(fr, s=(p, p))
+        Gp = np.fft.fft2(g, s=(p, p))
+        full = np.real(np.fft.ifft2(np.conj(Fp) * Gp))
+        return full[np.ix_(s, s)]
+    Wp = dft_matrix(p)[:, :n]
+    Fp = Wp @ fr @ Wp.T
+    Gp = Wp @ g @ Wp.T
+    Wi = dft_matrix(p, s, sign=+1)
+    return np.real(Wi @ (np.conj(Fp) * Gp) @ Wi.T) / (p * p)
+
+
+def xcorr2d_brute(fr, g, pad_mode, lag_list=None):
+    """The translation scores by brute force, c[s] = sum_x fr(x) g(x + s) summed for each lag on
+    its own (Eq. 3, 8; no transform).  Returns the full surface over lags(N)^2 in lag order, or,
+    given lag_list [(s_y, s_x), ...], the scores at those lags."""
+    n = fr.shape[0]
+    if lag_list is not None:
+        return np.array([xcorr2d_direct(fr, g, int(sy), int(sx), pad_mode) for sy, sx in lag_list])
+    L = lags(n)
+    c = np.empty((n, n))
+    for i, sy in enumerate(L):
+        for j, sx in enumerate(L):
+            c[i, j] = xcorr2d_direct(fr, g, int(sy), int(sx), pad_mode)
+    return c
 
 
 def xcorr2d_direct(fr, g, sy, sx, pad_mode):
@@ -265,7 +315,7 @@ def pose(f, g, cfg, keep=False):
         # With g(x) = f'(x - t) and f' = rotate(f, theta) (reading A8), g turned back by theta is f
         # shifted by t' = R(-theta) t, so the scores peak at t' and t = R(theta) t'
         gr = rotate(g, -theta)
-        c_xy = xcorr2d(f, gr, cfg["pad_mode"])
+        c_xy = xcorr2d(f, gr, cfg["pad_mode"], cfg.get("route", "direct"))
         p_xy = soft_argmax(c_xy, cfg["temp_xy"], cfg["score_norm"])
         s = lags(n) * cfg["delta_xy"]
         tpx = float(np.sum(p_xy * s[None, :]))
@@ -277,13 +327,13 @@ def pose(f, g, cfg, keep=False):
             out.update(Ff=Ff, Fg=Fg, af=af, ag=ag, pf=pf, pg=pg, p_theta=p_theta, gr=gr, p_xy=p_xy)
         return out
     fr = rotate(f, theta)
-    c_xy = xcorr2d(fr, g, cfg["pad_mode"])
+    c_xy = xcorr2d(fr, g, cfg["pad_mode"], cfg.get("route", "direct"))
     if cfg.get("full_circle", 0) == 1:
         # |F| cannot tell theta from theta + pi (Sec. V suggests the decoupled search for arbitrary
         # headings): correlate at both and keep the one whose translation peak is higher
         theta_b = theta + np.pi if theta < 0 else theta - np.pi
         fr_b = rotate(f, theta_b)
-        c_b = xcorr2d(fr_b, g, cfg["pad_mode"])
+        c_b = xcorr2d(fr_b, g, cfg["pad_mode"], cfg.get("route", "direct"))
         if c_b.max() > c_xy.max():
             theta, fr, c_xy = theta_b, fr_b, c_b
     p_xy = soft_argmax(c_xy, cfg["temp_xy"], cfg["score_norm"])
@@ -309,7 +359,7 @@ def pose_exhaustive(f, g, cfg, angles):
     peaks = np.empty(len(angles))
     best = None
     for k, th in enumerate(angles):
-        c_xy = xcorr2d(rotate(f, float(th)), g, cfg["pad_mode"])
+        c_xy = xcorr2d(rotate(f, float(th)), g, cfg["pad_mode"], cfg.get("route", "direct"))
         peaks[k] = c_xy.max()
         if best is None or peaks[k] > peaks[best[0]]:
             best = (k, c_xy)
@@ -350,22 +400,38 @@ def soft_argmax_backward(c, p, q, temp, score_norm):
     return ((dz - dz.mean() - z * np.mean(dz * z)) / sd).reshape(shape)
 
 
-def xcorr2d_backward(fr, g, dc, pad_mode):
-    """Adjoint of c[s] = sum_x fr(x) g(x + s) (Eq. 3, lags s in [-N/2, N/2)^2).
+def xcorr2d_backward(fr, g, dc, pad_mode, route="direct"):
+    """Adjoint of c[s] = sum_x fr(x) g(x + s) (Eq. 3, lags s in lags(N)^2).
 
     d fr(x) = sum_s dc[s] g(x + s)  (correlation of dc with g)
     d g(y)  = sum_s dc[s] fr(y - s) (convolution of dc with fr)
-    both evaluated through the same padded transforms as the forward pass."""
+    both evaluated through the same padded transforms as the forward pass: with D the lag surface
+    embedded at s mod P, d fr = iDFT(conj(DFT D) DFT g) and d g = iDFT(DFT D DFT fr), read on the
+    scan x < N.  route "direct" takes every DFT as its direct sum (the forward sums over the
+    non-zero support, the inverse sums at the scan's N positions only)."""
     n = fr.shape[0]
     p = n if pad_mode == 1 else 2 * n
-    D = np.zeros((p, p))
+    fr = np.asarray(fr, np.float64)
+    g = np.asarray(g, np.float64)
     s = np.mod(lags(n), p)
-    D[np.ix_(s, s)] = dc
-    Dh = np.fft.fft2(D)
-    Gh = np.fft.fft2(np.asarray(g, np.float64), s=(p, p))
-    Fh = np.fft.fft2(np.asarray(fr, np.float64), s=(p, p))
-    dfr = np.real(np.fft.ifft2(np.conj(Dh) * Gh))[:n, :n]
-    dg = np.real(np.fft.ifft2(Dh * Fh))[:n, :n]
+    if route == "fft":
+        D = np.zeros((p, p))
+        D[np.ix_(s, s)] = dc
+        Dh = np.fft.fft2(D)
+        Gh = np.fft.fft2(g, s=(p, p))
+        Fh = np.fft.fft2(fr, s=(p, p))
+        dfr = np.real(np.fft.ifft2(np.conj(Dh) * Gh))[:n, :n]
+        dg = np.real(np.fft.ifft2(Dh * Fh))[:n, :n]
+        return dfr, dg
+    W = dft_matrix(p)
+    Wn = W[:, :n]
+    Ws = W[:, s]                     # D is non-zero only at the lag positions s mod P
+    Dh = Ws @ np.asarray(dc, np.float64) @ Ws.T
+    Gh = Wn @ g @ Wn.T
+    Fh = Wn @ fr @ Wn.T
+    Wi = dft_matrix(p, np.arange(n), sign=+1)
+    dfr = np.real(Wi @ (np.conj(Dh) * Gh) @ Wi.T) / (p * p)
+    dg = np.real(Wi @ (Dh * Fh) @ Wi.T) / (p * p)
     return dfr, dg
 
 
@@ -449,11 +515,14 @@ def magnitude_backward(F, da, cfg):
 
 def spectrum_backward(dF, cfg):
     """Adjoint of the windowed half-plane DFT: d x[y,x] = w[y] w[x] Re sum_{v, u<=N/2} dF[v,u]
-    exp(+2 pi i (v y + u x) / N)."""
+    exp(+2 pi i (v y + u x) / N), as the direct sum conj(W_N) dF conj(W_half)."""
     n = cfg["n"]
-    D = np.zeros((n, n), dtype=np.complex128)
-    D[:, : n // 2 + 1] = dF
-    dx = np.real(np.fft.ifft2(D)) * (n * n)
+    if cfg.get("route", "direct") == "fft":
+        D = np.zeros((n, n), dtype=np.complex128)
+        D[:, : n // 2 + 1] = dF
+        dx = np.real(np.fft.ifft2(D)) * (n * n)
+    else:
+        dx = np.real(np.conj(dft_matrix(n)) @ dF @ np.conj(dft_matrix(n, np.arange(n // 2 + 1))))
     if cfg["window"]:
         w = hann(n)
         dx = dx * w[:, None] * w[None, :]
@@ -477,13 +546,14 @@ def pose_backward(f, g, cfg, dpose):
         dth_t = dtx * (-st * r["tpx"] - ct * r["tpy"]) + dty * (ct * r["tpx"] - st * r["tpy"])
         q_xy = dtpx * s[None, :] + dtpy * s[:, None]
         dc_xy = soft_argmax_backward(r["c_xy"], r["p_xy"], q_xy, cfg["temp_xy"], cfg["score_norm"])
-        df, dgr = xcorr2d_backward(np.asarray(f, np.float64), r["gr"], dc_xy, cfg["pad_mode"])
+        df, dgr = xcorr2d_backward(np.asarray(f, np.float64), r["gr"], dc_xy, cfg["pad_mode"],
+                                   cfg.get("route", "direct"))
         dg, dth_rot_arg = rotate_backward(g, -th, dgr)
         dth_rot = dth_t - dth_rot_arg
     else:
         q_xy = dtx * s[None, :] + dty * s[:, None]
         dc_xy = soft_argmax_backward(r["c_xy"], r["p_xy"], q_xy, cfg["temp_xy"], cfg["score_norm"])
-        dfr, dg = xcorr2d_backward(r["fr"], g, dc_xy, cfg["pad_mode"])
+        dfr, dg = xcorr2d_backward(r["fr"], g, dc_xy, cfg["pad_mode"], cfg.get("route", "direct"))
         df, dth_rot = rotate_backward(f, r["theta"], dfr)
     dth = dth_out + dth_rot
     q_t = dth * lags(nt) * (np.pi / nt)

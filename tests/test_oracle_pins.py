@@ -254,15 +254,83 @@ def test_xcorr2d_matches_scipy_correlate(n):
     assert rel(O.xcorr2d(fr, g, 0), full[np.ix_(s, s)]) < 1e-12
 
 
-def test_xcorr2d_fft_route_equals_direct_sum():
+def test_xcorr2d_transform_routes_equal_the_direct_sum():
+    """Both routes of the correlation theorem (direct DFT sums, numpy FFT) give the definition's
+    value at single lags, the +-N/2 edges among them."""
     n = 40
     fr = RNG.random((n, n))
     g = RNG.random((n, n))
     for pad in (0, 1):
-        c = O.xcorr2d(fr, g, pad)
-        for sy, sx in [(-20, -20), (-20, 19), (0, 0), (7, -3), (19, 19), (-1, 12)]:
-            d = O.xcorr2d_direct(fr, g, sy, sx, pad)
-            assert abs(c[sy + n // 2, sx + n // 2] - d) < 1e-11 * abs(d)
+        for route in ("direct", "fft"):
+            c = O.xcorr2d(fr, g, pad, route)
+            for sy, sx in [(-20, -20), (-20, 19), (0, 0), (7, -3), (19, 19), (-1, 12)]:
+                d = O.xcorr2d_direct(fr, g, sy, sx, pad)
+                assert abs(c[sy + n // 2, sx + n // 2] - d) < 1e-11 * abs(d), (pad, route, sy, sx)
+
+
+@pytest.mark.parametrize("n", [16, 17])
+def test_xcorr2d_brute_is_the_definition(n):
+    """The brute-force surface against scipy's correlate2d (zero outside the scan) and against the
+    sum with np.roll (N-periodic), over every lag."""
+    fr = RNG.random((n, n))
+    g = RNG.random((n, n))
+    full = sig.correlate2d(g, fr, mode="full")
+    s = O.lags(n) + n - 1
+    assert rel(O.xcorr2d_brute(fr, g, 0), full[np.ix_(s, s)]) < 1e-13
+    ref = np.array([[np.sum(fr * np.roll(g, (-sy, -sx), axis=(0, 1))) for sx in O.lags(n)] for sy in O.lags(n)])
+    assert rel(O.xcorr2d_brute(fr, g, 1), ref) < 1e-13
+    lag_list = [(int(O.lags(n)[0]), int(O.lags(n)[-1])), (0, 0), (3, -2)]
+    vals = O.xcorr2d_brute(fr, g, 0, lag_list)
+    for (sy, sx), v in zip(lag_list, vals):
+        assert v == full[sy + n - 1, sx + n - 1] or abs(v - full[sy + n - 1, sx + n - 1]) < 1e-12 * abs(v)
+
+
+def test_dft_matrix_is_the_unitary_root_table():
+    """W[k, j] = exp(-2 pi i k j / n): symmetric, unit modulus, W W^H = n I, row 1 the first root."""
+    for n in (12, 127, 768):
+        W = O.dft_matrix(n)
+        assert np.max(np.abs(W - W.T)) == 0.0
+        assert np.max(np.abs(np.abs(W) - 1.0)) < 1e-15
+        assert np.max(np.abs(W @ np.conj(W).T - n * np.eye(n))) < 1e-10 * n
+        assert abs(W[1, 1] - complex(math.cos(2 * math.pi / n), -math.sin(2 * math.pi / n))) < 1e-16
+        rows = [0, 5, n - 1]
+        assert np.array_equal(O.dft_matrix(n, rows), W[rows])
+        assert np.array_equal(O.dft_matrix(n, rows, +1), np.conj(W[rows]))
+
+
+@pytest.mark.parametrize("n,nt,nr", [(128, 128, 64), (127, 733, 16), (64, 50, 32)])
+def test_direct_sum_route_agrees_with_the_fft_route(n, nt, nr):
+    """Every DFT of the search by its direct sum against numpy's FFT on the same sums: spectra,
+    the padded correlation and both adjoints, and the whole forward and backward search."""
+    f, g = RNG.random((n, n)), RNG.random((n, n))
+    c = O.make_cfg(n, nt, nr)
+    cf = dict(c, route="fft")
+    assert rel(O.spectrum(f, c), O.spectrum(f, cf)) < 1e-13
+    dF = RNG.standard_normal((n, n // 2 + 1)) + 1j * RNG.standard_normal((n, n // 2 + 1))
+    assert rel(O.spectrum_backward(dF, c), O.spectrum_backward(dF, cf)) < 1e-13
+    dc = RNG.standard_normal((n, n))
+    for pad in (0, 1):
+        assert rel(O.xcorr2d(f, g, pad), O.xcorr2d(f, g, pad, "fft")) < 1e-13
+        a = O.xcorr2d_backward(f, g, dc, pad)
+        b = O.xcorr2d_backward(f, g, dc, pad, "fft")
+        assert rel(a[0], b[0]) < 1e-13 and rel(a[1], b[1]) < 1e-13
+    r, rf = O.pose(f, g, c), O.pose(f, g, cf)
+    for k in ("theta", "tx", "ty"):
+        assert abs(r[k] - rf[k]) < 1e-12
+    assert rel(r["c_xy"], rf["c_xy"]) < 1e-13 and rel(r["c_theta"], rf["c_theta"]) < 1e-13
+    dp = np.array([0.7, -0.2, 0.4])
+    a, b = O.pose_backward(f, g, c, dp), O.pose_backward(f, g, cf, dp)
+    assert rel(a[0], b[0]) < 1e-11 and rel(a[1], b[1]) < 1e-11
+
+
+def test_brute_force_scores_of_a_benchmark_pair_at_128():
+    """The padded correlation of a 128^2 benchmark pair, every one of its 128^2 lags by the sum of
+    the definition, against the direct-DFT route that pose() takes (and the circular variant)."""
+    from paper_2203_00459_gb300 import synth
+    f, g, _ = synth.make_batch("single128", pairs=1)
+    fr = O.rotate(f[0], 0.05)
+    for pad in (0, 1):
+        assert rel(O.xcorr2d_brute(fr, g[0], pad), O.xcorr2d(fr, g[0], pad)) < 1e-13
 
 
 @pytest.mark.parametrize("n", [64, 63])
