@@ -32,6 +32,43 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def check_device_tensor(t, name, device, shape=None, min_numel=None):
+    """Rejects, before any library call, a buffer the kernels cannot read or write as float32
+    device memory: not a tensor, not on CUDA, not float32, not contiguous, on another device than
+    the handle's, of the wrong shape, or holding fewer than min_numel elements.  A CPU tensor's
+    address handed to a kernel would be an illegal access, a float64 or strided one silent garbage."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (got device {t.device})")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32 (got {t.dtype})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the handle on {device}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)} (got {tuple(t.shape)})")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} holds {t.numel()} elements; the pairs need {min_numel}")
+    return t
+
+
+def check_host_tensor(t, name, numel=None):
+    """Rejects a host buffer of fmbym_pose_host that is not a contiguous CPU float32 tensor."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor, got {type(t).__name__}")
+    if t.is_cuda or t.device.type != "cpu":
+        raise ValueError(f"{name} must be a CPU tensor (got device {t.device})")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32 (got {t.dtype})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, expected {numel}")
+    return t
+
+
 class PoseSearch:
     """A library handle: plans and workspace for the given sizes and up to max_pairs pairs per call."""
 
@@ -83,8 +120,25 @@ class PoseSearch:
         return int(_lib.lib().fmbym_workspace_bytes(self.handle))
 
     # -- layout helpers ------------------------------------------------------------------------
+    def _scans(self, f, g, size_idx, offsets):
+        """Validates the scan buffers f and g against the handle and the pair layout (before any
+        library call) and returns _layout's tuple."""
+        check_device_tensor(f, "f", self.device)
+        check_device_tensor(g, "g", self.device, shape=f.shape)
+        lay = self._layout(f, size_idx, offsets)
+        n_pairs, si, off, _, ns = lay
+        if off is not None and off.size != n_pairs:
+            raise ValueError("offsets must have one entry per pair")
+        if off is None:
+            end = sum(n * n for n in ns)
+        else:
+            end = max((int(o) + n * n for o, n in zip(off, ns)), default=0)
+        if end > f.numel():
+            raise ValueError(f"the pairs reach element {end}, beyond the {f.numel()} elements of f and g")
+        return lay
+
     def _layout(self, f, size_idx, offsets):
-        """Returns (n_pairs, size_idx array or None, offsets array or None, n_theta list)."""
+        """Returns (n_pairs, size_idx array or None, offsets array or None, n_theta list, N list)."""
         if size_idx is None:
             if f.dim() != 3:
                 raise ValueError("f must be [B, N, N] when size_idx is not given")
@@ -94,6 +148,8 @@ class PoseSearch:
             return n_pairs, None, None, [self.sizes[0]["n_theta"]] * n_pairs, [self.sizes[0]["n"]] * n_pairs
         si = np.ascontiguousarray(np.asarray(size_idx, dtype=np.int32))
         n_pairs = si.size
+        if n_pairs and (si.min() < 0 or si.max() >= len(self.sizes)):
+            raise ValueError("size_idx out of range")
         off = None if offsets is None else np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
         return n_pairs, si, off, [self.sizes[i]["n_theta"] for i in si], [self.sizes[i]["n"] for i in si]
 
@@ -101,7 +157,9 @@ class PoseSearch:
     def pose(self, f, g, size_idx=None, offsets=None, want_c_theta=False, want_c_xy=False, stream=None,
              out=None):
         """Forward search; returns dict(pose [B,3], c_theta (flat) or None, c_xy (like f) or None)."""
-        n_pairs, si, off, nts, _ = self._layout(f, size_idx, offsets)
+        n_pairs, si, off, nts, _ = self._scans(f, g, size_idx, offsets)
+        if out is not None:
+            check_device_tensor(out, "out", self.device, shape=(n_pairs, 3))
         pose = out if out is not None else torch.empty((n_pairs, 3), device=f.device, dtype=torch.float32)
         ct = torch.empty(sum(nts), device=f.device, dtype=torch.float32) if want_c_theta else None
         cxy = torch.empty_like(f) if want_c_xy else None
@@ -114,10 +172,10 @@ class PoseSearch:
 
     def pose_backward(self, f, g, dpose, size_idx=None, offsets=None, stream=None):
         """Adjoint: (df, dg) given dL/dpose [B, 3]."""
-        n_pairs, si, off, _, _ = self._layout(f, size_idx, offsets)
+        n_pairs, si, off, _, _ = self._scans(f, g, size_idx, offsets)
+        check_device_tensor(dpose, "dpose", self.device, shape=(n_pairs, 3))
         df = torch.empty_like(f)
         dg = torch.empty_like(g)
-        dpose = dpose.contiguous().to(torch.float32)
         st = _lib.lib().fmbym_pose_backward(self.handle, _stream(stream), n_pairs,
                                             None if si is None else si.ctypes.data_as(ctypes.c_void_p),
                                             None if off is None else off.ctypes.data_as(ctypes.c_void_p),
@@ -130,14 +188,20 @@ class PoseSearch:
         2 = L2) and the adjoint of that loss, the adjoint reading the forward's intermediates instead
         of recomputing them.  out: optional preallocated (pose, loss, dpose, df, dg).  Returns
         (pose, loss, dpose, df, dg)."""
-        n_pairs, si, off, _, _ = self._layout(f, size_idx, offsets)
+        n_pairs, si, off, _, _ = self._scans(f, g, size_idx, offsets)
+        check_device_tensor(gt, "gt", self.device, shape=(n_pairs, 3))
+        if out is not None:
+            if len(out) != 5:
+                raise ValueError("out must be (pose, loss, dpose, df, dg)")
+            for t, nm, shp in zip(out, ("pose", "loss", "dpose", "df", "dg"),
+                                  ((n_pairs, 3), (1,), (n_pairs, 3), tuple(f.shape), tuple(g.shape))):
+                check_device_tensor(t, "out." + nm, self.device, shape=shp)
         if out is None:
             out = (torch.empty((n_pairs, 3), device=f.device, dtype=torch.float32),
                    torch.empty(1, device=f.device, dtype=torch.float32),
                    torch.empty((n_pairs, 3), device=f.device, dtype=torch.float32),
                    torch.empty_like(f), torch.empty_like(g))
         pose, loss, dpose, df, dg = out
-        gt = gt.contiguous().to(torch.float32)
         st = _lib.lib().fmbym_pose_train(self.handle, _stream(stream), n_pairs,
                                          None if si is None else si.ctypes.data_as(ctypes.c_void_p),
                                          None if off is None else off.ctypes.data_as(ctypes.c_void_p),
@@ -149,12 +213,22 @@ class PoseSearch:
     def pose_exhaustive(self, f, g, angles, size=0, offsets=None, want_peaks=False, stream=None, out=None):
         """Exhaustive rotate-then-correlate search over the candidate headings `angles` (radians):
         returns dict(pose [B, 3], peaks [B, len(angles)] or None).  Every pair has size `size`."""
+        check_device_tensor(f, "f", self.device)
+        check_device_tensor(g, "g", self.device, shape=f.shape)
+        if not 0 <= int(size) < len(self.sizes):
+            raise ValueError("size index out of range")
+        nn = self.sizes[int(size)]["n"] ** 2
         if offsets is None:
             n_pairs = f.shape[0]
             off = None
         else:
             off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
             n_pairs = off.size
+        end = n_pairs * nn if off is None else max((int(o) + nn for o in off), default=0)
+        if end > f.numel():
+            raise ValueError(f"the pairs reach element {end}, beyond the {f.numel()} elements of f and g")
+        if out is not None:
+            check_device_tensor(out, "out", self.device, shape=(n_pairs, 3))
         ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float32))
         pose = out if out is not None else torch.empty((n_pairs, 3), device=f.device, dtype=torch.float32)
         peaks = torch.empty((n_pairs, ang.size), device=f.device, dtype=torch.float32) if want_peaks else None
@@ -167,17 +241,26 @@ class PoseSearch:
 
     def pose_loss(self, pose, gt, kind=1, loss=None, dpose=None, stream=None):
         """Eq. 13 loss (kind 1 = L1, 2 = L2; mean over pairs) and dloss/dpose, on the device."""
+        check_device_tensor(pose, "pose", self.device)
         n_pairs = pose.shape[0]
+        check_device_tensor(pose, "pose", self.device, shape=(n_pairs, 3))
+        check_device_tensor(gt, "gt", self.device, shape=(n_pairs, 3))
+        if loss is not None:
+            check_device_tensor(loss, "loss", self.device, shape=(1,))
+        if dpose is not None:
+            check_device_tensor(dpose, "dpose", self.device, shape=(n_pairs, 3))
         loss = torch.empty(1, device=pose.device) if loss is None else loss
         dpose = torch.empty_like(pose) if dpose is None else dpose
-        st = _lib.lib().fmbym_pose_loss(self.handle, _stream(stream), n_pairs, _ptr(pose.contiguous()),
-                                        _ptr(gt.contiguous()), int(kind), _ptr(loss), _ptr(dpose))
+        st = _lib.lib().fmbym_pose_loss(self.handle, _stream(stream), n_pairs, _ptr(pose),
+                                        _ptr(gt), int(kind), _ptr(loss), _ptr(dpose))
         _lib.check(st, self.handle)
         return loss, dpose
 
     def pose_host(self, f_host, g_host, size_idx=None, offsets=None, stream=None):
         """Forward search from host (CPU, ideally pinned) tensors; returns the pose as a CPU tensor.
         Copies in, computes and copies out inside the call, which synchronises the stream."""
+        check_host_tensor(f_host, "f_host")
+        check_host_tensor(g_host, "g_host", numel=f_host.numel())
         if size_idx is None:
             n_pairs = f_host.shape[0]
             si = off = None
@@ -206,7 +289,8 @@ class PoseFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dpose):
         f, g = ctx.saved_tensors
-        df, dg = ctx.search.pose_backward(f.contiguous(), g.contiguous(), dpose, ctx.size_idx, ctx.offsets)
+        df, dg = ctx.search.pose_backward(f.contiguous(), g.contiguous(), dpose.contiguous(), ctx.size_idx,
+                                          ctx.offsets)
         return df, dg, None, None, None
 
 
