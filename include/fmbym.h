@@ -236,17 +236,20 @@ long long fmbym_launch_count(const fmbym_handle* h);
  * size tables, the pair table, counters and every intermediate) lives in one static device array
  * of fmbym_noalloc_capacity() bytes (16 MiB) inside the library, which every device that loads the
  * library reserves until the process exits.
- *   cfg       host pointer to one size configuration (validated as in fmbym_create)
+ *   cfg       host pointer to one size configuration, validated as in fmbym_create except that
+ *             n_theta must be 128, 256 or 400 (the counts with an FFT plan along angle; other counts
+ *             return FMBYM_ERR_UNSUPPORTED_SIZE)
  *   n_pairs   pairs packed back to back: pair p at element offset p * N * N of f, g and c_xy
  *   f, g, pose, c_theta, c_xy  as in fmbym_pose (device, caller-owned; c_theta and c_xy may be NULL)
  * Limit: the whole footprint must fit the array (with the benchmark grids: one 512x512 pair, five
  * 256x256 pairs or 24 128x128 pairs); larger requests return FMBYM_ERR_WORKSPACE and the message
  * gives the bytes needed.  The first call on a device does a one-time set-up (it looks up the array's
  * device address and sets kernel attributes), so make that first call before any stream capture.
- * Every call shares the one array, which keeps the last call's contents: the call clears what must
- * start at zero itself, and re-uploads the size tables (a small synchronous host-to-device copy)
- * when cfg differs from the previous call's.  Calls that overlap on the GPU (other streams, other
- * host threads) race on the array.  Errors are reported by fmbym_noalloc_last_error(). */
+ * Every call shares the one array, which keeps the last call's contents.  Each call therefore
+ * rebuilds, with one small kernel on the stream, everything it reads before writing it: the size
+ * tables, the pair table and the zeroed completion counters; it copies nothing from host memory.
+ * Calls that overlap on the GPU (other streams, other host threads) race on the array.  Errors are
+ * reported by fmbym_noalloc_last_error(). */
 int fmbym_pose_noalloc(void* stream, const fmbym_size_cfg* cfg, int n_pairs, const float* f,
                        const float* g, float* pose, float* c_theta, float* c_xy);
 

@@ -11,10 +11,8 @@
 // The kernels are the ones fmbym_pose runs (launch_forward); only the memory they use differs.
 #include <cmath>
 #include <cstdint>
-#include <cstring>
 #include <mutex>
 #include <string>
-#include <vector>
 
 #include "../../include/fmbym.h"
 #include "common.cuh"
@@ -38,15 +36,11 @@ static __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
 struct DeviceState {
     bool ready = false;
     unsigned char* base = nullptr;  // device address of g_scratch on this device
-    bool have_tables = false;
-    fmbym_size_cfg tables_for{};    // configuration whose tables the array currently holds
 };
 DeviceState g_dev[kMaxDevices];
 std::mutex g_mutex;
 thread_local std::string g_error;
 thread_local Tracer g_tracer;       // counts launches; never records events
-
-constexpr double kPi = 3.14159265358979323846;
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -58,8 +52,6 @@ int fail(int code, const std::string& msg) {
 int cuda_fail(cudaError_t e, const char* what) {
     return fail(FMBYM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
-
-bool same_cfg(const fmbym_size_cfg& a, const fmbym_size_cfg& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
 
 struct Layout {
     size_t win, tw_n, tw_p, tw_t, polar, tab, cnt, work, total;
@@ -80,40 +72,63 @@ Layout layout(const DevPlan& p, int n_pairs) {
     return l;
 }
 
-// Copies the per-size tables (double precision on the host, rounded to float) into the array.
-cudaError_t upload_tables(const DevPlan& p, unsigned char* base, const Layout& l, cudaStream_t st) {
-    std::vector<float> win(p.n);
-    for (int i = 0; i < p.n; ++i) win[i] = (float)(0.5 - 0.5 * std::cos(2.0 * kPi * i / p.n));
-    auto twiddles = [](int L) {
-        std::vector<float2> t(L);
-        for (int k = 0; k < L; ++k) {
-            const double a = -2.0 * kPi * (double)k / (double)L;
-            t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+// Writes every table of one call into the array on the GPU: the periodic Hann window, the
+// twiddles of lengths N, P and n_theta, the bilinear Cart2Pol samples (all in double precision,
+// rounded to float as the handle's host-built tables are), the pair table (packed pairs: scan
+// offset i N^2, c_theta offset i n_theta, pair index i) and the zeroed completion counters.  No
+// host memory is read, so nothing has to stay alive on the host after the call returns.
+__global__ void k_noalloc_tables(int n, int pp, int nt, int nr, int n_pairs, float* __restrict__ win,
+                                 float2* __restrict__ tw_n, float2* __restrict__ tw_p, float2* __restrict__ tw_t,
+                                 PolarSample* __restrict__ polar, long long* __restrict__ tab,
+                                 unsigned* __restrict__ cnt) {
+    const long long n_pol = (long long)nt * nr;
+    const long long total = n + n + pp + nt + n_pol + n_pairs;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long k = i;
+        if (k < n) {   // w[k] = 0.5 - 0.5 cos(2 pi k / N)
+            win[k] = (float)(0.5 - 0.5 * cospi(2.0 * (double)k / (double)n));
+            continue;
         }
-        return t;
-    };
-    const std::vector<float2> twn = twiddles(p.n), twp = twiddles(p.p), twt = twiddles(p.nt);
-    std::vector<PolarSample> pol((size_t)p.nt * p.nr);
-    for (int a = 0; a < p.nt; ++a) {
-        const double alpha = (double)a * kPi / p.nt;
-        for (int r = 0; r < p.nr; ++r) {
-            const double rho = (double)r * (p.n / 2.0) / p.nr;
-            const double u = rho * std::cos(alpha), v = rho * std::sin(alpha);
-            const double x0 = std::floor(u), y0 = std::floor(v);
-            pol[(size_t)a * p.nr + r] = PolarSample{(int)x0, (int)y0, (float)(u - x0), (float)(v - y0)};
+        k -= n;
+        // tw[k] = exp(-2 pi i k / L) for L = N, P, n_theta
+        if (k < n) {
+            double sv, cv;
+            sincospi(-2.0 * (double)k / (double)n, &sv, &cv);
+            tw_n[k] = make_float2((float)cv, (float)sv);
+            continue;
         }
+        k -= n;
+        if (k < pp) {
+            double sv, cv;
+            sincospi(-2.0 * (double)k / (double)pp, &sv, &cv);
+            tw_p[k] = make_float2((float)cv, (float)sv);
+            continue;
+        }
+        k -= pp;
+        if (k < nt) {
+            double sv, cv;
+            sincospi(-2.0 * (double)k / (double)nt, &sv, &cv);
+            tw_t[k] = make_float2((float)cv, (float)sv);
+            continue;
+        }
+        k -= nt;
+        if (k < n_pol) {   // alpha_a = a pi / n_theta, rho_r = r (N/2) / n_r
+            const int a = (int)(k / nr), r = (int)(k % nr);
+            double sa, ca;
+            sincospi((double)a / (double)nt, &sa, &ca);
+            const double rho = (double)r * (n / 2.0) / nr;
+            const double u = rho * ca, v = rho * sa;
+            const double x0 = floor(u), y0 = floor(v);
+            polar[k] = PolarSample{(int)x0, (int)y0, (float)(u - x0), (float)(v - y0)};
+            continue;
+        }
+        k -= n_pol;
+        tab[3 * k] = k * n * n;
+        tab[3 * k + 1] = k * nt;
+        tab[3 * k + 2] = k;
+        cnt[k] = 0u;   // the counters keep whatever the last call left: clear them
     }
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(base + l.win, win.data(), sizeof(float) * win.size(), cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(base + l.tw_n, twn.data(), sizeof(float2) * twn.size(), cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(base + l.tw_p, twp.data(), sizeof(float2) * twp.size(), cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(base + l.tw_t, twt.data(), sizeof(float2) * twt.size(), cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(base + l.polar, pol.data(), sizeof(PolarSample) * pol.size(), cudaMemcpyHostToDevice,
-                             st)))
-        return e;
-    // copies from pageable host memory return once the source has been read, so the vectors
-    // may be released here
-    return cudaSuccess;
 }
 
 std::string check_cfg(const fmbym_size_cfg& c) {
@@ -199,33 +214,21 @@ int fmbym_pose_noalloc(void* stream, const fmbym_size_cfg* cfg, int n_pairs, con
         ds.ready = true;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (!ds.have_tables || !same_cfg(ds.tables_for, *cfg)) {
-        ds.have_tables = false;
-        if ((e = upload_tables(p, ds.base, l, st)) != cudaSuccess) return cuda_fail(e, "table upload");
-        ds.tables_for = *cfg;
-        ds.have_tables = true;
-    }
-    p.win = (const float*)(ds.base + l.win);
-    p.tw_n = (const float2*)(ds.base + l.tw_n);
-    p.tw_p = (const float2*)(ds.base + l.tw_p);
-    p.tw_t = (const float2*)(ds.base + l.tw_t);
-    p.polar = (const PolarSample*)(ds.base + l.polar);
-
-    // pair table: packed pairs, offset p N^2, c_theta offset p n_theta
-    std::vector<long long> tab(3 * (size_t)n_pairs);
-    for (int i = 0; i < n_pairs; ++i) {
-        tab[3 * i] = (long long)i * p.n * p.n;
-        tab[3 * i + 1] = (long long)i * p.nt;
-        tab[3 * i + 2] = i;
-    }
+    float* d_win = (float*)(ds.base + l.win);
+    float2* d_twn = (float2*)(ds.base + l.tw_n);
+    float2* d_twp = (float2*)(ds.base + l.tw_p);
+    float2* d_twt = (float2*)(ds.base + l.tw_t);
+    PolarSample* d_pol = (PolarSample*)(ds.base + l.polar);
     long long* d_tab = (long long*)(ds.base + l.tab);
     unsigned* d_cnt = (unsigned*)(ds.base + l.cnt);
-    if ((e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
-        return cuda_fail(e, "pair table copy");
-    // the counters keep whatever the last call left: clear them
-    if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * n_pairs, st)) != cudaSuccess)
-        return cuda_fail(e, "counter clear");
+    k_noalloc_tables<<<152, 256, 0, st>>>(p.n, p.p, p.nt, p.nr, n_pairs, d_win, d_twn, d_twp, d_twt, d_pol, d_tab,
+                                          d_cnt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "table launch");
+    p.win = d_win;
+    p.tw_n = d_twn;
+    p.tw_p = d_twp;
+    p.tw_t = d_twt;
+    p.polar = d_pol;
     Ws w = ws_carve(p, n_pairs, ds.base + l.work, false);
     w.tr = &g_tracer;
     w.cnt = d_cnt;
