@@ -363,13 +363,14 @@ def exhaustive_comparison(pairs=64, steps=3, warmup=1):
     return out
 
 
-def angle_count_comparison(pairs=64, steps=10, warmup=3):
+def angle_count_comparison(fma_peak, pairs=64, steps=10, warmup=3):
     """Alg. 1's own angle count n_theta = 733 (no FFT plan: the angle correlation and its adjoint
     as direct circular sums) beside n_theta = 400 (FFT route) on the same 256^2 pairs of the
     batch256 workload, n_r = 128: pairs/s of the forward and of the training step (CUDA events,
     L2 flushed before each timed call), and the device time of the angle stage from the library's
     tracer.  The direct sums are bound by FP32 multiply-adds: n_theta^2 n_r per pair forward,
-    twice that in the adjoint, against 152 SMs x 128 lanes x the SM clock."""
+    twice that in the adjoint, against fma_peak, the FP32 multiply-add rate measured on this GPU
+    in the same run (fmbym_fp32_fma_rate)."""
     import ctypes
     import torch
     from paper_2203_00459_gb300 import _lib, synth
@@ -410,7 +411,6 @@ def angle_count_comparison(pairs=64, steps=10, warmup=3):
             ms.append(a.elapsed_time(b))
         return sum(ms) / len(ms)
 
-    fma_peak = 152 * 128 * 2070e6   # FP32 multiply-adds per second at the maximum SM clock
     for nt in (400, 733):
         cfg = size_cfg(256, nt, 128)
         srch = PoseSearch([cfg], max_pairs=pairs, flags=_lib.FLAG_GRAPH)
@@ -437,7 +437,7 @@ def angle_count_comparison(pairs=64, steps=10, warmup=3):
         if nt != 400 and kern.get("angle") and kern.get("b_angle"):
             fmas = nt * nt * 128 * pairs
             row["direct_roofline"] = {
-                "bound": "alu", "unit": "TFMA/s", "peak": round(fma_peak / 1e12, 2),
+                "bound": "alu", "unit": "TFMA/s", "peak": round(fma_peak / 1e12, 2), "peak_source": "measured",
                 "achieved_fwd": round(fmas / (kern["angle"] * 1e-3) / 1e12, 2),
                 "achieved_adjoint": round(2 * fmas / (kern["b_angle"] * 1e-3) / 1e12, 2),
                 "frac_fwd": round(fmas / (kern["angle"] * 1e-3) / fma_peak, 4),
@@ -702,30 +702,21 @@ def main():
             e2e = {"value": B / dt, "unit": "scan-pairs/s", "h2d_bytes_per_step": 2 * f.nbytes,
                    "d2h_bytes_per_step": B * 12, "mode": "fwd", "api": "fmbym_pose_host"}
         else:
+            # the public host-buffer training call: H2D of f, g and gt, the training call, D2H of
+            # pose, loss, df and dg, all inside fmbym_pose_train_host (which synchronises)
             gth = torch.from_numpy(gt.astype(np.float32)).pin_memory()
-            pose_h = torch.empty((B, 3), pin_memory=True)
-            loss_h = torch.empty(1, pin_memory=True)
-            fe, ge, gte = torch.empty_like(fd), torch.empty_like(gd), torch.empty_like(gtd)
-
-            def e2e_step():
-                fe.copy_(fh, non_blocking=True)
-                ge.copy_(gh, non_blocking=True)
-                gte.copy_(gth, non_blocking=True)
-                run_step(search, fe, ge, gte, pose, dpose, loss, df, dg, B)
-                pose_h.copy_(pose, non_blocking=True)
-                loss_h.copy_(loss, non_blocking=True)
-                torch.cuda.current_stream().synchronize()
-
+            outs = (torch.empty((B, 3), pin_memory=True), torch.empty(1, pin_memory=True),
+                    torch.empty(fh.shape, pin_memory=True), torch.empty(gh.shape, pin_memory=True))
             for _ in range(2):
-                e2e_step()
+                search.pose_train_host(fh, gh, gth, kind=2, out=outs)
             reps = max(3, args.steps)
             t0 = time.perf_counter()
             for _ in range(reps):
-                e2e_step()
+                search.pose_train_host(fh, gh, gth, kind=2, out=outs)
             dt = (time.perf_counter() - t0) / reps
             e2e = {"value": B / dt, "unit": "scan-pairs/s", "h2d_bytes_per_step": 2 * f.nbytes + B * 12,
-                   "d2h_bytes_per_step": B * 12 + 4, "mode": "fwdbwd",
-                   "api": "fmbym_pose_train from pinned host buffers (H2D of f, g, gt; D2H of pose, loss)"}
+                   "d2h_bytes_per_step": B * 12 + 4 + 2 * f.nbytes, "mode": "fwdbwd",
+                   "api": "fmbym_pose_train_host (pinned host f, g, gt in; pose, loss, df, dg out)"}
 
     # ---- forward-only rate and the plain one-pair-per-call path ----
     extra = {}
@@ -774,9 +765,25 @@ def main():
             extra["batched_vs_plain_step"] = value / extra["plain_step_pairs_per_s"]
             one.close()
 
+    # ---- the FP32 ceiling, measured on this GPU in this run, and the path-level floor ----
+    from paper_2203_00459_gb300.search import fp32_fma_rate
+    fp32_peak = 2.0 * fp32_fma_rate()          # FLOP/s
+    if roof is not None:
+        roof["fp32_peak_tflops_measured"] = round(fp32_peak / 1e12, 2)
+        roof["fp32_frac"] = round(model[dom][1] * B / (roof["avg_launch_ms"] * 1e-3) / fp32_peak, 4)
+    step_flop = sum(model[k][1] for k in model if k in kernels) * B
+    io_bytes = (28 if args.mode == "fwdbwd" else 12) * n * n * B   # scans in, scores / gradients out
+    t_floor = max(io_bytes / (peaks["hbm_gbs"] * 1e9), step_flop / fp32_peak)
+    extra["step_floor"] = {
+        "io_bytes_per_step": io_bytes, "fft_flop_per_step": step_flop,
+        "fp32_peak_tflops_measured": round(fp32_peak / 1e12, 2), "hbm_gbs": peaks["hbm_gbs"],
+        "t_floor_ms": round(t_floor * 1e3, 5), "bound": "fp32" if step_flop / fp32_peak > io_bytes / (peaks["hbm_gbs"] * 1e9) else "hbm",
+        "frac": round(t_floor / (ms_step * 1e-3), 4),
+        "note": "T_floor = max(inputs+outputs / HBM, nominal 5 L log2 L FFT FLOPs of the step / measured FP32 peak)"}
+
     if rank == 0 and args.workload == WORKLOAD:
         extra["exhaustive_256"] = exhaustive_comparison()
-        extra["alg1_n_theta_733"] = angle_count_comparison()
+        extra["alg1_n_theta_733"] = angle_count_comparison(fp32_peak / 2.0)
         extra["radar_frontend"] = frontend_rate()
 
     cpu = None

@@ -213,6 +213,28 @@ int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_
                     const long long* offsets, long long total_elems, const float* f_host,
                     const float* g_host, float* pose_host);
 
+/* fmbym_pose_train with HOST buffers, for callers whose scans and gradients live in CPU memory:
+ * copies f, g (host float32, total_elems each, laid out by offsets as in fmbym_pose) and gt (host
+ * float32 [n_pairs][3]) into the handle's device staging area, runs the training call of
+ * fmbym_pose_train there, copies the pose (host float32 [n_pairs][3]), the loss (host float32 [1])
+ * and df, dg (host float32, total_elems each) back, and synchronises the stream.  Elements of df
+ * and dg outside every pair's scan are unspecified.  total_elems must not exceed what max_pairs
+ * scans of the largest configured size hold (FMBYM_ERR_WORKSPACE).  Pinned host memory makes the
+ * copies asynchronous with respect to the host; pageable memory works but copies slower.  Errors
+ * as fmbym_pose_train. */
+int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx,
+                          const long long* offsets, long long total_elems, const float* f_host,
+                          const float* g_host, const float* gt_host, int loss_kind, float* pose_host,
+                          float* loss_host, float* df_host, float* dg_host);
+
+/* Measures the FP32 multiply-add rate of the current device, the ALU ceiling of the search's FFT
+ * arithmetic: a kernel of independent fmaf chains (16 per thread, 4 CTAs of 256 threads per SM)
+ * is launched once to warm up and then timed `reps` times with CUDA events on the stream; the
+ * best rate is written to *fma_per_s (multiply-adds per second; FLOP/s is twice that).  iters is
+ * the chain length per thread (>= 1; 50000 runs about 3 ms on a GB300).  Synchronous.  Allocates
+ * nothing.  Returns FMBYM_ERR_INVALID_ARG for iters < 1, reps < 1 or a NULL output. */
+int fmbym_fp32_fma_rate(void* stream, int iters, int reps, double* fma_per_s);
+
 /* Launch tracing (the CUDA-event timing of Sec. IV-C, per kernel).  With on = 1 the handle records a
  * CUDA event on the launching stream before each kernel launch and after the last launch of each
  * call, so that every kernel's device time is the interval to the next event; on = 0 stops

@@ -49,6 +49,8 @@ SIGNATURES = {
     "fmbym_pose": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "fmbym_pose_backward": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "fmbym_pose_host": (_I, [_P, _P, _I, _P, _P, _LL, _P, _P, _P]),
+    "fmbym_pose_train_host": (_I, [_P, _P, _I, _P, _P, _LL, _P, _P, _P, _I, _P, _P, _P, _P]),
+    "fmbym_fp32_fma_rate": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "fmbym_pose_loss": (_I, [_P, _P, _I, _P, _P, _I, _P, _P]),
     "fmbym_pose_train": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
     "fmbym_pose_exhaustive": (_I, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P]),

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libfmbym.so")
-SOURCES = ["api.cu", "fwd.cu", "bwd.cu", "angle_direct.cu", "noalloc.cu", "exhaustive.cu", "unet_api.cu",
+SOURCES = ["api.cu", "fwd.cu", "bwd.cu", "angle_direct.cu", "noalloc.cu", "exhaustive.cu", "unet_api.cu", "peak.cu",
            "frontend.cu"]
 HEADERS = ["common.cuh", "fft.cuh", "dev_util.cuh", "unet_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -57,9 +57,12 @@ struct fmbym_handle {
     long long* d_tab = nullptr;   // [max_pairs][3]
     long long* h_tab = nullptr;   // pinned staging of the pair table
     cudaEvent_t tab_free = nullptr;
-    float* d_stage_f = nullptr;   // host-buffer entry point staging
+    float* d_stage_f = nullptr;   // host-buffer entry points' staging
     float* d_stage_g = nullptr;
     float* d_stage_pose = nullptr;
+    float* d_stage_df = nullptr;  // [stage_elems] each: the training call's gradients
+    float* d_stage_dg = nullptr;
+    float* d_stage_small = nullptr;  // [max_pairs][3] gt, [max_pairs][3] dpose, [1] loss
     unsigned* d_cnt = nullptr;    // [max_pairs] completion counters, zero between launches
     float* d_bpose = nullptr;     // [max_pairs][3] pose recomputed by the adjoint
     float4* d_best = nullptr;     // [max_pairs] running best of the exhaustive search
@@ -624,6 +627,9 @@ void fmbym_destroy(fmbym_handle* h) {
     cudaFree(h->d_stage_f);
     cudaFree(h->d_stage_g);
     cudaFree(h->d_stage_pose);
+    cudaFree(h->d_stage_df);
+    cudaFree(h->d_stage_dg);
+    cudaFree(h->d_stage_small);
     cudaFree(h->d_cnt);
     cudaFree(h->d_bpose);
     cudaFree(h->d_best);
@@ -706,6 +712,9 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
     if ((e = cudaMalloc(&h->d_stage_f, sizeof(float) * h->stage_elems)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_g, sizeof(float) * h->stage_elems)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_pose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_stage_df, sizeof(float) * h->stage_elems)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_stage_dg, sizeof(float) * h->stage_elems)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_stage_small, sizeof(float) * (6 * (size_t)cfg->max_pairs + 1))) != cudaSuccess ||
         (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_bpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
@@ -888,6 +897,55 @@ int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_
     if (rc != FMBYM_OK) return rc;
     if ((e = cudaMemcpyAsync(pose_host, h->d_stage_pose, sizeof(float) * 3 * n_pairs, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
+        return cuda_fail(h, e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return FMBYM_OK;
+}
+
+int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
+                          long long total_elems, const float* f_host, const float* g_host, const float* gt_host,
+                          int loss_kind, float* pose_host, float* loss_host, float* df_host, float* dg_host) {
+    if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    h->err.clear();
+    if (n_pairs == 0) return FMBYM_OK;
+    if (loss_kind != 1 && loss_kind != 2) return fail(h, FMBYM_ERR_INVALID_ARG, "loss_kind not 1/2");
+    if (!f_host || !g_host || !gt_host || !pose_host || !loss_host || !df_host || !dg_host)
+        return fail(h, FMBYM_ERR_INVALID_ARG, "NULL buffer");
+    if (total_elems < 0 || total_elems > h->stage_elems)
+        return fail(h, FMBYM_ERR_WORKSPACE, "total_elems exceeds the staging area");
+    std::vector<Group> groups;
+    long long need = 0;
+    int rc = make_table(h, n_pairs, size_idx, offsets, groups, &need);
+    if (rc != FMBYM_OK) return rc;
+    if (need > total_elems) return fail(h, FMBYM_ERR_INVALID_ARG, "offsets reach beyond total_elems");
+    cudaStream_t st = (cudaStream_t)stream;
+    float* d_gt = h->d_stage_small;
+    float* d_dpose = h->d_stage_small + 3 * (size_t)h->max_pairs;
+    float* d_loss = h->d_stage_small + 6 * (size_t)h->max_pairs;
+    const size_t bytes = sizeof(float) * (size_t)total_elems;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->d_stage_f, f_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->d_stage_g, g_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_gt, gt_host, sizeof(float) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(h, e, "host-to-device copy");
+    LaunchArgs a{};
+    a.kind = 2;
+    a.f = h->d_stage_f;
+    a.g = h->d_stage_g;
+    a.pose = h->d_stage_pose;
+    a.gt = d_gt;
+    a.loss_kind = loss_kind;
+    a.loss = d_loss;
+    a.dpose_out = d_dpose;
+    a.df = h->d_stage_df;
+    a.dg = h->d_stage_dg;
+    rc = run_call(h, st, n_pairs, groups, a);
+    if (rc != FMBYM_OK) return rc;
+    if ((e = cudaMemcpyAsync(pose_host, h->d_stage_pose, sizeof(float) * 3 * n_pairs, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(loss_host, d_loss, sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(df_host, h->d_stage_df, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dg_host, h->d_stage_dg, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(h, e, "device-to-host copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     return FMBYM_OK;

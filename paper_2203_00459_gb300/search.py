@@ -277,6 +277,47 @@ class PoseSearch:
         return pose
 
 
+    def pose_train_host(self, f_host, g_host, gt_host, kind=1, size_idx=None, offsets=None, stream=None, out=None):
+        """fmbym_pose_train from host (CPU float32, ideally pinned) tensors: copies f, g, gt in, runs
+        the training call, copies pose, loss, df and dg out, and synchronises the stream.  out:
+        optional preallocated host (pose [B, 3], loss [1], df like f, dg like g).  Returns
+        (pose, loss, df, dg) as CPU tensors."""
+        check_host_tensor(f_host, "f_host")
+        check_host_tensor(g_host, "g_host", numel=f_host.numel())
+        if size_idx is None:
+            n_pairs = f_host.shape[0]
+            si = off = None
+        else:
+            si = np.ascontiguousarray(np.asarray(size_idx, dtype=np.int32))
+            n_pairs = si.size
+            off = None if offsets is None else np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        check_host_tensor(gt_host, "gt_host", numel=3 * n_pairs)
+        pin = f_host.is_pinned()
+        if out is None:
+            out = (torch.empty((n_pairs, 3), dtype=torch.float32, pin_memory=pin),
+                   torch.empty(1, dtype=torch.float32, pin_memory=pin),
+                   torch.empty_like(f_host, pin_memory=pin), torch.empty_like(g_host, pin_memory=pin))
+        for t, nm, k in zip(out, ("pose", "loss", "df", "dg"), (3 * n_pairs, 1, f_host.numel(), g_host.numel())):
+            check_host_tensor(t, "out." + nm, numel=k)
+        pose, loss, df, dg = out
+        st = _lib.lib().fmbym_pose_train_host(self.handle, _stream(stream), n_pairs,
+                                              None if si is None else si.ctypes.data_as(ctypes.c_void_p),
+                                              None if off is None else off.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.c_longlong(f_host.numel()), _ptr(f_host), _ptr(g_host),
+                                              _ptr(gt_host), int(kind), _ptr(pose), _ptr(loss), _ptr(df), _ptr(dg))
+        _lib.check(st, self.handle)
+        return pose, loss, df, dg
+
+
+def fp32_fma_rate(iters=50000, reps=3, stream=None):
+    """The device's measured FP32 multiply-add rate (fmbym_fp32_fma_rate), in multiply-adds/s."""
+    v = ctypes.c_double()
+    st = _lib.lib().fmbym_fp32_fma_rate(_stream(stream), int(iters), int(reps), ctypes.byref(v))
+    if st != 0:
+        raise _lib.FmbymError(st, "fmbym_fp32_fma_rate")
+    return v.value
+
+
 class PoseFunction(torch.autograd.Function):
     """pose = ScanMatch(f, g) with the library's hand-written adjoint as backward."""
 

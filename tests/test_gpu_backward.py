@@ -236,3 +236,22 @@ def test_adjoint_rotate_target_g(lib):
     with pytest.raises(_lib.FmbymError):
         PoseSearch([lib.size_cfg(128, 128, 64, rotate_target=1, full_circle=1)], max_pairs=1)
     s.close()
+
+
+def test_host_buffer_training_call_equals_the_device_call(lib):
+    """fmbym_pose_train_host (host f, g, gt in; host pose, loss, df, dg out) against
+    fmbym_pose_train on device buffers of the same handle: bitwise equal, twice in a row."""
+    from paper_2203_00459_gb300.search import PoseSearch
+    f, g, gt = synth.make_batch("batch256", pairs=4, start=40)
+    s = PoseSearch([lib.size_cfg(256, 400, 128)], max_pairs=4)
+    F, G = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    GT = torch.from_numpy(gt.astype(np.float32)).cuda()
+    pose, loss, _, df, dg = s.pose_train(F, G, GT, kind=2)
+    torch.cuda.synchronize()
+    fh, gh = torch.from_numpy(f).pin_memory(), torch.from_numpy(g).pin_memory()
+    gth = torch.from_numpy(gt.astype(np.float32)).pin_memory()
+    for _ in range(2):
+        ph, lh, dfh, dgh = s.pose_train_host(fh, gh, gth, kind=2)
+        assert torch.equal(ph, pose.cpu()) and torch.equal(lh, loss.cpu())
+        assert torch.equal(dfh, df.cpu()) and torch.equal(dgh, dg.cpu())
+    s.close()
