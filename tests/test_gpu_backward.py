@@ -75,24 +75,34 @@ def test_adjoint_circular_padding(lib):
 
 def test_adjoint_matches_central_differences_512(lib):
     """The 512^2 configuration's check: the GPU gradient of an L2 pose loss against FP64 central
-    finite differences (h = 1e-4) of the oracle's forward search on 64 random pixels."""
+    finite differences (h = 1e-4) of the oracle's forward search on 64 random pixels, pixel by
+    pixel.  Where |FD| is at least 1e-3 of the image's largest gradient the GPU gradient must lie
+    within 1e-3 of FD relative to that pixel's own value (measured on a GB300: at most 1.4e-4);
+    below that floor the float32 sums' cancellation sets the error, and the bound is 1e-3 of the
+    largest gradient.  The oracle's own adjoint is held to 1e-4 of FD per pixel above the floor
+    (measured: at most 1e-6).  The FD loop evaluates the oracle with its FFT route, the same sums
+    as its direct route (pinned against each other), to keep 128 evaluations at 512^2 short."""
     spec = synth.WORKLOADS["batch512"]
     f, g, gt = synth.make_batch("batch512", pairs=1, start=5)
     cfg = lib.size_cfg(512, spec["n_theta"], spec["n_r"])
     oc = oracle_cfg(cfg)
+    ofd = dict(oc, route="fft")
     f64, g64 = f[0].astype(np.float64), g[0].astype(np.float64)
     r = O.pose(f64, g64, oc)
     pose = np.array([r["theta"], r["tx"], r["ty"]])
 
     def loss(a, b):
-        rr = O.pose(a, b, oc)
+        rr = O.pose(a, b, ofd)
         return float(np.sum((np.array([rr["theta"], rr["tx"], rr["ty"]]) - gt[0]) ** 2))
 
     dpose = 2.0 * (pose - gt[0])
     df, dg = gpu_backward(lib, cfg, f, g, dpose[None, :])
+    odf, odg, _ = O.pose_backward(f64, g64, oc, dpose)
     rng = np.random.default_rng(64)
     h = 1e-4
     scale = max(np.max(np.abs(df[0])), np.max(np.abs(dg[0])))
+    floor = 1e-3 * scale
+    above = 0
     for k in range(64):
         which = k % 2
         y, x = rng.integers(0, 512, 2)
@@ -103,7 +113,13 @@ def test_adjoint_matches_central_differences_512(lib):
         lm = loss(a, b)
         fd = (lp - lm) / (2 * h)
         an = (df if which == 0 else dg)[0, y, x]
+        ora = (odf if which == 0 else odg)[y, x]
         assert abs(fd - an) <= TOL_GRAD * scale, (k, which, y, x, fd, an, scale)
+        if abs(fd) >= floor:
+            above += 1
+            assert abs(fd - an) <= 1e-3 * abs(fd), (k, which, y, x, fd, an)
+            assert abs(fd - ora) <= 1e-4 * abs(fd), (k, which, y, x, fd, ora)
+    assert above >= 48, above   # the per-pixel bound must cover most of the sample
 
 
 def test_autograd_function_and_determinism(lib):

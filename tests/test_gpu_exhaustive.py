@@ -49,8 +49,15 @@ def test_exhaustive_rejects_bad_arguments(search):
     f = torch.zeros((1, 128, 128), device="cuda")
     with pytest.raises(_lib.FmbymError):
         s.pose_exhaustive(f, f, np.zeros(0, np.float32))
-    with pytest.raises(_lib.FmbymError):
+    with pytest.raises(ValueError):    # the binding refuses a size index the handle lacks
         s.pose_exhaustive(f, f, np.zeros(3, np.float32), size=1)
+    import ctypes
+    ang = np.zeros(3, np.float32)
+    pose = torch.empty((1, 3), device="cuda")
+    st = _lib.lib().fmbym_pose_exhaustive(s.handle, None, 1, 1, None, ctypes.c_void_p(f.data_ptr()),
+                                          ctypes.c_void_p(f.data_ptr()), 3, ang.ctypes.data_as(ctypes.c_void_p),
+                                          ctypes.c_void_p(pose.data_ptr()), None)
+    assert st == _lib.ERR_INVALID_ARG   # and so does the library
     f2 = torch.zeros((2, 128, 128), device="cuda")
     with pytest.raises(_lib.FmbymError):
         s.pose_exhaustive(f2, f2, np.zeros(3, np.float32))
