@@ -263,8 +263,8 @@ long long fmbym_launch_count(const fmbym_handle* h);
  *             return FMBYM_ERR_UNSUPPORTED_SIZE)
  *   n_pairs   pairs packed back to back: pair p at element offset p * N * N of f, g and c_xy
  *   f, g, pose, c_theta, c_xy  as in fmbym_pose (device, caller-owned; c_theta and c_xy may be NULL)
- * Limit: the whole footprint must fit the array (with the benchmark grids: one 512x512 pair, five
- * 256x256 pairs or 24 128x128 pairs); larger requests return FMBYM_ERR_WORKSPACE and the message
+ * Limit: the whole footprint must fit the array (with the benchmark grids: one 512x512 pair, six
+ * 256x256 pairs or 29 128x128 pairs); larger requests return FMBYM_ERR_WORKSPACE and the message
  * gives the bytes needed.  The first call on a device does a one-time set-up (it looks up the array's
  * device address and sets kernel attributes), so make that first call before any stream capture.
  * Every call shares the one array, which keeps the last call's contents.  Each call therefore

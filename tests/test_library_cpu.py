@@ -93,6 +93,19 @@ def test_noalloc_keeps_the_fft_angle_counts(L, n_theta, status):
     assert st == status and L.fmbym_noalloc_last_error().decode()
 
 
+@pytest.mark.parametrize("n,n_theta,n_r,most", [(512, 400, 256, 1), (256, 400, 128, 6), (128, 128, 64, 29)])
+def test_noalloc_limit_of_the_static_array(L, n, n_theta, n_r, most):
+    """The pair counts the header states for the 16 MiB array with the benchmark grids: one more
+    pair is FMBYM_ERR_WORKSPACE, decided on the host before any CUDA call (without a GPU the
+    request that fits stops later, at the first CUDA call)."""
+    from paper_2203_00459_gb300 import _lib
+    from paper_2203_00459_gb300.search import size_cfg
+    c = _lib.SizeCfg(**size_cfg(n, n_theta, n_r))
+    p = ctypes.c_void_p(16)
+    assert L.fmbym_pose_noalloc(None, ctypes.byref(c), most + 1, p, p, p, None, None) == _lib.ERR_WORKSPACE
+    assert L.fmbym_pose_noalloc(None, ctypes.byref(c), most, p, p, p, None, None) != _lib.ERR_WORKSPACE
+
+
 def test_polar_wrapper_rejects_host_tensors():
     torch = pytest.importorskip("torch")
     from paper_2203_00459_gb300.search import polar_to_cartesian
