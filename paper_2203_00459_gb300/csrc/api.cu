@@ -25,7 +25,8 @@ struct HostPlan {
 
 thread_local std::string g_create_error;
 
-bool supported_n(int n) { return n == 128 || n == 256 || n == 512; }
+// the power-of-two sides, and the paper's odd sides 127, 255, 511 (Sec. IV-B resolutions)
+bool supported_n(int n) { return n == 128 || n == 256 || n == 512 || n == 127 || n == 255 || n == 511; }
 // 128, 256 and 400 angles take the FFT route; any other count up to 1024 (Alg. 1's 733 among them)
 // the direct sums of angle_direct.cu
 bool supported_nt(int nt) { return nt >= 8 && nt <= 1024; }
@@ -82,14 +83,15 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
         off += (bytes + 255) & ~size_t(255);
         return r;
     };
-    const size_t n = p.n, P = p.p, Wn = n / 2, Wp = P / 2, b = (size_t)B;
+    // Wn: the packed row spectra's width (N/2 for even N, (N + 1)/2 for odd N); ne: stage 2's frame
+    const size_t n = p.n, P = p.p, Wn = (n + 1) / 2, Wp = P / 2, b = (size_t)B, ne = frame_n(p.n);
     Ws t{};
     t.s1 = (float2*)take(2 * b * n * Wn * sizeof(float2));
-    t.mt = (float*)take(2 * b * (Wn + 1) * n * sizeof(float));
+    t.mt = (float*)take(2 * b * (n / 2 + 1) * n * sizeof(float));
     t.sp = (float2*)take(b * angle_chunks_max(p) * p.nt * sizeof(float2));
     t.th = (float*)take(b * 8 * sizeof(float));
-    t.s2 = (float2*)take(2 * b * n * Wp * sizeof(float2));
-    t.s3 = (float2*)take(b * n * Wp * sizeof(float2));
+    t.s2 = (float2*)take(2 * b * ne * Wp * sizeof(float2));
+    t.s3 = (float2*)take(b * ne * Wp * sizeof(float2));
     t.cxy = (float*)take(b * n * n * sizeof(float));
     t.st = (float*)take(b * c2r_blocks(p) * 4 * sizeof(float));
     t.sx = (float*)take(b * kSplitXY * 8 * sizeof(float));
@@ -99,16 +101,16 @@ static size_t carve(const DevPlan& p, int B, char* base, Ws* w, bool backward) {
     t.ct = (float*)take(b * p.nt * sizeof(float));
     if (backward) {
         t.ahat = (float2*)take(b * p.nt * p.nr * sizeof(float2));
-        t.phs = (float2*)take(2 * b * (Wn + 1) * n * sizeof(float2));
+        t.phs = (float2*)take(2 * b * (n / 2 + 1) * n * sizeof(float2));
         t.s2hat = (float2*)take(2 * b * P * Wp * sizeof(float2));
         t.bsc = (float*)take(b * 16 * sizeof(float));
-        t.gpart = (float*)take(b * (n * n / 256) * sizeof(float));
-        t.b1 = (float2*)take(b * n * Wp * sizeof(float2));
-        t.b2 = (float2*)take(2 * b * n * Wp * sizeof(float2));
+        t.gpart = (float*)take(b * (ne * ne / 256) * sizeof(float));
+        t.b1 = (float2*)take(b * ne * Wp * sizeof(float2));
+        t.b2 = (float2*)take(2 * b * ne * Wp * sizeof(float2));
         t.gfr = (float*)take(b * n * n * sizeof(float));
         t.bdc = (float2*)take(b * p.nt * sizeof(float2));
         t.gpol = (float2*)take(b * p.nt * p.nr * sizeof(float2));
-        t.gmt = (float2*)take(b * (Wn + 1) * n * sizeof(float2));
+        t.gmt = (float2*)take(b * (n / 2 + 1) * n * sizeof(float2));
         t.gs1 = (float2*)take(2 * b * n * Wn * sizeof(float2));
     }
     if (w) *w = t;
@@ -147,7 +149,7 @@ int cuda_fail(fmbym_handle* h, cudaError_t e, const char* what) {
 std::string validate(const fmbym_size_cfg& c) {
     char buf[256];
     if (!supported_n(c.n)) {
-        snprintf(buf, sizeof buf, "n=%d not supported (128, 256, 512)", c.n);
+        snprintf(buf, sizeof buf, "n=%d not supported (127, 128, 255, 256, 511, 512)", c.n);
         return buf;
     }
     if (!supported_nt(c.n_theta)) {
@@ -159,6 +161,7 @@ std::string validate(const fmbym_size_cfg& c) {
         return "temperatures and delta_xy must be positive";
     if (c.window != 0 && c.window != 1) return "window must be 0 or 1";
     if (c.pad_mode != 0 && c.pad_mode != 1) return "pad_mode must be 0 or 1";
+    if (c.pad_mode == 1 && (c.n & 1)) return "pad_mode 1 (N-periodic) needs an even n";
     if (c.score_norm != 0 && c.score_norm != 1) return "score_norm must be 0 or 1";
     if (c.angle_score != 0 && c.angle_score != 1) return "angle_score must be 0 or 1";
     if (c.full_circle != 0 && c.full_circle != 1) return "full_circle must be 0 or 1";
@@ -173,7 +176,10 @@ cudaError_t build_plan(HostPlan& hp) {
     const fmbym_size_cfg& c = hp.cfg;
     DevPlan& d = hp.dev;
     d.n = c.n;
-    d.p = c.pad_mode == 1 ? c.n : 3 * c.n / 2;  // zero pad to 1.5 N: lags |s| <= N/2 never alias
+    // zero pad to 1.5 N (1.5 (N + 1) for odd N): lags |s| <= N/2 never alias
+    d.p = c.pad_mode == 1 ? c.n : 3 * frame_n(c.n) / 2;
+    d.m = (c.n & 1) ? 2 * (c.n + 1) : 0;
+    d.tw_m = d.chirp = d.bh = nullptr;
     d.col_tile = tpb_for(d.p) / fft_threads(d.p);
     d.angle_rc = kAngleRadii;
     d.rot_px = kRotPixels;
@@ -207,6 +213,44 @@ cudaError_t build_plan(HostPlan& hp) {
         return t;
     };
     std::vector<float2> twn = twiddles(d.n), twp = twiddles(d.p), twt = twiddles(d.nt);
+    // Bluestein tables of an odd N: N k = (n^2 + k^2 - (k - n)^2) / 2 turns the N-point DFT into
+    // X[k] = conj(w[k]) sum_n (x[n] conj(w[n])) w[k - n] with w[n] = exp(i pi n^2 / N), a linear
+    // convolution of length 2N - 1 <= M done by M-point FFTs: bh = FFT_M(b) / M of the circular
+    // filter b[m] = w[m], b[M - m] = w[m] (0 < m < N).  n^2 is reduced modulo 2N in integers, and
+    // bh is a direct DFT sum in double precision.
+    std::vector<float2> twm, chirp, bh;
+    if (d.m) {
+        twm = twiddles(d.m);
+        const int N = d.n, M = d.m;
+        std::vector<double> wr(N), wi(N);
+        for (int k = 0; k < N; ++k) {
+            const long long e = ((long long)k * k) % (2LL * N);
+            wr[k] = std::cos(kPi * (double)e / N);
+            wi[k] = std::sin(kPi * (double)e / N);
+        }
+        chirp.resize(N);
+        for (int k = 0; k < N; ++k) chirp[k] = make_float2((float)wr[k], (float)wi[k]);
+        std::vector<double> br(M, 0.0), bi(M, 0.0);
+        for (int k = 0; k < N; ++k) {
+            br[k] = wr[k];
+            bi[k] = wi[k];
+            if (k > 0) {
+                br[M - k] = wr[k];
+                bi[M - k] = wi[k];
+            }
+        }
+        bh.resize(M);
+        for (int k = 0; k < M; ++k) {
+            double sr = 0.0, si = 0.0;
+            for (int j = 0; j < M; ++j) {
+                const long long e = ((long long)j * k) % M;
+                const double a = -2.0 * kPi * (double)e / M, ca = std::cos(a), sa = std::sin(a);
+                sr += br[j] * ca - bi[j] * sa;
+                si += br[j] * sa + bi[j] * ca;
+            }
+            bh[k] = make_float2((float)(sr / M), (float)(si / M));
+        }
+    }
     std::vector<PolarSample> pol((size_t)d.nt * d.nr);
     for (int a = 0; a < d.nt; ++a) {
         const double alpha = (double)a * kPi / d.nt;
@@ -231,9 +275,9 @@ cudaError_t build_plan(HostPlan& hp) {
             const float wy[2] = {1.f - ps.fy, ps.fy}, wx[2] = {1.f - ps.fx, ps.fx};
             for (int dy = 0; dy < 2; ++dy)
                 for (int dx = 0; dx < 2; ++dx) {
-                    int vi = (ps.y0 + dy) & (d.n - 1), ui = (ps.x0 + dx) & (d.n - 1);
+                    int vi = ((ps.y0 + dy) % d.n + d.n) % d.n, ui = ((ps.x0 + dx) % d.n + d.n) % d.n;
                     if (ui > d.n / 2) {
-                        vi = (d.n - vi) & (d.n - 1);
+                        vi = (d.n - vi) % d.n;
                         ui = d.n - ui;
                     }
                     taps.push_back(Tap{ui * d.n + vi, (int)sidx, wy[dy] * wx[dx]});
@@ -258,9 +302,11 @@ cudaError_t build_plan(HostPlan& hp) {
     const size_t b_win = al(win.size() * 4), b_twn = al(twn.size() * 8), b_twp = al(twp.size() * 8),
                  b_twt = al(twt.size() * 8), b_pol = al(pol.size() * sizeof(PolarSample)),
                  b_ptr = al(cnt.size() * 4), b_col = al(col.size() * 4), b_wt = al(wt.size() * 4),
-                 b_hv = al(heavy.size() * 4);
+                 b_hv = al(heavy.size() * 4), b_twm = al(twm.size() * 8), b_chirp = al(chirp.size() * 8),
+                 b_bh = al(bh.size() * 8);
     char* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, b_win + b_twn + b_twp + b_twt + b_pol + b_ptr + b_col + b_wt + b_hv);
+    cudaError_t e = cudaMalloc(&base, b_win + b_twn + b_twp + b_twt + b_pol + b_ptr + b_col + b_wt + b_hv + b_twm +
+                                          b_chirp + b_bh);
     if (e != cudaSuccess) return e;
     hp.tables = base;
     char* cur = base;
@@ -281,6 +327,16 @@ cudaError_t build_plan(HostPlan& hp) {
     auto r9 = put(heavy.data(), heavy.size() * 4, b_hv);
     for (auto& r : {r1, r2, r3, r4, r5, r6, r7, r8, r9})
         if (r.second != cudaSuccess) return r.second;
+    if (d.m) {
+        auto r10 = put(twm.data(), twm.size() * 8, b_twm);
+        auto r11 = put(chirp.data(), chirp.size() * 8, b_chirp);
+        auto r12 = put(bh.data(), bh.size() * 8, b_bh);
+        for (auto& r : {r10, r11, r12})
+            if (r.second != cudaSuccess) return r.second;
+        d.tw_m = (const float2*)r10.first;
+        d.chirp = (const float2*)r11.first;
+        d.bh = (const float2*)r12.first;
+    }
     d.heavy = (const int*)r9.first;
     d.csr_ptr = (const int*)r6.first;
     d.csr_col = (const int*)r7.first;
@@ -649,7 +705,8 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
     for (int i = 0; i < cfg->n_sizes; ++i) {
         const std::string v = validate(cfg->sizes[i]);
         if (!v.empty()) {
-            const bool size = !supported_n(cfg->sizes[i].n) || !supported_nt(cfg->sizes[i].n_theta);
+            const bool size = !supported_n(cfg->sizes[i].n) || !supported_nt(cfg->sizes[i].n_theta) ||
+                              (cfg->sizes[i].pad_mode == 1 && (cfg->sizes[i].n & 1));
             return fail(nullptr, size ? FMBYM_ERR_UNSUPPORTED_SIZE : FMBYM_ERR_INVALID_ARG,
                         "size " + std::to_string(i) + ": " + v);
         }

@@ -70,7 +70,9 @@ __device__ __forceinline__ float dcxy(const DevPlan& p, const float* r, float cv
 // Lag rows of D (row i holds s_y = i - N/2; column j sits at P-position (j - N/2) mod P), two
 // rows per complex FFT of length P, packed real-FFT output rows [N][P/2].  The first pass forms
 // d c_xy straight from global memory.
-template <int N, int P>
+// ODD: the scan side is N - 1 inside the frame N; c_xy is [N - 1][N - 1] at frame lags 1 .. N - 1, and
+// D is zero at frame lag index 0 (lag -N/2, not a candidate of an odd side).
+template <int N, int P, bool ODD>
 __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long* __restrict__ tab,
                                                      const float* __restrict__ cxy, const float* __restrict__ xm,
                                                      const float* __restrict__ fwd_pose,
@@ -94,15 +96,17 @@ __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long*
         tx = c;
         ty = d;
     }
-    if (threadIdx.x == 0) xy_adjoint_scalars(p, xm + (size_t)q * 8, tx, ty, dtx, dty, N, r);
+    constexpr int NI = ODD ? N - 1 : N, LO = ODD ? 1 : 0;
+    if (threadIdx.x == 0) xy_adjoint_scalars(p, xm + (size_t)q * 8, tx, ty, dtx, dty, NI, r);
     __syncthreads();
-    const float* c = cxy + (size_t)q * N * N + (size_t)i * N;
+    const float* c = cxy + (size_t)q * NI * NI + (size_t)(i - LO) * NI - LO;
+    const bool oka = i >= LO;
     first_pass_global<P>(sm + k * SL, 1, jt, [&](int x) {
         const int j = x + N / 2 < P ? x + N / 2 : x + N / 2 - P;   // lag column at P-position x
         float2 v = make_float2(0.f, 0.f);
-        if (j < N) {
-            v.x = dcxy(p, r, __ldg(c + j), i, j, N, dtx, dty);
-            v.y = dcxy(p, r, __ldg(c + N + j), i + 1, j, N, dtx, dty);
+        if (j < N && j >= LO) {
+            if (oka) v.x = dcxy(p, r, __ldg(c + j), i, j, N, dtx, dty);
+            v.y = dcxy(p, r, __ldg(c + NI + j), i + 1, j, N, dtx, dty);
         }
         return v;
     });
@@ -250,12 +254,15 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
 // z = 0 -> d f' (workspace), z = 1 -> d g (stage-2 part, written to the caller's buffer); under
 // rotate_target 1, z = 0 -> d f (caller) and z = 1 -> d g' (workspace).  The
 // first pass builds its inputs from global memory and the last pass stores straight to it.
-template <int N, int P>
+// ODD: the scan side is N - 1 inside the frame N: rows and columns below N - 1 are kept, with stride
+// N - 1 (the frame's last row and column belong to no pixel).
+template <int N, int P, bool ODD>
 __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* __restrict__ tab,
                                                     const float2* __restrict__ b2, float* __restrict__ gfr,
                                                     float* __restrict__ df, float* __restrict__ dg, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
+    constexpr int NI = ODD ? N - 1 : N;
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, i0 = blockIdx.x * FPC * 2;
     const int k = threadIdx.x / T, j = threadIdx.x % T, y = i0 + 2 * k;
@@ -265,11 +272,12 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
     const float scale = 1.f / ((float)P * (float)P);
     // the rotated operand's gradient goes to the workspace for the Rotate adjoint, the other one
     // straight to the caller (f' and g by default; f and g' under rotate_target 1)
-    float* out = (s == p.rotate_target ? gfr + (size_t)q * N * N : (s == 0 ? df : dg) + tab[3 * q]) + (size_t)y * N;
+    float* out = (s == p.rotate_target ? gfr + (size_t)q * NI * NI : (s == 0 ? df : dg) + tab[3 * q]) + (size_t)y * NI;
+    const bool okb = !ODD || y + 1 < NI;
     rest_global<P, +1>(sm + k * SL, 1, j, p.tw_p, [&](int x, float2 z) {
-        if (x < N) {
+        if (x < NI) {
             out[x] = z.x * scale;
-            out[N + x] = z.y * scale;
+            if (okb) out[NI + x] = z.y * scale;
         }
     });
 }
@@ -292,7 +300,9 @@ __global__ void __launch_bounds__(kThreads) k_b_c2r(DevPlan p, const long long* 
 // Under rotate_target 1 the rotated scan is g, turned by -theta: f and df here are g and dg, the
 // sine changes sign, d theta takes the rotation term with the opposite sign, and the translation
 // t = R(theta) t' adds dt . (dR/dtheta) t' = t_x dt_y - t_y dt_x (fwd_pose holds t).
-template <int N, int PX>
+// ODD: the scan side is N - 1 inside the frame N: the pixels of the frame's last row and column are
+// skipped, strides and bounds are N - 1 and the centre (N - 1)/2.
+template <int N, int PX, bool ODD>
 __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* __restrict__ tab,
                                                     const float* __restrict__ f, const float* __restrict__ th,
                                                     const float* __restrict__ gfr, const float* __restrict__ dpose,
@@ -302,19 +312,21 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     __shared__ float red[32];
     __shared__ bool last;
-    constexpr int NB = N * N / (kThreads * PX);
+    constexpr int NB = N * N / (kThreads * PX), NI = ODD ? N - 1 : N;
     const int q = blockIdx.y;
     const float* t = th + 8 * q;
     const float sg = p.rotate_target ? -1.f : 1.f;
     const float ct = t[1] + t[2], stn = sg * (t[3] + t[4]);
-    const float c = 0.5f * N;
+    const float c = 0.5f * NI;
     const float* src = f + tab[3 * q];
-    const float* d = gfr + (size_t)q * N * N;
+    const float* d = gfr + (size_t)q * NI * NI;
     float contrib = 0.f;
 #pragma unroll
     for (int m = 0; m < PX; ++m) {
-        const int idx = (blockIdx.x * PX + m) * kThreads + threadIdx.x;
-        const int Y = idx / N, X = idx % N;
+        const int fidx = (blockIdx.x * PX + m) * kThreads + threadIdx.x;
+        const int Y = fidx / N, X = fidx % N;
+        if (ODD && (X >= NI || Y >= NI)) continue;
+        const int idx = Y * NI + X;
         const float dX = (float)X - c, dY = (float)Y - c;
         // (a) d theta at output pixel X, sampled at c + R(-theta)(X - c)
         {
@@ -323,8 +335,8 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
             const int x0 = (int)fx0, y0 = (int)fy0;
             const float fx = px - fx0, fy = py - fy0;
             auto at = [&](int yy, int xx) {
-                return ((unsigned)yy < (unsigned)N && (unsigned)xx < (unsigned)N) ? __ldg(src + (size_t)yy * N + xx)
-                                                                                  : 0.f;
+                return ((unsigned)yy < (unsigned)NI && (unsigned)xx < (unsigned)NI) ? __ldg(src + (size_t)yy * NI + xx)
+                                                                                    : 0.f;
             };
             const float v00 = at(y0, x0), v01 = at(y0, x0 + 1), v10 = at(y0 + 1, x0), v11 = at(y0 + 1, x0 + 1);
             const float dvx = (1.f - fy) * (v01 - v00) + fy * (v11 - v10);
@@ -348,8 +360,8 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
                 for (int ox = 0; ox < 3; ++ox) {
                     const int mx = mx0 + ox;
                     const float wx = 1.f - fabsf(fmaf(ct, (float)ox, dxr)), wy = 1.f - fabsf(fmaf(-stn, (float)ox, dyr));
-                    if (wx > 0.f && wy > 0.f && (unsigned)my < (unsigned)N && (unsigned)mx < (unsigned)N)
-                        acc = fmaf(wy * wx, __ldg(d + (size_t)my * N + mx), acc);
+                    if (wx > 0.f && wy > 0.f && (unsigned)my < (unsigned)NI && (unsigned)mx < (unsigned)NI)
+                        acc = fmaf(wy * wx, __ldg(d + (size_t)my * NI + mx), acc);
                 }
             }
             df[tab[3 * q] + idx] = acc;
@@ -592,6 +604,73 @@ __global__ void __launch_bounds__(kThreads) k_b_s1rows(DevPlan p, const long lon
     });
 }
 
+// The same two steps for an odd side, whose N-point inverse DFTs run as Bluestein convolutions:
+// the inverse DFT is conj(DFT(conj x)).  The half plane of an odd N has no Nyquist column; the
+// interior columns u in [1, (N - 1)/2] are halved and the DC column is not.
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads) k_b_s1cols_odd(DevPlan p, const float2* __restrict__ phs,
+                                                           const float2* __restrict__ gmt, float2* __restrict__ gs1,
+                                                           int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    constexpr int T = FftPlan<M>::T, C = kThreads / T, ES = C, W = (N + 1) / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
+    const int c = threadIdx.x % C, j = threadIdx.x / C, u = u0 + c;
+    const float* dm = reinterpret_cast<const float*>(gmt + (size_t)q * W * N) + s;   // stride 2
+    const float2* ph = phs + (size_t)(s * B + q) * W * N;
+    bluestein<M>(sm + c, ES, j, N, p, [&](int v) {
+        if (u >= W) return make_float2(0.f, 0.f);
+        const float sc = u == 0 ? 1.f : 0.5f;
+        return c_conj(c_scale(__ldg(ph + (size_t)u * N + v), sc * __ldg(dm + 2 * ((size_t)u * N + v))));
+    });
+    float2* out = gs1 + (size_t)(s * B + q) * N * W + u0;
+    for (int idx = threadIdx.x; idx < C * N; idx += kThreads) {
+        const int cc = idx % C, y = idx / C;
+        if (u0 + cc < W) out[(size_t)y * W + cc] = c_conj(c_cjmul(__ldg(&p.chirp[y]), sm[spad(y) * ES + cc]));
+    }
+}
+
+// Row part for an odd side: rows y and y + 1 of the column-transformed half plane H, extended
+// Hermitian (G[0] = Re H[0], G[u] = H[u], G[N - u] = conj H[u]) and packed as G_y + i G_{y+1}; the
+// inverse N-point DFT gives row y in the real part and row y + 1 in the imaginary part.
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads) k_b_s1rows_odd(DevPlan p, const long long* __restrict__ tab,
+                                                           const float2* __restrict__ gs1, float* __restrict__ df,
+                                                           float* __restrict__ dg, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    constexpr int T = FftPlan<M>::T, FPC = kThreads / T, SL = spad(M), W = (N + 1) / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
+    const int k = threadIdx.x / T, j = threadIdx.x % T, y = r0 + 2 * k;
+    const bool oka = y < N, okb = y + 1 < N;
+    const float2* ra = gs1 + ((size_t)(s * B + q) * N + y) * W;
+    const float2* rb = ra + W;
+    bluestein<M>(sm + k * SL, 1, j, N, p, [&](int x) {
+        float2 a = make_float2(0.f, 0.f), b = a;
+        const int u = x <= N / 2 ? x : N - x;
+        if (oka) a = __ldg(ra + u);
+        if (okb) b = __ldg(rb + u);
+        float2 z;
+        if (x == 0) z = make_float2(a.x, b.x);
+        else if (x <= N / 2) z = make_float2(a.x - b.y, a.y + b.x);
+        else z = make_float2(a.x + b.y, b.x - a.y);
+        return c_conj(z);
+    });
+    float* out = (s ? dg : df) + tab[3 * q] + (size_t)y * N;
+    const float wa = p.window && oka ? __ldg(&p.win[y]) : 1.f, wb = p.window && okb ? __ldg(&p.win[y + 1]) : 1.f;
+    for (int x = j; x < N; x += T) {
+        const float2 z = c_conj(c_cjmul(__ldg(&p.chirp[x]), sm[k * SL + spad(x)]));
+        float va = z.x, vb = z.y;
+        if (p.window) {
+            const float wx = __ldg(&p.win[x]);
+            va *= wa * wx;
+            vb *= wb * wx;
+        }
+        if (oka) out[x] += va;
+        if (okb) out[N + x] += vb;
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // pose loss (Eq. 13) and its gradient
 // ---------------------------------------------------------------------------------------------
@@ -654,49 +733,55 @@ static void launch_stage1_adjoint(const DevPlan& p, const Ws& w, int B, cudaStre
             p, w.ahat, w.bdc, w.gpol, B);
 }
 
-template <int N, int PX>
+template <int N, int PX, bool ODD>
 static void launch_b_rot(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                          const float* dpose, float* df, cudaStream_t st, const float* fwd_pose) {
-    launch_pdl(k_b_rot<N, PX>, dim3(N * N / (kThreads * PX), B), kThreads, 0, st, p, tab, f, w.th, w.gfr, dpose, df, w.gpart,
-                                                                          w.cnt, w.bsc, fwd_pose);
+    launch_pdl(k_b_rot<N, PX, ODD>, dim3(N * N / (kThreads * PX), B), kThreads, 0, st, p, tab, f, w.th, w.gfr, dpose, df,
+               w.gpart, w.cnt, w.bsc, fwd_pose);
 }
 
-template <int N, int P>
+// N: the scan side; NE: stage 2's frame (N, or N + 1 for odd N); M: Bluestein length (0: none).
+template <int N, int NE, int M, int P>
 static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                             const float* g, const float* dpose, float* df, float* dg, cudaStream_t st,
                             const float* fwd_pose) {
+    constexpr bool ODD = (N & 1) != 0;
     StageRange range("fmbym adjoint");
     if (!fwd_pose) {
         cudaError_t e = launch_forward(p, w, B, tab, f, g, w.bpose, nullptr, nullptr, st);
         if (e != cudaSuccess) return e;
         fwd_pose = w.bpose;
     }
-    constexpr int T1 = FftPlan<N>::T, T2 = FftPlan<P>::T, TB2 = tpb_for(P);
+    constexpr int T2 = FftPlan<P>::T, TB2 = tpb_for(P);
     w.tr->before(K_B_ROWS, st);
-    launch_pdl(k_b_rows<N, P>, dim3((N / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st, p, tab, w.cxy, w.xm, fwd_pose,
-                                                                                   dpose, w.b1, B);
+    launch_pdl(k_b_rows<NE, P, ODD>, dim3((NE / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st, p, tab, w.cxy, w.xm,
+               fwd_pose, dpose, w.b1, B);
     w.tr->before(K_B_COLS, st);
     constexpr int C0 = TB2 / T2;   // the default tile; the 3 * 2^k lengths also have half and double
     if constexpr (P % 3 == 0) {
         if (p.col_tile == C0 / 2)
-            launch_pdl(k_b_cols<N, P, C0 / 2>, dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, b_smem_cols<P, C0 / 2>(), st, 
-                p, w.b1, w.s2hat, w.b2, B);
+            launch_pdl(k_b_cols<NE, P, C0 / 2>, dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, b_smem_cols<P, C0 / 2>(), st,
+                       p, w.b1, w.s2hat, w.b2, B);
         else if (p.col_tile == 2 * C0)
-            launch_pdl(k_b_cols<N, P, 2 * C0>, dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, b_smem_cols<P, 2 * C0>(), st, 
-                p, w.b1, w.s2hat, w.b2, B);
+            launch_pdl(k_b_cols<NE, P, 2 * C0>, dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, b_smem_cols<P, 2 * C0>(), st,
+                       p, w.b1, w.s2hat, w.b2, B);
         else
-            launch_pdl(k_b_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2, B);
+            launch_pdl(k_b_cols<NE, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2,
+                       B);
     } else {
-        launch_pdl(k_b_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2, B);
+        launch_pdl(k_b_cols<NE, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2, B);
     }
     w.tr->before(K_B_C2R, st);
-    launch_pdl(k_b_c2r<N, P>, dim3((N / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st, p, tab, w.b2, w.gfr, df, dg, B);
+    launch_pdl(k_b_c2r<NE, P, ODD>, dim3((NE / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st, p, tab, w.b2, w.gfr, df,
+               dg, B);
     w.tr->before(K_B_ROT, st);
+    const float* rsrc = p.rotate_target ? g : f;
+    float* rdst = p.rotate_target ? dg : df;
     switch (p.rot_px) {
-        case 1: launch_b_rot<N, 1>(p, w, B, tab, p.rotate_target ? g : f, dpose, p.rotate_target ? dg : df, st, fwd_pose); break;
-        case 2: launch_b_rot<N, 2>(p, w, B, tab, p.rotate_target ? g : f, dpose, p.rotate_target ? dg : df, st, fwd_pose); break;
-        case 8: launch_b_rot<N, 8>(p, w, B, tab, p.rotate_target ? g : f, dpose, p.rotate_target ? dg : df, st, fwd_pose); break;
-        default: launch_b_rot<N, 4>(p, w, B, tab, p.rotate_target ? g : f, dpose, p.rotate_target ? dg : df, st, fwd_pose); break;
+        case 1: launch_b_rot<NE, 1, ODD>(p, w, B, tab, rsrc, dpose, rdst, st, fwd_pose); break;
+        case 2: launch_b_rot<NE, 2, ODD>(p, w, B, tab, rsrc, dpose, rdst, st, fwd_pose); break;
+        case 8: launch_b_rot<NE, 8, ODD>(p, w, B, tab, rsrc, dpose, rdst, st, fwd_pose); break;
+        default: launch_b_rot<NE, 4, ODD>(p, w, B, tab, rsrc, dpose, rdst, st, fwd_pose); break;
     }
     if (p.nt == 128) launch_stage1_adjoint<128>(p, w, B, st);
     else if (p.nt == 256) launch_stage1_adjoint<256>(p, w, B, st);
@@ -706,12 +791,23 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     const int E = (N / 2 + 1) * N, lb = (E + kThreads - 1) / kThreads;
     const int hb = (p.n_heavy + kThreads / 32 - 1) / (kThreads / 32);
     launch_pdl(k_b_polT, dim3(lb + hb, B), kThreads, 0, st, p, w.gpol, w.gmt, B, lb);
-    w.tr->before(K_B_S1COLS, st);
-    launch_pdl(k_b_s1cols<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st, p, w.phs, w.gmt,
-                                                                                                 w.gs1, B);
-    w.tr->before(K_B_S1ROWS, st);
-    launch_pdl(k_b_s1rows<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_rows<N>(), st, p, tab, w.gs1, df, dg,
-                                                                                               B);
+    if constexpr (M == 0) {
+        constexpr int T1 = FftPlan<N>::T;
+        w.tr->before(K_B_S1COLS, st);
+        launch_pdl(k_b_s1cols<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_s1cols<N>(), st, p, w.phs,
+                   w.gmt, w.gs1, B);
+        w.tr->before(K_B_S1ROWS, st);
+        launch_pdl(k_b_s1rows<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, b_smem_rows<N>(), st, p, tab, w.gs1,
+                   df, dg, B);
+    } else {
+        constexpr int TM = FftPlan<M>::T, W = (N + 1) / 2;
+        w.tr->before(K_B_S1COLS, st);
+        launch_pdl(k_b_s1cols_odd<N, M>, dim3(W / (kThreads / TM), B, 2), kThreads, b_smem_s1cols<M>(), st, p, w.phs,
+                   w.gmt, w.gs1, B);
+        w.tr->before(K_B_S1ROWS, st);
+        launch_pdl(k_b_s1rows_odd<N, M>, dim3(W / (kThreads / TM), B, 2), kThreads, b_smem_rows<M>(), st, p, tab, w.gs1,
+                   df, dg, B);
+    }
     w.tr->close(st);
     return cudaGetLastError();
 }
@@ -720,12 +816,17 @@ cudaError_t launch_backward(const DevPlan& p, const Ws& w, int B, const long lon
                             const float* g, const float* dpose, float* df, float* dg, cudaStream_t st,
                             const float* fwd_pose) {
     if (B <= 0) return cudaSuccess;
-    if (p.n == 128) return p.p == 192 ? launch_b<128, 192>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
-                                      : launch_b<128, 128>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
-    if (p.n == 256) return p.p == 384 ? launch_b<256, 384>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
-                                      : launch_b<256, 256>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
-    return p.p == 768 ? launch_b<512, 768>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
-                      : launch_b<512, 512>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+    switch (p.n) {
+        case 127: return launch_b<127, 128, 256, 192>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+        case 255: return launch_b<255, 256, 512, 384>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+        case 511: return launch_b<511, 512, 1024, 768>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+        case 128: return p.p == 192 ? launch_b<128, 128, 0, 192>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
+                                    : launch_b<128, 128, 0, 128>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+        case 256: return p.p == 384 ? launch_b<256, 256, 0, 384>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
+                                    : launch_b<256, 256, 0, 256>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+        default: return p.p == 768 ? launch_b<512, 512, 0, 768>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose)
+                                   : launch_b<512, 512, 0, 512>(p, w, B, tab, f, g, dpose, df, dg, st, fwd_pose);
+    }
 }
 
 template <typename K>
@@ -733,29 +834,38 @@ static cudaError_t allow(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int N, int P>
+template <int N, int P, bool ODD>
 static cudaError_t prepare_b() {
     cudaError_t e;
-    if ((e = allow(k_b_rows<N, P>, b_smem_rows<P>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_rows<N, P, ODD>, b_smem_rows<P>())) != cudaSuccess) return e;
     constexpr int C0 = tpb_for(P) / FftPlan<P>::T;
     if ((e = allow(k_b_cols<N, P, C0>, b_smem_cols<P, C0>())) != cudaSuccess) return e;
     if constexpr (P % 3 == 0) {
         if ((e = allow(k_b_cols<N, P, C0 / 2>, b_smem_cols<P, C0 / 2>())) != cudaSuccess) return e;
         if ((e = allow(k_b_cols<N, P, 2 * C0>, b_smem_cols<P, 2 * C0>())) != cudaSuccess) return e;
     }
-    if ((e = allow(k_b_c2r<N, P>, b_smem_rows<P>())) != cudaSuccess) return e;
-    if ((e = allow(k_b_s1cols<N>, b_smem_s1cols<N>())) != cudaSuccess) return e;
-    return allow(k_b_s1rows<N>, b_smem_rows<N>());
+    if ((e = allow(k_b_c2r<N, P, ODD>, b_smem_rows<P>())) != cudaSuccess) return e;
+    if constexpr (ODD) {
+        constexpr int M = 2 * N;   // the Bluestein length of the odd side N - 1
+        if ((e = allow(k_b_s1cols_odd<N - 1, M>, b_smem_s1cols<M>())) != cudaSuccess) return e;
+        return allow(k_b_s1rows_odd<N - 1, M>, b_smem_rows<M>());
+    } else {
+        if ((e = allow(k_b_s1cols<N>, b_smem_s1cols<N>())) != cudaSuccess) return e;
+        return allow(k_b_s1rows<N>, b_smem_rows<N>());
+    }
 }
 
 cudaError_t prepare_backward_kernels() {
     cudaError_t e;
-    if ((e = prepare_b<128, 192>()) != cudaSuccess) return e;
-    if ((e = prepare_b<128, 128>()) != cudaSuccess) return e;
-    if ((e = prepare_b<256, 384>()) != cudaSuccess) return e;
-    if ((e = prepare_b<256, 256>()) != cudaSuccess) return e;
-    if ((e = prepare_b<512, 768>()) != cudaSuccess) return e;
-    if ((e = prepare_b<512, 512>()) != cudaSuccess) return e;
+    if ((e = prepare_b<128, 192, false>()) != cudaSuccess) return e;
+    if ((e = prepare_b<128, 128, false>()) != cudaSuccess) return e;
+    if ((e = prepare_b<256, 384, false>()) != cudaSuccess) return e;
+    if ((e = prepare_b<256, 256, false>()) != cudaSuccess) return e;
+    if ((e = prepare_b<512, 768, false>()) != cudaSuccess) return e;
+    if ((e = prepare_b<512, 512, false>()) != cudaSuccess) return e;
+    if ((e = prepare_b<128, 192, true>()) != cudaSuccess) return e;
+    if ((e = prepare_b<256, 384, true>()) != cudaSuccess) return e;
+    if ((e = prepare_b<512, 768, true>()) != cudaSuccess) return e;
     if ((e = allow(k_b_angle<128, 8>, b_smem_angle<128, 8>())) != cudaSuccess) return e;
     if ((e = allow(k_b_angle<256, 8>, b_smem_angle<256, 8>())) != cudaSuccess) return e;
     if ((e = allow(k_b_angle<400, 8>, b_smem_angle<400, 8>())) != cudaSuccess) return e;

@@ -66,6 +66,12 @@ struct DevPlan {
     const float2* tw_p;    // [P]  exp(-2 pi i k / P)
     const float2* tw_t;    // [n_theta] exp(-2 pi i k / n_theta)
     const PolarSample* polar;  // [n_theta][n_r]
+    // odd N only (the paper's 127, 255, 511): the N-point DFTs of stage 1 run as Bluestein
+    // convolutions through M-point FFTs, M = 2 (N + 1) >= 2N - 1
+    int m;                 // M (0 for even N)
+    const float2* tw_m;    // [M]  exp(-2 pi i k / M)
+    const float2* chirp;   // [N]  w[n] = exp(+i pi n^2 / N), exponent reduced mod 2N in integers
+    const float2* bh;      // [M]  FFT_M of the chirp filter b (b[m] = w[|m|] for |m| < N), times 1/M
     // transpose of the bilinear polar gather onto the u-major half plane [N/2+1][N]: the
     // samples that read element e are csr_col[csr_ptr[e] .. csr_ptr[e+1]) with weights csr_w
     const int* csr_ptr;
@@ -82,10 +88,14 @@ struct DevPlan {
 
 constexpr int kHeavyRow = 32;
 
+// Stage 2 of an odd scan side N runs in the even frame N + 1 (one zero row and column; the lag
+// set of the frame has one extra lag, -(N + 1)/2, that the kernels leave out).
+__host__ __device__ constexpr int frame_n(int n) { return n + (n & 1); }
+
 inline int angle_chunks(const DevPlan& p) { return (p.nr + p.angle_rc - 1) / p.angle_rc; }
 inline int angle_chunks_max(const DevPlan& p) { return (p.nr + kAngleRadiiMin - 1) / kAngleRadiiMin; }
 inline int fft_threads(int L) { return L / 16 == 25 ? 25 : L / 16; }
-inline int c2r_blocks(const DevPlan& p) { return (p.n / 2) / (tpb_for(p.p) / fft_threads(p.p)); }
+inline int c2r_blocks(const DevPlan& p) { return (frame_n(p.n) / 2) / (tpb_for(p.p) / fft_threads(p.p)); }
 
 // Kernel kinds, for the launch tracer.
 enum Kind {

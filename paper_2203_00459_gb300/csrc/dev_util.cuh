@@ -65,6 +65,15 @@ __device__ __forceinline__ void block_sum_n(float (&v)[K], float* red) {
 // The (f, g) magnitude pair at (vi, ui) of the N-periodic spectrum from the u-major half plane of
 // interleaved pairs (the Hermitian mirror for ui > N/2).
 __device__ __forceinline__ float2 mag2_at(const float2* __restrict__ m, int n, int vi, int ui) {
+    if (n & 1) {   // odd N (the paper's 127, 255, 511): reduce by division; the half plane has u <= (N-1)/2
+        vi = (vi % n + n) % n;
+        ui = (ui % n + n) % n;
+        if (ui > (n >> 1)) {
+            vi = vi == 0 ? 0 : n - vi;
+            ui = n - ui;
+        }
+        return __ldg(&m[ui * n + vi]);
+    }
     vi &= n - 1;
     ui &= n - 1;
     if (ui > (n >> 1)) {
@@ -84,6 +93,26 @@ __device__ __forceinline__ float mag_at(const float* __restrict__ m, int n, int 
     return __ldg(&m[ui * n + vi]);
 }
 
+// Bluestein's chirp convolution of one length-N sequence (element i at buf[spad(i) * es]) by
+// thread j < M/16 of its group.  With w[n] = exp(i pi n^2 / N), n k = (n^2 + k^2 - (k - n)^2) / 2
+// gives X[k] = sum_n x[n] exp(-2 pi i n k / N) = conj(w[k]) sum_n (x[n] conj(w[n])) w[k - n], a
+// linear convolution that the M-point FFTs (M >= 2N - 1) evaluate as
+// y = IFFT_M(FFT_M(a) * bh) with bh = FFT_M(b) / M of the circular filter b.  On return buf holds
+// y; X[k] = conj(w[k]) y[k] for k < N is the caller's.  load(n) gives x[n] for n < N.  Every
+// thread of the CTA must call it (it contains barriers).
+template <int M, class Load>
+__device__ __forceinline__ void bluestein(float2* buf, int es, int j, int n, const DevPlan& p, Load load) {
+    constexpr int T = FftPlan<M>::T;
+    first_pass_global<M>(buf, es, j, [&](int m) {
+        return m < n ? c_cjmul(__ldg(&p.chirp[m]), load(m)) : make_float2(0.f, 0.f);
+    });
+    __syncthreads();
+    fft_passes_from<M, -1, 2>(buf, es, j, p.tw_m);
+    for (int k = j; k < M; k += T) buf[spad(k) * es] = c_mul(buf[spad(k) * es], __ldg(&p.bh[k]));
+    __syncthreads();
+    fft<M, +1>(buf, es, j, true, p.tw_m);
+}
+
 // Exact fixed-point sampling coordinates of the Rotate step: with C = cos(theta) 2^40 and
 // S = sin(theta) 2^40 rounded to integers (from the double cosine and sine the splits carry), the
 // sample of output pixel (X, Y) sits at p = c + R(-theta)((X, Y) - c), i.e.
@@ -99,9 +128,11 @@ __device__ __forceinline__ RotFixed rot_fixed(float ch, float cl, float sh, floa
     RotFixed r;
     r.C = __double2ll_rn(((double)ch + (double)cl) * one);
     r.S = __double2ll_rn(((double)sh + (double)sl) * one);
-    const long long c = (long long)(n / 2) << 40, h = n / 2;
-    r.px0 = c - r.C * h - r.S * h;
-    r.py0 = c + r.S * h - r.C * h;
+    // centre c = n/2 (a half-integer for odd n): c 2^40 = n 2^39, and C c = (C n) / 2, exact for even n
+    // and within 2^-41 px for odd n
+    const long long c = (long long)n << 39, Cc = (r.C * n) >> 1, Sc = (r.S * n) >> 1;
+    r.px0 = c - Cc - Sc;
+    r.py0 = c + Sc - Cc;
     return r;
 }
 
@@ -127,17 +158,19 @@ __device__ __forceinline__ float rotated_sample_fixed(const float* __restrict__ 
 }
 
 // Combines per-block (mean, M2, max, count) statistics of the translation scores into the mean,
-// population std and maximum over all `total` scores (equal block counts; Chan's update).  Run by
-// one full warp; every lane returns the results.
+// population std and maximum over all `total` scores (Chan's update).  With equal block counts
+// (even N) the mean is the mean of the block means; the blocks of an odd N's frame hold different
+// counts (the left-out lag), and the mean is weighted by them.  Run by one full warp; every lane
+// returns the results.
 __device__ __forceinline__ void xy_stats_warp(const float* __restrict__ s, int nblk, float total, float& mu,
-                                              float& sd, float& cmax) {
+                                              float& sd, float& cmax, bool weighted = false) {
     const int lane = threadIdx.x & 31;
     float lsum = 0.f, lmax = -FLT_MAX;
     for (int i = lane; i < nblk; i += 32) {
-        lsum += s[4 * i];
+        lsum += weighted ? s[4 * i] * s[4 * i + 3] : s[4 * i];
         lmax = fmaxf(lmax, s[4 * i + 2]);
     }
-    mu = warp_sum(lsum) / nblk;
+    mu = weighted ? warp_sum(lsum) / total : warp_sum(lsum) / nblk;
     cmax = warp_max(lmax);
     float lm2 = 0.f;
     for (int i = lane; i < nblk; i += 32) {

@@ -96,6 +96,77 @@ __global__ void __launch_bounds__(kThreads) k_s1_cols(DevPlan p, const float2* _
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// stage 1 for the odd sides 127, 255, 511 (Sec. IV-B resolutions): the N-point DFTs by Bluestein
+// ---------------------------------------------------------------------------------------------
+
+// Hann-windowed row DFTs of an odd-sided scan (f for z = 0, g for z = 1), two real rows per complex
+// DFT: Z = DFT_N(x_r + i x_{r+1}) gives X_r[u] = (Z[u] + conj Z[N - u]) / 2 and
+// X_{r+1}[u] = (Z[u] - conj Z[N - u]) / 2i for u in [0, (N - 1)/2]; an odd N has no Nyquist
+// column, so the packed rows hold (N + 1)/2 complex values, u = 0 the real DC value.  The last
+// pair of rows has no second row (it reads as zero).
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads) k_s1_rows_odd(DevPlan p, const long long* __restrict__ tab,
+                                                          const float* __restrict__ f, const float* __restrict__ g,
+                                                          float2* __restrict__ s1, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    constexpr int T = FftPlan<M>::T, FPC = kThreads / T, SL = spad(M), W = (N + 1) / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
+    const int k = threadIdx.x / T, j = threadIdx.x % T, r = r0 + 2 * k;
+    const bool oka = r < N, okb = r + 1 < N;
+    const float* __restrict__ rp = (s ? g : f) + tab[3 * q] + (size_t)r * N;
+    const float wa = oka ? (p.window ? __ldg(&p.win[r]) : 1.f) : 0.f;
+    const float wb = okb ? (p.window ? __ldg(&p.win[r + 1]) : 1.f) : 0.f;
+    bluestein<M>(sm + k * SL, 1, j, N, p, [&](int x) {
+        const float wx = p.window ? __ldg(&p.win[x]) : 1.f;
+        return make_float2(oka ? __ldg(rp + x) * (wa * wx) : 0.f, okb ? __ldg(rp + N + x) * (wb * wx) : 0.f);
+    });
+    float2* out = s1 + (size_t)(s * B + q) * N * W;
+    for (int idx = threadIdx.x; idx < FPC * W; idx += kThreads) {
+        const int kk = idx / W, u = idx % W, row = r0 + 2 * kk, um = u == 0 ? 0 : N - u;
+        const float2* Z = sm + kk * SL;
+        const float2 zu = c_cjmul(__ldg(&p.chirp[u]), Z[spad(u)]);
+        const float2 zm = c_cjmul(__ldg(&p.chirp[um]), Z[spad(um)]);
+        if (row < N)
+            out[(size_t)row * W + u] = u == 0 ? make_float2(zu.x, 0.f)
+                                              : make_float2(0.5f * (zu.x + zm.x), 0.5f * (zu.y - zm.y));
+        if (row + 1 < N)
+            out[(size_t)(row + 1) * W + u] = u == 0 ? make_float2(zu.y, 0.f)
+                                                    : make_float2(0.5f * (zu.y + zm.y), -0.5f * (zu.x - zm.x));
+    }
+}
+
+// Column DFTs of the packed row spectra of an odd side (every column u in [0, (N - 1)/2] is an
+// ordinary complex column), band-pass, magnitude and, with ph non-NULL, the unit phasors kept for
+// the adjoint: the layout of k_s1_cols, u-major [(N + 1)/2][N] with (f, g) interleaved.
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads) k_s1_cols_odd(DevPlan p, const float2* __restrict__ s1,
+                                                          float* __restrict__ mt, float2* __restrict__ ph, int B) {
+    grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
+    constexpr int T = FftPlan<M>::T, C = kThreads / T, ES = C + 1, W = (N + 1) / 2;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
+    const int c = threadIdx.x % C, j = threadIdx.x / C, u = u0 + c;
+    const float2* in = s1 + (size_t)(s * B + q) * N * W;
+    bluestein<M>(sm + c, ES, j, N, p, [&](int v) {
+        return u < W ? __ldg(&in[(size_t)v * W + u]) : make_float2(0.f, 0.f);
+    });
+    float* out = mt + (size_t)q * W * N * 2 + s;   // (f, g) pairs: this scan's half of each
+    float2* pho = ph ? ph + (size_t)(s * B + q) * W * N : nullptr;
+    for (int idx = threadIdx.x; idx < C * N; idx += kThreads) {
+        const int cc = idx / N, v = idx % N, uu = u0 + cc;
+        if (uu >= W) continue;
+        const float2 z = c_cjmul(__ldg(&p.chirp[v]), sm[spad(v) * ES + cc]);
+        const int vs = v <= N / 2 ? v : v - N, m2 = vs * vs + uu * uu;
+        const bool in_band = m2 >= p.m_lo && m2 <= p.m_hi;
+        const float a = in_band ? sqrtf(fmaf(z.x, z.x, z.y * z.y)) : 0.f;
+        const size_t at = (size_t)uu * N + v;
+        out[2 * at] = a;
+        if (pho) pho[at] = a > 0.f ? make_float2(z.x / a, z.y / a) : make_float2(0.f, 0.f);
+    }
+}
+
 // Cart2Pol of both magnitudes for RC radii, packed as z[a] = A_f[a] + i A_g[a], FFT along
 // angle, then S[k] = sum_r conj(A^_f[k, r]) A^_g[k, r] for this chunk of radii.  The inverse FFT of
 // S summed over chunks is the circular correlation along angle summed over radius (Eq. 7).
@@ -287,32 +358,37 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
 // real row FFTs packed two rows per complex FFT, output u in [0, P/2) (DC/Nyquist packed in 0).
 // Under Alg. 1's own stage 2 (rotate_target 1) f is read as it is and g is turned back by theta.
 // The first pass takes its inputs straight from the gather (no staging in shared memory).
-template <int N, int P>
+// ODD: the scan side is N - 1 (odd) inside this kernel's frame N: the scan's rows and columns are
+// read with stride N - 1, its last frame row and column are zero, and Rotate turns about (N - 1)/2.
+template <int N, int P, bool ODD>
 __global__ void __launch_bounds__(tpb_for(P), P == 768 ? 6 : 65536 / (tpb_for(P) * 64)) k_s2_rows(DevPlan p, const long long* __restrict__ tab,
                                                         const float* __restrict__ f, const float* __restrict__ g,
                                                         const float* __restrict__ th, float2* __restrict__ s2, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
+    constexpr int NI = ODD ? N - 1 : N;   // the scan side
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, r0 = blockIdx.x * FPC * 2;
     const int k = threadIdx.x / T, j = threadIdx.x % T;
     const int r = r0 + 2 * k;                                 // rows r and r + 1
+    const bool okb = !ODD || r + 1 < NI;                      // row r + 1 lies in the scan
     const float* __restrict__ src = (s ? g : f) + tab[3 * q];
     if (s == p.rotate_target) {
         const float* t = th + 8 * q;
         const float sg = p.rotate_target ? -1.f : 1.f;   // g turns by -theta
-        const RotFixed rf = rot_fixed(t[1], t[2], sg * t[3], sg * t[4], N);
+        const RotFixed rf = rot_fixed(t[1], t[2], sg * t[3], sg * t[4], NI);
         // rows r and r + 1: (Y - c) steps add S to px and C to py
         const long long pxr = rf.px0 + rf.S * r, pyr = rf.py0 + rf.C * r;
         first_pass_global<P>(sm + k * SL, 1, j, [&](int x) {
-            if (x >= N) return make_float2(0.f, 0.f);
+            if (x >= NI) return make_float2(0.f, 0.f);
             const long long px = pxr + rf.C * x, py = pyr - rf.S * x;
-            return make_float2(rotated_sample_fixed(src, N, px, py), rotated_sample_fixed(src, N, px + rf.S, py + rf.C));
+            return make_float2(rotated_sample_fixed(src, NI, px, py),
+                               okb ? rotated_sample_fixed(src, NI, px + rf.S, py + rf.C) : 0.f);
         });
     } else {
-        const float* rp = src + (size_t)r * N;
+        const float* rp = src + (size_t)r * NI;
         first_pass_global<P>(sm + k * SL, 1, j, [&](int x) {
-            return x < N ? make_float2(__ldg(rp + x), __ldg(rp + N + x)) : make_float2(0.f, 0.f);
+            return x < NI ? make_float2(__ldg(rp + x), okb ? __ldg(rp + NI + x) : 0.f) : make_float2(0.f, 0.f);
         });
     }
     __syncthreads();
@@ -424,12 +500,15 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_
 // writes the mean, sum of squared deviations and maximum of its scores for the z-score.  The
 // first pass builds its inputs from global memory and the last pass stores the kept columns
 // straight to global memory (and to the tile, for the second statistics pass).
-template <int N, int P>
+// ODD: the scan side is N - 1 inside this kernel's frame N; frame lag index 0 (lag -N/2, not a
+// candidate of an odd side) is left out of c_xy (layout [N - 1][N - 1]) and of the statistics.
+template <int N, int P, bool ODD>
 __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long* __restrict__ tab,
                                                      const float2* __restrict__ s3, float* __restrict__ cxy_ws,
                                                      float* __restrict__ cxy_out, float* __restrict__ st, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     constexpr int T = FftPlan<P>::T, TPB = tpb_for(P), FPC = TPB / T, SL = spad(P), W = P / 2;
+    constexpr int NI = ODD ? N - 1 : N, LO = ODD ? 1 : 0;   // candidates per axis; first kept frame index
     extern __shared__ float2 sm[];
     __shared__ float red[32];
     const int q = blockIdx.y, i0 = blockIdx.x * FPC * 2;
@@ -439,29 +518,37 @@ __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long*
     first_pass_global<P, +1>(buf, 1, j, [&](int x) { return pack_inverse(ra, ra + W, x, P); });
     __syncthreads();
     const float scale = 1.f / ((float)P * (float)P);
-    float* out = (cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N) + (size_t)i * N;
+    const bool oka = i >= LO;   // frame lag row i holds a candidate (row i + 1 always does)
+    float* out = (cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * NI * NI) + (size_t)(i - LO) * NI - LO;
     float lsum = 0.f, lmax = -FLT_MAX;
     // P-position pos holds lag s_x = pos (pos < P/2) or pos - P; column jj = s_x + N/2
     rest_global<P, +1>(buf, 1, j, p.tw_p, [&](int pos, float2 z) {
         if (pos < N / 2 || pos >= P - N / 2) {
             const int jj = pos < N / 2 ? pos + N / 2 : pos - P + N / 2;
             const float va = z.x * scale, vb = z.y * scale;
-            out[jj] = va;
-            out[N + jj] = vb;
-            lsum += va + vb;
-            lmax = fmaxf(lmax, fmaxf(va, vb));
+            if (jj >= LO) {
+                if (oka) {
+                    out[jj] = va;
+                    lsum += va;
+                    lmax = fmaxf(lmax, va);
+                }
+                out[NI + jj] = vb;
+                lsum += vb;
+                lmax = fmaxf(lmax, vb);
+            }
             buf[spad(pos)] = make_float2(va, vb);   // same position the last pass read: no race
         }
     });
-    constexpr float cnt = (float)(FPC * 2 * N);
+    const float cnt = (float)((FPC * 2 - (ODD && blockIdx.x == 0 ? 1 : 0)) * NI);
     const float mean = block_reduce<false>(lsum, red) * (1.f / cnt);
     const float bmax = block_reduce<true>(lmax, red);
     float lm2 = 0.f;
     for (int idx = threadIdx.x; idx < FPC * N; idx += TPB) {
         const int kk = idx / N, jj = idx % N, nn = (jj - N / 2 + P) % P;
+        if (jj < LO) continue;
         const float2 z = sm[kk * SL + spad(nn)];
         const float da = z.x - mean, db = z.y - mean;
-        lm2 += da * da + db * db;
+        lm2 += (i0 + 2 * kk >= LO ? da * da : 0.f) + db * db;
     }
     const float m2 = block_reduce<false>(lm2, red);
     if (threadIdx.x == 0) {
@@ -479,7 +566,9 @@ __global__ void __launch_bounds__(kThreads) k_s2_c2r(DevPlan p, const long long*
 // of the pair adds the slabs in order and writes (t_x, t_y) = delta_xy E[s].  It also keeps, for
 // the adjoint, the statistics and the sums of e z, e z s_x and e z s_y with z = (c - mean) / std:
 // with them the z-score adjoint needs no second pass over the scores (see k_b_rows).
-template <int N>
+// ODD: the scan side is N - 1 inside the frame N; the scores are the (N - 1)^2 candidates of an odd
+// side, c_xy [N - 1][N - 1] at frame lags 1 .. N - 1 (lag = frame index - N/2), read one by one.
+template <int N, bool ODD>
 __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __restrict__ tab,
                                                   const float* __restrict__ cxy_ws, const float* __restrict__ cxy_out,
                                                   const float* __restrict__ st, int nblk, float* __restrict__ sx,
@@ -490,21 +579,24 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
     __shared__ float stat[4];
     __shared__ bool last;
     const int q = blockIdx.y;
+    constexpr int NI = ODD ? N - 1 : N;
     constexpr int ROWS = N / kSplitXY, TOT = ROWS * (N / 4), PER = (TOT + kThreads - 1) / kThreads;
     const int y0 = blockIdx.x * ROWS;
-    const float* c = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * N * N;
+    const float* c = cxy_out ? cxy_out + tab[3 * q] : cxy_ws + (size_t)q * NI * NI;
     // the scores first (they do not depend on the statistics), so their loads overlap the
     // statistics' reduction below
     float4 vv[PER];
+    if constexpr (!ODD) {
 #pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int idx = threadIdx.x + m * kThreads;
-        if (TOT % kThreads == 0 || idx < TOT)
-            vv[m] = *reinterpret_cast<const float4*>(c + (size_t)(y0 + idx / (N / 4)) * N + (idx % (N / 4)) * 4);
+        for (int m = 0; m < PER; ++m) {
+            const int idx = threadIdx.x + m * kThreads;
+            if (TOT % kThreads == 0 || idx < TOT)
+                vv[m] = *reinterpret_cast<const float4*>(c + (size_t)(y0 + idx / (N / 4)) * N + (idx % (N / 4)) * 4);
+        }
     }
     if (threadIdx.x < 32) {
         float mu, sd, cmax;
-        xy_stats_warp(st + (size_t)q * nblk * 4, nblk, (float)N * (float)N, mu, sd, cmax);
+        xy_stats_warp(st + (size_t)q * nblk * 4, nblk, (float)NI * (float)NI, mu, sd, cmax, ODD);
         if (threadIdx.x == 0) {
             stat[0] = cmax;
             stat[1] = p.score_norm == 1 ? 1.f / p.temp_xy : (sd > 0.f ? 1.f / (sd * p.temp_xy) : 0.f);
@@ -516,6 +608,21 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
     const float cmax = stat[0], inv = stat[1], mu = stat[2], sd = stat[3];
     const float isd = sd > 0.f ? 1.f / sd : 0.f;
     float le = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lzx = 0.f, lzy = 0.f;
+    if constexpr (ODD) {
+        for (int idx = threadIdx.x; idx < ROWS * N; idx += kThreads) {
+            const int yy = y0 + idx / N, xx = idx % N;
+            if (yy < 1 || xx < 1) continue;
+            const float v = __ldg(c + (size_t)(yy - 1) * NI + (xx - 1));
+            const float e = expf((v - cmax) * inv), z = (v - mu) * isd;
+            const float sxv = (float)(xx - N / 2), syv = (float)(yy - N / 2);
+            le += e;
+            lx += e * sxv;
+            ly += e * syv;
+            lz += e * z;
+            lzx += e * z * sxv;
+            lzy += e * z * syv;
+        }
+    } else {
 #pragma unroll
     for (int m = 0; m < PER; ++m) {
         const int idx = threadIdx.x + m * kThreads;
@@ -535,6 +642,7 @@ __global__ void __launch_bounds__(kThreads) k_sxy(DevPlan p, const long long* __
         lz += ez;
         lzx += ez * sx0 + (e1 * z1 + 2.f * e2 * z2 + 3.f * e3 * z3);
         lzy += ez * sy;
+    }
     }
     float sums[6] = {le, lx, ly, lz, lzx, lzy};
     block_sum_n<6>(sums, red);
@@ -646,7 +754,7 @@ template <int N> constexpr size_t smem_cols1() {
 template <int P, int C> constexpr size_t smem_cols2() { return 2 * (size_t)spad(P) * C * sizeof(float2); }
 template <int NT, int RC> constexpr size_t smem_angle() { return (size_t)spad(NT) * RC * sizeof(float2); }
 
-template <int N, int P>
+template <int N, int P, bool ODD>
 static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                                  const float* g, float* pose, float* c_xy, cudaStream_t st);
 
@@ -664,43 +772,66 @@ static cudaError_t launch_stage1_angle(const DevPlan& p, const Ws& w, int B, con
     return cudaGetLastError();
 }
 
-template <int N, int P>
+// Stage 1 of a scan side N: the power-of-two FFTs, or (M > 0) the Bluestein DFTs of an odd N.
+template <int N, int M>
+static void launch_stage1_spectra(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
+                                  const float* g, cudaStream_t st) {
+    if constexpr (M == 0) {
+        constexpr int T1 = FftPlan<N>::T;
+        w.tr->before(K_S1_ROWS, st);
+        launch_pdl(k_s1_rows<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st, p, tab, f, g, w.s1, B);
+        w.tr->before(K_S1_COLS, st);
+        launch_pdl(k_s1_cols<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_cols1<N>(), st, p, w.s1, w.mt, w.phs,
+                   B);
+    } else {
+        constexpr int TM = FftPlan<M>::T, FPC = kThreads / TM, W = (N + 1) / 2;
+        static_assert(W % FPC == 0 && W % (kThreads / TM) == 0, "row pairs and columns fill whole CTAs");
+        w.tr->before(K_S1_ROWS, st);
+        launch_pdl(k_s1_rows_odd<N, M>, dim3(W / FPC, B, 2), kThreads, (size_t)FPC * spad(M) * sizeof(float2), st, p, tab,
+                   f, g, w.s1, B);
+        w.tr->before(K_S1_COLS, st);
+        launch_pdl(k_s1_cols_odd<N, M>, dim3(W / (kThreads / TM), B, 2), kThreads, smem_cols1<M>(), st, p, w.s1, w.mt,
+                   w.phs, B);
+    }
+}
+
+// N: the scan side; NE: stage 2's frame (N, or N + 1 for odd N); M: Bluestein length (0: none).
+template <int N, int NE, int M, int P>
 static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                              const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
-    constexpr int T1 = FftPlan<N>::T;
+    constexpr bool ODD = (N & 1) != 0;
     StageRange range("fmbym forward");
-    w.tr->before(K_S1_ROWS, st);
-    launch_pdl(k_s1_rows<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_rows<N>(), st, p, tab, f, g, w.s1, B);
-    w.tr->before(K_S1_COLS, st);
-    launch_pdl(k_s1_cols<N>, dim3((N / 2) / (kThreads / T1), B, 2), kThreads, smem_cols1<N>(), st, p, w.s1, w.mt, w.phs, B);
+    launch_stage1_spectra<N, M>(p, w, B, tab, f, g, st);
     cudaError_t e;
     if (p.nt == 128) e = launch_stage1_angle<128>(p, w, B, tab, pose, c_theta, st);
     else if (p.nt == 256) e = launch_stage1_angle<256>(p, w, B, tab, pose, c_theta, st);
     else if (p.nt == 400) e = launch_stage1_angle<400>(p, w, B, tab, pose, c_theta, st);
     else e = launch_stage1_direct(p, w, B, tab, pose, c_theta, st);   // no FFT plan: direct sums
     if (e != cudaSuccess) return e;
-    if (!p.full_circle) return launch_stage2<N, P>(p, w, B, tab, f, g, pose, c_xy, st);
+    if (!p.full_circle) return launch_stage2<NE, P, ODD>(p, w, B, tab, f, g, pose, c_xy, st);
     // full circle: the two candidate passes keep nothing for the adjoint and write no scores for
     // the caller; the third pass runs at each pair's winner
     Ws wc = w;
     wc.s2hat = nullptr;
     const int nb = (B + 127) / 128, nblk = c2r_blocks(p);
     launch_pdl(k_fc_flip, nb, 128, 0, st, w.th, w.fc, B);
-    if ((e = launch_stage2<N, P>(p, wc, B, tab, f, g, w.fcpose, nullptr, st)) != cudaSuccess) return e;
+    if ((e = launch_stage2<NE, P, ODD>(p, wc, B, tab, f, g, w.fcpose, nullptr, st)) != cudaSuccess) return e;
     launch_pdl(k_fc_restore, nb, 128, 0, st, (const float*)w.st, nblk, w.th, w.fc, B);
-    if ((e = launch_stage2<N, P>(p, wc, B, tab, f, g, pose, nullptr, st)) != cudaSuccess) return e;
+    if ((e = launch_stage2<NE, P, ODD>(p, wc, B, tab, f, g, pose, nullptr, st)) != cudaSuccess) return e;
     launch_pdl(k_fc_select, nb, 128, 0, st, tab, (const float*)w.st, nblk, w.th, (const float*)w.fc, pose, B);
-    return launch_stage2<N, P>(p, w, B, tab, f, g, pose, c_xy, st);
+    return launch_stage2<NE, P, ODD>(p, w, B, tab, f, g, pose, c_xy, st);
 }
 
 // Stage 2 of Alg. 1 for the headings in w.th: Rotate, the padded correlation and the translation
-// soft-argmax -> pose[.][1..2], block statistics of c_xy in w.st.
-template <int N, int P>
+// soft-argmax -> pose[.][1..2], block statistics of c_xy in w.st.  N is the frame (ODD: the scan
+// side is N - 1).
+template <int N, int P, bool ODD>
 static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                                  const float* g, float* pose, float* c_xy, cudaStream_t st) {
     constexpr int T2 = FftPlan<P>::T, TB2 = tpb_for(P);
     w.tr->before(K_S2_ROWS, st);
-    launch_pdl(k_s2_rows<N, P>, dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st, p, tab, f, g, w.th, w.s2, B);
+    launch_pdl(k_s2_rows<N, P, ODD>, dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st, p, tab, f, g, w.th, w.s2,
+               B);
     w.tr->before(K_S2_COLS, st);
     constexpr int C0 = TB2 / T2;   // the default tile; the 3 * 2^k lengths also have half and double
     if constexpr (P % 3 == 0) {
@@ -717,9 +848,10 @@ static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const lon
     }
     const int nblk = (N / 2) / (TB2 / T2);
     w.tr->before(K_S2_C2R, st);
-    launch_pdl(k_s2_c2r<N, P>, dim3(nblk, B), TB2, smem_rows<P>(), st, p, tab, w.s3, w.cxy, c_xy, w.st, B);
+    launch_pdl(k_s2_c2r<N, P, ODD>, dim3(nblk, B), TB2, smem_rows<P>(), st, p, tab, w.s3, w.cxy, c_xy, w.st, B);
     w.tr->before(K_SXY, st);
-    launch_pdl(k_sxy<N>, dim3(kSplitXY, B), kThreads, 0, st, p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose, w.xm, w.th);
+    launch_pdl(k_sxy<N, ODD>, dim3(kSplitXY, B), kThreads, 0, st, p, tab, w.cxy, c_xy, w.st, nblk, w.sx, w.cnt, pose, w.xm,
+               w.th);
     w.tr->close(st);
     return cudaGetLastError();
 }
@@ -727,23 +859,33 @@ static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const lon
 cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                            const float* g, float* pose, float* c_theta, float* c_xy, cudaStream_t st) {
     if (B <= 0) return cudaSuccess;
-    if (p.n == 128) return p.p == 192 ? launch_np<128, 192>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
-                                      : launch_np<128, 128>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
-    if (p.n == 256) return p.p == 384 ? launch_np<256, 384>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
-                                      : launch_np<256, 256>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
-    return p.p == 768 ? launch_np<512, 768>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
-                      : launch_np<512, 512>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+    switch (p.n) {
+        case 127: return launch_np<127, 128, 256, 192>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+        case 255: return launch_np<255, 256, 512, 384>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+        case 511: return launch_np<511, 512, 1024, 768>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+        case 128: return p.p == 192 ? launch_np<128, 128, 0, 192>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+                                    : launch_np<128, 128, 0, 128>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+        case 256: return p.p == 384 ? launch_np<256, 256, 0, 384>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+                                    : launch_np<256, 256, 0, 256>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+        default: return p.p == 768 ? launch_np<512, 512, 0, 768>(p, w, B, tab, f, g, pose, c_theta, c_xy, st)
+                                   : launch_np<512, 512, 0, 512>(p, w, B, tab, f, g, pose, c_theta, c_xy, st);
+    }
 }
 
 cudaError_t launch_forward_stage2(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                                   const float* g, float* pose, float* c_xy, cudaStream_t st) {
     if (B <= 0) return cudaSuccess;
-    if (p.n == 128) return p.p == 192 ? launch_stage2<128, 192>(p, w, B, tab, f, g, pose, c_xy, st)
-                                      : launch_stage2<128, 128>(p, w, B, tab, f, g, pose, c_xy, st);
-    if (p.n == 256) return p.p == 384 ? launch_stage2<256, 384>(p, w, B, tab, f, g, pose, c_xy, st)
-                                      : launch_stage2<256, 256>(p, w, B, tab, f, g, pose, c_xy, st);
-    return p.p == 768 ? launch_stage2<512, 768>(p, w, B, tab, f, g, pose, c_xy, st)
-                      : launch_stage2<512, 512>(p, w, B, tab, f, g, pose, c_xy, st);
+    switch (p.n) {
+        case 127: return launch_stage2<128, 192, true>(p, w, B, tab, f, g, pose, c_xy, st);
+        case 255: return launch_stage2<256, 384, true>(p, w, B, tab, f, g, pose, c_xy, st);
+        case 511: return launch_stage2<512, 768, true>(p, w, B, tab, f, g, pose, c_xy, st);
+        case 128: return p.p == 192 ? launch_stage2<128, 192, false>(p, w, B, tab, f, g, pose, c_xy, st)
+                                    : launch_stage2<128, 128, false>(p, w, B, tab, f, g, pose, c_xy, st);
+        case 256: return p.p == 384 ? launch_stage2<256, 384, false>(p, w, B, tab, f, g, pose, c_xy, st)
+                                    : launch_stage2<256, 256, false>(p, w, B, tab, f, g, pose, c_xy, st);
+        default: return p.p == 768 ? launch_stage2<512, 768, false>(p, w, B, tab, f, g, pose, c_xy, st)
+                                   : launch_stage2<512, 512, false>(p, w, B, tab, f, g, pose, c_xy, st);
+    }
 }
 
 template <typename K>
@@ -751,19 +893,29 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int N, int P>
+template <int N, int P, bool ODD>
 static cudaError_t prepare_np() {
     cudaError_t e;
-    if ((e = allow_smem(k_s1_rows<N>, smem_rows<N>())) != cudaSuccess) return e;
-    if ((e = allow_smem(k_s1_cols<N>, smem_cols1<N>())) != cudaSuccess) return e;
-    if ((e = allow_smem(k_s2_rows<N, P>, smem_rows<P>())) != cudaSuccess) return e;
+    if constexpr (!ODD) {
+        if ((e = allow_smem(k_s1_rows<N>, smem_rows<N>())) != cudaSuccess) return e;
+        if ((e = allow_smem(k_s1_cols<N>, smem_cols1<N>())) != cudaSuccess) return e;
+    }
+    if ((e = allow_smem(k_s2_rows<N, P, ODD>, smem_rows<P>())) != cudaSuccess) return e;
     constexpr int C0 = tpb_for(P) / FftPlan<P>::T;
     if ((e = allow_smem(k_s2_cols<N, P, C0>, smem_cols2<P, C0>())) != cudaSuccess) return e;
     if constexpr (P % 3 == 0) {
         if ((e = allow_smem(k_s2_cols<N, P, C0 / 2>, smem_cols2<P, C0 / 2>())) != cudaSuccess) return e;
         if ((e = allow_smem(k_s2_cols<N, P, 2 * C0>, smem_cols2<P, 2 * C0>())) != cudaSuccess) return e;
     }
-    return allow_smem(k_s2_c2r<N, P>, smem_rows<P>());
+    return allow_smem(k_s2_c2r<N, P, ODD>, smem_rows<P>());
+}
+
+template <int N, int M>
+static cudaError_t prepare_odd() {
+    cudaError_t e;
+    constexpr int FPC = kThreads / FftPlan<M>::T;
+    if ((e = allow_smem(k_s1_rows_odd<N, M>, (size_t)FPC * spad(M) * sizeof(float2))) != cudaSuccess) return e;
+    return allow_smem(k_s1_cols_odd<N, M>, smem_cols1<M>());
 }
 
 const char* const kKindNames[K_COUNT] = {
@@ -773,12 +925,18 @@ const char* const kKindNames[K_COUNT] = {
 
 cudaError_t prepare_forward_kernels() {
     cudaError_t e;
-    if ((e = prepare_np<128, 192>()) != cudaSuccess) return e;
-    if ((e = prepare_np<128, 128>()) != cudaSuccess) return e;
-    if ((e = prepare_np<256, 384>()) != cudaSuccess) return e;
-    if ((e = prepare_np<256, 256>()) != cudaSuccess) return e;
-    if ((e = prepare_np<512, 768>()) != cudaSuccess) return e;
-    if ((e = prepare_np<512, 512>()) != cudaSuccess) return e;
+    if ((e = prepare_np<128, 192, false>()) != cudaSuccess) return e;
+    if ((e = prepare_np<128, 128, false>()) != cudaSuccess) return e;
+    if ((e = prepare_np<256, 384, false>()) != cudaSuccess) return e;
+    if ((e = prepare_np<256, 256, false>()) != cudaSuccess) return e;
+    if ((e = prepare_np<512, 768, false>()) != cudaSuccess) return e;
+    if ((e = prepare_np<512, 512, false>()) != cudaSuccess) return e;
+    if ((e = prepare_np<128, 192, true>()) != cudaSuccess) return e;
+    if ((e = prepare_np<256, 384, true>()) != cudaSuccess) return e;
+    if ((e = prepare_np<512, 768, true>()) != cudaSuccess) return e;
+    if ((e = prepare_odd<127, 256>()) != cudaSuccess) return e;
+    if ((e = prepare_odd<255, 512>()) != cudaSuccess) return e;
+    if ((e = prepare_odd<511, 1024>()) != cudaSuccess) return e;
     if ((e = allow_smem(k_angle<128, 8>, smem_angle<128, 8>())) != cudaSuccess) return e;
     if ((e = allow_smem(k_angle<256, 8>, smem_angle<256, 8>())) != cudaSuccess) return e;
     if ((e = allow_smem(k_angle<400, 8>, smem_angle<400, 8>())) != cudaSuccess) return e;

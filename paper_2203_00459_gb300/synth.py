@@ -112,6 +112,14 @@ WORKLOADS = {
     # 512^2, theta ~ U(-8, 8) deg, t ~ U(-16, 16) px
     "batch512": dict(n=512, n_points=400, n_walls=40, n_theta=400, n_r=256, pairs=32, seed_id=3,
                      theta_deg=8.0, t_px=16.0),
+    # the paper's odd sides (Sec. IV-B: 0.8, 0.4, 0.2 m cells): the same scenes and pose ranges as the
+    # power-of-two workloads above, continuous poses, n_r <= N/2
+    "batch127": dict(n=127, n_points=40, n_walls=6, n_theta=128, n_r=63, pairs=16, seed_id=4,
+                     theta_deg=5.0, t_px=4.0),
+    "batch255": dict(n=255, n_points=150, n_walls=20, n_theta=400, n_r=127, pairs=64, seed_id=5,
+                     theta_deg=5.0, t_px=8.0),
+    "batch511": dict(n=511, n_points=400, n_walls=40, n_theta=400, n_r=255, pairs=32, seed_id=6,
+                     theta_deg=8.0, t_px=16.0),
 }
 
 SEED_BASE = 20220301

@@ -435,9 +435,8 @@ def test_adjoint_dot_products():
     assert abs(lhs - np.sum(x * O.spectrum_backward(dF, cfg))) < 1e-10 * abs(lhs)
 
 
-@pytest.mark.parametrize("score_norm", [0, 1])
-def test_pose_gradient_matches_central_differences(score_norm):
-    n = 32
+@pytest.mark.parametrize("score_norm,n", [(0, 32), (1, 32), (0, 33)])   # 33: an odd side (no Nyquist column)
+def test_pose_gradient_matches_central_differences(score_norm, n):
     spec = dict(n=n, n_points=10, n_walls=2, n_theta=32, n_r=16, pairs=1, seed_id=9,
                 theta_deg=8.0, t_px=3.0)
     f, g, _ = synth.make_batch("custom", spec=spec)
