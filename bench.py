@@ -447,6 +447,52 @@ def angle_count_comparison(fma_peak, pairs=64, steps=10, warmup=3):
     return out
 
 
+def odd_side_rates(steps=10, warmup=3):
+    """The paper's odd side 511 (Sec. IV-B's 0.2 m cells: stage-1 DFTs by Bluestein through 1024-point
+    FFTs, stage 2 in the even frame 512) beside 512 on the same scene generator, 32 pairs each,
+    n_theta 400: pairs/s of the forward and of the training step (graph replay, CUDA events, L2
+    flushed before each timed call)."""
+    import numpy as np
+    import torch
+    from paper_2203_00459_gb300 import _lib, synth
+    from paper_2203_00459_gb300.search import PoseSearch, size_cfg
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    out = {}
+    for name in ("batch511", "batch512"):
+        spec = synth.WORKLOADS[name]
+        B = spec["pairs"]
+        f, g, gt = synth.make_batch(name, pairs=B)
+        fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+        gtd = torch.from_numpy(gt.astype(np.float32)).cuda()
+        srch = PoseSearch([size_cfg(spec["n"], spec["n_theta"], spec["n_r"])], max_pairs=B, flags=_lib.FLAG_GRAPH)
+        pose = torch.empty((B, 3), device="cuda")
+        outs = (pose, torch.empty(1, device="cuda"), torch.empty((B, 3), device="cuda"), torch.empty_like(fd),
+                torch.empty_like(gd))
+
+        def timed(fn):
+            for _ in range(warmup):
+                fn()
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            return sum(ms) / len(ms)
+
+        ms_f = timed(lambda: srch.pose(fd, gd, out=pose))
+        ms_t = timed(lambda: srch.pose_train(fd, gd, gtd, kind=2, out=outs))
+        err = np.mean(np.abs(pose.cpu().numpy().astype(np.float64) - gt), axis=0)
+        out[name] = {"n": spec["n"], "pairs": B, "fwd_pairs_per_s": B / (ms_f * 1e-3),
+                     "step_pairs_per_s": B / (ms_t * 1e-3),
+                     "mean_abs_err": {"theta_deg": float(np.degrees(err[0])), "tx_px": float(err[1]), "ty_px": float(err[2])}}
+        srch.close()
+    return out
+
+
 def frontend_rate(scans=64, n=256, delta_xy=0.4, steps=20, warmup=3):
     """Radar front end (fmbym_polar_to_cartesian) on Navtech-sized synthetic scans (400 azimuths x
     3768 range bins of 0.0438 m) to n x n Cartesian scans of delta_xy metres: scans/s (CUDA events,
@@ -785,6 +831,7 @@ def main():
         extra["exhaustive_256"] = exhaustive_comparison()
         extra["alg1_n_theta_733"] = angle_count_comparison(fp32_peak / 2.0)
         extra["radar_frontend"] = frontend_rate()
+        extra["odd_side_511"] = odd_side_rates()
 
     cpu = None
     if pool is not None:

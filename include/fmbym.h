@@ -34,7 +34,8 @@ extern "C" {
 enum fmbym_status {
     FMBYM_OK = 0,
     FMBYM_ERR_INVALID_ARG = 1,      /* NULL or out-of-range argument                         */
-    FMBYM_ERR_UNSUPPORTED_SIZE = 2, /* N not in {128,256,512} or n_theta not in 8..1024   */
+    FMBYM_ERR_UNSUPPORTED_SIZE = 2, /* N not in {127,128,255,256,511,512}, n_theta not in 8..1024,
+                                       or pad_mode 1 with an odd N                          */
     FMBYM_ERR_WORKSPACE = 3,        /* more pairs than the handle was created for            */
     FMBYM_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed                  */
     FMBYM_ERR_TIMEOUT = 5           /* a bounded device-side wait ran out                    */
@@ -42,7 +43,10 @@ enum fmbym_status {
 
 /* Parameters of one scan size: the arguments of ScanMatch in Alg. 1 plus the readings of
  * the places the paper leaves open.
- *   n           scan side N (n_xy of Alg. 1); supported: 128, 256, 512
+ *   n           scan side N (n_xy of Alg. 1); supported: 128, 256, 512 and the paper's odd sides
+ *               127, 255, 511 (Sec. IV-B cell sizes; Alg. 1's n_xy = 255), whose stage-1 DFTs run as
+ *               Bluestein convolutions and whose stage 2 runs in the even frame N + 1 (pad_mode 0
+ *               only)
  *   n_theta     number of angle candidates over a half turn (delta_theta = pi / n_theta,
  *               Alg. 1 first Linspace); 8..1024: 128, 256 and 400 take the FFT correlation,
  *               any other count (Alg. 1's default 733 among them) direct circular sums
@@ -132,7 +136,9 @@ unsigned long long fmbym_workspace_bytes(const fmbym_handle* h);
 /* Forward search (Alg. 1) for n_pairs scan pairs in one call.
  *   size_idx  host int[n_pairs]: index into cfg->sizes of each pair, or NULL for all 0
  *   offsets   host long long[n_pairs]: element offset of pair p's scan in f and g (and in
- *             c_xy), or NULL for packed order (offset of p = sum of N^2 over pairs < p)
+ *             c_xy), or NULL for packed order (offset of p = sum of N^2 over pairs < p); the
+ *             offset of a pair of an even side must be a multiple of 4 (16-byte rows), that of an
+ *             odd side (127, 255, 511) may be any
  *   f, g      device float32: source and target scans
  *   pose      device float32 [n_pairs][3] out: (theta, t_x, t_y)
  *   c_theta   device float32 out or NULL: the n_theta angle scores of each pair, packed in pair

@@ -368,7 +368,11 @@ int make_table(fmbym_handle* h, int n_pairs, const int* size_idx, const long lon
         if (s < 0 || s >= ns) return fail(h, FMBYM_ERR_INVALID_ARG, "size_idx out of range");
         const long long nn = (long long)h->plans[s].cfg.n * h->plans[s].cfg.n;
         off[i] = offsets ? offsets[i] : acc;
-        if (off[i] < 0 || (off[i] & 3)) return fail(h, FMBYM_ERR_INVALID_ARG, "offsets must be >= 0 and multiples of 4");
+        // the kernels of the power-of-two sides read scans, scores and gradients as float4 rows;
+        // those of the odd sides read them element by element
+        const bool odd = (h->plans[s].cfg.n & 1) != 0;
+        if (off[i] < 0 || (!odd && (off[i] & 3)))
+            return fail(h, FMBYM_ERR_INVALID_ARG, "offsets must be >= 0, and multiples of 4 for the even sides");
         acc += nn;
         ct[i] = acc_t;
         acc_t += h->plans[s].cfg.n_theta;

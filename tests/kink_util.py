@@ -23,12 +23,13 @@ def _fma32(a, b, c):
 
 
 def _dtheta32(x, d, theta32):
-    """The d theta term of the Rotate adjoint, sample positions in fp32 (about c = N/2)."""
+    """The d theta term of the Rotate adjoint, sample positions in fp32 (about c = N/2, a
+    half-integer for an odd side)."""
     n = x.shape[0]
     c = f32(n / 2)
     ct, st = f32(math.cos(float(theta32))), f32(math.sin(float(theta32)))
     Y, X = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
-    dX, dY = (X - n // 2).astype(f32), (Y - n // 2).astype(f32)
+    dX, dY = X.astype(f32) - c, Y.astype(f32) - c
     px = _fma32(ct, dX, _fma32(st, dY, c))
     py = _fma32(ct, dY, _fma32(-st, dX, c))
     x0, y0 = np.floor(px).astype(np.int64), np.floor(py).astype(np.int64)

@@ -80,3 +80,27 @@ def test_schedule_variant_case(monkeypatch):
     f, g = _batch("batch256", 2, 31)
     cfg = O.make_cfg(256, 400, 128)
     assert dtheta_kink_margin(f[0], g[0], cfg, np.array([0.7, -0.4, 0.5]), monkeypatch) < 1e-3
+
+
+ODD_DP = np.array([[0.9, -0.4, 0.25], [-0.3, 0.6, 0.5], [0.2, 0.1, -0.8]])
+
+
+@pytest.mark.parametrize("name,pairs,start,kw", [
+    ("batch127", 3, 3, {}), ("batch255", 2, 3, {}), ("batch511", 1, 5, {}),
+    ("batch127", 2, 31, dict(rotate_target=1, temp_theta=0.5)),
+    ("batch127", 2, 33, dict(score_norm=1, temp_theta=2.0e8, temp_xy=1.0e4, window=0))])
+def test_odd_side_adjoint_cases(monkeypatch, name, pairs, start, kw):
+    """The odd-side adjoint parity cases (the paper's 127, 255, 511; rotation about the half-integer
+    centre N/2) and the variants at 127."""
+    spec = synth.WORKLOADS[name]
+    f, g, _ = synth.make_batch(name, pairs=pairs, start=start)
+    cfg = O.make_cfg(spec["n"], spec["n_theta"], spec["n_r"], **kw)
+    for i in range(pairs):
+        assert dtheta_kink_margin(f[i], g[i], cfg, ODD_DP[i], monkeypatch) < 1e-3, (name, start, i)
+
+
+def test_the_odd_side_case_next_to_an_edge_is_seen(monkeypatch):
+    spec = synth.WORKLOADS["batch511"]
+    f, g, _ = synth.make_batch("batch511", pairs=1, start=3)
+    cfg = O.make_cfg(spec["n"], spec["n_theta"], spec["n_r"])
+    assert dtheta_kink_margin(f[0], g[0], cfg, ODD_DP[0], monkeypatch) > 1e-3
