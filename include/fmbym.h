@@ -397,8 +397,18 @@ long long fmbym_unet_launch_count(const fmbym_unet* u);
 int fmbym_unet_set_conv_path(fmbym_unet* u, int path);
 
 /* Number of tcgen05 convolution CTAs whose bounded mbarrier wait gave up since creation (their
- * outputs are not written); 0 in a healthy run.  Synchronous. */
+ * outputs are not written); 0 in a healthy run.  Synchronous.
+ * A call of fmbym_unet_forward or fmbym_unet_backward that runs tcgen05 convolutions waits for its
+ * stream at the end and returns FMBYM_ERR_TIMEOUT when one of its CTAs gave up: the producer's wait
+ * for a shared-memory slot ran out, the CTA issued no further MMA, waited for the MMAs it had issued
+ * to finish (a drain of seconds, far beyond any MMA), released its tensor memory and wrote nothing.
+ * The handle stays usable. */
 long long fmbym_unet_tc_timeouts(fmbym_unet* u);
+
+/* Polls after which a tcgen05 producer's wait for a shared-memory slot gives up (0 restores the
+ * default of 2^22, far beyond a healthy wait).  The drain of issued MMAs is not shortened.  A small
+ * limit makes waits run out on purpose, so that the FMBYM_ERR_TIMEOUT path can be exercised. */
+int fmbym_unet_set_tc_wait_limit(fmbym_unet* u, unsigned polls);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int fmbym_version(void);

@@ -83,6 +83,7 @@ SIGNATURES = {
     "fmbym_unet_load_adam": (_I, [_P, _P, _P, _P]),
     "fmbym_unet_set_conv_path": (_I, [_P, _I]),
     "fmbym_unet_tc_timeouts": (_LL, [_P]),
+    "fmbym_unet_set_tc_wait_limit": (_I, [_P, ctypes.c_uint]),
 }
 
 _lib = None

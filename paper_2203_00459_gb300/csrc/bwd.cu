@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const float2* __restrict__ tw = p.tw_p;
     const float2* inD = b1 + (size_t)q * N * W + u0 + c;
-    const float2* hF = s2hat + (size_t)q * P * W;          // F'^ [P][W]
-    const float2* hG = s2hat + (size_t)(B + q) * P * W;    // G^  [P][W]
+    const float2* hF = s2hat + (size_t)q * P * W;          // F'^ [W][P], column-major
+    const float2* hG = s2hat + (size_t)(B + q) * P * W;    // G^  [W][P]
     const float2 zero = make_float2(0.f, 0.f);
     // P-row v of D holds lag row i = (v + N/2) mod P (zero when i >= N)
     first_pass_global<P>(tD + c, ES, j, [&](int v) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
 #pragma unroll
                 for (int t = 0; t < RL; ++t) {
                     tD[spad(b + t * NBL) * ES + c] = d[t];
-                    o[t] = c_cjmul(d[t], __ldg(hG + (size_t)(b + t * NBL) * W + u));
+                    o[t] = c_cjmul(d[t], __ldg(hG + (size_t)u * P + b + t * NBL));
                 }
                 dft<RL, +1>(o);
 #pragma unroll
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
             if (NBL % T == 0 || b < NBL) {
 #pragma unroll
                 for (int t = 0; t < RL; ++t)
-                    o2[m][t] = c_mul(tD[spad(b + t * NBL) * ES + c], __ldg(hF + (size_t)(b + t * NBL) * W + u));
+                    o2[m][t] = c_mul(tD[spad(b + t * NBL) * ES + c], __ldg(hF + (size_t)u * P + b + t * NBL));
                 dft<RL, +1>(o2[m]);
             }
         }
@@ -214,13 +214,13 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
         for (int m = 0; m < PER; ++m) {
             const int idx = threadIdx.x + m * TPB, v = idx / C, cc = idx % C, u = u0 + cc;
             const float2 D = tD[spad(v) * ES + cc];
-            const float2 G = __ldg(hG + (size_t)v * W + u), F = __ldg(hF + (size_t)v * W + u);
+            const float2 G = __ldg(hG + (size_t)u * P + v), F = __ldg(hF + (size_t)u * P + v);
             if (cc == 0) {
                 const int vm = v == 0 ? 0 : P - v;
                 float2 ad, bd, ag, bg, af, bf;
                 split0(D, tD[spad(vm) * ES + cc], ad, bd);
-                split0(G, __ldg(hG + (size_t)vm * W + u), ag, bg);
-                split0(F, __ldg(hF + (size_t)vm * W + u), af, bf);
+                split0(G, __ldg(hG + (size_t)u * P + vm), ag, bg);
+                split0(F, __ldg(hF + (size_t)u * P + vm), af, bf);
                 const float2 g0 = c_cjmul(ad, ag), gn = c_cjmul(bd, bg);
                 const float2 f0 = c_mul(ad, af), fn = c_mul(bd, bf);
                 q1[m] = make_float2(g0.x - gn.y, g0.y + gn.x);

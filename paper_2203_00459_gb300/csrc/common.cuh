@@ -147,7 +147,8 @@ struct Ws {
     float2* ahat; // [B][n_theta][n_r] FFT along angle of A_f + i A_g, kept by the forward for the
                   //                  adjoint (NULL: not kept)
     float2* phs;  // [2][B][N/2+1][N] band-limited unit phasors F/|F| of stage 1, kept likewise
-    float2* s2hat;  // [2][B][P][P/2] column spectra of f' and g (both 2D transforms), kept likewise
+    float2* s2hat;  // [2][B][P/2][P] column spectra of f' and g (both 2D transforms), column-major,
+                    //                kept likewise
     // adjoint
     float* bpose; // [pairs][3]       recomputed pose, indexed by pair (handle-wide)
     float* bsc;   // [B][16]          per-pair scalars of the adjoint (d theta at 8)

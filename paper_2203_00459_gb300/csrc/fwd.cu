@@ -436,15 +436,16 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_
         [&](int v) { return v < N ? __ldg(ing + (size_t)v * W) : make_float2(0.f, 0.f); });
     __syncthreads();
     if constexpr (PL::NP == 3) fft_pass2<P, T, PL::R2, 16, -1>(tf + c, tg + c, ES, j, tw);
-    // with s2hat the two transforms are kept for the adjoint ([2][B][P][P/2], row = P-position)
+    // with s2hat the two transforms are kept for the adjoint ([2][B][P/2][P], column-major: the
+    // adjoint's column pass reads each column's P positions in runs)
     float2* kf = s2hat ? s2hat + (size_t)q * P * W : nullptr;
     float2* kg = s2hat ? s2hat + (size_t)(B + q) * P * W : nullptr;
     if (blockIdx.x != 0) {
         fused_turn<P, 0>(tf + c, tg + c, ES, j, tw, [](float2 F, float2 G) { return c_cjmul(F, G); },
                          [&](int pos, float2 F, float2 G) {
                              if (kf) {
-                                 kf[(size_t)pos * W + u0 + c] = F;
-                                 kg[(size_t)pos * W + u0 + c] = G;
+                                 kf[(size_t)(u0 + c) * P + pos] = F;
+                                 kg[(size_t)(u0 + c) * P + pos] = G;
                              }
                          });
     } else {
@@ -453,9 +454,9 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_
         fft_pass2<P, T, RL, NBL, -1>(tf + c, tg + c, ES, j, tw);
         if (kf) {
             for (int idx = threadIdx.x; idx < P * C; idx += TPB) {
-                const int v = idx / C, cc = idx % C;
-                kf[(size_t)v * W + u0 + cc] = tf[spad(v) * ES + cc];
-                kg[(size_t)v * W + u0 + cc] = tg[spad(v) * ES + cc];
+                const int v = idx % P, cc = idx / P;
+                kf[(size_t)(u0 + cc) * P + v] = tf[spad(v) * ES + cc];
+                kg[(size_t)(u0 + cc) * P + v] = tg[spad(v) * ES + cc];
             }
         }
         constexpr int PER = P * C / TPB;

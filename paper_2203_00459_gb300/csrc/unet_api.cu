@@ -68,6 +68,9 @@ struct fmbym_unet {
     int gw_slots = 0;                   // resident CTAs of the flat-GEMM weight gradient
     int conv_path = 0;                  // flat-GEMM convolutions: 0 mma.sync, 1 tcgen05
     unsigned* tc_timeouts = nullptr;    // device counter of tcgen05 CTAs whose wait gave up
+    unsigned tc_spin = kTcSpin;         // polls before a tcgen05 producer's wait gives up
+    unsigned tc_seen = 0;               // counter value the calls have already reported
+    bool tc_ran = false;                // this call launched a tcgen05 convolution
     std::vector<void*> allocs;
     long long launches = 0;
     int last_batch = -1;
@@ -77,6 +80,28 @@ struct fmbym_unet {
 namespace {
 
 thread_local std::string g_unet_create_error;
+
+// After a call that ran tcgen05 convolutions: waits for the stream and reports a CTA that gave up
+// a bounded wait (its outputs are incomplete) as FMBYM_ERR_TIMEOUT.  Calls on the mma.sync path
+// stay asynchronous.
+int tc_status(fmbym_unet* u, cudaStream_t st, const char* what) {
+    if (!u->tc_ran) return FMBYM_OK;
+    u->tc_ran = false;
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, u->tc_timeouts, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        u->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return FMBYM_ERR_CUDA;
+    }
+    if (v != u->tc_seen) {
+        u->err = std::string(what) + ": " + std::to_string(v - u->tc_seen) +
+                 " tcgen05 convolution CTA(s) gave up a bounded wait; their outputs are incomplete";
+        u->tc_seen = v;
+        return FMBYM_ERR_TIMEOUT;
+    }
+    return FMBYM_OK;
+}
 
 int ufail(fmbym_unet* u, int code, const std::string& m) {
     if (u) u->err = m;
@@ -192,14 +217,15 @@ cudaError_t tc_conv_launch(fmbym_unet* u, const Layer& L, int B, bool dgrad, cud
     const int co = dgrad ? L.cin : L.cout, G = (dgrad ? L.coutp : L.cinp) / 8;
     const dim3 grid((unsigned)((long long)B * L.H * L.W / 128), (unsigned)(co / NT));
     ++u->launches;
+    u->tc_ran = true;
     if (dgrad)
         k_conv3x3_tc<NT><<<grid, 256, tc_conv_smem(NT), st>>>(L.dy, L.cout, nullptr, 0, L.wd, G, co, out0, out1,
                                                               split, acc0, acc1, nullptr, B, L.H, L.W,
-                                                              u->tc_timeouts);
+                                                              u->tc_timeouts, u->tc_spin);
     else
         k_conv3x3_tc<NT><<<grid, 256, tc_conv_smem(NT), st>>>(L.in0, L.c0, L.in1, L.c1, L.wf, G, co, out0, out1,
                                                               split, acc0, acc1, stats, B, L.H, L.W,
-                                                              u->tc_timeouts);
+                                                              u->tc_timeouts, u->tc_spin);
     return cudaGetLastError();
 }
 
@@ -553,6 +579,12 @@ int fmbym_unet_set_conv_path(fmbym_unet* u, int path) {
     return FMBYM_OK;
 }
 
+int fmbym_unet_set_tc_wait_limit(fmbym_unet* u, unsigned polls) {
+    if (!u) return ufail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
+    u->tc_spin = polls == 0 ? kTcSpin : polls;
+    return FMBYM_OK;
+}
+
 long long fmbym_unet_tc_timeouts(fmbym_unet* u) {
     if (!u || !u->tc_timeouts) return 0;
     unsigned v = 0;
@@ -705,7 +737,7 @@ int fmbym_unet_forward(fmbym_unet* u, void* stream, int n, const float* f, const
     }
     if (e != cudaSuccess) return ucuda(u, e, "U-Net forward");
     u->last_batch = training ? n : -1;
-    return FMBYM_OK;
+    return tc_status(u, st, "U-Net forward");
 }
 
 int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, const float* g, const float* df_out,
@@ -796,7 +828,7 @@ int fmbym_unet_backward(fmbym_unet* u, void* stream, int n, const float* f, cons
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return ucuda(u, e, "U-Net backward");
-    return FMBYM_OK;
+    return tc_status(u, st, "U-Net backward");
 }
 
 int fmbym_unet_adam(fmbym_unet* u, void* stream, float lr, float beta1, float beta2, float eps, int step) {

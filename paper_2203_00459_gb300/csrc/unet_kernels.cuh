@@ -495,19 +495,42 @@ __global__ void __launch_bounds__(256) k_conv3x3_gemm(const bf16* __restrict__ i
 // commits it to the slot's mbarrier, which the producers wait on before refilling the slot; the
 // accumulator lives in NT TMEM columns.  The epilogue reads TMEM with tcgen05.ld (warp w: lanes
 // 32 (w % 4) .., columns (w / 4) NT / 2 ..), stores, and forms the statistics as k_conv3x3_gemm
-// does.  Every mbarrier wait is bounded: on a timeout the CTA counts it in *timeouts, stops
-// issuing, waits (bounded) for what it issued, frees its TMEM and returns.
+// does.
+//
+// Every mbarrier wait is bounded.  A producer's wait for a slot (the MMAs of the chunk before have
+// read it) gives up after `spin` non-blocking polls (host-settable, kTcSpin by default); the CTA
+// then issues no
+// further MMA, lets its cp.async copies land, and drains: it waits for the commit of the last
+// chunk it issued, which covers every MMA it issued, for up to kTcDrain polls -- MMAs finish in
+// microseconds, kTcDrain is seconds, so it runs out only when the GPU no longer makes progress.
+// Only then does the CTA release its TMEM and exit: no MMA is in flight when its tensor memory
+// or its shared-memory operands change hands.  A CTA that gave up counts itself in *timeouts and
+// writes no output; the host turns the count into FMBYM_ERR_TIMEOUT.
 __host__ __device__ constexpr size_t tc_conv_smem(int NT) { return kGStages * (size_t)(128 + NT) * kGK * 16; }
-constexpr unsigned kTcSpin = 1u << 22;   // mbarrier polls before a wait gives up
+constexpr unsigned kTcSpin = 1u << 22;   // default polls before a producer's wait gives up
+constexpr unsigned kTcDrain = 1u << 28;  // polls of the drain before the CTA releases its TMEM
 
 __device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
     return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
            ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+// Up to `limit` non-blocking tests of the barrier's phase (a producer's wait: the limit counts
+// polls exactly, however short).
+__device__ __forceinline__ bool mbar_poll(unsigned bar, unsigned parity, unsigned limit) {
     unsigned done = 0;
-    for (unsigned it = 0; it < kTcSpin && !done; ++it)
+    for (unsigned it = 0; it < limit && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+    return done != 0;
+}
+
+// Up to `limit` potentially blocking waits for the barrier's phase (the drain).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned limit) {
+    unsigned done = 0;
+    for (unsigned it = 0; it < limit && !done; ++it)
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
                      : "r"(bar), "r"(parity)
@@ -520,7 +543,7 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(const bf16* __restrict__ in0
                                                     int c1, const bf16* __restrict__ wt, int G, int cout,
                                                     float* __restrict__ out0, float* __restrict__ out1, int split,
                                                     int acc0, int acc1, float2* __restrict__ stats, int B, int H,
-                                                    int W, unsigned* __restrict__ timeouts) {
+                                                    int W, unsigned* __restrict__ timeouts, unsigned spin) {
     constexpr int MT = 128;
     constexpr size_t SLOT = (size_t)(MT + NT) * kGK * 16;
     extern __shared__ __align__(1024) unsigned char smem_t[];
@@ -590,7 +613,7 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(const bf16* __restrict__ in0
         if (nk < nchunk) {
             if (nk >= kGStages) {   // the slot's previous chunk (kc - 1) must have been consumed
                 const unsigned bar = (unsigned)__cvta_generic_to_shared(&mbar[nk % kGStages]);
-                if (!mbar_wait(bar, (unsigned)(((nk - kGStages) / kGStages) & 1))) failed = 1;
+                if (!mbar_poll(bar, (unsigned)(((nk - kGStages) / kGStages) & 1), spin)) failed = 1;
             }
             __syncthreads();
             if (failed) break;
@@ -618,12 +641,13 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(const bf16* __restrict__ in0
         issued = kc + 1;
     }
     cp_async_wait_n(0);
-    // the last committed chunk's barrier covers every MMA issued before it; the outcome is shared
-    // so that the whole CTA takes the same branch around the warp-collective TMEM loads
+    // drain: the last committed chunk's barrier covers every MMA issued before it (after a
+    // producer gave up too); the outcome is shared so that the whole CTA takes the same branch
+    // around the warp-collective TMEM loads
     if (issued > 0) {
         const int last = issued - 1;
         const unsigned bar = (unsigned)__cvta_generic_to_shared(&mbar[last % kGStages]);
-        if (!mbar_wait(bar, (unsigned)((last / kGStages) & 1))) failed = 1;
+        if (!mbar_wait(bar, (unsigned)((last / kGStages) & 1), kTcDrain)) failed = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();

@@ -153,3 +153,7 @@ class MaskNet:
 
     def tc_timeouts(self):
         return int(_lib.lib().fmbym_unet_tc_timeouts(self._h))
+
+    def set_tc_wait_limit(self, polls):
+        """Polls before a tcgen05 producer's slot wait gives up (0: the default)."""
+        _lib.check_unet(_lib.lib().fmbym_unet_set_tc_wait_limit(self._h, int(polls)), self._h)

@@ -300,3 +300,33 @@ def test_tcgen05_and_mma_paths_agree(mn):
     scale = np.concatenate([np.concatenate([np.sqrt(np.abs(ref[k + co:k + 2 * co])), np.abs(ref[k + co:k + 2 * co])])
                             for k, co in _running_blocks(TAB2)])
     assert np.max(np.abs(r1.numpy() - ref) / (np.abs(ref) + scale + 1e-6)) <= 1e-2
+
+
+def test_tcgen05_wait_that_runs_out_returns_timeout_and_the_handle_recovers(mn):
+    """A producer's slot wait cut to one poll runs out while the slot's MMAs are in flight: the CTA
+    stops issuing, drains the MMAs it issued, frees its tensor memory and counts itself, and the
+    forward returns FMBYM_ERR_TIMEOUT.  With the default limit restored the same handle runs the
+    same forward again, with no new timeout and the masks of an untouched twin handle."""
+    from paper_2203_00459_gb300 import _lib
+    f, g = scans(256, 2, start=23)
+    ft, gt = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    twin, _ = setup(mn, TAB2, 256, 2, seed=7)
+    twin.set_conv_path(1)
+    _, _, m_ref = twin.forward(ft, gt, training=False, want_masks=True)
+    torch.cuda.synchronize()
+    net, _ = setup(mn, TAB2, 256, 2, seed=7)
+    net.set_conv_path(1)
+    net.set_tc_wait_limit(1)
+    with pytest.raises(_lib.FmbymError) as e:
+        net.forward(ft, gt, training=False, want_masks=True)
+    assert e.value.status == _lib.ERR_TIMEOUT
+    n_out = net.tc_timeouts()
+    assert n_out > 0
+    net.set_tc_wait_limit(0)
+    _, _, m = net.forward(ft, gt, training=False, want_masks=True)
+    torch.cuda.synchronize()
+    assert net.tc_timeouts() == n_out
+    assert torch.equal(m, m_ref)
+    assert twin.tc_timeouts() == 0
+    net.close()
+    twin.close()
