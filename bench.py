@@ -292,9 +292,39 @@ def run_mixed(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+
+    # the same step for one size group at a time (its mask inference and its search call alone),
+    # to see what running the groups concurrently on forked streams gains over running them
+    # back to back: the sum of the lone groups against the mixed call
+    def group_step(s):
+        net, st, cnt, n = nets[s]
+        view = lambda t: t[st:st + cnt * n * n].view(cnt, n, n)
+        net.forward(view(F), view(G), training=False, f_out=view(FM), g_out=view(GM))
+        idx = per[s]
+        k = len(idx)
+        search.pose_train(FM, GM, gt, kind=1, size_idx=np.full(k, s, np.int32), offsets=offs[idx],
+                          out=(pose[:k], loss, dpose[:k], dF, dG))
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    alone = {}
+    gt_full = gt
+    for s in range(3):
+        gt = gt_full[torch.from_numpy(per[s]).cuda()].contiguous()
+        for _ in range(2):
+            group_step(s)
+        ms_s = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            group_step(s)
+            b.record()
+            torch.cuda.synchronize()
+            ms_s.append(a.elapsed_time(b))
+        alone[str(cfgs[s]["n"])] = sum(ms_s) / len(ms_s)
+    gt = gt_full
     l0 = L.fmbym_launch_count(search.handle) + sum(net.launch_count() for net, *_ in nets)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
     for k in range(args.steps):
         flush.zero_()
         evs[k][0].record()
@@ -303,12 +333,18 @@ def run_mixed(args):
     torch.cuda.synchronize()
     launches = L.fmbym_launch_count(search.handle) + sum(net.launch_count() for net, *_ in nets) - l0
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    concurrency = {"alone_ms_per_size": {k: round(v, 4) for k, v in alone.items()},
+                   "sum_alone_ms": round(sum(alone.values()), 4), "mixed_ms": round(ms, 4),
+                   "gain_of_concurrent_groups": round(sum(alone.values()) / ms, 3),
+                   "note": "each size group's step timed alone (mask inference + pose_train of its pairs) "
+                           "against the mixed call that runs the three groups on forked streams"}
     line = {"metric": "scan-pairs/s, uneven batch with mask inference, search fwd+bwd", "value": len(order) / (ms * 1e-3),
             "unit": "scan-pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 search, bf16 mask",
             "data": "synthetic", "gpu_launches": int(launches),
             "config": {"workload": "mixed", "pairs": {"128": counts[0], "256": counts[1], "512": counts[2]},
-                       "mask_levels": {"128": 3, "256": 4, "512": 4}, "l2": "flushed between timed steps"}}
+                       "mask_levels": {"128": 3, "256": 4, "512": 4}, "l2": "flushed between timed steps"},
+            "concurrency": concurrency}
     print(json.dumps(line), flush=True)
 
 

@@ -35,8 +35,11 @@ def init_params(channels=(8, 16, 32, 64), seed=1):
 class MaskedSearch:
     """The masking network in front of the decoupled search, trained through it."""
 
-    def __init__(self, n=256, n_theta=400, n_r=128, channels=(8, 16, 32, 64), batch=64, seed=1, loss_kind=1):
-        self.cfg = size_cfg(n, n_theta, n_r)
+    def __init__(self, n=256, n_theta=400, n_r=128, channels=(8, 16, 32, 64), batch=64, seed=1, loss_kind=1,
+                 delta_xy=1.0):
+        # delta_xy: the cell size in the units the translation is wanted in (Alg. 1's delta_xy); the
+        # pose's translation, and the ground truth given to train_step, are in those units
+        self.cfg = size_cfg(n, n_theta, n_r, delta_xy=delta_xy)
         self.search = PoseSearch([self.cfg], max_pairs=batch)
         self.net = masknet.MaskNet(channels, n, n, max_batch=batch)
         self.net.load(init_params(channels, seed).cuda())

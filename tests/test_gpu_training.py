@@ -1,7 +1,7 @@
-"""What the learned mask gains (Sec. III-D, Tab. IIIb in spirit): the masking network trained end to end
+"""What the learned mask gains (Sec. III-E, Tab. IIIb in spirit): the masking network trained end to end
 through the decoupled search on synthetic trajectories (moving scatterers, fresh per-frame speckle)
-lowers the translation error on held-out pairs, judged against ground truth and against the
-unmasked search -- both the GPU search and the FP64 oracle."""
+lowers the translation error on held-out pairs, over three seeds, judged against ground truth and
+against the unmasked search -- both the GPU search and the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -18,34 +18,45 @@ def _oracle_errors(args):
 
 
 def test_trained_mask_lowers_translation_error():
+    """Three seeds of the network's initial weights, each trained 400 steps (12.5 epochs of 2048
+    pairs), judged by the mean over the seeds of the held-out error at the last three checkpoints.
+    Measured on a GB300: translation error 0.708 / 0.774 / 0.733 of the unmasked search (mean
+    0.738), heading error 1.106 / 1.130 / 1.067 of it (mean 1.10).  The L1 loss of Eq. 13 is
+    dominated by the translation (pixels, or metres at 0.4 m cells, against radians), and a
+    multiplicative mask blurs the magnitude spectrum that the heading is read from, so the heading
+    is held to a bounded regression, not to a gain."""
     from paper_2203_00459_gb300 import build
     build.build()
     from paper_2203_00459_gb300 import train
     F, G, P = train.trajectory_data(64, 33, 20220304, parallel=True)     # 2048 training pairs
     Fe, Ge, Pe = train.trajectory_data(16, 17, 20229999, parallel=True)  # 256 held-out pairs
-    ms = train.MaskedSearch(batch=64, seed=1)
     Ft, Gt = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
     Pt = torch.from_numpy(P.astype(np.float32)).cuda()
     Fe_t, Ge_t = torch.from_numpy(Fe).cuda(), torch.from_numpy(Ge).cuda()
-    plain = ms.poses(Fe_t, Ge_t, masked=False).cpu().numpy()
-    rng = np.random.default_rng(0)
     nb = F.shape[0] // 64
-    # Adam at 2e-3, then 5e-4 from step 300: at a constant rate the held-out error of the mask jumps
-    # by +-15 % between neighbouring checkpoints, after the decay it settles, and the mean of the
-    # last three checkpoints is what is judged
-    masked = []
-    for step in range(400):   # 12.5 epochs of the 2048 pairs
-        if step % nb == 0:
-            perm = torch.from_numpy(rng.permutation(F.shape[0])).cuda()
-        idx = perm[(step % nb) * 64:(step % nb + 1) * 64]
-        ms.train_step(Ft[idx].contiguous(), Gt[idx].contiguous(), Pt[idx].contiguous(),
-                      lr=2e-3 if step < 300 else 5e-4)
-        if step + 1 in (320, 360, 400):
-            masked.append(ms.poses(Fe_t, Ge_t, masked=True).cpu().numpy())
-    torch.cuda.synchronize()
-    ms.close()
+    plain, per_seed = None, []
+    for seed in (1, 2, 3):
+        ms = train.MaskedSearch(batch=64, seed=seed)
+        if plain is None:
+            plain = ms.poses(Fe_t, Ge_t, masked=False).cpu().numpy()
+        rng = np.random.default_rng(0)
+        # Adam at 2e-3, then 5e-4 from step 300: at a constant rate the held-out error of the mask
+        # jumps by +-15 % between neighbouring checkpoints, after the decay it settles, and the mean
+        # of the last three checkpoints is what is judged
+        masked = []
+        for step in range(400):
+            if step % nb == 0:
+                perm = torch.from_numpy(rng.permutation(F.shape[0])).cuda()
+            idx = perm[(step % nb) * 64:(step % nb + 1) * 64]
+            ms.train_step(Ft[idx].contiguous(), Gt[idx].contiguous(), Pt[idx].contiguous(),
+                          lr=2e-3 if step < 300 else 5e-4)
+            if step + 1 in (320, 360, 400):
+                masked.append(ms.poses(Fe_t, Ge_t, masked=True).cpu().numpy())
+        torch.cuda.synchronize()
+        ms.close()
+        per_seed.append(np.mean([train.pose_errors(m, Pe) for m in masked], axis=0))
     e_plain = train.pose_errors(plain, Pe)
-    e_mask = np.mean([train.pose_errors(m, Pe) for m in masked], axis=0)
+    e_mask = np.mean(per_seed, axis=0)
     # the FP64 oracle's unmasked search on the same held-out pairs
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(16) as pool:
@@ -57,11 +68,10 @@ def test_trained_mask_lowers_translation_error():
     assert np.max(np.abs(plain[:, 1:] - orc[:, 4:])) <= 1e-3
     t_plain, t_mask, t_orc = e_plain[1:].sum(), e_mask[1:].sum(), e_orc[1:].sum()
     print("held-out mean |error| (theta rad, tx px, ty px): unmasked GPU", e_plain, "FP64 oracle", e_orc,
-          "trained mask", e_mask)
+          "trained mask, per seed", per_seed)
     assert t_mask <= 0.88 * t_plain and t_mask <= 0.88 * t_orc, (e_mask, e_plain, e_orc)
-    # the summed L1 loss of Eq. 13 is dominated by the translation (pixels against radians), so the
-    # mask is judged on translation; the heading must not get materially worse
-    assert e_mask[0] <= 1.25 * e_plain[0]
+    assert all(e[1:].sum() <= 0.95 * t_plain for e in per_seed), per_seed   # every seed gains
+    assert e_mask[0] <= 1.15 * e_plain[0], (e_mask, e_plain)
 
 
 def test_checkpoint_resume_is_bitwise(tmp_path):
