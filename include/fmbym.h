@@ -226,8 +226,11 @@ int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_
  * and df, dg (host float32, total_elems each) back, and synchronises the stream.  Elements of df
  * and dg outside every pair's scan are unspecified.  total_elems must not exceed what max_pairs
  * scans of the largest configured size hold (FMBYM_ERR_WORKSPACE).  Pinned host memory makes the
- * copies asynchronous with respect to the host; pageable memory works but copies slower.  Errors
- * as fmbym_pose_train. */
+ * copies asynchronous with respect to the host; pageable memory works but copies slower.  A packed
+ * call (offsets NULL) of 16 pairs or more runs as a pipeline of up to 4 chunks of pairs, the copies
+ * in and out on the handle's own streams overlapping the chunks' training calls; the results are
+ * those of the one-piece call (each chunk's loss is normalised by the call's pair count, and the
+ * loss is taken over every pair at the end).  Errors as fmbym_pose_train. */
 int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx,
                           const long long* offsets, long long total_elems, const float* f_host,
                           const float* g_host, const float* gt_host, int loss_kind, float* pose_host,

@@ -63,7 +63,9 @@ struct fmbym_handle {
     float* d_stage_pose = nullptr;
     float* d_stage_df = nullptr;  // [stage_elems] each: the training call's gradients
     float* d_stage_dg = nullptr;
-    float* d_stage_small = nullptr;  // [max_pairs][3] gt, [max_pairs][3] dpose, [1] loss
+    float* d_stage_small = nullptr;  // [max_pairs][3] gt, [max_pairs][3] dpose, [1] loss, [1] chunk loss
+    cudaStream_t s_in = nullptr, s_out = nullptr;   // host-buffer training call: copy streams
+    cudaEvent_t ev_start = nullptr, ev_in[4] = {}, ev_done[4] = {};
     unsigned* d_cnt = nullptr;    // [max_pairs] completion counters, zero between launches
     float* d_bpose = nullptr;     // [max_pairs][3] pose recomputed by the adjoint
     float4* d_best = nullptr;     // [max_pairs] running best of the exhaustive search
@@ -415,6 +417,7 @@ struct LaunchArgs {
     int loss_kind;        // kind 2: 1 = L1 (Eq. 13), 2 = L2
     float* loss;          // kind 2: the loss (device scalar)
     float* dpose_out;     // kind 2: dL/dpose, written by the loss and read by the adjoint
+    int norm_pairs;       // kind 2: the count the loss averages over (0: this call's pairs)
 };
 
 // phase 0 launches the forward of one size group, phase 1 its adjoint (after a forward recompute
@@ -469,7 +472,8 @@ cudaError_t enqueue(fmbym_handle* h, cudaStream_t st, const std::vector<Group>& 
                     const LaunchArgs& a, int n_pairs) {
     if (a.kind != 2) return enqueue_phase(h, st, groups, dtab, a, a.kind);
     cudaError_t e = enqueue_phase(h, st, groups, dtab, a, 0);
-    if (e == cudaSuccess) e = launch_pose_loss(n_pairs, a.pose, a.gt, a.loss_kind, a.loss, a.dpose_out, &h->tracer, st);
+    if (e == cudaSuccess)
+        e = launch_pose_loss(n_pairs, a.pose, a.gt, a.loss_kind, a.loss, a.dpose_out, &h->tracer, st, a.norm_pairs);
     if (e == cudaSuccess) e = enqueue_phase(h, st, groups, dtab, a, 1);
     return e;
 }
@@ -489,7 +493,7 @@ int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Gr
                                       (long long)(uintptr_t)a.c_xy, (long long)(uintptr_t)a.dpose,
                                       (long long)(uintptr_t)a.df, (long long)(uintptr_t)a.dg,
                                       (long long)(uintptr_t)a.gt, a.loss_kind, (long long)(uintptr_t)a.loss,
-                                      (long long)(uintptr_t)a.dpose_out};
+                                      (long long)(uintptr_t)a.dpose_out, a.norm_pairs};
         key.insert(key.end(), h->h_tab, h->h_tab + 3 * (size_t)n_pairs);
         GraphEntry* ge = nullptr;
         for (auto& x : h->graphs)
@@ -690,6 +694,13 @@ void fmbym_destroy(fmbym_handle* h) {
     cudaFree(h->d_stage_df);
     cudaFree(h->d_stage_dg);
     cudaFree(h->d_stage_small);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    for (int c = 0; c < 4; ++c) {
+        if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
+        if (h->ev_done[c]) cudaEventDestroy(h->ev_done[c]);
+    }
     cudaFree(h->d_cnt);
     cudaFree(h->d_bpose);
     cudaFree(h->d_best);
@@ -775,7 +786,10 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
         (e = cudaMalloc(&h->d_stage_pose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_df, sizeof(float) * h->stage_elems)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_dg, sizeof(float) * h->stage_elems)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_stage_small, sizeof(float) * (6 * (size_t)cfg->max_pairs + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_stage_small, sizeof(float) * (6 * (size_t)cfg->max_pairs + 2))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_bpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
@@ -783,6 +797,14 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
         (e = cudaMalloc(&h->d_fcpose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess) {
         fmbym_destroy(h);
         return cuda_fail(nullptr, e, "staging allocation");
+    }
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+        if ((e = cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming)) == cudaSuccess)
+            e = cudaEventCreateWithFlags(&h->ev_done[c], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        fmbym_destroy(h);
+        return cuda_fail(nullptr, e, "copy events");
     }
     if (cfg->flags & FMBYM_FLAG_AUTOTUNE) {
         const int rc = autotune(h);
@@ -983,32 +1005,94 @@ int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int*
     float* d_gt = h->d_stage_small;
     float* d_dpose = h->d_stage_small + 3 * (size_t)h->max_pairs;
     float* d_loss = h->d_stage_small + 6 * (size_t)h->max_pairs;
-    const size_t bytes = sizeof(float) * (size_t)total_elems;
+    float* d_chunk_loss = d_loss + 1;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(h->d_stage_f, f_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(h->d_stage_g, g_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_gt, gt_host, sizeof(float) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_fail(h, e, "host-to-device copy");
     LaunchArgs a{};
     a.kind = 2;
     a.f = h->d_stage_f;
     a.g = h->d_stage_g;
-    a.pose = h->d_stage_pose;
     a.gt = d_gt;
     a.loss_kind = loss_kind;
-    a.loss = d_loss;
-    a.dpose_out = d_dpose;
     a.df = h->d_stage_df;
     a.dg = h->d_stage_dg;
-    rc = run_call(h, st, n_pairs, groups, a);
-    if (rc != FMBYM_OK) return rc;
-    if ((e = cudaMemcpyAsync(pose_host, h->d_stage_pose, sizeof(float) * 3 * n_pairs, cudaMemcpyDeviceToHost, st)) !=
+    // Packed pairs (offsets NULL) of a large enough call run as a pipeline of up to 4 chunks of
+    // pairs: chunk c's copies in (stream s_in) overlap chunk c - 1's training call (the caller's
+    // stream), and chunk c - 1's gradients go back (stream s_out) while chunk c computes.  Each
+    // chunk's loss is normalised by the whole call's pair count, so dpose, pose, df and dg are
+    // those of the one-piece call; the call's loss is then taken over all pairs at the end.
+    const int chunks = (!offsets && n_pairs >= 16) ? std::min(4, n_pairs / 8) : 1;
+    if (chunks == 1) {
+        const size_t bytes = sizeof(float) * (size_t)total_elems;
+        if ((e = cudaMemcpyAsync(h->d_stage_f, f_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(h->d_stage_g, g_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d_gt, gt_host, sizeof(float) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess)
+            return cuda_fail(h, e, "host-to-device copy");
+        a.pose = h->d_stage_pose;
+        a.loss = d_loss;
+        a.dpose_out = d_dpose;
+        rc = run_call(h, st, n_pairs, groups, a);
+        if (rc != FMBYM_OK) return rc;
+        if ((e = cudaMemcpyAsync(pose_host, h->d_stage_pose, sizeof(float) * 3 * n_pairs, cudaMemcpyDeviceToHost,
+                                 st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(loss_host, d_loss, sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(df_host, h->d_stage_df, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(dg_host, h->d_stage_dg, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(h, e, "device-to-host copy");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+        return FMBYM_OK;
+    }
+    // element offset of every pair in the packed layout, and the chunk boundaries
+    std::vector<long long> off(n_pairs + 1, 0);
+    for (int i = 0; i < n_pairs; ++i) {
+        const long long nn = (long long)h->plans[size_idx ? size_idx[i] : 0].cfg.n;
+        off[i + 1] = off[i] + nn * nn;
+    }
+    if ((e = cudaEventRecord(h->ev_start, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h->s_in, h->ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h->s_out, h->ev_start, 0)) != cudaSuccess)
+        return cuda_fail(h, e, "copy stream fork");
+    for (int c = 0; c < chunks; ++c) {
+        const int i0 = (int)((long long)n_pairs * c / chunks), i1 = (int)((long long)n_pairs * (c + 1) / chunks);
+        const size_t e0 = (size_t)off[i0], ne = (size_t)(off[i1] - off[i0]);
+        if ((e = cudaMemcpyAsync(h->d_stage_f + e0, f_host + e0, sizeof(float) * ne, cudaMemcpyHostToDevice, h->s_in)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(h->d_stage_g + e0, g_host + e0, sizeof(float) * ne, cudaMemcpyHostToDevice, h->s_in)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(d_gt + 3 * (size_t)i0, gt_host + 3 * (size_t)i0, sizeof(float) * 3 * (i1 - i0),
+                                 cudaMemcpyHostToDevice, h->s_in)) != cudaSuccess ||
+            (e = cudaEventRecord(h->ev_in[c], h->s_in)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, h->ev_in[c], 0)) != cudaSuccess)
+            return cuda_fail(h, e, "host-to-device copy");
+        std::vector<Group> cg;
+        rc = make_table(h, i1 - i0, size_idx ? size_idx + i0 : nullptr, off.data() + i0, cg, nullptr);
+        if (rc != FMBYM_OK) return rc;
+        LaunchArgs ac = a;
+        ac.gt = d_gt + 3 * (size_t)i0;
+        ac.pose = h->d_stage_pose + 3 * (size_t)i0;
+        ac.dpose_out = d_dpose + 3 * (size_t)i0;
+        ac.loss = d_chunk_loss;
+        ac.norm_pairs = n_pairs;
+        rc = run_call(h, st, i1 - i0, cg, ac);
+        if (rc != FMBYM_OK) return rc;
+        if ((e = cudaEventRecord(h->ev_done[c], st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->s_out, h->ev_done[c], 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(df_host + e0, h->d_stage_df + e0, sizeof(float) * ne, cudaMemcpyDeviceToHost,
+                                 h->s_out)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(dg_host + e0, h->d_stage_dg + e0, sizeof(float) * ne, cudaMemcpyDeviceToHost,
+                                 h->s_out)) != cudaSuccess)
+            return cuda_fail(h, e, "device-to-host copy");
+    }
+    // the call's loss over every pair (the chunks' losses were partial)
+    if ((e = launch_pose_loss(n_pairs, h->d_stage_pose, d_gt, loss_kind, d_loss, nullptr, &h->tracer, st)) !=
             cudaSuccess ||
-        (e = cudaMemcpyAsync(loss_host, d_loss, sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(df_host, h->d_stage_df, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(dg_host, h->d_stage_dg, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        (e = cudaMemcpyAsync(pose_host, h->d_stage_pose, sizeof(float) * 3 * n_pairs, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(loss_host, d_loss, sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(h, e, "device-to-host copy");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess || (e = cudaStreamSynchronize(h->s_out)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->s_in)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaStreamSynchronize");
     return FMBYM_OK;
 }
 

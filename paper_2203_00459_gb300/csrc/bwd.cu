@@ -676,13 +676,14 @@ __global__ void __launch_bounds__(kThreads) k_b_s1rows_odd(DevPlan p, const long
 // ---------------------------------------------------------------------------------------------
 
 // L = mean over pairs of sum over (theta, t_x, t_y) of |pose - gt| (kind 1, Eq. 13) or
-// (pose - gt)^2 (kind 2); dpose = dL/dpose.  One block; fixed-order reduction.
-__global__ void __launch_bounds__(256) k_pose_loss(int n_pairs, const float* __restrict__ pose,
+// (pose - gt)^2 (kind 2); dpose = dL/dpose.  One block; fixed-order reduction.  The mean is over
+// norm_pairs pairs (n_pairs, or the whole call when these pairs are one chunk of it).
+__global__ void __launch_bounds__(256) k_pose_loss(int n_pairs, int norm_pairs, const float* __restrict__ pose,
                                                    const float* __restrict__ gt, int kind, float* __restrict__ loss,
                                                    float* __restrict__ dpose) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
     __shared__ float red[32];
-    const float inv = 1.f / (float)n_pairs;
+    const float inv = 1.f / (float)norm_pairs;
     float acc = 0.f;
     for (int i = threadIdx.x; i < 3 * n_pairs; i += blockDim.x) {
         const float d = pose[i] - gt[i];
@@ -702,9 +703,9 @@ __global__ void __launch_bounds__(256) k_pose_loss(int n_pairs, const float* __r
 }
 
 cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, int kind, float* loss, float* dpose,
-                             Tracer* tr, cudaStream_t st) {
+                             Tracer* tr, cudaStream_t st, int norm_pairs) {
     tr->before(K_LOSS, st);
-    launch_pdl(k_pose_loss, 1, 256, 0, st, n_pairs, pose, gt, kind, loss, dpose);
+    launch_pdl(k_pose_loss, 1, 256, 0, st, n_pairs, norm_pairs > 0 ? norm_pairs : n_pairs, pose, gt, kind, loss, dpose);
     tr->close(st);
     return cudaGetLastError();
 }

@@ -186,8 +186,9 @@ cudaError_t launch_forward(const DevPlan& p, const Ws& w, int B, const long long
 cudaError_t launch_backward(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                             const float* g, const float* dpose, float* df, float* dg, cudaStream_t st,
                             const float* fwd_pose);
+// norm_pairs: the count the mean divides by (0: n_pairs)
 cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, int kind, float* loss, float* dpose,
-                             Tracer* tr, cudaStream_t st);
+                             Tracer* tr, cudaStream_t st, int norm_pairs = 0);
 cudaError_t prepare_kernels();
 
 }  // namespace fmbym
