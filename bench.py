@@ -35,12 +35,42 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwd", "fwdbwd"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "mixed", "masked256", "masked256_tab2"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batch256", "batch511", "batch255", "batch127", "mixed", "masked256",
+                             "masked256_tab2"])
     ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1],
                     help="masked workloads: the mask network's flat-GEMM convolutions on mma.sync (0) or tcgen05 (1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="for profilers: W + K training calls of --pairs pairs of the workload, launched directly "
+                         "with the default schedules, and nothing else")
+    ap.add_argument("--pairs", type=int, default=0, help="with --profile: pairs per call (default: the workload's)")
     return ap.parse_args()
+
+
+def run_profile(args):
+    """W + K training calls (or forwards, --mode fwd) of the workload, launched kernel by kernel
+    with the default launch schedules, for a profiler to capture; prints one short line."""
+    import numpy as np
+    import torch
+    from paper_2203_00459_gb300 import build, synth
+    build.build()
+    from paper_2203_00459_gb300.search import PoseSearch, size_cfg
+    spec = synth.WORKLOADS[args.workload]
+    B = args.pairs or spec["pairs"]
+    f, g, gt = synth.make_batch(args.workload, pairs=B)
+    s = PoseSearch([size_cfg(spec["n"], spec["n_theta"], spec["n_r"])], max_pairs=B)
+    F, G = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    GT = torch.from_numpy(gt.astype(np.float32)).cuda()
+    for _ in range(args.warmup + args.steps):
+        if args.mode == "fwdbwd":
+            out = s.pose_train(F, G, GT, kind=2)
+        else:
+            out = (s.pose(F, G)["pose"],)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.workload, "pairs": B, "calls": args.warmup + args.steps, "mode": args.mode}))
+    s.close()
 
 
 # ---------------------------------------------------------------------------------------------
@@ -639,6 +669,8 @@ def run_masked256(args):
 
 def main():
     args = parse()
+    if args.profile:
+        return run_profile(args)
     from paper_2203_00459_gb300 import synth
     if args.workload == "mixed" and args.impl == "ours":
         return run_mixed(args)
@@ -770,7 +802,7 @@ def main():
 
     # ---- dominant kernel roofline ----
     chunks = (nr + 15) // 16
-    model = kernel_model(n, 3 * n // 2, nt, nr, chunks)   # zero padding to P = 1.5 N
+    model = kernel_model(n, 3 * (n + (n & 1)) // 2, nt, nr, chunks)   # zero padding to P = 1.5 N (its even frame)
     total_ms = sum(v[0] for v in kernels.values())
     dom = max(kernels, key=lambda k: kernels[k][0]) if kernels else None
     peaks, peak_src = measured_peaks()
