@@ -110,12 +110,13 @@ def kernel_model(n, p, nt, nr, chunks):
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel:
 # (bytes, hash of the search sources it was taken on, pairs in that launch, column tile of the
 # variant).  Reported, scaled to the launch's pairs, only while the sources are unchanged and the
-# autotuner picked the same variant.  k_b_cols<512, 768, 4> over 32 pairs at 512^2:
-#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
-#       --clock-control none -k regex:k_b_cols -s 2 -c 1 --csv \
-#       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-plain
-#   -> 201,415,680 read + 72,549,888 written (cold cache: ncu flushes the caches before the launch)
-TRAFFIC = {"b_cols": (201415680 + 72549888, "da95872a5357c0e8", 32, 4)}
+# autotuner picked the same variant.  k_b_cols<512, 768, 4> over 32 pairs at 512^2 (the third of
+# three training calls; ncu flushes the caches before the launch):
+#   python bench.py --profile --pairs 32 --steps 2 --warmup 1 &&
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
+#       -k regex:k_b_cols -s 2 -c 1 --csv python bench.py --profile --pairs 32 --steps 2 --warmup 1
+#   -> 201,434,112 read + 69,799,168 written, 99.5 us
+TRAFFIC = {"b_cols": (201434112 + 69799168, "407ca928d53bf3b4", 32, 4)}
 
 
 # the sources that define, plan and launch the adjoint kernels (k_b_cols among them)
