@@ -21,7 +21,8 @@ def search():
     return s
 
 
-@pytest.mark.parametrize("name,n,nt,nr,pairs", [("single128", 128, 128, 64, 3), ("batch256", 256, 400, 128, 2)])
+@pytest.mark.parametrize("name,n,nt,nr,pairs", [("single128", 128, 128, 64, 3), ("batch256", 256, 400, 128, 2),
+                                                 ("batch127", 127, 128, 63, 2)])   # 127: an odd side
 def test_exhaustive_matches_oracle(search, name, n, nt, nr, pairs):
     cfg = search.size_cfg(n, nt, nr)
     f, g, gt = synth.make_batch(name, pairs=pairs, start=7)

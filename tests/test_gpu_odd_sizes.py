@@ -158,3 +158,27 @@ def test_odd_side_with_circular_padding_is_refused(lib):
     with pytest.raises(_lib.FmbymError) as e:
         search.PoseSearch([search.size_cfg(255, 400, 127, pad_mode=1)], max_pairs=1)
     assert e.value.status == _lib.ERR_UNSUPPORTED_SIZE
+
+
+def test_autotuned_graph_handle_at_255_equals_a_plain_handle(lib):
+    """The autotuner (timed training calls of every schedule) and the graph cache at an odd side:
+    the tuned, graph-replayed handle's forward and training call against a plain handle's with the
+    same schedules, bitwise."""
+    search, _lib = lib
+    f, g, gt = synth.make_batch("batch255", pairs=6, start=90)
+    cfg = cfg_of(search, "batch255")
+    tuned = search.PoseSearch([cfg], max_pairs=6, flags=_lib.FLAG_GRAPH | _lib.FLAG_AUTOTUNE)
+    plain = search.PoseSearch([cfg], max_pairs=6)
+    plain.set_tuning(0, **tuned.tuning(0))
+    F, G = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    GT = torch.from_numpy(gt.astype(np.float32)).cuda()
+    for _ in range(2):   # the second call replays the captured graphs
+        a = tuned.pose(F, G, want_c_xy=True)
+        b = plain.pose(F, G, want_c_xy=True)
+        ta = tuned.pose_train(F, G, GT, kind=2)
+        tb = plain.pose_train(F, G, GT, kind=2)
+        torch.cuda.synchronize()
+        assert torch.equal(a["pose"], b["pose"]) and torch.equal(a["c_xy"], b["c_xy"])
+        assert all(torch.equal(x, y) for x, y in zip(ta, tb))
+    tuned.close()
+    plain.close()
