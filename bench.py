@@ -542,6 +542,71 @@ def angle_count_comparison(fma_peak, pairs=64, steps=10, warmup=3):
     return out
 
 
+def mixed_concurrency(counts=(64, 45, 19), steps=10, warmup=3):
+    """The uneven mix's size groups in one training call (concurrent groups on forked streams,
+    graph replay) against each group's training call alone, back to back: 128 pairs in the
+    proportions of the 512-pair mixed workload (50 / 35 / 15 % at 128^2, 256^2, 512^2), search
+    only.  If the groups left SMs idle at their tails, the mixed call would beat the sum of the
+    lone calls by the idle time."""
+    import numpy as np
+    import torch
+    from paper_2203_00459_gb300 import _lib, synth
+    from paper_2203_00459_gb300.search import PoseSearch, size_cfg
+    names = ["single128", "batch256", "batch512"]
+    cfgs = [size_cfg(128, 128, 64), size_cfg(256, 400, 128), size_cfg(512, 400, 256)]
+    order = np.concatenate([np.full(c, k) for k, c in enumerate(counts)])
+    np.random.default_rng(5).shuffle(order)
+    per = [np.flatnonzero(order == k) for k in range(3)]
+    sizes = [c["n"] ** 2 for c in cfgs]
+    offs = np.zeros(len(order), np.int64)
+    base = 0
+    F = []
+    G = []
+    gts = np.zeros((len(order), 3), np.float32)
+    for k in range(3):
+        offs[per[k]] = base + np.arange(len(per[k])) * sizes[k]
+        base += len(per[k]) * sizes[k]
+        f, g, gt = synth.make_batch(names[k], pairs=len(per[k]), spec=dict(synth.WORKLOADS[names[k]], pairs=len(per[k])))
+        F.append(f.ravel())
+        G.append(g.ravel())
+        gts[per[k]] = gt
+    Ft, Gt = torch.from_numpy(np.concatenate(F)).cuda(), torch.from_numpy(np.concatenate(G)).cuda()
+    GT = torch.from_numpy(gts).cuda()
+    s = PoseSearch(cfgs, max_pairs=len(order), flags=_lib.FLAG_GRAPH)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    n = len(order)
+    pose, dpose = torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda")
+    loss, dF, dG = torch.empty(1, device="cuda"), torch.empty_like(Ft), torch.empty_like(Gt)
+
+    def call(idx, si):
+        k = len(idx)
+        s.pose_train(Ft, Gt, GT[torch.from_numpy(idx).cuda()].contiguous() if k < n else GT, kind=1, size_idx=si,
+                     offsets=offs[idx], out=(pose[:k], loss, dpose[:k], dF, dG))
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms)
+
+    allidx = np.arange(n)
+    mixed = timed(lambda: call(allidx, order.astype(np.int32)))
+    alone = {str(cfgs[k]["n"]): timed(lambda k=k: call(per[k], np.full(len(per[k]), k, np.int32))) for k in range(3)}
+    s.close()
+    return {"pairs": {str(cfgs[k]["n"]): int(counts[k]) for k in range(3)}, "mixed_ms": round(mixed, 4),
+            "alone_ms": {k: round(v, 4) for k, v in alone.items()}, "sum_alone_ms": round(sum(alone.values()), 4),
+            "gain_of_concurrent_groups": round(sum(alone.values()) / mixed, 3),
+            "note": "search training calls only; each group alone vs the three groups in one call"}
+
+
 def odd_side_rates(steps=10, warmup=3):
     """The paper's odd side 511 (Sec. IV-B's 0.2 m cells: stage-1 DFTs by Bluestein through 1024-point
     FFTs, stage 2 in the even frame 512) beside 512 on the same scene generator, 32 pairs each,
@@ -585,6 +650,32 @@ def odd_side_rates(steps=10, warmup=3):
                      "step_pairs_per_s": B / (ms_t * 1e-3),
                      "mean_abs_err": {"theta_deg": float(np.degrees(err[0])), "tx_px": float(err[1]), "ty_px": float(err[2])}}
         srch.close()
+    # Alg. 1's own settings at the paper's 511 (the f-raw rows of Tab. IIIa): n_theta 733 (direct
+    # angle sums), T_theta 2, delta_xy 0.4, the radial-mean angle score and Alg. 1's stage 2; one
+    # pair per call (the paper's batch of 1) and 32 pairs per call
+    f, g, gt = synth.make_batch("batch511", pairs=32)
+    fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    cfg = size_cfg(511, 733, 255, temp_theta=2.0, delta_xy=0.4, angle_score=1, rotate_target=1)
+    lit = {}
+    for B in (1, 32):
+        srch = PoseSearch([cfg], max_pairs=B, flags=_lib.FLAG_GRAPH)
+        pose = torch.empty((B, 3), device="cuda")
+        for _ in range(warmup):
+            srch.pose(fd[:B], gd[:B], out=pose)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            srch.pose(fd[:B], gd[:B], out=pose)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        lit[f"batch{B}_fwd_pairs_per_s"] = B / (sum(ms) / len(ms) * 1e-3)
+        srch.close()
+    out["alg1_literal_511"] = dict(lit, config="n 511, n_theta 733, n_r 255, T_theta 2, delta_xy 0.4, radial-mean "
+                                               "score, g turned back (Alg. 1 stage 2); forward, graph replay")
     return out
 
 
@@ -929,6 +1020,7 @@ def main():
         extra["alg1_n_theta_733"] = angle_count_comparison(fp32_peak / 2.0)
         extra["radar_frontend"] = frontend_rate()
         extra["odd_side_511"] = odd_side_rates()
+        extra["mixed_concurrency"] = mixed_concurrency()
 
     cpu = None
     if pool is not None:
