@@ -46,12 +46,15 @@ def parse():
                     help="for profilers: W + K training calls of --pairs pairs of the workload, launched directly "
                          "with the default schedules, and nothing else")
     ap.add_argument("--pairs", type=int, default=0, help="with --profile: pairs per call (default: the workload's)")
+    ap.add_argument("--schedule", default="",
+                    help="with --profile: launch schedules as knob=value,... (default: the library's defaults)")
     return ap.parse_args()
 
 
 def run_profile(args):
     """W + K training calls (or forwards, --mode fwd) of the workload, launched kernel by kernel
-    with the default launch schedules, for a profiler to capture; prints one short line."""
+    with the default launch schedules (or --schedule's), for a profiler to capture; prints one
+    short line."""
     import numpy as np
     import torch
     from paper_2203_00459_gb300 import build, synth
@@ -61,6 +64,8 @@ def run_profile(args):
     B = args.pairs or spec["pairs"]
     f, g, gt = synth.make_batch(args.workload, pairs=B)
     s = PoseSearch([size_cfg(spec["n"], spec["n_theta"], spec["n_r"])], max_pairs=B)
+    if args.schedule:
+        s.set_tuning(0, **{k: int(v) for k, v in (kv.split("=") for kv in args.schedule.split(","))})
     F, G = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
     GT = torch.from_numpy(gt.astype(np.float32)).cuda()
     for _ in range(args.warmup + args.steps):
@@ -69,7 +74,8 @@ def run_profile(args):
         else:
             out = (s.pose(F, G)["pose"],)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": args.workload, "pairs": B, "calls": args.warmup + args.steps, "mode": args.mode}))
+    print(json.dumps({"profile": args.workload, "pairs": B, "calls": args.warmup + args.steps, "mode": args.mode,
+                      "schedule": s.tuning(0)}))
     s.close()
 
 
@@ -108,15 +114,15 @@ def kernel_model(n, p, nt, nr, chunks):
 
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel:
-# (bytes, hash of the search sources it was taken on, pairs in that launch, column tile of the
-# variant).  Reported, scaled to the launch's pairs, only while the sources are unchanged and the
+# (bytes, hash of the search sources it was taken on, pairs in that launch, column tile and radix
+# order of the variant).  Reported, scaled to the launch's pairs, only while the sources are unchanged and the
 # autotuner picked the same variant.  k_b_cols<512, 768, 4> over 32 pairs at 512^2 (the third of
 # three training calls; ncu flushes the caches before the launch):
 #   python bench.py --profile --pairs 32 --steps 2 --warmup 1 &&
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
 #       -k regex:k_b_cols -s 2 -c 1 --csv python bench.py --profile --pairs 32 --steps 2 --warmup 1
 #   -> 201,434,112 read + 69,799,168 written, 99.5 us
-TRAFFIC = {"b_cols": (201434112 + 69799168, "407ca928d53bf3b4", 32, 4)}
+TRAFFIC = {"b_cols": (201434112 + 69799168, "407ca928d53bf3b4", 32, 4, 0)}
 
 
 # the sources that define, plan and launch the adjoint kernels (k_b_cols among them)
@@ -906,7 +912,8 @@ def main():
         flops = model[dom][1] * B
         achieved = byts / (avg_ms * 1e-3) / 1e9
         tr = TRAFFIC.get(dom)
-        same = tr and tr[1] == src_hash() and tr[3] == search.tuning(0)["col_tile"]
+        tun = search.tuning(0)
+        same = tr and tr[1] == src_hash() and (tr[3], tr[4]) == (tun["col_tile"], tun["col_plan"])
         traffic = tr[0] * B / tr[2] if same else None
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,

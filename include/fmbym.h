@@ -101,9 +101,13 @@ enum fmbym_flags { FMBYM_FLAG_GRAPH = 1, FMBYM_FLAG_AUTOTUNE = 2 };
  *                           lengths P = 3N/2 one of {C/2, C, 2C} with C = 192 / (P/16) (default C);
  *                           otherwise C = 256 / (P/16) only
  *   FMBYM_TUNE_ANGLE_RADII  radii per CTA of the angle correlation and its adjoint: 16 (default) or 8
- *   FMBYM_TUNE_ROT_PIXELS   pixels per thread of the Rotate adjoint: 4 (default), 1, 2 or 8 */
+ *   FMBYM_TUNE_ROT_PIXELS   pixels per thread of the Rotate adjoint: 4 (default), 1, 2 or 8
+ *   FMBYM_TUNE_COL_PLAN     radix order of the stage-2 column FFTs: 0 (default) = 16, R, 3 with
+ *                           R = P / 48; 1 = 16, 3, R (the middle and last radices swapped).  Both are
+ *                           valid only for the zero-padded lengths P = 3N/2 (192, 384, 768);
+ *                           otherwise 0 only */
 enum fmbym_tune_knob { FMBYM_TUNE_COL_TILE = 0, FMBYM_TUNE_ANGLE_RADII = 1, FMBYM_TUNE_ROT_PIXELS = 2,
-                       FMBYM_TUNE_COUNT = 3 };
+                       FMBYM_TUNE_COL_PLAN = 3, FMBYM_TUNE_COUNT = 4 };
 
 /* Handle configuration: n_sizes size configurations (host array, copied by fmbym_create),
  * the largest number of pairs one call may carry, and flags (fmbym_flags).  Pairs of different

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libfmbym.so")
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT = range(6)
 FLAG_GRAPH = 1
 FLAG_AUTOTUNE = 2
-TUNE_KNOBS = ("col_tile", "angle_radii", "rot_pixels")   # fmbym_tune_knob order
+TUNE_KNOBS = ("col_tile", "angle_radii", "rot_pixels", "col_plan")   # fmbym_tune_knob order
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE", 4: "CUDA", 5: "TIMEOUT"}
 
 

@@ -185,6 +185,7 @@ cudaError_t build_plan(HostPlan& hp) {
     d.col_tile = tpb_for(d.p) / fft_threads(d.p);
     d.angle_rc = kAngleRadii;
     d.rot_px = kRotPixels;
+    d.col_plan = 0;
     d.nt = c.n_theta;
     d.nr = c.n_r;
     d.window = c.window;
@@ -564,11 +565,15 @@ std::vector<int> tune_candidates(const DevPlan& d, int knob) {
     const int c0 = tpb_for(d.p) / fft_threads(d.p);
     if (knob == FMBYM_TUNE_COL_TILE) return d.p % 3 == 0 ? std::vector<int>{c0, c0 / 2, 2 * c0} : std::vector<int>{c0};
     if (knob == FMBYM_TUNE_ANGLE_RADII) return {kAngleRadii, kAngleRadiiMin};
+    if (knob == FMBYM_TUNE_COL_PLAN) return d.p % 3 == 0 ? std::vector<int>{0, 1} : std::vector<int>{0};
     return {kRotPixels, 1, 2, 8};
 }
 
 int& tune_field(DevPlan& d, int knob) {
-    return knob == FMBYM_TUNE_COL_TILE ? d.col_tile : knob == FMBYM_TUNE_ANGLE_RADII ? d.angle_rc : d.rot_px;
+    return knob == FMBYM_TUNE_COL_TILE      ? d.col_tile
+           : knob == FMBYM_TUNE_ANGLE_RADII ? d.angle_rc
+           : knob == FMBYM_TUNE_COL_PLAN    ? d.col_plan
+                                            : d.rot_px;
 }
 
 void release_graphs(fmbym_handle* h) {
@@ -825,6 +830,7 @@ int fmbym_get_tuning(const fmbym_handle* h, int size, int* values) {
     values[FMBYM_TUNE_COL_TILE] = d.col_tile;
     values[FMBYM_TUNE_ANGLE_RADII] = d.angle_rc;
     values[FMBYM_TUNE_ROT_PIXELS] = d.rot_px;
+    values[FMBYM_TUNE_COL_PLAN] = d.col_plan;
     return FMBYM_OK;
 }
 

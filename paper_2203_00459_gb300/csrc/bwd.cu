@@ -134,14 +134,15 @@ __device__ __forceinline__ void split0(float2 z, float2 zm, float2& a, float2& b
 // multiplies its DC and Nyquist parts separately.  D's first pass reads global memory; its last
 // pass, both products and both inverses' first passes run in registers (the inverse in the
 // reverse radix order); both inverses' last passes store to global memory.
-template <int N, int P, int C>
+// V: the radix order (FftPlan<P, V>).
+template <int N, int P, int C, int V>
 __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_cols(DevPlan p, const float2* __restrict__ b1,
                                                                        const float2* __restrict__ s2hat,
                                                                        float2* __restrict__ b2, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
-    using PL = FftPlan<P>;
+    using PL = FftPlan<P, V>;
     constexpr int T = PL::T, TPB = C * T, ES = C, W = P / 2, TILE = spad(P) * ES;
-    constexpr int RL = last_radix<P>(), NBL = P / RL, BPL = (NBL + T - 1) / T, PER = P * C / TPB;
+    constexpr int RL = last_radix<P, V>(), NBL = P / RL, BPL = (NBL + T - 1) / T, PER = P * C / TPB;
     extern __shared__ float2 sm[];
     float2* tD = sm;
     float2* tX = sm + TILE;
@@ -152,6 +153,10 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
     const float2* hF = s2hat + (size_t)q * P * W;          // F'^ [W][P], column-major
     const float2* hG = s2hat + (size_t)(B + q) * P * W;    // G^  [W][P]
     const float2 zero = make_float2(0.f, 0.f);
+    // the tile's columns of F'^ and G^ (C runs of P positions each) are read only after D's first
+    // two passes: start bringing them into L2 now
+    if (threadIdx.x < 2 * C)
+        prefetch_l2((threadIdx.x < C ? hF : hG) + (size_t)(u0 + threadIdx.x % C) * P, P * sizeof(float2));
     // P-row v of D holds lag row i = (v + N/2) mod P (zero when i >= N)
     first_pass_global<P>(tD + c, ES, j, [&](int v) {
         const int i = v + N / 2 < P ? v + N / 2 : v + N / 2 - P;
@@ -161,8 +166,14 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
     if constexpr (PL::NP == 3) fft_pass<P, T, PL::R2, 16, -1>(tD + c, ES, j, true, tw);
     if (blockIdx.x != 0) {
         const int u = u0 + c;
-        // D's last forward pass (final values back in place: same thread, same positions), then
-        // Q1 = conj(D) G^ and its inverse first pass straight into tX, which nothing reads here
+        // D's last forward pass, then Q1 = conj(D) G^ and its inverse first pass straight into tX,
+        // which nothing reads here.  Q2 = D F'^ and its inverse first pass are held in registers
+        // until every thread has read its D, then written over tD.  With one butterfly per thread
+        // (BPL = 1) Q2 is formed from the D values in registers; with several, D's final values go
+        // back in place (same thread, same positions) and Q2 is formed after the Q1 loop, which
+        // keeps fewer values live while the loads of G^ are in flight (measured faster there).
+        constexpr bool KEEP_D = BPL > 1;
+        float2 o2[BPL][RL];
 #pragma unroll
         for (int m = 0; m < BPL; ++m) {
             const int b = j + m * T;
@@ -174,25 +185,27 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
                 dft<RL, -1>(d);
 #pragma unroll
                 for (int t = 0; t < RL; ++t) {
-                    tD[spad(b + t * NBL) * ES + c] = d[t];
-                    o[t] = c_cjmul(d[t], __ldg(hG + (size_t)u * P + b + t * NBL));
+                    const size_t gi = (size_t)u * P + b + t * NBL;
+                    if constexpr (KEEP_D) tD[spad(b + t * NBL) * ES + c] = d[t];
+                    else o2[m][t] = c_mul(d[t], __ldg(hF + gi));
+                    o[t] = c_cjmul(d[t], __ldg(hG + gi));
                 }
                 dft<RL, +1>(o);
+                if constexpr (!KEEP_D) dft<RL, +1>(o2[m]);
 #pragma unroll
                 for (int t = 0; t < RL; ++t) tX[spad(RL * b + t) * ES + c] = o[t];
             }
         }
-        // Q2 = D F'^ from the thread's own final D values; written over tD once every thread
-        // has read its D
-        float2 o2[BPL][RL];
+        if constexpr (KEEP_D) {
 #pragma unroll
-        for (int m = 0; m < BPL; ++m) {
-            const int b = j + m * T;
-            if (NBL % T == 0 || b < NBL) {
+            for (int m = 0; m < BPL; ++m) {
+                const int b = j + m * T;
+                if (NBL % T == 0 || b < NBL) {
 #pragma unroll
-                for (int t = 0; t < RL; ++t)
-                    o2[m][t] = c_mul(tD[spad(b + t * NBL) * ES + c], __ldg(hF + (size_t)u * P + b + t * NBL));
-                dft<RL, +1>(o2[m]);
+                    for (int t = 0; t < RL; ++t)
+                        o2[m][t] = c_mul(tD[spad(b + t * NBL) * ES + c], __ldg(hF + (size_t)u * P + b + t * NBL));
+                    dft<RL, +1>(o2[m]);
+                }
             }
         }
         __syncthreads();
@@ -242,12 +255,9 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
     }
     float2* o1 = b2 + (size_t)q * N * W + u0 + c;
     float2* o2 = b2 + (size_t)(B + q) * N * W + u0 + c;
-    inverse_rest_global<P>(tX + c, ES, j, tw, [&](int y, float2 v) {
-        if (y < N) o1[(size_t)y * W] = v;
-    });
-    inverse_rest_global<P>(tD + c, ES, j, tw, [&](int y, float2 v) {
-        if (y < N) o2[(size_t)y * W] = v;
-    });
+    inverse_rest_global2<P, V>(
+        tX + c, tD + c, ES, j, tw, [&](int y, float2 v) { if (y < N) o1[(size_t)y * W] = v; },
+        [&](int y, float2 v) { if (y < N) o2[(size_t)y * W] = v; });
 }
 
 // Inverse row FFTs of the two adjoint spectra, keep x in [0, N), scale 1/P^2:
@@ -742,6 +752,26 @@ static void launch_b_rot(const DevPlan& p, const Ws& w, int B, const long long* 
 }
 
 // N: the scan side; NE: stage 2's frame (N, or N + 1 for odd N); M: Bluestein length (0: none).
+// The adjoint's column pass in radix order V with the size's column tile.
+template <int N, int P, int V>
+static void launch_b_cols(const DevPlan& p, const Ws& w, int B, cudaStream_t st) {
+    constexpr int T2 = FftPlan<P>::T, C0 = tpb_for(P) / T2;   // the default tile; the 3 * 2^k lengths
+    if constexpr (P % 3 == 0) {                                  // also have half and double
+        if (p.col_tile == C0 / 2)
+            launch_pdl(k_b_cols<N, P, C0 / 2, V>, dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, b_smem_cols<P, C0 / 2>(), st,
+                       p, w.b1, w.s2hat, w.b2, B);
+        else if (p.col_tile == 2 * C0)
+            launch_pdl(k_b_cols<N, P, 2 * C0, V>, dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, b_smem_cols<P, 2 * C0>(), st,
+                       p, w.b1, w.s2hat, w.b2, B);
+        else
+            launch_pdl(k_b_cols<N, P, C0, V>, dim3((P / 2) / C0, B), C0 * T2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat,
+                       w.b2, B);
+    } else {
+        launch_pdl(k_b_cols<N, P, C0, V>, dim3((P / 2) / C0, B), C0 * T2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat,
+                   w.b2, B);
+    }
+}
+
 template <int N, int NE, int M, int P>
 static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long long* tab, const float* f,
                             const float* g, const float* dpose, float* df, float* dg, cudaStream_t st,
@@ -758,19 +788,11 @@ static cudaError_t launch_b(const DevPlan& p, const Ws& w, int B, const long lon
     launch_pdl(k_b_rows<NE, P, ODD>, dim3((NE / 2) / (TB2 / T2), B), TB2, b_smem_rows<P>(), st, p, tab, w.cxy, w.xm,
                fwd_pose, dpose, w.b1, B);
     w.tr->before(K_B_COLS, st);
-    constexpr int C0 = TB2 / T2;   // the default tile; the 3 * 2^k lengths also have half and double
     if constexpr (P % 3 == 0) {
-        if (p.col_tile == C0 / 2)
-            launch_pdl(k_b_cols<NE, P, C0 / 2>, dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, b_smem_cols<P, C0 / 2>(), st,
-                       p, w.b1, w.s2hat, w.b2, B);
-        else if (p.col_tile == 2 * C0)
-            launch_pdl(k_b_cols<NE, P, 2 * C0>, dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, b_smem_cols<P, 2 * C0>(), st,
-                       p, w.b1, w.s2hat, w.b2, B);
-        else
-            launch_pdl(k_b_cols<NE, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2,
-                       B);
+        if (p.col_plan == 1) launch_b_cols<NE, P, 1>(p, w, B, st);
+        else launch_b_cols<NE, P, 0>(p, w, B, st);
     } else {
-        launch_pdl(k_b_cols<NE, P, C0>, dim3((P / 2) / C0, B), TB2, b_smem_cols<P, C0>(), st, p, w.b1, w.s2hat, w.b2, B);
+        launch_b_cols<NE, P, 0>(p, w, B, st);
     }
     w.tr->before(K_B_C2R, st);
     launch_pdl(k_b_c2r<NE, P, ODD>, dim3((NE / 2) / (TB2 / T2), B, 2), TB2, b_smem_rows<P>(), st, p, tab, w.b2, w.gfr, df,
@@ -840,10 +862,13 @@ static cudaError_t prepare_b() {
     cudaError_t e;
     if ((e = allow(k_b_rows<N, P, ODD>, b_smem_rows<P>())) != cudaSuccess) return e;
     constexpr int C0 = tpb_for(P) / FftPlan<P>::T;
-    if ((e = allow(k_b_cols<N, P, C0>, b_smem_cols<P, C0>())) != cudaSuccess) return e;
+    if ((e = allow(k_b_cols<N, P, C0, 0>, b_smem_cols<P, C0>())) != cudaSuccess) return e;
     if constexpr (P % 3 == 0) {
-        if ((e = allow(k_b_cols<N, P, C0 / 2>, b_smem_cols<P, C0 / 2>())) != cudaSuccess) return e;
-        if ((e = allow(k_b_cols<N, P, 2 * C0>, b_smem_cols<P, 2 * C0>())) != cudaSuccess) return e;
+        if ((e = allow(k_b_cols<N, P, C0 / 2, 0>, b_smem_cols<P, C0 / 2>())) != cudaSuccess) return e;
+        if ((e = allow(k_b_cols<N, P, 2 * C0, 0>, b_smem_cols<P, 2 * C0>())) != cudaSuccess) return e;
+        if ((e = allow(k_b_cols<N, P, C0, 1>, b_smem_cols<P, C0>())) != cudaSuccess) return e;
+        if ((e = allow(k_b_cols<N, P, C0 / 2, 1>, b_smem_cols<P, C0 / 2>())) != cudaSuccess) return e;
+        if ((e = allow(k_b_cols<N, P, 2 * C0, 1>, b_smem_cols<P, 2 * C0>())) != cudaSuccess) return e;
     }
     if ((e = allow(k_b_c2r<N, P, ODD>, b_smem_rows<P>())) != cudaSuccess) return e;
     if constexpr (ODD) {

@@ -82,8 +82,9 @@ struct DevPlan {
     const int* heavy;
     int n_heavy;
     // launch schedules: columns per CTA of the stage-2 column passes (half, the default, or twice
-    // tpb_for(P) / T), radii per CTA of the angle kernels, pixels per thread of the Rotate adjoint
-    int col_tile, angle_rc, rot_px;
+    // tpb_for(P) / T), radii per CTA of the angle kernels, pixels per thread of the Rotate adjoint,
+    // radix order of the stage-2 column passes (FftPlan<P, col_plan>; 1 only for P = 3 * 2^k)
+    int col_tile, angle_rc, rot_px, col_plan;
 };
 
 constexpr int kHeavyRow = 32;

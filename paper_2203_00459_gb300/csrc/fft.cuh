@@ -31,6 +31,11 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 // Waits for every cp.async this thread issued (a __syncthreads must follow before others read).
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Hint that brings [p, p + bytes) of global memory into L2 (one bulk prefetch; p and bytes
+// multiples of 16).  No value is read into the SM, so a later load of the range hits L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -280,7 +285,12 @@ __device__ __forceinline__ void fft_passes(float2* buf, int es, int j, bool acti
 // product and an inverse run the inverse in the reverse radix order: the forward's last pass and
 // the inverse's first pass then read and write the same butterfly positions, so the product
 // happens in registers between them.
-template <int L> struct FftPlan;
+//
+// V = 1 is the other valid order of the 3 * 2^k lengths, the middle and last radices swapped
+// (16, 3, R): its last pass has L / R = 48 butterflies for every such length, one per thread at
+// 768, so the fused turn of a column pass has no ragged tail, at the cost of holding R points per
+// butterfly.  The autotuner picks the order of the stage-2 column passes per size.
+template <int L, int V = 0> struct FftPlan;
 template <> struct FftPlan<128> { static constexpr int T = 8, NP = 2, R2 = 8, R3 = 1; };
 template <> struct FftPlan<192> { static constexpr int T = 12, NP = 3, R2 = 4, R3 = 3; };
 template <> struct FftPlan<256> { static constexpr int T = 16, NP = 2, R2 = 16, R3 = 1; };
@@ -289,6 +299,9 @@ template <> struct FftPlan<400> { static constexpr int T = 25, NP = 3, R2 = 5, R
 template <> struct FftPlan<512> { static constexpr int T = 32, NP = 3, R2 = 16, R3 = 2; };
 template <> struct FftPlan<768> { static constexpr int T = 48, NP = 3, R2 = 16, R3 = 3; };
 template <> struct FftPlan<1024> { static constexpr int T = 64, NP = 3, R2 = 16, R3 = 4; };
+template <> struct FftPlan<192, 1> { static constexpr int T = 12, NP = 3, R2 = 3, R3 = 4; };
+template <> struct FftPlan<384, 1> { static constexpr int T = 24, NP = 3, R2 = 3, R3 = 8; };
+template <> struct FftPlan<768, 1> { static constexpr int T = 48, NP = 3, R2 = 3, R3 = 16; };
 
 // In-place FFT of one sequence (element i at buf[spad(i) * es]) by thread j < T of its group.
 // S = -1 forward, +1 inverse.  Threads with active = false only take part in the barriers.
@@ -347,10 +360,10 @@ __device__ __forceinline__ void first_pass_global(float2* b0, int es, int j, Loa
 // no barrier needed); 2: a already holds its final values.  prod(A, X) gives the product; the
 // inverse first pass's outputs go to tb.  keep(pos, A, X) sees both transformed values at each
 // position (to store them for a later pass).  Every thread of the CTA must call it.
-template <int L, int MODE_A, class Prod, class Keep>
+template <int L, int MODE_A, int V, class Prod, class Keep>
 __device__ __forceinline__ void fused_turn(float2* ta, float2* tb, int es, int j, const float2* __restrict__ tw,
                                            Prod prod, Keep keep) {
-    using PL = FftPlan<L>;
+    using PL = FftPlan<L, V>;
     constexpr int T = PL::T, RL = PL::NP == 3 ? PL::R3 : PL::R2, NBL = L / RL, BPL = (NBL + T - 1) / T;
     float2 o[BPL][RL];
 #pragma unroll
@@ -394,19 +407,19 @@ __device__ __forceinline__ void fused_turn(float2* ta, float2* tb, int es, int j
 }
 
 // fused_turn without keeping the transformed values.
-template <int L, int MODE_A, class Prod>
+template <int L, int MODE_A, int V, class Prod>
 __device__ __forceinline__ void fused_turn(float2* ta, float2* tb, int es, int j, const float2* __restrict__ tw,
                                            Prod prod) {
-    fused_turn<L, MODE_A>(ta, tb, es, j, tw, prod, [](int, float2, float2) {});
+    fused_turn<L, MODE_A, V>(ta, tb, es, j, tw, prod, [](int, float2, float2) {});
 }
 
 // The inverse transform's remaining passes after fused_turn (or after its first pass): the middle
 // pass (three-pass plans), then the last pass (radix 16, stride T) with its outputs handed to
 // store(pos, value) instead of the tile.
-template <int L, class Store>
+template <int L, int V, class Store>
 __device__ __forceinline__ void inverse_rest_global(float2* buf, int es, int j, const float2* __restrict__ tw,
                                                     Store store) {
-    using PL = FftPlan<L>;
+    using PL = FftPlan<L, V>;
     constexpr int T = PL::T, RL = PL::NP == 3 ? PL::R3 : PL::R2;
     if constexpr (PL::NP == 3) fft_pass<L, T, PL::R2, RL, +1>(buf, es, j, true, tw);
     float2 v[16];
@@ -416,6 +429,29 @@ __device__ __forceinline__ void inverse_rest_global(float2* buf, int es, int j, 
     dft16<+1>(v);
 #pragma unroll
     for (int t = 0; t < 16; ++t) store(j + t * T, v[t]);
+}
+
+// inverse_rest_global of two sequences: one middle pass over both (one pair of barriers), then each
+// last pass.
+template <int L, int V, class Store0, class Store1>
+__device__ __forceinline__ void inverse_rest_global2(float2* b0, float2* b1, int es, int j,
+                                                     const float2* __restrict__ tw, Store0 store0, Store1 store1) {
+    using PL = FftPlan<L, V>;
+    constexpr int T = PL::T, RL = PL::NP == 3 ? PL::R3 : PL::R2;
+    if constexpr (PL::NP == 3) fft_pass2<L, T, PL::R2, RL, +1>(b0, b1, es, j, tw);
+    float2 v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = b0[spad(j + t * T) * es];
+    twiddle<L, 16, T, +1>(v, j, tw);
+    dft16<+1>(v);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) store0(j + t * T, v[t]);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = b1[spad(j + t * T) * es];
+    twiddle<L, 16, T, +1>(v, j, tw);
+    dft16<+1>(v);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) store1(j + t * T, v[t]);
 }
 
 // The passes after the first (FIRST = 2), in the plan's own radix order, in shared memory.
@@ -479,7 +515,9 @@ __device__ __forceinline__ float2 pack_inverse(const float2* __restrict__ ra, co
 }
 
 // Last radix of the forward plan and the stride of its pass.
-template <int L> __host__ __device__ constexpr int last_radix() { return FftPlan<L>::NP == 3 ? FftPlan<L>::R3 : FftPlan<L>::R2; }
+template <int L, int V = 0> __host__ __device__ constexpr int last_radix() {
+    return FftPlan<L, V>::NP == 3 ? FftPlan<L, V>::R3 : FftPlan<L, V>::R2;
+}
 
 // Threads of a CTA that runs several length-L sequences side by side: a multiple of both the
 // group size and 32 (192 for the 3 * 2^k lengths, 256 otherwise).

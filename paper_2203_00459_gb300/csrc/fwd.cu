@@ -414,13 +414,14 @@ __global__ void __launch_bounds__(tpb_for(P), P == 768 ? 6 : 65536 / (tpb_for(P)
 // straight to global memory.  Threads are column-fastest (c = tid mod C) over a tile of stride
 // C, which makes every shared access phase free of bank conflicts and every global access a run
 // of C consecutive columns.
-template <int N, int P, int C>
+// V: the radix order (FftPlan<P, V>).
+template <int N, int P, int C, int V>
 __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_cols(DevPlan p, const float2* __restrict__ s2,
                                                       float2* __restrict__ s3, float2* __restrict__ s2hat, int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
-    using PL = FftPlan<P>;
+    using PL = FftPlan<P, V>;
     constexpr int T = PL::T, TPB = C * T, ES = C, W = P / 2, TILE = spad(P) * ES;
-    constexpr int RL = last_radix<P>(), NBL = P / RL;
+    constexpr int RL = last_radix<P, V>(), NBL = P / RL;
     extern __shared__ float2 sm[];
     float2* tf = sm;
     float2* tg = sm + TILE;
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_
     float2* kf = s2hat ? s2hat + (size_t)q * P * W : nullptr;
     float2* kg = s2hat ? s2hat + (size_t)(B + q) * P * W : nullptr;
     if (blockIdx.x != 0) {
-        fused_turn<P, 0>(tf + c, tg + c, ES, j, tw, [](float2 F, float2 G) { return c_cjmul(F, G); },
+        fused_turn<P, 0, V>(tf + c, tg + c, ES, j, tw, [](float2 F, float2 G) { return c_cjmul(F, G); },
                          [&](int pos, float2 F, float2 G) {
                              if (kf) {
                                  kf[(size_t)(u0 + c) * P + pos] = F;
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_
     // inverse middle and last passes; P-position pos holds lag s_y = pos (pos < P/2) or pos - P,
     // kept as lag row i = s_y + N/2 when 0 <= i < N
     float2* out = s3 + (size_t)q * N * W + u0 + c;
-    inverse_rest_global<P>(tg + c, ES, j, tw, [&](int pos, float2 v) {
+    inverse_rest_global<P, V>(tg + c, ES, j, tw, [&](int pos, float2 v) {
         const int i = pos < P / 2 ? pos + N / 2 : pos - P + N / 2;
         if (i >= 0 && i < N) out[(size_t)i * W] = v;
     });
@@ -823,6 +824,26 @@ static cudaError_t launch_np(const DevPlan& p, const Ws& w, int B, const long lo
     return launch_stage2<NE, P, ODD>(p, w, B, tab, f, g, pose, c_xy, st);
 }
 
+// The stage-2 column pass in radix order V with the size's column tile.
+template <int N, int P, int V>
+static void launch_s2_cols(const DevPlan& p, const Ws& w, int B, cudaStream_t st) {
+    constexpr int T2 = FftPlan<P>::T, C0 = tpb_for(P) / T2;   // the default tile; the 3 * 2^k lengths
+    if constexpr (P % 3 == 0) {                                  // also have half and double
+        if (p.col_tile == C0 / 2)
+            launch_pdl(k_s2_cols<N, P, C0 / 2, V>, dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, smem_cols2<P, C0 / 2>(), st,
+                       p, w.s2, w.s3, w.s2hat, B);
+        else if (p.col_tile == 2 * C0)
+            launch_pdl(k_s2_cols<N, P, 2 * C0, V>, dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, smem_cols2<P, 2 * C0>(), st,
+                       p, w.s2, w.s3, w.s2hat, B);
+        else
+            launch_pdl(k_s2_cols<N, P, C0, V>, dim3((P / 2) / C0, B), C0 * T2, smem_cols2<P, C0>(), st, p, w.s2, w.s3,
+                       w.s2hat, B);
+    } else {
+        launch_pdl(k_s2_cols<N, P, C0, V>, dim3((P / 2) / C0, B), C0 * T2, smem_cols2<P, C0>(), st, p, w.s2, w.s3, w.s2hat,
+                   B);
+    }
+}
+
 // Stage 2 of Alg. 1 for the headings in w.th: Rotate, the padded correlation and the translation
 // soft-argmax -> pose[.][1..2], block statistics of c_xy in w.st.  N is the frame (ODD: the scan
 // side is N - 1).
@@ -834,18 +855,11 @@ static cudaError_t launch_stage2(const DevPlan& p, const Ws& w, int B, const lon
     launch_pdl(k_s2_rows<N, P, ODD>, dim3((N / 2) / (TB2 / T2), B, 2), TB2, smem_rows<P>(), st, p, tab, f, g, w.th, w.s2,
                B);
     w.tr->before(K_S2_COLS, st);
-    constexpr int C0 = TB2 / T2;   // the default tile; the 3 * 2^k lengths also have half and double
     if constexpr (P % 3 == 0) {
-        if (p.col_tile == C0 / 2)
-            launch_pdl(k_s2_cols<N, P, C0 / 2>, dim3((P / 2) / (C0 / 2), B), (C0 / 2) * T2, smem_cols2<P, C0 / 2>(), st, 
-                p, w.s2, w.s3, w.s2hat, B);
-        else if (p.col_tile == 2 * C0)
-            launch_pdl(k_s2_cols<N, P, 2 * C0>, dim3((P / 2) / (2 * C0), B), 2 * C0 * T2, smem_cols2<P, 2 * C0>(), st, 
-                p, w.s2, w.s3, w.s2hat, B);
-        else
-            launch_pdl(k_s2_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, smem_cols2<P, C0>(), st, p, w.s2, w.s3, w.s2hat, B);
+        if (p.col_plan == 1) launch_s2_cols<N, P, 1>(p, w, B, st);
+        else launch_s2_cols<N, P, 0>(p, w, B, st);
     } else {
-        launch_pdl(k_s2_cols<N, P, C0>, dim3((P / 2) / C0, B), TB2, smem_cols2<P, C0>(), st, p, w.s2, w.s3, w.s2hat, B);
+        launch_s2_cols<N, P, 0>(p, w, B, st);
     }
     const int nblk = (N / 2) / (TB2 / T2);
     w.tr->before(K_S2_C2R, st);
@@ -903,10 +917,13 @@ static cudaError_t prepare_np() {
     }
     if ((e = allow_smem(k_s2_rows<N, P, ODD>, smem_rows<P>())) != cudaSuccess) return e;
     constexpr int C0 = tpb_for(P) / FftPlan<P>::T;
-    if ((e = allow_smem(k_s2_cols<N, P, C0>, smem_cols2<P, C0>())) != cudaSuccess) return e;
+    if ((e = allow_smem(k_s2_cols<N, P, C0, 0>, smem_cols2<P, C0>())) != cudaSuccess) return e;
     if constexpr (P % 3 == 0) {
-        if ((e = allow_smem(k_s2_cols<N, P, C0 / 2>, smem_cols2<P, C0 / 2>())) != cudaSuccess) return e;
-        if ((e = allow_smem(k_s2_cols<N, P, 2 * C0>, smem_cols2<P, 2 * C0>())) != cudaSuccess) return e;
+        if ((e = allow_smem(k_s2_cols<N, P, C0 / 2, 0>, smem_cols2<P, C0 / 2>())) != cudaSuccess) return e;
+        if ((e = allow_smem(k_s2_cols<N, P, 2 * C0, 0>, smem_cols2<P, 2 * C0>())) != cudaSuccess) return e;
+        if ((e = allow_smem(k_s2_cols<N, P, C0, 1>, smem_cols2<P, C0>())) != cudaSuccess) return e;
+        if ((e = allow_smem(k_s2_cols<N, P, C0 / 2, 1>, smem_cols2<P, C0 / 2>())) != cudaSuccess) return e;
+        if ((e = allow_smem(k_s2_cols<N, P, 2 * C0, 1>, smem_cols2<P, 2 * C0>())) != cudaSuccess) return e;
     }
     return allow_smem(k_s2_c2r<N, P, ODD>, smem_rows<P>());
 }

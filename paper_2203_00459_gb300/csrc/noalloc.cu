@@ -184,6 +184,7 @@ int fmbym_pose_noalloc(void* stream, const fmbym_size_cfg* cfg, int n_pairs, con
     p.col_tile = tpb_for(p.p) / fft_threads(p.p);   // the default launch schedules
     p.angle_rc = kAngleRadii;
     p.rot_px = kRotPixels;
+    p.col_plan = 0;
     const int mmax = (cfg->n / 2) * (cfg->n / 2) * 2;
     p.m_lo = mmax + 1;
     p.m_hi = -1;

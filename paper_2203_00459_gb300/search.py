@@ -104,7 +104,7 @@ class PoseSearch:
             pass
 
     def tuning(self, size=0):
-        """The launch schedules of a size: dict(col_tile, angle_radii, rot_pixels)."""
+        """The launch schedules of a size: dict(col_tile, angle_radii, rot_pixels, col_plan)."""
         v = (ctypes.c_int * len(_lib.TUNE_KNOBS))()
         _lib.check(_lib.lib().fmbym_get_tuning(self.handle, int(size), v), self.handle)
         return dict(zip(_lib.TUNE_KNOBS, list(v)))

@@ -18,7 +18,7 @@ def test_step_model_at_512():
 
 
 def test_traffic_record_is_per_launch_of_the_recorded_tile():
-    bytes_, h, pairs, tile = bench.TRAFFIC["b_cols"]
-    assert pairs == 32 and tile in (4, 8, 16) and len(h) == 16
+    bytes_, h, pairs, tile, plan = bench.TRAFFIC["b_cols"]
+    assert pairs == 32 and tile in (2, 4, 8) and plan in (0, 1) and len(h) == 16
     # ncu traffic below the algorithmic bytes of the same launch: nothing is re-read
     assert 0.8 < bytes_ / (bench.kernel_model(512, 768, 400, 256, 16)["b_cols"][0] * pairs) < 1.0
