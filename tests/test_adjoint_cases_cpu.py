@@ -104,3 +104,14 @@ def test_the_odd_side_case_next_to_an_edge_is_seen(monkeypatch):
     f, g, _ = synth.make_batch("batch511", pairs=1, start=3)
     cfg = O.make_cfg(spec["n"], spec["n_theta"], spec["n_r"])
     assert dtheta_kink_margin(f[0], g[0], cfg, ODD_DP[0], monkeypatch) > 1e-3
+
+
+def test_radix_order_case_at_512(monkeypatch):
+    """The 512^2 pair of the radix-order parity test (start 3; start 9 sits on an edge)."""
+    spec = synth.WORKLOADS["batch512"]
+    cfg = O.make_cfg(512, spec["n_theta"], spec["n_r"])
+    dp = np.array([0.7, -0.4, 0.5])
+    f, g, _ = synth.make_batch("batch512", pairs=1, start=3)
+    assert dtheta_kink_margin(f[0], g[0], cfg, dp, monkeypatch) < 1e-3
+    f, g, _ = synth.make_batch("batch512", pairs=1, start=9)
+    assert dtheta_kink_margin(f[0], g[0], cfg, dp, monkeypatch) > 1e-3

@@ -87,7 +87,7 @@ def test_radix_orders_at_512_match_oracle(lib, col_plan):
     pose and surfaces, and the adjoint, against the FP64 oracle on one pair."""
     _, search = lib
     spec = synth.WORKLOADS["batch512"]
-    f, g, _ = synth.make_batch("batch512", pairs=1, start=9)
+    f, g, _ = synth.make_batch("batch512", pairs=1, start=3)   # clear of cell edges (reading A14)
     cfg = search.size_cfg(512, spec["n_theta"], spec["n_r"])
     s = search.PoseSearch([cfg], max_pairs=1)
     s.set_tuning(0, col_plan=col_plan)
