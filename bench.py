@@ -116,13 +116,14 @@ def kernel_model(n, p, nt, nr, chunks):
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel:
 # (bytes, hash of the search sources it was taken on, pairs in that launch, column tile and radix
 # order of the variant).  Reported, scaled to the launch's pairs, only while the sources are unchanged and the
-# autotuner picked the same variant.  k_b_cols<512, 768, 4> over 32 pairs at 512^2 (the third of
+# autotuner picked the same variant.  k_b_cols<512, 768, 4, 1> over 32 pairs at 512^2 (the third of
 # three training calls; ncu flushes the caches before the launch):
-#   python bench.py --profile --pairs 32 --steps 2 --warmup 1 &&
+#   S=col_tile=4,angle_radii=8,rot_pixels=8,col_plan=1
+#   python bench.py --profile --pairs 32 --steps 2 --warmup 1 --schedule $S &&
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
-#       -k regex:k_b_cols -s 2 -c 1 --csv python bench.py --profile --pairs 32 --steps 2 --warmup 1
-#   -> 201,434,112 read + 69,799,168 written, 99.5 us
-TRAFFIC = {"b_cols": (201434112 + 69799168, "407ca928d53bf3b4", 32, 4, 0)}
+#       -k regex:k_b_cols -s 2 -c 1 --csv python bench.py --profile --pairs 32 --steps 2 --warmup 1 --schedule $S
+#   -> 201,424,640 read + 72,315,648 written, 92.9 us
+TRAFFIC = {"b_cols": (201424640 + 72315648, "8c2313f00a7e7590", 32, 4, 1)}
 
 
 # the sources that define, plan and launch the adjoint kernels (k_b_cols among them)
