@@ -185,15 +185,20 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_b_c
                 dft<RL, -1>(d);
 #pragma unroll
                 for (int t = 0; t < RL; ++t) {
-                    const size_t gi = (size_t)u * P + b + t * NBL;
                     if constexpr (KEEP_D) tD[spad(b + t * NBL) * ES + c] = d[t];
-                    else o2[m][t] = c_mul(d[t], __ldg(hF + gi));
-                    o[t] = c_cjmul(d[t], __ldg(hG + gi));
+                    o[t] = c_cjmul(d[t], __ldg(hG + (size_t)u * P + b + t * NBL));
                 }
                 dft<RL, +1>(o);
-                if constexpr (!KEEP_D) dft<RL, +1>(o2[m]);
 #pragma unroll
                 for (int t = 0; t < RL; ++t) tX[spad(RL * b + t) * ES + c] = o[t];
+                if constexpr (!KEEP_D) {
+                    // F'^ is loaded only now (the fence keeps the compiler from hoisting the loads
+                    // above Q1), so that G^, F'^ and D are not all live at once
+                    asm volatile("" ::: "memory");
+#pragma unroll
+                    for (int t = 0; t < RL; ++t) o2[m][t] = c_mul(d[t], __ldg(hF + (size_t)u * P + b + t * NBL));
+                    dft<RL, +1>(o2[m]);
+                }
             }
         }
         if constexpr (KEEP_D) {

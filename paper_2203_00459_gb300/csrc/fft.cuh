@@ -431,14 +431,22 @@ __device__ __forceinline__ void inverse_rest_global(float2* buf, int es, int j, 
     for (int t = 0; t < 16; ++t) store(j + t * T, v[t]);
 }
 
-// inverse_rest_global of two sequences: one middle pass over both (one pair of barriers), then each
-// last pass.
+// inverse_rest_global of two sequences: one middle pass over both (one pair of barriers) when a
+// thread holds one butterfly of it, else one middle pass after the other (fewer live registers),
+// then each last pass.
 template <int L, int V, class Store0, class Store1>
 __device__ __forceinline__ void inverse_rest_global2(float2* b0, float2* b1, int es, int j,
                                                      const float2* __restrict__ tw, Store0 store0, Store1 store1) {
     using PL = FftPlan<L, V>;
     constexpr int T = PL::T, RL = PL::NP == 3 ? PL::R3 : PL::R2;
-    if constexpr (PL::NP == 3) fft_pass2<L, T, PL::R2, RL, +1>(b0, b1, es, j, tw);
+    if constexpr (PL::NP == 3) {
+        if constexpr (L / PL::R2 <= T) {
+            fft_pass2<L, T, PL::R2, RL, +1>(b0, b1, es, j, tw);
+        } else {
+            fft_pass<L, T, PL::R2, RL, +1>(b0, es, j, true, tw);
+            fft_pass<L, T, PL::R2, RL, +1>(b1, es, j, true, tw);
+        }
+    }
     float2 v[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) v[t] = b0[spad(j + t * T) * es];
