@@ -436,7 +436,16 @@ __global__ void __launch_bounds__(C * FftPlan<P>::T, col_min_blocks(P, C)) k_s2_
         [&](int v) { return v < N ? __ldg(inf + (size_t)v * W) : make_float2(0.f, 0.f); },
         [&](int v) { return v < N ? __ldg(ing + (size_t)v * W) : make_float2(0.f, 0.f); });
     __syncthreads();
-    if constexpr (PL::NP == 3) fft_pass2<P, T, PL::R2, 16, -1>(tf + c, tg + c, ES, j, tw);
+    // the middle pass of both images: in one pair of barriers when a thread holds one butterfly of
+    // it, else one image after the other (fewer live registers)
+    if constexpr (PL::NP == 3) {
+        if constexpr (P / PL::R2 <= T) {
+            fft_pass2<P, T, PL::R2, 16, -1>(tf + c, tg + c, ES, j, tw);
+        } else {
+            fft_pass<P, T, PL::R2, 16, -1>(tf + c, ES, j, true, tw);
+            fft_pass<P, T, PL::R2, 16, -1>(tg + c, ES, j, true, tw);
+        }
+    }
     // with s2hat the two transforms are kept for the adjoint ([2][B][P/2][P], column-major: the
     // adjoint's column pass reads each column's P positions in runs)
     float2* kf = s2hat ? s2hat + (size_t)q * P * W : nullptr;
