@@ -353,7 +353,19 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
                 return ((unsigned)yy < (unsigned)NI && (unsigned)xx < (unsigned)NI) ? __ldg(src + (size_t)yy * NI + xx)
                                                                                     : 0.f;
             };
-            const float v00 = at(y0, x0), v01 = at(y0, x0 + 1), v10 = at(y0 + 1, x0), v11 = at(y0 + 1, x0 + 1);
+            float v00, v01, v10, v11;
+            if ((unsigned)x0 < (unsigned)(NI - 1) && (unsigned)y0 < (unsigned)(NI - 1)) {   // all four taps inside
+                const float* s0 = src + (size_t)y0 * NI + x0;
+                v00 = __ldg(s0);
+                v01 = __ldg(s0 + 1);
+                v10 = __ldg(s0 + NI);
+                v11 = __ldg(s0 + NI + 1);
+            } else {
+                v00 = at(y0, x0);
+                v01 = at(y0, x0 + 1);
+                v10 = at(y0 + 1, x0);
+                v11 = at(y0 + 1, x0 + 1);
+            }
             const float dvx = (1.f - fy) * (v01 - v00) + fy * (v11 - v10);
             const float dvy = (1.f - fx) * (v10 - v00) + fx * (v11 - v01);
             contrib += __ldg(d + idx) * (dvx * (py - c) - dvy * (px - c));
@@ -367,16 +379,32 @@ __global__ void __launch_bounds__(kThreads) k_b_rot(DevPlan p, const long long* 
             const float ex0 = (float)mx0 - qx, ey0 = (float)my0 - qy;
             const float dx0 = fmaf(ct, ex0, stn * ey0), dy0 = fmaf(ct, ey0, -stn * ex0);
             float acc = 0.f;
+            if ((unsigned)mx0 < (unsigned)(NI - 2) && (unsigned)my0 < (unsigned)(NI - 2)) {
+                // the whole box inside: no bounds tests, and a tap outside the tent adds 0 * d
+                // (clamped weights), which leaves the sum bitwise as skipping it would
+                const float* dm = d + (size_t)my0 * NI + mx0;
 #pragma unroll
-            for (int oy = 0; oy < 3; ++oy) {
-                const int my = my0 + oy;
-                const float dxr = fmaf(stn, (float)oy, dx0), dyr = fmaf(ct, (float)oy, dy0);
+                for (int oy = 0; oy < 3; ++oy) {
+                    const float dxr = fmaf(stn, (float)oy, dx0), dyr = fmaf(ct, (float)oy, dy0);
 #pragma unroll
-                for (int ox = 0; ox < 3; ++ox) {
-                    const int mx = mx0 + ox;
-                    const float wx = 1.f - fabsf(fmaf(ct, (float)ox, dxr)), wy = 1.f - fabsf(fmaf(-stn, (float)ox, dyr));
-                    if (wx > 0.f && wy > 0.f && (unsigned)my < (unsigned)NI && (unsigned)mx < (unsigned)NI)
-                        acc = fmaf(wy * wx, __ldg(d + (size_t)my * NI + mx), acc);
+                    for (int ox = 0; ox < 3; ++ox) {
+                        const float wx = fmaxf(1.f - fabsf(fmaf(ct, (float)ox, dxr)), 0.f);
+                        const float wy = fmaxf(1.f - fabsf(fmaf(-stn, (float)ox, dyr)), 0.f);
+                        acc = fmaf(wy * wx, __ldg(dm + oy * NI + ox), acc);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int oy = 0; oy < 3; ++oy) {
+                    const int my = my0 + oy;
+                    const float dxr = fmaf(stn, (float)oy, dx0), dyr = fmaf(ct, (float)oy, dy0);
+#pragma unroll
+                    for (int ox = 0; ox < 3; ++ox) {
+                        const int mx = mx0 + ox;
+                        const float wx = 1.f - fabsf(fmaf(ct, (float)ox, dxr)), wy = 1.f - fabsf(fmaf(-stn, (float)ox, dyr));
+                        if (wx > 0.f && wy > 0.f && (unsigned)my < (unsigned)NI && (unsigned)mx < (unsigned)NI)
+                            acc = fmaf(wy * wx, __ldg(d + (size_t)my * NI + mx), acc);
+                    }
                 }
             }
             df[tab[3 * q] + idx] = acc;

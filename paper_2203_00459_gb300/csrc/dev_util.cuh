@@ -143,6 +143,15 @@ __device__ __forceinline__ float rotated_sample_fixed(const float* __restrict__ 
     const float fx = (float)(int)((px >> 16) & 0xFFFFFF) * (1.f / 16777216.f);
     const float fy = (float)(int)((py >> 16) & 0xFFFFFF) * (1.f / 16777216.f);
     float v = 0.f;
+    if ((unsigned)x0 < (unsigned)(n - 1) && (unsigned)y0 < (unsigned)(n - 1)) {
+        // all four taps inside (the same sum, in the same order, without the bounds tests)
+        const float* r = src + (size_t)y0 * n + x0;
+        v += (1.f - fy) * (1.f - fx) * __ldg(r);
+        v += (1.f - fy) * fx * __ldg(r + 1);
+        v += fy * (1.f - fx) * __ldg(r + n);
+        v += fy * fx * __ldg(r + n + 1);
+        return v;
+    }
     const bool xin0 = (unsigned)x0 < (unsigned)n, xin1 = (unsigned)(x0 + 1) < (unsigned)n;
     if ((unsigned)y0 < (unsigned)n) {
         const float* r = src + (size_t)y0 * n;
