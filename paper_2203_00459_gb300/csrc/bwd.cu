@@ -99,14 +99,17 @@ __global__ void __launch_bounds__(kThreads) k_b_rows(DevPlan p, const long long*
     constexpr int NI = ODD ? N - 1 : N, LO = ODD ? 1 : 0;
     if (threadIdx.x == 0) xy_adjoint_scalars(p, xm + (size_t)q * 8, tx, ty, dtx, dty, NI, r);
     __syncthreads();
+    float rv[11];   // the pair's scalars in registers: each of the thread's 32 lags reads them
+#pragma unroll
+    for (int t = 0; t < 11; ++t) rv[t] = r[t];
     const float* c = cxy + (size_t)q * NI * NI + (size_t)(i - LO) * NI - LO;
     const bool oka = i >= LO;
     first_pass_global<P>(sm + k * SL, 1, jt, [&](int x) {
         const int j = x + N / 2 < P ? x + N / 2 : x + N / 2 - P;   // lag column at P-position x
         float2 v = make_float2(0.f, 0.f);
         if (j < N && j >= LO) {
-            if (oka) v.x = dcxy(p, r, __ldg(c + j), i, j, N, dtx, dty);
-            v.y = dcxy(p, r, __ldg(c + NI + j), i + 1, j, N, dtx, dty);
+            if (oka) v.x = dcxy(p, rv, __ldg(c + j), i, j, N, dtx, dty);
+            v.y = dcxy(p, rv, __ldg(c + NI + j), i + 1, j, N, dtx, dty);
         }
         return v;
     });
