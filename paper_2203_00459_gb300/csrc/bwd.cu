@@ -592,20 +592,28 @@ __global__ void __launch_bounds__(kThreads) k_b_polT(DevPlan p, const float2* __
 // d x[y,x] = Re sum_{v, u <= N/2} dF[v,u] exp(+2 pi i (v y + u x)/N): here the inverse column
 // transform, with interior columns halved (a real row transform counts them twice) and the
 // DC/Nyquist columns made Hermitian (only the real part of their row sums counts) so that they
-// can share the packed column 0.  Threads are column-fastest; the first pass forms dF straight
-// from global memory and the last pass stores straight to it.
+// can share the packed column 0.  The first pass forms dF straight from global memory.
+// The inputs are u-major (a column's N values are contiguous): with one warp per column (N = 512)
+// a warp reads 32 consecutive positions, and the transposed result leaves through the tile (each
+// column's sequence at a stride of 2 mod 16 float2 apart, so the row-wise read-back is free of
+// bank conflicts) as runs of C columns; the smaller sides are column-fastest (c = tid mod C) and
+// store straight from the last pass.
+template <int N> __host__ __device__ constexpr bool s1cols_warp() { return FftPlan<N>::T == 32; }
+template <int N> __host__ __device__ constexpr int s1cols_stride() { return (spad(N) + 15) / 16 * 16 + 2; }
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_b_s1cols(DevPlan p, const float2* __restrict__ phs,
                                                        const float2* __restrict__ gmt, float2* __restrict__ gs1,
                                                        int B) {
     grid_dep_wait();   // the previous kernel on the stream has completed (PDL launch)
-    constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = C, W = N / 2;
+    constexpr bool WARP = s1cols_warp<N>();
+    constexpr int T = FftPlan<N>::T, C = kThreads / T, ES = WARP ? 1 : C, W = N / 2, SC = s1cols_stride<N>();
     extern __shared__ float2 sm[];
     const int q = blockIdx.y, s = blockIdx.z, u0 = blockIdx.x * C;
-    const int c = threadIdx.x % C, j = threadIdx.x / C, u = u0 + c;
+    const int c = WARP ? threadIdx.x / T : threadIdx.x % C, j = WARP ? threadIdx.x % T : threadIdx.x / C, u = u0 + c;
+    float2* seq = WARP ? sm + c * SC : sm + c;
     const float* dm = reinterpret_cast<const float*>(gmt + (size_t)q * (W + 1) * N) + s;   // stride 2
     const float2* ph = phs + (size_t)(s * B + q) * (W + 1) * N;
-    first_pass_global<N, +1>(sm + c, ES, j, [&](int v) {
+    first_pass_global<N, +1>(seq, ES, j, [&](int v) {
         if (u != 0) return c_scale(__ldg(ph + (size_t)u * N + v), 0.5f * __ldg(dm + 2 * ((size_t)u * N + v)));
         // packed DC (u = 0) and Nyquist (u = N/2) columns, each made Hermitian
         const int vm = (N - v) & (N - 1);
@@ -618,8 +626,20 @@ __global__ void __launch_bounds__(kThreads) k_b_s1cols(DevPlan p, const float2* 
         return make_float2(sa.x - sb.y, sa.y + sb.x);
     });
     __syncthreads();
-    float2* out = gs1 + (size_t)(s * B + q) * N * W + u;
-    rest_global<N, +1>(sm + c, ES, j, p.tw_n, [&](int y, float2 v) { out[(size_t)y * W] = v; });
+    if constexpr (WARP) {
+        // the last pass writes its outputs back to the positions it read (same thread), then the
+        // tile leaves row by row
+        rest_global<N, +1>(seq, 1, j, p.tw_n, [&](int y, float2 v) { seq[spad(y)] = v; });
+        __syncthreads();
+        float2* out = gs1 + (size_t)(s * B + q) * N * W + u0;
+        for (int idx = threadIdx.x; idx < C * N; idx += kThreads) {
+            const int cc = idx % C, y = idx / C;
+            out[(size_t)y * W + cc] = sm[cc * SC + spad(y)];
+        }
+    } else {
+        float2* out = gs1 + (size_t)(s * B + q) * N * W + u;
+        rest_global<N, +1>(seq, ES, j, p.tw_n, [&](int y, float2 v) { out[(size_t)y * W] = v; });
+    }
 }
 
 // Row part of the half-plane DFT adjoint (a real inverse FFT of each row, two rows per complex
@@ -763,7 +783,7 @@ cudaError_t launch_pose_loss(int n_pairs, const float* pose, const float* gt, in
 template <int L> constexpr size_t b_smem_rows() { return (size_t)(tpb_for(L) / FftPlan<L>::T) * spad(L) * sizeof(float2); }
 template <int P, int C> constexpr size_t b_smem_cols() { return 2 * (size_t)spad(P) * C * sizeof(float2); }
 template <int N> constexpr size_t b_smem_s1cols() {
-    return (size_t)spad(N) * (kThreads / FftPlan<N>::T) * sizeof(float2);
+    return (size_t)(s1cols_warp<N>() ? s1cols_stride<N>() : spad(N)) * (kThreads / FftPlan<N>::T) * sizeof(float2);
 }
 template <int NT, int RC> constexpr size_t b_smem_angle() { return (size_t)spad(NT) * RC * sizeof(float2); }
 
