@@ -1021,12 +1021,16 @@ int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int*
     a.loss_kind = loss_kind;
     a.df = h->d_stage_df;
     a.dg = h->d_stage_dg;
-    // Packed pairs (offsets NULL) of a large enough call run as a pipeline of up to 4 chunks of
-    // pairs: chunk c's copies in (stream s_in) overlap chunk c - 1's training call (the caller's
-    // stream), and chunk c - 1's gradients go back (stream s_out) while chunk c computes.  Each
-    // chunk's loss is normalised by the whole call's pair count, so dpose, pose, df and dg are
-    // those of the one-piece call; the call's loss is then taken over all pairs at the end.
-    const int chunks = (!offsets && n_pairs >= 16) ? std::min(4, n_pairs / 8) : 1;
+    // Packed pairs (offsets NULL) of 16 or more run as a pipeline of 4 chunks of pairs: chunk c's
+    // copies in (stream s_in) overlap chunk c - 1's training call (the caller's stream), and chunk
+    // c - 1's gradients go back (stream s_out) while chunk c computes.  The first and last chunks
+    // hold an eighth of the pairs each and the middle two three eighths: only the first chunk's
+    // copy in and the last one's copy out are not hidden behind a training call, while every
+    // chunk adds the fixed cost of a call.  Each chunk's loss is normalised by the whole call's pair
+    // count, so dpose, pose, df and dg are those of the one-piece call; the call's loss is then
+    // taken over all pairs at the end.
+    const int chunks = (!offsets && n_pairs >= 16) ? 4 : 1;
+    const double bound[5] = {0.0, 0.125, 0.5, 0.875, 1.0};
     if (chunks == 1) {
         const size_t bytes = sizeof(float) * (size_t)total_elems;
         if ((e = cudaMemcpyAsync(h->d_stage_f, f_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
@@ -1059,7 +1063,7 @@ int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int*
         (e = cudaStreamWaitEvent(h->s_out, h->ev_start, 0)) != cudaSuccess)
         return cuda_fail(h, e, "copy stream fork");
     for (int c = 0; c < chunks; ++c) {
-        const int i0 = (int)((long long)n_pairs * c / chunks), i1 = (int)((long long)n_pairs * (c + 1) / chunks);
+        const int i0 = (int)std::lround(n_pairs * bound[c]), i1 = (int)std::lround(n_pairs * bound[c + 1]);
         const size_t e0 = (size_t)off[i0], ne = (size_t)(off[i1] - off[i0]);
         if ((e = cudaMemcpyAsync(h->d_stage_f + e0, f_host + e0, sizeof(float) * ne, cudaMemcpyHostToDevice, h->s_in)) !=
                 cudaSuccess ||
