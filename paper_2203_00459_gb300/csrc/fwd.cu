@@ -248,13 +248,21 @@ __global__ void __launch_bounds__(256) k_theta(DevPlan p, const float2* __restri
     __shared__ float c[NT];
     __shared__ float red[32], red2[64];
     const int q = blockIdx.x;
+    // one CTA per pair reads all nch chunk spectra: 16 loads in flight per thread and bin (the
+    // sum keeps the chunk order)
     for (int k = threadIdx.x; k < NT; k += blockDim.x) {
         float sx = 0.f, sy = 0.f;
-#pragma unroll 8
-        for (int h = 0; h < nch; ++h) {
-            const float2 v = sp[((size_t)q * nch + h) * NT + k];
-            sx += v.x;
-            sy += v.y;
+        for (int h0 = 0; h0 < nch; h0 += 16) {
+            float2 v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                if (h0 + u < nch) v[u] = sp[((size_t)q * nch + h0 + u) * NT + k];
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                if (h0 + u < nch) {
+                    sx += v[u].x;
+                    sy += v[u].y;
+                }
         }
         z[spad(k)] = make_float2(sx, sy);
     }
