@@ -233,7 +233,8 @@ int fmbym_pose_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_
  * copies asynchronous with respect to the host; pageable memory works but copies slower.  A packed
  * call (offsets NULL) of 16 pairs or more runs as a pipeline of 4 chunks of pairs (1/8, 3/8, 3/8
  * and 1/8 of them), the copies in and out on the handle's own streams overlapping the chunks'
- * training calls; the results are
+ * training calls (with a single size, alternate chunks run on a second internal stream in the
+ * second half of the handle's workspace, so consecutive chunks overlap); the results are
  * those of the one-piece call (each chunk's loss is normalised by the call's pair count, and the
  * loss is taken over every pair at the end).  Errors as fmbym_pose_train. */
 int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx,

@@ -48,6 +48,7 @@ struct fmbym_handle {
     int flags = 0;
     std::vector<HostPlan> plans;
     std::vector<void*> ws;        // one workspace region per size, for max_pairs pairs
+    std::vector<size_t> ws_slot;  // byte offset of each size's second slot (half of max_pairs)
     size_t ws_size = 0;
     std::vector<cudaStream_t> side;   // streams of the size groups after the first
     cudaEvent_t ev_fork = nullptr;
@@ -56,6 +57,7 @@ struct fmbym_handle {
     std::vector<GraphEntry> graphs;
     unsigned long long use_clock = 0;
     long long* d_tab = nullptr;   // [max_pairs][3]
+    long long* d_tab2 = nullptr;  // [max_pairs][3] pair table of calls in workspace slot 1
     long long* h_tab = nullptr;   // pinned staging of the pair table
     cudaEvent_t tab_free = nullptr;
     float* d_stage_f = nullptr;   // host-buffer entry points' staging
@@ -63,9 +65,10 @@ struct fmbym_handle {
     float* d_stage_pose = nullptr;
     float* d_stage_df = nullptr;  // [stage_elems] each: the training call's gradients
     float* d_stage_dg = nullptr;
-    float* d_stage_small = nullptr;  // [max_pairs][3] gt, [max_pairs][3] dpose, [1] loss, [1] chunk loss
+    float* d_stage_small = nullptr;  // [max_pairs][3] gt, [max_pairs][3] dpose, [1] loss, [2] chunk losses
     cudaStream_t s_in = nullptr, s_out = nullptr;   // host-buffer training call: copy streams
-    cudaEvent_t ev_start = nullptr, ev_in[4] = {}, ev_done[4] = {};
+    cudaStream_t s_alt = nullptr;                   // host-buffer training call: odd chunks' calls
+    cudaEvent_t ev_start = nullptr, ev_in[4] = {}, ev_done[4] = {}, ev_alt = nullptr;
     unsigned* d_cnt = nullptr;    // [max_pairs] completion counters, zero between launches
     float* d_bpose = nullptr;     // [max_pairs][3] pose recomputed by the adjoint
     float4* d_best = nullptr;     // [max_pairs] running best of the exhaustive search
@@ -419,6 +422,8 @@ struct LaunchArgs {
     float* loss;          // kind 2: the loss (device scalar)
     float* dpose_out;     // kind 2: dL/dpose, written by the loss and read by the adjoint
     int norm_pairs;       // kind 2: the count the loss averages over (0: this call's pairs)
+    int slot;             // workspace slot: 0 = the whole region; 1 = the second half (at most
+                          // (max_pairs + 1) / 2 pairs), so that two calls can run concurrently
 };
 
 // phase 0 launches the forward of one size group, phase 1 its adjoint (after a forward recompute
@@ -426,11 +431,12 @@ struct LaunchArgs {
 cudaError_t launch_group(fmbym_handle* h, const Group& gr, const long long* dtab, const LaunchArgs& a,
                          cudaStream_t s, int phase) {
     const DevPlan& p = h->plans[gr.size_idx].dev;
-    Ws w = ws_carve(p, gr.count, h->ws[gr.size_idx], true);
+    const size_t half = a.slot ? (size_t)(h->max_pairs + 1) / 2 : 0;   // slot 1: the upper halves
+    Ws w = ws_carve(p, gr.count, (char*)h->ws[gr.size_idx] + (a.slot ? h->ws_slot[gr.size_idx] : 0), true);
     w.tr = &h->tracer;
-    w.cnt = h->d_cnt + (size_t)gr.size_idx * h->max_pairs;
-    w.bpose = h->d_bpose;
-    w.fcpose = h->d_fcpose;   // indexed by the call's pair index, which spans every group
+    w.cnt = h->d_cnt + (size_t)gr.size_idx * h->max_pairs + half;
+    w.bpose = h->d_bpose + 3 * half;
+    w.fcpose = h->d_fcpose + 3 * half;   // indexed by the call's pair index, which spans every group
     const long long* tab = dtab + 3 * gr.first;
     if (phase == 0) {
         const bool train = a.kind == 2;
@@ -494,7 +500,7 @@ int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Gr
                                       (long long)(uintptr_t)a.c_xy, (long long)(uintptr_t)a.dpose,
                                       (long long)(uintptr_t)a.df, (long long)(uintptr_t)a.dg,
                                       (long long)(uintptr_t)a.gt, a.loss_kind, (long long)(uintptr_t)a.loss,
-                                      (long long)(uintptr_t)a.dpose_out, a.norm_pairs};
+                                      (long long)(uintptr_t)a.dpose_out, a.norm_pairs, a.slot};
         key.insert(key.end(), h->h_tab, h->h_tab + 3 * (size_t)n_pairs);
         GraphEntry* ge = nullptr;
         for (auto& x : h->graphs)
@@ -503,7 +509,9 @@ int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Gr
             if (h->graphs.size() >= kMaxGraphs) {
                 auto lru = std::min_element(h->graphs.begin(), h->graphs.end(),
                                             [](const GraphEntry& x, const GraphEntry& y) { return x.last_use < y.last_use; });
-                if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+                // the released graph may still run on this stream or on the second slot's
+                if ((e = cudaStreamSynchronize(st)) != cudaSuccess || (e = cudaStreamSynchronize(h->s_alt)) != cudaSuccess)
+                    return cuda_fail(h, e, "cudaStreamSynchronize");
                 cudaGraphExecDestroy(lru->exec);
                 cudaFree(lru->d_tab);
                 h->graphs.erase(lru);
@@ -545,11 +553,12 @@ int run_call(fmbym_handle* h, cudaStream_t st, int n_pairs, const std::vector<Gr
         h->tracer.launches += ge->kernels;
         return FMBYM_OK;
     }
-    if ((e = cudaMemcpyAsync(h->d_tab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) !=
+    long long* dtab = a.slot ? h->d_tab2 : h->d_tab;
+    if ((e = cudaMemcpyAsync(dtab, h->h_tab, sizeof(long long) * 3 * n_pairs, cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return cuda_fail(h, e, "pair table copy");
     if ((e = cudaEventRecord(h->tab_free, st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
-    if ((e = enqueue(h, st, groups, h->d_tab, a, n_pairs)) != cudaSuccess)
+    if ((e = enqueue(h, st, groups, dtab, a, n_pairs)) != cudaSuccess)
         return cuda_fail(h, e, a.kind == 0 ? "forward launch" : a.kind == 1 ? "backward launch" : "training launch");
     return FMBYM_OK;
 }
@@ -693,6 +702,7 @@ void fmbym_destroy(fmbym_handle* h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->cap) cudaStreamDestroy(h->cap);
     cudaFree(h->d_tab);
+    cudaFree(h->d_tab2);
     cudaFree(h->d_stage_f);
     cudaFree(h->d_stage_g);
     cudaFree(h->d_stage_pose);
@@ -701,6 +711,8 @@ void fmbym_destroy(fmbym_handle* h) {
     cudaFree(h->d_stage_small);
     if (h->s_in) cudaStreamDestroy(h->s_in);
     if (h->s_out) cudaStreamDestroy(h->s_out);
+    if (h->s_alt) cudaStreamDestroy(h->s_alt);
+    if (h->ev_alt) cudaEventDestroy(h->ev_alt);
     if (h->ev_start) cudaEventDestroy(h->ev_start);
     for (int c = 0; c < 4; ++c) {
         if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
@@ -758,13 +770,16 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
             fmbym_destroy(h);
             return cuda_fail(nullptr, e, "plan tables");
         }
-        const size_t b = ws_bytes(hp.dev, cfg->max_pairs, true);
+        // the region holds max_pairs pairs, or two slots of (max_pairs + 1) / 2 pairs each
+        const size_t off = (ws_bytes(hp.dev, (cfg->max_pairs + 1) / 2, true) + 255) & ~(size_t)255;
+        const size_t b = std::max(ws_bytes(hp.dev, cfg->max_pairs, true), 2 * off);
         void* w = nullptr;
         if ((e = cudaMalloc(&w, b)) != cudaSuccess || (e = cudaMemset(w, 0, b)) != cudaSuccess) {
             fmbym_destroy(h);
             return cuda_fail(nullptr, e, "workspace allocation");
         }
         h->ws.push_back(w);
+        h->ws_slot.push_back(off);
         h->ws_size += b;
         nmax = std::max(nmax, hp.cfg.n);
     }
@@ -780,6 +795,7 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess ||
         (e = cudaMalloc(&h->d_tab, sizeof(long long) * 3 * cfg->max_pairs)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_tab2, sizeof(long long) * 3 * cfg->max_pairs)) != cudaSuccess ||
         (e = cudaMallocHost(&h->h_tab, sizeof(long long) * 3 * cfg->max_pairs)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->tab_free, cudaEventDisableTiming)) != cudaSuccess) {
         fmbym_destroy(h);
@@ -791,9 +807,11 @@ int fmbym_create(fmbym_handle** out, const fmbym_config* cfg) {
         (e = cudaMalloc(&h->d_stage_pose, sizeof(float) * 3 * cfg->max_pairs)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_df, sizeof(float) * h->stage_elems)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_stage_dg, sizeof(float) * h->stage_elems)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_stage_small, sizeof(float) * (6 * (size_t)cfg->max_pairs + 2))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_stage_small, sizeof(float) * (6 * (size_t)cfg->max_pairs + 3))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->s_alt, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_alt, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_cnt, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
         (e = cudaMemset(h->d_cnt, 0, sizeof(unsigned) * cfg->max_pairs * cfg->n_sizes)) != cudaSuccess ||
@@ -1028,7 +1046,9 @@ int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int*
     // copy in and the last one's copy out are not hidden behind a training call, while every
     // chunk adds the fixed cost of a call.  Each chunk's loss is normalised by the whole call's pair
     // count, so dpose, pose, df and dg are those of the one-piece call; the call's loss is then
-    // taken over all pairs at the end.
+    // taken over all pairs at the end.  When every pair has one size, the odd chunks run on a
+    // second stream in the workspace's second slot, so that a chunk's first kernels overlap the
+    // previous chunk's last ones (each call ends in kernels of one CTA per pair).
     const int chunks = (!offsets && n_pairs >= 16) ? 4 : 1;
     const double bound[5] = {0.0, 0.125, 0.5, 0.875, 1.0};
     if (chunks == 1) {
@@ -1058,11 +1078,15 @@ int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int*
         const long long nn = (long long)h->plans[size_idx ? size_idx[i] : 0].cfg.n;
         off[i + 1] = off[i] + nn * nn;
     }
+    const bool two = groups.size() == 1;
     if ((e = cudaEventRecord(h->ev_start, st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(h->s_in, h->ev_start, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(h->s_out, h->ev_start, 0)) != cudaSuccess)
+        (e = cudaStreamWaitEvent(h->s_out, h->ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h->s_alt, h->ev_start, 0)) != cudaSuccess)
         return cuda_fail(h, e, "copy stream fork");
     for (int c = 0; c < chunks; ++c) {
+        const int slot = two ? (c & 1) : 0;
+        cudaStream_t cs = slot ? h->s_alt : st;
         const int i0 = (int)std::lround(n_pairs * bound[c]), i1 = (int)std::lround(n_pairs * bound[c + 1]);
         const size_t e0 = (size_t)off[i0], ne = (size_t)(off[i1] - off[i0]);
         if ((e = cudaMemcpyAsync(h->d_stage_f + e0, f_host + e0, sizeof(float) * ne, cudaMemcpyHostToDevice, h->s_in)) !=
@@ -1072,7 +1096,7 @@ int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int*
             (e = cudaMemcpyAsync(d_gt + 3 * (size_t)i0, gt_host + 3 * (size_t)i0, sizeof(float) * 3 * (i1 - i0),
                                  cudaMemcpyHostToDevice, h->s_in)) != cudaSuccess ||
             (e = cudaEventRecord(h->ev_in[c], h->s_in)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(st, h->ev_in[c], 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(cs, h->ev_in[c], 0)) != cudaSuccess)
             return cuda_fail(h, e, "host-to-device copy");
         std::vector<Group> cg;
         rc = make_table(h, i1 - i0, size_idx ? size_idx + i0 : nullptr, off.data() + i0, cg, nullptr);
@@ -1081,11 +1105,12 @@ int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int*
         ac.gt = d_gt + 3 * (size_t)i0;
         ac.pose = h->d_stage_pose + 3 * (size_t)i0;
         ac.dpose_out = d_dpose + 3 * (size_t)i0;
-        ac.loss = d_chunk_loss;
+        ac.loss = d_chunk_loss + slot;
         ac.norm_pairs = n_pairs;
-        rc = run_call(h, st, i1 - i0, cg, ac);
+        ac.slot = slot;
+        rc = run_call(h, cs, i1 - i0, cg, ac);
         if (rc != FMBYM_OK) return rc;
-        if ((e = cudaEventRecord(h->ev_done[c], st)) != cudaSuccess ||
+        if ((e = cudaEventRecord(h->ev_done[c], cs)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(h->s_out, h->ev_done[c], 0)) != cudaSuccess ||
             (e = cudaMemcpyAsync(df_host + e0, h->d_stage_df + e0, sizeof(float) * ne, cudaMemcpyDeviceToHost,
                                  h->s_out)) != cudaSuccess ||
@@ -1093,7 +1118,9 @@ int fmbym_pose_train_host(fmbym_handle* h, void* stream, int n_pairs, const int*
                                  h->s_out)) != cudaSuccess)
             return cuda_fail(h, e, "device-to-host copy");
     }
-    // the call's loss over every pair (the chunks' losses were partial)
+    // the call's loss over every pair (the chunks' losses were partial), after both streams' chunks
+    if ((e = cudaEventRecord(h->ev_alt, h->s_alt)) != cudaSuccess || (e = cudaStreamWaitEvent(st, h->ev_alt, 0)) != cudaSuccess)
+        return cuda_fail(h, e, "stream join");
     if ((e = launch_pose_loss(n_pairs, h->d_stage_pose, d_gt, loss_kind, d_loss, nullptr, &h->tracer, st)) !=
             cudaSuccess ||
         (e = cudaMemcpyAsync(pose_host, h->d_stage_pose, sizeof(float) * 3 * n_pairs, cudaMemcpyDeviceToHost, st)) !=

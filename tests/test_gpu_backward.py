@@ -273,11 +273,15 @@ def test_host_buffer_training_call_equals_the_device_call(lib):
     s.close()
 
 
+@pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("sizes", [(0,) * 24, (0, 1) * 8])
-def test_pipelined_host_buffer_training_call(lib, sizes):
+def test_pipelined_host_buffer_training_call(lib, sizes, graph):
     """Packed calls of 16 pairs or more run the host-buffer training call as a pipeline of chunks
-    (copies in and out on their own streams, overlapping the chunks' training calls); pose, loss,
-    df and dg must be bitwise those of fmbym_pose_train on device buffers, also with mixed sizes."""
+    (copies in and out on their own streams, overlapping the chunks' training calls; with one size,
+    alternate chunks on a second stream in the workspace's second slot); pose, loss, df and dg must
+    be bitwise those of fmbym_pose_train on device buffers, also with mixed sizes, launched directly
+    or from captured graphs."""
+    from paper_2203_00459_gb300 import _lib
     from paper_2203_00459_gb300.search import PoseSearch
     cfgs = [lib.size_cfg(128, 128, 64), lib.size_cfg(256, 400, 128)]
     names = ["single128", "batch256"]
@@ -285,13 +289,13 @@ def test_pipelined_host_buffer_training_call(lib, sizes):
     F = np.concatenate([f.ravel() for f, _, _ in scans])
     G = np.concatenate([g.ravel() for _, g, _ in scans])
     GT = np.concatenate([p for _, _, p in scans]).astype(np.float32)
-    s = PoseSearch(cfgs, max_pairs=len(sizes))
+    s = PoseSearch(cfgs, max_pairs=len(sizes), flags=_lib.FLAG_GRAPH if graph else 0)
     si = list(sizes)
     pose, loss, _, df, dg = s.pose_train(torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda(),
                                          torch.from_numpy(GT).cuda(), kind=2, size_idx=si)
     torch.cuda.synchronize()
     fh, gh, gth = torch.from_numpy(F).pin_memory(), torch.from_numpy(G).pin_memory(), torch.from_numpy(GT).pin_memory()
-    for _ in range(2):
+    for _ in range(3):
         ph, lh, dfh, dgh = s.pose_train_host(fh, gh, gth, kind=2, size_idx=si)
         assert torch.equal(ph, pose.cpu()) and torch.equal(lh, loss.cpu())
         assert torch.equal(dfh, df.cpu()) and torch.equal(dgh, dg.cpu())
