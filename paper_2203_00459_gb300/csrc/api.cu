@@ -870,6 +870,48 @@ int fmbym_set_tuning(fmbym_handle* h, int size, const int* values) {
     return FMBYM_OK;
 }
 
+// A packed call of one size and 16 or more pairs runs as two halves on two streams (the caller's
+// and an internal one) in the workspace's two slots, so that each half's kernels overlap the
+// other's ramps, tails and one-CTA-per-pair kernels.  Per pair the results are those of one call:
+// in a training call each half's loss gradient is normalised by the whole call's pair count, and
+// the call's loss is taken over all pairs once both halves are done.
+bool halves_apply(const fmbym_handle* h, const long long* offsets, const std::vector<Group>& groups, int n_pairs) {
+    return !offsets && groups.size() == 1 && n_pairs >= 16 && !h->tracer.on;
+}
+
+int run_halves(fmbym_handle* h, cudaStream_t st, int n_pairs, const int* size_idx, const LaunchArgs& a) {
+    cudaError_t e;
+    if ((e = cudaEventRecord(h->ev_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(h->s_alt, h->ev_start, 0)) != cudaSuccess)
+        return cuda_fail(h, e, "stream fork");
+    const fmbym_size_cfg& c = h->plans[size_idx ? size_idx[0] : 0].cfg;
+    const long long nn = (long long)c.n * c.n;
+    for (int k = 0; k < 2; ++k) {
+        const int i0 = k ? n_pairs / 2 : 0, i1 = k ? n_pairs : n_pairs / 2;
+        std::vector<long long> off(i1 - i0);
+        for (int i = i0; i < i1; ++i) off[i - i0] = (long long)i * nn;
+        std::vector<Group> cg;
+        int rc = make_table(h, i1 - i0, size_idx ? size_idx + i0 : nullptr, off.data(), cg, nullptr);
+        if (rc != FMBYM_OK) return rc;
+        LaunchArgs ak = a;   // per-pair outputs and inputs indexed by the pair: shifted to the half
+        if (ak.pose) ak.pose += 3 * (size_t)i0;
+        if (ak.c_theta) ak.c_theta += (size_t)i0 * c.n_theta;
+        if (ak.dpose) ak.dpose += 3 * (size_t)i0;
+        if (a.kind == 2) {
+            ak.gt += 3 * (size_t)i0;
+            ak.dpose_out += 3 * (size_t)i0;
+            ak.loss = h->d_stage_small + 6 * (size_t)h->max_pairs + 1 + k;   // the halves' partial losses
+            ak.norm_pairs = n_pairs;
+        }
+        ak.slot = k;
+        if ((rc = run_call(h, k ? h->s_alt : st, i1 - i0, cg, ak)) != FMBYM_OK) return rc;
+    }
+    if ((e = cudaEventRecord(h->ev_alt, h->s_alt)) != cudaSuccess || (e = cudaStreamWaitEvent(st, h->ev_alt, 0)) != cudaSuccess)
+        return cuda_fail(h, e, "stream join");
+    if (a.kind == 2 && (e = launch_pose_loss(n_pairs, a.pose, a.gt, a.loss_kind, a.loss, nullptr, &h->tracer, st)) != cudaSuccess)
+        return cuda_fail(h, e, "loss");
+    return FMBYM_OK;
+}
+
 int fmbym_pose(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
                const float* f, const float* g, float* pose, float* c_theta, float* c_xy) {
     if (!h) return fail(nullptr, FMBYM_ERR_INVALID_ARG, "handle is NULL");
@@ -888,7 +930,8 @@ int fmbym_pose(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, 
     a.pose = pose;
     a.c_theta = c_theta;
     a.c_xy = c_xy;
-    return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
+    if (!halves_apply(h, offsets, groups, n_pairs)) return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
+    return run_halves(h, (cudaStream_t)stream, n_pairs, size_idx, a);
 }
 
 int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
@@ -909,7 +952,8 @@ int fmbym_pose_backward(fmbym_handle* h, void* stream, int n_pairs, const int* s
     a.dpose = dpose;
     a.df = df;
     a.dg = dg;
-    return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
+    if (!halves_apply(h, offsets, groups, n_pairs)) return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
+    return run_halves(h, (cudaStream_t)stream, n_pairs, size_idx, a);
 }
 
 int fmbym_pose_train(fmbym_handle* h, void* stream, int n_pairs, const int* size_idx, const long long* offsets,
@@ -936,7 +980,9 @@ int fmbym_pose_train(fmbym_handle* h, void* stream, int n_pairs, const int* size
     a.dpose_out = dpose;
     a.df = df;
     a.dg = dg;
-    return run_call(h, (cudaStream_t)stream, n_pairs, groups, a);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!halves_apply(h, offsets, groups, n_pairs)) return run_call(h, st, n_pairs, groups, a);
+    return run_halves(h, st, n_pairs, size_idx, a);
 }
 
 int fmbym_pose_exhaustive(fmbym_handle* h, void* stream, int n_pairs, int size, const long long* offsets,
