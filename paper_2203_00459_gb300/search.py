@@ -138,7 +138,10 @@ class PoseSearch:
         return lay
 
     def _layout(self, f, size_idx, offsets):
-        """Returns (n_pairs, size_idx array or None, offsets array or None, n_theta list, N list)."""
+        """Returns (n_pairs, size_idx array or None, offsets array or None, n_theta list, N list).
+        Offsets without size_idx place pairs of size 0."""
+        if size_idx is None and offsets is not None:
+            size_idx = np.zeros(len(offsets), np.int32)
         if size_idx is None:
             if f.dim() != 3:
                 raise ValueError("f must be [B, N, N] when size_idx is not given")

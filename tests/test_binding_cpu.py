@@ -132,3 +132,12 @@ def test_checks_accept_good_buffers():
     h = torch.zeros(5)
     assert check_host_tensor(h, "h", numel=5) is h
     assert search.check_device_tensor is check_device_tensor
+
+
+def test_offsets_without_size_idx_place_pairs_of_size_0(handle):
+    """Offsets given without size_idx are honoured (pairs of the handle's first size), not dropped."""
+    f = torch.zeros((3, 128, 128))
+    n_pairs, si, off, nts, ns = handle._layout(f, None, [0, 128 * 128 * 2])
+    assert n_pairs == 2 and list(si) == [0, 0] and list(off) == [0, 128 * 128 * 2] and ns == [128, 128]
+    n_pairs, si, off, _, _ = handle._layout(f, None, None)
+    assert n_pairs == 3 and si is None and off is None
