@@ -112,7 +112,10 @@ enum fmbym_tune_knob { FMBYM_TUNE_COL_TILE = 0, FMBYM_TUNE_ANGLE_RADII = 1, FMBY
 /* Handle configuration: n_sizes size configurations (host array, copied by fmbym_create),
  * the largest number of pairs one call may carry, and flags (fmbym_flags).  Pairs of different
  * sizes in one call run as concurrent groups, one per size, on internal streams forked from and
- * joined back to the caller's stream. */
+ * joined back to the caller's stream.  A packed call (offsets NULL) of one size and 16 pairs or
+ * more runs as two halves, one on the caller's stream and one on an internal stream forked from
+ * and joined back to it, each in its own half of the handle's workspace; the results are those
+ * of one call, pair by pair.  Calls on one handle must not overlap (one stream at a time). */
 typedef struct fmbym_config {
     int n_sizes;
     const fmbym_size_cfg* sizes;
